@@ -1,0 +1,130 @@
+"""Seeded synthetic inputs and workload shapes.
+
+This module holds no HE arithmetic: it draws integers from a counter-based
+generator and lists layer shapes.  It is the one module that both the
+product's callers (tests, bench) and the CPU oracle's callers use, so that
+both sides see the same inputs.
+
+Generator: SplitMix64 (G. Steele, D. Lea, C. Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014), used counter-style: word i of
+stream (seed, sid) is mix64(base + (i + 1) * 0x9E3779B97F4A7C15) with
+base = (seed << 32) ^ sid.  Values in a range [0, m) take the high 32 bits
+times m, shifted down by 32 (multiply-shift range reduction).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def sid(name: str) -> int:
+    """Stable 32-bit stream id of a name (FNV-1a)."""
+    h = 0x811C9DC5
+    for ch in name.encode():
+        h = ((h ^ ch) * 0x01000193) & 0xFFFFFFFF
+    return h
+
+
+def u64(seed: int, stream: int | str, n: int) -> np.ndarray:
+    """n SplitMix64 words of stream (seed, stream)."""
+    if isinstance(stream, str):
+        stream = sid(stream)
+    base = np.uint64(((int(seed) & 0xFFFFFFFF) << 32) ^ (int(stream) & 0xFFFFFFFF))
+    with np.errstate(over="ignore"):
+        z = base + (np.arange(1, n + 1, dtype=np.uint64) * _GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def below(seed: int, stream, n: int, m: int) -> np.ndarray:
+    """n integers uniform in [0, m) (m < 2^32) as uint64."""
+    hi = u64(seed, stream, n) >> np.uint64(32)
+    return (hi * np.uint64(m)) >> np.uint64(32)
+
+
+def ints(seed: int, stream, shape, lo: int, hi: int) -> np.ndarray:
+    """Integers uniform in [lo, hi] (inclusive), int64, given shape."""
+    n = int(np.prod(shape)) if len(shape) else 1
+    v = below(seed, stream, n, hi - lo + 1).astype(np.int64) + lo
+    return v.reshape(shape)
+
+
+def residues(seed: int, stream, shape, primes: list[int]) -> np.ndarray:
+    """uint32 array of the given shape whose axis -2 is the limb axis (length
+    len(primes)); entries uniform in [0, q_l)."""
+    shape = tuple(shape)
+    L, N = shape[-2], shape[-1]
+    assert L == len(primes)
+    outer = int(np.prod(shape[:-2])) if len(shape) > 2 else 1
+    out = np.empty((outer, L, N), dtype=np.uint32)
+    for l, q in enumerate(primes):
+        out[:, l, :] = below(seed, f"{stream}/limb{l}", outer * N, q).reshape(outer, N)
+    return out.reshape(shape)
+
+
+def ternary(seed: int, stream, n: int) -> np.ndarray:
+    """Uniform {-1, 0, 1} (a ternary secret)."""
+    return below(seed, stream, n, 3).astype(np.int64) - 1
+
+
+def cbd(seed: int, stream, n: int, eta: int = 3) -> np.ndarray:
+    """Centered binomial: sum of eta bits minus sum of eta bits."""
+    w = u64(seed, stream, n)
+    a = np.zeros(n, dtype=np.int64)
+    for i in range(eta):
+        a += ((w >> np.uint64(i)) & np.uint64(1)).astype(np.int64)
+        a -= ((w >> np.uint64(i + 32)) & np.uint64(1)).astype(np.int64)
+    return a
+
+
+def v_poly(seed: int, stream, n: int) -> np.ndarray:
+    """Coefficients 0, 1, -1 with probability 1/2, 1/4, 1/4."""
+    u = below(seed, stream, n, 4).astype(np.int64)
+    return np.where(u < 2, 0, np.where(u == 2, 1, -1))
+
+
+# ----------------------------------------------------------------------------
+# Workload shapes (plain-20 on CIFAR-shaped inputs, only the shapes are used)
+# ----------------------------------------------------------------------------
+
+def plain20_conv_layers(width: int = 1) -> list[dict]:
+    """The 19 3x3 Conv layers of a plain-20 network on 32x32x3 inputs:
+    3->16w @32x32, 6x 16w->16w @32x32, 16w->32w stride 2 (evaluated on
+    32x32), 5x 32w->32w @16x16, 32w->64w stride 2 (on 16x16),
+    5x 64w->64w @8x8."""
+    c1, c2, c3 = 16 * width, 32 * width, 64 * width
+    L = [dict(ci=3, co=c1, h=32, w=32, stride=1)]
+    L += [dict(ci=c1, co=c1, h=32, w=32, stride=1) for _ in range(6)]
+    L += [dict(ci=c1, co=c2, h=32, w=32, stride=2)]
+    L += [dict(ci=c2, co=c2, h=16, w=16, stride=1) for _ in range(5)]
+    L += [dict(ci=c2, co=c3, h=16, w=16, stride=2)]
+    L += [dict(ci=c3, co=c3, h=8, w=8, stride=1) for _ in range(5)]
+    for d in L:
+        d.update(fh=3, fw=3, pad=1)
+    return L
+
+
+WORKLOADS = {
+    "conv1": dict(N=2048, L=1, t=65537, B=1,
+                  conv=[dict(ci=3, co=4, h=16, w=16, stride=1, fh=3, fw=3, pad=1)],
+                  fc=None, wlo=-8, whi=7),
+    "plain20_c10": dict(N=8192, L=3, t=65537, B=1, conv=plain20_conv_layers(1),
+                        fc=dict(n_in=64, n_out=10), wlo=-128, whi=127),
+    "plain20_c100_wide4": dict(N=16384, L=6, t=65537, B=8, conv=plain20_conv_layers(4),
+                               fc=dict(n_in=256, n_out=100), wlo=-128, whi=127),
+}
+
+
+def conv_weights(seed: int, stream, co: int, ci: int, fh: int, fw: int,
+                 lo: int, hi: int) -> np.ndarray:
+    return ints(seed, stream, (co, ci, fh, fw), lo, hi).astype(np.int8)
+
+
+def fc_weights(seed: int, stream, n_out: int, n_in: int, lo: int, hi: int) -> np.ndarray:
+    return ints(seed, stream, (n_out, n_in), lo, hi).astype(np.int8)
