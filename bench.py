@@ -1,0 +1,507 @@
+#!/usr/bin/env python
+"""Benchmark: encrypted Conv+FC layers/sec and plain-20 ms/inference (p50/p99).
+
+Workload (default): the plain-20 CIFAR-10 shape at batch 1 -- 19 3x3 Conv
+layers (16 ch at 32x32, 32 ch at 16x16, 64 ch at 8x8, the two stride-2
+transitions evaluated at stride 1) and FC 64->10; ring N = 8192, 3 RNS limbs
+of 30-bit primes, t = 65537; int8 weights uniform in [-128, 127]; every layer
+input a fresh uniform ciphertext (c0, c1) in every limb.  One step = one
+inference = the 20 server-side layer calls.
+
+Forms measured:
+  graph  the 20 independent layer calls captured once in a CUDA graph over
+         several streams (input NTTs and channel kernels run concurrently),
+         replayed once per step -- the headline `value`;
+  plain  one layer at a time on one stream, CUDA events around every launch
+         (the per-kernel durations behind the roofline figures).
+Both rotate over 3 model replicas and 3 input sets (> 2x the 129 MB L2), so no
+step reads weights another step left in L2.
+
+--impl reference times the CPU oracle (its independent NTT tier, all host
+cores) on a bounded sample of the same layers.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "encrypted Conv+FC layers/sec and plain-20 ms/inference (p50/p99) vs plain GPU form"
+L2_BYTES = 129 * 1024 * 1024
+SEED = 2
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+
+def workload(name: str):
+    from paper_2409_05205_gb300 import synth
+    wl = dict(synth.WORKLOADS[name])
+    wl["name"] = name
+    return wl
+
+
+def layer_list(wl):
+    out = [dict(kind="conv", **d) for d in wl["conv"]]
+    if wl["fc"]:
+        out.append(dict(kind="fc", **wl["fc"]))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sms)) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ----------------------------------------------------------------------------
+# our GPU arm
+# ----------------------------------------------------------------------------
+
+class Model:
+    """One replica of the network's packed banks (device-resident)."""
+
+    def __init__(self, H, p, wl, layers, rep):
+        from paper_2409_05205_gb300 import synth
+        self.H = H
+        self.banks = []
+        for i, Ld in enumerate(layers):
+            if Ld["kind"] == "conv":
+                F = synth.conv_weights(SEED + rep, f"w{i}", Ld["co"], Ld["ci"], 3, 3, wl["wlo"], wl["whi"])
+                self.banks.append(H.he_pack_filters(p, Ld, F))
+            else:
+                W = synth.fc_weights(SEED + rep, f"w{i}", Ld["n_out"], Ld["n_in"], wl["wlo"], wl["whi"])
+                Bv = synth.ints(SEED + rep, f"b{i}", (Ld["n_out"],), -1000, 1000)
+                self.banks.append(H.he_pack_fc(p, Ld["n_in"], Ld["n_out"], W, Bv))
+
+    def free(self):
+        for f in self.banks:
+            self.H.he_filters_destroy(f)
+
+
+class Arm:
+    def __init__(self, wl, device: int, replicas: int = 3):
+        import torch
+        from paper_2409_05205_gb300 import build
+        from paper_2409_05205_gb300 import he as H
+        from paper_2409_05205_gb300 import synth
+        build.build()
+        self.torch, self.H = torch, H
+        self.wl = wl
+        self.N, self.L, self.B = wl["N"], wl["L"], wl["B"]
+        self.layers = layer_list(wl)
+        self.p = H.he_params_create(self.N, self.L, None, wl["t"], device)
+        ps = H.he_params_primes(self.p, self.L)
+        N, L, B = self.N, self.L, self.B
+        # per-layer geometry
+        self.geo = []
+        for Ld in self.layers:
+            if Ld["kind"] == "conv":
+                lay = H.he_conv_layout_query(self.p, Ld)
+                nin = B * lay["G"] * 2 * L * N
+                nout = B * lay["H"] * 2 * L * N
+                wbytes = Ld["co"] * lay["G"] * L * N * 4
+                self.geo.append(dict(lay=lay, nin=nin, nout=nout, npoly=B * lay["G"] * 2,
+                                     wbytes=wbytes))
+            else:
+                fl = H.he_fc_layout_query(self.p, Ld["n_in"], Ld["n_out"])
+                self.geo.append(dict(lay=fl, nin=B * 2 * L * N, nout=B * fl["P_fc"] * 2 * L * N,
+                                     npoly=B * 2, wbytes=fl["P_fc"] * L * N * 4))
+        self.models = [Model(H, self.p, wl, self.layers, r) for r in range(replicas)]
+        # inputs / NTT buffers / outputs per replica (device resident)
+        self.x, self.xn, self.y = [], [], []
+        for r in range(replicas):
+            xs, xns, ys = [], [], []
+            for i, g in enumerate(self.geo):
+                shape = (g["nin"] // (L * N), L, N)
+                a = synth.residues(SEED + 10 * r, f"x{i}", shape, ps)
+                xs.append(torch.from_numpy(a.view(np.int32).ravel()).cuda())
+                xns.append(torch.empty(g["nin"], dtype=torch.int32, device="cuda"))
+                ys.append(torch.empty(g["nout"], dtype=torch.int32, device="cuda"))
+            self.x.append(xs)
+            self.xn.append(xns)
+            self.y.append(ys)
+        self.R = replicas
+        torch.cuda.synchronize()
+
+    # one layer: input NTT (K1) then the channel kernel (K2 / K4) on NTT input
+    def _layer(self, r, i, stream, ev=None):
+        H = self.H
+        g, Ld = self.geo[i], self.layers[i]
+        if ev is not None:
+            ev[0].record(stream)
+        H.he_ntt_forward(self.p, self.x[r][i], self.xn[r][i], g["npoly"], stream)
+        if ev is not None:
+            ev[1].record(stream)
+        if Ld["kind"] == "conv":
+            H.he_conv_layer(self.p, self.models[r].banks[i], self.xn[r][i], H.HE_NTT, self.y[r][i],
+                            H.HE_OUT_EXTRACTED, self.B, stream)
+        else:
+            H.he_fc_layer(self.p, self.models[r].banks[i], self.xn[r][i], H.HE_NTT, self.y[r][i],
+                          H.HE_OUT_EXTRACTED, self.B, stream)
+        if ev is not None:
+            ev[2].record(stream)
+
+    def step_plain(self, k, stream, evs=None):
+        r = k % self.R
+        for i in range(len(self.layers)):
+            self._layer(r, i, stream, None if evs is None else evs[i])
+
+    def capture_graphs(self, nstreams=8):
+        torch = self.torch
+        self.graphs = []
+        main = torch.cuda.Stream()
+        side = [torch.cuda.Stream() for _ in range(nstreams)]
+        for r in range(self.R):
+            g = torch.cuda.CUDAGraph()
+            # warm the kernels' attributes outside capture
+            with torch.cuda.stream(main):
+                self.step_plain(r, main)
+            torch.cuda.synchronize()
+            with torch.cuda.graph(g, stream=main):
+                fork = torch.cuda.Event()
+                fork.record(main)
+                joins = []
+                for si, s in enumerate(side):
+                    s.wait_event(fork)
+                # largest layers first, round-robin over streams
+                order = sorted(range(len(self.layers)), key=lambda i: -self.geo[i]["wbytes"])
+                for n, i in enumerate(order):
+                    s = side[n % nstreams]
+                    self._layer(r, i, s)
+                for s in side:
+                    e = torch.cuda.Event()
+                    e.record(s)
+                    joins.append(e)
+                for e in joins:
+                    main.wait_event(e)
+            self.graphs.append(g)
+        torch.cuda.synchronize()
+
+    def algorithmic(self):
+        """Algorithmic bytes per inference of the channel kernels and of the
+        input NTTs (read + write), and the NTT butterfly count."""
+        N, L, B = self.N, self.L, self.B
+        ch_bytes, ntt_bytes, bfly = 0, 0, 0
+        logN = N.bit_length() - 1
+        for g, Ld in zip(self.geo, self.layers):
+            ch_bytes += g["wbytes"] + (g["nin"] + g["nout"]) * 4
+            ntt_bytes += 2 * g["nin"] * 4
+            bfly += g["npoly"] * L * (N // 2) * logN
+        return ch_bytes, ntt_bytes, bfly
+
+    def free(self):
+        for m in self.models:
+            m.free()
+        self.H.he_params_destroy(self.p)
+
+
+def run_ours(args, rank, world, device):
+    import torch
+    wl = workload(args.workload)
+    arm = Arm(wl, device)
+    nl = len(arm.layers)
+    stream = torch.cuda.Stream()
+    K, W = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---------------- plain form: one layer at a time, events per launch
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nl)] for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            arm.step_plain(k, stream)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for k in range(K):
+            step_ev[k][0].record(stream)
+            arm.step_plain(k, stream, evs[k])
+            step_ev[k][1].record(stream)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    plain_ms = t0.elapsed_time(t1)
+    plain_steps = [a.elapsed_time(b) for a, b in step_ev]
+    ntt_ms = sum(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(K) for i in range(nl))
+    ch_ms = sum(evs[k][i][1].elapsed_time(evs[k][i][2]) for k in range(K) for i in range(nl))
+
+    # ---------------- graph form: all layers of a step in one graph launch
+    arm.capture_graphs()
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            arm.graphs[k % arm.R].replay()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = ClockSampler(device)
+    clocks.start()
+    g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for k in range(K):
+            g_ev[k][0].record(stream)
+            arm.graphs[k % arm.R].replay()
+            g_ev[k][1].record(stream)
+        t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    graph_ms = t0.elapsed_time(t1)
+    graph_steps = [a.elapsed_time(b) for a, b in g_ev]
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([graph_ms, plain_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        graph_ms, plain_ms = float(tt[0]), float(tt[1])
+
+    # ---------------- e2e: host buffers, H2D + layers + D2H every step
+    e2e = run_e2e(arm, args, stream)
+
+    ch_bytes, ntt_bytes, bfly = arm.algorithmic()
+    hbm, peak_src = _peaks()
+    ch_gbs = ch_bytes * K / (ch_ms * 1e-3) / 1e9
+    res = {
+        "metric": METRIC, "value": nl * K * world / (graph_ms * 1e-3), "unit": "layers/s",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": graph_ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 (exact residues mod 30-bit primes)", "data": "synthetic",
+        "config": {"workload": wl["name"], "N": arm.N, "L": arm.L, "B": arm.B, "t": wl["t"],
+                   "layers_per_step": nl, "form": "graph (20 independent layer calls, 8 streams)",
+                   "l2": "rotates 3 model replicas + 3 input sets (> 2x L2); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(graph_steps, 50)),
+                       "p99": float(np.percentile(graph_steps, 99))},
+        "plain_form": {"value": nl * K * world / (plain_ms * 1e-3), "unit": "layers/s",
+                       "ms_per_step": plain_ms / K,
+                       "latency_ms": {"p50": float(np.percentile(plain_steps, 50)),
+                                      "p99": float(np.percentile(plain_steps, 99))},
+                       "kernel_ms_per_step": {"input_ntt": ntt_ms / K, "channel": ch_ms / K}},
+        "roofline": {"kernel": "channel MAC + folded INTT + extraction (plain form, per-launch events)",
+                     "bound": "hbm", "achieved": ch_gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": ch_gbs / hbm, "peak_source": peak_src,
+                     "algorithmic_bytes_per_step": ch_bytes, "traffic": None},
+        "ntt": {"ms_per_step": ntt_ms / K, "butterflies_per_step": bfly,
+                "gbfly_per_s": bfly * K / (ntt_ms * 1e-3) / 1e9, "bytes_per_step": ntt_bytes},
+        "e2e": e2e,
+        "gpu_launches": 2 * nl * K,
+        "clocks": clk,
+    }
+    arm.free()
+    return res
+
+
+def run_e2e(arm, args, stream):
+    torch = arm.torch
+    K = max(3, args.steps // 2)
+    hx = [torch.empty(g["nin"], dtype=torch.int32, pin_memory=True) for g in arm.geo]
+    hy = [torch.empty(g["nout"], dtype=torch.int32, pin_memory=True) for g in arm.geo]
+    for i in range(len(hx)):
+        hx[i].copy_(arm.x[0][i].cpu())
+    h2d = sum(g["nin"] * 4 for g in arm.geo)
+    d2h = sum(g["nout"] * 4 for g in arm.geo)
+    H = arm.H
+
+    def step(r):
+        for i, Ld in enumerate(arm.layers):
+            arm.x[r][i].copy_(hx[i], non_blocking=True)
+        for i, Ld in enumerate(arm.layers):
+            if Ld["kind"] == "conv":
+                H.he_conv_layer(arm.p, arm.models[r].banks[i], arm.x[r][i], H.HE_COEFF, arm.y[r][i],
+                                H.HE_OUT_EXTRACTED, arm.B, stream)
+            else:
+                H.he_fc_layer(arm.p, arm.models[r].banks[i], arm.x[r][i], H.HE_COEFF, arm.y[r][i],
+                              H.HE_OUT_EXTRACTED, arm.B, stream)
+        for i in range(len(arm.layers)):
+            hy[i].copy_(arm.y[r][i], non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for k in range(3):
+            step(k % arm.R)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(K):
+            step(k % arm.R)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": len(arm.layers) * K / dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": K,
+            "how": "pinned host inputs -> H2D, he_conv_layer/he_fc_layer (coefficient-domain input), "
+                   "D2H of every output, one stream, wall clock"}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_layers_per_s(wl, budget_s: float, max_layers: int | None = None, start: int = 0):
+    """Runs the oracle's NTT tier over the workload's layers (cycling, from
+    layer `start`) until the time budget is spent or max_layers are done.
+    Returns (layers/s, layers done, threads)."""
+    from oracle import oracle as O
+    from paper_2409_05205_gb300 import synth
+    N, L, B = wl["N"], wl["L"], wl["B"]
+    ps = O.select_primes(N, L)
+    psis = [O.root_2n(q, N) for q in ps]
+    layers = layer_list(wl)
+    done, t0 = 0, time.perf_counter()
+    while True:
+        Ld = layers[(start + done) % len(layers)]
+        if Ld["kind"] == "conv":
+            lay = O.conv_layout(N, Ld["ci"], Ld["co"], Ld["h"], Ld["w"])
+            cts = synth.residues(SEED, f"cpu{done}", (B, lay["G"], 2, L, N), ps)
+            F = synth.conv_weights(SEED, f"cpuw{done}", Ld["co"], Ld["ci"], 3, 3, wl["wlo"], wl["whi"])
+            O.conv_layer(cts, F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt")
+        else:
+            fl = O.fc_layout(N, Ld["n_in"], Ld["n_out"])
+            ct = synth.residues(SEED, f"cpu{done}", (B, 2, L, N), ps)
+            W = synth.fc_weights(SEED, f"cpuw{done}", Ld["n_out"], Ld["n_in"], wl["wlo"], wl["whi"])
+            O.fc_layer(ct, W, None, ps, psis, wl["t"], fl, O.OUT_EXTRACTED, tier="ntt")
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or (max_layers and done >= max_layers):
+            return done / el, done, O.threads()
+
+
+def cpu_baseline(wl, budget_s=15.0):
+    v, n, th = oracle_layers_per_s(wl, budget_s)
+    return {"value": v, "unit": "layers/s", "cores": th, "kind": "oracle",
+            "sample": f"{n} layer calls of the same workload cycled in order, ~{budget_s:.0f} s "
+                      f"budget, oracle NTT tier (OpenMP, {th} threads)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    wl = workload(args.workload)
+    per_step = 2
+    for w in range(args.warmup):
+        oracle_layers_per_s(wl, 0.0, max_layers=1, start=w)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        _, n, th = oracle_layers_per_s(wl, 0.0, max_layers=per_step, start=k * per_step)
+        done += n
+    dt = time.perf_counter() - t0
+    v = done / dt
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "layers/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32 (exact residues mod 30-bit primes)", "data": "synthetic",
+            "config": {"workload": wl["name"], "N": wl["N"], "L": wl["L"], "B": wl["B"],
+                       "layers_per_step": per_step},
+            "cpu_baseline": {"value": v, "unit": "layers/s", "cores": th, "kind": "oracle",
+                             "sample": f"{per_step} layer calls per step, cycling through the "
+                                       "20 layers in order, oracle NTT tier on the host cores"},
+            "e2e": {"value": v, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ----------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="plain20_c10")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res))
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    res = run_ours(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(workload(args.workload))
+        print(json.dumps(res))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

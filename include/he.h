@@ -1,0 +1,216 @@
+/*
+ * he.h -- C ABI of the GB300 (sm_103a) server hot path for rotation-free
+ * homomorphically encrypted Conv and FC layers (Akherati & Zhang,
+ * "Efficient Homomorphically Encrypted Convolutional Neural Network Without
+ * Rotation", arXiv 2409.05205).
+ *
+ * The library (libhe.so) evaluates, on one GPU, the server side of the
+ * paper's Conv layer (Sec. III-A, Alg. 1: one product per input polynomial
+ * and output channel summed, then the slot copy that gathers every output
+ * channel into one polynomial without rotation) and FC layer (Sec. III-B,
+ * Alg. 2 and Theorem 1), in the ciphertext x plaintext form of Sec. II-A:
+ * both ciphertext polynomials (c0, c1) are multiplied by the packed filter
+ * polynomials.  Arithmetic is exact over the ring Z_q[X]/(X^N+1) for each
+ * RNS prime q_l (RNS/CRT limbs, Sec. I); nothing is approximated.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ *  - A "polynomial" is N uint32 residues in [0, q_l), coefficient k at
+ *    index k (coefficient domain) or, in the NTT domain, the value at
+ *    X = psi_l^(2*brv_N(k)+1) at index k (brv_N = log2(N)-bit reversal,
+ *    psi_l the primitive 2N-th root returned by he_params_psi).
+ *  - An "RNS polynomial" is L polynomials, limb-major: [L][N].
+ *  - Device pointers are plain CUDA device addresses on the params' device;
+ *    host pointers are ordinary host memory.  Streams are cudaStream_t
+ *    passed as void* (NULL = the legacy default stream).
+ *  - Every function returns HE_OK or an error status and never throws.
+ *    On error, he_last_error() returns a message (thread-local).  Argument
+ *    and shape errors are detected before any GPU work is queued.  Errors
+ *    of asynchronous GPU work surface as HE_ERR_CUDA at a later call or at
+ *    he_sync().  Residues >= q_l in the inputs are not checked; they give
+ *    unspecified (but memory-safe) results.
+ *  - Ownership: params and filter banks are created and freed by the
+ *    library; activation buffers (inputs, outputs) are caller-owned device
+ *    memory.  The layer calls allocate nothing, except that a call whose
+ *    forward NTT workspace exceeds the params' current workspace grows it
+ *    once (cudaMalloc, which synchronizes the device); he_params_reserve
+ *    pre-sizes it so that later calls, and stream capture, never allocate.
+ *    Calls that share one params handle share its workspace and must not
+ *    overlap on the GPU (issue them on one stream).
+ */
+#ifndef HE_H
+#define HE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HE_OK = 0,
+    HE_ERR_ARG = 1,          /* NULL pointer, bad enum, out-of-range scalar */
+    HE_ERR_SHAPE = 2,        /* layer shape does not fit the ring (s * P > N, n_i > N) */
+    HE_ERR_UNSUPPORTED = 3,  /* valid but not implemented (e.g. interleave s > 128) */
+    HE_ERR_NOMEM = 4,        /* device or host allocation failed */
+    HE_ERR_CUDA = 5,         /* a CUDA runtime call or kernel failed */
+    HE_ERR_TIMEOUT = 6       /* a bounded device-side wait gave up */
+} he_status;
+
+enum { HE_COEFF = 0, HE_NTT = 1 };           /* domain of layer inputs */
+
+enum {
+    HE_OUT_EXTRACTED = 0,          /* rotation-free packed output (Alg. 1 slot copy),
+                                      computed by the valid-slot-only inverse transform */
+    HE_OUT_PER_CHANNEL = 1,        /* every output channel's full product, no extraction */
+    HE_OUT_EXTRACTED_UNFOLDED = 2  /* same words as HE_OUT_EXTRACTED, computed by a full
+                                      length-N INTT per channel followed by the slot copy */
+};
+
+#define HE_MAX_LIMBS 16
+#define HE_DEVICE_NONE (-1)   /* params for host-side queries only (no device tables) */
+#define HE_MAX_INTERLEAVE 128
+
+typedef struct he_params_s *he_params_t;    /* opaque, library-owned */
+typedef struct he_filters_s *he_filters_t;  /* opaque, device-resident packed bank */
+
+/* One Conv layer.  ci/co: input/output channels; h x w: input image;
+ * fh x fw: filter; pad: zero padding on every side (1 = "same" for 3x3);
+ * stride: 1 or 2.  A stride-2 layer is evaluated as its stride-1
+ * counterpart: its output (k, l) is the stride-1 output (2k, 2l), which the
+ * client reads off the extracted polynomial (the paper treats stride 1
+ * only, Sec. II-C). */
+typedef struct {
+    uint32_t ci, co, h, w, fh, fw, stride, pad;
+} he_conv_desc;
+
+/* Where the packed data lives (Sec. II-C eq. (i_batch), Sec. III-A eq.
+ * (k_batch_new)).  hp = w + 2 pad is the packed row stride and
+ * P = (h + 2 pad) * hp the packed footprint of one channel.  s is the
+ * channel interleave: the largest power of two with s * P <= N, capped at
+ * the next power of two >= ci.  Input channel m = g*s + m' sits in input
+ * polynomial g (of G = ceil(ci / s)) at exponents s*(k*hp + l) + m'.
+ * Output channel n sits in output polynomial floor(n / s) (of
+ * H = ceil(co / s)) at slots s*(k*hp + l) + off_n, with
+ * off_n = (n mod s) * floor(s / min(co, s)); row k < h_out, column
+ * l < w_out.  M = N / s is the length of the valid-slot-only inverse
+ * transform. */
+typedef struct {
+    uint32_t s, G, H, P, hp, h_out, w_out, M, off_mult;
+} he_conv_layout;
+
+/* FC layout (Sec. III-B eqs. (i(x) formula), (w(x) formula), Theorem 1).
+ * n_in_p: input length padded to a power of two; rows_per_poly =
+ * N / n_in_p rows of W per weight polynomial; P_fc = ceil(n_out /
+ * rows_per_poly) weight polynomials.  The input packs I_l at exponent
+ * l * rows_per_poly; output row R = j * rows_per_poly + k is coefficient k
+ * of output polynomial j. */
+typedef struct {
+    uint32_t n_in, n_in_p, n_out, rows_per_poly, P_fc;
+} he_fc_layout;
+
+/* Ring parameters on one device (Sec. II-A: R_Q = Z_Q[X]/(X^N+1) with
+ * Q = q_0 ... q_{L-1}).
+ *   N: ring degree, a power of two, 64 <= N <= 32768 (one polynomial per
+ *     CTA in shared memory).
+ *   L: number of RNS limbs, 1 <= L <= HE_MAX_LIMBS.
+ *   primes: NULL for the default rule (the L largest primes q with
+ *     2^29 < q < 2^30 and q = 1 mod 2N, descending), else L distinct primes
+ *     with q = 1 mod 2N and q < 2^30 (the kernels keep lazy values below
+ *     4q < 2^32).
+ *   t: plaintext modulus (> 1, < q_l); it only enters Delta_Q = floor(Q/t),
+ *     the scale of the FC bias (he_pack_fc).
+ *   device: CUDA device ordinal, or HE_DEVICE_NONE for a host-only handle
+ *     that answers the parameter and layout queries (no GPU needed) and
+ *     rejects every call that would touch a device with HE_ERR_ARG.
+ * Builds the twiddle tables on the device.  Blocking. */
+he_status he_params_create(uint32_t N, uint32_t L, const uint32_t *primes,
+                           uint32_t t, int device, he_params_t *out);
+/* primes_out[L] <- q_l. */
+he_status he_params_primes(he_params_t p, uint32_t *primes_out);
+/* psi_out[L] <- psi_l = g^((q_l - 1) / 2N), g the smallest generator mod q_l. */
+he_status he_params_psi(he_params_t p, uint32_t *psi_out);
+/* delta_out[L] <- floor(Q / t) mod q_l. */
+he_status he_params_delta(he_params_t p, uint32_t *delta_out);
+/* Grow the forward-NTT workspace to at least `bytes` now (blocking). */
+he_status he_params_reserve(he_params_t p, size_t bytes);
+/* Workspace bytes a he_conv_layer / he_fc_layer call with these arguments needs. */
+he_status he_conv_workspace_bytes(he_params_t p, const he_conv_desc *d, uint32_t B,
+                                  size_t *bytes);
+void he_params_destroy(he_params_t p);
+
+he_status he_conv_layout_query(he_params_t p, const he_conv_desc *d, he_conv_layout *out);
+he_status he_fc_layout_query(he_params_t p, uint32_t n_in, uint32_t n_out, he_fc_layout *out);
+
+/* Server model load for one Conv layer (Sec. III-A eq. (k_batch_new); Sec.
+ * IV-A: the NTTs of the filter polynomials are computed once and stored).
+ *   w: HOST int8 weights [co][ci][fh][fw], F^(m,n)_{k',l'} at
+ *      w[((n*ci + m)*fh + k')*fw + l'].
+ * Packs fhat_{g,n}(X) = sum_{m'} sum_{k',l'} F^(g s + m', n)_{k',l'}
+ * X^(off_n - m' - s(k' hp + l')) (X^-e = -X^(N-e)), transforms every
+ * polynomial to the NTT domain for every limb on the device and keeps the
+ * bank resident (co * G * L * N * 4 bytes).  Blocking. */
+he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w,
+                          he_filters_t *out);
+
+/* Server model load for one FC layer (Sec. III-B eq. (w(x) formula) and
+ * d(X) of Theorem 1).
+ *   W: HOST int8 [n_out][n_in], row-major.
+ *   bias: HOST int32 [n_out] or NULL (no bias).
+ * Packs the P_fc weight polynomials and keeps them resident in the NTT
+ * domain; the bias is added as Delta_Q * d(X) to c0 by he_fc_layer.
+ * Blocking. */
+he_status he_pack_fc(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t *W,
+                     const int32_t *bias, he_filters_t *out);
+void he_filters_destroy(he_filters_t f);
+
+/* Server evaluation of one Conv layer for B ciphertexts (Alg. 1 line 16 and
+ * the slot-copy loop that follows, in ciphertext x plaintext form):
+ *   y_n^(j) = sum_{g<G} c_g^(j) * fhat_{g,n}  in Z_q[X]/(X^N+1), j = 0, 1,
+ * then output polynomial h takes from each channel n it holds the
+ * coefficients s*e + off_n, e < N/s; every other coefficient is 0.
+ *   d_in:  DEVICE uint32 [B][G][2][L][N], ciphertext (c0, c1) of each input
+ *          group, in the domain `in_domain` (HE_COEFF or HE_NTT).  Read only.
+ *   d_out: DEVICE uint32, coefficient domain:
+ *          HE_OUT_EXTRACTED / HE_OUT_EXTRACTED_UNFOLDED: [B][H][2][L][N];
+ *          HE_OUT_PER_CHANNEL: [B][co][2][L][N] (y_n itself).
+ *          Every word is written.  Must not overlap d_in.
+ *   B >= 1.  Asynchronous on `stream`. */
+he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain,
+                        uint32_t *d_out, int out_mode, uint32_t B, void *stream);
+
+/* Server evaluation of one FC layer for B ciphertexts (Alg. 2 in
+ * ciphertext x plaintext form, Theorem 1):
+ *   y_j^(c) = c^(c) * w_j, plus Delta_Q * d_j(X) on c0 (c = 0).
+ *   d_in:  DEVICE uint32 [B][2][L][N] in `in_domain`; the input vector is
+ *          packed as I_l at exponent l * rows_per_poly.
+ *   d_out: DEVICE uint32 [B][P_fc][2][L][N], coefficient domain.
+ *          HE_OUT_EXTRACTED: coefficients k < rows_j of block j hold rows
+ *          j*rows_per_poly + k of W I + B ("only the first n_o coefficients
+ *          need to be computed", Sec. III-B); the rest are 0.
+ *          HE_OUT_PER_CHANNEL: every coefficient of the product (+ bias).
+ *   Asynchronous on `stream`. */
+he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain,
+                      uint32_t *d_out, int out_mode, uint32_t B, void *stream);
+
+/* The forward negacyclic NTT of `count` RNS polynomials (the input
+ * transform of the server step, Sec. IV-A).  d_in, d_out: DEVICE uint32
+ * [count][L][N]; in place if equal.  Output in the canonical NTT order
+ * above, residues in [0, q_l).  Asynchronous. */
+he_status he_ntt_forward(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
+                         uint32_t count, void *stream);
+/* Its inverse (including N^-1).  Asynchronous. */
+he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
+                         uint32_t count, void *stream);
+
+/* Wait for `stream` and report any pending CUDA error. */
+he_status he_sync(void *stream);
+
+/* Message of the last non-OK status returned on this thread ("" if none). */
+const char *he_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HE_H */

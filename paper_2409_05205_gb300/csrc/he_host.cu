@@ -1,0 +1,572 @@
+// he_host.cu -- C ABI entry points of libhe (declared in include/he.h).
+//
+// Host work: ring parameters (NTT-friendly primes, primitive 2N-th roots,
+// twiddle tables with Shoup constants, Delta_Q mod q_l), layout rules,
+// argument validation, device memory for params / filter banks /
+// workspace, and kernel launches.  No HE arithmetic runs on the CPU for the
+// layer calls: every step of the server path is a kernel in he_kernels.cu.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "he_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+he_status fail(he_status s, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+he_status fail(he_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+he_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(HE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// number theory on the host (64-bit intermediates)
+// ---------------------------------------------------------------------------
+uint32_t mul_mod(uint32_t a, uint32_t b, uint32_t m) { return (uint32_t)((uint64_t)a * b % m); }
+
+uint32_t pow_mod(uint32_t b, uint64_t e, uint32_t m) {
+    uint64_t r = 1 % m, x = b % m;
+    while (e) {
+        if (e & 1) r = r * x % m;
+        x = x * x % m;
+        e >>= 1;
+    }
+    return (uint32_t)r;
+}
+
+// Deterministic Miller-Rabin for n < 2^32 with witnesses 2, 7, 61
+// (G. Jaeschke, Math. Comp. 1993: no strong pseudoprime to all three below
+// 4,759,123,141).
+bool is_prime_u32(uint32_t n) {
+    if (n < 2) return false;
+    for (uint32_t p : {2u, 3u, 5u, 7u, 11u, 13u, 61u})
+        if (n % p == 0) return n == p;
+    uint32_t d = n - 1, r = 0;
+    while ((d & 1) == 0) {
+        d >>= 1;
+        ++r;
+    }
+    for (uint32_t a : {2u, 7u, 61u}) {
+        uint32_t x = pow_mod(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (uint32_t i = 1; i < r; ++i) {
+            x = mul_mod(x, x, n);
+            if (x == n - 1) {
+                comp = false;
+                break;
+            }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+// Smallest generator of Z_q^*: g with g^((q-1)/f) != 1 for each prime f | q-1.
+uint32_t generator(uint32_t q) {
+    std::vector<uint32_t> fs;
+    uint32_t m = q - 1;
+    for (uint32_t f = 2; (uint64_t)f * f <= m; ++f) {
+        if (m % f == 0) {
+            fs.push_back(f);
+            while (m % f == 0) m /= f;
+        }
+    }
+    if (m > 1) fs.push_back(m);
+    for (uint32_t g = 2; g < q; ++g) {
+        bool ok = true;
+        for (uint32_t f : fs)
+            if (pow_mod(g, (q - 1) / f, q) == 1) {
+                ok = false;
+                break;
+            }
+        if (ok) return g;
+    }
+    return 0;
+}
+
+uint32_t shoup(uint32_t w, uint32_t q) { return (uint32_t)(((uint64_t)w << 32) / q); }
+
+uint32_t bitrev(uint32_t x, uint32_t bits) {
+    uint32_t r = 0;
+    for (uint32_t i = 0; i < bits; ++i) {
+        r = (r << 1) | (x & 1);
+        x >>= 1;
+    }
+    return r;
+}
+
+uint32_t log2_exact(uint32_t x) {
+    uint32_t l = 0;
+    while ((1u << l) < x) ++l;
+    return (1u << l) == x ? l : 0xFFFFFFFFu;
+}
+
+uint32_t pow2_floor(uint32_t x) {
+    uint32_t p = 1;
+    while (p * 2u <= x) p *= 2u;
+    return p;
+}
+
+uint32_t pow2_ceil(uint32_t x) {
+    uint32_t p = 1;
+    while (p < x) p *= 2u;
+    return p;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+he_status conv_layout(const he_params_s *p, const he_conv_desc *d, he_conv_layout *lay) {
+    if (!d) return fail(HE_ERR_ARG, "conv desc is NULL");
+    if (d->ci == 0 || d->co == 0 || d->h == 0 || d->w == 0 || d->fh == 0 || d->fw == 0)
+        return fail(HE_ERR_ARG, "conv desc has a zero dimension");
+    if (d->stride != 1 && d->stride != 2) return fail(HE_ERR_ARG, "stride must be 1 or 2");
+    if (d->pad > 8) return fail(HE_ERR_ARG, "pad %u too large", d->pad);
+    const uint64_t hpad = (uint64_t)d->h + 2ull * d->pad, wpad = (uint64_t)d->w + 2ull * d->pad;
+    if (d->fh > hpad || d->fw > wpad) return fail(HE_ERR_SHAPE, "filter larger than padded input");
+    const uint64_t P = hpad * wpad;
+    if (P > p->N) return fail(HE_ERR_SHAPE, "one channel (%llu slots) does not fit N = %u",
+                              (unsigned long long)P, p->N);
+    const uint32_t s = std::min(pow2_floor((uint32_t)(p->N / P)), pow2_ceil(d->ci));
+    lay->s = s;
+    lay->G = (d->ci + s - 1) / s;
+    lay->H = (d->co + s - 1) / s;
+    lay->P = (uint32_t)P;
+    lay->hp = (uint32_t)wpad;
+    lay->h_out = (uint32_t)(hpad - d->fh + 1);
+    lay->w_out = (uint32_t)(wpad - d->fw + 1);
+    lay->M = p->N / s;
+    lay->off_mult = s / std::min(d->co, s);
+    return HE_OK;
+}
+
+he_status fc_layout(const he_params_s *p, uint32_t n_in, uint32_t n_out, he_fc_layout *fl) {
+    if (n_in == 0 || n_out == 0) return fail(HE_ERR_ARG, "FC with zero inputs or outputs");
+    if (n_in > p->N) return fail(HE_ERR_SHAPE, "FC input length %u exceeds N = %u", n_in, p->N);
+    fl->n_in = n_in;
+    fl->n_in_p = pow2_ceil(n_in);
+    fl->n_out = n_out;
+    fl->rows_per_poly = p->N / fl->n_in_p;
+    fl->P_fc = (n_out + fl->rows_per_poly - 1) / fl->rows_per_poly;
+    return HE_OK;
+}
+
+he_status need_device(const he_params_s *p) {
+    if (p->device == HE_DEVICE_NONE) return fail(HE_ERR_ARG, "params were created without a device");
+    return HE_OK;
+}
+
+he_status ensure_ws(he_params_s *p, size_t bytes) {
+    if (bytes <= p->ws_bytes) return HE_OK;
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    if (p->ws) {
+        cudaError_t e = cudaFree(p->ws);
+        p->ws = nullptr;
+        p->ws_bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+    }
+    cudaError_t e = cudaMalloc(&p->ws, bytes);
+    if (e != cudaSuccess) {
+        p->ws = nullptr;
+        cudaGetLastError();
+        return fail(HE_ERR_NOMEM, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+    p->ws_bytes = bytes;
+    return HE_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *he_last_error(void) { return g_err; }
+
+he_status he_params_create(uint32_t N, uint32_t L, const uint32_t *primes, uint32_t t, int device,
+                           he_params_t *out) {
+    g_err[0] = 0;
+    if (!out) return fail(HE_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    const uint32_t logN = log2_exact(N);
+    if (logN == 0xFFFFFFFFu || N < 64 || N > 32768)
+        return fail(HE_ERR_ARG, "N = %u must be a power of two in [64, 32768]", N);
+    if (L < 1 || L > HE_MAX_LIMBS) return fail(HE_ERR_ARG, "L = %u must be in [1, %d]", L, HE_MAX_LIMBS);
+    if (t < 2) return fail(HE_ERR_ARG, "t = %u must be > 1", t);
+    if (device != HE_DEVICE_NONE) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+            cudaGetLastError();
+            return fail(HE_ERR_CUDA, "no CUDA device %d", device);
+        }
+    }
+    he_params_s *p = new (std::nothrow) he_params_s();
+    if (!p) return fail(HE_ERR_NOMEM, "params");
+    p->device = device;
+    p->N = N;
+    p->L = L;
+    p->logN = logN;
+    p->t = t;
+    // primes
+    if (primes) {
+        for (uint32_t l = 0; l < L; ++l) {
+            const uint32_t q = primes[l];
+            if (q >= (1u << 30) || q % (2u * N) != 1u || !is_prime_u32(q)) {
+                delete p;
+                return fail(HE_ERR_ARG, "prime %u is not a prime < 2^30 with q = 1 mod 2N", q);
+            }
+            for (uint32_t k = 0; k < l; ++k)
+                if (primes[k] == q) {
+                    delete p;
+                    return fail(HE_ERR_ARG, "prime %u repeated", q);
+                }
+            p->q[l] = q;
+        }
+    } else {
+        uint32_t found = 0;
+        for (uint64_t q = (1ull << 30) + 1ull - 2ull * N; q > (1ull << 29) && found < L; q -= 2ull * N)
+            if (is_prime_u32((uint32_t)q)) p->q[found++] = (uint32_t)q;
+        if (found < L) {
+            delete p;
+            return fail(HE_ERR_ARG, "fewer than %u NTT-friendly 30-bit primes for N = %u", L, N);
+        }
+    }
+    for (uint32_t l = 0; l < L; ++l)
+        if (p->q[l] <= t) {
+            delete p;
+            return fail(HE_ERR_ARG, "t = %u must be below every prime", t);
+        }
+    // roots, constants, Delta_Q mod q_l = -(Q mod t) * t^-1 mod q_l
+    uint64_t Qmodt = 1;
+    for (uint32_t l = 0; l < L; ++l) Qmodt = Qmodt * (p->q[l] % t) % t;
+    std::vector<uint2> twf((size_t)L * N), twi((size_t)L * N);
+    std::vector<uint32_t> pw((size_t)L * 2 * N);
+    RingView &r = p->ring;
+    memset(&r, 0, sizeof(r));
+    r.N = N;
+    r.logN = logN;
+    r.L = L;
+    for (uint32_t l = 0; l < L; ++l) {
+        const uint32_t q = p->q[l];
+        const uint32_t g = generator(q);
+        const uint32_t psi = pow_mod(g, (q - 1) / (2u * N), q);
+        const uint32_t psi_inv = pow_mod(psi, 2ull * N - 1, q);
+        p->psi[l] = psi;
+        const uint32_t tinv = pow_mod(t % q, q - 2, q);
+        p->delta[l] = mul_mod((uint32_t)((q - Qmodt % q) % q), tinv, q);
+        LimbK &k = r.limb[l];
+        k.q = q;
+        k.q2 = 2u * q;
+        k.r32 = (uint32_t)((1ull << 32) % q);
+        k.r32s = shoup(k.r32, q);
+        k.ones = shoup(1u, q);
+        k.ninv = pow_mod(N % q, q - 2, q);
+        k.ninvs = shoup(k.ninv, q);
+        for (uint32_t i = 0; i < N; ++i) {
+            const uint32_t e = bitrev(i, logN);
+            const uint32_t wf = pow_mod(psi, e, q), wi = pow_mod(psi_inv, e, q);
+            twf[(size_t)l * N + i] = make_uint2(wf, shoup(wf, q));
+            twi[(size_t)l * N + i] = make_uint2(wi, shoup(wi, q));
+        }
+        uint64_t x = 1;
+        for (uint32_t e = 0; e < 2u * N; ++e) {
+            pw[(size_t)l * 2 * N + e] = (uint32_t)x;
+            x = x * psi % q;
+        }
+    }
+    if (device == HE_DEVICE_NONE) {
+        *out = p;
+        return HE_OK;
+    }
+    DeviceGuard dg(device);
+    if (!dg.ok) {
+        delete p;
+        return fail(HE_ERR_CUDA, "cannot select device %d", device);
+    }
+    cudaError_t e = cudaMalloc(&p->d_tw_fwd, twf.size() * sizeof(uint2));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_inv, twi.size() * sizeof(uint2));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_psi_pow, pw.size() * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw_fwd, twf.data(), twf.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_tw_inv, twi.data(), twi.size() * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_psi_pow, pw.data(), pw.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        he_params_destroy(p);
+        return cuda_fail(e, "params tables");
+    }
+    r.tw_fwd = p->d_tw_fwd;
+    r.tw_inv = p->d_tw_inv;
+    r.psi_pow = p->d_psi_pow;
+    *out = p;
+    return HE_OK;
+}
+
+he_status he_params_primes(he_params_t p, uint32_t *primes_out) {
+    if (!p || !primes_out) return fail(HE_ERR_ARG, "NULL argument");
+    memcpy(primes_out, p->q, p->L * sizeof(uint32_t));
+    return HE_OK;
+}
+
+he_status he_params_psi(he_params_t p, uint32_t *psi_out) {
+    if (!p || !psi_out) return fail(HE_ERR_ARG, "NULL argument");
+    memcpy(psi_out, p->psi, p->L * sizeof(uint32_t));
+    return HE_OK;
+}
+
+he_status he_params_delta(he_params_t p, uint32_t *delta_out) {
+    if (!p || !delta_out) return fail(HE_ERR_ARG, "NULL argument");
+    memcpy(delta_out, p->delta, p->L * sizeof(uint32_t));
+    return HE_OK;
+}
+
+he_status he_params_reserve(he_params_t p, size_t bytes) {
+    if (!p) return fail(HE_ERR_ARG, "params is NULL");
+    return ensure_ws(p, bytes);
+}
+
+he_status he_conv_workspace_bytes(he_params_t p, const he_conv_desc *d, uint32_t B, size_t *bytes) {
+    if (!p || !bytes) return fail(HE_ERR_ARG, "NULL argument");
+    he_conv_layout lay{};
+    he_status s = conv_layout(p, d, &lay);
+    if (s != HE_OK) return s;
+    *bytes = (size_t)B * lay.G * 2u * p->L * p->N * sizeof(uint32_t);
+    return HE_OK;
+}
+
+void he_params_destroy(he_params_t p) {
+    if (!p) return;
+    if (p->device == HE_DEVICE_NONE) {
+        delete p;
+        return;
+    }
+    DeviceGuard g(p->device);
+    cudaFree(p->d_tw_fwd);
+    cudaFree(p->d_tw_inv);
+    cudaFree(p->d_psi_pow);
+    cudaFree(p->ws);
+    delete p;
+}
+
+he_status he_conv_layout_query(he_params_t p, const he_conv_desc *d, he_conv_layout *out) {
+    if (!p || !out) return fail(HE_ERR_ARG, "NULL argument");
+    return conv_layout(p, d, out);
+}
+
+he_status he_fc_layout_query(he_params_t p, uint32_t n_in, uint32_t n_out, he_fc_layout *out) {
+    if (!p || !out) return fail(HE_ERR_ARG, "NULL argument");
+    return fc_layout(p, n_in, n_out, out);
+}
+
+he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w, he_filters_t *out) {
+    if (!p || !d || !w || !out) return fail(HE_ERR_ARG, "NULL argument");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    *out = nullptr;
+    he_conv_layout lay{};
+    he_status st = conv_layout(p, d, &lay);
+    if (st != HE_OK) return st;
+    if (lay.s > HE_MAX_INTERLEAVE)
+        return fail(HE_ERR_UNSUPPORTED, "interleave s = %u above %d", lay.s, HE_MAX_INTERLEAVE);
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    he_filters_s *f = new (std::nothrow) he_filters_s();
+    if (!f) return fail(HE_ERR_NOMEM, "filters");
+    f->p = p;
+    f->kind = HE_KIND_CONV;
+    f->desc = *d;
+    f->lay = lay;
+    f->bank_bytes = (size_t)d->co * p->L * lay.G * p->N * sizeof(uint32_t);
+    const size_t wbytes = (size_t)d->co * d->ci * d->fh * d->fw;
+    int8_t *d_w = nullptr;
+    cudaError_t e = cudaMalloc(&f->bank, f->bank_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const size_t nb = f->bank_bytes;
+        delete f;
+        return fail(HE_ERR_NOMEM, "filter bank of %zu bytes", nb);
+    }
+    e = cudaMalloc(&d_w, wbytes);
+    if (e == cudaSuccess) e = cudaMemcpy(d_w, w, wbytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = he_launch_pack_conv(p->ring, d_w, *d, lay, f->bank, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_w);
+    if (e != cudaSuccess) {
+        he_filters_destroy(f);
+        return cuda_fail(e, "pack filters");
+    }
+    *out = f;
+    return HE_OK;
+}
+
+he_status he_pack_fc(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t *W, const int32_t *bias,
+                     he_filters_t *out) {
+    if (!p || !W || !out) return fail(HE_ERR_ARG, "NULL argument");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    *out = nullptr;
+    he_fc_layout fl{};
+    he_status st = fc_layout(p, n_in, n_out, &fl);
+    if (st != HE_OK) return st;
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    he_filters_s *f = new (std::nothrow) he_filters_s();
+    if (!f) return fail(HE_ERR_NOMEM, "filters");
+    f->p = p;
+    f->kind = HE_KIND_FC;
+    f->fl = fl;
+    f->bank_bytes = (size_t)fl.P_fc * p->L * p->N * sizeof(uint32_t);
+    const size_t wbytes = (size_t)n_out * n_in;
+    int8_t *d_W = nullptr;
+    cudaError_t e = cudaMalloc(&f->bank, f->bank_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const size_t nb = f->bank_bytes;
+        delete f;
+        return fail(HE_ERR_NOMEM, "FC bank of %zu bytes", nb);
+    }
+    if (bias) {
+        std::vector<uint32_t> hb((size_t)p->L * n_out);
+        for (uint32_t l = 0; l < p->L; ++l) {
+            const uint32_t q = p->q[l];
+            for (uint32_t k = 0; k < n_out; ++k) {
+                const int64_t b = bias[k];
+                const uint32_t br = (uint32_t)(((b % (int64_t)q) + (int64_t)q) % (int64_t)q);
+                hb[(size_t)l * n_out + k] = mul_mod(br, p->delta[l], q);
+            }
+        }
+        e = cudaMalloc(&f->bias, hb.size() * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMemcpy(f->bias, hb.data(), hb.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&d_W, wbytes);
+    if (e == cudaSuccess) e = cudaMemcpy(d_W, W, wbytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = he_launch_pack_fc(p->ring, d_W, fl, f->bank, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_W);
+    if (e != cudaSuccess) {
+        he_filters_destroy(f);
+        return cuda_fail(e, "pack FC");
+    }
+    *out = f;
+    return HE_OK;
+}
+
+void he_filters_destroy(he_filters_t f) {
+    if (!f) return;
+    DeviceGuard g(f->p->device);
+    cudaFree(f->bank);
+    cudaFree(f->bias);
+    delete f;
+}
+
+he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain, uint32_t *d_out,
+                        int out_mode, uint32_t B, void *stream) {
+    if (!p || !f || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
+    if (f->kind != HE_KIND_CONV || f->p != p) return fail(HE_ERR_ARG, "filters are not a Conv bank of these params");
+    if (in_domain != HE_COEFF && in_domain != HE_NTT) return fail(HE_ERR_ARG, "bad in_domain %d", in_domain);
+    if (out_mode != HE_OUT_EXTRACTED && out_mode != HE_OUT_PER_CHANNEL && out_mode != HE_OUT_EXTRACTED_UNFOLDED)
+        return fail(HE_ERR_ARG, "bad out_mode %d", out_mode);
+    if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
+    if (!aligned16(d_in) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
+    const he_conv_layout &lay = f->lay;
+    const size_t nin = (size_t)B * lay.G * 2u * p->L * p->N;
+    const size_t nout = (size_t)B * (out_mode == HE_OUT_PER_CHANNEL ? f->desc.co : lay.H) * 2u * p->L * p->N;
+    if (d_in < d_out + nout && d_out < d_in + nin) return fail(HE_ERR_ARG, "d_in and d_out overlap");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t *x = d_in;
+    if (in_domain == HE_COEFF) {
+        he_status s = ensure_ws(p, nin * sizeof(uint32_t));
+        if (s != HE_OK) return s;
+        cudaError_t e = he_launch_ntt(p->ring, d_in, (uint32_t *)p->ws, (uint32_t)(nin / ((size_t)p->L * p->N) * p->L), false, st);
+        if (e != cudaSuccess) return cuda_fail(e, "input NTT");
+        x = (const uint32_t *)p->ws;
+    }
+    cudaError_t e = he_launch_conv(p->ring, f->desc, lay, f->bank, x, d_out, out_mode, B, st);
+    if (e != cudaSuccess) return cuda_fail(e, "conv kernel");
+    return HE_OK;
+}
+
+he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain, uint32_t *d_out,
+                      int out_mode, uint32_t B, void *stream) {
+    if (!p || !f || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
+    if (f->kind != HE_KIND_FC || f->p != p) return fail(HE_ERR_ARG, "filters are not an FC bank of these params");
+    if (in_domain != HE_COEFF && in_domain != HE_NTT) return fail(HE_ERR_ARG, "bad in_domain %d", in_domain);
+    if (out_mode != HE_OUT_EXTRACTED && out_mode != HE_OUT_PER_CHANNEL)
+        return fail(HE_ERR_ARG, "bad out_mode %d for an FC layer", out_mode);
+    if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
+    if (!aligned16(d_in) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
+    const size_t nin = (size_t)B * 2u * p->L * p->N;
+    const size_t nout = (size_t)B * f->fl.P_fc * 2u * p->L * p->N;
+    if (d_in < d_out + nout && d_out < d_in + nin) return fail(HE_ERR_ARG, "d_in and d_out overlap");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t *x = d_in;
+    if (in_domain == HE_COEFF) {
+        he_status s = ensure_ws(p, nin * sizeof(uint32_t));
+        if (s != HE_OK) return s;
+        cudaError_t e = he_launch_ntt(p->ring, d_in, (uint32_t *)p->ws, 2u * B * p->L, false, st);
+        if (e != cudaSuccess) return cuda_fail(e, "input NTT");
+        x = (const uint32_t *)p->ws;
+    }
+    cudaError_t e = he_launch_fc(p->ring, f->fl, f->bank, f->bias, x, d_out, out_mode, B, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fc kernel");
+    return HE_OK;
+}
+
+he_status he_ntt_forward(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count, void *stream) {
+    if (!p || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    if (!aligned16(d_in) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    cudaError_t e = he_launch_ntt(p->ring, d_in, d_out, count * p->L, false, (cudaStream_t)stream);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "forward NTT");
+}
+
+he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count, void *stream) {
+    if (!p || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    if (!aligned16(d_in) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    cudaError_t e = he_launch_ntt(p->ring, d_in, d_out, count * p->L, true, (cudaStream_t)stream);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "inverse NTT");
+}
+
+he_status he_sync(void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "sync");
+}
+
+}  // extern "C"

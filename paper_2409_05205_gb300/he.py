@@ -1,0 +1,226 @@
+"""ctypes binding of libhe (include/he.h), one Python function per C entry point,
+with the same names.  It only marshals arguments: device buffers are passed as
+raw device addresses (an int, or any object with ``data_ptr()`` such as a
+torch tensor), streams as raw ``cudaStream_t`` values (an int, or an object
+with ``cuda_stream``).  Every step of the server path runs in the CUDA
+library; if the library is missing, every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhe.so")
+
+HE_OK, HE_ERR_ARG, HE_ERR_SHAPE, HE_ERR_UNSUPPORTED, HE_ERR_NOMEM, HE_ERR_CUDA, HE_ERR_TIMEOUT = range(7)
+HE_COEFF, HE_NTT = 0, 1
+HE_OUT_EXTRACTED, HE_OUT_PER_CHANNEL, HE_OUT_EXTRACTED_UNFOLDED = 0, 1, 2
+HE_MAX_LIMBS = 16
+HE_MAX_INTERLEAVE = 128
+HE_DEVICE_NONE = -1
+
+_STATUS = {0: "HE_OK", 1: "HE_ERR_ARG", 2: "HE_ERR_SHAPE", 3: "HE_ERR_UNSUPPORTED",
+           4: "HE_ERR_NOMEM", 5: "HE_ERR_CUDA", 6: "HE_ERR_TIMEOUT"}
+
+
+class HEError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class he_conv_desc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("ci", "co", "h", "w", "fh", "fw", "stride", "pad")]
+
+
+class he_conv_layout(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("s", "G", "H", "P", "hp", "h_out", "w_out", "M", "off_mult")]
+
+
+class he_fc_layout(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("n_in", "n_in_p", "n_out", "rows_per_poly", "P_fc")]
+
+
+_lib = None
+
+_vp, _u32, _i32, _sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
+_SIGS = {
+    "he_params_create": [_u32, _u32, _vp, _u32, _i32, ctypes.POINTER(_vp)],
+    "he_params_primes": [_vp, _vp],
+    "he_params_psi": [_vp, _vp],
+    "he_params_delta": [_vp, _vp],
+    "he_params_reserve": [_vp, _sz],
+    "he_conv_workspace_bytes": [_vp, ctypes.POINTER(he_conv_desc), _u32, ctypes.POINTER(_sz)],
+    "he_params_destroy": [_vp],
+    "he_conv_layout_query": [_vp, ctypes.POINTER(he_conv_desc), ctypes.POINTER(he_conv_layout)],
+    "he_fc_layout_query": [_vp, _u32, _u32, ctypes.POINTER(he_fc_layout)],
+    "he_pack_filters": [_vp, ctypes.POINTER(he_conv_desc), _vp, ctypes.POINTER(_vp)],
+    "he_pack_fc": [_vp, _u32, _u32, _vp, _vp, ctypes.POINTER(_vp)],
+    "he_filters_destroy": [_vp],
+    "he_conv_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
+    "he_fc_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
+    "he_ntt_forward": [_vp, _vp, _vp, _u32, _vp],
+    "he_ntt_inverse": [_vp, _vp, _vp, _u32, _vp],
+    "he_sync": [_vp],
+    "he_last_error": [],
+}
+_VOID = {"he_params_destroy", "he_filters_destroy"}
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libhe.so.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it first (__graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = None if name in _VOID else (ctypes.c_char_p if name == "he_last_error" else ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != HE_OK:
+        raise HEError(status, lib().he_last_error().decode(errors="replace"))
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    raise TypeError(f"cannot take a device address of {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def _desc(d) -> he_conv_desc:
+    if isinstance(d, he_conv_desc):
+        return d
+    return he_conv_desc(d["ci"], d["co"], d["h"], d["w"], d.get("fh", 3), d.get("fw", 3),
+                        d.get("stride", 1), d.get("pad", 1))
+
+
+# ----------------------------------------------------------------------------
+# entry points
+# ----------------------------------------------------------------------------
+
+def he_last_error() -> str:
+    return lib().he_last_error().decode(errors="replace")
+
+
+def he_params_create(N: int, L: int, primes=None, t: int = 65537, device: int = 0) -> int:
+    out = _vp()
+    arr = None
+    if primes is not None:
+        arr = np.ascontiguousarray(primes, dtype=np.uint32)
+        assert arr.size == L
+    _check(lib().he_params_create(N, L, None if arr is None else arr.ctypes.data, t, device,
+                                  ctypes.byref(out)))
+    return out.value
+
+
+def _limb_query(fn, p, L):
+    a = np.zeros(L, dtype=np.uint32)
+    _check(fn(p, a.ctypes.data))
+    return [int(x) for x in a]
+
+
+def he_params_primes(p: int, L: int) -> list[int]:
+    return _limb_query(lib().he_params_primes, p, L)
+
+
+def he_params_psi(p: int, L: int) -> list[int]:
+    return _limb_query(lib().he_params_psi, p, L)
+
+
+def he_params_delta(p: int, L: int) -> list[int]:
+    return _limb_query(lib().he_params_delta, p, L)
+
+
+def he_params_reserve(p: int, nbytes: int) -> None:
+    _check(lib().he_params_reserve(p, nbytes))
+
+
+def he_conv_workspace_bytes(p: int, desc, B: int) -> int:
+    out = _sz()
+    d = _desc(desc)
+    _check(lib().he_conv_workspace_bytes(p, ctypes.byref(d), B, ctypes.byref(out)))
+    return out.value
+
+
+def he_params_destroy(p: int) -> None:
+    lib().he_params_destroy(p)
+
+
+def he_conv_layout_query(p: int, desc) -> dict:
+    out = he_conv_layout()
+    d = _desc(desc)
+    _check(lib().he_conv_layout_query(p, ctypes.byref(d), ctypes.byref(out)))
+    return {n: getattr(out, n) for n, _ in he_conv_layout._fields_}
+
+
+def he_fc_layout_query(p: int, n_in: int, n_out: int) -> dict:
+    out = he_fc_layout()
+    _check(lib().he_fc_layout_query(p, n_in, n_out, ctypes.byref(out)))
+    return {n: getattr(out, n) for n, _ in he_fc_layout._fields_}
+
+
+def he_pack_filters(p: int, desc, w: np.ndarray) -> int:
+    d = _desc(desc)
+    w = np.ascontiguousarray(w, dtype=np.int8)
+    assert w.size == d.co * d.ci * d.fh * d.fw
+    out = _vp()
+    _check(lib().he_pack_filters(p, ctypes.byref(d), w.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
+def he_pack_fc(p: int, n_in: int, n_out: int, W: np.ndarray, bias: np.ndarray | None = None) -> int:
+    W = np.ascontiguousarray(W, dtype=np.int8)
+    assert W.shape == (n_out, n_in)
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.int32)
+    out = _vp()
+    _check(lib().he_pack_fc(p, n_in, n_out, W.ctypes.data, None if b is None else b.ctypes.data,
+                            ctypes.byref(out)))
+    return out.value
+
+
+def he_filters_destroy(f: int) -> None:
+    lib().he_filters_destroy(f)
+
+
+def he_conv_layer(p: int, f: int, d_in, in_domain: int, d_out, out_mode: int, B: int,
+                  stream=None) -> None:
+    _check(lib().he_conv_layer(p, f, _ptr(d_in), in_domain, _ptr(d_out), out_mode, B, _stream(stream)))
+
+
+def he_fc_layer(p: int, f: int, d_in, in_domain: int, d_out, out_mode: int, B: int,
+                stream=None) -> None:
+    _check(lib().he_fc_layer(p, f, _ptr(d_in), in_domain, _ptr(d_out), out_mode, B, _stream(stream)))
+
+
+def he_ntt_forward(p: int, d_in, d_out, count: int, stream=None) -> None:
+    _check(lib().he_ntt_forward(p, _ptr(d_in), _ptr(d_out), count, _stream(stream)))
+
+
+def he_ntt_inverse(p: int, d_in, d_out, count: int, stream=None) -> None:
+    _check(lib().he_ntt_inverse(p, _ptr(d_in), _ptr(d_out), count, _stream(stream)))
+
+
+def he_sync(stream=None) -> None:
+    _check(lib().he_sync(_stream(stream)))

@@ -1,0 +1,256 @@
+"""GPU parity: every output word of the CUDA path, called through the C ABI,
+equals the oracle's (bit-exact: the work is integer arithmetic mod q_l).
+
+Sizes: small rings that span several tiles with ragged tails, the single
+Conv config (N = 2048), every distinct plain-20 layer shape at N = 8192 with
+3 limbs, and wide layers at N = 16384 with 6 limbs and B = 8.  Edge cases:
+interleave s = 1, 2 and 128, c_o < s, a partly filled last output
+polynomial, several input groups, inputs already in the NTT domain, and
+argument errors."""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2409_05205_gb300 import synth
+
+import _gpu_helpers as U
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["extracted", "unfolded", "per_channel"]
+
+
+def _mode(H, name):
+    return {"extracted": H.HE_OUT_EXTRACTED, "unfolded": H.HE_OUT_EXTRACTED_UNFOLDED,
+            "per_channel": H.HE_OUT_PER_CHANNEL}[name]
+
+
+def _ref_conv(cts, F, ps, psis, lay, mode_name, tier="ntt"):
+    m = O.OUT_PER_CHANNEL if mode_name == "per_channel" else O.OUT_EXTRACTED
+    return O.conv_layer(cts, F, ps, psis, lay, m, tier=tier)
+
+
+# ----------------------------------------------------------------------------
+# NTT
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,L,count", [(64, 1, 3), (1024, 2, 2), (2048, 1, 5), (8192, 3, 4),
+                                       (16384, 6, 2), (32768, 1, 2)])
+def test_forward_and_inverse_ntt_match_oracle(N, L, count):
+    H = U.he()
+    ps, psis = U.ring(N, L)
+    a = synth.residues(N, "ntt", (count, L, N), ps)
+    with U.params(N, L) as p:
+        d = U.to_dev(a)
+        out = U.empty_dev(a.shape)
+        H.he_ntt_forward(p, d, out, count)
+        H.he_sync()
+        got = U.from_dev(out).reshape(a.shape)
+        for l in range(L):
+            np.testing.assert_array_equal(got[:, l], O.ntt_fwd(a[:, l], ps[l], psis[l]))
+        back = U.empty_dev(a.shape)
+        H.he_ntt_inverse(p, out, back, count)
+        H.he_ntt_forward(p, back, back, count)      # in place
+        H.he_ntt_inverse(p, back, back, count)
+        H.he_sync()
+        np.testing.assert_array_equal(U.from_dev(back).reshape(a.shape), a)
+
+
+# ----------------------------------------------------------------------------
+# Conv: small rings, every mode, edge cases
+# ----------------------------------------------------------------------------
+
+SMALL = [
+    # N, L, ci, co, h, w, B, fh, fw, pad       (s, G, H) noted
+    (256, 1, 3, 4, 4, 4, 1, 3, 3, 1),        # s=4 G=1 H=1
+    (256, 2, 8, 2, 4, 4, 2, 3, 3, 1),        # s=4, c_o=2 < s: offsets spread by 2
+    (512, 1, 16, 10, 4, 4, 3, 3, 3, 1),      # s=8, G=2, H=2 with a ragged last output poly
+    (1024, 2, 5, 7, 6, 5, 1, 3, 3, 1),       # odd shapes
+    (1024, 1, 1, 3, 8, 8, 2, 3, 3, 1),       # s = 1
+    (256, 1, 16, 16, 8, 8, 1, 3, 3, 1),      # s = 2 (P = 100), G = 8
+    (512, 2, 200, 130, 2, 2, 1, 2, 1, 0),    # s = 128 (P = 4), G = 2, H = 2 ragged
+    (64, 1, 4, 4, 2, 2, 1, 2, 1, 0),         # the paper's tiny example, N = 64
+    (2048, 1, 32, 64, 4, 4, 2, 3, 3, 1),     # s = 32, H = 2
+]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("case", SMALL, ids=[f"N{c[0]}_ci{c[2]}_co{c[3]}" for c in SMALL])
+def test_conv_small_rings_all_modes(case, mode):
+    H = U.he()
+    N, L, ci, co, h, w, B, fh, fw, pad = case
+    ps, psis, lay, cts, F, desc = U.conv_case(N, L, ci, co, h, w, B, seed=7, fh=fh, fw=fw, pad=pad)
+    ref = _ref_conv(cts, F, ps, psis, lay, mode)
+    with U.params(N, L) as p, U.conv_bank(p, desc, F) as f:
+        got = U.run_conv(p, f, cts, _mode(H, mode), ref.shape[1])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_conv_small_schoolbook_reference():
+    H = U.he()
+    ps, psis, lay, cts, F, desc = U.conv_case(256, 2, 5, 6, 4, 4, 2, seed=8)
+    ref = _ref_conv(cts, F, ps, psis, lay, "extracted", tier="schoolbook")
+    with U.params(256, 2) as p, U.conv_bank(p, desc, F) as f:
+        got = U.run_conv(p, f, cts, H.HE_OUT_EXTRACTED, lay["H"])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_conv_inputs_in_ntt_domain():
+    H = U.he()
+    ps, psis, lay, cts, F, desc = U.conv_case(1024, 3, 16, 8, 8, 8, 2, seed=9)
+    ref = _ref_conv(cts, F, ps, psis, lay, "extracted")
+    with U.params(1024, 3) as p, U.conv_bank(p, desc, F) as f:
+        got = U.run_conv(p, f, cts, H.HE_OUT_EXTRACTED, lay["H"], in_domain=H.HE_NTT)
+    np.testing.assert_array_equal(got, ref)
+
+
+# ----------------------------------------------------------------------------
+# The single Conv config: N = 2048, one 30-bit prime, 3x16x16 input, 4 outputs
+# ----------------------------------------------------------------------------
+
+def test_conv1_config_bit_exact_and_decrypts():
+    H = U.he()
+    N, ci, co, h, w = 2048, 3, 4, 16, 16
+    ps, psis = U.ring(N, 1)
+    lay = O.conv_layout(N, ci, co, h, w)
+    F = synth.conv_weights(1, "conv1/F", co, ci, 3, 3, -8, 7)
+    I = synth.ints(1, "conv1/I", (ci, h, w), -8, 7)
+    desc = dict(ci=ci, co=co, h=h, w=w)
+    # uniform ciphertext, every mode, schoolbook reference
+    cts = synth.residues(1, "conv1/ct", (1, 1, 2, 1, N), ps)
+    with U.params(N, 1) as p, U.conv_bank(p, desc, F) as f:
+        for mode in MODES:
+            ref = _ref_conv(cts, F, ps, psis, lay, mode, tier="schoolbook")
+            got = U.run_conv(p, f, cts, _mode(H, mode), ref.shape[1])
+            np.testing.assert_array_equal(got, ref)
+        # a real RLWE encryption: ternary secret, centered-binomial error (eta 3)
+        s = synth.ternary(1, "conv1/s", N)
+        a = synth.residues(1, "conv1/a", (1, N), ps)
+        e = synth.cbd(1, "conv1/e", N, 3)
+        ct = O.encrypt_sk(O.pack_input(I, lay)[0], s, a, e, ps, U.T)[None, None]
+        y = U.run_conv(p, f, ct, H.HE_OUT_PER_CHANNEL, co)
+    want = O.centered(O.direct_conv(I, F, 1), U.T)
+    for n in range(co):
+        m = O.decrypt(y[0, n], s, ps, U.T)
+        got = np.array([[m[O.output_slot(lay, n, k, l)[1]] for l in range(w)] for k in range(h)])
+        np.testing.assert_array_equal(got, want[n])
+
+
+# ----------------------------------------------------------------------------
+# plain-20 layer shapes at N = 8192, 3 limbs, B = 1 (every word vs the CPU
+# NTT tier, plus sampled coefficients by schoolbook dot products)
+# ----------------------------------------------------------------------------
+
+PLAIN20_SHAPES = [(3, 16, 32), (16, 16, 32), (16, 32, 32), (32, 32, 16), (32, 64, 16), (64, 64, 8)]
+
+
+@pytest.mark.parametrize("ci,co,hw", PLAIN20_SHAPES)
+def test_plain20_layer_shapes_full_size(ci, co, hw):
+    H = U.he()
+    N, L = 8192, 3
+    ps, psis, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, 1, seed=20)
+    ref = _ref_conv(cts, F, ps, psis, lay, "extracted")
+    with U.params(N, L) as p, U.conv_bank(p, desc, F) as f:
+        got = U.run_conv(p, f, cts, H.HE_OUT_EXTRACTED, lay["H"])
+    np.testing.assert_array_equal(got, ref)
+    rng = np.random.default_rng(ci * 1000 + co)
+    picks = [(0, int(rng.integers(lay["H"])), int(rng.integers(2)), int(rng.integers(L)),
+              int(rng.integers(N))) for _ in range(24)]
+    np.testing.assert_array_equal(O.conv_layer_sampled(cts, F, ps, lay, picks),
+                                  np.array([got[pk] for pk in picks], dtype=np.uint32))
+
+
+# ----------------------------------------------------------------------------
+# wide layers: N = 16384, 6 limbs, B = 8
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("ci,co,hw", [(256, 256, 8), (3, 64, 32), (64, 128, 32)])
+def test_wide_layers_batch8(ci, co, hw):
+    H = U.he()
+    N, L, B = 16384, 6, 8
+    ps, psis, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, B, seed=40)
+    with U.params(N, L) as p, U.conv_bank(p, desc, F) as f:
+        got = U.run_conv(p, f, cts, H.HE_OUT_EXTRACTED, lay["H"])
+    # every word of two limbs against the CPU NTT tier, sampled words of all
+    for l in (0, L - 1):
+        ref = O.conv_layer(np.ascontiguousarray(cts[:, :, :, l:l + 1]), F, [ps[l]], [psis[l]],
+                           lay, O.OUT_EXTRACTED, tier="ntt")
+        np.testing.assert_array_equal(got[:, :, :, l:l + 1], ref)
+    rng = np.random.default_rng(co)
+    picks = [(int(rng.integers(B)), int(rng.integers(lay["H"])), int(rng.integers(2)),
+              int(rng.integers(L)), int(rng.integers(N))) for _ in range(16)]
+    np.testing.assert_array_equal(O.conv_layer_sampled(cts, F, ps, lay, picks),
+                                  np.array([got[pk] for pk in picks], dtype=np.uint32))
+
+
+# ----------------------------------------------------------------------------
+# FC
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,L,n_in,n_out,B,bias", [
+    (8192, 3, 64, 10, 1, True), (4096, 2, 64, 100, 2, True), (16384, 6, 256, 100, 8, False),
+    (512, 1, 6, 40, 3, True), (256, 2, 64, 10, 1, False)])
+def test_fc_matches_oracle(N, L, n_in, n_out, B, bias):
+    H = U.he()
+    ps, psis = U.ring(N, L)
+    lay = O.fc_layout(N, n_in, n_out)
+    W = synth.fc_weights(N, "fcW", n_out, n_in, -128, 127)
+    Bv = synth.ints(N, "fcB", (n_out,), -30000, 30000) if bias else None
+    ct = synth.residues(N, "fcct", (B, 2, L, N), ps)
+    with U.params(N, L) as p, U.fc_bank(p, n_in, n_out, W, Bv) as f:
+        for mode, omode in ((H.HE_OUT_EXTRACTED, O.OUT_EXTRACTED), (H.HE_OUT_PER_CHANNEL, O.OUT_PER_CHANNEL)):
+            got = U.run_fc(p, f, ct, mode, lay["P"])
+            ref = O.fc_layer(ct, W, Bv, ps, psis, U.T, lay, omode, tier="ntt")
+            np.testing.assert_array_equal(got, ref)
+
+
+def test_fc_encrypt_eval_decrypt():
+    H = U.he()
+    N, L, n_in, n_out = 8192, 3, 64, 10
+    ps, psis = U.ring(N, L)
+    lay = O.fc_layout(N, n_in, n_out)
+    W = synth.fc_weights(5, "W", n_out, n_in, -128, 127)
+    I = synth.ints(5, "I", (n_in,), -100, 100)
+    Bv = synth.ints(5, "B", (n_out,), -1000, 1000)
+    s = synth.ternary(5, "s", N)
+    a = synth.residues(5, "a", (L, N), ps)
+    ct = O.encrypt_sk(O.pack_fc_input(I, lay), s, a, synth.cbd(5, "e", N), ps, U.T)[None]
+    with U.params(N, L) as p, U.fc_bank(p, n_in, n_out, W, Bv) as f:
+        y = U.run_fc(p, f, ct, H.HE_OUT_PER_CHANNEL, lay["P"])
+    m = O.decrypt(y[0, 0], s, ps, U.T)
+    np.testing.assert_array_equal(m[:n_out], O.centered(W.astype(np.int64) @ I + Bv, U.T))
+
+
+# ----------------------------------------------------------------------------
+# argument errors, workspace growth, repeatability
+# ----------------------------------------------------------------------------
+
+def test_argument_errors_and_workspace_growth():
+    H = U.he()
+    torch = U.torch_cuda()
+    ps, psis, lay, cts, F, desc = U.conv_case(1024, 1, 8, 8, 6, 6, 4, seed=11)
+    with U.params(1024, 1) as p, U.conv_bank(p, desc, F) as f:
+        buf = U.empty_dev((8, lay["G"] * 2 * 1024 * 8))
+        with pytest.raises(H.HEError) as ei:   # overlapping input and output
+            H.he_conv_layer(p, f, buf, H.HE_COEFF, buf, H.HE_OUT_EXTRACTED, 1)
+        assert ei.value.status == H.HE_ERR_ARG
+        with pytest.raises(H.HEError) as ei:   # misaligned
+            H.he_conv_layer(p, f, buf.data_ptr() + 4, H.HE_COEFF, U.empty_dev((1 << 16,)),
+                            H.HE_OUT_EXTRACTED, 1)
+        assert ei.value.status == H.HE_ERR_ARG
+        with pytest.raises(H.HEError) as ei:   # conv bank given to the FC entry point
+            H.he_fc_layer(p, f, buf, H.HE_COEFF, U.empty_dev((1 << 16,)), H.HE_OUT_EXTRACTED, 1)
+        assert ei.value.status == H.HE_ERR_ARG
+        with pytest.raises(H.HEError) as ei:
+            H.he_conv_layer(p, f, buf, 7, U.empty_dev((1 << 16,)), H.HE_OUT_EXTRACTED, 1)
+        assert ei.value.status == H.HE_ERR_ARG
+        # the workspace grows from B = 1 to B = 4; results stay exact and repeatable
+        ref = O.conv_layer(cts, F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt")
+        got1 = U.run_conv(p, f, cts[:1], H.HE_OUT_EXTRACTED, lay["H"])
+        np.testing.assert_array_equal(got1, ref[:1])
+        got4 = U.run_conv(p, f, cts, H.HE_OUT_EXTRACTED, lay["H"])
+        got4b = U.run_conv(p, f, cts, H.HE_OUT_EXTRACTED, lay["H"])
+        np.testing.assert_array_equal(got4, ref)
+        np.testing.assert_array_equal(got4b, ref)
+    torch.cuda.synchronize()
