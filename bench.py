@@ -8,14 +8,17 @@ of 30-bit primes, t = 65537; int8 weights uniform in [-128, 127]; every layer
 input a fresh uniform ciphertext (c0, c1) in every limb.  One step = one
 inference = the 20 server-side layer calls.
 
-Forms measured:
-  graph  the 20 independent layer calls captured once in a CUDA graph over
-         several streams (input NTTs and channel kernels run concurrently),
-         replayed once per step -- the headline `value`;
-  plain  one layer at a time on one stream, CUDA events around every launch
-         (the per-kernel durations behind the roofline figures).
-Both rotate over 3 model replicas and 3 input sets (> 2x the 129 MB L2), so no
-step reads weights another step left in L2.
+Forms measured (same model, same inputs, same output words):
+  graph  a plan of the 20 independent layer calls (he_plan_create): one
+         kernel for every input NTT, one for every channel work unit of all
+         layers, captured once in a CUDA graph and replayed once per step --
+         the headline `value` and its p50/p99 per-inference latency;
+  phases the same plan run without the graph, CUDA events between its two
+         kernels -- the per-kernel durations behind the roofline figures;
+  plain  one layer at a time on one stream (he_ntt_forward then
+         he_conv_layer / he_fc_layer per layer), events around every launch.
+All forms rotate over 3 model replicas and 3 input sets (> 2x the 129 MB L2),
+so no step reads weights another step left in L2.
 
 --impl reference times the CPU oracle (its independent NTT tier, all host
 cores) on a bounded sample of the same layers.
@@ -87,7 +90,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -212,34 +215,22 @@ class Arm:
         for i in range(len(self.layers)):
             self._layer(r, i, stream, None if evs is None else evs[i])
 
-    def capture_graphs(self, nstreams=8):
-        torch = self.torch
-        self.graphs = []
-        main = torch.cuda.Stream()
-        side = [torch.cuda.Stream() for _ in range(nstreams)]
+    def make_plans(self):
+        """One plan per replica over all layer calls, and a CUDA graph of each."""
+        torch, H = self.torch, self.H
+        self.plans, self.graphs = [], []
         for r in range(self.R):
-            g = torch.cuda.CUDAGraph()
-            # warm the kernels' attributes outside capture
-            with torch.cuda.stream(main):
-                self.step_plain(r, main)
+            calls = [(self.models[r].banks[i], self.x[r][i], H.HE_COEFF, self.y[r][i], self.B)
+                     for i in range(len(self.layers))]
+            self.plans.append(H.he_plan_create(calls))
+        s = torch.cuda.Stream()
+        for r in range(self.R):
+            with torch.cuda.stream(s):
+                H.he_plan_run(self.plans[r], s)          # warm-up outside capture
             torch.cuda.synchronize()
-            with torch.cuda.graph(g, stream=main):
-                fork = torch.cuda.Event()
-                fork.record(main)
-                joins = []
-                for si, s in enumerate(side):
-                    s.wait_event(fork)
-                # largest layers first, round-robin over streams
-                order = sorted(range(len(self.layers)), key=lambda i: -self.geo[i]["wbytes"])
-                for n, i in enumerate(order):
-                    s = side[n % nstreams]
-                    self._layer(r, i, s)
-                for s in side:
-                    e = torch.cuda.Event()
-                    e.record(s)
-                    joins.append(e)
-                for e in joins:
-                    main.wait_event(e)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                H.he_plan_run(self.plans[r], s)
             self.graphs.append(g)
         torch.cuda.synchronize()
 
@@ -256,37 +247,45 @@ class Arm:
         return ch_bytes, ntt_bytes, bfly
 
     def free(self):
+        for pl in getattr(self, "plans", []):
+            self.H.he_plan_destroy(pl)
         for m in self.models:
             m.free()
         self.H.he_params_destroy(self.p)
+
+
+def _events(n):
+    import torch
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
 def run_ours(args, rank, world, device):
     import torch
     wl = workload(args.workload)
     arm = Arm(wl, device)
+    H = arm.H
     nl = len(arm.layers)
     stream = torch.cuda.Stream()
     K, W = args.steps, args.warmup
+    k_plain, k_phase = min(K, 200), min(K, 500)
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    # ---------------- plain form: one layer at a time, events per launch
-    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nl)] for _ in range(K)]
+    # ---------------- plain form: one layer at a time, events around every launch
+    evs = [[_events(3) for _ in range(nl)] for _ in range(k_plain)]
     with torch.cuda.stream(stream):
         for k in range(W):
             arm.step_plain(k, stream)
     torch.cuda.synchronize()
     barrier()
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
-    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t0, t1 = _events(2)
+    step_ev = [_events(2) for _ in range(k_plain)]
     with torch.cuda.stream(stream):
         t0.record(stream)
-        for k in range(K):
+        for k in range(k_plain):
             step_ev[k][0].record(stream)
             arm.step_plain(k, stream, evs[k])
             step_ev[k][1].record(stream)
@@ -295,11 +294,31 @@ def run_ours(args, rank, world, device):
     barrier()
     plain_ms = t0.elapsed_time(t1)
     plain_steps = [a.elapsed_time(b) for a, b in step_ev]
-    ntt_ms = sum(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(K) for i in range(nl))
-    ch_ms = sum(evs[k][i][1].elapsed_time(evs[k][i][2]) for k in range(K) for i in range(nl))
+    plain_ntt_ms = sum(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(k_plain) for i in range(nl))
+    plain_ch_ms = sum(evs[k][i][1].elapsed_time(evs[k][i][2]) for k in range(k_plain) for i in range(nl))
 
-    # ---------------- graph form: all layers of a step in one graph launch
-    arm.capture_graphs()
+    # ---------------- plan, phase by phase: events between its two kernels
+    arm.make_plans()
+    ph = [_events(3) for _ in range(k_phase)]
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            H.he_plan_run(arm.plans[k % arm.R], stream)
+    torch.cuda.synchronize()
+    barrier()
+    with torch.cuda.stream(stream):
+        for k in range(k_phase):
+            pl = arm.plans[k % arm.R]
+            ph[k][0].record(stream)
+            H.he_plan_run_phase(pl, 0, stream)
+            ph[k][1].record(stream)
+            H.he_plan_run_phase(pl, 1, stream)
+            ph[k][2].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ntt_ms = [e[0].elapsed_time(e[1]) for e in ph]
+    ch_ms = [e[1].elapsed_time(e[2]) for e in ph]
+
+    # ---------------- headline: the plan as a CUDA graph, one replay per step
     with torch.cuda.stream(stream):
         for k in range(W):
             arm.graphs[k % arm.R].replay()
@@ -307,7 +326,8 @@ def run_ours(args, rank, world, device):
     barrier()
     clocks = ClockSampler(device)
     clocks.start()
-    g_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    time.sleep(0.3)
+    g_ev = [_events(2) for _ in range(K)]
     with torch.cuda.stream(stream):
         t0.record(stream)
         for k in range(K):
@@ -326,36 +346,45 @@ def run_ours(args, rank, world, device):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         graph_ms, plain_ms = float(tt[0]), float(tt[1])
 
-    # ---------------- e2e: host buffers, H2D + layers + D2H every step
+    # ---------------- e2e: pinned host buffers, H2D + plan + D2H every step
     e2e = run_e2e(arm, args, stream)
 
     ch_bytes, ntt_bytes, bfly = arm.algorithmic()
     hbm, peak_src = _peaks()
-    ch_gbs = ch_bytes * K / (ch_ms * 1e-3) / 1e9
+    ch_avg = float(np.mean(ch_ms))
+    ntt_avg = float(np.mean(ntt_ms))
+    ch_gbs = ch_bytes / (ch_avg * 1e-3) / 1e9
     res = {
         "metric": METRIC, "value": nl * K * world / (graph_ms * 1e-3), "unit": "layers/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": graph_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 (exact residues mod 30-bit primes)", "data": "synthetic",
         "config": {"workload": wl["name"], "N": arm.N, "L": arm.L, "B": arm.B, "t": wl["t"],
-                   "layers_per_step": nl, "form": "graph (20 independent layer calls, 8 streams)",
+                   "layers_per_step": nl,
+                   "form": "plan of 20 layer calls (2 kernels) replayed as a CUDA graph",
                    "l2": "rotates 3 model replicas + 3 input sets (> 2x L2); no flush",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(graph_steps, 50)),
                        "p99": float(np.percentile(graph_steps, 99))},
-        "plain_form": {"value": nl * K * world / (plain_ms * 1e-3), "unit": "layers/s",
-                       "ms_per_step": plain_ms / K,
+        "plain_form": {"value": nl * k_plain * world / (plain_ms * 1e-3), "unit": "layers/s",
+                       "steps": k_plain, "ms_per_step": plain_ms / k_plain,
                        "latency_ms": {"p50": float(np.percentile(plain_steps, 50)),
                                       "p99": float(np.percentile(plain_steps, 99))},
-                       "kernel_ms_per_step": {"input_ntt": ntt_ms / K, "channel": ch_ms / K}},
-        "roofline": {"kernel": "channel MAC + folded INTT + extraction (plain form, per-launch events)",
+                       "kernel_ms_per_step": {"input_ntt": plain_ntt_ms / k_plain,
+                                              "channel": plain_ch_ms / k_plain}},
+        "speedup_vs_plain_form": (plain_ms / k_plain) / (graph_ms / K),
+        "roofline": {"kernel": "k_plan_chan<2>: channel MAC + folded INTT + extraction, all 20 layers",
                      "bound": "hbm", "achieved": ch_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": ch_gbs / hbm, "peak_source": peak_src,
-                     "algorithmic_bytes_per_step": ch_bytes, "traffic": None},
-        "ntt": {"ms_per_step": ntt_ms / K, "butterflies_per_step": bfly,
-                "gbfly_per_s": bfly * K / (ntt_ms * 1e-3) / 1e9, "bytes_per_step": ntt_bytes},
+                     "frac": ch_gbs / hbm, "peak_source": peak_src + " (hbm_gbs burst copy)",
+                     "algorithmic_bytes": ch_bytes, "avg_launch_ms": ch_avg, "launches": k_phase,
+                     "traffic": None},
+        "kernels": {"k_plan_ntt": {"avg_launch_ms": ntt_avg, "butterflies": bfly,
+                                   "gbfly_per_s": bfly / (ntt_avg * 1e-3) / 1e9,
+                                   "bytes": ntt_bytes, "gbs": ntt_bytes / (ntt_avg * 1e-3) / 1e9},
+                    "k_plan_chan": {"avg_launch_ms": ch_avg, "bytes": ch_bytes, "gbs": ch_gbs},
+                    "share_ntt": ntt_avg / (ntt_avg + ch_avg)},
         "e2e": e2e,
-        "gpu_launches": 2 * nl * K,
+        "gpu_launches": 2 * K,
         "clocks": clk,
     }
     arm.free()
@@ -363,26 +392,21 @@ def run_ours(args, rank, world, device):
 
 
 def run_e2e(arm, args, stream):
+    """Per step: H2D of the 20 layer inputs from pinned host memory, the plan
+    (graph replay), D2H of the 20 extracted outputs into pinned host memory."""
     torch = arm.torch
-    K = max(3, args.steps // 2)
+    K = max(20, min(args.steps, 2000))
     hx = [torch.empty(g["nin"], dtype=torch.int32, pin_memory=True) for g in arm.geo]
     hy = [torch.empty(g["nout"], dtype=torch.int32, pin_memory=True) for g in arm.geo]
     for i in range(len(hx)):
         hx[i].copy_(arm.x[0][i].cpu())
     h2d = sum(g["nin"] * 4 for g in arm.geo)
     d2h = sum(g["nout"] * 4 for g in arm.geo)
-    H = arm.H
 
     def step(r):
-        for i, Ld in enumerate(arm.layers):
+        for i in range(len(arm.layers)):
             arm.x[r][i].copy_(hx[i], non_blocking=True)
-        for i, Ld in enumerate(arm.layers):
-            if Ld["kind"] == "conv":
-                H.he_conv_layer(arm.p, arm.models[r].banks[i], arm.x[r][i], H.HE_COEFF, arm.y[r][i],
-                                H.HE_OUT_EXTRACTED, arm.B, stream)
-            else:
-                H.he_fc_layer(arm.p, arm.models[r].banks[i], arm.x[r][i], H.HE_COEFF, arm.y[r][i],
-                              H.HE_OUT_EXTRACTED, arm.B, stream)
+        arm.graphs[r].replay()
         for i in range(len(arm.layers)):
             hy[i].copy_(arm.y[r][i], non_blocking=True)
 
@@ -398,8 +422,8 @@ def run_e2e(arm, args, stream):
     dt = time.perf_counter() - t0
     return {"value": len(arm.layers) * K / dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": K,
-            "how": "pinned host inputs -> H2D, he_conv_layer/he_fc_layer (coefficient-domain input), "
-                   "D2H of every output, one stream, wall clock"}
+            "how": "per step: 20 H2D copies from pinned host memory, the plan (CUDA graph), "
+                   "20 D2H copies of the extracted outputs; one stream, wall clock"}
 
 
 # ----------------------------------------------------------------------------
@@ -473,8 +497,8 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain20_c10")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -204,6 +204,43 @@ he_status he_ntt_forward(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
 he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
                          uint32_t count, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Plans: many independent layer calls in one launch pair.
+ *
+ * A plan fixes a list of Conv / FC layer calls (any mix of ring degrees,
+ * limb counts, shapes and batch sizes whose params live on one device) and
+ * their buffers.  he_plan_run then issues exactly two kernels per batch-size
+ * class: one that computes every coefficient-domain input NTT of every call,
+ * and one that runs every channel work unit (one output channel x limb x
+ * column tile of a Conv call, or one weight polynomial x limb x column of an
+ * FC call) of every call, longest first.  Each call computes the words that
+ * he_conv_layer / he_fc_layer with HE_OUT_EXTRACTED would write.  The plan
+ * owns its NTT workspace and descriptor tables, so he_plan_run allocates
+ * nothing and can be captured into a CUDA graph.  Runs of one plan must not
+ * overlap on the GPU; different plans may run concurrently.
+ * (Batching pattern; the paper evaluates one layer at a time, Sec. IV.)
+ * ------------------------------------------------------------------------ */
+typedef struct he_plan_s *he_plan_t;
+
+typedef struct {
+    he_filters_t filters;   /* a Conv bank (he_pack_filters) or FC bank (he_pack_fc) */
+    const uint32_t *d_in;   /* DEVICE input, the layout of he_conv_layer / he_fc_layer */
+    int in_domain;          /* HE_COEFF or HE_NTT */
+    uint32_t *d_out;        /* DEVICE output, the HE_OUT_EXTRACTED layout */
+    uint32_t B;             /* ciphertexts in this call, >= 1 */
+} he_layer_call;
+
+/* Validates every call (shapes, alignment, one device, no output overlapping
+ * any input or other output) and builds the plan.  Blocking. */
+he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t *out);
+/* Runs every call of the plan.  Asynchronous on `stream`. */
+he_status he_plan_run(he_plan_t plan, void *stream);
+/* One half of he_plan_run: phase 0 = the input-NTT kernel, phase 1 = the
+ * channel kernels.  Phase 1 must follow phase 0 of the same run on the same
+ * stream (or be ordered after it); for timing each kernel separately. */
+he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream);
+void he_plan_destroy(he_plan_t plan);
+
 /* Wait for `stream` and report any pending CUDA error. */
 he_status he_sync(void *stream);
 

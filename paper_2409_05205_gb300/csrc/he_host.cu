@@ -563,6 +563,198 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out, u
     return e == cudaSuccess ? HE_OK : cuda_fail(e, "inverse NTT");
 }
 
+he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t *out) {
+    if (!calls || !out || ncalls == 0) return fail(HE_ERR_ARG, "NULL argument or empty plan");
+    *out = nullptr;
+    const he_params_s *p0 = calls[0].filters ? calls[0].filters->p : nullptr;
+    if (!p0) return fail(HE_ERR_ARG, "call 0 has no filters");
+    const int device = p0->device;
+    if (device == HE_DEVICE_NONE) return fail(HE_ERR_ARG, "params were created without a device");
+    struct Range {
+        uintptr_t lo, hi;
+        bool is_out;
+        uint32_t call;
+    };
+    std::vector<Range> ranges;
+    std::vector<CallDesc> descs(ncalls);
+    std::vector<size_t> ws_off(ncalls, 0);
+    size_t ws_words = 0;
+    for (uint32_t i = 0; i < ncalls; ++i) {
+        const he_layer_call &c = calls[i];
+        const he_filters_s *f = c.filters;
+        if (!f || !c.d_in || !c.d_out) return fail(HE_ERR_ARG, "call %u: NULL argument", i);
+        const he_params_s *p = f->p;
+        if (p->device != device) return fail(HE_ERR_ARG, "call %u: params on another device", i);
+        if (c.B == 0) return fail(HE_ERR_ARG, "call %u: B must be >= 1", i);
+        if (c.in_domain != HE_COEFF && c.in_domain != HE_NTT) return fail(HE_ERR_ARG, "call %u: bad in_domain", i);
+        if (!aligned16(c.d_in) || !aligned16(c.d_out)) return fail(HE_ERR_ARG, "call %u: buffers must be 16-byte aligned", i);
+        CallDesc &cd = descs[i];
+        memset(&cd, 0, sizeof(cd));
+        const RingView &r = p->ring;
+        ConvGeo &g = cd.g;
+        g.bank = f->bank;
+        g.out = c.d_out;
+        g.tw_inv = r.tw_inv;
+        g.psi_pow = r.psi_pow;
+        g.N = r.N;
+        g.logN = r.logN;
+        g.L = r.L;
+        g.ncols = 2u * c.B;
+        g.mode = HE_OUT_EXTRACTED;
+        cd.tw_fwd = r.tw_fwd;
+        for (uint32_t l = 0; l < r.L; ++l) cd.limb[l] = r.limb[l];
+        size_t nin, nout;
+        if (f->kind == HE_KIND_CONV) {
+            const he_conv_layout &lay = f->lay;
+            if ((size_t)2 * lay.M * 4u > 192u * 1024u)
+                return fail(HE_ERR_UNSUPPORTED, "call %u: N/s = %u too long for a plan", i, lay.M);
+            cd.kind = HE_KIND_CONV;
+            g.G = lay.G;
+            g.H = lay.H;
+            g.s = lay.s;
+            g.logs = he_ilog2(lay.s);
+            g.M = lay.M;
+            g.logM = he_ilog2(lay.M);
+            g.co = f->desc.co;
+            g.mult = lay.off_mult;
+            cd.nj = he_conv_nj(g.ncols, lay.M);
+            cd.nb = lay.s >= 4 ? 1 : (lay.s == 2 ? 2 : 4);
+            nin = (size_t)c.B * lay.G * 2u * r.L * r.N;
+            nout = (size_t)c.B * lay.H * 2u * r.L * r.N;
+        } else {
+            cd.kind = HE_KIND_FC;
+            g.bias = f->bias;
+            g.P = f->fl.P_fc;
+            g.rpp = f->fl.rows_per_poly;
+            g.n_out = f->fl.n_out;
+            cd.nj = 2;
+            nin = (size_t)c.B * 2u * r.L * r.N;
+            nout = (size_t)c.B * f->fl.P_fc * 2u * r.L * r.N;
+        }
+        if (c.in_domain == HE_COEFF) {
+            cd.x_coeff = c.d_in;
+            ws_off[i] = ws_words;
+            ws_words += nin;
+        } else {
+            g.x = c.d_in;
+        }
+        ranges.push_back({(uintptr_t)c.d_in, (uintptr_t)(c.d_in + nin), false, i});
+        ranges.push_back({(uintptr_t)c.d_out, (uintptr_t)(c.d_out + nout), true, i});
+    }
+    for (size_t a = 0; a < ranges.size(); ++a)
+        for (size_t b = a + 1; b < ranges.size(); ++b) {
+            if (!ranges[a].is_out && !ranges[b].is_out) continue;  // inputs may be shared
+            if (ranges[a].lo < ranges[b].hi && ranges[b].lo < ranges[a].hi)
+                return fail(HE_ERR_ARG, "calls %u and %u: an output overlaps another buffer", ranges[a].call,
+                            ranges[b].call);
+        }
+    DeviceGuard dg(device);
+    if (!dg.ok) return fail(HE_ERR_CUDA, "cannot select device %d", device);
+    he_plan_s *pl = new (std::nothrow) he_plan_s();
+    if (!pl) return fail(HE_ERR_NOMEM, "plan");
+    pl->device = device;
+    pl->ncalls = ncalls;
+    cudaError_t e = cudaSuccess;
+    if (ws_words) e = cudaMalloc(&pl->ws, ws_words * sizeof(uint32_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete pl;
+        return fail(HE_ERR_NOMEM, "plan workspace of %zu bytes", ws_words * 4);
+    }
+    // work items
+    std::vector<NttItem> ntt;
+    std::vector<std::pair<double, ChanItem>> chan[5];
+    std::vector<std::pair<double, NttItem>> ntt_cost;
+    for (uint32_t i = 0; i < ncalls; ++i) {
+        CallDesc &cd = descs[i];
+        ConvGeo &g = cd.g;
+        const double N = g.N, logN = g.logN;
+        if (cd.x_coeff) {
+            g.x = pl->ws + ws_off[i];
+            const size_t npoly = (cd.kind == HE_KIND_CONV ? (size_t)calls[i].B * g.G * 2u : (size_t)calls[i].B * 2u) * g.L;
+            for (size_t pidx = 0; pidx < npoly; ++pidx)
+                ntt_cost.push_back({N * logN, NttItem{i, (uint32_t)pidx}});
+        }
+        if (cd.kind == HE_KIND_CONV) {
+            const int cls = cd.nj == 2 ? 0 : cd.nj == 4 ? 1 : cd.nj == 8 ? 2 : 3;
+            const double cost = (double)g.G * N * cd.nj + 3.0 * cd.nj * (g.M / 2.0) * g.logM;
+            for (uint32_t n = 0; n < g.co; ++n)
+                for (uint32_t l = 0; l < g.L; ++l)
+                    for (uint32_t t = 0; t < g.ncols / cd.nj; ++t) chan[cls].push_back({cost, ChanItem{i, n, l, t}});
+        } else {
+            const double cost = N + 3.0 * (N / 2.0) * logN;
+            for (uint32_t jp = 0; jp < g.P; ++jp)
+                for (uint32_t l = 0; l < g.L; ++l)
+                    for (uint32_t col = 0; col < g.ncols; ++col) chan[0].push_back({cost, ChanItem{i, jp, l, col}});
+        }
+    }
+    auto by_cost = [](const auto &x, const auto &y) { return x.first > y.first; };
+    std::stable_sort(ntt_cost.begin(), ntt_cost.end(), by_cost);
+    for (auto &it : ntt_cost) {
+        ntt.push_back(it.second);
+        pl->smem_ntt = std::max(pl->smem_ntt, (size_t)descs[it.second.call].g.N * 4u);
+    }
+    pl->n_ntt = (uint32_t)ntt.size();
+    e = cudaMalloc(&pl->d_calls, sizeof(CallDesc) * ncalls);
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_calls, descs.data(), sizeof(CallDesc) * ncalls, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ntt.empty()) {
+        e = cudaMalloc(&pl->d_ntt, sizeof(NttItem) * ntt.size());
+        if (e == cudaSuccess) e = cudaMemcpy(pl->d_ntt, ntt.data(), sizeof(NttItem) * ntt.size(), cudaMemcpyHostToDevice);
+    }
+    for (int cls = 0; cls < 4 && e == cudaSuccess; ++cls) {
+        std::stable_sort(chan[cls].begin(), chan[cls].end(), by_cost);
+        std::vector<ChanItem> items;
+        size_t smem = 16;
+        const uint32_t nj = 2u << cls;
+        for (auto &it : chan[cls]) {
+            items.push_back(it.second);
+            const CallDesc &cd = descs[it.second.call];
+            smem = std::max(smem, cd.kind == HE_KIND_FC ? (size_t)cd.g.N * 4u : (size_t)nj * cd.g.M * 4u);
+        }
+        pl->n_chan[cls] = (uint32_t)items.size();
+        pl->smem_chan[cls] = smem;
+        if (!items.empty()) {
+            e = cudaMalloc(&pl->d_chan[cls], sizeof(ChanItem) * items.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(pl->d_chan[cls], items.data(), sizeof(ChanItem) * items.size(), cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess) e = he_plan_prepare(*pl);
+    if (e != cudaSuccess) {
+        he_plan_destroy(pl);
+        return cuda_fail(e, "plan tables");
+    }
+    *out = pl;
+    return HE_OK;
+}
+
+he_status he_plan_run(he_plan_t plan, void *stream) {
+    if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
+    cudaError_t e = he_launch_plan(*plan, (cudaStream_t)stream, -1);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "plan run");
+}
+
+he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream) {
+    if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
+    if (phase != 0 && phase != 1) return fail(HE_ERR_ARG, "phase must be 0 or 1");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
+    cudaError_t e = he_launch_plan(*plan, (cudaStream_t)stream, phase);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "plan run phase");
+}
+
+void he_plan_destroy(he_plan_t plan) {
+    if (!plan) return;
+    DeviceGuard g(plan->device);
+    cudaFree(plan->ws);
+    cudaFree(plan->d_calls);
+    cudaFree(plan->d_ntt);
+    for (int c = 0; c < 5; ++c) cudaFree(plan->d_chan[c]);
+    delete plan;
+}
+
 he_status he_sync(void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaGetLastError();

@@ -53,6 +53,48 @@ struct he_params_s {
 
 enum { HE_KIND_CONV = 1, HE_KIND_FC = 2 };
 
+// Geometry of one layer call as the channel kernels see it (no limb constants).
+struct ConvGeo {
+    const uint32_t *bank;     // conv: [co][L][G][N]; fc: [P][L][N]
+    const uint32_t *bias;     // fc: [L][n_out] or nullptr
+    const uint32_t *x;        // NTT-domain inputs: conv [B][G][2][L][N], fc [B][2][L][N]
+    uint32_t *out;            // conv [B][H|co][2][L][N], fc [B][P][2][L][N]
+    const uint2 *tw_inv;      // [L][N]
+    const uint32_t *psi_pow;  // [L][2N]
+    uint32_t N, logN, L, G, H, s, logs, M, logM, co, mult, ncols, mode;
+    uint32_t P, rpp, n_out;   // fc
+};
+
+// One layer call inside a plan (device-resident table).
+struct CallDesc {
+    ConvGeo g;
+    const uint32_t *x_coeff;  // coefficient-domain input (nullptr when the call's input is in NTT form)
+    const uint2 *tw_fwd;      // [L][N]
+    uint32_t kind, nj, nb, pad;
+    LimbK limb[HE_MAX_LIMBS];
+};
+
+struct NttItem {
+    uint32_t call, poly;      // poly index within the call's [npoly][L][N] input
+};
+
+struct ChanItem {
+    uint32_t call, a, l, b;   // conv: (channel n, limb, column tile); fc: (weight poly, limb, column)
+};
+
+struct he_plan_s {
+    int device;
+    uint32_t ncalls, n_ntt, n_chan[5];  // channel items per NJ class (2, 4, 8, 16) and FC
+    CallDesc *d_calls;
+    NttItem *d_ntt;
+    ChanItem *d_chan[5];
+    size_t smem_ntt, smem_chan[5];
+    uint32_t *ws;
+};
+
+cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase);
+cudaError_t he_plan_prepare(const he_plan_s &pl);
+
 struct he_filters_s {
     he_params_t p;
     int kind;
@@ -73,6 +115,8 @@ cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_c
                                 const he_conv_layout &lay, uint32_t *bank, cudaStream_t st);
 cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_layout &fl,
                               uint32_t *bank, cudaStream_t st);
+uint32_t he_conv_nj(uint32_t ncols, uint32_t M);
+uint32_t he_ilog2(uint32_t x);
 cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay,
                            const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out,
                            int mode, uint32_t B, cudaStream_t st);

@@ -6,7 +6,7 @@
 //  k_pack_conv    model load: packs fhat_{g,n} (Sec. III-A eq. (k_batch_new)),
 //                 transforms it and multiplies slot k by X_k^-off_n / N, the
 //                 factor that turns the channel sum below into the valid-slot-
-//                 only inverse transform (derivation at k_conv_fold).
+//                 only inverse transform (derivation at conv_fold_body).
 //  k_pack_fc      model load: packs w_j (Sec. III-B eq. (w(x) formula)).
 //  k_conv_fold    the hot kernel: NTT-domain channel MAC (Alg. 1 line 16,
 //                 summed over input groups), folded to the N/s slots one
@@ -16,6 +16,10 @@
 //                 whole product (per-channel output) or the slot copy.
 //  k_fc           FC server step (Alg. 2): product, INTT, first n_o
 //                 coefficients, + Delta_Q d(X) on c0.
+//  k_plan_ntt /   a plan: every input NTT of many independent layer calls
+//  k_plan_chan    (any ring degree, limb count and shape) in one launch, then
+//                 every channel work unit of all calls in one launch.
+#include <algorithm>
 #include <mutex>
 
 #include "he_internal.h"
@@ -29,23 +33,23 @@ __device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
 }
 
 // ---------------------------------------------------------------------------
-// NTT of independent RNS polynomials ([count][L][N]; polynomial p has limb p % L)
+// device bodies
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_ntt(const RingView r, const uint32_t *__restrict__ in,
-                                                 uint32_t *__restrict__ out, int inverse) {
-    extern __shared__ uint4 smem4[];
+
+// Transform polynomial `src` (N residues) into `dst` with the whole CTA.
+__device__ __forceinline__ void ntt_body(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                         uint32_t logN, const uint2 *tw, const LimbK &K, bool inverse,
+                                         uint4 *smem4) {
     uint32_t *a = reinterpret_cast<uint32_t *>(smem4);
-    const uint32_t p = blockIdx.x, N = r.N, l = p % r.L;
-    const LimbK K = r.limb[l];
-    const uint4 *src = reinterpret_cast<const uint4 *>(in + (size_t)p * N);
-    for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) smem4[i] = __ldg(src + i);
+    const uint32_t N = 1u << logN;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) smem4[i] = __ldg(s4 + i);
     __syncthreads();
-    if (!inverse) {
-        ntt_fwd_smem(a, r.logN, r.tw_fwd + (size_t)l * N, K.q);
-    } else {
-        ntt_inv_smem(a, 1, r.logN, r.tw_inv + (size_t)l * N, K.q);
-    }
-    uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)p * N);
+    if (!inverse)
+        ntt_fwd_smem(a, logN, tw, K.q);
+    else
+        ntt_inv_smem(a, 1, logN, tw, K.q);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
     for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) {
         uint4 v = smem4[i];
         if (!inverse) {
@@ -59,13 +63,233 @@ __global__ void __launch_bounds__(kThreads) k_ntt(const RingView r, const uint32
             v.z = red_2q(shoup_lazy(v.z, K.ninv, K.ninvs, K.q), K.q);
             v.w = red_2q(shoup_lazy(v.w, K.ninv, K.ninvs, K.q), K.q);
         }
-        dst[i] = v;
+        d4[i] = v;
+    }
+}
+
+// Zero the residue classes of output polynomial h that no channel uses
+// (c_o < s, or a last polynomial with fewer than s channels).
+__device__ __forceinline__ void zero_unused_classes(const ConvGeo &a, uint32_t h, uint32_t l, uint32_t col0,
+                                                    uint32_t ncol) {
+    const uint32_t cnt = min(a.s, a.co - h * a.s);
+    if (a.mult == 1 && cnt == a.s) return;
+    const uint32_t N = a.N, L = a.L;
+    for (uint32_t idx = threadIdx.x; idx < ncol * N; idx += blockDim.x) {
+        const uint32_t jj = idx / N, k = idx % N, c = col0 + jj;
+        const uint32_t r = k & (a.s - 1);
+        const bool used = (r % a.mult == 0) && (r / a.mult < cnt);
+        if (!used) a.out[((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N + k] = 0;
+    }
+}
+
+template <int NJ, int NB>
+__device__ __forceinline__ void mac4(uint64_t (&acc)[NJ][NB], const uint4 &w, const uint4 (&x)[NJ]) {
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+        const uint64_t p0 = (uint64_t)w.x * x[jj].x, p1 = (uint64_t)w.y * x[jj].y;
+        const uint64_t p2 = (uint64_t)w.z * x[jj].z, p3 = (uint64_t)w.w * x[jj].w;
+        if (NB == 1) {
+            acc[jj][0] += p0 + p1 + p2 + p3;
+        } else if (NB == 2) {
+            acc[jj][0] += p0 + p1;
+            acc[jj][NB - 1] += p2 + p3;
+        } else {
+            acc[jj][0] += p0;
+            acc[jj][1 % NB] += p1;
+            acc[jj][2 % NB] += p2;
+            acc[jj][3 % NB] += p3;
+        }
+    }
+}
+
+// Valid-slot-only form of one output channel n, limb l, NJ ciphertext
+// polynomials (columns col0 .. col0+NJ-1; column c = (b = c/2, j = c%2)).
+//
+// Write channel n's product y(X) = sum_{r'<s} X^r' y_r'(X^s).  The s NTT slots
+// of block kb (slots kb*s .. kb*s+s-1) are the s points X that share
+// X^s = zeta^(2 brv_M(kb)+1), zeta = psi^s, M = N/s; summing X^-r y(X) / s
+// over the block gives y_r(X^s) with r = off_n.  The bank holds fhat * X^-r / N,
+// so the channel MAC summed over each block gives y_r at the length-M NTT's
+// canonical point kb, and a length-M INTT (its M^-1 already in the bank)
+// returns y_r's coefficients: y's coefficients s*e + r, exactly the slots
+// the rotation-free copy keeps.
+//
+// Each thread owns 4 consecutive slots (one 128-bit load per operand); NB is
+// the number of blocks those 4 slots span (s >= 4: 1, s = 2: 2, s = 1: 4).
+// Groups are consumed 4 at a time with all their loads issued first.  A
+// 64-bit accumulator takes at most 16 products < (q-1)^2 on top of a residue
+// < q (16 (2^30-2)^2 + 2^30 < 2^64), then is reduced.
+template <int NJ, int NB>
+__device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K, uint32_t n, uint32_t l,
+                                               uint32_t col0, uint4 *smem4) {
+    uint32_t *Z = reinterpret_cast<uint32_t *>(smem4);  // [NJ][M]
+    const uint32_t N = a.N, L = a.L, G = a.G, s = a.s, M = a.M;
+    const uint32_t *W = a.bank + (size_t)(n * L + l) * G * N;
+    const size_t gstride = (size_t)2 * L * N;
+    const uint32_t *X[NJ];
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj) {
+        const uint32_t c = col0 + jj;
+        X[jj] = a.x + ((size_t)((c >> 1) * G * 2 + (c & 1)) * L + l) * N;
+    }
+    constexpr uint32_t kU = NB == 1 ? 4 : (NB == 2 ? 8 : 16);  // groups per reduction (16 products)
+    constexpr uint32_t kLd = 4;                               // groups whose loads are issued together
+    const uint32_t lanes = s >= 4 ? (s >> 2) : 1u;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nchunk = N >> 2;
+    for (uint32_t c0 = threadIdx.x & ~31u; c0 < nchunk; c0 += blockDim.x) {
+        const uint32_t c = c0 + lane;
+        const bool act = c < nchunk;
+        uint64_t acc[NJ][NB];
+#pragma unroll
+        for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+            for (int b = 0; b < NB; ++b) acc[jj][b] = 0;
+        if (act) {
+            uint32_t since = 0, g = 0;
+            for (; g + kLd <= G; g += kLd) {
+                uint4 w[kLd], x[kLd][NJ];
+#pragma unroll
+                for (uint32_t u = 0; u < kLd; ++u) {
+                    w[u] = ldg4(W + (size_t)(g + u) * N + 4u * c);
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj) x[u][jj] = ldg4(X[jj] + (g + u) * gstride + 4u * c);
+                }
+#pragma unroll
+                for (uint32_t u = 0; u < kLd; ++u) mac4<NJ, NB>(acc, w[u], x[u]);
+                since += kLd;
+                if (since + kLd > kU) {
+                    since = 0;
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) acc[jj][b] = reduce64(acc[jj][b], K);
+                }
+            }
+            for (; g < G; ++g) {
+                uint4 x[NJ];
+                const uint4 w = ldg4(W + (size_t)g * N + 4u * c);
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj) x[jj] = ldg4(X[jj] + g * gstride + 4u * c);
+                mac4<NJ, NB>(acc, w, x);
+                if (++since == kU) {
+                    since = 0;
+#pragma unroll
+                    for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+                        for (int b = 0; b < NB; ++b) acc[jj][b] = reduce64(acc[jj][b], K);
+                }
+            }
+        }
+        if (NB == 1) {
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj) {
+                uint32_t v = reduce64(acc[jj][0], K);
+                for (uint32_t o = 1; o < lanes; o <<= 1) {
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+                    v = v >= K.q ? v - K.q : v;
+                }
+                if (act && (lane & (lanes - 1)) == 0) Z[jj * M + ((4u * c) >> a.logs)] = v;
+            }
+        } else if (act) {
+#pragma unroll
+            for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+                for (int b = 0; b < NB; ++b) Z[jj * M + c * NB + b] = reduce64(acc[jj][b], K);
+        }
+    }
+    __syncthreads();
+    ntt_inv_smem(Z, NJ, a.logM, a.tw_inv + (size_t)l * N, K.q);
+    const uint32_t h = n >> a.logs, off = (n & (s - 1)) * a.mult;
+    for (uint32_t idx = threadIdx.x; idx < NJ * M; idx += blockDim.x) {
+        const uint32_t jj = idx >> a.logM, e = idx & (M - 1), c = col0 + jj;
+        uint32_t *o = a.out + ((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N;
+        o[(e << a.logs) + off] = red_2q(Z[idx], K.q);
+    }
+    if ((n & (s - 1)) == 0) zero_unused_classes(a, h, l, col0, NJ);
+}
+
+// Plain form: full products, length-N INTT, one column.  The bank holds
+// fhat * X^-r / N; slot k is multiplied back by X_k^r.
+__device__ __forceinline__ void conv_full_body(const ConvGeo &a, const LimbK &K, uint32_t n, uint32_t l,
+                                               uint32_t c, uint4 *smem4) {
+    uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
+    const uint32_t N = a.N, L = a.L, G = a.G, s = a.s, logN = a.logN;
+    const uint32_t *W = a.bank + (size_t)(n * L + l) * G * N;
+    const uint32_t *Xc = a.x + ((size_t)((c >> 1) * G * 2 + (c & 1)) * L + l) * N;
+    const size_t gstride = (size_t)2 * L * N;
+    const uint32_t off = (n & (s - 1)) * a.mult;
+    const uint32_t mask2n = 2u * N - 1u;
+    const uint32_t *pp = a.psi_pow + (size_t)l * 2u * N;
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+        uint64_t acc = 0;
+        int gc = 0;
+        for (uint32_t g = 0; g < G; ++g) {
+            acc += (uint64_t)__ldg(W + (size_t)g * N + k) * __ldg(Xc + g * gstride + k);
+            if (++gc == 16) {
+                gc = 0;
+                acc = reduce64(acc, K);
+            }
+        }
+        const uint32_t v = reduce64(acc, K);
+        const uint32_t ex = (off * (2u * brv(k, logN) + 1u)) & mask2n;
+        Y[k] = mulmod(v, __ldg(pp + ex), K);
+    }
+    __syncthreads();
+    ntt_inv_smem(Y, 1, logN, a.tw_inv + (size_t)l * N, K.q);
+    if (a.mode == HE_OUT_PER_CHANNEL) {
+        uint32_t *o = a.out + ((size_t)(((c >> 1) * a.co + n) * 2 + (c & 1)) * L + l) * N;
+        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) o[k] = red_2q(Y[k], K.q);
+    } else {
+        const uint32_t h = n >> a.logs;
+        uint32_t *o = a.out + ((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N;
+        for (uint32_t e = threadIdx.x; e < a.M; e += blockDim.x) {
+            const uint32_t k = (e << a.logs) + off;
+            o[k] = red_2q(Y[k], K.q);
+        }
+        if ((n & (s - 1)) == 0) zero_unused_classes(a, h, l, c, 1);
+    }
+}
+
+// FC server step for weight polynomial jp, limb l, column c.
+__device__ __forceinline__ void fc_body(const ConvGeo &a, const LimbK &K, uint32_t jp, uint32_t l, uint32_t c,
+                                        uint4 *smem4) {
+    uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
+    const uint32_t N = a.N, L = a.L;
+    const uint32_t *W = a.bank + (size_t)(jp * L + l) * N;
+    const uint32_t *Xc = a.x + ((size_t)c * L + l) * N;
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) Y[k] = mulmod(__ldg(W + k), __ldg(Xc + k), K);
+    __syncthreads();
+    ntt_inv_smem(Y, 1, a.logN, a.tw_inv + (size_t)l * N, K.q);
+    const uint32_t rows = min(a.rpp, a.n_out - jp * a.rpp);
+    uint32_t *o = a.out + ((size_t)(((c >> 1) * a.P + jp) * 2 + (c & 1)) * L + l) * N;
+    const bool c0 = (c & 1) == 0;
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+        uint32_t v = red_2q(Y[k], K.q);
+        if (k < rows) {
+            if (c0 && a.bias) {
+                v += __ldg(a.bias + (size_t)l * a.n_out + jp * a.rpp + k);
+                v = v >= K.q ? v - K.q : v;
+            }
+        } else if (a.mode != HE_OUT_PER_CHANNEL) {
+            v = 0;
+        }
+        o[k] = v;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Model load: Conv filter bank
+// single-call kernels
 // ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_ntt(const RingView r, const uint32_t *__restrict__ in,
+                                                 uint32_t *__restrict__ out, int inverse) {
+    extern __shared__ uint4 smem4[];
+    const uint32_t p = blockIdx.x, N = r.N, l = p % r.L;
+    const LimbK K = r.limb[l];
+    ntt_body(in + (size_t)p * N, out + (size_t)p * N, r.logN,
+             (inverse ? r.tw_inv : r.tw_fwd) + (size_t)l * N, K, inverse != 0, smem4);
+}
+
 struct PackConvArgs {
     RingView r;
     const int8_t *w;   // [co][ci][fh][fw]
@@ -113,9 +337,6 @@ __global__ void __launch_bounds__(kThreads) k_pack_conv(const PackConvArgs a) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// Model load: FC weight polynomials
-// ---------------------------------------------------------------------------
 struct PackFcArgs {
     RingView r;
     const int8_t *W;   // [n_out][n_in]
@@ -157,212 +378,52 @@ __global__ void __launch_bounds__(kThreads) k_pack_fc(const PackFcArgs a) {
     }
 }
 
-// ---------------------------------------------------------------------------
-// Conv server step
-// ---------------------------------------------------------------------------
-struct ConvArgs {
-    RingView r;
-    const uint32_t *bank;  // [co][L][G][N]
-    const uint32_t *x;     // [B][G][2][L][N], NTT domain
-    uint32_t *out;
-    uint32_t G, H, s, logs, M, logM, co, mult, ncols, mode;
-};
-
-// Zero the residue classes of output polynomial h that no channel uses
-// (c_o < s, or a last polynomial with fewer than s channels).
-__device__ __forceinline__ void zero_unused_classes(const ConvArgs &a, uint32_t h, uint32_t l,
-                                                    uint32_t col0, uint32_t ncol) {
-    const uint32_t cnt = min(a.s, a.co - h * a.s);
-    if (a.mult == 1 && cnt == a.s) return;
-    const uint32_t N = a.r.N, L = a.r.L;
-    for (uint32_t idx = threadIdx.x; idx < ncol * N; idx += blockDim.x) {
-        const uint32_t jj = idx / N, k = idx % N, c = col0 + jj;
-        const uint32_t r = k & (a.s - 1);
-        const bool used = (r % a.mult == 0) && (r / a.mult < cnt);
-        if (!used)
-            a.out[((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N + k] = 0;
-    }
-}
-
-// Valid-slot-only form.  For channel n with offset r = off_n write
-// y(X) = sum_{r'<s} X^r' y_r'(X^s).  The s NTT slots of block kb (slots
-// kb*s .. kb*s+s-1) are the s points X with the same X^s = zeta^(2 brv_M(kb)+1),
-// zeta = psi^s, M = N/s, and sum over the block of X^-r y(X) / s = y_r(X^s).
-// With the bank pre-multiplied by X^-r / N, the channel MAC summed over each
-// block gives, per block, the value of y_r at the length-M NTT's canonical
-// point, so a length-M INTT (without M^-1) returns y_r's coefficients, i.e.
-// y's coefficients s*e + r -- exactly the slots the rotation-free copy keeps.
-//
-// Grid: (co, L, ncols / NJ).  NJ ciphertext polynomials (b, j) per CTA share
-// every weight load.  Each thread owns 4 consecutive slots (one 128-bit load
-// per operand); NB = number of blocks those 4 slots span (s >= 4: 1).
 template <int NJ, int NB>
-__global__ void __launch_bounds__(kThreads) k_conv_fold(const ConvArgs a) {
+__global__ void __launch_bounds__(kThreads) k_conv_fold(const ConvGeo a, const RingView r) {
     extern __shared__ uint4 smem4[];
-    uint32_t *Z = reinterpret_cast<uint32_t *>(smem4);  // [NJ][M]
-    const uint32_t n = blockIdx.x, l = blockIdx.y, col0 = blockIdx.z * NJ;
-    const uint32_t N = a.r.N, L = a.r.L, G = a.G, s = a.s, M = a.M;
-    const LimbK K = a.r.limb[l];
-    const uint32_t *W = a.bank + (size_t)(n * L + l) * G * N;
-    const size_t gstride = (size_t)2 * L * N;
-    const uint32_t *X[NJ];
-#pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) {
-        const uint32_t c = col0 + jj;
-        X[jj] = a.x + ((size_t)((c >> 1) * G * 2 + (c & 1)) * L + l) * N;
-    }
-    constexpr int kPerG = 4 / NB;       // products per accumulator per group
-    constexpr int kGR = 15 / kPerG;     // groups between reductions (<= 15 products + residue < 2^64)
-    const uint32_t lanes = s >= 4 ? (s >> 2) : 1u;
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t nchunk = N >> 2;
-    for (uint32_t c0 = threadIdx.x & ~31u; c0 < nchunk; c0 += blockDim.x) {
-        const uint32_t c = c0 + lane;
-        const bool act = c < nchunk;
-        uint64_t acc[NJ][NB];
-#pragma unroll
-        for (int jj = 0; jj < NJ; ++jj)
-#pragma unroll
-            for (int b = 0; b < NB; ++b) acc[jj][b] = 0;
-        if (act) {
-            int gc = 0;
-            for (uint32_t g = 0; g < G; ++g) {
-                const uint4 w = ldg4(W + (size_t)g * N + 4u * c);
-#pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) {
-                    const uint4 x = ldg4(X[jj] + g * gstride + 4u * c);
-                    const uint64_t p0 = (uint64_t)w.x * x.x, p1 = (uint64_t)w.y * x.y;
-                    const uint64_t p2 = (uint64_t)w.z * x.z, p3 = (uint64_t)w.w * x.w;
-                    if (NB == 1) {
-                        acc[jj][0] += p0 + p1 + p2 + p3;
-                    } else if (NB == 2) {
-                        acc[jj][0] += p0 + p1;
-                        acc[jj][NB - 1] += p2 + p3;
-                    } else {
-                        acc[jj][0] += p0;
-                        acc[jj][1 % NB] += p1;
-                        acc[jj][2 % NB] += p2;
-                        acc[jj][3 % NB] += p3;
-                    }
-                }
-                if (++gc == kGR) {
-                    gc = 0;
-#pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj)
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) acc[jj][b] = reduce64(acc[jj][b], K);
-                }
-            }
-        }
-        if (NB == 1) {
-#pragma unroll
-            for (int jj = 0; jj < NJ; ++jj) {
-                uint32_t v = reduce64(acc[jj][0], K);
-                for (uint32_t o = 1; o < lanes; o <<= 1) {
-                    v += __shfl_xor_sync(0xffffffffu, v, o);
-                    v = v >= K.q ? v - K.q : v;
-                }
-                if (act && (lane & (lanes - 1)) == 0) Z[jj * M + ((4u * c) >> a.logs)] = v;
-            }
-        } else if (act) {
-#pragma unroll
-            for (int jj = 0; jj < NJ; ++jj)
-#pragma unroll
-                for (int b = 0; b < NB; ++b) Z[jj * M + c * NB + b] = reduce64(acc[jj][b], K);
-        }
-    }
-    __syncthreads();
-    ntt_inv_smem(Z, NJ, a.logM, a.r.tw_inv + (size_t)l * N, K.q);
-    const uint32_t h = n >> a.logs, off = (n & (s - 1)) * a.mult;
-    for (uint32_t idx = threadIdx.x; idx < NJ * M; idx += blockDim.x) {
-        const uint32_t jj = idx >> a.logM, e = idx & (M - 1), c = col0 + jj;
-        uint32_t *o = a.out + ((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N;
-        o[(e << a.logs) + off] = red_2q(Z[idx], K.q);
-    }
-    if ((n & (s - 1)) == 0) zero_unused_classes(a, h, l, col0, NJ);
+    conv_fold_body<NJ, NB>(a, r.limb[blockIdx.y], blockIdx.x, blockIdx.y, blockIdx.z * NJ, smem4);
 }
 
-// Plain form: full products, length-N INTT.  Grid (co, L, ncols).
-// The bank holds fhat * X^-r / N; slot k is multiplied back by X_k^r.
-__global__ void __launch_bounds__(kThreads) k_conv_full(const ConvArgs a) {
+__global__ void __launch_bounds__(kThreads) k_conv_full(const ConvGeo a, const RingView r) {
     extern __shared__ uint4 smem4[];
-    uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
-    const uint32_t n = blockIdx.x, l = blockIdx.y, c = blockIdx.z;
-    const uint32_t N = a.r.N, L = a.r.L, G = a.G, s = a.s, logN = a.r.logN;
-    const LimbK K = a.r.limb[l];
-    const uint32_t *W = a.bank + (size_t)(n * L + l) * G * N;
-    const uint32_t *Xc = a.x + ((size_t)((c >> 1) * G * 2 + (c & 1)) * L + l) * N;
-    const size_t gstride = (size_t)2 * L * N;
-    const uint32_t off = (n & (s - 1)) * a.mult;
-    const uint32_t mask2n = 2u * N - 1u;
-    const uint32_t *pp = a.r.psi_pow + (size_t)l * 2u * N;
-    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
-        uint64_t acc = 0;
-        int gc = 0;
-        for (uint32_t g = 0; g < G; ++g) {
-            acc += (uint64_t)__ldg(W + (size_t)g * N + k) * __ldg(Xc + g * gstride + k);
-            if (++gc == 15) {
-                gc = 0;
-                acc = reduce64(acc, K);
-            }
-        }
-        uint32_t v = reduce64(acc, K);
-        const uint32_t ex = (off * (2u * brv(k, logN) + 1u)) & mask2n;
-        Y[k] = mulmod(v, __ldg(pp + ex), K);
-    }
-    __syncthreads();
-    ntt_inv_smem(Y, 1, logN, a.r.tw_inv + (size_t)l * N, K.q);
-    if (a.mode == HE_OUT_PER_CHANNEL) {
-        uint32_t *o = a.out + ((size_t)(((c >> 1) * a.co + n) * 2 + (c & 1)) * L + l) * N;
-        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) o[k] = red_2q(Y[k], K.q);
+    conv_full_body(a, r.limb[blockIdx.y], blockIdx.x, blockIdx.y, blockIdx.z, smem4);
+}
+
+__global__ void __launch_bounds__(kThreads) k_fc(const ConvGeo a, const RingView r) {
+    extern __shared__ uint4 smem4[];
+    fc_body(a, r.limb[blockIdx.y], blockIdx.x, blockIdx.y, blockIdx.z, smem4);
+}
+
+// ---------------------------------------------------------------------------
+// plan kernels (one CTA per item; items are ordered longest first on the host)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) k_plan_ntt(const CallDesc *__restrict__ calls,
+                                                      const NttItem *__restrict__ items) {
+    extern __shared__ uint4 smem4[];
+    const NttItem it = items[blockIdx.x];
+    const CallDesc &cd = calls[it.call];
+    const uint32_t N = cd.g.N, L = cd.g.L, l = it.poly % L;
+    const LimbK K = cd.limb[l];
+    ntt_body(cd.x_coeff + (size_t)it.poly * N, const_cast<uint32_t *>(cd.g.x) + (size_t)it.poly * N, cd.g.logN,
+             cd.tw_fwd + (size_t)l * N, K, false, smem4);
+}
+
+template <int NJ>
+__global__ void __launch_bounds__(kThreads) k_plan_chan(const CallDesc *__restrict__ calls,
+                                                       const ChanItem *__restrict__ items) {
+    extern __shared__ uint4 smem4[];
+    const ChanItem it = items[blockIdx.x];
+    const CallDesc &cd = calls[it.call];
+    const ConvGeo g = cd.g;
+    const LimbK K = cd.limb[it.l];
+    if (cd.kind == HE_KIND_FC) {
+        fc_body(g, K, it.a, it.l, it.b, smem4);
+    } else if (cd.nb == 1) {
+        conv_fold_body<NJ, 1>(g, K, it.a, it.l, it.b * NJ, smem4);
+    } else if (cd.nb == 2) {
+        conv_fold_body<NJ, 2>(g, K, it.a, it.l, it.b * NJ, smem4);
     } else {
-        const uint32_t h = n >> a.logs;
-        uint32_t *o = a.out + ((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N;
-        for (uint32_t e = threadIdx.x; e < a.M; e += blockDim.x) {
-            const uint32_t k = (e << a.logs) + off;
-            o[k] = red_2q(Y[k], K.q);
-        }
-        if ((n & (s - 1)) == 0) zero_unused_classes(a, h, l, c, 1);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// FC server step.  Grid (P, L, ncols).
-// ---------------------------------------------------------------------------
-struct FcArgs {
-    RingView r;
-    const uint32_t *bank;  // [P][L][N]
-    const uint32_t *bias;  // [L][n_out] or nullptr
-    const uint32_t *x;     // [B][2][L][N], NTT domain
-    uint32_t *out;         // [B][P][2][L][N]
-    uint32_t P, rpp, n_out, mode;
-};
-
-__global__ void __launch_bounds__(kThreads) k_fc(const FcArgs a) {
-    extern __shared__ uint4 smem4[];
-    uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
-    const uint32_t jp = blockIdx.x, l = blockIdx.y, c = blockIdx.z;
-    const uint32_t N = a.r.N, L = a.r.L;
-    const LimbK K = a.r.limb[l];
-    const uint32_t *W = a.bank + (size_t)(jp * L + l) * N;
-    const uint32_t *Xc = a.x + ((size_t)c * L + l) * N;
-    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) Y[k] = mulmod(__ldg(W + k), __ldg(Xc + k), K);
-    __syncthreads();
-    ntt_inv_smem(Y, 1, a.r.logN, a.r.tw_inv + (size_t)l * N, K.q);
-    const uint32_t rows = min(a.rpp, a.n_out - jp * a.rpp);
-    uint32_t *o = a.out + ((size_t)(((c >> 1) * a.P + jp) * 2 + (c & 1)) * L + l) * N;
-    const bool c0 = (c & 1) == 0;
-    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
-        uint32_t v = red_2q(Y[k], K.q);
-        if (k < rows) {
-            if (c0 && a.bias) {
-                v += __ldg(a.bias + (size_t)l * a.n_out + jp * a.rpp + k);
-                v = v >= K.q ? v - K.q : v;
-            }
-        } else if (a.mode != HE_OUT_PER_CHANNEL) {
-            v = 0;
-        }
-        o[k] = v;
+        conv_fold_body<NJ, 4>(g, K, it.a, it.l, it.b * NJ, smem4);
     }
 }
 
@@ -378,8 +439,8 @@ std::mutex g_smem_mu;
 SmemOptIn g_smem[256];
 int g_nsmem = 0;
 
-template <typename K>
-cudaError_t set_smem(K kernel, size_t bytes) {
+template <typename Kern>
+cudaError_t set_smem(Kern kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -399,20 +460,28 @@ cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 template <int NJ, int NB>
-cudaError_t launch_fold(const ConvArgs &a, uint32_t co, uint32_t L, cudaStream_t st) {
-    const size_t smem = (size_t)NJ * a.M * 4u < 16 ? 16 : (size_t)NJ * a.M * 4u;
+cudaError_t launch_fold(const ConvGeo &a, const RingView &r, cudaStream_t st) {
+    const size_t smem = std::max<size_t>(16, (size_t)NJ * a.M * 4u);
     cudaError_t e = set_smem(k_conv_fold<NJ, NB>, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid(co, L, a.ncols / NJ);
-    k_conv_fold<NJ, NB><<<grid, kThreads, smem, st>>>(a);
+    k_conv_fold<NJ, NB><<<dim3(a.co, a.L, a.ncols / NJ), kThreads, smem, st>>>(a, r);
     return cudaGetLastError();
 }
 
 template <int NJ>
-cudaError_t launch_fold_nb(const ConvArgs &a, uint32_t co, uint32_t L, cudaStream_t st) {
-    if (a.s >= 4) return launch_fold<NJ, 1>(a, co, L, st);
-    if (a.s == 2) return launch_fold<NJ, 2>(a, co, L, st);
-    return launch_fold<NJ, 4>(a, co, L, st);
+cudaError_t launch_fold_nb(const ConvGeo &a, const RingView &r, cudaStream_t st) {
+    if (a.s >= 4) return launch_fold<NJ, 1>(a, r, st);
+    if (a.s == 2) return launch_fold<NJ, 2>(a, r, st);
+    return launch_fold<NJ, 4>(a, r, st);
+}
+
+template <int NJ>
+cudaError_t plan_chan_launch(const he_plan_s &pl, int cls, cudaStream_t st) {
+    if (pl.n_chan[cls] == 0) return cudaSuccess;
+    cudaError_t e = set_smem(k_plan_chan<NJ>, pl.smem_chan[cls]);
+    if (e != cudaSuccess) return e;
+    k_plan_chan<NJ><<<pl.n_chan[cls], kThreads, pl.smem_chan[cls], st>>>(pl.d_calls, pl.d_chan[cls]);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -420,8 +489,22 @@ cudaError_t launch_fold_nb(const ConvArgs &a, uint32_t co, uint32_t L, cudaStrea
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-cudaError_t he_launch_ntt(const RingView &r, const uint32_t *in, uint32_t *out, uint32_t npolys,
-                          bool inverse, cudaStream_t st) {
+uint32_t he_ilog2(uint32_t x) {
+    uint32_t l = 0;
+    while ((1u << l) < x) ++l;
+    return l;
+}
+
+// Columns per CTA of the folded kernel: the largest power of two <= 16 that
+// divides 2B and whose block vectors fit 160 KB of shared memory.
+uint32_t he_conv_nj(uint32_t ncols, uint32_t M) {
+    uint32_t nj = 16;
+    while (nj > 2 && ((ncols % nj) != 0 || (size_t)nj * M * 4u > 160u * 1024u)) nj >>= 1;
+    return nj;
+}
+
+cudaError_t he_launch_ntt(const RingView &r, const uint32_t *in, uint32_t *out, uint32_t npolys, bool inverse,
+                          cudaStream_t st) {
     if (npolys == 0) return cudaSuccess;
     const size_t smem = (size_t)r.N * 4u;
     cudaError_t e = set_smem(k_ntt, smem);
@@ -451,8 +534,8 @@ cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_c
     return cudaGetLastError();
 }
 
-cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_layout &fl,
-                              uint32_t *bank, cudaStream_t st) {
+cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_layout &fl, uint32_t *bank,
+                              cudaStream_t st) {
     PackFcArgs a;
     a.r = r;
     a.W = d_W;
@@ -468,61 +551,55 @@ cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_
     return cudaGetLastError();
 }
 
-static uint32_t ilog2u(uint32_t x) {
-    uint32_t l = 0;
-    while ((1u << l) < x) ++l;
-    return l;
+static ConvGeo geo_of(const RingView &r) {
+    ConvGeo a{};
+    a.tw_inv = r.tw_inv;
+    a.psi_pow = r.psi_pow;
+    a.N = r.N;
+    a.logN = r.logN;
+    a.L = r.L;
+    return a;
 }
 
 cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay,
-                           const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out, int mode,
-                           uint32_t B, cudaStream_t st) {
-    ConvArgs a;
-    a.r = r;
+                           const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out, int mode, uint32_t B,
+                           cudaStream_t st) {
+    ConvGeo a = geo_of(r);
     a.bank = bank;
     a.x = x_ntt;
     a.out = out;
     a.G = lay.G;
     a.H = lay.H;
     a.s = lay.s;
-    a.logs = ilog2u(lay.s);
+    a.logs = he_ilog2(lay.s);
     a.M = lay.M;
-    a.logM = ilog2u(lay.M);
+    a.logM = he_ilog2(lay.M);
     a.co = d.co;
     a.mult = lay.off_mult;
     a.ncols = 2u * B;
-    a.mode = (uint32_t)mode;
     // The folded kernel keeps 2 * M words per CTA in shared memory; for
     // M = N / s above 24K words (s = 1 at N = 32768) the unfolded kernel
     // produces the same words with N words of shared memory.
-    if (mode == HE_OUT_EXTRACTED && (size_t)2 * lay.M * 4u > 192u * 1024u) {
-        a.mode = HE_OUT_EXTRACTED_UNFOLDED;
-        mode = HE_OUT_EXTRACTED_UNFOLDED;
-    }
+    if (mode == HE_OUT_EXTRACTED && (size_t)2 * lay.M * 4u > 192u * 1024u) mode = HE_OUT_EXTRACTED_UNFOLDED;
+    a.mode = (uint32_t)mode;
     if (mode == HE_OUT_EXTRACTED) {
-        // columns per CTA: largest power of two <= 16 dividing 2B whose
-        // block vectors fit 160 KB of shared memory
-        uint32_t nj = 16;
-        while (nj > 2 && ((a.ncols % nj) != 0 || (size_t)nj * lay.M * 4u > 160u * 1024u)) nj >>= 1;
-        switch (nj) {
-            case 16: return launch_fold_nb<16>(a, d.co, r.L, st);
-            case 8: return launch_fold_nb<8>(a, d.co, r.L, st);
-            case 4: return launch_fold_nb<4>(a, d.co, r.L, st);
-            default: return launch_fold_nb<2>(a, d.co, r.L, st);
+        switch (he_conv_nj(a.ncols, lay.M)) {
+            case 16: return launch_fold_nb<16>(a, r, st);
+            case 8: return launch_fold_nb<8>(a, r, st);
+            case 4: return launch_fold_nb<4>(a, r, st);
+            default: return launch_fold_nb<2>(a, r, st);
         }
     }
     const size_t smem = (size_t)r.N * 4u;
     cudaError_t e = set_smem(k_conv_full, smem);
     if (e != cudaSuccess) return e;
-    k_conv_full<<<dim3(d.co, r.L, a.ncols), kThreads, smem, st>>>(a);
+    k_conv_full<<<dim3(d.co, r.L, a.ncols), kThreads, smem, st>>>(a, r);
     return cudaGetLastError();
 }
 
-cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32_t *bank,
-                         const uint32_t *bias, const uint32_t *x_ntt, uint32_t *out, int mode,
-                         uint32_t B, cudaStream_t st) {
-    FcArgs a;
-    a.r = r;
+cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32_t *bank, const uint32_t *bias,
+                         const uint32_t *x_ntt, uint32_t *out, int mode, uint32_t B, cudaStream_t st) {
+    ConvGeo a = geo_of(r);
     a.bank = bank;
     a.bias = bias;
     a.x = x_ntt;
@@ -534,6 +611,34 @@ cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32
     const size_t smem = (size_t)r.N * 4u;
     cudaError_t e = set_smem(k_fc, smem);
     if (e != cudaSuccess) return e;
-    k_fc<<<dim3(fl.P_fc, r.L, 2u * B), kThreads, smem, st>>>(a);
+    k_fc<<<dim3(fl.P_fc, r.L, 2u * B), kThreads, smem, st>>>(a, r);
     return cudaGetLastError();
+}
+
+// Sets the shared-memory opt-ins a plan needs (called once, outside capture).
+cudaError_t he_plan_prepare(const he_plan_s &pl) {
+    cudaError_t e = cudaSuccess;
+    if (pl.n_ntt) e = set_smem(k_plan_ntt, pl.smem_ntt);
+    if (e == cudaSuccess && pl.n_chan[0]) e = set_smem(k_plan_chan<2>, pl.smem_chan[0]);
+    if (e == cudaSuccess && pl.n_chan[1]) e = set_smem(k_plan_chan<4>, pl.smem_chan[1]);
+    if (e == cudaSuccess && pl.n_chan[2]) e = set_smem(k_plan_chan<8>, pl.smem_chan[2]);
+    if (e == cudaSuccess && pl.n_chan[3]) e = set_smem(k_plan_chan<16>, pl.smem_chan[3]);
+    return e;
+}
+
+// phase: -1 = both, 0 = input NTTs only, 1 = channel kernels only.
+cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
+    cudaError_t e = cudaSuccess;
+    if (pl.n_ntt && phase != 1) {
+        e = set_smem(k_plan_ntt, pl.smem_ntt);
+        if (e != cudaSuccess) return e;
+        k_plan_ntt<<<pl.n_ntt, kThreads, pl.smem_ntt, st>>>(pl.d_calls, pl.d_ntt);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (phase == 0) return cudaSuccess;
+    if ((e = plan_chan_launch<2>(pl, 0, st)) != cudaSuccess) return e;
+    if ((e = plan_chan_launch<4>(pl, 1, st)) != cudaSuccess) return e;
+    if ((e = plan_chan_launch<8>(pl, 2, st)) != cudaSuccess) return e;
+    return plan_chan_launch<16>(pl, 3, st);
 }

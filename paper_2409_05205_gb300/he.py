@@ -45,6 +45,11 @@ class he_fc_layout(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("n_in", "n_in_p", "n_out", "rows_per_poly", "P_fc")]
 
 
+class he_layer_call(ctypes.Structure):
+    _fields_ = [("filters", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("in_domain", ctypes.c_int),
+                ("d_out", ctypes.c_void_p), ("B", ctypes.c_uint32)]
+
+
 _lib = None
 
 _vp, _u32, _i32, _sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
@@ -65,10 +70,14 @@ _SIGS = {
     "he_fc_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
     "he_ntt_forward": [_vp, _vp, _vp, _u32, _vp],
     "he_ntt_inverse": [_vp, _vp, _vp, _u32, _vp],
+    "he_plan_create": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(_vp)],
+    "he_plan_run": [_vp, _vp],
+    "he_plan_run_phase": [_vp, _i32, _vp],
+    "he_plan_destroy": [_vp],
     "he_sync": [_vp],
     "he_last_error": [],
 }
-_VOID = {"he_params_destroy", "he_filters_destroy"}
+_VOID = {"he_params_destroy", "he_filters_destroy", "he_plan_destroy"}
 
 
 def lib() -> ctypes.CDLL:
@@ -220,6 +229,31 @@ def he_ntt_forward(p: int, d_in, d_out, count: int, stream=None) -> None:
 
 def he_ntt_inverse(p: int, d_in, d_out, count: int, stream=None) -> None:
     _check(lib().he_ntt_inverse(p, _ptr(d_in), _ptr(d_out), count, _stream(stream)))
+
+
+def he_plan_create(calls) -> int:
+    """calls: sequence of (filters, d_in, in_domain, d_out, B) tuples or dicts."""
+    arr = (he_layer_call * len(calls))()
+    for i, c in enumerate(calls):
+        if isinstance(c, dict):
+            c = (c["filters"], c["d_in"], c.get("in_domain", HE_COEFF), c["d_out"], c["B"])
+        f, d_in, dom, d_out, B = c
+        arr[i] = he_layer_call(f, _ptr(d_in), dom, _ptr(d_out), B)
+    out = _vp()
+    _check(lib().he_plan_create(arr, len(calls), ctypes.byref(out)))
+    return out.value
+
+
+def he_plan_run(plan: int, stream=None) -> None:
+    _check(lib().he_plan_run(plan, _stream(stream)))
+
+
+def he_plan_run_phase(plan: int, phase: int, stream=None) -> None:
+    _check(lib().he_plan_run_phase(plan, phase, _stream(stream)))
+
+
+def he_plan_destroy(plan: int) -> None:
+    lib().he_plan_destroy(plan)
 
 
 def he_sync(stream=None) -> None:

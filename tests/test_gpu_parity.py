@@ -254,3 +254,123 @@ def test_argument_errors_and_workspace_growth():
         np.testing.assert_array_equal(got4, ref)
         np.testing.assert_array_equal(got4b, ref)
     torch.cuda.synchronize()
+
+
+# ----------------------------------------------------------------------------
+# plans: many calls in one launch pair, bit-exact against the oracle
+# ----------------------------------------------------------------------------
+
+def _plan_case(H, p, N, L, shape, B, seed, fc=False):
+    ps, psis = U.ring(N, L)
+    if fc:
+        n_in, n_out = shape
+        lay = O.fc_layout(N, n_in, n_out)
+        W = synth.fc_weights(seed, "pW", n_out, n_in, -128, 127)
+        Bv = synth.ints(seed, "pB", (n_out,), -999, 999)
+        ct = synth.residues(seed, "pct", (B, 2, L, N), ps)
+        ref = O.fc_layer(ct, W, Bv, ps, psis, U.T, lay, O.OUT_EXTRACTED, tier="ntt")
+        f = H.he_pack_fc(p, n_in, n_out, W, Bv)
+        return f, ct, ref
+    ci, co, hw = shape
+    _, _, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, B, seed=seed)
+    ref = O.conv_layer(cts, F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt")
+    f = H.he_pack_filters(p, desc, F)
+    return f, cts, ref
+
+
+def test_plan_mixed_rings_and_shapes_bit_exact():
+    """A plan over independent calls with N in {1024, 2048, 4096}, 1-3 limbs,
+    B in {1, 2, 8}, Conv shapes with s = 2 .. 64 and FC layers (one of them
+    split over 2 weight polynomials), some inputs already in the NTT domain."""
+    H = U.he()
+    torch = U.torch_cuda()
+    specs = [(1024, 2, (16, 16, 8), 1, False), (2048, 1, (3, 4, 16), 1, False),
+             (4096, 3, (16, 16, 32), 1, False), (4096, 2, (64, 100), 1, True),
+             (2048, 3, (32, 64, 4), 2, False), (1024, 1, (64, 10), 2, True),
+             (4096, 2, (8, 16, 8), 8, False)]
+    pars = {}
+    calls, refs, outs, keep = [], [], [], []
+    try:
+        for k, (N, L, shape, B, fc) in enumerate(specs):
+            if (N, L) not in pars:
+                pars[(N, L)] = H.he_params_create(N, L, None, U.T, 0)
+            p = pars[(N, L)]
+            f, x, ref = _plan_case(H, p, N, L, shape, B, seed=100 + k, fc=fc)
+            dom = H.HE_NTT if k % 3 == 2 else H.HE_COEFF
+            if dom == H.HE_NTT:
+                ps, psis = U.ring(N, L)
+                x = x.copy()
+                for l in range(L):
+                    x[..., l, :] = O.ntt_fwd(np.ascontiguousarray(x[..., l, :]), ps[l], psis[l])
+            d_in = U.to_dev(x)
+            d_out = U.empty_dev(ref.shape)
+            keep += [d_in, d_out]
+            calls.append((f, d_in, dom, d_out, B))
+            refs.append(ref)
+            outs.append(d_out)
+        plan = H.he_plan_create(calls)
+        try:
+            s = torch.cuda.current_stream()
+            for _ in range(2):           # repeatable: every word rewritten each run
+                for o in outs:
+                    o.fill_(-1)
+                H.he_plan_run(plan, s)
+                H.he_sync(s)
+                for o, ref in zip(outs, refs):
+                    np.testing.assert_array_equal(U.from_dev(o).reshape(ref.shape), ref)
+        finally:
+            H.he_plan_destroy(plan)
+    finally:
+        for c in calls:
+            H.he_filters_destroy(c[0])
+        for p in pars.values():
+            H.he_params_destroy(p)
+
+
+def test_plan_captured_in_cuda_graph_matches_single_calls():
+    H = U.he()
+    torch = U.torch_cuda()
+    N, L = 8192, 3
+    with U.params(N, L) as p:
+        shapes = [(3, 16, 32), (16, 32, 32), (64, 64, 8)]
+        banks, calls, singles = [], [], []
+        for k, sh in enumerate(shapes):
+            ps, psis, lay, cts, F, desc = U.conv_case(N, L, sh[0], sh[1], sh[2], sh[2], 1, seed=200 + k)
+            f = H.he_pack_filters(p, desc, F)
+            banks.append(f)
+            singles.append(U.run_conv(p, f, cts, H.HE_OUT_EXTRACTED, lay["H"]))
+            d_in, d_out = U.to_dev(cts), U.empty_dev(singles[-1].shape)
+            calls.append((f, d_in, H.HE_COEFF, d_out, 1))
+        plan = H.he_plan_create(calls)
+        try:
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                H.he_plan_run(plan, s)          # warm-up outside capture
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                H.he_plan_run(plan, s)
+            for c in calls:
+                c[3].fill_(-1)
+            g.replay()
+            torch.cuda.synchronize()
+            for c, ref in zip(calls, singles):
+                np.testing.assert_array_equal(U.from_dev(c[3]).reshape(ref.shape), ref)
+        finally:
+            H.he_plan_destroy(plan)
+            for f in banks:
+                H.he_filters_destroy(f)
+
+
+def test_plan_rejects_overlapping_outputs():
+    H = U.he()
+    ps, psis, lay, cts, F, desc = U.conv_case(1024, 1, 8, 8, 6, 6, 1, seed=12)
+    with U.params(1024, 1) as p, U.conv_bank(p, desc, F) as f:
+        d_in = U.to_dev(cts)
+        d_out = U.empty_dev((lay["H"] * 2 * 1024,))
+        with pytest.raises(H.HEError) as ei:
+            H.he_plan_create([(f, d_in, H.HE_COEFF, d_out, 1), (f, d_in, H.HE_COEFF, d_out, 1)])
+        assert ei.value.status == H.HE_ERR_ARG
+        with pytest.raises(H.HEError) as ei:
+            H.he_plan_create([(f, d_in, H.HE_COEFF, d_in, 1)])
+        assert ei.value.status == H.HE_ERR_ARG
