@@ -214,7 +214,11 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
  * and one that runs every channel work unit (one output channel x limb x
  * column tile of a Conv call, or one weight polynomial x limb x column of an
  * FC call) of every call, longest first.  Each call computes the words that
- * he_conv_layer / he_fc_layer with HE_OUT_EXTRACTED would write.  The plan
+ * he_conv_layer / he_fc_layer with HE_OUT_EXTRACTED would write.  Conv calls
+ * with B = 1 take a split form: one kernel streams each slot tile's weights
+ * for every output channel (bulk copies into shared memory) and stores the
+ * folded channel sums in the plan's workspace, a second kernel runs the
+ * inverse transforms and writes each extracted output polynomial.  The plan
  * owns its NTT workspace and descriptor tables, so he_plan_run allocates
  * nothing and can be captured into a CUDA graph.  Runs of one plan must not
  * overlap on the GPU; different plans may run concurrently.
@@ -239,6 +243,11 @@ he_status he_plan_run(he_plan_t plan, void *stream);
  * channel kernels.  Phase 1 must follow phase 0 of the same run on the same
  * stream (or be ordered after it); for timing each kernel separately. */
 he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream);
+/* Reports whether a bounded device-side wait of an earlier run gave up
+ * (HE_ERR_TIMEOUT; the outputs of that run are then unspecified) and clears
+ * the flag.  Blocking; call it after the streams the plan ran on are
+ * synchronized. */
+he_status he_plan_check(he_plan_t plan);
 void he_plan_destroy(he_plan_t plan);
 
 /* Wait for `stream` and report any pending CUDA error. */

@@ -404,6 +404,9 @@ he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w,
     f->kind = HE_KIND_CONV;
     f->desc = *d;
     f->lay = lay;
+    f->logTS = bank_tile_log(p->logN, lay.s, lay.G);
+    f->lcs = bank_chunk_log(f->logTS, lay.s, lay.G);
+    f->nc = std::min(d->co, std::max(1u, kMacItemWords / (lay.G << f->logTS)));
     f->bank_bytes = (size_t)d->co * p->L * lay.G * p->N * sizeof(uint32_t);
     const size_t wbytes = (size_t)d->co * d->ci * d->fh * d->fw;
     int8_t *d_w = nullptr;
@@ -416,7 +419,7 @@ he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w,
     }
     e = cudaMalloc(&d_w, wbytes);
     if (e == cudaSuccess) e = cudaMemcpy(d_w, w, wbytes, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = he_launch_pack_conv(p->ring, d_w, *d, lay, f->bank, 0);
+    if (e == cudaSuccess) e = he_launch_pack_conv(p->ring, d_w, *d, lay, f->logTS, f->lcs, f->bank, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_w);
     if (e != cudaSuccess) {
@@ -510,7 +513,7 @@ he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int
         if (e != cudaSuccess) return cuda_fail(e, "input NTT");
         x = (const uint32_t *)p->ws;
     }
-    cudaError_t e = he_launch_conv(p->ring, f->desc, lay, f->bank, x, d_out, out_mode, B, st);
+    cudaError_t e = he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, f->bank, x, d_out, out_mode, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "conv kernel");
     return HE_OK;
 }
@@ -577,7 +580,7 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
     };
     std::vector<Range> ranges;
     std::vector<CallDesc> descs(ncalls);
-    std::vector<size_t> ws_off(ncalls, 0);
+    std::vector<size_t> ws_off(ncalls, 0), z_off(ncalls, 0);
     size_t ws_words = 0;
     for (uint32_t i = 0; i < ncalls; ++i) {
         const he_layer_call &c = calls[i];
@@ -606,7 +609,7 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
         size_t nin, nout;
         if (f->kind == HE_KIND_CONV) {
             const he_conv_layout &lay = f->lay;
-            if ((size_t)2 * lay.M * 4u > 192u * 1024u)
+            if (fold_smem_bytes(2, lay.M) > 192u * 1024u)
                 return fail(HE_ERR_UNSUPPORTED, "call %u: N/s = %u too long for a plan", i, lay.M);
             cd.kind = HE_KIND_CONV;
             g.G = lay.G;
@@ -617,8 +620,20 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
             g.logM = he_ilog2(lay.M);
             g.co = f->desc.co;
             g.mult = lay.off_mult;
-            cd.nj = he_conv_nj(g.ncols, lay.M);
+            g.logTS = f->logTS;
+            g.lcs = f->lcs;
+            cd.nj = he_conv_nj(g.ncols, lay.M, lay.s);
             cd.nb = lay.s >= 4 ? 1 : (lay.s == 2 ? 2 : 4);
+            cd.cpt = he_conv_cpt(cd.nj, cd.nb, lay.G);
+            // split form for one ciphertext per call with s >= 4 and G in
+            // {1, 2, 4} whose output polynomials fit shared memory
+            cd.split = (c.B == 1 && split_mac_ok(lay.s, lay.G) &&
+                        (size_t)std::min(lay.s, f->desc.co) * fin_stride(lay.M) * 4u <= 200u * 1024u)
+                           ? 1u
+                           : 0u;
+            g.cs = split_cs(lay.s, lay.G);
+            g.nc = f->nc;
+            if (cd.split && (1u << f->lcs) != g.cs) cd.split = 0;  // bank interleave must match the MAC's
             nin = (size_t)c.B * lay.G * 2u * r.L * r.N;
             nout = (size_t)c.B * lay.H * 2u * r.L * r.N;
         } else {
@@ -633,14 +648,22 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
         }
         if (c.in_domain == HE_COEFF) {
             cd.x_coeff = c.d_in;
-            ws_off[i] = ws_words;
-            ws_words += nin;
+            if (cd.kind == HE_KIND_CONV) {  // FC items transform their input in shared memory
+                ws_off[i] = ws_words;
+                ws_words += nin;
+            }
         } else {
             g.x = c.d_in;
         }
         ranges.push_back({(uintptr_t)c.d_in, (uintptr_t)(c.d_in + nin), false, i});
         ranges.push_back({(uintptr_t)c.d_out, (uintptr_t)(c.d_out + nout), true, i});
     }
+    for (uint32_t i = 0; i < ncalls; ++i)
+        if (descs[i].split) {
+            const ConvGeo &g = descs[i].g;
+            z_off[i] = ws_words;
+            ws_words += (size_t)g.L * g.ncols * g.co * g.M;
+        }
     for (size_t a = 0; a < ranges.size(); ++a)
         for (size_t b = a + 1; b < ranges.size(); ++b) {
             if (!ranges[a].is_out && !ranges[b].is_out) continue;  // inputs may be shared
@@ -656,50 +679,89 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
     pl->ncalls = ncalls;
     cudaError_t e = cudaSuccess;
     if (ws_words) e = cudaMalloc(&pl->ws, ws_words * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_status, sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(pl->d_status, 0, sizeof(uint32_t));
     if (e != cudaSuccess) {
         cudaGetLastError();
-        delete pl;
+        he_plan_destroy(pl);
         return fail(HE_ERR_NOMEM, "plan workspace of %zu bytes", ws_words * 4);
     }
-    // work items
-    std::vector<NttItem> ntt;
-    std::vector<std::pair<double, ChanItem>> chan[5];
-    std::vector<std::pair<double, NttItem>> ntt_cost;
+    // work items, each list ordered longest first
+    using Costed = std::pair<double, ChanItem>;
+    std::vector<std::pair<double, NttItem>> ntt_cost, fc_cost;
+    std::vector<Costed> chan[4], mac[kMacClasses], fin;
     for (uint32_t i = 0; i < ncalls; ++i) {
         CallDesc &cd = descs[i];
         ConvGeo &g = cd.g;
         const double N = g.N, logN = g.logN;
+        if (cd.kind == HE_KIND_FC) {
+            // fused FC items (input transform, product, inverse, output) run
+            // in the input-transform kernel, ahead of the conv transforms
+            const double cost = 3.0 * N * logN;
+            for (uint32_t jp = 0; jp < g.P; ++jp)
+                for (uint32_t l = 0; l < g.L; ++l)
+                    for (uint32_t col = 0; col < g.ncols; ++col)
+                        fc_cost.push_back({cost, NttItem{i, (jp * g.L + l) * g.ncols + col}});
+            continue;
+        }
         if (cd.x_coeff) {
             g.x = pl->ws + ws_off[i];
-            const size_t npoly = (cd.kind == HE_KIND_CONV ? (size_t)calls[i].B * g.G * 2u : (size_t)calls[i].B * 2u) * g.L;
-            for (size_t pidx = 0; pidx < npoly; ++pidx)
-                ntt_cost.push_back({N * logN, NttItem{i, (uint32_t)pidx}});
+            const size_t npoly = (size_t)calls[i].B * g.G * 2u * g.L;
+            for (size_t pidx_ = 0; pidx_ < npoly; ++pidx_) ntt_cost.push_back({N * logN, NttItem{i, (uint32_t)pidx_}});
         }
-        if (cd.kind == HE_KIND_CONV) {
+        if (cd.split) {
+            cd.z = pl->ws + z_off[i];
+            const int cls = he_mac_class(g.G, g.cs);
+            const uint32_t T = g.N >> g.logTS;
+            const double mcost = (double)std::min(g.nc, g.co) * g.G * (1u << g.logTS);
+            for (uint32_t t = 0; t < T; ++t)
+                for (uint32_t l = 0; l < g.L; ++l)
+                    for (uint32_t n0 = 0; n0 < g.co; n0 += g.nc) mac[cls].push_back({mcost, ChanItem{i, t, l, n0}});
+            const double fcost = 3.0 * (N / 2.0) * g.logM + N;
+            for (uint32_t h = 0; h < g.H; ++h)
+                for (uint32_t l = 0; l < g.L; ++l)
+                    for (uint32_t col = 0; col < g.ncols; ++col) fin.push_back({fcost, ChanItem{i, h, l, col}});
+        } else {
             const int cls = cd.nj == 2 ? 0 : cd.nj == 4 ? 1 : cd.nj == 8 ? 2 : 3;
             const double cost = (double)g.G * N * cd.nj + 3.0 * cd.nj * (g.M / 2.0) * g.logM;
             for (uint32_t n = 0; n < g.co; ++n)
                 for (uint32_t l = 0; l < g.L; ++l)
                     for (uint32_t t = 0; t < g.ncols / cd.nj; ++t) chan[cls].push_back({cost, ChanItem{i, n, l, t}});
-        } else {
-            const double cost = N + 3.0 * (N / 2.0) * logN;
-            for (uint32_t jp = 0; jp < g.P; ++jp)
-                for (uint32_t l = 0; l < g.L; ++l)
-                    for (uint32_t col = 0; col < g.ncols; ++col) chan[0].push_back({cost, ChanItem{i, jp, l, col}});
         }
     }
     auto by_cost = [](const auto &x, const auto &y) { return x.first > y.first; };
+    std::vector<NttItem> ntt;
     std::stable_sort(ntt_cost.begin(), ntt_cost.end(), by_cost);
     for (auto &it : ntt_cost) {
         ntt.push_back(it.second);
-        pl->smem_ntt = std::max(pl->smem_ntt, (size_t)descs[it.second.call].g.N * 4u);
+        pl->smem_ntt = std::max(pl->smem_ntt, (size_t)padded_words(descs[it.second.call].g.N) * 4u);
     }
     pl->n_ntt = (uint32_t)ntt.size();
+    std::vector<NttItem> fcs;
+    std::stable_sort(fc_cost.begin(), fc_cost.end(), by_cost);
+    for (auto &it : fc_cost) {
+        fcs.push_back(it.second);
+        pl->smem_fc = std::max(pl->smem_fc, (size_t)padded_words(descs[it.second.call].g.N) * 4u);
+    }
+    pl->n_fc = (uint32_t)fcs.size();
+    auto upload = [&](ChanItem **dst, const std::vector<ChanItem> &v) -> cudaError_t {
+        if (v.empty()) return cudaSuccess;
+        cudaError_t err = cudaMalloc(dst, sizeof(ChanItem) * v.size());
+        if (err == cudaSuccess) err = cudaMemcpy(*dst, v.data(), sizeof(ChanItem) * v.size(), cudaMemcpyHostToDevice);
+        return err;
+    };
     e = cudaMalloc(&pl->d_calls, sizeof(CallDesc) * ncalls);
     if (e == cudaSuccess) e = cudaMemcpy(pl->d_calls, descs.data(), sizeof(CallDesc) * ncalls, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !ntt.empty()) {
         e = cudaMalloc(&pl->d_ntt, sizeof(NttItem) * ntt.size());
         if (e == cudaSuccess) e = cudaMemcpy(pl->d_ntt, ntt.data(), sizeof(NttItem) * ntt.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess && !fcs.empty()) {
+        e = cudaMalloc(&pl->d_fc, sizeof(NttItem) * fcs.size());
+        if (e == cudaSuccess) e = cudaMemcpy(pl->d_fc, fcs.data(), sizeof(NttItem) * fcs.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
     }
     for (int cls = 0; cls < 4 && e == cudaSuccess; ++cls) {
         std::stable_sort(chan[cls].begin(), chan[cls].end(), by_cost);
@@ -708,16 +770,82 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
         const uint32_t nj = 2u << cls;
         for (auto &it : chan[cls]) {
             items.push_back(it.second);
-            const CallDesc &cd = descs[it.second.call];
-            smem = std::max(smem, cd.kind == HE_KIND_FC ? (size_t)cd.g.N * 4u : (size_t)nj * cd.g.M * 4u);
+            smem = std::max(smem, fold_smem_bytes(nj, descs[it.second.call].g.M));
         }
         pl->n_chan[cls] = (uint32_t)items.size();
         pl->smem_chan[cls] = smem;
-        if (!items.empty()) {
-            e = cudaMalloc(&pl->d_chan[cls], sizeof(ChanItem) * items.size());
-            if (e == cudaSuccess)
-                e = cudaMemcpy(pl->d_chan[cls], items.data(), sizeof(ChanItem) * items.size(), cudaMemcpyHostToDevice);
+        e = upload(&pl->d_chan[cls], items);
+    }
+    if (e == cudaSuccess) {
+        std::vector<ChanItem> items;
+        // persistent MAC CTAs (2 per SM): longest item first onto the least
+        // loaded CTA; each CTA runs its items in that order
+        std::vector<Costed> all;
+        for (int cls = 0; cls < kMacClasses; ++cls) all.insert(all.end(), mac[cls].begin(), mac[cls].end());
+        std::stable_sort(all.begin(), all.end(), by_cost);
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+        const uint32_t nctas = (uint32_t)std::min<size_t>(all.size(), (size_t)std::max(1, sms) * 2u);
+        std::vector<std::vector<ChanItem>> per(nctas);
+        std::vector<std::pair<double, uint32_t>> heap;  // (load, cta), min-heap
+        for (uint32_t b = 0; b < nctas; ++b) heap.push_back({0.0, b});
+        auto cmp = [](const std::pair<double, uint32_t> &x, const std::pair<double, uint32_t> &y) {
+            return x.first > y.first || (x.first == y.first && x.second > y.second);
+        };
+        std::make_heap(heap.begin(), heap.end(), cmp);
+        for (auto &it : all) {
+            std::pop_heap(heap.begin(), heap.end(), cmp);
+            auto &h = heap.back();
+            per[h.second].push_back(it.second);
+            h.first += it.first;
+            std::push_heap(heap.begin(), heap.end(), cmp);
         }
+        std::vector<uint32_t> offs(nctas + 1, 0);
+        for (uint32_t b = 0; b < nctas; ++b) {
+            offs[b] = (uint32_t)items.size();
+            items.insert(items.end(), per[b].begin(), per[b].end());
+        }
+        offs[nctas] = (uint32_t)items.size();
+        std::vector<MacCopy> copies;
+        for (const ChanItem &it : items) {
+            const CallDesc &cd = descs[it.call];
+            const ConvGeo &g = cd.g;
+            const uint32_t lt = g.logTS, nc = std::min(g.nc, g.co - it.b);
+            MacCopy c;
+            c.w = g.bank + bank_index(it.b, it.l, 0, it.a << lt, g.logN, lt, g.lcs, g.co, g.G);
+            c.x = g.x + (size_t)it.l * g.N + ((size_t)it.a << lt);
+            c.nwords = (nc * g.G) << lt;
+            c.xstride = g.L * g.N;
+            c.xrows = 2 * g.G;
+            c.xwords = 1u << lt;
+            copies.push_back(c);
+        }
+        pl->n_mac = (uint32_t)items.size();
+        pl->mac_ctas = nctas;
+        pl->smem_mac = mac_smem_bytes();
+        if (e == cudaSuccess) e = upload(&pl->d_mac, items);
+        if (e == cudaSuccess && !copies.empty()) {
+            e = cudaMalloc(&pl->d_mac_copy, sizeof(MacCopy) * copies.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(pl->d_mac_copy, copies.data(), sizeof(MacCopy) * copies.size(), cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess && nctas) {
+            e = cudaMalloc(&pl->d_mac_offs, sizeof(uint32_t) * offs.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(pl->d_mac_offs, offs.data(), sizeof(uint32_t) * offs.size(), cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess) {
+        std::stable_sort(fin.begin(), fin.end(), by_cost);
+        std::vector<ChanItem> items;
+        pl->smem_fin = 16;
+        for (auto &it : fin) {
+            items.push_back(it.second);
+            const CallDesc &cd = descs[it.second.call];
+            pl->smem_fin = std::max(pl->smem_fin, (size_t)std::min(cd.g.s, cd.g.co) * fin_stride(cd.g.M) * 4u);
+        }
+        pl->n_fin = (uint32_t)items.size();
+        e = upload(&pl->d_fin, items);
     }
     if (e == cudaSuccess) e = he_plan_prepare(*pl);
     if (e != cudaSuccess) {
@@ -725,6 +853,21 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
         return cuda_fail(e, "plan tables");
     }
     *out = pl;
+    return HE_OK;
+}
+
+he_status he_plan_check(he_plan_t plan) {
+    if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
+    uint32_t st = 0;
+    cudaError_t e = cudaMemcpy(&st, plan->d_status, sizeof(st), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "plan status");
+    if (st) {
+        const uint32_t zero = 0;
+        cudaMemcpy(plan->d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        return fail(HE_ERR_TIMEOUT, "a bounded wait of the MAC kernel gave up (status 0x%x)", st);
+    }
     return HE_OK;
 }
 
@@ -751,7 +894,16 @@ void he_plan_destroy(he_plan_t plan) {
     cudaFree(plan->ws);
     cudaFree(plan->d_calls);
     cudaFree(plan->d_ntt);
-    for (int c = 0; c < 5; ++c) cudaFree(plan->d_chan[c]);
+    for (int c = 0; c < 4; ++c) cudaFree(plan->d_chan[c]);
+    cudaFree(plan->d_mac);
+    cudaFree(plan->d_mac_offs);
+    cudaFree(plan->d_mac_copy);
+    cudaFree(plan->d_fin);
+    cudaFree(plan->d_status);
+    cudaFree(plan->d_fc);
+    if (plan->side) cudaStreamDestroy(plan->side);
+    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
     delete plan;
 }
 

@@ -53,6 +53,15 @@ struct he_params_s {
 
 enum { HE_KIND_CONV = 1, HE_KIND_FC = 2 };
 
+// words of shared memory for n values in the padded layout (one pad word
+// per 32, see pidx)
+__host__ __device__ __forceinline__ uint32_t padded_words(uint32_t n) { return n + (n >> 5) + 1; }
+
+// bytes of shared memory for the folded kernel's nj polynomials of M words
+__host__ __device__ __forceinline__ size_t fold_smem_bytes(uint32_t nj, uint32_t M) {
+    return (size_t)nj * padded_words(M) * 4u;
+}
+
 // Geometry of one layer call as the channel kernels see it (no limb constants).
 struct ConvGeo {
     const uint32_t *bank;     // conv: [co][L][G][N]; fc: [P][L][N]
@@ -63,33 +72,130 @@ struct ConvGeo {
     const uint32_t *psi_pow;  // [L][2N]
     uint32_t N, logN, L, G, H, s, logs, M, logM, co, mult, ncols, mode;
     uint32_t P, rpp, n_out;   // fc
+    uint32_t logTS;           // conv bank tile: TS = 2^logTS slots
+    uint32_t lcs;             // conv bank chunk interleave (log2)
+    uint32_t cs, n0, nc;      // split MAC: chunks per thread; (per item) channel range
 };
+
+// Conv filter bank layout: [L][N/TS][co][G][TS] (TS = 2^lt slots, a
+// power of two <= N chosen per bank), so the weights one slot tile of one
+// limb needs, for any range of channels, are one contiguous region.  Inside
+// a row of TS words the 4-word chunks are interleaved by CS = 2^lcs: chunk
+// j sits at chunk position (j mod CS) * (TS / 4CS) + j / CS, so the threads
+// that each own CS consecutive chunks read consecutive 16-byte words.
+__host__ __device__ __forceinline__ uint32_t bank_row_pos(uint32_t kk, uint32_t lt, uint32_t lcs) {
+    const uint32_t chunk = kk >> 2, lng = lt - 2 - lcs;
+    return ((((chunk & ((1u << lcs) - 1u)) << lng) + (chunk >> lcs)) << 2) + (kk & 3u);
+}
+__host__ __device__ __forceinline__ size_t bank_index(uint32_t n, uint32_t l, uint32_t g, uint32_t k, uint32_t logN,
+                                                      uint32_t lt, uint32_t lcs, uint32_t co, uint32_t G) {
+    const size_t tile = ((size_t)l << (logN - lt)) + (k >> lt);
+    return (((tile * co + n) * G + g) << lt) + bank_row_pos(k & ((1u << lt) - 1u), lt, lcs);
+}
+
+// Split-form MAC geometry of a Conv layer: chunks of 4 slots per thread
+// (cs) and bank tile log2 (lt).  The split form needs s >= 4 and G in
+// {1, 2, 4}; then cs = min(4 / G, s / 4), so a thread's inputs are 8 uint4 and
+// a channel's products per column are at most 16.  Other layers use a
+// 512-slot tile.
+__host__ __device__ __forceinline__ bool split_mac_ok(uint32_t s, uint32_t G) {
+    return s >= 4 && (G == 1 || G == 2 || G == 4);
+}
+__host__ __device__ __forceinline__ uint32_t split_cs(uint32_t s, uint32_t G) {
+    const uint32_t a = 4u / G, b = s / 4u;
+    return a < b ? a : b;
+}
+// log2 of the chunk interleave of a bank: log2(split_cs) for split layers,
+// else 0 (no interleave); never more than the tile allows
+__host__ __device__ __forceinline__ uint32_t bank_chunk_log(uint32_t lt, uint32_t s, uint32_t G) {
+    uint32_t lcs = 0;
+    if (split_mac_ok(s, G)) {
+        const uint32_t cs = split_cs(s, G);
+        lcs = cs == 4 ? 2u : (cs == 2 ? 1u : 0u);
+    }
+    return lcs + 2 <= lt ? lcs : 0u;
+}
+__host__ __device__ __forceinline__ uint32_t bank_tile_log(uint32_t logN, uint32_t s, uint32_t G) {
+    uint32_t lt = 9;
+    if (split_mac_ok(s, G)) {
+        const uint32_t cs = split_cs(s, G);
+        lt += cs == 4 ? 2u : (cs == 2 ? 1u : 0u);
+    }
+    return lt < logN ? lt : logN;
+}
 
 // One layer call inside a plan (device-resident table).
 struct CallDesc {
     ConvGeo g;
     const uint32_t *x_coeff;  // coefficient-domain input (nullptr when the call's input is in NTT form)
     const uint2 *tw_fwd;      // [L][N]
-    uint32_t kind, nj, nb, pad;
+    uint32_t *z;              // split form: folded channel sums [L][2B][co][M]
+    uint32_t kind, nj, nb, cpt;
+    uint32_t split;           // 1: MAC kernel + finishing kernel; 0: one fused channel kernel
+    uint32_t pad[3];
     LimbK limb[HE_MAX_LIMBS];
 };
 
-struct NttItem {
-    uint32_t call, poly;      // poly index within the call's [npoly][L][N] input
+// split MAC kernel classes by (G, CS): (1,1) (1,2) (1,4) (2,1) (2,2) (4,1)
+constexpr int kMacClasses = 6;
+__host__ __device__ __forceinline__ int he_mac_class(uint32_t G, uint32_t cs) {
+    if (G == 1) return cs == 1 ? 0 : (cs == 2 ? 1 : 2);
+    if (G == 2) return cs == 1 ? 3 : 4;
+    return 5;
+}
+
+// split form: bulk-copy ring of the MAC kernel
+constexpr uint32_t kMacStageWords = 4096;   // 16 KB per stage
+constexpr uint32_t kMacStages = 5;
+constexpr uint32_t kMacHdrBytes = 64;       // mbarriers at the start of shared memory
+constexpr uint32_t kMacItemWords = 32768;   // weights per work item (128 KB)
+constexpr uint32_t kMacXWords = 4096;       // one input buffer: 2 columns x G*TS <= 2048 words
+
+// Copy descriptors of one MAC item, built on the host so the producer thread
+// issues bulk copies without walking the call table.
+struct MacCopy {
+    const uint32_t *w;       // first weight word of the item's contiguous region
+    const uint32_t *x;       // input row (g = 0, column 0); row (g, jj) at x + (2g + jj) * xstride
+    uint32_t nwords;         // weight words
+    uint32_t xstride;        // words between input rows
+    uint32_t xrows;          // 2 * G
+    uint32_t xwords;         // words per input row (TS)
 };
+
+__host__ __device__ __forceinline__ size_t mac_smem_bytes() {
+    return kMacHdrBytes + (size_t)2 * kMacXWords * 4u + (size_t)kMacStages * kMacStageWords * 4u;
+}
+// polynomial stride (words) of the finishing kernel: padded and odd, so the
+// transposed reads of the extraction hit distinct banks
+__host__ __device__ __forceinline__ uint32_t fin_stride(uint32_t M) { return padded_words(M) | 1u; }
+
+struct NttItem {
+    uint32_t call, poly;      // conv: poly index within the call's [npoly][L][N] input;
+};                            // fc: poly = (jp * L + l) * ncols + column of a fused FC item
 
 struct ChanItem {
     uint32_t call, a, l, b;   // conv: (channel n, limb, column tile); fc: (weight poly, limb, column)
-};
+};                            // split MAC: (tile, limb, first channel); finishing: (output poly, limb, column)
 
 struct he_plan_s {
     int device;
-    uint32_t ncalls, n_ntt, n_chan[5];  // channel items per NJ class (2, 4, 8, 16) and FC
+    uint32_t ncalls, n_ntt, n_chan[4];  // fused channel items per NJ class (2, 4, 8, 16)
+    uint32_t n_mac, n_fin;              // split form: MAC items, finishing items (and every FC item)
     CallDesc *d_calls;
     NttItem *d_ntt;
-    ChanItem *d_chan[5];
-    size_t smem_ntt, smem_chan[5];
+    ChanItem *d_chan[4];
+    ChanItem *d_mac, *d_fin;
+    uint32_t *d_mac_offs;               // persistent MAC CTAs: items of CTA b at [offs[b], offs[b+1])
+    MacCopy *d_mac_copy;                // per item, same order as d_mac
+    uint32_t mac_ctas;
+    uint32_t n_fc;                      // fused FC items, run on a side stream
+    NttItem *d_fc;
+    size_t smem_fc;
+    cudaStream_t side;                  // FC work forks off the caller's stream and joins it again
+    cudaEvent_t ev_fork, ev_join;
+    size_t smem_ntt, smem_chan[4], smem_mac, smem_fin;
     uint32_t *ws;
+    uint32_t *d_status;                 // bit 0: a bounded wait in the MAC kernel gave up
 };
 
 cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase);
@@ -100,6 +206,9 @@ struct he_filters_s {
     int kind;
     he_conv_desc desc;
     he_conv_layout lay;
+    uint32_t logTS;   // conv bank tile
+    uint32_t lcs;     // conv bank chunk interleave (log2)
+    uint32_t nc;      // split MAC: channels per work item
     he_fc_layout fl;
     uint32_t *bank;   // conv: [co][L][G][N]; fc: [P][L][N]; NTT domain, pre-scaled
     uint32_t *bias;   // fc: [L][n_out] Delta_Q * B mod q_l, or nullptr
@@ -112,13 +221,14 @@ struct he_filters_s {
 cudaError_t he_launch_ntt(const RingView &r, const uint32_t *in, uint32_t *out,
                           uint32_t npolys, bool inverse, cudaStream_t st);
 cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_conv_desc &d,
-                                const he_conv_layout &lay, uint32_t *bank, cudaStream_t st);
+                                const he_conv_layout &lay, uint32_t lt, uint32_t lcs, uint32_t *bank, cudaStream_t st);
 cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_layout &fl,
                               uint32_t *bank, cudaStream_t st);
-uint32_t he_conv_nj(uint32_t ncols, uint32_t M);
+uint32_t he_conv_nj(uint32_t ncols, uint32_t M, uint32_t s);
+uint32_t he_conv_cpt(uint32_t nj, uint32_t nb, uint32_t G);
 uint32_t he_ilog2(uint32_t x);
-cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay,
-                           const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out,
+cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt,
+                           uint32_t lcs, const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out,
                            int mode, uint32_t B, cudaStream_t st);
 cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32_t *bank,
                          const uint32_t *bias, const uint32_t *x_ntt, uint32_t *out, int mode,
@@ -134,11 +244,12 @@ __device__ __forceinline__ uint32_t shoup_lazy(uint32_t a, uint32_t w, uint32_t 
     return a * w - qh * q;  // [0, 2q)
 }
 
-__device__ __forceinline__ uint32_t red_2q(uint32_t x, uint32_t q) { return x >= q ? x - q : x; }
+// x in [0, 2q) -> [0, q): min(x, x - q) as unsigned (x - q wraps when x < q)
+__device__ __forceinline__ uint32_t red_2q(uint32_t x, uint32_t q) { return min(x, x - q); }
 
 __device__ __forceinline__ uint32_t red_4q(uint32_t x, uint32_t q2, uint32_t q) {
-    x = x >= q2 ? x - q2 : x;
-    return x >= q ? x - q : x;
+    x = min(x, x - q2);
+    return min(x, x - q);
 }
 
 // x < 2^64 -> x mod q in [0, q)
@@ -150,6 +261,19 @@ __device__ __forceinline__ uint32_t reduce64(uint64_t x, const LimbK &k) {
 
 __device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b, const LimbK &k) {
     return reduce64((uint64_t)a * b, k);
+}
+
+// Asks the memory system to bring [p, p + bytes) into L2 without using
+// registers or shared memory (bulk prefetch, sm_90+).  p 16-byte aligned,
+// bytes a multiple of 16; issued by one thread.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    const char *c = static_cast<const char *>(p);
+    while (bytes) {
+        const uint32_t n = bytes < 65536u ? bytes : 65536u;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c), "r"(n) : "memory");
+        c += n;
+        bytes -= n;
+    }
 }
 
 __device__ __forceinline__ uint32_t brv(uint32_t x, uint32_t bits) {
@@ -210,5 +334,424 @@ __device__ __forceinline__ void ntt_inv_smem(uint32_t *a, uint32_t npoly, uint32
         __syncthreads();
     }
 }
+
+
+// ---------------------------------------------------------------------------
+// Register-blocked transforms (hot path).
+//
+// A pass applies k <= 5 consecutive butterfly stages to groups of 2^k
+// values held in registers: a group is the 2^k indices that differ only in
+// bits [lo, lo+k).  The forward transform runs its passes from the top bits
+// down and ends with a pass on bits [0, 5); the inverse starts with bits
+// [0, 5) and runs upwards.  Intermediate values live in shared memory at
+// pidx(i) = i + i/32 (one pad word per 32): an access by consecutive
+// threads to consecutive indices, or to groups of 8, 16 or 32 consecutive
+// indices each, then touches 32 distinct banks.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t pidx(uint32_t i) { return i + (i >> 5); }
+
+
+
+__device__ __forceinline__ void bf_fwd(uint32_t &U, uint32_t &V, const uint2 w, uint32_t q, uint32_t q2) {
+    U = min(U, U - q2);
+    const uint32_t T = shoup_lazy(V, w.x, w.y, q);
+    V = U - T + q2;
+    U = U + T;
+}
+
+__device__ __forceinline__ void bf_inv(uint32_t &U, uint32_t &V, const uint2 w, uint32_t q, uint32_t q2) {
+    const uint32_t X = U + V;
+    const uint32_t Y = U - V + q2;
+    U = min(X, X - q2);
+    V = shoup_lazy(Y, w.x, w.y, q);
+}
+
+// index of the group's element 0: zeros inserted at bits [lo, lo+k) of gid
+__device__ __forceinline__ uint32_t group_base(uint32_t gid, uint32_t lo, uint32_t k) {
+    return ((gid >> lo) << (lo + k)) | (gid & ((1u << lo) - 1u));
+}
+
+// K forward (Cooley-Tukey) stages on bits lo+K-1 .. lo of a group.  The
+// stage on bit p is stage s = logN-1-p; its twiddle for index i is
+// tw[2^s + (i >> (p+1))], shared by every pair of a block of 2^(K-J) values.
+// Stage J of the group is FwdStage<K, J>; the recursion keeps every index a
+// compile-time constant so the group stays in registers.
+template <int K, int J>
+struct FwdStage {
+    static __device__ __forceinline__ void run(uint32_t (&v)[1 << K], uint32_t base, uint32_t lo, uint32_t logN,
+                                               const uint2 *__restrict__ tw, uint32_t q, uint32_t q2) {
+        constexpr int kHalf = 1 << (K - 1 - J);
+        const uint32_t p = lo + K - 1 - J;
+        const uint32_t t0 = (1u << (logN - 1 - p)) + (base >> (p + 1));
+#pragma unroll
+        for (int blk = 0; blk < (1 << J); ++blk) {
+            const uint2 w = __ldg(tw + t0 + blk);
+#pragma unroll
+            for (int u = 0; u < kHalf; ++u) bf_fwd(v[blk * 2 * kHalf + u], v[blk * 2 * kHalf + u + kHalf], w, q, q2);
+        }
+        FwdStage<K, J + 1>::run(v, base, lo, logN, tw, q, q2);
+    }
+};
+template <int K>
+struct FwdStage<K, K> {
+    static __device__ __forceinline__ void run(uint32_t (&)[1 << K], uint32_t, uint32_t, uint32_t, const uint2 *,
+                                               uint32_t, uint32_t) {}
+};
+
+template <int K>
+__device__ __forceinline__ void fwd_group(uint32_t (&v)[1 << K], uint32_t base, uint32_t lo, uint32_t logN,
+                                          const uint2 *__restrict__ tw, uint32_t q) {
+    FwdStage<K, 0>::run(v, base, lo, logN, tw, q, 2u * q);
+}
+
+// K inverse (Gentleman-Sande) stages on bits lo .. lo+K-1 of a group of a
+// length-M transform: the stage on bit p uses twi[M/2^(p+1) + (i >> (p+1))].
+template <int K, int J>
+struct InvStage {
+    static __device__ __forceinline__ void run(uint32_t (&v)[1 << K], uint32_t base, uint32_t lo, uint32_t logM,
+                                               const uint2 *__restrict__ twi, uint32_t q, uint32_t q2) {
+        constexpr int kHalf = 1 << J;
+        const uint32_t p = lo + J;
+        const uint32_t t0 = (1u << (logM - 1 - p)) + (base >> (p + 1));
+#pragma unroll
+        for (int blk = 0; blk < (1 << (K - 1 - J)); ++blk) {
+            const uint2 w = __ldg(twi + t0 + blk);
+#pragma unroll
+            for (int u = 0; u < kHalf; ++u) bf_inv(v[blk * 2 * kHalf + u], v[blk * 2 * kHalf + u + kHalf], w, q, q2);
+        }
+        InvStage<K, J + 1>::run(v, base, lo, logM, twi, q, q2);
+    }
+};
+template <int K>
+struct InvStage<K, K> {
+    static __device__ __forceinline__ void run(uint32_t (&)[1 << K], uint32_t, uint32_t, uint32_t, const uint2 *,
+                                               uint32_t, uint32_t) {}
+};
+
+template <int K>
+__device__ __forceinline__ void inv_group(uint32_t (&v)[1 << K], uint32_t base, uint32_t lo, uint32_t logM,
+                                          const uint2 *__restrict__ twi, uint32_t q) {
+    InvStage<K, 0>::run(v, base, lo, logM, twi, q, 2u * q);
+}
+
+// Split of the forward passes: the last pass takes bits [0, min(5, logN)),
+// the bits above are split into passes of at most 5, larger ones first.
+__device__ __forceinline__ uint32_t fwd_pass_k(uint32_t logN, uint32_t pass, uint32_t &lo, uint32_t &npass) {
+    const uint32_t last = logN < 5 ? logN : 5u;
+    const uint32_t rem = logN - last;
+    const uint32_t nmid = (rem + 4) / 5;
+    npass = nmid + 1;
+    if (pass == nmid) {
+        lo = 0;
+        return last;
+    }
+    // pass i < nmid covers the top `rem` bits, chunk sizes differ by at most one
+    uint32_t hi = logN, k = 0;
+    for (uint32_t i = 0; i <= pass; ++i) {
+        k = rem / nmid + (i < rem % nmid ? 1u : 0u);
+        hi -= k;
+    }
+    lo = hi;
+    return k;
+}
+
+// The same split for the inverse, mirrored: the first pass takes bits
+// [0, KMAX), the rest passes of at most KMAX bits.
+template <int KMAX>
+__device__ __forceinline__ uint32_t inv_pass_k(uint32_t logM, uint32_t pass, uint32_t &lo, uint32_t &npass) {
+    const uint32_t first = logM < (uint32_t)KMAX ? logM : (uint32_t)KMAX;
+    const uint32_t rem = logM - first;
+    const uint32_t nmid = (rem + KMAX - 1) / KMAX;
+    npass = nmid + 1;
+    if (pass == 0) {
+        lo = 0;
+        return first;
+    }
+    uint32_t l0 = first, k = 0;
+    for (uint32_t i = 1; i <= pass; ++i) {
+        l0 += k;
+        k = rem / nmid + (i - 1 < rem % nmid ? 1u : 0u);
+    }
+    lo = l0;
+    return k;
+}
+
+// One forward pass with group size 2^K over a polynomial of 2^logN values.
+// src_global / dst_global select where the pass reads and writes (global
+// memory, or the padded shared buffer `sm`).  The last pass (lo == 0)
+// reduces to [0, q) and writes 2^K consecutive words per group.
+template <int K>
+__device__ __forceinline__ void fwd_pass(const uint32_t *__restrict__ gsrc, uint32_t *__restrict__ gdst,
+                                         uint32_t *sm, uint32_t logN, uint32_t lo, const uint2 *__restrict__ tw,
+                                         uint32_t q) {
+    const uint32_t ngroups = 1u << (logN - K);
+    for (uint32_t gid = threadIdx.x; gid < ngroups; gid += blockDim.x) {
+        const uint32_t base = group_base(gid, lo, K);
+        uint32_t v[1 << K];
+#pragma unroll
+        for (int r = 0; r < (1 << K); ++r) {
+            const uint32_t i = base + ((uint32_t)r << lo);
+            v[r] = gsrc ? __ldg(gsrc + i) : sm[pidx(i)];
+        }
+        fwd_group<K>(v, base, lo, logN, tw, q);
+        if (gdst) {
+            const uint32_t q2 = 2u * q;
+#pragma unroll
+            for (int r = 0; r < (1 << K); ++r) v[r] = red_4q(v[r], q2, q);
+            if (K >= 2 && lo == 0) {
+#pragma unroll
+                for (int r = 0; r < (1 << K); r += 4)
+                    *reinterpret_cast<uint4 *>(gdst + base + r) = make_uint4(v[r], v[r + 1], v[r + 2], v[r + 3]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < (1 << K); ++r) gdst[base + ((uint32_t)r << lo)] = v[r];
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < (1 << K); ++r) sm[pidx(base + ((uint32_t)r << lo))] = v[r];
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void inv_pass(uint32_t *sm, uint32_t npoly, uint32_t logM, uint32_t lo,
+                                         const uint2 *__restrict__ twi, uint32_t q) {
+    const uint32_t per = 1u << (logM - K);
+    for (uint32_t idx = threadIdx.x; idx < npoly * per; idx += blockDim.x) {
+        const uint32_t pj = idx >> (logM - K), gid = idx & (per - 1u);
+        const uint32_t base = group_base(gid, lo, K);
+        const uint32_t off = pj << logM;
+        uint32_t v[1 << K];
+#pragma unroll
+        for (int r = 0; r < (1 << K); ++r) v[r] = sm[pidx(off + base + ((uint32_t)r << lo))];
+        inv_group<K>(v, base, lo, logM, twi, q);
+#pragma unroll
+        for (int r = 0; r < (1 << K); ++r) sm[pidx(off + base + ((uint32_t)r << lo))] = v[r];
+    }
+}
+
+// Forward negacyclic NTT of one polynomial by the whole CTA: global `src`
+// (residues < 4q) -> global `dst` (residues in [0, q), canonical
+// bit-reversed order).  `sm` holds padded_words(N) words.  Ends with a
+// barrier.  src may equal dst.
+__device__ __forceinline__ void ntt_fwd_global(const uint32_t *src, uint32_t *dst, uint32_t *sm, uint32_t logN,
+                                               const uint2 *__restrict__ tw, uint32_t q) {
+    uint32_t npass = 0, lo = 0;
+    for (uint32_t pass = 0;; ++pass) {
+        const uint32_t k = fwd_pass_k(logN, pass, lo, npass);
+        const uint32_t *gs = pass == 0 ? src : nullptr;
+        uint32_t *gd = pass + 1 == npass ? dst : nullptr;
+        switch (k) {
+            case 1: fwd_pass<1>(gs, gd, sm, logN, lo, tw, q); break;
+            case 2: fwd_pass<2>(gs, gd, sm, logN, lo, tw, q); break;
+            case 3: fwd_pass<3>(gs, gd, sm, logN, lo, tw, q); break;
+            case 4: fwd_pass<4>(gs, gd, sm, logN, lo, tw, q); break;
+            default: fwd_pass<5>(gs, gd, sm, logN, lo, tw, q); break;
+        }
+        __syncthreads();
+        if (pass + 1 == npass) break;
+    }
+}
+
+// In-place inverse negacyclic NTT (no M^-1 factor) of `npoly` polynomials of
+// length 2^logM stored back to back in the padded shared buffer, passes of
+// at most KMAX stages.  Input residues < 2q; output in [0, 2q).  Caller
+// synchronizes before; ends with a barrier.
+template <int KMAX>
+__device__ __forceinline__ void intt_smem_padded(uint32_t *sm, uint32_t npoly, uint32_t logM,
+                                                 const uint2 *__restrict__ twi, uint32_t q) {
+    if (logM == 0) return;
+    uint32_t npass = 0, lo = 0;
+    for (uint32_t pass = 0;; ++pass) {
+        const uint32_t k = inv_pass_k<KMAX>(logM, pass, lo, npass);
+        switch (k) {
+            case 1: inv_pass<1>(sm, npoly, logM, lo, twi, q); break;
+            case 2: inv_pass<2>(sm, npoly, logM, lo, twi, q); break;
+            case 3: inv_pass<3>(sm, npoly, logM, lo, twi, q); break;
+            case 4: inv_pass<4>(sm, npoly, logM, lo, twi, q); break;
+            default:
+                if constexpr (KMAX >= 5) inv_pass<5>(sm, npoly, logM, lo, twi, q);
+                break;
+        }
+        __syncthreads();
+        if (pass + 1 == npass) break;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Compile-time transforms.  LOG is log2 of the length; every pass's bit range
+// [LO, LO+K) with K <= 4 is a constant, so shared-memory and twiddle offsets
+// are immediates.  In the padded layout a group's element r sits at
+// pidx(base) + off(r), off(r) = (r << LO) + ((r << LO) >> 5): this holds when
+// LO = 0 (base is a multiple of 2^K, K <= 5) and when LO + K >= 5 (then
+// base mod 32 < 2^LO), which every pass below satisfies.
+// ---------------------------------------------------------------------------
+constexpr int kMaxPassStages = 4;
+
+template <int LOG, bool INV>
+struct PassPlan {
+    // the pass on bits [0, kLow) comes last (forward) or first (inverse)
+    static constexpr int kLow = LOG < kMaxPassStages ? LOG : kMaxPassStages;
+    static constexpr int kRem = LOG - kLow;
+    static constexpr int kMid = (kRem + kMaxPassStages - 1) / kMaxPassStages;
+    static constexpr int kPasses = kMid + 1;
+    static constexpr int mid_k(int i) { return kMid == 0 ? 0 : kRem / kMid + (i < kRem % kMid ? 1 : 0); }
+    static constexpr int fwd_lo(int i) {
+        int hi = LOG;
+        for (int j = 0; j <= i; ++j) hi -= mid_k(j);
+        return hi;
+    }
+    static constexpr int k(int pass) {
+        return INV ? (pass == 0 ? kLow : mid_k(pass - 1)) : (pass == kMid ? kLow : mid_k(pass));
+    }
+    static constexpr int lo(int pass) {
+        if (INV) {
+            int l = kLow;
+            for (int j = 1; j < pass; ++j) l += mid_k(j - 1);
+            return pass == 0 ? 0 : l;
+        }
+        return pass == kMid ? 0 : fwd_lo(pass);
+    }
+};
+
+template <int LO>
+__device__ __forceinline__ constexpr uint32_t sm_off(int r) {
+    return ((uint32_t)r << LO) + (((uint32_t)r << LO) >> 5);
+}
+
+template <int K, int LO, int LOG, int J>
+struct FwdStageC {
+    static __device__ __forceinline__ void run(uint32_t (&v)[1 << K], uint32_t base, const uint2 *__restrict__ tw,
+                                               uint32_t q, uint32_t q2) {
+        constexpr int kHalf = 1 << (K - 1 - J);
+        constexpr int P = LO + K - 1 - J;
+        const uint2 *t = tw + (1u << (LOG - 1 - P)) + (base >> (P + 1));
+#pragma unroll
+        for (int blk = 0; blk < (1 << J); ++blk) {
+            const uint2 w = __ldg(t + blk);
+#pragma unroll
+            for (int u = 0; u < kHalf; ++u) bf_fwd(v[blk * 2 * kHalf + u], v[blk * 2 * kHalf + u + kHalf], w, q, q2);
+        }
+        FwdStageC<K, LO, LOG, J + 1>::run(v, base, tw, q, q2);
+    }
+};
+template <int K, int LO, int LOG>
+struct FwdStageC<K, LO, LOG, K> {
+    static __device__ __forceinline__ void run(uint32_t (&)[1 << K], uint32_t, const uint2 *, uint32_t, uint32_t) {}
+};
+
+template <int K, int LO, int LOG, int J>
+struct InvStageC {
+    static __device__ __forceinline__ void run(uint32_t (&v)[1 << K], uint32_t base, const uint2 *__restrict__ twi,
+                                               uint32_t q, uint32_t q2) {
+        constexpr int kHalf = 1 << J;
+        constexpr int P = LO + J;
+        const uint2 *t = twi + (1u << (LOG - 1 - P)) + (base >> (P + 1));
+#pragma unroll
+        for (int blk = 0; blk < (1 << (K - 1 - J)); ++blk) {
+            const uint2 w = __ldg(t + blk);
+#pragma unroll
+            for (int u = 0; u < kHalf; ++u) bf_inv(v[blk * 2 * kHalf + u], v[blk * 2 * kHalf + u + kHalf], w, q, q2);
+        }
+        InvStageC<K, LO, LOG, J + 1>::run(v, base, twi, q, q2);
+    }
+};
+template <int K, int LO, int LOG>
+struct InvStageC<K, LO, LOG, K> {
+    static __device__ __forceinline__ void run(uint32_t (&)[1 << K], uint32_t, const uint2 *, uint32_t, uint32_t) {}
+};
+
+// Forward pass PASS of a length-2^LOG transform.  The first pass reads the
+// global source, the last one reduces to [0, q) and writes the global
+// destination (2^K consecutive words per group, 128-bit stores).
+template <int LOG, int PASS>
+struct FwdPassC {
+    using Plan = PassPlan<LOG, false>;
+    static __device__ __forceinline__ void run(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                               uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q) {
+        constexpr int K = Plan::k(PASS), LO = Plan::lo(PASS);
+        static_assert(LO == 0 || LO + K >= 5, "padded offsets need LO = 0 or LO + K >= 5");
+        constexpr bool kFirst = PASS == 0, kLast = PASS + 1 == Plan::kPasses;
+        const uint32_t q2 = 2u * q;
+        for (uint32_t gid = threadIdx.x; gid < (1u << (LOG - K)); gid += blockDim.x) {
+            const uint32_t base = ((gid >> LO) << (LO + K)) | (gid & ((1u << LO) - 1u));
+            const uint32_t pb = pidx(base);
+            uint32_t v[1 << K];
+#pragma unroll
+            for (int r = 0; r < (1 << K); ++r)
+                v[r] = kFirst ? __ldg(src + base + ((uint32_t)r << LO)) : sm[pb + sm_off<LO>(r)];
+            FwdStageC<K, LO, LOG, 0>::run(v, base, tw, q, q2);
+            if (kLast) {
+#pragma unroll
+                for (int r = 0; r < (1 << K); ++r) v[r] = red_4q(v[r], q2, q);
+                if (dst == nullptr) {
+#pragma unroll
+                    for (int r = 0; r < (1 << K); ++r) sm[pb + sm_off<LO>(r)] = v[r];
+                } else if (LO == 0 && K >= 2) {
+#pragma unroll
+                    for (int r = 0; r < (1 << K); r += 4)
+                        *reinterpret_cast<uint4 *>(dst + base + r) = make_uint4(v[r], v[r + 1], v[r + 2], v[r + 3]);
+                } else {
+#pragma unroll
+                    for (int r = 0; r < (1 << K); ++r) dst[base + ((uint32_t)r << LO)] = v[r];
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < (1 << K); ++r) sm[pb + sm_off<LO>(r)] = v[r];
+            }
+        }
+        __syncthreads();
+        FwdPassC<LOG, PASS + 1>::run(src, dst, sm, tw, q);
+    }
+};
+template <int LOG>
+struct FwdPassC<LOG, PassPlan<LOG, false>::kPasses> {
+    static __device__ __forceinline__ void run(const uint32_t *, uint32_t *, uint32_t *, const uint2 *, uint32_t) {}
+};
+
+// Inverse pass PASS over `npoly` padded polynomials of length 2^LOG in
+// shared memory, polynomial p's element i at p * pstride + pidx(i)
+// (pstride >= padded_words(2^LOG)); no 2^-LOG factor.
+template <int LOG, int PASS>
+struct InvPassC {
+    using Plan = PassPlan<LOG, true>;
+    static __device__ __forceinline__ void run(uint32_t *sm, uint32_t npoly, uint32_t pstride,
+                                               const uint2 *__restrict__ twi, uint32_t q) {
+        constexpr int K = Plan::k(PASS), LO = Plan::lo(PASS);
+        static_assert(LO == 0 || LO + K >= 5, "padded offsets need LO = 0 or LO + K >= 5");
+        constexpr uint32_t kPer = 1u << (LOG - K);
+        const uint32_t q2 = 2u * q;
+        for (uint32_t idx = threadIdx.x; idx < npoly * kPer; idx += blockDim.x) {
+            const uint32_t gid = idx & (kPer - 1u);
+            const uint32_t base = ((gid >> LO) << (LO + K)) | (gid & ((1u << LO) - 1u));
+            const uint32_t pb = (idx / kPer) * pstride + pidx(base);
+            uint32_t v[1 << K];
+#pragma unroll
+            for (int r = 0; r < (1 << K); ++r) v[r] = sm[pb + sm_off<LO>(r)];
+            InvStageC<K, LO, LOG, 0>::run(v, base, twi, q, q2);
+#pragma unroll
+            for (int r = 0; r < (1 << K); ++r) sm[pb + sm_off<LO>(r)] = v[r];
+        }
+        __syncthreads();
+        InvPassC<LOG, PASS + 1>::run(sm, npoly, pstride, twi, q);
+    }
+};
+template <int LOG>
+struct InvPassC<LOG, PassPlan<LOG, true>::kPasses> {
+    static __device__ __forceinline__ void run(uint32_t *, uint32_t, uint32_t, const uint2 *, uint32_t) {}
+};
+
+// Dispatchers over lengths (he_kernels.cu; compiled once, not inlined).
+// Forward: global src (< 4q) -> global dst ([0, q), canonical order), length
+// 2^6 .. 2^15, `sm` = padded_words(N) words; with dst == nullptr the result
+// stays in `sm` (padded layout).  Inverse: in place on `npoly`
+// padded polynomials in shared memory, length 2^0 .. 2^15, input < 2q,
+// output [0, 2q).  Both end with a barrier; the caller synchronizes before
+// the inverse.
+__device__ void ntt_fwd_c(const uint32_t *src, uint32_t *dst, uint32_t *sm, uint32_t logN,
+                          const uint2 *__restrict__ tw, uint32_t q);
+__device__ void intt_c(uint32_t *sm, uint32_t npoly, uint32_t pstride, uint32_t logM, const uint2 *__restrict__ twi,
+                       uint32_t q);
 
 #endif  // __CUDACC__

@@ -24,6 +24,44 @@
 
 #include "he_internal.h"
 
+__device__ __noinline__ void ntt_fwd_c(const uint32_t *src, uint32_t *dst, uint32_t *sm, uint32_t logN,
+                                       const uint2 *__restrict__ tw, uint32_t q) {
+    switch (logN) {
+        case 6: FwdPassC<6, 0>::run(src, dst, sm, tw, q); break;
+        case 7: FwdPassC<7, 0>::run(src, dst, sm, tw, q); break;
+        case 8: FwdPassC<8, 0>::run(src, dst, sm, tw, q); break;
+        case 9: FwdPassC<9, 0>::run(src, dst, sm, tw, q); break;
+        case 10: FwdPassC<10, 0>::run(src, dst, sm, tw, q); break;
+        case 11: FwdPassC<11, 0>::run(src, dst, sm, tw, q); break;
+        case 12: FwdPassC<12, 0>::run(src, dst, sm, tw, q); break;
+        case 13: FwdPassC<13, 0>::run(src, dst, sm, tw, q); break;
+        case 14: FwdPassC<14, 0>::run(src, dst, sm, tw, q); break;
+        default: FwdPassC<15, 0>::run(src, dst, sm, tw, q); break;
+    }
+}
+
+__device__ __noinline__ void intt_c(uint32_t *sm, uint32_t npoly, uint32_t pstride, uint32_t logM,
+                                    const uint2 *__restrict__ twi, uint32_t q) {
+    switch (logM) {
+        case 0: break;
+        case 1: InvPassC<1, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 2: InvPassC<2, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 3: InvPassC<3, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 4: InvPassC<4, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 5: InvPassC<5, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 6: InvPassC<6, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 7: InvPassC<7, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 8: InvPassC<8, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 9: InvPassC<9, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 10: InvPassC<10, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 11: InvPassC<11, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 12: InvPassC<12, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 13: InvPassC<13, 0>::run(sm, npoly, pstride, twi, q); break;
+        case 14: InvPassC<14, 0>::run(sm, npoly, pstride, twi, q); break;
+        default: InvPassC<15, 0>::run(sm, npoly, pstride, twi, q); break;
+    }
+}
+
 namespace {
 
 constexpr int kThreads = 256;
@@ -37,32 +75,29 @@ __device__ __forceinline__ uint4 ldg4(const uint32_t *p) {
 // ---------------------------------------------------------------------------
 
 // Transform polynomial `src` (N residues) into `dst` with the whole CTA.
+// Forward: register-blocked passes (padded shared buffer of
+// padded_words(N) words).  Inverse (utility entry point only): radix-2
+// stages in an unpadded buffer, then N^-1.
 __device__ __forceinline__ void ntt_body(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
                                          uint32_t logN, const uint2 *tw, const LimbK &K, bool inverse,
                                          uint4 *smem4) {
     uint32_t *a = reinterpret_cast<uint32_t *>(smem4);
+    if (!inverse) {
+        ntt_fwd_c(src, dst, a, logN, tw, K.q);
+        return;
+    }
     const uint32_t N = 1u << logN;
     const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
     for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) smem4[i] = __ldg(s4 + i);
     __syncthreads();
-    if (!inverse)
-        ntt_fwd_smem(a, logN, tw, K.q);
-    else
-        ntt_inv_smem(a, 1, logN, tw, K.q);
+    ntt_inv_smem(a, 1, logN, tw, K.q);
     uint4 *d4 = reinterpret_cast<uint4 *>(dst);
     for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) {
         uint4 v = smem4[i];
-        if (!inverse) {
-            v.x = red_4q(v.x, K.q2, K.q);
-            v.y = red_4q(v.y, K.q2, K.q);
-            v.z = red_4q(v.z, K.q2, K.q);
-            v.w = red_4q(v.w, K.q2, K.q);
-        } else {
-            v.x = red_2q(shoup_lazy(v.x, K.ninv, K.ninvs, K.q), K.q);
-            v.y = red_2q(shoup_lazy(v.y, K.ninv, K.ninvs, K.q), K.q);
-            v.z = red_2q(shoup_lazy(v.z, K.ninv, K.ninvs, K.q), K.q);
-            v.w = red_2q(shoup_lazy(v.w, K.ninv, K.ninvs, K.q), K.q);
-        }
+        v.x = red_2q(shoup_lazy(v.x, K.ninv, K.ninvs, K.q), K.q);
+        v.y = red_2q(shoup_lazy(v.y, K.ninv, K.ninvs, K.q), K.q);
+        v.z = red_2q(shoup_lazy(v.z, K.ninv, K.ninvs, K.q), K.q);
+        v.w = red_2q(shoup_lazy(v.w, K.ninv, K.ninvs, K.q), K.q);
         d4[i] = v;
     }
 }
@@ -120,11 +155,27 @@ __device__ __forceinline__ void mac4(uint64_t (&acc)[NJ][NB], const uint4 &w, co
 // 64-bit accumulator takes at most 16 products < (q-1)^2 on top of a residue
 // < q (16 (2^30-2)^2 + 2^30 < 2^64), then is reduced.
 template <int NJ, int NB>
+__device__ __forceinline__ void reduce_acc(uint64_t (&acc)[NJ][NB], const LimbK &K) {
+#pragma unroll
+    for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+        for (int b = 0; b < NB; ++b) acc[jj][b] = reduce64(acc[jj][b], K);
+}
+
+template <int NJ, int NB, int CPT>
 __device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K, uint32_t n, uint32_t l,
                                                uint32_t col0, uint4 *smem4) {
-    uint32_t *Z = reinterpret_cast<uint32_t *>(smem4);  // [NJ][M]
+    uint32_t *Z = reinterpret_cast<uint32_t *>(smem4);  // NJ padded polynomials of M words
     const uint32_t N = a.N, L = a.L, G = a.G, s = a.s, M = a.M;
-    const uint32_t *W = a.bank + (size_t)(n * L + l) * G * N;
+    const uint32_t PS = padded_words(M);
+    const uint32_t lt = a.logTS, TS = 1u << lt;
+    // channel n's weights for tile t: G rows of TS words at W(t)
+    const uint32_t *Wb = a.bank + bank_index(n, l, 0, 0, a.logN, a.logTS, a.lcs, a.co, G);
+    const size_t tstride = (size_t)a.co * G << lt;
+    // put every tile segment of this channel's weights in flight to L2 at
+    // once, so the loads below wait on L2, not on DRAM
+    if (threadIdx.x == 0)
+        for (uint32_t t = 0; t < (N >> lt); ++t) prefetch_l2_bulk(Wb + t * tstride, (G << lt) * 4u);
     const size_t gstride = (size_t)2 * L * N;
     const uint32_t *X[NJ];
 #pragma unroll
@@ -133,78 +184,97 @@ __device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K,
         X[jj] = a.x + ((size_t)((c >> 1) * G * 2 + (c & 1)) * L + l) * N;
     }
     constexpr uint32_t kU = NB == 1 ? 4 : (NB == 2 ? 8 : 16);  // groups per reduction (16 products)
-    constexpr uint32_t kLd = 4;                               // groups whose loads are issued together
+    // groups per load batch: 6 128-bit loads in flight per thread for NJ = 2
+    constexpr uint32_t kGL = (NJ == 2 && CPT == 1) ? 2u : 1u;
     const uint32_t lanes = s >= 4 ? (s >> 2) : 1u;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nchunk = N >> 2;
-    for (uint32_t c0 = threadIdx.x & ~31u; c0 < nchunk; c0 += blockDim.x) {
-        const uint32_t c = c0 + lane;
-        const bool act = c < nchunk;
-        uint64_t acc[NJ][NB];
+    for (uint32_t c0 = threadIdx.x & ~31u; c0 < nchunk; c0 += blockDim.x * CPT) {
+        uint32_t c[CPT];
+        bool act[CPT];
+        uint64_t acc[CPT][NJ][NB];
 #pragma unroll
-        for (int jj = 0; jj < NJ; ++jj)
-#pragma unroll
-            for (int b = 0; b < NB; ++b) acc[jj][b] = 0;
-        if (act) {
-            uint32_t since = 0, g = 0;
-            for (; g + kLd <= G; g += kLd) {
-                uint4 w[kLd], x[kLd][NJ];
-#pragma unroll
-                for (uint32_t u = 0; u < kLd; ++u) {
-                    w[u] = ldg4(W + (size_t)(g + u) * N + 4u * c);
-#pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj) x[u][jj] = ldg4(X[jj] + (g + u) * gstride + 4u * c);
-                }
-#pragma unroll
-                for (uint32_t u = 0; u < kLd; ++u) mac4<NJ, NB>(acc, w[u], x[u]);
-                since += kLd;
-                if (since + kLd > kU) {
-                    since = 0;
-#pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj)
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) acc[jj][b] = reduce64(acc[jj][b], K);
-                }
-            }
-            for (; g < G; ++g) {
-                uint4 x[NJ];
-                const uint4 w = ldg4(W + (size_t)g * N + 4u * c);
-#pragma unroll
-                for (int jj = 0; jj < NJ; ++jj) x[jj] = ldg4(X[jj] + g * gstride + 4u * c);
-                mac4<NJ, NB>(acc, w, x);
-                if (++since == kU) {
-                    since = 0;
-#pragma unroll
-                    for (int jj = 0; jj < NJ; ++jj)
-#pragma unroll
-                        for (int b = 0; b < NB; ++b) acc[jj][b] = reduce64(acc[jj][b], K);
-                }
-            }
-        }
-        if (NB == 1) {
-#pragma unroll
-            for (int jj = 0; jj < NJ; ++jj) {
-                uint32_t v = reduce64(acc[jj][0], K);
-                for (uint32_t o = 1; o < lanes; o <<= 1) {
-                    v += __shfl_xor_sync(0xffffffffu, v, o);
-                    v = v >= K.q ? v - K.q : v;
-                }
-                if (act && (lane & (lanes - 1)) == 0) Z[jj * M + ((4u * c) >> a.logs)] = v;
-            }
-        } else if (act) {
+        for (int u = 0; u < CPT; ++u) {
+            c[u] = c0 + u * blockDim.x + lane;
+            act[u] = c[u] < nchunk;
 #pragma unroll
             for (int jj = 0; jj < NJ; ++jj)
 #pragma unroll
-                for (int b = 0; b < NB; ++b) Z[jj * M + c * NB + b] = reduce64(acc[jj][b], K);
+                for (int b = 0; b < NB; ++b) acc[u][jj][b] = 0;
+        }
+        uint32_t since = 0, g = 0;
+        for (; g + kGL <= G; g += kGL) {
+            uint4 w[CPT][kGL], x[CPT][kGL][NJ];
+#pragma unroll
+            for (int u = 0; u < CPT; ++u)
+#pragma unroll
+                for (uint32_t gg = 0; gg < kGL; ++gg) {
+                    if (act[u]) {
+                        w[u][gg] = ldg4(Wb + ((4u * c[u]) >> lt) * tstride + (size_t)(g + gg) * TS +
+                                        bank_row_pos((4u * c[u]) & (TS - 1), lt, a.lcs));
+#pragma unroll
+                        for (int jj = 0; jj < NJ; ++jj) x[u][gg][jj] = ldg4(X[jj] + (g + gg) * gstride + 4u * c[u]);
+                    } else {
+                        w[u][gg] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+                        for (int jj = 0; jj < NJ; ++jj) x[u][gg][jj] = make_uint4(0, 0, 0, 0);
+                    }
+                }
+#pragma unroll
+            for (int u = 0; u < CPT; ++u)
+#pragma unroll
+                for (uint32_t gg = 0; gg < kGL; ++gg) mac4<NJ, NB>(acc[u], w[u][gg], x[u][gg]);
+            since += kGL;
+            if (since + kGL > kU) {
+                since = 0;
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) reduce_acc<NJ, NB>(acc[u], K);
+            }
+        }
+        for (; g < G; ++g) {
+#pragma unroll
+            for (int u = 0; u < CPT; ++u) {
+                if (!act[u]) continue;
+                uint4 x[NJ];
+                const uint4 w = ldg4(Wb + ((4u * c[u]) >> lt) * tstride + (size_t)g * TS +
+                                     bank_row_pos((4u * c[u]) & (TS - 1), lt, a.lcs));
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj) x[jj] = ldg4(X[jj] + g * gstride + 4u * c[u]);
+                mac4<NJ, NB>(acc[u], w, x);
+            }
+            if (++since == kU) {
+                since = 0;
+#pragma unroll
+                for (int u = 0; u < CPT; ++u) reduce_acc<NJ, NB>(acc[u], K);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CPT; ++u) {
+            if (NB == 1) {
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj) {
+                    uint32_t v = reduce64(acc[u][jj][0], K);
+                    for (uint32_t o = 1; o < lanes; o <<= 1) {
+                        v += __shfl_xor_sync(0xffffffffu, v, o);
+                        v = v >= K.q ? v - K.q : v;
+                    }
+                    if (act[u] && (lane & (lanes - 1)) == 0) Z[jj * PS + pidx((4u * c[u]) >> a.logs)] = v;
+                }
+            } else if (act[u]) {
+#pragma unroll
+                for (int jj = 0; jj < NJ; ++jj)
+#pragma unroll
+                    for (int b = 0; b < NB; ++b) Z[jj * PS + pidx(c[u] * NB + b)] = reduce64(acc[u][jj][b], K);
+            }
         }
     }
     __syncthreads();
-    ntt_inv_smem(Z, NJ, a.logM, a.tw_inv + (size_t)l * N, K.q);
+    intt_c(Z, NJ, PS, a.logM, a.tw_inv + (size_t)l * N, K.q);
     const uint32_t h = n >> a.logs, off = (n & (s - 1)) * a.mult;
     for (uint32_t idx = threadIdx.x; idx < NJ * M; idx += blockDim.x) {
         const uint32_t jj = idx >> a.logM, e = idx & (M - 1), c = col0 + jj;
         uint32_t *o = a.out + ((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N;
-        o[(e << a.logs) + off] = red_2q(Z[idx], K.q);
+        o[(e << a.logs) + off] = red_2q(Z[jj * PS + pidx(e)], K.q);
     }
     if ((n & (s - 1)) == 0) zero_unused_classes(a, h, l, col0, NJ);
 }
@@ -215,7 +285,9 @@ __device__ __forceinline__ void conv_full_body(const ConvGeo &a, const LimbK &K,
                                                uint32_t c, uint4 *smem4) {
     uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
     const uint32_t N = a.N, L = a.L, G = a.G, s = a.s, logN = a.logN;
-    const uint32_t *W = a.bank + (size_t)(n * L + l) * G * N;
+    const uint32_t *Wb = a.bank + bank_index(n, l, 0, 0, logN, a.logTS, a.lcs, a.co, G);
+    const uint32_t lt = a.logTS, TS = 1u << lt;
+    const size_t tstride = (size_t)a.co * G << lt;
     const uint32_t *Xc = a.x + ((size_t)((c >> 1) * G * 2 + (c & 1)) * L + l) * N;
     const size_t gstride = (size_t)2 * L * N;
     const uint32_t off = (n & (s - 1)) * a.mult;
@@ -224,8 +296,9 @@ __device__ __forceinline__ void conv_full_body(const ConvGeo &a, const LimbK &K,
     for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
         uint64_t acc = 0;
         int gc = 0;
+        const uint32_t *Wk = Wb + (k >> lt) * tstride + bank_row_pos(k & (TS - 1), lt, a.lcs);
         for (uint32_t g = 0; g < G; ++g) {
-            acc += (uint64_t)__ldg(W + (size_t)g * N + k) * __ldg(Xc + g * gstride + k);
+            acc += (uint64_t)__ldg(Wk + (size_t)g * TS) * __ldg(Xc + g * gstride + k);
             if (++gc == 16) {
                 gc = 0;
                 acc = reduce64(acc, K);
@@ -233,22 +306,50 @@ __device__ __forceinline__ void conv_full_body(const ConvGeo &a, const LimbK &K,
         }
         const uint32_t v = reduce64(acc, K);
         const uint32_t ex = (off * (2u * brv(k, logN) + 1u)) & mask2n;
-        Y[k] = mulmod(v, __ldg(pp + ex), K);
+        Y[pidx(k)] = mulmod(v, __ldg(pp + ex), K);
     }
     __syncthreads();
-    ntt_inv_smem(Y, 1, logN, a.tw_inv + (size_t)l * N, K.q);
+    intt_c(Y, 1, padded_words(N), logN, a.tw_inv + (size_t)l * N, K.q);
     if (a.mode == HE_OUT_PER_CHANNEL) {
         uint32_t *o = a.out + ((size_t)(((c >> 1) * a.co + n) * 2 + (c & 1)) * L + l) * N;
-        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) o[k] = red_2q(Y[k], K.q);
+        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) o[k] = red_2q(Y[pidx(k)], K.q);
     } else {
         const uint32_t h = n >> a.logs;
         uint32_t *o = a.out + ((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N;
         for (uint32_t e = threadIdx.x; e < a.M; e += blockDim.x) {
             const uint32_t k = (e << a.logs) + off;
-            o[k] = red_2q(Y[k], K.q);
+            o[k] = red_2q(Y[pidx(k)], K.q);
         }
         if ((n & (s - 1)) == 0) zero_unused_classes(a, h, l, c, 1);
     }
+}
+
+// Y[pidx(k)] *= W[k] for k < N (N a multiple of 4 * blockDim or of 4),
+// loading W 128 bits at a time with 4 loads in flight per thread.  Ends
+// with a barrier when `sync`.
+__device__ __forceinline__ void mul_by_row(uint32_t *Y, const uint32_t *__restrict__ W, uint32_t N, const LimbK &K,
+                                           bool sync) {
+    const uint32_t nq = N >> 2;
+    for (uint32_t q0 = 0; q0 < nq; q0 += 4u * blockDim.x) {
+        uint4 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t qi = q0 + u * blockDim.x + threadIdx.x;
+            if (qi < nq) w[u] = __ldg(reinterpret_cast<const uint4 *>(W) + qi);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t qi = q0 + u * blockDim.x + threadIdx.x;
+            if (qi < nq) {
+                const uint32_t k = qi << 2;
+                Y[pidx(k)] = mulmod(w[u].x, Y[pidx(k)], K);
+                Y[pidx(k + 1)] = mulmod(w[u].y, Y[pidx(k + 1)], K);
+                Y[pidx(k + 2)] = mulmod(w[u].z, Y[pidx(k + 2)], K);
+                Y[pidx(k + 3)] = mulmod(w[u].w, Y[pidx(k + 3)], K);
+            }
+        }
+    }
+    if (sync) __syncthreads();
 }
 
 // FC server step for weight polynomial jp, limb l, column c.
@@ -258,14 +359,15 @@ __device__ __forceinline__ void fc_body(const ConvGeo &a, const LimbK &K, uint32
     const uint32_t N = a.N, L = a.L;
     const uint32_t *W = a.bank + (size_t)(jp * L + l) * N;
     const uint32_t *Xc = a.x + ((size_t)c * L + l) * N;
-    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) Y[k] = mulmod(__ldg(W + k), __ldg(Xc + k), K);
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) Y[pidx(k)] = __ldg(Xc + k);
     __syncthreads();
-    ntt_inv_smem(Y, 1, a.logN, a.tw_inv + (size_t)l * N, K.q);
+    mul_by_row(Y, W, N, K, true);
+    intt_c(Y, 1, padded_words(N), a.logN, a.tw_inv + (size_t)l * N, K.q);
     const uint32_t rows = min(a.rpp, a.n_out - jp * a.rpp);
     uint32_t *o = a.out + ((size_t)(((c >> 1) * a.P + jp) * 2 + (c & 1)) * L + l) * N;
     const bool c0 = (c & 1) == 0;
     for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
-        uint32_t v = red_2q(Y[k], K.q);
+        uint32_t v = red_2q(Y[pidx(k)], K.q);
         if (k < rows) {
             if (c0 && a.bias) {
                 v += __ldg(a.bias + (size_t)l * a.n_out + jp * a.rpp + k);
@@ -278,10 +380,40 @@ __device__ __forceinline__ void fc_body(const ConvGeo &a, const LimbK &K, uint32
     }
 }
 
+// A whole FC item in one CTA: column c's input transform (skipped for
+// NTT-domain input), the product with weight polynomial jp, the inverse
+// transform and the output window -- the words fc_body writes.
+__device__ __forceinline__ void fc_fused_body(const ConvGeo &a, const uint32_t *x_coeff, const uint2 *tw_fwd,
+                                              const LimbK &K, uint32_t jp, uint32_t l, uint32_t c, uint4 *smem4) {
+    uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
+    const uint32_t N = a.N, L = a.L;
+    const size_t off = ((size_t)c * L + l) * N;
+    if (x_coeff) {
+        ntt_fwd_c(x_coeff + off, nullptr, Y, a.logN, tw_fwd + (size_t)l * N, K.q);
+    } else {
+        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) Y[pidx(k)] = __ldg(a.x + off + k);
+        __syncthreads();
+    }
+    const uint32_t *W = a.bank + (size_t)(jp * L + l) * N;
+    mul_by_row(Y, W, N, K, true);
+    intt_c(Y, 1, padded_words(N), a.logN, a.tw_inv + (size_t)l * N, K.q);
+    const uint32_t rows = min(a.rpp, a.n_out - jp * a.rpp);
+    uint32_t *o = a.out + ((size_t)(((c >> 1) * a.P + jp) * 2 + (c & 1)) * L + l) * N;
+    const bool c0 = (c & 1) == 0;
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+        uint32_t v = k < rows ? red_2q(Y[pidx(k)], K.q) : 0u;
+        if (k < rows && c0 && a.bias) {
+            v += __ldg(a.bias + (size_t)l * a.n_out + jp * a.rpp + k);
+            v = min(v, v - K.q);
+        }
+        o[k] = v;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // single-call kernels
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_ntt(const RingView r, const uint32_t *__restrict__ in,
+__global__ void __launch_bounds__(kThreads, 3) k_ntt(const RingView r, const uint32_t *__restrict__ in,
                                                  uint32_t *__restrict__ out, int inverse) {
     extern __shared__ uint4 smem4[];
     const uint32_t p = blockIdx.x, N = r.N, l = p % r.L;
@@ -293,8 +425,8 @@ __global__ void __launch_bounds__(kThreads) k_ntt(const RingView r, const uint32
 struct PackConvArgs {
     RingView r;
     const int8_t *w;   // [co][ci][fh][fw]
-    uint32_t *bank;    // [co][L][G][N]
-    uint32_t ci, co, fh, fw, hp, s, G, mult;
+    uint32_t *bank;    // tile-major, see bank_index
+    uint32_t ci, co, fh, fw, hp, s, G, mult, lt, lcs;
 };
 
 // Slot k of the NTT domain is the value at X_k = psi^(2 brv(k) + 1).  The
@@ -327,13 +459,12 @@ __global__ void __launch_bounds__(kThreads) k_pack_conv(const PackConvArgs a) {
     ntt_fwd_smem(A, logN, a.r.tw_fwd + (size_t)l * N, K.q);
     const uint32_t mask2n = 2u * N - 1u;
     const uint32_t *pp = a.r.psi_pow + (size_t)l * 2u * N;
-    uint32_t *dst = a.bank + ((size_t)(n * a.r.L + l) * a.G + g) * N;
     for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
         uint32_t x = red_4q(A[k], K.q2, K.q);
         const uint32_t ex = (off * (2u * brv(k, logN) + 1u)) & mask2n;
         x = mulmod(x, __ldg(pp + ((2u * N - ex) & mask2n)), K);
         x = red_2q(shoup_lazy(x, K.ninv, K.ninvs, K.q), K.q);
-        dst[k] = x;
+        a.bank[bank_index(n, l, g, k, logN, a.lt, a.lcs, a.co, a.G)] = x;
     }
 }
 
@@ -378,10 +509,16 @@ __global__ void __launch_bounds__(kThreads) k_pack_fc(const PackFcArgs a) {
     }
 }
 
-template <int NJ, int NB>
-__global__ void __launch_bounds__(kThreads) k_conv_fold(const ConvGeo a, const RingView r) {
+// resident CTAs per SM the register budget is set for, by column tile width
+template <int NJ>
+struct MinBlocks {
+    static constexpr int value = NJ <= 2 ? 4 : (NJ == 4 ? 3 : (NJ == 8 ? 2 : 1));
+};
+
+template <int NJ, int NB, int CPT>
+__global__ void __launch_bounds__(kThreads, MinBlocks<NJ>::value) k_conv_fold(const ConvGeo a, const RingView r) {
     extern __shared__ uint4 smem4[];
-    conv_fold_body<NJ, NB>(a, r.limb[blockIdx.y], blockIdx.x, blockIdx.y, blockIdx.z * NJ, smem4);
+    conv_fold_body<NJ, NB, CPT>(a, r.limb[blockIdx.y], blockIdx.x, blockIdx.y, blockIdx.z * NJ, smem4);
 }
 
 __global__ void __launch_bounds__(kThreads) k_conv_full(const ConvGeo a, const RingView r) {
@@ -397,33 +534,328 @@ __global__ void __launch_bounds__(kThreads) k_fc(const ConvGeo a, const RingView
 // ---------------------------------------------------------------------------
 // plan kernels (one CTA per item; items are ordered longest first on the host)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_plan_ntt(const CallDesc *__restrict__ calls,
+__global__ void __launch_bounds__(kThreads, 3) k_plan_ntt(const CallDesc *__restrict__ calls,
                                                       const NttItem *__restrict__ items) {
     extern __shared__ uint4 smem4[];
     const NttItem it = items[blockIdx.x];
     const CallDesc &cd = calls[it.call];
-    const uint32_t N = cd.g.N, L = cd.g.L, l = it.poly % L;
+    const uint32_t N = cd.g.N, L = cd.g.L;
+    const uint32_t l = it.poly % L;
     const LimbK K = cd.limb[l];
     ntt_body(cd.x_coeff + (size_t)it.poly * N, const_cast<uint32_t *>(cd.g.x) + (size_t)it.poly * N, cd.g.logN,
              cd.tw_fwd + (size_t)l * N, K, false, smem4);
 }
 
+// Fused FC items of a plan: item.poly = (jp * L + l) * ncols + column.
+__global__ void __launch_bounds__(kThreads) k_plan_fc(const CallDesc *__restrict__ calls,
+                                                     const NttItem *__restrict__ items) {
+    extern __shared__ uint4 smem4[];
+    const NttItem it = items[blockIdx.x];
+    const CallDesc &cd = calls[it.call];
+    const uint32_t L = cd.g.L, col = it.poly % cd.g.ncols, l = (it.poly / cd.g.ncols) % L,
+                   jp = it.poly / (cd.g.ncols * L);
+    const ConvGeo g = cd.g;
+    fc_fused_body(g, cd.x_coeff, cd.tw_fwd, cd.limb[l], jp, l, col, smem4);
+}
+
 template <int NJ>
-__global__ void __launch_bounds__(kThreads) k_plan_chan(const CallDesc *__restrict__ calls,
+__global__ void __launch_bounds__(kThreads, MinBlocks<NJ>::value) k_plan_chan(const CallDesc *__restrict__ calls,
                                                        const ChanItem *__restrict__ items) {
     extern __shared__ uint4 smem4[];
     const ChanItem it = items[blockIdx.x];
     const CallDesc &cd = calls[it.call];
     const ConvGeo g = cd.g;
     const LimbK K = cd.limb[it.l];
-    if (cd.kind == HE_KIND_FC) {
-        fc_body(g, K, it.a, it.l, it.b, smem4);
-    } else if (cd.nb == 1) {
-        conv_fold_body<NJ, 1>(g, K, it.a, it.l, it.b * NJ, smem4);
-    } else if (cd.nb == 2) {
-        conv_fold_body<NJ, 2>(g, K, it.a, it.l, it.b * NJ, smem4);
+    if (cd.nb == 1) {
+        if constexpr (NJ <= 4) {
+            if (cd.cpt == 2) {
+                conv_fold_body<NJ, 1, 2>(g, K, it.a, it.l, it.b * NJ, smem4);
+                return;
+            }
+        }
+        conv_fold_body<NJ, 1, 1>(g, K, it.a, it.l, it.b * NJ, smem4);
+    } else if constexpr (NJ <= 8) {
+        if (cd.nb == 2) {
+            conv_fold_body<NJ, 2, 1>(g, K, it.a, it.l, it.b * NJ, smem4);
+        } else if constexpr (NJ <= 4) {
+            conv_fold_body<NJ, 4, 1>(g, K, it.a, it.l, it.b * NJ, smem4);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// split form of the channel step (plans): a MAC kernel per slot tile, then a
+// finishing kernel per output polynomial
+// ---------------------------------------------------------------------------
+constexpr uint32_t kSpinLimit = 1u << 20;  // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// One bulk copy global -> shared whose completion is counted on `bar`.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Waits for phase `parity` of `bar`; gives up after kSpinLimit polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Persistent MAC kernel of the split form (one ciphertext per call:
+// columns c0, c1).  Each CTA owns a list of work items (call, limb l, slot
+// tile t of TS slots, channels n0 .. n0+nc-1), assigned longest first on the
+// host.  Thread 0 keeps one continuous bulk-copy stream of 16 KB weight
+// stages through a ring across the CTA's whole list -- the weights of an
+// item's channel range for its tile are one contiguous region of nc*G*TS
+// words in the tile-major bank -- and double-buffers each item's ciphertext
+// inputs (2 columns x G groups x TS slots).
+//
+// Thread (column jj, slot group c) owns the CS*4 consecutive slots
+// t*TS + 4*CS*c ..; its inputs for the item sit in registers.  With
+// G*CS <= 4 a channel adds at most 16 products of (q-1)^2 per column, so
+// one 64-bit accumulator per column needs a single reduction per channel.
+// The per-thread sum covers CS*4 slots of one s-slot block; the block sum
+// (the valid-slot-only fold, see conv_fold_body) adds s/(4*CS) neighbouring
+// lanes and goes to the folded buffer z[l][jj][n][block].
+struct MacStream {        // thread 0's producer cursor
+    uint32_t k, st, issued;
+    MacCopy c;            // descriptor of item k (loaded when the cursor reaches it)
+};
+
+// thread 0: issue the next weight stage of the CTA's stream, if any
+__device__ __forceinline__ void mac_issue_next(MacStream &cur, uint32_t ie, const MacCopy *__restrict__ copies,
+                                               uint64_t *rbars, uint32_t *ring) {
+    if (cur.k >= ie) return;
+    if (cur.st == 0) cur.c = copies[cur.k];
+    const uint32_t w = min(kMacStageWords, cur.c.nwords - cur.st * kMacStageWords);
+    const uint32_t buf = cur.issued % kMacStages;
+    if (cur.issued >= kMacStages) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect(rbars + buf, w * 4u);
+    bulk_load(ring + buf * kMacStageWords, cur.c.w + (size_t)cur.st * kMacStageWords, w * 4u, rbars + buf);
+    ++cur.issued;
+    if ((++cur.st) * kMacStageWords >= cur.c.nwords) {
+        cur.st = 0;
+        ++cur.k;
+    }
+}
+
+// thread 0: an item's ciphertext inputs into input buffer X
+__device__ __forceinline__ void mac_issue_inputs(const MacCopy &c, uint32_t *X, uint64_t *xbar) {
+    mbar_expect(xbar, c.xrows * c.xwords * 4u);
+    for (uint32_t r = 0; r < c.xrows; ++r) {
+        // buffer row order [jj][g]: input row (g, jj) = 2g + jj
+        const uint32_t g = r >> 1, jj = r & 1u;
+        bulk_load(X + (jj * (c.xrows >> 1) + g) * c.xwords, c.x + (size_t)r * c.xstride, c.xwords * 4u, xbar);
+    }
+}
+
+template <int G, int CS>
+__device__ __forceinline__ bool mac_item(const CallDesc &cd, const ChanItem it, const uint32_t *X, uint32_t *ring,
+                                         uint64_t *rbars, uint32_t &gs, MacStream &cur, uint32_t ie,
+                                         const MacCopy *__restrict__ copies) {
+    constexpr int NJ = 2;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    const uint32_t t = it.a, l = it.l, n0 = it.b;
+    const uint32_t co = cd.g.co, lt = cd.g.logTS, logs = cd.g.logs, s = cd.g.s, M = cd.g.M;
+    const uint32_t nc = min(cd.g.nc, co - n0);
+    const LimbK K = cd.limb[l];
+    const uint32_t lanes = max(1u, s / (4u * CS));                     // threads whose sums make one block
+    const uint32_t lgr = lt - 2 - (CS == 4 ? 2 : (CS == 2 ? 1 : 0));  // log2 slot groups per column
+    const uint32_t jj = tid >> lgr, c = tid & ((1u << lgr) - 1u);
+    const bool act = jj < NJ;
+    const uint32_t so = 4u * CS * c;                                   // first slot within the tile
+    uint4 x[G][CS];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int u = 0; u < CS; ++u)
+            x[g][u] = act ? *reinterpret_cast<const uint4 *>(X + (((jj & 1u) * G + g) << lt) + so + 4u * u)
+                          : make_uint4(0, 0, 0, 0);
+    uint32_t *zc = cd.z + ((size_t)(l * NJ + (jj & 1u)) * co) * M + (((t << lt) + so) >> logs);
+    const uint32_t nwords = (nc * G) << lt;
+    const uint32_t nst = (nwords + kMacStageWords - 1) / kMacStageWords;
+    const uint32_t chps = kMacStageWords >> lt;  // weight rows per stage
+    uint32_t n = n0;
+    for (uint32_t st = 0; st < nst; ++st, ++gs) {
+        const uint32_t buf = gs % kMacStages;
+        // one barrier per stage: it publishes the wait's outcome and tells
+        // thread 0 that every thread is done with the previous stage's buffer
+        if (!__syncthreads_and(mbar_wait(rbars + buf, (gs / kMacStages) & 1u))) return false;
+        if (tid == 0 && gs > 0) mac_issue_next(cur, ie, copies, rbars, ring);
+        // the bank interleaves chunks: this thread's u-th chunk is uint4 u*NG + c
+        const uint32_t *Wst = ring + buf * kMacStageWords + 4u * c;
+        const uint32_t rows = min(chps, nc * G - st * chps);
+        for (uint32_t r0 = 0; r0 < rows; r0 += G, ++n) {
+            // at most 16 products per column per channel: four independent
+            // chains, summed without overflow
+            uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int u = 0; u < CS; ++u) {
+                    const uint4 w =
+                        *reinterpret_cast<const uint4 *>(Wst + ((r0 + g) << lt) + ((uint32_t)u << (lgr + 2)));
+                    a0 += (uint64_t)w.x * x[g][u].x;
+                    a1 += (uint64_t)w.y * x[g][u].y;
+                    a2 += (uint64_t)w.z * x[g][u].z;
+                    a3 += (uint64_t)w.w * x[g][u].w;
+                }
+            uint32_t v = reduce64((a0 + a1) + (a2 + a3), K);
+            for (uint32_t o = 1; o < lanes; o <<= 1) {
+                v += __shfl_xor_sync(0xffffffffu, v, o);
+                v = min(v, v - K.q);
+            }
+            if (act && (lane & (lanes - 1)) == 0) zc[(size_t)n * M] = v;
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_plan_mac(const CallDesc *__restrict__ calls,
+                                                         const ChanItem *__restrict__ items,
+                                                         const MacCopy *__restrict__ copies,
+                                                         const uint32_t *__restrict__ offs,
+                                                         uint32_t *__restrict__ status) {
+    extern __shared__ uint4 smem4[];
+    uint64_t *xbars = reinterpret_cast<uint64_t *>(smem4);  // [2] input buffers
+    uint64_t *rbars = xbars + 2;                             // [kMacStages] ring
+    uint32_t *Xb = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(smem4) + kMacHdrBytes);
+    uint32_t *ring = Xb + 2 * kMacXWords;
+    const uint32_t ib = offs[blockIdx.x], ie = offs[blockIdx.x + 1];
+    const uint32_t tid = threadIdx.x;
+    if (ib >= ie) return;
+    if (tid == 0) {
+        for (uint32_t i = 0; i < 2 + kMacStages; ++i) mbar_init(xbars + i, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    MacStream cur;
+    cur.k = ib;
+    cur.st = 0;
+    cur.issued = 0;
+    uint32_t xissued = 0;  // input buffers issued (thread 0)
+    if (tid == 0) {
+        for (uint32_t k = ib; k < ie && k < ib + 2; ++k) {
+            mac_issue_inputs(copies[k], Xb + (k - ib) * kMacXWords, xbars + (k - ib));
+            ++xissued;
+        }
+        for (uint32_t i = 0; i < kMacStages; ++i) mac_issue_next(cur, ie, copies, rbars, ring);
+    }
+    uint32_t gs = 0;   // weight stages consumed
+    bool ok = true;
+    for (uint32_t k = ib; ok && k < ie; ++k) {
+        const ChanItem it = items[k];
+        const CallDesc &cd = calls[it.call];
+        const uint32_t xb = (k - ib) & 1u;
+        ok = __syncthreads_and(mbar_wait(xbars + xb, ((k - ib) >> 1) & 1u)) != 0;
+        if (!ok) break;
+        const uint32_t *X = Xb + xb * kMacXWords;
+        switch (he_mac_class(cd.g.G, cd.g.cs)) {
+            case 0: ok = mac_item<1, 1>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
+            case 1: ok = mac_item<1, 2>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
+            case 2: ok = mac_item<1, 4>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
+            case 3: ok = mac_item<2, 1>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
+            case 4: ok = mac_item<2, 2>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
+            default: ok = mac_item<4, 1>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
+        }
+        // every thread read item k's inputs into registers and has passed a
+        // barrier inside mac_item since (items have >= 1 stage), so buffer
+        // xb is free
+        if (ok && tid == 0 && k + 2 < ie) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mac_issue_inputs(copies[k + 2], Xb + xb * kMacXWords, xbars + xb);
+            ++xissued;
+        }
+    }
+    if (!ok) {
+        // a wait gave up: report, then give every copy this CTA issued a
+        // bounded chance to land before its shared memory is released
+        if (tid == 0) {
+            atomicOr(status, 1u);
+            for (uint32_t i = 0; i < xissued; ++i) mbar_wait(xbars + (i & 1u), (i >> 1) & 1u);
+            for (uint32_t i = gs; i < cur.issued; ++i) mbar_wait(rbars + i % kMacStages, (i / kMacStages) & 1u);
+        }
+        __syncthreads();
+    }
+}
+
+// Finishing kernel: items (call, h, l, column) run the length-M inverse
+// transforms of the s channels of output polynomial h and write the whole
+// extracted polynomial (coalesced; classes no channel uses are 0).
+constexpr int kFinThreads = 256;
+
+__global__ void __launch_bounds__(kFinThreads, 4) k_plan_fin(const CallDesc *__restrict__ calls,
+                                                      const ChanItem *__restrict__ items) {
+    extern __shared__ uint4 smem4[];
+    const ChanItem it = items[blockIdx.x];
+    const CallDesc &cd = calls[it.call];
+    const LimbK K = cd.limb[it.l];
+    uint32_t *Zs = reinterpret_cast<uint32_t *>(smem4);
+    const uint32_t h = it.a, l = it.l, c = it.b;
+    const uint32_t N = cd.g.N, L = cd.g.L, co = cd.g.co, s = cd.g.s, logs = cd.g.logs, M = cd.g.M,
+                   logM = cd.g.logM, mult = cd.g.mult, H = cd.g.H;
+    const uint32_t sh = min(s, co - h * s);
+    const uint32_t PS = fin_stride(M);
+    const uint32_t *zsrc = cd.z + (((size_t)l * cd.g.ncols + c) * co + h * s) * M;
+    // sh*M words, 4 at a time, 8 loads in flight per thread
+    const uint32_t nq = (sh << logM) >> 2;
+    for (uint32_t q0 = 0; q0 < nq; q0 += 8u * blockDim.x) {
+        uint4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t qi = q0 + u * blockDim.x + threadIdx.x;
+            if (qi < nq) v[u] = __ldcs(reinterpret_cast<const uint4 *>(zsrc) + qi);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t qi = q0 + u * blockDim.x + threadIdx.x;
+            if (qi < nq) {
+                const uint32_t idx = qi << 2, r = idx >> logM, e = idx & (M - 1);
+                uint32_t *d = Zs + r * PS;
+                d[pidx(e)] = v[u].x;
+                d[pidx(e + 1)] = v[u].y;
+                d[pidx(e + 2)] = v[u].z;
+                d[pidx(e + 3)] = v[u].w;
+            }
+        }
+    }
+    __syncthreads();
+    intt_c(Zs, sh, PS, logM, cd.g.tw_inv + (size_t)l * N, K.q);
+    uint32_t *o = cd.g.out + ((size_t)(((c >> 1) * H + h) * 2 + (c & 1)) * L + l) * N;
+    if (mult == 1 && sh == s) {
+        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x)
+            o[k] = red_2q(Zs[(k & (s - 1)) * PS + pidx(k >> logs)], K.q);
     } else {
-        conv_fold_body<NJ, 4>(g, K, it.a, it.l, it.b * NJ, smem4);
+        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+            const uint32_t r = k & (s - 1), rr = r / mult;
+            uint32_t v = 0;
+            if (r == rr * mult && rr < sh) v = red_2q(Zs[rr * PS + pidx(k >> logs)], K.q);
+            o[k] = v;
+        }
     }
 }
 
@@ -459,20 +891,28 @@ cudaError_t set_smem(Kern kernel, size_t bytes) {
     return e;
 }
 
-template <int NJ, int NB>
+template <int NJ, int NB, int CPT>
 cudaError_t launch_fold(const ConvGeo &a, const RingView &r, cudaStream_t st) {
-    const size_t smem = std::max<size_t>(16, (size_t)NJ * a.M * 4u);
-    cudaError_t e = set_smem(k_conv_fold<NJ, NB>, smem);
+    const size_t smem = fold_smem_bytes(NJ, a.M);
+    cudaError_t e = set_smem(k_conv_fold<NJ, NB, CPT>, smem);
     if (e != cudaSuccess) return e;
-    k_conv_fold<NJ, NB><<<dim3(a.co, a.L, a.ncols / NJ), kThreads, smem, st>>>(a, r);
+    k_conv_fold<NJ, NB, CPT><<<dim3(a.co, a.L, a.ncols / NJ), kThreads, smem, st>>>(a, r);
     return cudaGetLastError();
 }
 
 template <int NJ>
 cudaError_t launch_fold_nb(const ConvGeo &a, const RingView &r, cudaStream_t st) {
-    if (a.s >= 4) return launch_fold<NJ, 1>(a, r, st);
-    if (a.s == 2) return launch_fold<NJ, 2>(a, r, st);
-    return launch_fold<NJ, 4>(a, r, st);
+    if (a.s >= 4) {
+        if constexpr (NJ <= 4) {
+            if (he_conv_cpt(NJ, 1, a.G) == 2) return launch_fold<NJ, 1, 2>(a, r, st);
+        }
+        return launch_fold<NJ, 1, 1>(a, r, st);
+    }
+    if constexpr (NJ <= 8) {
+        if (a.s == 2) return launch_fold<NJ, 2, 1>(a, r, st);
+        if constexpr (NJ <= 4) return launch_fold<NJ, 4, 1>(a, r, st);
+    }
+    return cudaErrorInvalidValue;  // he_conv_nj never picks these
 }
 
 template <int NJ>
@@ -496,17 +936,25 @@ uint32_t he_ilog2(uint32_t x) {
 }
 
 // Columns per CTA of the folded kernel: the largest power of two <= 16 that
-// divides 2B and whose block vectors fit 160 KB of shared memory.
-uint32_t he_conv_nj(uint32_t ncols, uint32_t M) {
-    uint32_t nj = 16;
-    while (nj > 2 && ((ncols % nj) != 0 || (size_t)nj * M * 4u > 160u * 1024u)) nj >>= 1;
+// divides 2B and whose block vectors fit 160 KB of shared memory; at most 8
+// for s = 2 and 4 for s = 1 (those keep 2 or 4 accumulators per column).
+uint32_t he_conv_nj(uint32_t ncols, uint32_t M, uint32_t s) {
+    uint32_t nj = s >= 4 ? 16u : (s == 2 ? 8u : 4u);
+    while (nj > 2 && ((ncols % nj) != 0 || fold_smem_bytes(nj, M) > 160u * 1024u)) nj >>= 1;
     return nj;
+}
+
+// Chunks of 4 slots per thread per MAC iteration: two when a single input
+// group would leave only 3 loads in flight.
+uint32_t he_conv_cpt(uint32_t nj, uint32_t nb, uint32_t G) {
+    if (nb != 1 || nj > 4) return 1;
+    return G >= 2 ? 1 : 2;
 }
 
 cudaError_t he_launch_ntt(const RingView &r, const uint32_t *in, uint32_t *out, uint32_t npolys, bool inverse,
                           cudaStream_t st) {
     if (npolys == 0) return cudaSuccess;
-    const size_t smem = (size_t)r.N * 4u;
+    const size_t smem = (size_t)padded_words(r.N) * 4u;
     cudaError_t e = set_smem(k_ntt, smem);
     if (e != cudaSuccess) return e;
     k_ntt<<<npolys, kThreads, smem, st>>>(r, in, out, inverse ? 1 : 0);
@@ -514,8 +962,11 @@ cudaError_t he_launch_ntt(const RingView &r, const uint32_t *in, uint32_t *out, 
 }
 
 cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_conv_desc &d,
-                                const he_conv_layout &lay, uint32_t *bank, cudaStream_t st) {
+                                const he_conv_layout &lay, uint32_t lt, uint32_t lcs, uint32_t *bank,
+                                cudaStream_t st) {
     PackConvArgs a;
+    a.lt = lt;
+    a.lcs = lcs;
     a.r = r;
     a.w = d_w;
     a.bank = bank;
@@ -561,9 +1012,9 @@ static ConvGeo geo_of(const RingView &r) {
     return a;
 }
 
-cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay,
-                           const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out, int mode, uint32_t B,
-                           cudaStream_t st) {
+cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt,
+                           uint32_t lcs, const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out, int mode,
+                           uint32_t B, cudaStream_t st) {
     ConvGeo a = geo_of(r);
     a.bank = bank;
     a.x = x_ntt;
@@ -577,20 +1028,23 @@ cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_co
     a.co = d.co;
     a.mult = lay.off_mult;
     a.ncols = 2u * B;
+    a.logTS = lt;
+    a.lcs = lcs;
     // The folded kernel keeps 2 * M words per CTA in shared memory; for
     // M = N / s above 24K words (s = 1 at N = 32768) the unfolded kernel
     // produces the same words with N words of shared memory.
-    if (mode == HE_OUT_EXTRACTED && (size_t)2 * lay.M * 4u > 192u * 1024u) mode = HE_OUT_EXTRACTED_UNFOLDED;
+    if (mode == HE_OUT_EXTRACTED && fold_smem_bytes(2, lay.M) > 192u * 1024u)
+        mode = HE_OUT_EXTRACTED_UNFOLDED;
     a.mode = (uint32_t)mode;
     if (mode == HE_OUT_EXTRACTED) {
-        switch (he_conv_nj(a.ncols, lay.M)) {
+        switch (he_conv_nj(a.ncols, lay.M, lay.s)) {
             case 16: return launch_fold_nb<16>(a, r, st);
             case 8: return launch_fold_nb<8>(a, r, st);
             case 4: return launch_fold_nb<4>(a, r, st);
             default: return launch_fold_nb<2>(a, r, st);
         }
     }
-    const size_t smem = (size_t)r.N * 4u;
+    const size_t smem = (size_t)padded_words(r.N) * 4u;
     cudaError_t e = set_smem(k_conv_full, smem);
     if (e != cudaSuccess) return e;
     k_conv_full<<<dim3(d.co, r.L, a.ncols), kThreads, smem, st>>>(a, r);
@@ -608,7 +1062,7 @@ cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32
     a.rpp = fl.rows_per_poly;
     a.n_out = fl.n_out;
     a.mode = (uint32_t)mode;
-    const size_t smem = (size_t)r.N * 4u;
+    const size_t smem = (size_t)padded_words(r.N) * 4u;
     cudaError_t e = set_smem(k_fc, smem);
     if (e != cudaSuccess) return e;
     k_fc<<<dim3(fl.P_fc, r.L, 2u * B), kThreads, smem, st>>>(a, r);
@@ -619,6 +1073,9 @@ cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32
 cudaError_t he_plan_prepare(const he_plan_s &pl) {
     cudaError_t e = cudaSuccess;
     if (pl.n_ntt) e = set_smem(k_plan_ntt, pl.smem_ntt);
+    if (e == cudaSuccess && pl.n_mac) e = set_smem(k_plan_mac, pl.smem_mac);
+    if (e == cudaSuccess && pl.n_fin) e = set_smem(k_plan_fin, pl.smem_fin);
+    if (e == cudaSuccess && pl.n_fc) e = set_smem(k_plan_fc, pl.smem_fc);
     if (e == cudaSuccess && pl.n_chan[0]) e = set_smem(k_plan_chan<2>, pl.smem_chan[0]);
     if (e == cudaSuccess && pl.n_chan[1]) e = set_smem(k_plan_chan<4>, pl.smem_chan[1]);
     if (e == cudaSuccess && pl.n_chan[2]) e = set_smem(k_plan_chan<8>, pl.smem_chan[2]);
@@ -629,6 +1086,16 @@ cudaError_t he_plan_prepare(const he_plan_s &pl) {
 // phase: -1 = both, 0 = input NTTs only, 1 = channel kernels only.
 cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     cudaError_t e = cudaSuccess;
+    // fused FC items: forked onto the plan's side stream with the channel
+    // work, joined back before the last channel kernel's completion
+    const bool fc = pl.n_fc && phase != 0;
+    if (fc) {
+        if ((e = cudaEventRecord(pl.ev_fork, st)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(pl.side, pl.ev_fork, 0)) != cudaSuccess) return e;
+        k_plan_fc<<<pl.n_fc, kThreads, pl.smem_fc, pl.side>>>(pl.d_calls, pl.d_fc);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(pl.ev_join, pl.side)) != cudaSuccess) return e;
+    }
     if (pl.n_ntt && phase != 1) {
         e = set_smem(k_plan_ntt, pl.smem_ntt);
         if (e != cudaSuccess) return e;
@@ -637,6 +1104,23 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         if (e != cudaSuccess) return e;
     }
     if (phase == 0) return cudaSuccess;
+    struct Join {
+        const he_plan_s &pl;
+        cudaStream_t st;
+        bool on;
+        ~Join() {
+            if (on) cudaStreamWaitEvent(st, pl.ev_join, 0);
+        }
+    } join{pl, st, fc};
+    if (pl.n_mac) {
+        k_plan_mac<<<pl.mac_ctas, kThreads, pl.smem_mac, st>>>(pl.d_calls, pl.d_mac, pl.d_mac_copy, pl.d_mac_offs,
+                                                               pl.d_status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (pl.n_fin) {
+        k_plan_fin<<<pl.n_fin, kFinThreads, pl.smem_fin, st>>>(pl.d_calls, pl.d_fin);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if ((e = plan_chan_launch<2>(pl, 0, st)) != cudaSuccess) return e;
     if ((e = plan_chan_launch<4>(pl, 1, st)) != cudaSuccess) return e;
     if ((e = plan_chan_launch<8>(pl, 2, st)) != cudaSuccess) return e;

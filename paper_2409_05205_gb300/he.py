@@ -73,6 +73,7 @@ _SIGS = {
     "he_plan_create": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(_vp)],
     "he_plan_run": [_vp, _vp],
     "he_plan_run_phase": [_vp, _i32, _vp],
+    "he_plan_check": [_vp],
     "he_plan_destroy": [_vp],
     "he_sync": [_vp],
     "he_last_error": [],
@@ -250,6 +251,10 @@ def he_plan_run(plan: int, stream=None) -> None:
 
 def he_plan_run_phase(plan: int, phase: int, stream=None) -> None:
     _check(lib().he_plan_run_phase(plan, phase, _stream(stream)))
+
+
+def he_plan_check(plan: int) -> None:
+    _check(lib().he_plan_check(plan))
 
 
 def he_plan_destroy(plan: int) -> None:

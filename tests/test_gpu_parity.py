@@ -316,6 +316,7 @@ def test_plan_mixed_rings_and_shapes_bit_exact():
                     o.fill_(-1)
                 H.he_plan_run(plan, s)
                 H.he_sync(s)
+                H.he_plan_check(plan)
                 for o, ref in zip(outs, refs):
                     np.testing.assert_array_equal(U.from_dev(o).reshape(ref.shape), ref)
         finally:
@@ -374,3 +375,37 @@ def test_plan_rejects_overlapping_outputs():
         with pytest.raises(H.HEError) as ei:
             H.he_plan_create([(f, d_in, H.HE_COEFF, d_in, 1)])
         assert ei.value.status == H.HE_ERR_ARG
+
+
+def test_plan_split_form_plain20_shapes_bit_exact():
+    """Every distinct plain-20 layer shape at N = 8192 with 3 limbs, B = 1
+    (the split MAC + finishing kernels) and the FC layer, in one plan,
+    against the oracle's NTT tier; the plan's status word stays clear."""
+    H = U.he()
+    torch = U.torch_cuda()
+    N, L = 8192, 3
+    ps, psis = U.ring(N, L)
+    with U.params(N, L) as p:
+        calls, refs, banks = [], [], []
+        for k, (ci, co, hw) in enumerate(PLAIN20_SHAPES):
+            _, _, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, 1, seed=300 + k)
+            refs.append(O.conv_layer(cts, F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt"))
+            f = H.he_pack_filters(p, desc, F)
+            banks.append(f)
+            calls.append((f, U.to_dev(cts), H.HE_COEFF, U.empty_dev(refs[-1].shape), 1))
+        f, ct, ref = _plan_case(H, p, N, L, (64, 10), 1, seed=399, fc=True)
+        banks.append(f)
+        refs.append(ref)
+        calls.append((f, U.to_dev(ct), H.HE_COEFF, U.empty_dev(ref.shape), 1))
+        plan = H.he_plan_create(calls)
+        try:
+            s = torch.cuda.current_stream()
+            H.he_plan_run(plan, s)
+            H.he_sync(s)
+            H.he_plan_check(plan)
+            for c, ref in zip(calls, refs):
+                np.testing.assert_array_equal(U.from_dev(c[3]).reshape(ref.shape), ref)
+        finally:
+            H.he_plan_destroy(plan)
+            for f in banks:
+                H.he_filters_destroy(f)
