@@ -180,6 +180,31 @@ void he_filters_destroy(he_filters_t f);
 he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain,
                         uint32_t *d_out, int out_mode, uint32_t B, void *stream);
 
+/* he_conv_layer with no device allocation on its path.  The paper has no
+ * counterpart: this is a library-side variant for callers that must never
+ * see a layer call allocate, such as a server that has divided its whole HBM
+ * budget between requests before it starts, or a process whose device memory
+ * belongs to an outside allocator.  he_conv_layer grows the params'
+ * workspace with cudaMalloc when a call needs more; this entry point instead
+ * transforms coefficient-domain inputs into a fixed 8 MiB scratch array
+ * compiled into the library (one per device), so a call never allocates.
+ *   Arguments, layouts, results and asynchrony are those of he_conv_layer,
+ *   which this call matches word for word.
+ *   Limit: with in_domain == HE_COEFF, B * G * 2 * L * N must be at most
+ *   2,097,152 words (8 MiB); larger calls fail with HE_ERR_ARG and a message,
+ *   and nothing is launched.  HE_NTT inputs use no scratch and have no limit.
+ *   Set-up: the first call on a device looks up the device address of the
+ *   scratch array (cudaGetSymbolAddress, with the params' device current);
+ *   make that first call before any stream capture.
+ *   The scratch is shared by every call on the device, whatever its params
+ *   or stream: calls that may overlap (on different streams, or from
+ *   different threads without ordering) race on it and give wrong results.
+ *   Order them on one stream.  Every scratch word a call reads was written
+ *   by the same call, so nothing needs clearing between calls. */
+he_status he_conv_layer_noalloc(he_params_t p, he_filters_t f, const uint32_t *d_in,
+                                int in_domain, uint32_t *d_out, int out_mode, uint32_t B,
+                                void *stream);
+
 /* Server evaluation of one FC layer for B ciphertexts (Alg. 2 in
  * ciphertext x plaintext form, Theorem 1):
  *   y_j^(c) = c^(c) * w_j, plus Delta_Q * d_j(X) on c0 (c = 0).

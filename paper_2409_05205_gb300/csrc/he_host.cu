@@ -206,6 +206,9 @@ he_status ensure_ws(he_params_s *p, size_t bytes) {
 
 }  // namespace
 
+// Sets the thread-local message of he_last_error for code outside this file.
+he_status he_fail(he_status s, const char *msg) { return fail(s, "%s", msg); }
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

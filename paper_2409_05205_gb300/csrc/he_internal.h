@@ -215,6 +215,8 @@ struct he_filters_s {
     size_t bank_bytes;
 };
 
+he_status he_fail(he_status s, const char *msg);  // he_host.cu
+
 // ---------------------------------------------------------------------------
 // kernel launchers (he_kernels.cu)
 // ---------------------------------------------------------------------------

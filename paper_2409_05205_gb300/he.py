@@ -67,6 +67,7 @@ _SIGS = {
     "he_pack_fc": [_vp, _u32, _u32, _vp, _vp, ctypes.POINTER(_vp)],
     "he_filters_destroy": [_vp],
     "he_conv_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
+    "he_conv_layer_noalloc": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
     "he_fc_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
     "he_ntt_forward": [_vp, _vp, _vp, _u32, _vp],
     "he_ntt_inverse": [_vp, _vp, _vp, _u32, _vp],
@@ -217,6 +218,16 @@ def he_filters_destroy(f: int) -> None:
 def he_conv_layer(p: int, f: int, d_in, in_domain: int, d_out, out_mode: int, B: int,
                   stream=None) -> None:
     _check(lib().he_conv_layer(p, f, _ptr(d_in), in_domain, _ptr(d_out), out_mode, B, _stream(stream)))
+
+
+def he_conv_layer_noalloc(p: int, f: int, d_in, in_domain: int, d_out, out_mode: int, B: int,
+                          stream=None) -> None:
+    """he_conv_layer without any device allocation: coefficient-domain
+    inputs are transformed in a fixed 8 MiB per-device scratch array
+    (B * G * 2 * L * N <= 2**21 words).  Calls that may overlap race on that
+    scratch; order them on one stream."""
+    _check(lib().he_conv_layer_noalloc(p, f, _ptr(d_in), in_domain, _ptr(d_out), out_mode, B,
+                                       _stream(stream)))
 
 
 def he_fc_layer(p: int, f: int, d_in, in_domain: int, d_out, out_mode: int, B: int,
