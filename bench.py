@@ -10,11 +10,14 @@ inference = the 20 server-side layer calls.
 
 Forms measured (same model, same inputs, same output words):
   graph  a plan of the 20 independent layer calls (he_plan_create): one
-         kernel for every input NTT, one for every channel work unit of all
-         layers, captured once in a CUDA graph and replayed once per step --
-         the headline `value` and its p50/p99 per-inference latency;
-  phases the same plan run without the graph, CUDA events between its two
-         kernels -- the per-kernel durations behind the roofline figures;
+         kernel for every input NTT, a persistent MAC kernel over every
+         Conv layer's weights, a finishing kernel (inverse transforms and
+         extraction) and the FC kernel on a forked stream, captured once in
+         a CUDA graph and replayed once per step -- the headline `value`
+         and its p50/p99 per-inference latency;
+  phases the same plan run without the graph in three phases (input NTTs,
+         MAC, the rest) with CUDA events between them -- the MAC kernel's
+         duration is the roofline figure;
   plain  one layer at a time on one stream (he_ntt_forward then
          he_conv_layer / he_fc_layer per layer), events around every launch.
 All forms rotate over 3 model replicas and 3 input sets (> 2x the 129 MB L2),
@@ -246,12 +249,33 @@ class Arm:
             bfly += g["npoly"] * L * (N // 2) * logN
         return ch_bytes, ntt_bytes, bfly
 
+    def mac_bytes(self, split):
+        """Algorithmic bytes of one k_plan_mac launch: for every split-form
+        Conv call, its NTT-domain weight bank (co * G * L * N words) and its
+        transformed inputs (B * G * 2 * L * N words), each read once."""
+        N, L, B = self.N, self.L, self.B
+        tot = 0
+        for g, Ld, sp in zip(self.geo, self.layers, split):
+            if sp and Ld["kind"] == "conv":
+                tot += g["wbytes"] + B * g["lay"]["G"] * 2 * L * N * 4
+        return tot
+
     def free(self):
         for pl in getattr(self, "plans", []):
             self.H.he_plan_destroy(pl)
         for m in self.models:
             m.free()
         self.H.he_params_destroy(self.p)
+
+
+# DRAM bytes (read + write) of one k_plan_mac launch, from an ncu capture of
+# this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where no
+# capture of the current kernel exists.
+TRAFFIC = {"plain20_c10": 136560640 + 4797184}
+
+
+def _traffic(name):
+    return TRAFFIC.get(name)
 
 
 def _events(n):
@@ -297,9 +321,10 @@ def run_ours(args, rank, world, device):
     plain_ntt_ms = sum(evs[k][i][0].elapsed_time(evs[k][i][1]) for k in range(k_plain) for i in range(nl))
     plain_ch_ms = sum(evs[k][i][1].elapsed_time(evs[k][i][2]) for k in range(k_plain) for i in range(nl))
 
-    # ---------------- plan, phase by phase: events between its two kernels
+    # ---------------- plan, phase by phase: events between its kernels
     arm.make_plans()
-    ph = [_events(3) for _ in range(k_phase)]
+    info = H.he_plan_query(arm.plans[0], nl)
+    ph = [_events(4) for _ in range(k_phase)]
     with torch.cuda.stream(stream):
         for k in range(W):
             H.he_plan_run(arm.plans[k % arm.R], stream)
@@ -309,14 +334,17 @@ def run_ours(args, rank, world, device):
         for k in range(k_phase):
             pl = arm.plans[k % arm.R]
             ph[k][0].record(stream)
-            H.he_plan_run_phase(pl, 0, stream)
+            H.he_plan_run_phase(pl, H.HE_PHASE_NTT, stream)
             ph[k][1].record(stream)
-            H.he_plan_run_phase(pl, 1, stream)
+            H.he_plan_run_phase(pl, H.HE_PHASE_MAC, stream)
             ph[k][2].record(stream)
+            H.he_plan_run_phase(pl, H.HE_PHASE_FINISH, stream)
+            ph[k][3].record(stream)
     torch.cuda.synchronize()
     barrier()
     ntt_ms = [e[0].elapsed_time(e[1]) for e in ph]
-    ch_ms = [e[1].elapsed_time(e[2]) for e in ph]
+    mac_ms = [e[1].elapsed_time(e[2]) for e in ph]
+    fin_ms = [e[2].elapsed_time(e[3]) for e in ph]
 
     # ---------------- headline: the plan as a CUDA graph, one replay per step
     with torch.cuda.stream(stream):
@@ -350,10 +378,13 @@ def run_ours(args, rank, world, device):
     e2e = run_e2e(arm, args, stream)
 
     ch_bytes, ntt_bytes, bfly = arm.algorithmic()
+    mac_bytes = arm.mac_bytes(info["split"])
     hbm, peak_src = _peaks()
-    ch_avg = float(np.mean(ch_ms))
+    mac_avg = float(np.mean(mac_ms))
+    fin_avg = float(np.mean(fin_ms))
     ntt_avg = float(np.mean(ntt_ms))
-    ch_gbs = ch_bytes / (ch_avg * 1e-3) / 1e9
+    mac_gbs = mac_bytes / (mac_avg * 1e-3) / 1e9
+    traffic = _traffic(wl["name"])
     res = {
         "metric": METRIC, "value": nl * K * world / (graph_ms * 1e-3), "unit": "layers/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": graph_ms / K,
@@ -361,7 +392,7 @@ def run_ours(args, rank, world, device):
         "dtype": "u32 (exact residues mod 30-bit primes)", "data": "synthetic",
         "config": {"workload": wl["name"], "N": arm.N, "L": arm.L, "B": arm.B, "t": wl["t"],
                    "layers_per_step": nl,
-                   "form": "plan of 20 layer calls (2 kernels) replayed as a CUDA graph",
+                   "form": f"plan of {nl} layer calls ({info['kernels_per_run']} kernels) replayed as a CUDA graph",
                    "l2": "rotates 3 model replicas + 3 input sets (> 2x L2); no flush",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(graph_steps, 50)),
@@ -373,18 +404,23 @@ def run_ours(args, rank, world, device):
                        "kernel_ms_per_step": {"input_ntt": plain_ntt_ms / k_plain,
                                               "channel": plain_ch_ms / k_plain}},
         "speedup_vs_plain_form": (plain_ms / k_plain) / (graph_ms / K),
-        "roofline": {"kernel": "k_plan_chan<2>: channel MAC + folded INTT + extraction, all 20 layers",
-                     "bound": "hbm", "achieved": ch_gbs, "peak": hbm, "unit": "GB/s",
-                     "frac": ch_gbs / hbm, "peak_source": peak_src + " (hbm_gbs burst copy)",
-                     "algorithmic_bytes": ch_bytes, "avg_launch_ms": ch_avg, "launches": k_phase,
-                     "traffic": None},
+        "roofline": {"kernel": "k_plan_mac: NTT-domain channel MAC of every split-form Conv layer "
+                               "(weights + transformed inputs read once)",
+                     "bound": "hbm", "achieved": mac_gbs, "peak": hbm, "unit": "GB/s",
+                     "frac": mac_gbs / hbm, "peak_source": peak_src + " (hbm_gbs burst copy)",
+                     "algorithmic_bytes": mac_bytes, "avg_launch_ms": mac_avg, "launches": k_phase,
+                     "traffic": traffic},
         "kernels": {"k_plan_ntt": {"avg_launch_ms": ntt_avg, "butterflies": bfly,
                                    "gbfly_per_s": bfly / (ntt_avg * 1e-3) / 1e9,
                                    "bytes": ntt_bytes, "gbs": ntt_bytes / (ntt_avg * 1e-3) / 1e9},
-                    "k_plan_chan": {"avg_launch_ms": ch_avg, "bytes": ch_bytes, "gbs": ch_gbs},
-                    "share_ntt": ntt_avg / (ntt_avg + ch_avg)},
+                    "k_plan_mac": {"avg_launch_ms": mac_avg, "bytes": mac_bytes, "gbs": mac_gbs},
+                    "finish_and_fc": {"avg_launch_ms": fin_avg,
+                                      "what": "k_plan_fin on the stream, k_plan_fc on the side stream"},
+                    "step_bytes": ch_bytes,
+                    "step_gbs_graph": ch_bytes / (graph_ms / K * 1e-3) / 1e9},
+        "plan": {k: v for k, v in info.items() if k != "split"},
         "e2e": e2e,
-        "gpu_launches": 2 * K,
+        "gpu_launches": info["kernels_per_run"] * K,
         "clocks": clk,
     }
     arm.free()

@@ -230,23 +230,30 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
                          uint32_t count, void *stream);
 
 /* ------------------------------------------------------------------------
- * Plans: many independent layer calls in one launch pair.
+ * Plans: many independent layer calls in a handful of launches.
  *
  * A plan fixes a list of Conv / FC layer calls (any mix of ring degrees,
  * limb counts, shapes and batch sizes whose params live on one device) and
- * their buffers.  he_plan_run then issues exactly two kernels per batch-size
- * class: one that computes every coefficient-domain input NTT of every call,
- * and one that runs every channel work unit (one output channel x limb x
- * column tile of a Conv call, or one weight polynomial x limb x column of an
- * FC call) of every call, longest first.  Each call computes the words that
- * he_conv_layer / he_fc_layer with HE_OUT_EXTRACTED would write.  Conv calls
- * with B = 1 take a split form: one kernel streams each slot tile's weights
- * for every output channel (bulk copies into shared memory) and stores the
- * folded channel sums in the plan's workspace, a second kernel runs the
- * inverse transforms and writes each extracted output polynomial.  The plan
- * owns its NTT workspace and descriptor tables, so he_plan_run allocates
- * nothing and can be captured into a CUDA graph.  Runs of one plan must not
- * overlap on the GPU; different plans may run concurrently.
+ * their buffers.  Each call computes the words that he_conv_layer /
+ * he_fc_layer with HE_OUT_EXTRACTED would write.  he_plan_run issues, in
+ * order on `stream`:
+ *   1. one kernel computing every coefficient-domain input NTT of every
+ *      Conv call;
+ *   2. for the Conv calls in the split form (B = 1, interleave s >= 4, G in
+ *      {1, 2, 4}): a persistent kernel that streams each slot tile's
+ *      weights for every output channel into shared memory with bulk copies
+ *      and stores the folded channel sums (Sec. III-A, valid slots only) in
+ *      the plan's workspace, then a kernel that runs the length-N/s inverse
+ *      transforms and writes each extracted output polynomial;
+ *   3. for the other Conv calls: one fused kernel per column-tile class
+ *      (MAC, folded inverse transform and extraction per output channel);
+ *   4. every FC call's work (input transform, product, inverse transform,
+ *      bias, output) in one kernel on a side stream that forks off `stream`
+ *      at the start and joins it again before the run completes.
+ * Work items are ordered longest first.  The plan owns its workspace and
+ * descriptor tables, so he_plan_run allocates nothing and can be captured
+ * into a CUDA graph.  Runs of one plan must not overlap on the GPU;
+ * different plans may run concurrently.
  * (Batching pattern; the paper evaluates one layer at a time, Sec. IV.)
  * ------------------------------------------------------------------------ */
 typedef struct he_plan_s *he_plan_t;
@@ -264,10 +271,35 @@ typedef struct {
 he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t *out);
 /* Runs every call of the plan.  Asynchronous on `stream`. */
 he_status he_plan_run(he_plan_t plan, void *stream);
-/* One half of he_plan_run: phase 0 = the input-NTT kernel, phase 1 = the
- * channel kernels.  Phase 1 must follow phase 0 of the same run on the same
- * stream (or be ordered after it); for timing each kernel separately. */
+/* Part of he_plan_run, for timing its kernels separately:
+ *   HE_PHASE_NTT (0)   the input-NTT kernel (step 1 above);
+ *   HE_PHASE_REST (1)  everything after it (steps 2-4);
+ *   HE_PHASE_MAC (2)   the split-form MAC kernel alone (first half of 2);
+ *   HE_PHASE_FINISH (3) everything after the MAC kernel (rest of 2, 3, 4).
+ * A full run is phases 0, 1 or phases 0, 2, 3, in that order on one stream
+ * (or otherwise ordered). */
+#define HE_PHASE_NTT 0
+#define HE_PHASE_REST 1
+#define HE_PHASE_MAC 2
+#define HE_PHASE_FINISH 3
 he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream);
+
+/* What a plan launches; filled by he_plan_query. */
+typedef struct {
+    uint32_t kernels_per_run; /* kernels he_plan_run launches (both streams) */
+    uint32_t ntt_items;       /* polynomials the input-NTT kernel transforms */
+    uint32_t mac_items;       /* split-form MAC items (channels x limb x tile) */
+    uint32_t mac_ctas;        /* persistent CTAs of the MAC kernel */
+    uint32_t finish_items;    /* output polynomial x limb x column items */
+    uint32_t fused_items;     /* non-split Conv channel items, all classes */
+    uint32_t fc_items;        /* FC items on the side stream */
+    uint32_t split_calls;     /* Conv calls in the split form */
+    uint64_t workspace_bytes; /* device workspace the plan owns */
+} he_plan_info;
+/* Fills *info; if `split` is not NULL, also split[i] = 1 for each call i
+ * (of the ncalls given to he_plan_create) that takes the split form, else
+ * 0.  Host only, non-blocking. */
+he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split);
 /* Reports whether a bounded device-side wait of an earlier run gave up
  * (HE_ERR_TIMEOUT; the outputs of that run are then unspecified) and clears
  * the flag.  Blocking; call it after the streams the plan ran on are

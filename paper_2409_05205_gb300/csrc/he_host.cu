@@ -681,6 +681,13 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
     pl->device = device;
     pl->ncalls = ncalls;
     cudaError_t e = cudaSuccess;
+    pl->split = new (std::nothrow) uint8_t[ncalls];
+    if (!pl->split) {
+        delete pl;
+        return fail(HE_ERR_NOMEM, "plan");
+    }
+    for (uint32_t i = 0; i < ncalls; ++i) pl->split[i] = descs[i].split ? 1 : 0;
+    pl->ws_bytes = ws_words * sizeof(uint32_t);
     if (ws_words) e = cudaMalloc(&pl->ws, ws_words * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_status, sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemset(pl->d_status, 0, sizeof(uint32_t));
@@ -884,11 +891,30 @@ he_status he_plan_run(he_plan_t plan, void *stream) {
 
 he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream) {
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
-    if (phase != 0 && phase != 1) return fail(HE_ERR_ARG, "phase must be 0 or 1");
+    if (phase < HE_PHASE_NTT || phase > HE_PHASE_FINISH) return fail(HE_ERR_ARG, "phase must be 0, 1, 2 or 3");
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
     cudaError_t e = he_launch_plan(*plan, (cudaStream_t)stream, phase);
     return e == cudaSuccess ? HE_OK : cuda_fail(e, "plan run phase");
+}
+
+he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
+    if (!plan || !info) return fail(HE_ERR_ARG, "NULL argument");
+    he_plan_info r{};
+    r.ntt_items = plan->n_ntt;
+    r.mac_items = plan->n_mac;
+    r.mac_ctas = plan->n_mac ? plan->mac_ctas : 0;
+    r.finish_items = plan->n_fin;
+    for (int c = 0; c < 4; ++c) r.fused_items += plan->n_chan[c];
+    r.fc_items = plan->n_fc;
+    r.kernels_per_run = (plan->n_ntt > 0) + (plan->n_mac > 0) + (plan->n_fin > 0) + (plan->n_fc > 0);
+    for (int c = 0; c < 4; ++c) r.kernels_per_run += plan->n_chan[c] > 0;
+    for (uint32_t i = 0; i < plan->ncalls; ++i) r.split_calls += plan->split[i];
+    r.workspace_bytes = plan->ws_bytes;
+    *info = r;
+    if (split)
+        for (uint32_t i = 0; i < plan->ncalls; ++i) split[i] = plan->split[i];
+    return HE_OK;
 }
 
 void he_plan_destroy(he_plan_t plan) {
@@ -907,6 +933,7 @@ void he_plan_destroy(he_plan_t plan) {
     if (plan->side) cudaStreamDestroy(plan->side);
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    delete[] plan->split;
     delete plan;
 }
 

@@ -195,7 +195,9 @@ struct he_plan_s {
     cudaEvent_t ev_fork, ev_join;
     size_t smem_ntt, smem_chan[4], smem_mac, smem_fin;
     uint32_t *ws;
+    size_t ws_bytes;
     uint32_t *d_status;                 // bit 0: a bounded wait in the MAC kernel gave up
+    uint8_t *split;                     // host: per call, 1 if it takes the split form
 };
 
 cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase);

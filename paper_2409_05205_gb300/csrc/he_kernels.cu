@@ -1088,7 +1088,9 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     cudaError_t e = cudaSuccess;
     // fused FC items: forked onto the plan's side stream with the channel
     // work, joined back before the last channel kernel's completion
-    const bool fc = pl.n_fc && phase != 0;
+    // phase: -1 whole run, 0 input NTTs, 1 everything after them, 2 the MAC
+    // kernel alone, 3 everything after the MAC kernel
+    const bool fc = pl.n_fc && (phase == -1 || phase == 1 || phase == 3);
     if (fc) {
         if ((e = cudaEventRecord(pl.ev_fork, st)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(pl.side, pl.ev_fork, 0)) != cudaSuccess) return e;
@@ -1096,7 +1098,7 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaEventRecord(pl.ev_join, pl.side)) != cudaSuccess) return e;
     }
-    if (pl.n_ntt && phase != 1) {
+    if (pl.n_ntt && (phase == -1 || phase == 0)) {
         e = set_smem(k_plan_ntt, pl.smem_ntt);
         if (e != cudaSuccess) return e;
         k_plan_ntt<<<pl.n_ntt, kThreads, pl.smem_ntt, st>>>(pl.d_calls, pl.d_ntt);
@@ -1112,11 +1114,12 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
             if (on) cudaStreamWaitEvent(st, pl.ev_join, 0);
         }
     } join{pl, st, fc};
-    if (pl.n_mac) {
+    if (pl.n_mac && phase != 3) {
         k_plan_mac<<<pl.mac_ctas, kThreads, pl.smem_mac, st>>>(pl.d_calls, pl.d_mac, pl.d_mac_copy, pl.d_mac_offs,
                                                                pl.d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
+    if (phase == 2) return cudaSuccess;
     if (pl.n_fin) {
         k_plan_fin<<<pl.n_fin, kFinThreads, pl.smem_fin, st>>>(pl.d_calls, pl.d_fin);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -22,6 +22,7 @@ HE_OUT_EXTRACTED, HE_OUT_PER_CHANNEL, HE_OUT_EXTRACTED_UNFOLDED = 0, 1, 2
 HE_MAX_LIMBS = 16
 HE_MAX_INTERLEAVE = 128
 HE_DEVICE_NONE = -1
+HE_PHASE_NTT, HE_PHASE_REST, HE_PHASE_MAC, HE_PHASE_FINISH = range(4)
 
 _STATUS = {0: "HE_OK", 1: "HE_ERR_ARG", 2: "HE_ERR_SHAPE", 3: "HE_ERR_UNSUPPORTED",
            4: "HE_ERR_NOMEM", 5: "HE_ERR_CUDA", 6: "HE_ERR_TIMEOUT"}
@@ -50,6 +51,12 @@ class he_layer_call(ctypes.Structure):
                 ("d_out", ctypes.c_void_p), ("B", ctypes.c_uint32)]
 
 
+class he_plan_info(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("kernels_per_run", "ntt_items", "mac_items", "mac_ctas",
+                                               "finish_items", "fused_items", "fc_items", "split_calls")] + \
+               [("workspace_bytes", ctypes.c_uint64)]
+
+
 _lib = None
 
 _vp, _u32, _i32, _sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
@@ -74,6 +81,7 @@ _SIGS = {
     "he_plan_create": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(_vp)],
     "he_plan_run": [_vp, _vp],
     "he_plan_run_phase": [_vp, _i32, _vp],
+    "he_plan_query": [_vp, ctypes.POINTER(he_plan_info), _vp],
     "he_plan_check": [_vp],
     "he_plan_destroy": [_vp],
     "he_sync": [_vp],
@@ -262,6 +270,18 @@ def he_plan_run(plan: int, stream=None) -> None:
 
 def he_plan_run_phase(plan: int, phase: int, stream=None) -> None:
     _check(lib().he_plan_run_phase(plan, phase, _stream(stream)))
+
+
+def he_plan_query(plan: int, ncalls: int | None = None) -> dict:
+    """The plan's he_plan_info as a dict; with ncalls, also "split": the
+    per-call split-form flags."""
+    info = he_plan_info()
+    sp = None if ncalls is None else np.zeros(ncalls, dtype=np.uint8)
+    _check(lib().he_plan_query(plan, ctypes.byref(info), None if sp is None else sp.ctypes.data))
+    out = {n: getattr(info, n) for n, _ in he_plan_info._fields_}
+    if sp is not None:
+        out["split"] = [bool(x) for x in sp]
+    return out
 
 
 def he_plan_check(plan: int) -> None:

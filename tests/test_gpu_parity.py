@@ -399,12 +399,28 @@ def test_plan_split_form_plain20_shapes_bit_exact():
         calls.append((f, U.to_dev(ct), H.HE_COEFF, U.empty_dev(ref.shape), 1))
         plan = H.he_plan_create(calls)
         try:
+            info = H.he_plan_query(plan, len(calls))
+            assert info["split"] == [True] * len(PLAIN20_SHAPES) + [False]
+            assert info["split_calls"] == len(PLAIN20_SHAPES)
+            assert info["kernels_per_run"] == 4        # NTT, MAC, finish, FC
+            assert info["fc_items"] > 0 and info["fused_items"] == 0
             s = torch.cuda.current_stream()
-            H.he_plan_run(plan, s)
-            H.he_sync(s)
-            H.he_plan_check(plan)
-            for c, ref in zip(calls, refs):
-                np.testing.assert_array_equal(U.from_dev(c[3]).reshape(ref.shape), ref)
+            # the whole run, then the same run in phases 0 + 1 and 0 + 2 + 3
+            for phases in (None, (H.HE_PHASE_NTT, H.HE_PHASE_REST),
+                           (H.HE_PHASE_NTT, H.HE_PHASE_MAC, H.HE_PHASE_FINISH)):
+                for c in calls:
+                    c[3].fill_(-1)
+                if phases is None:
+                    H.he_plan_run(plan, s)
+                else:
+                    for ph in phases:
+                        H.he_plan_run_phase(plan, ph, s)
+                H.he_sync(s)
+                H.he_plan_check(plan)
+                for c, ref in zip(calls, refs):
+                    np.testing.assert_array_equal(U.from_dev(c[3]).reshape(ref.shape), ref)
+            with pytest.raises(H.HEError):
+                H.he_plan_run_phase(plan, 4, s)
         finally:
             H.he_plan_destroy(plan)
             for f in banks:
