@@ -271,7 +271,7 @@ class Arm:
 # DRAM bytes (read + write) of one k_plan_mac launch, from an ncu capture of
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where no
 # capture of the current kernel exists.
-TRAFFIC = {"plain20_c10": 136560640 + 4797184}
+TRAFFIC = {}
 
 
 def _traffic(name):

@@ -636,7 +636,8 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
                            : 0u;
             g.cs = split_cs(lay.s, lay.G);
             g.nc = f->nc;
-            if (cd.split && (1u << f->lcs) != g.cs) cd.split = 0;  // bank interleave must match the MAC's
+            // bank interleave and tile must match the MAC kernel's
+            if (cd.split && ((1u << f->lcs) != g.cs || f->logTS != split_tile_log(f->lcs))) cd.split = 0;
             nin = (size_t)c.B * lay.G * 2u * r.L * r.N;
             nout = (size_t)c.B * lay.H * 2u * r.L * r.N;
         } else {
@@ -817,6 +818,7 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
         }
         offs[nctas] = (uint32_t)items.size();
         std::vector<MacCopy> copies;
+        std::vector<MacDesc> mdescs;
         for (const ChanItem &it : items) {
             const CallDesc &cd = descs[it.call];
             const ConvGeo &g = cd.g;
@@ -829,6 +831,21 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
             c.xrows = 2 * g.G;
             c.xwords = 1u << lt;
             copies.push_back(c);
+            MacDesc d{};
+            d.z = cd.z + ((size_t)it.l * 2u * g.co + it.b) * g.M + (((size_t)it.a << lt) >> g.logs);
+            d.colstride = g.co * g.M;
+            d.M = g.M;
+            d.nch = nc;
+            d.cls = (uint32_t)he_mac_class(g.G, g.cs);
+            d.logs = g.logs;
+            d.nst = (c.nwords + kMacStageWords - 1) / kMacStageWords;
+            const LimbK &K = cd.limb[it.l];
+            d.q = K.q;
+            d.q2 = K.q2;
+            d.r32 = K.r32;
+            d.r32s = K.r32s;
+            d.ones = K.ones;
+            mdescs.push_back(d);
         }
         pl->n_mac = (uint32_t)items.size();
         pl->mac_ctas = nctas;
@@ -838,6 +855,9 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
             e = cudaMalloc(&pl->d_mac_copy, sizeof(MacCopy) * copies.size());
             if (e == cudaSuccess)
                 e = cudaMemcpy(pl->d_mac_copy, copies.data(), sizeof(MacCopy) * copies.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&pl->d_mac_desc, sizeof(MacDesc) * mdescs.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(pl->d_mac_desc, mdescs.data(), sizeof(MacDesc) * mdescs.size(), cudaMemcpyHostToDevice);
         }
         if (e == cudaSuccess && nctas) {
             e = cudaMalloc(&pl->d_mac_offs, sizeof(uint32_t) * offs.size());
@@ -927,6 +947,7 @@ void he_plan_destroy(he_plan_t plan) {
     cudaFree(plan->d_mac);
     cudaFree(plan->d_mac_offs);
     cudaFree(plan->d_mac_copy);
+    cudaFree(plan->d_mac_desc);
     cudaFree(plan->d_fin);
     cudaFree(plan->d_status);
     cudaFree(plan->d_fc);

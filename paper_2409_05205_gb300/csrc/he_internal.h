@@ -98,12 +98,14 @@ __host__ __device__ __forceinline__ size_t bank_index(uint32_t n, uint32_t l, ui
 // {1, 2, 4}; then cs = min(4 / G, s / 4), so a thread's inputs are 8 uint4 and
 // a channel's products per column are at most 16.  Other layers use a
 // 512-slot tile.
-__host__ __device__ __forceinline__ bool split_mac_ok(uint32_t s, uint32_t G) {
-    return s >= 4 && (G == 1 || G == 2 || G == 4);
-}
 __host__ __device__ __forceinline__ uint32_t split_cs(uint32_t s, uint32_t G) {
     const uint32_t a = 4u / G, b = s / 4u;
     return a < b ? a : b;
+}
+// The s-slot block of one output value must lie within one warp's lanes
+// (s / (4 CS) <= 32) for the block sum.
+__host__ __device__ __forceinline__ bool split_mac_ok(uint32_t s, uint32_t G) {
+    return s >= 4 && (G == 1 || G == 2 || G == 4) && s <= 128u * split_cs(s, G);
 }
 // log2 of the chunk interleave of a bank: log2(split_cs) for split layers,
 // else 0 (no interleave); never more than the tile allows
@@ -147,9 +149,12 @@ __host__ __device__ __forceinline__ int he_mac_class(uint32_t G, uint32_t cs) {
 // split form: bulk-copy ring of the MAC kernel
 constexpr uint32_t kMacStageWords = 4096;   // 16 KB per stage
 constexpr uint32_t kMacStages = 5;
-constexpr uint32_t kMacHdrBytes = 64;       // mbarriers at the start of shared memory
+constexpr uint32_t kMacHdrBytes = 256;      // mbarriers (0..127) and two item descriptors (128..255)
 constexpr uint32_t kMacItemWords = 32768;   // weights per work item (128 KB)
 constexpr uint32_t kMacXWords = 4096;       // one input buffer: 2 columns x G*TS <= 2048 words
+// the split MAC kernel's slot tile: TS = 2^(9 + log2 CS) slots, so that its
+// 256 compute threads own 4*CS slots of one column each
+__host__ __device__ __forceinline__ constexpr uint32_t split_tile_log(uint32_t lcs) { return 9u + lcs; }
 
 // Copy descriptors of one MAC item, built on the host so the producer thread
 // issues bulk copies without walking the call table.
@@ -161,6 +166,21 @@ struct MacCopy {
     uint32_t xrows;          // 2 * G
     uint32_t xwords;         // words per input row (TS)
 };
+
+// What the compute warps need about one MAC item, built on the host and
+// copied into shared memory together with the item's inputs.
+struct alignas(16) MacDesc {
+    uint32_t *z;             // folded sums of the item's first channel, column 0, first slot block of the tile
+    uint32_t colstride;      // words between the two columns' planes of z (co * M)
+    uint32_t M;              // words between channels of z
+    uint32_t nch;            // channels in the item
+    uint32_t cls;            // he_mac_class(G, CS)
+    uint32_t logs;           // log2 s
+    uint32_t nst;            // weight stages of the item
+    uint32_t q, q2, r32, r32s, ones;  // limb constants
+    uint32_t pad[3];
+};
+static_assert(sizeof(MacDesc) == 64, "MacDesc is one 64-byte bulk copy");
 
 __host__ __device__ __forceinline__ size_t mac_smem_bytes() {
     return kMacHdrBytes + (size_t)2 * kMacXWords * 4u + (size_t)kMacStages * kMacStageWords * 4u;
@@ -187,6 +207,7 @@ struct he_plan_s {
     ChanItem *d_mac, *d_fin;
     uint32_t *d_mac_offs;               // persistent MAC CTAs: items of CTA b at [offs[b], offs[b+1])
     MacCopy *d_mac_copy;                // per item, same order as d_mac
+    MacDesc *d_mac_desc;                // per item, same order as d_mac
     uint32_t mac_ctas;
     uint32_t n_fc;                      // fused FC items, run on a side stream
     NttItem *d_fc;

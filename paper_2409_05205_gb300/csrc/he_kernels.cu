@@ -625,47 +625,100 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     return false;
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Persistent MAC kernel of the split form (one ciphertext per call:
 // columns c0, c1).  Each CTA owns a list of work items (call, limb l, slot
 // tile t of TS slots, channels n0 .. n0+nc-1), assigned longest first on the
-// host.  Thread 0 keeps one continuous bulk-copy stream of 16 KB weight
-// stages through a ring across the CTA's whole list -- the weights of an
-// item's channel range for its tile are one contiguous region of nc*G*TS
-// words in the tile-major bank -- and double-buffers each item's ciphertext
-// inputs (2 columns x G groups x TS slots).
-//
+// host.  Warp-specialized:
+//   * warp 8, lane 0 (producer) walks the list and keeps a 5-deep ring of
+//     16 KB weight stages filled with bulk copies -- the weights of an
+//     item's channel range for its tile are one contiguous region of
+//     nc*G*TS words in the tile-major bank -- and double-buffers each item's
+//     ciphertext inputs (2 columns x G groups x TS slots) together with the
+//     item's 64-byte descriptor;
+//   * warps 0..7 compute.  Stage b is guarded by full[b] (the copy landed)
+//     and empty[b] (all 8 compute warps are done with it); an input buffer by
+//     xfull / xempty.  There is no block-wide barrier after the start.
 // Thread (column jj, slot group c) owns the CS*4 consecutive slots
 // t*TS + 4*CS*c ..; its inputs for the item sit in registers.  With
 // G*CS <= 4 a channel adds at most 16 products of (q-1)^2 per column, so
-// one 64-bit accumulator per column needs a single reduction per channel.
+// two 64-bit accumulators per column need a single reduction per channel.
 // The per-thread sum covers CS*4 slots of one s-slot block; the block sum
 // (the valid-slot-only fold, see conv_fold_body) adds s/(4*CS) neighbouring
 // lanes and goes to the folded buffer z[l][jj][n][block].
-struct MacStream {        // thread 0's producer cursor
-    uint32_t k, st, issued;
-    MacCopy c;            // descriptor of item k (loaded when the cursor reaches it)
-};
-
-// thread 0: issue the next weight stage of the CTA's stream, if any
-__device__ __forceinline__ void mac_issue_next(MacStream &cur, uint32_t ie, const MacCopy *__restrict__ copies,
-                                               uint64_t *rbars, uint32_t *ring) {
-    if (cur.k >= ie) return;
-    if (cur.st == 0) cur.c = copies[cur.k];
-    const uint32_t w = min(kMacStageWords, cur.c.nwords - cur.st * kMacStageWords);
-    const uint32_t buf = cur.issued % kMacStages;
-    if (cur.issued >= kMacStages) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect(rbars + buf, w * 4u);
-    bulk_load(ring + buf * kMacStageWords, cur.c.w + (size_t)cur.st * kMacStageWords, w * 4u, rbars + buf);
-    ++cur.issued;
-    if ((++cur.st) * kMacStageWords >= cur.c.nwords) {
-        cur.st = 0;
-        ++cur.k;
+template <int G, int CS>
+__device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, uint64_t *xempty,
+                                         const uint32_t *ring, uint64_t *full, uint64_t *empty, uint32_t &buf,
+                                         uint32_t &ph) {
+    constexpr uint32_t LT = split_tile_log(CS == 4 ? 2 : (CS == 2 ? 1 : 0));
+    constexpr uint32_t ROWS = kMacStageWords >> LT;  // weight rows of TS words per stage
+    constexpr uint32_t NCH = ROWS / G;               // channels per full stage
+    static_assert(NCH >= 1 && NCH * G == ROWS, "a stage holds whole channels");
+    const uint32_t tid = threadIdx.x, lane = tid & 31u;
+    const uint32_t jj = tid >> 7, c = tid & 127u;  // 128 slot groups per column
+    uint4 x[G][CS];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int u = 0; u < CS; ++u)
+            x[g][u] = *reinterpret_cast<const uint4 *>(X + ((jj * G + g) << LT) + 4u * CS * c + 4u * u);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(xempty);  // the producer may refill this input buffer
+    LimbK K;
+    K.q = d.q;
+    K.q2 = d.q2;
+    K.r32 = d.r32;
+    K.r32s = d.r32s;
+    K.ones = d.ones;
+    uint32_t *zc = d.z + jj * d.colstride + ((4u * CS * c) >> d.logs);
+    const uint32_t M = d.M, nch = d.nch, nst = d.nst;
+    const uint32_t lanes = max(1u, (1u << d.logs) / (4u * CS));  // threads whose sums make one block
+    const bool lead = (lane & (lanes - 1u)) == 0;
+    uint32_t n = 0;
+    for (uint32_t st = 0; st < nst; ++st, n += NCH) {
+        if (!mbar_wait(full + buf, ph)) return false;
+        // the bank interleaves chunks: this thread's u-th chunk is uint4 u*128 + c
+        const uint32_t *W = ring + buf * kMacStageWords + 4u * c;
+#pragma unroll
+        for (uint32_t ch = 0; ch < NCH; ++ch) {
+            if (n + ch < nch) {  // the item's last stage may hold fewer channels
+                uint64_t a0 = 0, a1 = 0;
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int u = 0; u < CS; ++u) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(W + ((ch * G + g) << LT) + ((uint32_t)u << 9));
+                        a0 += (uint64_t)w.x * x[g][u].x;
+                        a1 += (uint64_t)w.y * x[g][u].y;
+                        a0 += (uint64_t)w.z * x[g][u].z;
+                        a1 += (uint64_t)w.w * x[g][u].w;
+                    }
+                uint32_t v = reduce64(a0 + a1, K);
+                for (uint32_t o = 1; o < lanes; o <<= 1) {
+                    v += __shfl_xor_sync(0xffffffffu, v, o);
+                    v = min(v, v - K.q);
+                }
+                if (lead) zc[(size_t)(n + ch) * M] = v;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + buf);
+        if (++buf == kMacStages) {
+            buf = 0;
+            ph ^= 1u;
+        }
     }
+    return true;
 }
 
-// thread 0: an item's ciphertext inputs into input buffer X
-__device__ __forceinline__ void mac_issue_inputs(const MacCopy &c, uint32_t *X, uint64_t *xbar) {
-    mbar_expect(xbar, c.xrows * c.xwords * 4u);
+// producer: the item's descriptor and ciphertext inputs into buffer xb
+__device__ __forceinline__ void mac_issue_inputs(const MacCopy &c, const MacDesc *desc, MacDesc *dslot, uint32_t *X,
+                                                 uint64_t *xbar) {
+    mbar_expect(xbar, c.xrows * c.xwords * 4u + (uint32_t)sizeof(MacDesc));
+    bulk_load(dslot, desc, (uint32_t)sizeof(MacDesc), xbar);
     for (uint32_t r = 0; r < c.xrows; ++r) {
         // buffer row order [jj][g]: input row (g, jj) = 2g + jj
         const uint32_t g = r >> 1, jj = r & 1u;
@@ -673,134 +726,103 @@ __device__ __forceinline__ void mac_issue_inputs(const MacCopy &c, uint32_t *X, 
     }
 }
 
-template <int G, int CS>
-__device__ __forceinline__ bool mac_item(const CallDesc &cd, const ChanItem it, const uint32_t *X, uint32_t *ring,
-                                         uint64_t *rbars, uint32_t &gs, MacStream &cur, uint32_t ie,
-                                         const MacCopy *__restrict__ copies) {
-    constexpr int NJ = 2;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u;
-    const uint32_t t = it.a, l = it.l, n0 = it.b;
-    const uint32_t co = cd.g.co, lt = cd.g.logTS, logs = cd.g.logs, s = cd.g.s, M = cd.g.M;
-    const uint32_t nc = min(cd.g.nc, co - n0);
-    const LimbK K = cd.limb[l];
-    const uint32_t lanes = max(1u, s / (4u * CS));                     // threads whose sums make one block
-    const uint32_t lgr = lt - 2 - (CS == 4 ? 2 : (CS == 2 ? 1 : 0));  // log2 slot groups per column
-    const uint32_t jj = tid >> lgr, c = tid & ((1u << lgr) - 1u);
-    const bool act = jj < NJ;
-    const uint32_t so = 4u * CS * c;                                   // first slot within the tile
-    uint4 x[G][CS];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-#pragma unroll
-        for (int u = 0; u < CS; ++u)
-            x[g][u] = act ? *reinterpret_cast<const uint4 *>(X + (((jj & 1u) * G + g) << lt) + so + 4u * u)
-                          : make_uint4(0, 0, 0, 0);
-    uint32_t *zc = cd.z + ((size_t)(l * NJ + (jj & 1u)) * co) * M + (((t << lt) + so) >> logs);
-    const uint32_t nwords = (nc * G) << lt;
-    const uint32_t nst = (nwords + kMacStageWords - 1) / kMacStageWords;
-    const uint32_t chps = kMacStageWords >> lt;  // weight rows per stage
-    uint32_t n = n0;
-    for (uint32_t st = 0; st < nst; ++st, ++gs) {
-        const uint32_t buf = gs % kMacStages;
-        // one barrier per stage: it publishes the wait's outcome and tells
-        // thread 0 that every thread is done with the previous stage's buffer
-        if (!__syncthreads_and(mbar_wait(rbars + buf, (gs / kMacStages) & 1u))) return false;
-        if (tid == 0 && gs > 0) mac_issue_next(cur, ie, copies, rbars, ring);
-        // the bank interleaves chunks: this thread's u-th chunk is uint4 u*NG + c
-        const uint32_t *Wst = ring + buf * kMacStageWords + 4u * c;
-        const uint32_t rows = min(chps, nc * G - st * chps);
-        for (uint32_t r0 = 0; r0 < rows; r0 += G, ++n) {
-            // at most 16 products per column per channel: four independent
-            // chains, summed without overflow
-            uint64_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-#pragma unroll
-            for (int g = 0; g < G; ++g)
-#pragma unroll
-                for (int u = 0; u < CS; ++u) {
-                    const uint4 w =
-                        *reinterpret_cast<const uint4 *>(Wst + ((r0 + g) << lt) + ((uint32_t)u << (lgr + 2)));
-                    a0 += (uint64_t)w.x * x[g][u].x;
-                    a1 += (uint64_t)w.y * x[g][u].y;
-                    a2 += (uint64_t)w.z * x[g][u].z;
-                    a3 += (uint64_t)w.w * x[g][u].w;
-                }
-            uint32_t v = reduce64((a0 + a1) + (a2 + a3), K);
-            for (uint32_t o = 1; o < lanes; o <<= 1) {
-                v += __shfl_xor_sync(0xffffffffu, v, o);
-                v = min(v, v - K.q);
-            }
-            if (act && (lane & (lanes - 1)) == 0) zc[(size_t)n * M] = v;
-        }
-    }
-    return true;
-}
-
-__global__ void __launch_bounds__(kThreads, 2) k_plan_mac(const CallDesc *__restrict__ calls,
-                                                         const ChanItem *__restrict__ items,
-                                                         const MacCopy *__restrict__ copies,
-                                                         const uint32_t *__restrict__ offs,
-                                                         uint32_t *__restrict__ status) {
+__global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__restrict__ copies,
+                                                              const MacDesc *__restrict__ descs,
+                                                              const uint32_t *__restrict__ offs,
+                                                              uint32_t *__restrict__ status) {
     extern __shared__ uint4 smem4[];
-    uint64_t *xbars = reinterpret_cast<uint64_t *>(smem4);  // [2] input buffers
-    uint64_t *rbars = xbars + 2;                             // [kMacStages] ring
+    uint64_t *xfull = reinterpret_cast<uint64_t *>(smem4);  // [2]
+    uint64_t *xempty = xfull + 2;                            // [2]
+    uint64_t *full = xempty + 2;                             // [kMacStages]
+    uint64_t *empty = full + kMacStages;                     // [kMacStages]
+    MacDesc *dslot = reinterpret_cast<MacDesc *>(reinterpret_cast<char *>(smem4) + 128);  // [2]
     uint32_t *Xb = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(smem4) + kMacHdrBytes);
     uint32_t *ring = Xb + 2 * kMacXWords;
+    constexpr uint32_t kWarps = kThreads / 32;  // compute warps
     const uint32_t ib = offs[blockIdx.x], ie = offs[blockIdx.x + 1];
     const uint32_t tid = threadIdx.x;
     if (ib >= ie) return;
     if (tid == 0) {
-        for (uint32_t i = 0; i < 2 + kMacStages; ++i) mbar_init(xbars + i, 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(xfull + i, 1);
+            mbar_init(xempty + i, kWarps);
+        }
+        for (uint32_t i = 0; i < kMacStages; ++i) {
+            mbar_init(full + i, 1);
+            mbar_init(empty + i, kWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    MacStream cur;
-    cur.k = ib;
-    cur.st = 0;
-    cur.issued = 0;
-    uint32_t xissued = 0;  // input buffers issued (thread 0)
-    if (tid == 0) {
-        for (uint32_t k = ib; k < ie && k < ib + 2; ++k) {
-            mac_issue_inputs(copies[k], Xb + (k - ib) * kMacXWords, xbars + (k - ib));
-            ++xissued;
+    if (tid >= kThreads) {
+        if (tid != kThreads) return;
+        // ---- producer
+        bool ok = true;
+        uint32_t issued = 0, xiss = 0;
+        for (uint32_t k = ib; k < ie && k < ib + 2; ++k, ++xiss)
+            mac_issue_inputs(copies[k], descs + k, dslot + (xiss & 1u), Xb + (xiss & 1u) * kMacXWords,
+                             xfull + (xiss & 1u));
+        MacCopy c = copies[ib];
+        for (uint32_t k = ib; ok && k < ie; ++k) {
+            MacCopy cn;
+            if (k + 1 < ie) cn = copies[k + 1];  // in flight while this item's stages go out
+            const uint32_t nst = (c.nwords + kMacStageWords - 1) / kMacStageWords;
+            for (uint32_t st = 0; st < nst; ++st, ++issued) {
+                const uint32_t b = issued % kMacStages;
+                if (issued >= kMacStages) {
+                    if (!mbar_wait(empty + b, ((issued / kMacStages) - 1u) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                }
+                const uint32_t w = min(kMacStageWords, c.nwords - st * kMacStageWords);
+                mbar_expect(full + b, w * 4u);
+                bulk_load(ring + b * kMacStageWords, c.w + (size_t)st * kMacStageWords, w * 4u, full + b);
+            }
+            // inputs of item k + 2 once the compute warps hold item k's in registers
+            if (ok && k + 2 < ie) {
+                const uint32_t xb = xiss & 1u;
+                if (!mbar_wait(xempty + xb, ((xiss >> 1) - 1u) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mac_issue_inputs(copies[k + 2], descs + k + 2, dslot + xb, Xb + xb * kMacXWords, xfull + xb);
+                ++xiss;
+            }
+            c = cn;
         }
-        for (uint32_t i = 0; i < kMacStages; ++i) mac_issue_next(cur, ie, copies, rbars, ring);
+        if (!ok) atomicOr(status, 1u);
+        // every copy lands before the CTA's shared memory is released; only
+        // the last two input loads and the last kMacStages stages can still
+        // be in flight (an older phase of a barrier must not be waited for)
+        for (uint32_t i = xiss > 2 ? xiss - 2 : 0; i < xiss; ++i) mbar_wait(xfull + (i & 1u), (i >> 1) & 1u);
+        for (uint32_t i = issued > kMacStages ? issued - kMacStages : 0; i < issued; ++i)
+            mbar_wait(full + i % kMacStages, (i / kMacStages) & 1u);
+        return;
     }
-    uint32_t gs = 0;   // weight stages consumed
+    // ---- compute warps
+    uint32_t buf = 0, ph = 0;
     bool ok = true;
     for (uint32_t k = ib; ok && k < ie; ++k) {
-        const ChanItem it = items[k];
-        const CallDesc &cd = calls[it.call];
         const uint32_t xb = (k - ib) & 1u;
-        ok = __syncthreads_and(mbar_wait(xbars + xb, ((k - ib) >> 1) & 1u)) != 0;
-        if (!ok) break;
+        if (!mbar_wait(xfull + xb, ((k - ib) >> 1) & 1u)) {
+            ok = false;
+            break;
+        }
+        const MacDesc d = dslot[xb];
         const uint32_t *X = Xb + xb * kMacXWords;
-        switch (he_mac_class(cd.g.G, cd.g.cs)) {
-            case 0: ok = mac_item<1, 1>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
-            case 1: ok = mac_item<1, 2>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
-            case 2: ok = mac_item<1, 4>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
-            case 3: ok = mac_item<2, 1>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
-            case 4: ok = mac_item<2, 2>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
-            default: ok = mac_item<4, 1>(cd, it, X, ring, rbars, gs, cur, ie, copies); break;
-        }
-        // every thread read item k's inputs into registers and has passed a
-        // barrier inside mac_item since (items have >= 1 stage), so buffer
-        // xb is free
-        if (ok && tid == 0 && k + 2 < ie) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mac_issue_inputs(copies[k + 2], Xb + xb * kMacXWords, xbars + xb);
-            ++xissued;
+        switch (d.cls) {
+            case 0: ok = mac_item<1, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
+            case 1: ok = mac_item<1, 2>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
+            case 2: ok = mac_item<1, 4>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
+            case 3: ok = mac_item<2, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
+            case 4: ok = mac_item<2, 2>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
+            default: ok = mac_item<4, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
         }
     }
-    if (!ok) {
-        // a wait gave up: report, then give every copy this CTA issued a
-        // bounded chance to land before its shared memory is released
-        if (tid == 0) {
-            atomicOr(status, 1u);
-            for (uint32_t i = 0; i < xissued; ++i) mbar_wait(xbars + (i & 1u), (i >> 1) & 1u);
-            for (uint32_t i = gs; i < cur.issued; ++i) mbar_wait(rbars + i % kMacStages, (i / kMacStages) & 1u);
-        }
-        __syncthreads();
-    }
+    if (!ok) atomicOr(status, 1u);
 }
 
 // Finishing kernel: items (call, h, l, column) run the length-M inverse
@@ -1115,8 +1137,8 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         }
     } join{pl, st, fc};
     if (pl.n_mac && phase != 3) {
-        k_plan_mac<<<pl.mac_ctas, kThreads, pl.smem_mac, st>>>(pl.d_calls, pl.d_mac, pl.d_mac_copy, pl.d_mac_offs,
-                                                               pl.d_status);
+        k_plan_mac<<<pl.mac_ctas, kThreads + 32, pl.smem_mac, st>>>(pl.d_mac_copy, pl.d_mac_desc, pl.d_mac_offs,
+                                                                    pl.d_status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (phase == 2) return cudaSuccess;
