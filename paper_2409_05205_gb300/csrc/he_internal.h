@@ -149,7 +149,10 @@ __host__ __device__ __forceinline__ int he_mac_class(uint32_t G, uint32_t cs) {
 // split form: bulk-copy ring of the MAC kernel
 constexpr uint32_t kMacStageWords = 4096;   // 16 KB per stage
 constexpr uint32_t kMacStages = 5;
-constexpr uint32_t kMacHdrBytes = 256;      // mbarriers (0..127) and two item descriptors (128..255)
+// shared-memory header: mbarriers xfull[2], xempty[2], full[S], empty[S],
+// then two 64-byte item descriptors
+constexpr uint32_t kMacBarBytes = ((4u + 2u * kMacStages) * 8u + 15u) / 16u * 16u;
+constexpr uint32_t kMacHdrBytes = kMacBarBytes + 128u;
 constexpr uint32_t kMacItemWords = 32768;   // weights per work item (128 KB)
 constexpr uint32_t kMacXWords = 4096;       // one input buffer: 2 columns x G*TS <= 2048 words
 // the split MAC kernel's slot tile: TS = 2^(9 + log2 CS) slots, so that its

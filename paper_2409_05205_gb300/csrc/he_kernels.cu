@@ -24,6 +24,15 @@
 
 #include "he_internal.h"
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the kernel before it finishes; pdl_wait()
+// blocks until that kernel has completed and its writes are visible.
+// pdl_trigger() lets the next such kernel start launching.  Both are no-ops
+// for a kernel launched the ordinary way.  Used between the input-NTT kernel
+// and the MAC kernel, whose weight stream does not depend on it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __noinline__ void ntt_fwd_c(const uint32_t *src, uint32_t *dst, uint32_t *sm, uint32_t logN,
                                        const uint2 *__restrict__ tw, uint32_t q) {
     switch (logN) {
@@ -537,6 +546,7 @@ __global__ void __launch_bounds__(kThreads) k_fc(const ConvGeo a, const RingView
 __global__ void __launch_bounds__(kThreads, 3) k_plan_ntt(const CallDesc *__restrict__ calls,
                                                       const NttItem *__restrict__ items) {
     extern __shared__ uint4 smem4[];
+    pdl_trigger();  // the MAC kernel may start streaming weights now
     const NttItem it = items[blockIdx.x];
     const CallDesc &cd = calls[it.call];
     const uint32_t N = cd.g.N, L = cd.g.L;
@@ -735,7 +745,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
     uint64_t *xempty = xfull + 2;                            // [2]
     uint64_t *full = xempty + 2;                             // [kMacStages]
     uint64_t *empty = full + kMacStages;                     // [kMacStages]
-    MacDesc *dslot = reinterpret_cast<MacDesc *>(reinterpret_cast<char *>(smem4) + 128);  // [2]
+    MacDesc *dslot = reinterpret_cast<MacDesc *>(reinterpret_cast<char *>(smem4) + kMacBarBytes);  // [2]
     uint32_t *Xb = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(smem4) + kMacHdrBytes);
     uint32_t *ring = Xb + 2 * kMacXWords;
     constexpr uint32_t kWarps = kThreads / 32;  // compute warps
@@ -759,15 +769,24 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
         // ---- producer
         bool ok = true;
         uint32_t issued = 0, xiss = 0;
+        MacCopy c = copies[ib];
+        // the weights do not depend on the input-NTT kernel: the first ring
+        // stages go out before waiting for it
+        uint32_t st0 = min(kMacStages, (c.nwords + kMacStageWords - 1) / kMacStageWords);
+        for (uint32_t st = 0; st < st0; ++st, ++issued) {
+            const uint32_t w = min(kMacStageWords, c.nwords - st * kMacStageWords);
+            mbar_expect(full + st, w * 4u);
+            bulk_load(ring + st * kMacStageWords, c.w + (size_t)st * kMacStageWords, w * 4u, full + st);
+        }
+        pdl_wait();
         for (uint32_t k = ib; k < ie && k < ib + 2; ++k, ++xiss)
             mac_issue_inputs(copies[k], descs + k, dslot + (xiss & 1u), Xb + (xiss & 1u) * kMacXWords,
                              xfull + (xiss & 1u));
-        MacCopy c = copies[ib];
         for (uint32_t k = ib; ok && k < ie; ++k) {
             MacCopy cn;
             if (k + 1 < ie) cn = copies[k + 1];  // in flight while this item's stages go out
             const uint32_t nst = (c.nwords + kMacStageWords - 1) / kMacStageWords;
-            for (uint32_t st = 0; st < nst; ++st, ++issued) {
+            for (uint32_t st = (k == ib ? st0 : 0u); st < nst; ++st, ++issued) {
                 const uint32_t b = issued % kMacStages;
                 if (issued >= kMacStages) {
                     if (!mbar_wait(empty + b, ((issued / kMacStages) - 1u) & 1u)) {
@@ -802,7 +821,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
             mbar_wait(full + i % kMacStages, (i / kMacStages) & 1u);
         return;
     }
-    // ---- compute warps
+    // ---- compute warps: blocked (not polling) until the input-NTT kernel is done
+    pdl_wait();
     uint32_t buf = 0, ph = 0;
     bool ok = true;
     for (uint32_t k = ib; ok && k < ie; ++k) {
@@ -1106,6 +1126,25 @@ cudaError_t he_plan_prepare(const he_plan_s &pl) {
 }
 
 // phase: -1 = both, 0 = input NTTs only, 1 = channel kernels only.
+// Launches `kern` so that it may start before the previous kernel on `st`
+// completes (programmatic dependent launch; the kernel calls pdl_wait()
+// before it reads what that kernel wrote).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), uint32_t grid, uint32_t block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     cudaError_t e = cudaSuccess;
     // fused FC items: forked onto the plan's side stream with the channel
@@ -1137,12 +1176,13 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         }
     } join{pl, st, fc};
     if (pl.n_mac && phase != 3) {
-        k_plan_mac<<<pl.mac_ctas, kThreads + 32, pl.smem_mac, st>>>(pl.d_mac_copy, pl.d_mac_desc, pl.d_mac_offs,
-                                                                    pl.d_status);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = launch_pdl(k_plan_mac, pl.mac_ctas, kThreads + 32, pl.smem_mac, st, (const MacCopy *)pl.d_mac_copy,
+                       (const MacDesc *)pl.d_mac_desc, (const uint32_t *)pl.d_mac_offs, pl.d_status);
+        if (e != cudaSuccess) return e;
     }
     if (phase == 2) return cudaSuccess;
     if (pl.n_fin) {
+        // an ordinary launch: started early, its blocks only wait (measured slower)
         k_plan_fin<<<pl.n_fin, kFinThreads, pl.smem_fin, st>>>(pl.d_calls, pl.d_fin);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
