@@ -67,13 +67,6 @@ def workload(name: str):
     return wl
 
 
-def layer_list(wl):
-    out = [dict(kind="conv", **d) for d in wl["conv"]]
-    if wl["fc"]:
-        out.append(dict(kind="fc", **wl["fc"]))
-    return out
-
-
 # ----------------------------------------------------------------------------
 # clocks
 # ----------------------------------------------------------------------------
@@ -130,20 +123,22 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 
 class Model:
-    """One replica of the network's packed banks (device-resident)."""
+    """One replica of the workload's packed banks (device-resident)."""
 
-    def __init__(self, H, p, wl, layers, rep):
+    def __init__(self, H, arm, rep):
         from paper_2409_05205_gb300 import synth
+        wl = arm.wl
         self.H = H
         self.banks = []
-        for i, Ld in enumerate(layers):
-            if Ld["kind"] == "conv":
-                F = synth.conv_weights(SEED + rep, f"w{i}", Ld["co"], Ld["ci"], 3, 3, wl["wlo"], wl["whi"])
-                self.banks.append(H.he_pack_filters(p, Ld, F))
+        for i, c in enumerate(arm.calls):
+            p = arm.params[(c["N"], c["L"])]
+            if c["kind"] == "conv":
+                F = synth.conv_weights(SEED + rep, f"w{i}", c["co"], c["ci"], 3, 3, wl["wlo"], wl["whi"])
+                self.banks.append(H.he_pack_filters(p, c, F))
             else:
-                W = synth.fc_weights(SEED + rep, f"w{i}", Ld["n_out"], Ld["n_in"], wl["wlo"], wl["whi"])
-                Bv = synth.ints(SEED + rep, f"b{i}", (Ld["n_out"],), -1000, 1000)
-                self.banks.append(H.he_pack_fc(p, Ld["n_in"], Ld["n_out"], W, Bv))
+                W = synth.fc_weights(SEED + rep, f"w{i}", c["n_out"], c["n_in"], wl["wlo"], wl["whi"])
+                Bv = synth.ints(SEED + rep, f"b{i}", (c["n_out"],), -1000, 1000)
+                self.banks.append(H.he_pack_fc(p, c["n_in"], c["n_out"], W, Bv))
 
     def free(self):
         for f in self.banks:
@@ -159,33 +154,33 @@ class Arm:
         build.build()
         self.torch, self.H = torch, H
         self.wl = wl
-        self.N, self.L, self.B = wl["N"], wl["L"], wl["B"]
-        self.layers = layer_list(wl)
-        self.p = H.he_params_create(self.N, self.L, None, wl["t"], device)
-        ps = H.he_params_primes(self.p, self.L)
-        N, L, B = self.N, self.L, self.B
-        # per-layer geometry
+        self.calls = synth.call_list(wl)
+        self.params, primes = {}, {}
+        for c in self.calls:
+            key = (c["N"], c["L"])
+            if key not in self.params:
+                self.params[key] = H.he_params_create(c["N"], c["L"], None, wl["t"], device)
+                primes[key] = H.he_params_primes(self.params[key], c["L"])
+        # per-call geometry
         self.geo = []
-        for Ld in self.layers:
-            if Ld["kind"] == "conv":
-                lay = H.he_conv_layout_query(self.p, Ld)
-                nin = B * lay["G"] * 2 * L * N
-                nout = B * lay["H"] * 2 * L * N
-                wbytes = Ld["co"] * lay["G"] * L * N * 4
-                self.geo.append(dict(lay=lay, nin=nin, nout=nout, npoly=B * lay["G"] * 2,
-                                     wbytes=wbytes))
+        for c in self.calls:
+            p, N, L, B = self.params[(c["N"], c["L"])], c["N"], c["L"], c["B"]
+            if c["kind"] == "conv":
+                lay = H.he_conv_layout_query(p, c)
+                self.geo.append(dict(lay=lay, nin=B * lay["G"] * 2 * L * N, nout=B * lay["H"] * 2 * L * N,
+                                     npoly=B * lay["G"] * 2, wbytes=c["co"] * lay["G"] * L * N * 4))
             else:
-                fl = H.he_fc_layout_query(self.p, Ld["n_in"], Ld["n_out"])
+                fl = H.he_fc_layout_query(p, c["n_in"], c["n_out"])
                 self.geo.append(dict(lay=fl, nin=B * 2 * L * N, nout=B * fl["P_fc"] * 2 * L * N,
                                      npoly=B * 2, wbytes=fl["P_fc"] * L * N * 4))
-        self.models = [Model(H, self.p, wl, self.layers, r) for r in range(replicas)]
+        self.models = [Model(H, self, r) for r in range(replicas)]
         # inputs / NTT buffers / outputs per replica (device resident)
         self.x, self.xn, self.y = [], [], []
         for r in range(replicas):
             xs, xns, ys = [], [], []
-            for i, g in enumerate(self.geo):
-                shape = (g["nin"] // (L * N), L, N)
-                a = synth.residues(SEED + 10 * r, f"x{i}", shape, ps)
+            for i, (c, g) in enumerate(zip(self.calls, self.geo)):
+                N, L = c["N"], c["L"]
+                a = synth.residues(SEED + 10 * r, f"x{i}", (g["nin"] // (L * N), L, N), primes[(N, L)])
                 xs.append(torch.from_numpy(a.view(np.int32).ravel()).cuda())
                 xns.append(torch.empty(g["nin"], dtype=torch.int32, device="cuda"))
                 ys.append(torch.empty(g["nout"], dtype=torch.int32, device="cuda"))
@@ -193,40 +188,58 @@ class Arm:
             self.xn.append(xns)
             self.y.append(ys)
         self.R = replicas
+        # layers per step: one per call and ciphertext of the batch
+        self.units = sum(c["B"] for c in self.calls)
         torch.cuda.synchronize()
+
+    def describe(self):
+        """The workload's ring(s) and batch size(s) for the JSON line."""
+        rings = sorted({(c["N"], c["L"]) for c in self.calls})
+        Bs = sorted({c["B"] for c in self.calls})
+        d = {"calls_per_step": len(self.calls), "layers_per_step": self.units, "t": self.wl["t"]}
+        if len(rings) == 1:
+            d.update(N=rings[0][0], L=rings[0][1])
+        else:
+            d["rings"] = [f"N={n},L={l}" for n, l in rings]
+        d["B"] = Bs[0] if len(Bs) == 1 else Bs
+        return d
 
     # one layer: input NTT (K1) then the channel kernel (K2 / K4) on NTT input
     def _layer(self, r, i, stream, ev=None):
         H = self.H
-        g, Ld = self.geo[i], self.layers[i]
+        c, g = self.calls[i], self.geo[i]
+        p = self.params[(c["N"], c["L"])]
         if ev is not None:
             ev[0].record(stream)
-        H.he_ntt_forward(self.p, self.x[r][i], self.xn[r][i], g["npoly"], stream)
+        H.he_ntt_forward(p, self.x[r][i], self.xn[r][i], g["npoly"], stream)
         if ev is not None:
             ev[1].record(stream)
-        if Ld["kind"] == "conv":
-            H.he_conv_layer(self.p, self.models[r].banks[i], self.xn[r][i], H.HE_NTT, self.y[r][i],
-                            H.HE_OUT_EXTRACTED, self.B, stream)
+        if c["kind"] == "conv":
+            H.he_conv_layer(p, self.models[r].banks[i], self.xn[r][i], H.HE_NTT, self.y[r][i],
+                            H.HE_OUT_EXTRACTED, c["B"], stream)
         else:
-            H.he_fc_layer(self.p, self.models[r].banks[i], self.xn[r][i], H.HE_NTT, self.y[r][i],
-                          H.HE_OUT_EXTRACTED, self.B, stream)
+            H.he_fc_layer(p, self.models[r].banks[i], self.xn[r][i], H.HE_NTT, self.y[r][i],
+                          H.HE_OUT_EXTRACTED, c["B"], stream)
         if ev is not None:
             ev[2].record(stream)
 
     def step_plain(self, k, stream, evs=None):
         r = k % self.R
-        for i in range(len(self.layers)):
+        for i in range(len(self.calls)):
             self._layer(r, i, stream, None if evs is None else evs[i])
 
     def make_plans(self):
         """One plan per replica over all layer calls, and a CUDA graph of each."""
         torch, H = self.torch, self.H
         self.plans, self.graphs = [], []
-        for r in range(self.R):
-            calls = [(self.models[r].banks[i], self.x[r][i], H.HE_COEFF, self.y[r][i], self.B)
-                     for i in range(len(self.layers))]
-            self.plans.append(H.he_plan_create(calls))
         s = torch.cuda.Stream()
+        for r in range(self.R):
+            calls = [(self.models[r].banks[i], self.x[r][i], H.HE_COEFF, self.y[r][i], c["B"])
+                     for i, c in enumerate(self.calls)]
+            # autotuned once (replicas share the signature, so 1 and 2 reuse it)
+            pl, self.tuning = H.he_plan_autotune(calls, 30, s)
+            self.plans.append(pl)
+        torch.cuda.synchronize()
         for r in range(self.R):
             with torch.cuda.stream(s):
                 H.he_plan_run(self.plans[r], s)          # warm-up outside capture
@@ -238,26 +251,25 @@ class Arm:
         torch.cuda.synchronize()
 
     def algorithmic(self):
-        """Algorithmic bytes per inference of the channel kernels and of the
-        input NTTs (read + write), and the NTT butterfly count."""
-        N, L, B = self.N, self.L, self.B
+        """Algorithmic bytes per step of the whole path (weights, inputs and
+        extracted outputs, each once), of the input NTTs (read + write), and
+        the NTT butterfly count."""
         ch_bytes, ntt_bytes, bfly = 0, 0, 0
-        logN = N.bit_length() - 1
-        for g, Ld in zip(self.geo, self.layers):
+        for c, g in zip(self.calls, self.geo):
+            N, L = c["N"], c["L"]
             ch_bytes += g["wbytes"] + (g["nin"] + g["nout"]) * 4
             ntt_bytes += 2 * g["nin"] * 4
-            bfly += g["npoly"] * L * (N // 2) * logN
+            bfly += g["npoly"] * L * (N // 2) * (N.bit_length() - 1)
         return ch_bytes, ntt_bytes, bfly
 
     def mac_bytes(self, split):
         """Algorithmic bytes of one k_plan_mac launch: for every split-form
         Conv call, its NTT-domain weight bank (co * G * L * N words) and its
         transformed inputs (B * G * 2 * L * N words), each read once."""
-        N, L, B = self.N, self.L, self.B
         tot = 0
-        for g, Ld, sp in zip(self.geo, self.layers, split):
-            if sp and Ld["kind"] == "conv":
-                tot += g["wbytes"] + B * g["lay"]["G"] * 2 * L * N * 4
+        for c, g, sp in zip(self.calls, self.geo, split):
+            if sp and c["kind"] == "conv":
+                tot += g["wbytes"] + c["B"] * g["lay"]["G"] * 2 * c["L"] * c["N"] * 4
         return tot
 
     def free(self):
@@ -265,7 +277,8 @@ class Arm:
             self.H.he_plan_destroy(pl)
         for m in self.models:
             m.free()
-        self.H.he_params_destroy(self.p)
+        for p in self.params.values():
+            self.H.he_params_destroy(p)
 
 
 # DRAM bytes (read + write) of one k_plan_mac launch, from an ncu capture of
@@ -288,7 +301,7 @@ def run_ours(args, rank, world, device):
     wl = workload(args.workload)
     arm = Arm(wl, device)
     H = arm.H
-    nl = len(arm.layers)
+    nl = len(arm.calls)
     stream = torch.cuda.Stream()
     K, W = args.steps, args.warmup
     k_plain, k_phase = min(K, 200), min(K, 500)
@@ -406,19 +419,18 @@ def run_ours(args, rank, world, device):
     mac_gbs = mac_bytes / (mac_avg * 1e-3) / 1e9
     traffic = _traffic(wl["name"])
     res = {
-        "metric": METRIC, "value": nl * K * world / (graph_ms * 1e-3), "unit": "layers/s",
+        "metric": METRIC, "value": arm.units * K * world / (graph_ms * 1e-3), "unit": "layers/s",
         "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": graph_ms / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u32 (exact residues mod 30-bit primes)", "data": "synthetic",
-        "config": {"workload": wl["name"], "N": arm.N, "L": arm.L, "B": arm.B, "t": wl["t"],
-                   "layers_per_step": nl,
+        "config": {"workload": wl["name"], **arm.describe(),
                    "form": f"plan of {nl} layer calls ({info['kernels_per_run']} kernels) replayed as a CUDA graph",
                    "l2": "rotates 3 model replicas + 3 input sets (> 2x L2); no flush",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(graph_steps, 50)),
                        "p99": float(np.percentile(graph_steps, 99)), "steps": k_lat,
                        "how": "CUDA events around each graph replay, a separate run of the same replays"},
-        "plain_form": {"value": nl * k_plain * world / (plain_ms * 1e-3), "unit": "layers/s",
+        "plain_form": {"value": arm.units * k_plain * world / (plain_ms * 1e-3), "unit": "layers/s",
                        "steps": k_plain, "ms_per_step": plain_ms / k_plain,
                        "latency_ms": {"p50": float(np.percentile(plain_steps, 50)),
                                       "p99": float(np.percentile(plain_steps, 99))},
@@ -442,6 +454,8 @@ def run_ours(args, rank, world, device):
                     "step_bytes": ch_bytes,
                     "step_gbs_graph": ch_bytes / (graph_ms / K * 1e-3) / 1e9},
         "plan": {k: v for k, v in info.items() if k != "split"},
+        "tuning": {"chosen": arm.tuning, "how": "he_plan_autotune: whole-plan runs timed per candidate, "
+                                                  "one knob at a time"},
         "e2e": e2e,
         "gpu_launches": info["kernels_per_run"] * K,
         "clocks": clk,
@@ -463,10 +477,10 @@ def run_e2e(arm, args, stream):
     d2h = sum(g["nout"] * 4 for g in arm.geo)
 
     def step(r):
-        for i in range(len(arm.layers)):
+        for i in range(len(arm.calls)):
             arm.x[r][i].copy_(hx[i], non_blocking=True)
         arm.graphs[r].replay()
-        for i in range(len(arm.layers)):
+        for i in range(len(arm.calls)):
             hy[i].copy_(arm.y[r][i], non_blocking=True)
 
     with torch.cuda.stream(stream):
@@ -479,7 +493,7 @@ def run_e2e(arm, args, stream):
             step(k % arm.R)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
-    return {"value": len(arm.layers) * K / dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
+    return {"value": arm.units * K / dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": K,
             "how": "per step: 20 H2D copies from pinned host memory, the plan (CUDA graph), "
                    "20 D2H copies of the extracted outputs; one stream, wall clock"}
@@ -489,65 +503,78 @@ def run_e2e(arm, args, stream):
 # CPU oracle (baseline leg and reference arm)
 # ----------------------------------------------------------------------------
 
-def oracle_layers_per_s(wl, budget_s: float, max_layers: int | None = None, start: int = 0):
-    """Runs the oracle's NTT tier over the workload's layers (cycling, from
-    layer `start`) until the time budget is spent or max_layers are done.
-    Returns (layers/s, layers done, threads)."""
+def oracle_layers_per_s(wl, budget_s: float, max_calls: int | None = None, start: int = 0):
+    """Runs the oracle's NTT tier over the workload's layer calls (cycling,
+    from call `start`) until the time budget is spent or max_calls are done.
+    Returns (layers/s, calls done, layers done, threads); a call of batch B
+    counts B layers."""
     from oracle import oracle as O
     from paper_2409_05205_gb300 import synth
-    N, L, B = wl["N"], wl["L"], wl["B"]
-    ps = O.select_primes(N, L)
-    psis = [O.root_2n(q, N) for q in ps]
-    layers = layer_list(wl)
-    done, t0 = 0, time.perf_counter()
+    calls = synth.call_list(wl)
+    rings = {}
+    done, units, t0 = 0, 0, time.perf_counter()
     while True:
-        Ld = layers[(start + done) % len(layers)]
-        if Ld["kind"] == "conv":
-            lay = O.conv_layout(N, Ld["ci"], Ld["co"], Ld["h"], Ld["w"])
+        c = calls[(start + done) % len(calls)]
+        N, L, B = c["N"], c["L"], c["B"]
+        if (N, L) not in rings:
+            ps = O.select_primes(N, L)
+            rings[(N, L)] = (ps, [O.root_2n(q, N) for q in ps])
+        ps, psis = rings[(N, L)]
+        if c["kind"] == "conv":
+            lay = O.conv_layout(N, c["ci"], c["co"], c["h"], c["w"])
             cts = synth.residues(SEED, f"cpu{done}", (B, lay["G"], 2, L, N), ps)
-            F = synth.conv_weights(SEED, f"cpuw{done}", Ld["co"], Ld["ci"], 3, 3, wl["wlo"], wl["whi"])
+            F = synth.conv_weights(SEED, f"cpuw{done}", c["co"], c["ci"], 3, 3, wl["wlo"], wl["whi"])
             O.conv_layer(cts, F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt")
         else:
-            fl = O.fc_layout(N, Ld["n_in"], Ld["n_out"])
+            fl = O.fc_layout(N, c["n_in"], c["n_out"])
             ct = synth.residues(SEED, f"cpu{done}", (B, 2, L, N), ps)
-            W = synth.fc_weights(SEED, f"cpuw{done}", Ld["n_out"], Ld["n_in"], wl["wlo"], wl["whi"])
+            W = synth.fc_weights(SEED, f"cpuw{done}", c["n_out"], c["n_in"], wl["wlo"], wl["whi"])
             O.fc_layer(ct, W, None, ps, psis, wl["t"], fl, O.OUT_EXTRACTED, tier="ntt")
         done += 1
+        units += B
         el = time.perf_counter() - t0
-        if el >= budget_s or (max_layers and done >= max_layers):
-            return done / el, done, O.threads()
+        if el >= budget_s or (max_calls and done >= max_calls):
+            return units / el, done, units, O.threads()
 
 
 def cpu_baseline(wl, budget_s=15.0):
-    v, n, th = oracle_layers_per_s(wl, budget_s)
+    v, n, u, th = oracle_layers_per_s(wl, budget_s)
     return {"value": v, "unit": "layers/s", "cores": th, "kind": "oracle",
-            "sample": f"{n} layer calls of the same workload cycled in order, ~{budget_s:.0f} s "
+            "sample": f"{n} layer calls ({u} layers) of the same workload cycled in order, ~{budget_s:.0f} s "
                       f"budget, oracle NTT tier (OpenMP, {th} threads)"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
+    from paper_2409_05205_gb300 import synth
     wl = workload(args.workload)
+    calls = synth.call_list(wl)
     per_step = 2
     for w in range(args.warmup):
-        oracle_layers_per_s(wl, 0.0, max_layers=1, start=w)
+        oracle_layers_per_s(wl, 0.0, max_calls=1, start=w)
     t0 = time.perf_counter()
     done = 0
     for k in range(args.steps):
-        _, n, th = oracle_layers_per_s(wl, 0.0, max_layers=per_step, start=k * per_step)
-        done += n
+        _, n, u, th = oracle_layers_per_s(wl, 0.0, max_calls=per_step, start=k * per_step)
+        done += u
     dt = time.perf_counter() - t0
     v = done / dt
+    rings = sorted({(c["N"], c["L"]) for c in calls})
+    cfg = {"workload": wl["name"], "calls_per_step": per_step, "t": wl["t"]}
+    if len(rings) == 1:
+        cfg.update(N=rings[0][0], L=rings[0][1])
+    else:
+        cfg["rings"] = [f"N={n},L={l}" for n, l in rings]
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": "layers/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "u32 (exact residues mod 30-bit primes)", "data": "synthetic",
-            "config": {"workload": wl["name"], "N": wl["N"], "L": wl["L"], "B": wl["B"],
-                       "layers_per_step": per_step},
+            "config": cfg,
             "cpu_baseline": {"value": v, "unit": "layers/s", "cores": th, "kind": "oracle",
                              "sample": f"{per_step} layer calls per step, cycling through the "
-                                       "20 layers in order, oracle NTT tier on the host cores"},
+                                       f"{len(calls)} calls of the workload in order, oracle NTT tier "
+                                       "on the host cores"},
             "e2e": {"value": v, "unit": "layers/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

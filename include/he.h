@@ -267,8 +267,47 @@ typedef struct {
 } he_layer_call;
 
 /* Validates every call (shapes, alignment, one device, no output overlapping
- * any input or other output) and builds the plan.  Blocking. */
+ * any input or other output) and builds the plan with the default tuning.
+ * Blocking. */
 he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t *out);
+
+/* How a plan maps its calls onto kernels.  None of these changes a result
+ * word; they change speed only.  (Library-side; the paper has no
+ * counterpart.)
+ *   split            1: Conv calls eligible for the split form take it
+ *                    (default); 0: every Conv call takes the fused form.
+ *   mac_item_kb      weight bytes of one split-form MAC work item: 32, 64 or
+ *                    128 (default 128).  Smaller items balance the
+ *                    persistent CTAs better and re-read inputs more often.
+ *   mac_ctas_per_sm  persistent MAC CTAs per SM: 1 or 2 (default 2).
+ *   fused_max_nj     the most ciphertext columns one fused-form CTA handles:
+ *                    2, 4, 8 or 16 (default 16; fewer also when shared
+ *                    memory requires). */
+typedef struct {
+    uint32_t split;
+    uint32_t mac_item_kb;
+    uint32_t mac_ctas_per_sm;
+    uint32_t fused_max_nj;
+} he_plan_tuning;
+
+/* The default tuning. */
+he_status he_plan_tuning_default(he_plan_tuning *t);
+/* he_plan_create with an explicit tuning; HE_ERR_ARG (nothing allocated)
+ * for a knob outside the values listed above.  Blocking. */
+he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *t,
+                               he_plan_t *out);
+/* Autotuner: finds the fastest tuning for these calls by timing whole plan
+ * runs on `stream` (CUDA events; per candidate 2 warm-up runs, then the
+ * best of three batches of `iters` timed runs; one knob at a time in the
+ * order listed above, keeping the best value of each before trying the
+ * next), then builds the plan with it.
+ * Every candidate run computes the calls in full, so the output buffers
+ * hold the calls' results afterwards.  The result is cached per process by
+ * the calls' shapes, rings, batch sizes, input domains and device: a later
+ * call with the same signature builds its plan with the cached tuning and
+ * runs nothing.  `best` (may be NULL) receives the tuning.  Blocking. */
+he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t iters, void *stream,
+                           he_plan_tuning *best, he_plan_t *out);
 /* Runs every call of the plan.  Asynchronous on `stream`. */
 he_status he_plan_run(he_plan_t plan, void *stream);
 /* Part of he_plan_run, for timing its kernels separately:
@@ -295,6 +334,7 @@ typedef struct {
     uint32_t fc_items;        /* FC items on the side stream */
     uint32_t split_calls;     /* Conv calls in the split form */
     uint64_t workspace_bytes; /* device workspace the plan owns */
+    he_plan_tuning tuning;    /* the tuning the plan was built with */
 } he_plan_info;
 /* Fills *info; if `split` is not NULL, also split[i] = 1 for each call i
  * (of the ncalls given to he_plan_create) that takes the split form, else

@@ -10,7 +10,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "he_internal.h"
@@ -569,7 +571,38 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out, u
     return e == cudaSuccess ? HE_OK : cuda_fail(e, "inverse NTT");
 }
 
+he_status he_plan_tuning_default(he_plan_tuning *t) {
+    if (!t) return fail(HE_ERR_ARG, "NULL argument");
+    t->split = 1;
+    t->mac_item_kb = 128;
+    t->mac_ctas_per_sm = 2;
+    t->fused_max_nj = 16;
+    return HE_OK;
+}
+
+namespace {
+he_status check_tuning(const he_plan_tuning &t) {
+    if (t.split > 1) return fail(HE_ERR_ARG, "tuning: split must be 0 or 1");
+    if (t.mac_item_kb != 32 && t.mac_item_kb != 64 && t.mac_item_kb != 128)
+        return fail(HE_ERR_ARG, "tuning: mac_item_kb must be 32, 64 or 128");
+    if (t.mac_ctas_per_sm != 1 && t.mac_ctas_per_sm != 2) return fail(HE_ERR_ARG, "tuning: mac_ctas_per_sm must be 1 or 2");
+    if (t.fused_max_nj != 2 && t.fused_max_nj != 4 && t.fused_max_nj != 8 && t.fused_max_nj != 16)
+        return fail(HE_ERR_ARG, "tuning: fused_max_nj must be 2, 4, 8 or 16");
+    return HE_OK;
+}
+}  // namespace
+
 he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t *out) {
+    he_plan_tuning t;
+    he_plan_tuning_default(&t);
+    return he_plan_create_tuned(calls, ncalls, &t, out);
+}
+
+he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning,
+                               he_plan_t *out) {
+    if (!tuning) return fail(HE_ERR_ARG, "NULL tuning");
+    if (check_tuning(*tuning) != HE_OK) return HE_ERR_ARG;
+    const he_plan_tuning tu = *tuning;
     if (!calls || !out || ncalls == 0) return fail(HE_ERR_ARG, "NULL argument or empty plan");
     *out = nullptr;
     const he_params_s *p0 = calls[0].filters ? calls[0].filters->p : nullptr;
@@ -625,17 +658,17 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
             g.mult = lay.off_mult;
             g.logTS = f->logTS;
             g.lcs = f->lcs;
-            cd.nj = he_conv_nj(g.ncols, lay.M, lay.s);
+            cd.nj = std::min(he_conv_nj(g.ncols, lay.M, lay.s), tu.fused_max_nj);
             cd.nb = lay.s >= 4 ? 1 : (lay.s == 2 ? 2 : 4);
             cd.cpt = he_conv_cpt(cd.nj, cd.nb, lay.G);
             // split form for one ciphertext per call with s >= 4 and G in
             // {1, 2, 4} whose output polynomials fit shared memory
-            cd.split = (c.B == 1 && split_mac_ok(lay.s, lay.G) &&
+            cd.split = (tu.split && c.B == 1 && split_mac_ok(lay.s, lay.G) &&
                         (size_t)std::min(lay.s, f->desc.co) * fin_stride(lay.M) * 4u <= 200u * 1024u)
                            ? 1u
                            : 0u;
             g.cs = split_cs(lay.s, lay.G);
-            g.nc = f->nc;
+            g.nc = std::min(f->desc.co, std::max(1u, (tu.mac_item_kb * 256u) / (lay.G << f->logTS)));
             // bank interleave and tile must match the MAC kernel's
             if (cd.split && ((1u << f->lcs) != g.cs || f->logTS != split_tile_log(f->lcs))) cd.split = 0;
             nin = (size_t)c.B * lay.G * 2u * r.L * r.N;
@@ -688,6 +721,7 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
         return fail(HE_ERR_NOMEM, "plan");
     }
     for (uint32_t i = 0; i < ncalls; ++i) pl->split[i] = descs[i].split ? 1 : 0;
+    pl->tuning = tu;
     pl->ws_bytes = ws_words * sizeof(uint32_t);
     if (ws_words) e = cudaMalloc(&pl->ws, ws_words * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_status, sizeof(uint32_t));
@@ -796,7 +830,7 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
         std::stable_sort(all.begin(), all.end(), by_cost);
         int sms = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-        const uint32_t nctas = (uint32_t)std::min<size_t>(all.size(), (size_t)std::max(1, sms) * 2u);
+        const uint32_t nctas = (uint32_t)std::min<size_t>(all.size(), (size_t)std::max(1, sms) * tu.mac_ctas_per_sm);
         std::vector<std::vector<ChanItem>> per(nctas);
         std::vector<std::pair<double, uint32_t>> heap;  // (load, cta), min-heap
         for (uint32_t b = 0; b < nctas; ++b) heap.push_back({0.0, b});
@@ -931,6 +965,7 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
     for (int c = 0; c < 4; ++c) r.kernels_per_run += plan->n_chan[c] > 0;
     for (uint32_t i = 0; i < plan->ncalls; ++i) r.split_calls += plan->split[i];
     r.workspace_bytes = plan->ws_bytes;
+    r.tuning = plan->tuning;
     *info = r;
     if (split)
         for (uint32_t i = 0; i < plan->ncalls; ++i) split[i] = plan->split[i];
@@ -956,6 +991,127 @@ void he_plan_destroy(he_plan_t plan) {
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);
     delete[] plan->split;
     delete plan;
+}
+
+namespace {
+// per-process cache of autotuned plans: signature -> tuning
+std::mutex g_tune_mu;
+std::vector<std::pair<std::string, he_plan_tuning>> g_tune_cache;
+
+std::string plan_signature(const he_layer_call *calls, uint32_t ncalls) {
+    std::string k;
+    char buf[160];
+    for (uint32_t i = 0; i < ncalls; ++i) {
+        const he_filters_s *f = calls[i].filters;
+        const he_params_s *p = f->p;
+        if (f->kind == HE_KIND_CONV)
+            snprintf(buf, sizeof(buf), "c%d:%u:%u:%u:%u:%u:%u:%u:%u:%u:%u:%u:%d;", p->device, p->N, p->L, calls[i].B,
+                     f->desc.ci, f->desc.co, f->desc.h, f->desc.w, f->desc.fh, f->desc.fw, f->desc.stride,
+                     f->desc.pad, calls[i].in_domain);
+        else
+            snprintf(buf, sizeof(buf), "f%d:%u:%u:%u:%u:%u:%d;", p->device, p->N, p->L, calls[i].B, f->fl.n_in,
+                     f->fl.n_out, calls[i].in_domain);
+        k += buf;
+    }
+    return k;
+}
+
+// mean run time (ms) of a plan built with tuning t; < 0 if it cannot be built or run
+float time_tuning(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning &t, uint32_t iters,
+                  cudaStream_t st) {
+    he_plan_t pl = nullptr;
+    if (he_plan_create_tuned(calls, ncalls, &t, &pl) != HE_OK) return -1.0f;
+    cudaEvent_t a = nullptr, b = nullptr;
+    float ms = -1.0f;
+    if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
+        bool ok = true;
+        for (int w = 0; w < 2 && ok; ++w) ok = he_plan_run(pl, st) == HE_OK;
+        // best of three timed batches of `iters` runs (robust to other work on the GPU)
+        for (int rep = 0; rep < 3 && ok; ++rep) {
+            ok = cudaEventRecord(a, st) == cudaSuccess;
+            for (uint32_t k = 0; k < iters && ok; ++k) ok = he_plan_run(pl, st) == HE_OK;
+            ok = ok && cudaEventRecord(b, st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess;
+            float t = 0.0f;
+            if (ok && cudaEventElapsedTime(&t, a, b) == cudaSuccess) {
+                t /= (float)std::max(1u, iters);
+                ms = (ms < 0.0f || t < ms) ? t : ms;
+            } else {
+                ok = false;
+            }
+        }
+        if (!ok || he_plan_check(pl) != HE_OK) ms = -1.0f;
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    he_plan_destroy(pl);
+    return ms;
+}
+}  // namespace
+
+he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t iters, void *stream,
+                           he_plan_tuning *best, he_plan_t *out) {
+    if (!calls || !out || ncalls == 0) return fail(HE_ERR_ARG, "NULL argument or empty plan");
+    for (uint32_t i = 0; i < ncalls; ++i)
+        if (!calls[i].filters) return fail(HE_ERR_ARG, "call %u: no filters", i);
+    const std::string key = plan_signature(calls, ncalls);
+    he_plan_tuning cur;
+    he_plan_tuning_default(&cur);
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto &kv : g_tune_cache)
+            if (kv.first == key) {
+                cur = kv.second;
+                cached = true;
+            }
+    }
+    if (!cached) {
+        cudaStream_t st = (cudaStream_t)stream;
+        DeviceGuard g(calls[0].filters->p->device);
+        if (!g.ok) return fail(HE_ERR_CUDA, "cannot select the calls' device");
+        // the default first: it must build and run, or there is nothing to tune
+        float best_ms = time_tuning(calls, ncalls, cur, iters, st);
+        if (best_ms < 0.0f) return he_plan_create_tuned(calls, ncalls, &cur, out);  // reports the error
+        // which knobs matter for these calls
+        he_plan_t probe = nullptr;
+        he_plan_info info{};
+        if (he_plan_create_tuned(calls, ncalls, &cur, &probe) == HE_OK) {
+            he_plan_query(probe, &info, nullptr);
+            he_plan_destroy(probe);
+        }
+        he_plan_tuning nosplit = cur;
+        nosplit.split = 0;
+        he_plan_t probe2 = nullptr;
+        he_plan_info info2{};
+        if (he_plan_create_tuned(calls, ncalls, &nosplit, &probe2) == HE_OK) {
+            he_plan_query(probe2, &info2, nullptr);
+            he_plan_destroy(probe2);
+        }
+        const bool has_split = info.split_calls > 0, has_fused = info.fused_items > 0 || info2.fused_items > 0;
+        auto try_knob = [&](uint32_t he_plan_tuning::*knob, std::initializer_list<uint32_t> vals) {
+            const uint32_t keep = cur.*knob;
+            for (uint32_t v : vals) {
+                if (v == keep) continue;
+                he_plan_tuning t = cur;
+                t.*knob = v;
+                const float ms = time_tuning(calls, ncalls, t, iters, st);
+                if (ms >= 0.0f && ms < best_ms) {
+                    best_ms = ms;
+                    cur = t;
+                }
+            }
+        };
+        if (has_split) try_knob(&he_plan_tuning::split, {1u, 0u});
+        if (has_split && cur.split) {
+            try_knob(&he_plan_tuning::mac_item_kb, {128u, 64u, 32u});
+            try_knob(&he_plan_tuning::mac_ctas_per_sm, {2u, 1u});
+        }
+        if (has_fused) try_knob(&he_plan_tuning::fused_max_nj, {16u, 8u, 4u, 2u});
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache.push_back({key, cur});
+    }
+    if (best) *best = cur;
+    return he_plan_create_tuned(calls, ncalls, &cur, out);
 }
 
 he_status he_sync(void *stream) {

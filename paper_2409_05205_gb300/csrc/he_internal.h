@@ -222,6 +222,7 @@ struct he_plan_s {
     size_t ws_bytes;
     uint32_t *d_status;                 // bit 0: a bounded wait in the MAC kernel gave up
     uint8_t *split;                     // host: per call, 1 if it takes the split form
+    he_plan_tuning tuning;
 };
 
 cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase);

@@ -51,10 +51,14 @@ class he_layer_call(ctypes.Structure):
                 ("d_out", ctypes.c_void_p), ("B", ctypes.c_uint32)]
 
 
+class he_plan_tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in ("split", "mac_item_kb", "mac_ctas_per_sm", "fused_max_nj")]
+
+
 class he_plan_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("kernels_per_run", "ntt_items", "mac_items", "mac_ctas",
                                                "finish_items", "fused_items", "fc_items", "split_calls")] + \
-               [("workspace_bytes", ctypes.c_uint64)]
+               [("workspace_bytes", ctypes.c_uint64), ("tuning", he_plan_tuning)]
 
 
 _lib = None
@@ -79,6 +83,10 @@ _SIGS = {
     "he_ntt_forward": [_vp, _vp, _vp, _u32, _vp],
     "he_ntt_inverse": [_vp, _vp, _vp, _u32, _vp],
     "he_plan_create": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(_vp)],
+    "he_plan_tuning_default": [ctypes.POINTER(he_plan_tuning)],
+    "he_plan_create_tuned": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(he_plan_tuning), ctypes.POINTER(_vp)],
+    "he_plan_autotune": [ctypes.POINTER(he_layer_call), _u32, _u32, _vp, ctypes.POINTER(he_plan_tuning),
+                         ctypes.POINTER(_vp)],
     "he_plan_run": [_vp, _vp],
     "he_plan_run_phase": [_vp, _i32, _vp],
     "he_plan_query": [_vp, ctypes.POINTER(he_plan_info), _vp],
@@ -251,17 +259,47 @@ def he_ntt_inverse(p: int, d_in, d_out, count: int, stream=None) -> None:
     _check(lib().he_ntt_inverse(p, _ptr(d_in), _ptr(d_out), count, _stream(stream)))
 
 
-def he_plan_create(calls) -> int:
-    """calls: sequence of (filters, d_in, in_domain, d_out, B) tuples or dicts."""
+def _calls(calls):
     arr = (he_layer_call * len(calls))()
     for i, c in enumerate(calls):
         if isinstance(c, dict):
             c = (c["filters"], c["d_in"], c.get("in_domain", HE_COEFF), c["d_out"], c["B"])
         f, d_in, dom, d_out, B = c
         arr[i] = he_layer_call(f, _ptr(d_in), dom, _ptr(d_out), B)
+    return arr
+
+
+def _tuning_dict(t: he_plan_tuning) -> dict:
+    return {n: getattr(t, n) for n, _ in he_plan_tuning._fields_}
+
+
+def he_plan_create(calls) -> int:
+    """calls: sequence of (filters, d_in, in_domain, d_out, B) tuples or dicts."""
     out = _vp()
-    _check(lib().he_plan_create(arr, len(calls), ctypes.byref(out)))
+    _check(lib().he_plan_create(_calls(calls), len(calls), ctypes.byref(out)))
     return out.value
+
+
+def he_plan_tuning_default() -> dict:
+    t = he_plan_tuning()
+    _check(lib().he_plan_tuning_default(ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def he_plan_create_tuned(calls, tuning: dict) -> int:
+    t = he_plan_tuning(**tuning)
+    out = _vp()
+    _check(lib().he_plan_create_tuned(_calls(calls), len(calls), ctypes.byref(t), ctypes.byref(out)))
+    return out.value
+
+
+def he_plan_autotune(calls, iters: int = 5, stream=None) -> tuple[int, dict]:
+    """(plan, chosen tuning).  Runs the calls while timing candidates."""
+    t = he_plan_tuning()
+    out = _vp()
+    _check(lib().he_plan_autotune(_calls(calls), len(calls), iters, _stream(stream), ctypes.byref(t),
+                                  ctypes.byref(out)))
+    return out.value, _tuning_dict(t)
 
 
 def he_plan_run(plan: int, stream=None) -> None:
@@ -278,7 +316,8 @@ def he_plan_query(plan: int, ncalls: int | None = None) -> dict:
     info = he_plan_info()
     sp = None if ncalls is None else np.zeros(ncalls, dtype=np.uint8)
     _check(lib().he_plan_query(plan, ctypes.byref(info), None if sp is None else sp.ctypes.data))
-    out = {n: getattr(info, n) for n, _ in he_plan_info._fields_}
+    out = {n: getattr(info, n) for n, _ in he_plan_info._fields_ if n != "tuning"}
+    out["tuning"] = _tuning_dict(info.tuning)
     if sp is not None:
         out["split"] = [bool(x) for x in sp]
     return out

@@ -110,6 +110,40 @@ def plain20_conv_layers(width: int = 1) -> list[dict]:
     return L
 
 
+# distinct Conv shapes of plain-20 (width 1) and the CIFAR-100 FC layer
+PLAIN20_DISTINCT = [dict(ci=3, co=16, h=32, w=32), dict(ci=16, co=16, h=32, w=32), dict(ci=16, co=32, h=32, w=32),
+                    dict(ci=32, co=32, h=16, w=16), dict(ci=32, co=64, h=16, w=16), dict(ci=64, co=64, h=8, w=8)]
+BATCHED_RINGS = [(4096, 2), (8192, 3), (16384, 6)]
+
+
+def batched_calls(seed: int, n: int = 64) -> list[dict]:
+    """n independent layer calls of one ciphertext each: ring (N, L) uniform
+    over BATCHED_RINGS, layer uniform over the distinct plain-20 Conv shapes
+    and FC 64->100."""
+    ring = below(seed, "batched/ring", n, len(BATCHED_RINGS))
+    shape = below(seed, "batched/shape", n, len(PLAIN20_DISTINCT) + 1)
+    out = []
+    for r, sh in zip(ring, shape):
+        N, L = BATCHED_RINGS[int(r)]
+        if int(sh) < len(PLAIN20_DISTINCT):
+            d = dict(kind="conv", N=N, L=L, B=1, stride=1, fh=3, fw=3, pad=1, **PLAIN20_DISTINCT[int(sh)])
+        else:
+            d = dict(kind="fc", N=N, L=L, B=1, n_in=64, n_out=100)
+        out.append(d)
+    return out
+
+
+def call_list(wl: dict) -> list[dict]:
+    """Every layer call of one step of a workload, each with its ring (N, L)
+    and batch size B."""
+    if "calls" in wl:
+        return [dict(c) for c in wl["calls"]]
+    out = [dict(kind="conv", N=wl["N"], L=wl["L"], B=wl["B"], **d) for d in wl["conv"]]
+    if wl["fc"]:
+        out.append(dict(kind="fc", N=wl["N"], L=wl["L"], B=wl["B"], **wl["fc"]))
+    return out
+
+
 WORKLOADS = {
     "conv1": dict(N=2048, L=1, t=65537, B=1,
                   conv=[dict(ci=3, co=4, h=16, w=16, stride=1, fh=3, fw=3, pad=1)],
@@ -118,6 +152,7 @@ WORKLOADS = {
                         fc=dict(n_in=64, n_out=10), wlo=-128, whi=127),
     "plain20_c100_wide4": dict(N=16384, L=6, t=65537, B=8, conv=plain20_conv_layers(4),
                                fc=dict(n_in=256, n_out=100), wlo=-128, whi=127),
+    "batched64": dict(t=65537, calls=batched_calls(3, 64), wlo=-128, whi=127),
 }
 
 

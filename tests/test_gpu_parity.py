@@ -425,3 +425,52 @@ def test_plan_split_form_plain20_shapes_bit_exact():
             H.he_plan_destroy(plan)
             for f in banks:
                 H.he_filters_destroy(f)
+
+
+# ----------------------------------------------------------------------------
+# the wide x4 network (N = 16384, 6 limbs, B = 8) through one plan: every
+# distinct Conv shape and the FC layer; every word equals the single-call
+# path, sampled words equal the oracle
+# ----------------------------------------------------------------------------
+
+WIDE4_SHAPES = [(3, 64, 32), (64, 64, 32), (64, 128, 32), (128, 128, 16), (128, 256, 16), (256, 256, 8)]
+
+
+def test_plan_wide4_batch8_matches_single_calls_and_oracle():
+    H = U.he()
+    torch = U.torch_cuda()
+    N, L, B = 16384, 6, 8
+    ps, psis = U.ring(N, L)
+    with U.params(N, L) as p:
+        calls, singles, banks, cases = [], [], [], []
+        for k, (ci, co, hw) in enumerate(WIDE4_SHAPES):
+            _, _, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, B, seed=500 + k)
+            f = H.he_pack_filters(p, desc, F)
+            banks.append(f)
+            singles.append(U.run_conv(p, f, cts, H.HE_OUT_EXTRACTED, lay["H"]))
+            calls.append((f, U.to_dev(cts), H.HE_COEFF, U.empty_dev(singles[-1].shape), B))
+            cases.append((cts, F, lay))
+        fc_f, fc_ct, fc_ref = _plan_case(H, p, N, L, (256, 100), B, seed=599, fc=True)
+        banks.append(fc_f)
+        calls.append((fc_f, U.to_dev(fc_ct), H.HE_COEFF, U.empty_dev(fc_ref.shape), B))
+        plan = H.he_plan_create(calls)
+        try:
+            info = H.he_plan_query(plan, len(calls))
+            assert info["split_calls"] == 0  # B = 8: every Conv call takes the fused form
+            s = torch.cuda.current_stream()
+            H.he_plan_run(plan, s)
+            H.he_sync(s)
+            H.he_plan_check(plan)
+            rng = np.random.default_rng(7)
+            for c, ref, (cts, F, lay) in zip(calls, singles, cases):
+                got = U.from_dev(c[3]).reshape(ref.shape)
+                np.testing.assert_array_equal(got, ref)
+                picks = [(int(rng.integers(B)), int(rng.integers(lay["H"])), int(rng.integers(2)),
+                          int(rng.integers(L)), int(rng.integers(N))) for _ in range(12)]
+                np.testing.assert_array_equal(O.conv_layer_sampled(cts, F, ps, lay, picks),
+                                              np.array([got[pk] for pk in picks], dtype=np.uint32))
+            np.testing.assert_array_equal(U.from_dev(calls[-1][3]).reshape(fc_ref.shape), fc_ref)
+        finally:
+            H.he_plan_destroy(plan)
+            for f in banks:
+                H.he_filters_destroy(f)

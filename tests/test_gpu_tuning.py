@@ -1,0 +1,113 @@
+"""Plan tuning changes speed only: every tuning gives the oracle's words,
+and the autotuner picks one of them, runs the calls, and caches its choice."""
+
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+import _gpu_helpers as U
+
+pytestmark = pytest.mark.gpu
+
+# split-form calls (B = 1, s >= 4), fused-form calls (B = 2; s = 2) and an FC call
+SPECS = [((16, 16, 32), 1), ((64, 64, 8), 1), ((16, 32, 32), 2), ((32, 32, 16), 1)]
+N, L = 8192, 3
+
+
+def _setup(H, p):
+    ps, psis = U.ring(N, L)
+    banks, calls, refs = [], [], []
+    for k, ((ci, co, hw), B) in enumerate(SPECS):
+        _, _, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, B, seed=700 + k)
+        refs.append(O.conv_layer(cts, F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt"))
+        banks.append(H.he_pack_filters(p, desc, F))
+        calls.append((banks[-1], U.to_dev(cts), H.HE_COEFF, U.empty_dev(refs[-1].shape), B))
+    n_in, n_out = 64, 10
+    lay = O.fc_layout(N, n_in, n_out)
+    W = U.synth.fc_weights(799, "tW", n_out, n_in, -128, 127)
+    Bv = U.synth.ints(799, "tB", (n_out,), -999, 999)
+    ct = U.synth.residues(799, "tct", (1, 2, L, N), ps)
+    refs.append(O.fc_layer(ct, W, Bv, ps, psis, U.T, lay, O.OUT_EXTRACTED, tier="ntt"))
+    banks.append(H.he_pack_fc(p, n_in, n_out, W, Bv))
+    calls.append((banks[-1], U.to_dev(ct), H.HE_COEFF, U.empty_dev(refs[-1].shape), 1))
+    return banks, calls, refs
+
+
+def _check(H, calls, refs):
+    for c, ref in zip(calls, refs):
+        np.testing.assert_array_equal(U.from_dev(c[3]).reshape(ref.shape), ref)
+
+
+TUNINGS = [dict(split=1, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16),
+           dict(split=0, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16),
+           dict(split=1, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=2),
+           dict(split=1, mac_item_kb=64, mac_ctas_per_sm=2, fused_max_nj=4),
+           dict(split=0, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=8)]
+
+
+def test_every_tuning_gives_the_oracle_words():
+    H = U.he()
+    torch = U.torch_cuda()
+    with U.params(N, L) as p:
+        banks, calls, refs = _setup(H, p)
+        try:
+            s = torch.cuda.current_stream()
+            for t in TUNINGS:
+                plan = H.he_plan_create_tuned(calls, t)
+                try:
+                    info = H.he_plan_query(plan, len(calls))
+                    assert info["tuning"] == t
+                    assert info["split"] == ([bool(t["split"])] * 2 + [False] + [bool(t["split"])] + [False])
+                    for c in calls:
+                        c[3].fill_(-1)
+                    H.he_plan_run(plan, s)
+                    H.he_sync(s)
+                    H.he_plan_check(plan)
+                    _check(H, calls, refs)
+                finally:
+                    H.he_plan_destroy(plan)
+        finally:
+            for f in banks:
+                H.he_filters_destroy(f)
+
+
+def test_autotune_picks_a_valid_tuning_and_caches_it():
+    H = U.he()
+    torch = U.torch_cuda()
+    with U.params(N, L) as p:
+        banks, calls, refs = _setup(H, p)
+        try:
+            s = torch.cuda.current_stream()
+            for c in calls:
+                c[3].fill_(-1)
+            plan, t = H.he_plan_autotune(calls, 3, s)
+            try:
+                H.he_sync(s)
+                _check(H, calls, refs)          # the tuning runs computed the calls
+                assert t["split"] in (0, 1) and t["mac_item_kb"] in (32, 64, 128)
+                assert t["mac_ctas_per_sm"] in (1, 2) and t["fused_max_nj"] in (2, 4, 8, 16)
+                assert H.he_plan_query(plan)["tuning"] == t
+                for c in calls:
+                    c[3].fill_(-1)
+                H.he_plan_run(plan, s)
+                H.he_sync(s)
+                _check(H, calls, refs)
+            finally:
+                H.he_plan_destroy(plan)
+            # same signature: the cached choice, and no tuning runs (outputs untouched)
+            for c in calls:
+                c[3].fill_(-1)
+            t0 = time.perf_counter()
+            plan2, t2 = H.he_plan_autotune(calls, 3, s)
+            dt = time.perf_counter() - t0
+            H.he_plan_destroy(plan2)
+            assert t2 == t
+            assert all((U.from_dev(c[3]) == 0xFFFFFFFF).all() for c in calls)
+            assert dt < 5.0
+        finally:
+            for f in banks:
+                H.he_filters_destroy(f)
