@@ -347,6 +347,76 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split);
 he_status he_plan_check(he_plan_t plan);
 void he_plan_destroy(he_plan_t plan);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request loop for encrypted inferences.
+ *
+ * A server holds registered models -- the ordered banks of a network's
+ * layers, all on the server's device, which stay resident -- and serves
+ * inference requests as they arrive.  A request carries the input
+ * ciphertexts of every layer of its model in HOST memory and receives the
+ * extracted outputs in HOST memory; its layer calls run in order, as in the
+ * paper's protocol where the client's non-linear step sits between layers
+ * (Sec. III, Alg. 1; the client's time is taken as zero here).  A
+ * scheduler thread batches up to max_batch requests waiting for the same
+ * (model, layer) into one plan run (continuous batching: a request joins
+ * the next batch of its layer as soon as it is there, while other batches
+ * run on other streams), copies host->device, runs, copies device->host.
+ * Device buffers for a batch (its inputs, outputs and plan workspace) are
+ * allocated on demand while their total stays within hbm_budget_bytes and
+ * are reused; when the budget is spent, requests wait.  Each request's
+ * words are those of he_conv_layer / he_fc_layer (HE_OUT_EXTRACTED) on its
+ * own, whatever it was batched with.  Host buffers in page-locked memory
+ * let the copies overlap; they must stay valid until the request finishes.
+ * (Library-side serving pattern; the paper evaluates one layer at a time.)
+ * ------------------------------------------------------------------------ */
+typedef struct he_server_s *he_server_t;
+
+typedef struct {
+    int device;
+    uint64_t hbm_budget_bytes;  /* device bytes for batch buffers and plan workspaces
+                                   (the registered banks are not counted) */
+    uint32_t max_batch;         /* ciphertexts per batch: 1, 2, 4 or 8 */
+    uint32_t streams;           /* streams batches run on, 1..32 */
+    uint32_t max_inflight;      /* batches on the device at once, >= 1 */
+} he_server_config;
+
+typedef struct {
+    double arrive_ms, done_ms;  /* steady-clock times of submission and completion */
+    double latency_ms;          /* done - arrive: the inference's network latency */
+} he_request_stats;
+
+typedef struct {
+    uint64_t submitted, finished, failed;
+    uint64_t batches, batched_calls;  /* plan runs; layer calls (ciphertexts) in them */
+    uint64_t lanes;                   /* batch buffers allocated now */
+    uint64_t bytes_in_use, bytes_peak;
+} he_server_report_t;
+
+/* Starts the scheduler thread.  Blocking. */
+he_status he_server_create(const he_server_config *cfg, he_server_t *out);
+/* Registers a model: `layers` are its banks in order (Conv and FC, one
+ * params).  The banks must outlive the server.  *model_id is the handle.
+ * HE_ERR_ARG if a layer's batch-1 buffers (twice its input plus output
+ * words) do not fit hbm_budget_bytes. */
+he_status he_server_add_model(he_server_t s, const he_filters_t *layers, uint32_t nlayers,
+                              uint32_t *model_id);
+/* Queues one inference.  h_in[i]: HOST uint32 input of layer i, the layout
+ * of he_conv_layer / he_fc_layer for B = 1 (coefficient domain); h_out[i]:
+ * HOST uint32 buffer for layer i's extracted output.  Non-blocking. */
+he_status he_server_submit(he_server_t s, uint32_t model_id, const uint32_t *const *h_in,
+                           uint32_t *const *h_out, uint64_t *ticket);
+/* Waits up to timeout_ms for an inference; HE_ERR_TIMEOUT if it has not
+ * finished (the ticket stays valid).  On success the ticket is released. */
+he_status he_server_wait(he_server_t s, uint64_t ticket, uint32_t timeout_ms, he_request_stats *st);
+he_status he_server_report(he_server_t s, he_server_report_t *rep);
+/* Recorded latencies in ms: which = 0 per inference (arrival to the last
+ * layer's outputs on the host), 1 per layer call (entry into the layer's
+ * queue to its outputs on the host).  Copies min(n, cap) values. */
+he_status he_server_latencies(he_server_t s, int which, double *out_ms, uint64_t cap, uint64_t *n);
+/* Stops the scheduler (queued requests that have not started are dropped;
+ * running batches finish), frees the server's buffers.  Blocking. */
+void he_server_destroy(he_server_t s);
+
 /* Wait for `stream` and report any pending CUDA error. */
 he_status he_sync(void *stream);
 

@@ -1,0 +1,453 @@
+// he_server.cu -- request loop for encrypted inferences (host code only).
+//
+// A server holds registered models (their layer banks stay resident on the
+// device) and serves inference requests as they arrive.  A request carries
+// the input ciphertexts of every layer of its model and receives the
+// extracted outputs; its layer calls run in order, one after the other, as
+// in the protocol where the client's non-linear step sits between layers
+// (taken here as zero time).  A scheduler thread forms batches of up to
+// max_batch requests waiting for the same (model, layer) -- continuous
+// batching: a request is admitted into the next batch of its layer as soon
+// as a slot is free, while other batches run -- and runs each batch on one
+// of several streams: host->device copies, the layer as a one-call plan,
+// device->host copies, then a host callback.  Device buffers ("lanes": the
+// batch's inputs and outputs and the plan's workspace) are allocated on
+// demand under an HBM budget and reused; when the budget is spent, requests
+// wait for a lane to free up.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "he_internal.h"
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct ModelLayer {
+    he_filters_t f;
+    size_t in_words, out_words;  // per ciphertext
+};
+
+struct Model {
+    std::vector<ModelLayer> layers;
+};
+
+struct Req {
+    uint64_t id;
+    uint32_t model, layer = 0;
+    std::vector<const uint32_t *> in;
+    std::vector<uint32_t *> out;
+    double t_arrive, t_layer;  // arrival; entry into the current layer's queue
+    bool done = false, failed = false;
+    double t_done = 0.0;
+};
+
+struct Lane {
+    uint32_t model, layer, bucket;
+    uint32_t *d_in = nullptr, *d_out = nullptr;
+    he_plan_t plan = nullptr;
+    size_t bytes = 0;
+    bool busy = false;
+};
+
+struct Batch;
+
+struct Server {
+    he_server_config cfg;
+    std::vector<Model> models;
+    std::vector<cudaStream_t> streams;
+    uint32_t next_stream = 0;
+
+    // Completed batches, pushed by the CUDA callback thread.  The callback
+    // takes only cb_mu, which is never held across a CUDA call, so a CUDA
+    // call that waits for streams (cudaFree, a pageable copy) cannot wait on
+    // a callback that waits on a lock.
+    std::mutex cb_mu;
+    std::condition_variable cv_sched;
+    std::vector<Batch *> completed;
+
+    std::mutex mu;  // everything below; the scheduler holds it across CUDA calls
+    std::condition_variable cv_done;
+    std::map<uint64_t, Req *> reqs;
+    std::map<std::pair<uint32_t, uint32_t>, std::deque<Req *>> queues;  // (model, layer) -> waiting
+    std::vector<Batch *> failed_launch;
+    std::vector<Lane *> lanes;
+    size_t bytes_in_use = 0, bytes_peak = 0;
+    uint64_t next_id = 1, submitted = 0, finished = 0, batches = 0, batched_calls = 0, failed = 0;
+    uint32_t inflight = 0;
+    std::vector<double> lat_layer, lat_net;
+    bool stop = false;
+    char error[256] = {0};
+    std::thread sched;
+};
+
+struct Batch {
+    Server *s;
+    Lane *lane;
+    std::vector<Req *> reqs;
+    bool ok;
+};
+
+void CUDART_CB on_batch_done(void *p) {
+    // runs on a CUDA callback thread: no CUDA calls here
+    Batch *b = static_cast<Batch *>(p);
+    Server *s = b->s;
+    std::lock_guard<std::mutex> lk(s->cb_mu);
+    s->completed.push_back(b);
+    s->cv_sched.notify_one();
+}
+
+// largest power of two <= n, at most max_batch
+uint32_t bucket_of(uint32_t n, uint32_t max_batch) {
+    uint32_t b = 1;
+    while (b * 2 <= n && b * 2 <= max_batch) b *= 2;
+    return b;
+}
+
+// a free lane for (model, layer, bucket), allocating one if the budget
+// allows; nullptr when none can be had now.  Called with s->mu held.
+Lane *get_lane(Server *s, uint32_t model, uint32_t layer, uint32_t bucket) {
+    for (Lane *l : s->lanes)
+        if (!l->busy && l->model == model && l->layer == layer && l->bucket == bucket) return l;
+    const ModelLayer &ml = s->models[model].layers[layer];
+    const size_t io = (ml.in_words + ml.out_words) * bucket * sizeof(uint32_t);
+    if (s->bytes_in_use + io > s->cfg.hbm_budget_bytes) {
+        // free an idle lane of another shape to make room
+        for (size_t i = 0; i < s->lanes.size(); ++i) {
+            Lane *l = s->lanes[i];
+            if (l->busy) continue;
+            he_plan_destroy(l->plan);
+            cudaFree(l->d_in);
+            cudaFree(l->d_out);
+            s->bytes_in_use -= l->bytes;
+            delete l;
+            s->lanes.erase(s->lanes.begin() + (long)i);
+            break;
+        }
+        if (s->bytes_in_use + io > s->cfg.hbm_budget_bytes) return nullptr;
+    }
+    Lane *l = new (std::nothrow) Lane();
+    if (!l) return nullptr;
+    l->model = model;
+    l->layer = layer;
+    l->bucket = bucket;
+    if (cudaMalloc(&l->d_in, ml.in_words * bucket * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMalloc(&l->d_out, ml.out_words * bucket * sizeof(uint32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(l->d_in);
+        cudaFree(l->d_out);
+        delete l;
+        return nullptr;
+    }
+    he_layer_call c{ml.f, l->d_in, HE_COEFF, l->d_out, bucket};
+    if (he_plan_create(&c, 1, &l->plan) != HE_OK) {
+        cudaFree(l->d_in);
+        cudaFree(l->d_out);
+        delete l;
+        return nullptr;
+    }
+    he_plan_info info{};
+    he_plan_query(l->plan, &info, nullptr);
+    l->bytes = io + info.workspace_bytes;
+    if (s->bytes_in_use + l->bytes > s->cfg.hbm_budget_bytes) {  // the workspace did not fit after all
+        he_plan_destroy(l->plan);
+        cudaFree(l->d_in);
+        cudaFree(l->d_out);
+        delete l;
+        return nullptr;
+    }
+    s->bytes_in_use += l->bytes;
+    s->bytes_peak = std::max(s->bytes_peak, s->bytes_in_use);
+    s->lanes.push_back(l);
+    return l;
+}
+
+// issue one batch on a stream.  Called with s->mu held.
+bool launch(Server *s, Lane *lane, std::vector<Req *> &rs) {
+    const ModelLayer &ml = s->models[lane->model].layers[lane->layer];
+    cudaStream_t st = s->streams[s->next_stream++ % s->streams.size()];
+    Batch *b = new (std::nothrow) Batch{s, lane, rs, true};
+    if (!b) return false;
+    bool ok = true;
+    for (size_t j = 0; j < rs.size() && ok; ++j)
+        ok = cudaMemcpyAsync(lane->d_in + j * ml.in_words, rs[j]->in[lane->layer], ml.in_words * sizeof(uint32_t),
+                             cudaMemcpyHostToDevice, st) == cudaSuccess;
+    ok = ok && he_plan_run(lane->plan, st) == HE_OK;
+    for (size_t j = 0; j < rs.size() && ok; ++j)
+        ok = cudaMemcpyAsync(rs[j]->out[lane->layer], lane->d_out + j * ml.out_words, ml.out_words * sizeof(uint32_t),
+                             cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    ok = ok && cudaLaunchHostFunc(st, on_batch_done, b) == cudaSuccess;
+    if (!ok) {
+        // nothing will call back: let what was issued drain, then fail the
+        // batch here
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        b->ok = false;
+        s->failed_launch.push_back(b);
+        snprintf(s->error, sizeof(s->error), "batch launch failed");
+        return false;
+    }
+    lane->busy = true;
+    ++s->inflight;
+    ++s->batches;
+    s->batched_calls += rs.size();
+    return true;
+}
+
+void finish_batch(Server *s, Batch *b) {
+    const double t = now_ms();
+    if (b->lane->busy) {
+        b->lane->busy = false;
+        --s->inflight;
+    }
+    for (Req *r : b->reqs) {
+        if (!b->ok) {
+            r->failed = true;
+            r->done = true;
+            r->t_done = t;
+            ++s->finished;
+            ++s->failed;
+            continue;
+        }
+        s->lat_layer.push_back(t - r->t_layer);
+        if (++r->layer == s->models[r->model].layers.size()) {
+            r->done = true;
+            r->t_done = t;
+            s->lat_net.push_back(t - r->t_arrive);
+            ++s->finished;
+        } else {
+            r->t_layer = t;
+            s->queues[{r->model, r->layer}].push_back(r);
+        }
+    }
+    delete b;
+}
+
+void scheduler(Server *s) {
+    cudaSetDevice(s->cfg.device);
+    for (;;) {
+        std::vector<Batch *> done;
+        {
+            std::lock_guard<std::mutex> ck(s->cb_mu);
+            done.swap(s->completed);
+        }
+        std::unique_lock<std::mutex> lk(s->mu);
+        // completions first: they free lanes and move requests to their next layer
+        done.insert(done.end(), s->failed_launch.begin(), s->failed_launch.end());
+        s->failed_launch.clear();
+        for (Batch *b : done) finish_batch(s, b);
+        if (!done.empty()) s->cv_done.notify_all();
+        if (s->stop && s->inflight == 0) break;
+        // dispatch: oldest waiting request first, each batch from one queue
+        bool progress = true;
+        while (!s->stop && progress && s->inflight < s->cfg.max_inflight) {
+            progress = false;
+            std::deque<Req *> *best = nullptr;
+            std::pair<uint32_t, uint32_t> key{0, 0};
+            double oldest = 0.0;
+            for (auto &kv : s->queues)
+                if (!kv.second.empty() && (!best || kv.second.front()->t_layer < oldest)) {
+                    best = &kv.second;
+                    key = kv.first;
+                    oldest = kv.second.front()->t_layer;
+                }
+            if (!best) break;
+            const uint32_t bucket = bucket_of((uint32_t)best->size(), s->cfg.max_batch);
+            Lane *lane = nullptr;
+            for (uint32_t b = bucket; b >= 1 && !lane; b /= 2) lane = get_lane(s, key.first, key.second, b);
+            if (!lane) break;  // budget spent and every lane busy: wait for a completion
+            std::vector<Req *> rs;
+            for (uint32_t j = 0; j < lane->bucket; ++j) {
+                rs.push_back(best->front());
+                best->pop_front();
+            }
+            launch(s, lane, rs);
+            progress = true;
+        }
+        const bool retry = !s->failed_launch.empty();
+        lk.unlock();
+        if (retry) continue;
+        std::unique_lock<std::mutex> ck(s->cb_mu);
+        if (s->completed.empty()) s->cv_sched.wait_for(ck, std::chrono::milliseconds(1));
+    }
+}
+
+}  // namespace
+
+struct he_server_s : Server {};
+
+extern "C" {
+
+he_status he_server_create(const he_server_config *cfg, he_server_t *out) {
+    if (!cfg || !out) return he_fail(HE_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (cfg->max_batch == 0 || cfg->max_batch > 8 || (cfg->max_batch & (cfg->max_batch - 1)))
+        return he_fail(HE_ERR_ARG, "max_batch must be 1, 2, 4 or 8");
+    if (cfg->streams == 0 || cfg->streams > 32) return he_fail(HE_ERR_ARG, "streams must be 1..32");
+    if (cfg->max_inflight == 0) return he_fail(HE_ERR_ARG, "max_inflight must be >= 1");
+    if (cfg->hbm_budget_bytes == 0) return he_fail(HE_ERR_ARG, "hbm_budget_bytes must be > 0");
+    he_server_s *s = new (std::nothrow) he_server_s();
+    if (!s) return he_fail(HE_ERR_NOMEM, "server");
+    s->cfg = *cfg;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(cfg->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        return he_fail(HE_ERR_CUDA, "cannot select the server's device");
+    }
+    for (uint32_t i = 0; i < cfg->streams; ++i) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+            cudaSetDevice(prev);
+            delete s;
+            return he_fail(HE_ERR_CUDA, "stream creation failed");
+        }
+        s->streams.push_back(st);
+    }
+    cudaSetDevice(prev);
+    s->sched = std::thread(scheduler, s);
+    *out = s;
+    return HE_OK;
+}
+
+he_status he_server_add_model(he_server_t s, const he_filters_t *layers, uint32_t nlayers, uint32_t *model_id) {
+    if (!s || !layers || !model_id || nlayers == 0) return he_fail(HE_ERR_ARG, "NULL argument or no layers");
+    Model m;
+    for (uint32_t i = 0; i < nlayers; ++i) {
+        const he_filters_s *f = layers[i];
+        if (!f) return he_fail(HE_ERR_ARG, "NULL layer");
+        if (f->p->device != s->cfg.device) return he_fail(HE_ERR_ARG, "layer on another device");
+        const size_t LN = (size_t)f->p->L * f->p->N;
+        ModelLayer ml{layers[i], 0, 0};
+        if (f->kind == HE_KIND_CONV) {
+            ml.in_words = (size_t)f->lay.G * 2u * LN;
+            ml.out_words = (size_t)f->lay.H * 2u * LN;
+        } else {
+            ml.in_words = 2u * LN;
+            ml.out_words = (size_t)f->fl.P_fc * 2u * LN;
+        }
+        // a batch-1 buffer set (inputs, outputs, and a workspace of about
+        // the same size) must fit the budget, or the layer could never run
+        if (2u * (ml.in_words + ml.out_words) * sizeof(uint32_t) > s->cfg.hbm_budget_bytes)
+            return he_fail(HE_ERR_ARG, "hbm_budget_bytes is too small for one of the model's layers");
+        m.layers.push_back(ml);
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    *model_id = (uint32_t)s->models.size();
+    s->models.push_back(std::move(m));
+    return HE_OK;
+}
+
+he_status he_server_submit(he_server_t s, uint32_t model_id, const uint32_t *const *h_in, uint32_t *const *h_out,
+                           uint64_t *ticket) {
+    if (!s || !h_in || !h_out || !ticket) return he_fail(HE_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (model_id >= s->models.size()) return he_fail(HE_ERR_ARG, "unknown model");
+    if (s->stop) return he_fail(HE_ERR_ARG, "server is stopping");
+    const size_t nl = s->models[model_id].layers.size();
+    for (size_t i = 0; i < nl; ++i)
+        if (!h_in[i] || !h_out[i]) return he_fail(HE_ERR_ARG, "NULL layer buffer");
+    Req *r = new (std::nothrow) Req();
+    if (!r) return he_fail(HE_ERR_NOMEM, "request");
+    r->id = s->next_id++;
+    r->model = model_id;
+    r->in.assign(h_in, h_in + nl);
+    r->out.assign(h_out, h_out + nl);
+    r->t_arrive = r->t_layer = now_ms();
+    s->reqs[r->id] = r;
+    s->queues[{model_id, 0}].push_back(r);
+    ++s->submitted;
+    *ticket = r->id;
+    s->cv_sched.notify_one();
+    return HE_OK;
+}
+
+he_status he_server_wait(he_server_t s, uint64_t ticket, uint32_t timeout_ms, he_request_stats *st) {
+    if (!s) return he_fail(HE_ERR_ARG, "NULL argument");
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return he_fail(HE_ERR_ARG, "unknown ticket");
+    Req *r = it->second;
+    if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [r] { return r->done; }))
+        return he_fail(HE_ERR_TIMEOUT, "request not finished within the timeout");
+    if (st) {
+        st->arrive_ms = r->t_arrive;
+        st->done_ms = r->t_done;
+        st->latency_ms = r->t_done - r->t_arrive;
+    }
+    const bool failed = r->failed;
+    s->reqs.erase(it);
+    delete r;
+    if (failed) return he_fail(HE_ERR_CUDA, "the request's batch failed");
+    return HE_OK;
+}
+
+he_status he_server_report(he_server_t s, he_server_report_t *rep) {
+    if (!s || !rep) return he_fail(HE_ERR_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    memset(rep, 0, sizeof(*rep));
+    rep->submitted = s->submitted;
+    rep->finished = s->finished;
+    rep->failed = s->failed;
+    rep->batches = s->batches;
+    rep->batched_calls = s->batched_calls;
+    rep->lanes = s->lanes.size();
+    rep->bytes_in_use = s->bytes_in_use;
+    rep->bytes_peak = s->bytes_peak;
+    return HE_OK;
+}
+
+he_status he_server_latencies(he_server_t s, int which, double *out_ms, uint64_t cap, uint64_t *n) {
+    if (!s || !n || (which != 0 && which != 1)) return he_fail(HE_ERR_ARG, "bad argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const std::vector<double> &v = which == 0 ? s->lat_net : s->lat_layer;
+    *n = v.size();
+    if (out_ms)
+        for (size_t i = 0; i < v.size() && i < cap; ++i) out_ms[i] = v[i];
+    return HE_OK;
+}
+
+void he_server_destroy(he_server_t s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        // requests still queued never start; in-flight batches finish first
+        for (auto &kv : s->queues) kv.second.clear();
+        s->cv_sched.notify_one();
+    }
+    s->sched.join();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(s->cfg.device);
+    for (cudaStream_t st : s->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (Lane *l : s->lanes) {
+        he_plan_destroy(l->plan);
+        cudaFree(l->d_in);
+        cudaFree(l->d_out);
+        delete l;
+    }
+    for (auto &kv : s->reqs) delete kv.second;
+    cudaSetDevice(prev);
+    delete s;
+}
+
+}  // extern "C"

@@ -61,6 +61,20 @@ class he_plan_info(ctypes.Structure):
                [("workspace_bytes", ctypes.c_uint64), ("tuning", he_plan_tuning)]
 
 
+class he_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("streams", ctypes.c_uint32), ("max_inflight", ctypes.c_uint32)]
+
+
+class he_request_stats(ctypes.Structure):
+    _fields_ = [("arrive_ms", ctypes.c_double), ("done_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class he_server_report_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "finished", "failed", "batches", "batched_calls",
+                                               "lanes", "bytes_in_use", "bytes_peak")]
+
+
 _lib = None
 
 _vp, _u32, _i32, _sz = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t
@@ -92,10 +106,18 @@ _SIGS = {
     "he_plan_query": [_vp, ctypes.POINTER(he_plan_info), _vp],
     "he_plan_check": [_vp],
     "he_plan_destroy": [_vp],
+    "he_server_create": [ctypes.POINTER(he_server_config), ctypes.POINTER(_vp)],
+    "he_server_add_model": [_vp, ctypes.POINTER(_vp), _u32, ctypes.POINTER(_u32)],
+    "he_server_submit": [_vp, _u32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_uint64)],
+    "he_server_wait": [_vp, ctypes.c_uint64, _u32, ctypes.POINTER(he_request_stats)],
+    "he_server_report": [_vp, ctypes.POINTER(he_server_report_t)],
+    "he_server_latencies": [_vp, _i32, ctypes.POINTER(ctypes.c_double), ctypes.c_uint64,
+                            ctypes.POINTER(ctypes.c_uint64)],
+    "he_server_destroy": [_vp],
     "he_sync": [_vp],
     "he_last_error": [],
 }
-_VOID = {"he_params_destroy", "he_filters_destroy", "he_plan_destroy"}
+_VOID = {"he_params_destroy", "he_filters_destroy", "he_plan_destroy", "he_server_destroy"}
 
 
 def lib() -> ctypes.CDLL:
@@ -329,6 +351,56 @@ def he_plan_check(plan: int) -> None:
 
 def he_plan_destroy(plan: int) -> None:
     lib().he_plan_destroy(plan)
+
+
+def he_server_create(device: int = 0, hbm_budget_bytes: int = 120 << 30, max_batch: int = 8, streams: int = 8,
+                     max_inflight: int = 16) -> int:
+    cfg = he_server_config(device, hbm_budget_bytes, max_batch, streams, max_inflight)
+    out = _vp()
+    _check(lib().he_server_create(ctypes.byref(cfg), ctypes.byref(out)))
+    return out.value
+
+
+def he_server_add_model(s: int, layers) -> int:
+    arr = (_vp * len(layers))(*layers)
+    mid = _u32()
+    _check(lib().he_server_add_model(s, arr, len(layers), ctypes.byref(mid)))
+    return mid.value
+
+
+def he_server_submit(s: int, model_id: int, h_in, h_out) -> int:
+    """h_in, h_out: per-layer HOST buffers (addresses or objects with
+    data_ptr(), e.g. pinned torch tensors)."""
+    ins = (_vp * len(h_in))(*[_ptr(x) for x in h_in])
+    outs = (_vp * len(h_out))(*[_ptr(x) for x in h_out])
+    t = ctypes.c_uint64()
+    _check(lib().he_server_submit(s, model_id, ins, outs, ctypes.byref(t)))
+    return t.value
+
+
+def he_server_wait(s: int, ticket: int, timeout_ms: int = 60000) -> dict:
+    st = he_request_stats()
+    _check(lib().he_server_wait(s, ticket, timeout_ms, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in he_request_stats._fields_}
+
+
+def he_server_report(s: int) -> dict:
+    r = he_server_report_t()
+    _check(lib().he_server_report(s, ctypes.byref(r)))
+    return {n: getattr(r, n) for n, _ in he_server_report_t._fields_}
+
+
+def he_server_latencies(s: int, which: int) -> np.ndarray:
+    n = ctypes.c_uint64()
+    _check(lib().he_server_latencies(s, which, None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.float64)
+    _check(lib().he_server_latencies(s, which, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n.value,
+                                     ctypes.byref(n)))
+    return out[: n.value]
+
+
+def he_server_destroy(s: int) -> None:
+    lib().he_server_destroy(s)
 
 
 def he_sync(stream=None) -> None:

@@ -159,3 +159,12 @@ def test_plan_tuning_default_and_validation(he):
         with pytest.raises(he.HEError) as ei:
             he.he_plan_create_tuned([(0, 16, he.HE_COEFF, 4096, 1)], bad)
         assert ei.value.status == he.HE_ERR_ARG and "tuning" in str(ei.value)
+
+
+def test_server_config_validation(he):
+    # refused before any device work
+    for kw in (dict(max_batch=3), dict(max_batch=16), dict(streams=0), dict(max_inflight=0),
+               dict(hbm_budget_bytes=0)):
+        with pytest.raises(he.HEError) as ei:
+            he.he_server_create(**kw)
+        assert ei.value.status == he.HE_ERR_ARG
