@@ -579,6 +579,177 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------
+# serving: Poisson arrivals of whole inferences into the request loop
+# ----------------------------------------------------------------------------
+
+SERVING = dict(rate=200.0, mix=(("plain20_c10", 0.5), ("plain20_c100_wide4", 0.5)), budget=120 << 30,
+               max_batch=8, streams=8, max_inflight=16, pool=24, input_sets=4)
+
+
+def run_serving(args, rank, world, device):
+    """Inferences of two networks (plain-20 CIFAR-10 shape on N = 8192 with 3
+    limbs, wide x4 CIFAR-100 shape on N = 16384 with 6 limbs; one ciphertext
+    per request) arrive as a Poisson process and are served by the library's
+    request loop (he_server_*): continuous batching per (model, layer), HBM
+    budget admission, host->device and device->host copies included.
+    Latency is measured from each request's scheduled arrival."""
+    import queue
+    import threading
+    import torch
+    from paper_2409_05205_gb300 import build
+    from paper_2409_05205_gb300 import he as H
+    from paper_2409_05205_gb300 import synth
+    build.build()
+    cfg = SERVING
+    seconds = args.serve_seconds
+    models, params, all_banks = [], [], []
+    for mi, (name, _) in enumerate(cfg["mix"]):
+        wl = workload(name)
+        calls = synth.call_list(wl)
+        N, L = calls[0]["N"], calls[0]["L"]
+        p = H.he_params_create(N, L, None, wl["t"], device)
+        params.append(p)
+        ps = H.he_params_primes(p, L)
+        banks, geo = [], []
+        for i, c in enumerate(calls):
+            if c["kind"] == "conv":
+                F = synth.conv_weights(SEED, f"s{mi}w{i}", c["co"], c["ci"], 3, 3, wl["wlo"], wl["whi"])
+                banks.append(H.he_pack_filters(p, c, F))
+                lay = H.he_conv_layout_query(p, c)
+                geo.append((lay["G"] * 2 * L * N, lay["H"] * 2 * L * N))
+            else:
+                W = synth.fc_weights(SEED, f"s{mi}w{i}", c["n_out"], c["n_in"], wl["wlo"], wl["whi"])
+                banks.append(H.he_pack_fc(p, c["n_in"], c["n_out"], W, None))
+                fl = H.he_fc_layout_query(p, c["n_in"], c["n_out"])
+                geo.append((2 * L * N, fl["P_fc"] * 2 * L * N))
+        all_banks += banks
+        # read-only input sets shared by requests; a pool of output sets
+        ins = []
+        for k in range(cfg["input_sets"]):
+            ins.append([torch.from_numpy(synth.residues(SEED + k, f"s{mi}x{i}", (g[0] // (L * N), L, N), ps)
+                                         .view(np.int32).ravel()).pin_memory() for i, g in enumerate(geo)])
+        pool = queue.Queue()
+        for k in range(cfg["pool"]):
+            pool.put([torch.empty(g[1], dtype=torch.int32).pin_memory() for g in geo])
+        models.append(dict(name=name, banks=banks, geo=geo, ins=ins, pool=pool, layers=len(calls),
+                           h2d=sum(g[0] for g in geo) * 4, d2h=sum(g[1] for g in geo) * 4))
+    # the arrival schedule: exponential gaps, model by its share (seeded)
+    rate = args.serve_rate
+    n_max = int(rate * seconds * 1.5) + 100
+    u = (synth.u64(SEED, "serve/gaps", n_max) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    times = np.cumsum(-np.log1p(-u) / rate)
+    times = times[times < seconds]
+    pick = (synth.u64(SEED, "serve/model", len(times)) >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    which = np.where(pick < cfg["mix"][0][1], 0, 1)
+    served = serve_run(H, models, times, which, device, cfg["budget"], cfg["max_batch"], cfg["streams"],
+                       cfg["max_inflight"], cfg["input_sets"])
+    plain = serve_run(H, models, times, which, device, cfg["budget"], 1, 1, 1, cfg["input_sets"])
+    for f in all_banks:
+        H.he_filters_destroy(f)
+    for p in params:
+        H.he_params_destroy(p)
+    n = served["n"]
+    h2d = sum(models[int(mi)]["h2d"] for mi in which) / max(1, n)
+    d2h = sum(models[int(mi)]["d2h"] for mi in which) / max(1, n)
+    return {
+        "metric": METRIC, "value": served["value"], "unit": "layers/s", "n_gpus": world, "steps": n,
+        "warmup": 2 * 15 * len(models), "ms_per_step": served["elapsed_s"] * 1e3 / max(1, n),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 (exact residues mod 30-bit primes)", "data": "synthetic",
+        "config": {"workload": "serving", "arrivals": f"Poisson {rate:.0f}/s for {seconds:.0f} s",
+                   "mix": {m["name"]: share for m, (_, share) in zip(models, cfg["mix"])},
+                   "rings": ["N=8192,L=3", "N=16384,L=6"], "B": 1,
+                   "hbm_budget_gb": cfg["budget"] / 2**30, "max_batch": cfg["max_batch"],
+                   "streams": cfg["streams"], "parallelism": f"replicas x{world}"},
+        "serving": served["report"],
+        "plain_form": dict(plain["report"], value=plain["value"], unit="layers/s",
+                           how="the same arrivals served one batch of one request at a time on one stream"),
+        "roofline": None,
+        "e2e": {"value": served["value"], "unit": "layers/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "how": "the serving run itself: host buffers in, host buffers out"},
+        "gpu_launches": None,
+        "clocks": served["clocks"],
+    }
+
+
+def serve_run(H, models, times, which, device, budget, max_batch, streams, max_inflight, input_sets):
+    """One pass of the arrival schedule through a server with this config."""
+    import queue
+    import threading
+    srv = H.he_server_create(device, budget, max_batch, streams, max_inflight)
+    mids = [H.he_server_add_model(srv, m["banks"]) for m in models]
+    # warm-up: bursts that make the server build every batch size's buffers
+    for _ in range(2):
+        tk = []
+        for mi, m in enumerate(models):
+            for k in range(15):
+                outs = m["pool"].get()
+                tk.append((H.he_server_submit(srv, mids[mi], m["ins"][k % input_sets], outs), mi, outs))
+        for t, mi, outs in tk:
+            H.he_server_wait(srv, t, 600000)
+            models[mi]["pool"].put(outs)
+    warm = H.he_server_report(srv)
+    lat_layer0 = len(H.he_server_latencies(srv, 1))
+    done_q = queue.Queue()
+    waits = [0.0]
+
+    def submitter(t0):
+        for k, (ta, mi) in enumerate(zip(times, which)):
+            m = models[int(mi)]
+            dt = t0 + ta - time.monotonic()
+            if dt > 0:
+                time.sleep(dt)
+            w0 = time.monotonic()
+            outs = m["pool"].get()
+            waits[0] = max(waits[0], time.monotonic() - w0)
+            tk = H.he_server_submit(srv, mids[int(mi)], m["ins"][k % input_sets], outs)
+            done_q.put((tk, int(mi), outs, (t0 + ta) * 1e3))
+        done_q.put(None)
+
+    clocks = ClockSampler(device)
+    clocks.start()
+    time.sleep(0.3)
+    t0 = time.monotonic() + 0.05
+    th = threading.Thread(target=submitter, args=(t0,))
+    th.start()
+    lat_sched, per_model = [], [[], []]
+    layers_done, t_last = 0, t0 * 1e3
+    while True:
+        item = done_q.get()
+        if item is None:
+            break
+        tk, mi, outs, t_arr = item
+        st = H.he_server_wait(srv, tk, 600000)
+        models[mi]["pool"].put(outs)
+        lat = st["done_ms"] - t_arr
+        lat_sched.append(lat)
+        per_model[mi].append(lat)
+        layers_done += models[mi]["layers"]
+        t_last = max(t_last, st["done_ms"])
+    th.join()
+    clk = clocks.stop()
+    elapsed_s = (t_last - t0 * 1e3) * 1e-3
+    rep = H.he_server_report(srv)
+    lat_layer = H.he_server_latencies(srv, 1)[lat_layer0:]
+    H.he_server_destroy(srv)
+    n = len(lat_sched)
+    pct = lambda v, q: float(np.percentile(v, q)) if len(v) else None
+    nb = rep["batches"] - warm["batches"]
+    ncalls = rep["batched_calls"] - warm["batched_calls"]
+    report = {"inferences": n, "inferences_per_s": n / elapsed_s,
+              "network_latency_ms": {"p50": pct(lat_sched, 50), "p99": pct(lat_sched, 99),
+                                     "from": "scheduled arrival to the last layer's outputs on the host"},
+              "network_latency_ms_by_model": {m["name"]: {"p50": pct(v, 50), "p99": pct(v, 99)}
+                                              for m, v in zip(models, per_model)},
+              "layer_latency_ms": {"p50": pct(lat_layer, 50), "p99": pct(lat_layer, 99),
+                                   "from": "entry into the layer's queue to its outputs on the host"},
+              "batches": nb, "mean_batch": ncalls / max(1, nb), "hbm_bytes_peak": rep["bytes_peak"],
+              "failed": rep["failed"], "max_submit_wait_s": waits[0],
+              "server": {"max_batch": max_batch, "streams": streams, "max_inflight": max_inflight}}
+    return {"n": n, "elapsed_s": elapsed_s, "value": layers_done / elapsed_s, "report": report, "clocks": clk}
+
+
+# ----------------------------------------------------------------------------
 
 def main():
     ap = argparse.ArgumentParser()
@@ -588,6 +759,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="plain20_c10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     rank = int(os.environ.get("RANK", 0))
@@ -603,6 +776,11 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload == "serving":
+        res = run_serving(args, rank, world, local)
+        if rank == 0:
+            print(json.dumps(res))
+        return
     res = run_ours(args, rank, world, local)
     if rank == 0:
         if not args.no_cpu_baseline:
