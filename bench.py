@@ -134,7 +134,8 @@ class Model:
             p = arm.params[(c["N"], c["L"])]
             if c["kind"] == "conv":
                 F = synth.conv_weights(SEED + rep, f"w{i}", c["co"], c["ci"], 3, 3, wl["wlo"], wl["whi"])
-                self.banks.append(H.he_pack_filters(p, c, F))
+                # batched calls (B >= 4) get the tensor-core bank layout where the shape allows
+                self.banks.append(H.he_pack_filters_for_batch(p, c, F, c["B"]))
             else:
                 W = synth.fc_weights(SEED + rep, f"w{i}", c["n_out"], c["n_in"], wl["wlo"], wl["whi"])
                 Bv = synth.ints(SEED + rep, f"b{i}", (c["n_out"],), -1000, 1000)
@@ -263,13 +264,16 @@ class Arm:
         return ch_bytes, ntt_bytes, bfly
 
     def mac_bytes(self, split):
-        """Algorithmic bytes of one k_plan_mac launch: for every split-form
-        Conv call, its NTT-domain weight bank (co * G * L * N words) and its
-        transformed inputs (B * G * 2 * L * N words), each read once."""
+        """Algorithmic bytes of one launch of the MAC phase (k_plan_mac for
+        split-form calls, k_tc_mac for tensor-core calls): for every such Conv
+        call, its NTT-domain weight bank (co * G * L * N words) and its
+        transformed inputs (B * G * 2 * L * N words) read once, and its folded
+        channel sums (L * 2B * co * N/s words) written once."""
         tot = 0
         for c, g, sp in zip(self.calls, self.geo, split):
             if sp and c["kind"] == "conv":
-                tot += g["wbytes"] + c["B"] * g["lay"]["G"] * 2 * c["L"] * c["N"] * 4
+                lay, L, N, B = g["lay"], c["L"], c["N"], c["B"]
+                tot += g["wbytes"] + B * lay["G"] * 2 * L * N * 4 + L * 2 * B * c["co"] * lay["M"] * 4
         return tot
 
     def free(self):
@@ -411,7 +415,10 @@ def run_ours(args, rank, world, device):
     e2e = run_e2e(arm, args, stream)
 
     ch_bytes, ntt_bytes, bfly = arm.algorithmic()
-    mac_bytes = arm.mac_bytes(info["split"])
+    mac_bytes = arm.mac_bytes(info["form"])
+    kinds = sorted({int(v) for v in info["form"] if v})
+    mac_name = " + ".join({1: "k_plan_mac", 2: "k_tc_mac"}[k] for k in kinds) or "none"
+    mac_what = " / ".join({1: "split-form (scalar)", 2: "tensor-core"}[k] for k in kinds) or "split-form"
     hbm, peak_src = _peaks()
     mac_avg = mac_b2b_ms
     fin_avg = float(np.mean(fin_ms))
@@ -437,8 +444,8 @@ def run_ours(args, rank, world, device):
                        "kernel_ms_per_step": {"input_ntt": plain_ntt_ms / k_plain,
                                               "channel": plain_ch_ms / k_plain}},
         "speedup_vs_plain_form": (plain_ms / k_plain) / (graph_ms / K),
-        "roofline": {"kernel": "k_plan_mac: NTT-domain channel MAC of every split-form Conv layer "
-                               "(weights + transformed inputs read once)",
+        "roofline": {"kernel": mac_name + ": NTT-domain channel MAC of every " + mac_what +
+                               " Conv layer (weights + transformed inputs read once, folded sums written once)",
                      "bound": "hbm", "achieved": mac_gbs, "peak": hbm, "unit": "GB/s",
                      "frac": mac_gbs / hbm, "peak_source": peak_src + " (hbm_gbs burst copy)",
                      "algorithmic_bytes": mac_bytes, "avg_launch_ms": mac_avg, "launches": k_phase,
@@ -446,14 +453,14 @@ def run_ours(args, rank, world, device):
         "kernels": {"k_plan_ntt": {"avg_launch_ms": ntt_avg, "butterflies": bfly,
                                    "gbfly_per_s": bfly / (ntt_avg * 1e-3) / 1e9,
                                    "bytes": ntt_bytes, "gbs": ntt_bytes / (ntt_avg * 1e-3) / 1e9},
-                    "k_plan_mac": {"avg_launch_ms": mac_avg, "bytes": mac_bytes, "gbs": mac_gbs,
+                    "mac_phase": {"kernels": mac_name, "avg_launch_ms": mac_avg, "bytes": mac_bytes, "gbs": mac_gbs,
                                    "after_ntt_ms": float(np.mean(mac_ms)),
                                    "timing": f"{k_phase} launches back to back, replicas rotated, CUDA events"},
                     "finish_and_fc": {"avg_launch_ms": fin_avg,
                                       "what": "k_plan_fin on the stream, k_plan_fc on the side stream"},
                     "step_bytes": ch_bytes,
                     "step_gbs_graph": ch_bytes / (graph_ms / K * 1e-3) / 1e9},
-        "plan": {k: v for k, v in info.items() if k != "split"},
+        "plan": {k: v for k, v in info.items() if k not in ("split", "form")},
         "tuning": {"chosen": arm.tuning, "how": "he_plan_autotune: whole-plan runs timed per candidate, "
                                                   "one knob at a time"},
         "e2e": e2e,

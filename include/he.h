@@ -154,6 +154,23 @@ he_status he_fc_layout_query(he_params_t p, uint32_t n_in, uint32_t n_out, he_fc
 he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w,
                           he_filters_t *out);
 
+/* he_pack_filters for a layer that will mostly see calls of about B
+ * ciphertexts.  The bank holds the same values; only their order in device
+ * memory differs.  For B >= 4 and a layer whose per-block contraction
+ * (Sec. III-A: channel n's valid slots of one block of s NTT slots are
+ * sum over the G*s input words of that block of weight x input) has
+ * K = G*s in [32, 256], a multiple of 16, with s >= 8 and co a multiple of
+ * 64, the bank is laid out per (limb, block, 64 channels) as a K-major
+ * matrix, and plan calls of up to 8 ciphertexts on it run the channel sum
+ * on the tensor cores (exact: 8-bit limbs in fp16, fp32 sums below 2^24).
+ * Single calls (he_conv_layer) and plan calls of more than 8 ciphertexts
+ * read the same bank with the scalar kernels.  Any other B or shape gives
+ * he_pack_filters' bank.  Results are bit-identical either way.  Blocking. */
+he_status he_pack_filters_for_batch(he_params_t p, const he_conv_desc *d, const int8_t *w,
+                                    uint32_t B, he_filters_t *out);
+/* *tc = 1 if f is a Conv bank in the tensor-core layout, else 0. */
+he_status he_filters_tensor_core(he_filters_t f, uint32_t *tc);
+
 /* Server model load for one FC layer (Sec. III-B eq. (w(x) formula) and
  * d(X) of Theorem 1).
  *   W: HOST int8 [n_out][n_in], row-major.
@@ -335,10 +352,14 @@ typedef struct {
     uint32_t split_calls;     /* Conv calls in the split form */
     uint64_t workspace_bytes; /* device workspace the plan owns */
     he_plan_tuning tuning;    /* the tuning the plan was built with */
+    uint32_t tc_items;        /* tensor-core MAC items (call x limb x run of slot blocks) */
+    uint32_t tc_ctas;         /* persistent CTAs of the tensor-core MAC kernel */
+    uint32_t tc_calls;        /* Conv calls on the tensor-core MAC kernel */
 } he_plan_info;
-/* Fills *info; if `split` is not NULL, also split[i] = 1 for each call i
- * (of the ncalls given to he_plan_create) that takes the split form, else
- * 0.  Host only, non-blocking. */
+/* Fills *info; if `split` is not NULL, also split[i] for each call i (of
+ * the ncalls given to he_plan_create): 1 if it takes the split form with the
+ * scalar MAC kernel, 2 if it takes the tensor-core MAC kernel, else 0 (one
+ * fused channel kernel).  Host only, non-blocking. */
 he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split);
 /* Reports whether a bounded device-side wait of an earlier run gave up
  * (HE_ERR_TIMEOUT; the outputs of that run are then unspecified) and clears

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhe.so")
-SOURCES = ["he_host.cu", "he_kernels.cu", "he_noalloc.cu", "he_server.cu"]
+SOURCES = ["he_host.cu", "he_kernels.cu", "he_noalloc.cu", "he_server.cu", "he_tc.cu"]
 HEADERS = ["he_internal.h", os.path.join("..", "..", "include", "he.h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -15,6 +15,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "he_internal.h"
 
 namespace {
@@ -392,7 +394,8 @@ he_status he_fc_layout_query(he_params_t p, uint32_t n_in, uint32_t n_out, he_fc
     return fc_layout(p, n_in, n_out, out);
 }
 
-he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w, he_filters_t *out) {
+static he_status pack_conv(he_params_t p, const he_conv_desc *d, const int8_t *w, uint32_t batch,
+                           he_filters_t *out) {
     if (!p || !d || !w || !out) return fail(HE_ERR_ARG, "NULL argument");
     if (need_device(p) != HE_OK) return HE_ERR_ARG;
     *out = nullptr;
@@ -411,6 +414,7 @@ he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w,
     f->lay = lay;
     f->logTS = bank_tile_log(p->logN, lay.s, lay.G);
     f->lcs = bank_chunk_log(f->logTS, lay.s, lay.G);
+    f->tc = (batch >= kTcMinBatch && tc_shape_ok(lay.s, lay.G, d->co)) ? 1u : 0u;
     f->nc = std::min(d->co, std::max(1u, kMacItemWords / (lay.G << f->logTS)));
     f->bank_bytes = (size_t)d->co * p->L * lay.G * p->N * sizeof(uint32_t);
     const size_t wbytes = (size_t)d->co * d->ci * d->fh * d->fw;
@@ -424,7 +428,7 @@ he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w,
     }
     e = cudaMalloc(&d_w, wbytes);
     if (e == cudaSuccess) e = cudaMemcpy(d_w, w, wbytes, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = he_launch_pack_conv(p->ring, d_w, *d, lay, f->logTS, f->lcs, f->bank, 0);
+    if (e == cudaSuccess) e = he_launch_pack_conv(p->ring, d_w, *d, lay, f->logTS, f->lcs, f->tc, f->bank, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_w);
     if (e != cudaSuccess) {
@@ -432,6 +436,22 @@ he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w,
         return cuda_fail(e, "pack filters");
     }
     *out = f;
+    return HE_OK;
+}
+
+he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w, he_filters_t *out) {
+    return pack_conv(p, d, w, 1, out);
+}
+
+he_status he_pack_filters_for_batch(he_params_t p, const he_conv_desc *d, const int8_t *w, uint32_t B,
+                                    he_filters_t *out) {
+    if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
+    return pack_conv(p, d, w, B, out);
+}
+
+he_status he_filters_tensor_core(he_filters_t f, uint32_t *tc) {
+    if (!f || !tc) return fail(HE_ERR_ARG, "NULL argument");
+    *tc = f->kind == HE_KIND_CONV ? f->tc : 0u;
     return HE_OK;
 }
 
@@ -518,7 +538,7 @@ he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int
         if (e != cudaSuccess) return cuda_fail(e, "input NTT");
         x = (const uint32_t *)p->ws;
     }
-    cudaError_t e = he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, f->bank, x, d_out, out_mode, B, st);
+    cudaError_t e = he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, f->tc, f->bank, x, d_out, out_mode, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "conv kernel");
     return HE_OK;
 }
@@ -590,6 +610,129 @@ he_status check_tuning(const he_plan_tuning &t) {
         return fail(HE_ERR_ARG, "tuning: fused_max_nj must be 2, 4, 8 or 16");
     return HE_OK;
 }
+}  // namespace
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver, looked up once per process
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Call table, tensor maps and work items of the tensor-core MAC kernel.
+// Items are (call, limb, run of blocks) of about 256 KB of weights, placed
+// longest first onto the least loaded of one persistent CTA per SM.
+cudaError_t build_tc_tables(he_plan_s *pl, const std::vector<CallDesc> &descs, const he_layer_call *calls,
+                            const std::vector<uint32_t> &tc_calls) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return cudaErrorNotSupported;
+    std::vector<TcCall> tcs(tc_calls.size());
+    std::vector<std::pair<double, TcItem>> all;
+    for (size_t t = 0; t < tc_calls.size(); ++t) {
+        const CallDesc &cd = descs[tc_calls[t]];
+        const ConvGeo &g = cd.g;
+        const uint32_t B = calls[tc_calls[t]].B;
+        TcCall &c = tcs[t];
+        memset(&c, 0, sizeof(c));
+        c.bank = g.bank;
+        c.z = cd.z;
+        c.K = g.G * g.s;
+        c.s = g.s;
+        c.logs = g.logs;
+        c.G = g.G;
+        c.co = g.co;
+        c.M = g.M;
+        c.ncols = g.ncols;
+        c.xbytes = g.s * 2u * g.G * B * 4u;
+        for (uint32_t l = 0; l < g.L; ++l) {
+            const LimbK &K = cd.limb[l];
+            TcLimb &tl = c.limb[l];
+            tl.q = K.q;
+            tl.q2 = K.q2;
+            tl.r32 = K.r32;
+            tl.r32s = K.r32s;
+            tl.ones = K.ones;
+            tl.w16 = (uint32_t)((1ull << 16) % K.q);
+            tl.w16s = (uint32_t)(((uint64_t)tl.w16 << 32) / K.q);
+        }
+        // inputs [B][G][2][L][N] as a 5-D tensor, innermost first; one box is
+        // the s slots of one block of one limb for every (b, g, j)
+        const cuuint64_t dims[5] = {g.N, g.L, 2, g.G, B};
+        const cuuint64_t strides[4] = {(cuuint64_t)g.N * 4u, (cuuint64_t)g.L * g.N * 4u,
+                                       (cuuint64_t)2u * g.L * g.N * 4u, (cuuint64_t)g.G * 2u * g.L * g.N * 4u};
+        const cuuint32_t box[5] = {g.s, 1, 2, g.G, B};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        CUtensorMap m;
+        const CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, const_cast<uint32_t *>(g.x), dims, strides,
+                               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        static_assert(sizeof(CUtensorMap) == sizeof(c.xmap), "tensor map size");
+        memcpy(c.xmap, &m, sizeof(m));
+        const uint32_t nch = g.co / kTcRows;
+        const uint32_t nb = std::max(1u, std::min(g.M, 1024u / (nch * c.K)));
+        for (uint32_t l = 0; l < g.L; ++l)
+            for (uint32_t b0 = 0; b0 < g.M; b0 += nb) {
+                const uint32_t n = std::min(nb, g.M - b0);
+                all.push_back({(double)n * nch * c.K, TcItem{(uint32_t)t, l, b0, n}});
+            }
+    }
+    std::stable_sort(all.begin(), all.end(),
+                     [](const std::pair<double, TcItem> &x, const std::pair<double, TcItem> &y) { return x.first > y.first; });
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device);
+    if (e != cudaSuccess) return e;
+    const uint32_t nctas = (uint32_t)std::min<size_t>(all.size(), (size_t)std::max(1, sms));
+    std::vector<std::vector<TcItem>> per(nctas);
+    std::vector<std::pair<double, uint32_t>> heap;
+    for (uint32_t b = 0; b < nctas; ++b) heap.push_back({0.0, b});
+    auto cmp = [](const std::pair<double, uint32_t> &x, const std::pair<double, uint32_t> &y) {
+        return x.first > y.first || (x.first == y.first && x.second > y.second);
+    };
+    std::make_heap(heap.begin(), heap.end(), cmp);
+    for (auto &it : all) {
+        std::pop_heap(heap.begin(), heap.end(), cmp);
+        auto &h = heap.back();
+        per[h.second].push_back(it.second);
+        h.first += it.first;
+        std::push_heap(heap.begin(), heap.end(), cmp);
+    }
+    std::vector<TcItem> items;
+    std::vector<uint32_t> offs(nctas + 1, 0);
+    for (uint32_t b = 0; b < nctas; ++b) {
+        offs[b] = (uint32_t)items.size();
+        items.insert(items.end(), per[b].begin(), per[b].end());
+    }
+    offs[nctas] = (uint32_t)items.size();
+    pl->n_tc = (uint32_t)items.size();
+    pl->tc_ctas = nctas;
+    e = cudaMalloc(&pl->d_tc_calls, sizeof(TcCall) * tcs.size());
+    if (e == cudaSuccess) e = cudaMemcpy(pl->d_tc_calls, tcs.data(), sizeof(TcCall) * tcs.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_tc_items, sizeof(TcItem) * items.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pl->d_tc_items, items.data(), sizeof(TcItem) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_tc_offs, sizeof(uint32_t) * offs.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(pl->d_tc_offs, offs.data(), sizeof(uint32_t) * offs.size(), cudaMemcpyHostToDevice);
+    return e;
+}
+
 }  // namespace
 
 he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t *out) {
@@ -671,6 +814,13 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             g.nc = std::min(f->desc.co, std::max(1u, (tu.mac_item_kb * 256u) / (lay.G << f->logTS)));
             // bank interleave and tile must match the MAC kernel's
             if (cd.split && ((1u << f->lcs) != g.cs || f->logTS != split_tile_log(f->lcs))) cd.split = 0;
+            // a tensor-core bank: the tensor-core MAC kernel for up to 16
+            // columns, then the finishing kernel; more columns take the fused form
+            g.tc = f->tc;
+            if (f->tc) {
+                cd.split = 0;
+                cd.zt = g.ncols <= kTcCols ? 1u : 0u;
+            }
             nin = (size_t)c.B * lay.G * 2u * r.L * r.N;
             nout = (size_t)c.B * lay.H * 2u * r.L * r.N;
         } else {
@@ -696,7 +846,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         ranges.push_back({(uintptr_t)c.d_out, (uintptr_t)(c.d_out + nout), true, i});
     }
     for (uint32_t i = 0; i < ncalls; ++i)
-        if (descs[i].split) {
+        if (descs[i].split || descs[i].zt) {
             const ConvGeo &g = descs[i].g;
             z_off[i] = ws_words;
             ws_words += (size_t)g.L * g.ncols * g.co * g.M;
@@ -720,7 +870,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         delete pl;
         return fail(HE_ERR_NOMEM, "plan");
     }
-    for (uint32_t i = 0; i < ncalls; ++i) pl->split[i] = descs[i].split ? 1 : 0;
+    for (uint32_t i = 0; i < ncalls; ++i) pl->split[i] = descs[i].split ? 1 : (descs[i].zt ? 2 : 0);
     pl->tuning = tu;
     pl->ws_bytes = ws_words * sizeof(uint32_t);
     if (ws_words) e = cudaMalloc(&pl->ws, ws_words * sizeof(uint32_t));
@@ -734,6 +884,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
     // work items, each list ordered longest first
     using Costed = std::pair<double, ChanItem>;
     std::vector<std::pair<double, NttItem>> ntt_cost, fc_cost;
+    std::vector<uint32_t> tc_calls;
     std::vector<Costed> chan[4], mac[kMacClasses], fin;
     for (uint32_t i = 0; i < ncalls; ++i) {
         CallDesc &cd = descs[i];
@@ -754,7 +905,14 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             const size_t npoly = (size_t)calls[i].B * g.G * 2u * g.L;
             for (size_t pidx_ = 0; pidx_ < npoly; ++pidx_) ntt_cost.push_back({N * logN, NttItem{i, (uint32_t)pidx_}});
         }
-        if (cd.split) {
+        if (cd.zt) {
+            cd.z = pl->ws + z_off[i];
+            tc_calls.push_back(i);
+            const double fcost = 3.0 * (N / 2.0) * g.logM + N;
+            for (uint32_t h = 0; h < g.H; ++h)
+                for (uint32_t l = 0; l < g.L; ++l)
+                    for (uint32_t col = 0; col < g.ncols; ++col) fin.push_back({fcost, ChanItem{i, h, l, col}});
+        } else if (cd.split) {
             cd.z = pl->ws + z_off[i];
             const int cls = he_mac_class(g.G, g.cs);
             const uint32_t T = g.N >> g.logTS;
@@ -899,6 +1057,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
                 e = cudaMemcpy(pl->d_mac_offs, offs.data(), sizeof(uint32_t) * offs.size(), cudaMemcpyHostToDevice);
         }
     }
+    if (e == cudaSuccess && !tc_calls.empty()) e = build_tc_tables(pl, descs, calls, tc_calls);
     if (e == cudaSuccess) {
         std::stable_sort(fin.begin(), fin.end(), by_cost);
         std::vector<ChanItem> items;
@@ -930,7 +1089,8 @@ he_status he_plan_check(he_plan_t plan) {
     if (st) {
         const uint32_t zero = 0;
         cudaMemcpy(plan->d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice);
-        return fail(HE_ERR_TIMEOUT, "a bounded wait of the MAC kernel gave up (status 0x%x)", st);
+        return fail(HE_ERR_TIMEOUT, "a bounded wait of a MAC kernel gave up (status 0x%x: bit 0 scalar, bit 1 tensor-core)",
+                    st);
     }
     return HE_OK;
 }
@@ -961,9 +1121,13 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
     r.finish_items = plan->n_fin;
     for (int c = 0; c < 4; ++c) r.fused_items += plan->n_chan[c];
     r.fc_items = plan->n_fc;
-    r.kernels_per_run = (plan->n_ntt > 0) + (plan->n_mac > 0) + (plan->n_fin > 0) + (plan->n_fc > 0);
+    r.kernels_per_run = (plan->n_ntt > 0) + (plan->n_mac > 0) + (plan->n_fin > 0) + (plan->n_fc > 0) +
+                        (plan->n_tc > 0);
+    r.tc_items = plan->n_tc;
+    r.tc_ctas = plan->n_tc ? plan->tc_ctas : 0;
+    for (uint32_t i = 0; i < plan->ncalls; ++i) r.tc_calls += plan->split[i] == 2;
     for (int c = 0; c < 4; ++c) r.kernels_per_run += plan->n_chan[c] > 0;
-    for (uint32_t i = 0; i < plan->ncalls; ++i) r.split_calls += plan->split[i];
+    for (uint32_t i = 0; i < plan->ncalls; ++i) r.split_calls += plan->split[i] == 1;
     r.workspace_bytes = plan->ws_bytes;
     r.tuning = plan->tuning;
     *info = r;
@@ -984,6 +1148,9 @@ void he_plan_destroy(he_plan_t plan) {
     cudaFree(plan->d_mac_copy);
     cudaFree(plan->d_mac_desc);
     cudaFree(plan->d_fin);
+    cudaFree(plan->d_tc_calls);
+    cudaFree(plan->d_tc_items);
+    cudaFree(plan->d_tc_offs);
     cudaFree(plan->d_status);
     cudaFree(plan->d_fc);
     if (plan->side) cudaStreamDestroy(plan->side);

@@ -75,6 +75,8 @@ struct ConvGeo {
     uint32_t logTS;           // conv bank tile: TS = 2^logTS slots
     uint32_t lcs;             // conv bank chunk interleave (log2)
     uint32_t cs, n0, nc;      // split MAC: chunks per thread; (per item) channel range
+    uint32_t tc;              // conv bank in the tensor-core layout (bank_index_tc)
+    uint32_t pad_geo[3];
 };
 
 // Conv filter bank layout: [L][N/TS][co][G][TS] (TS = 2^lt slots, a
@@ -126,6 +128,54 @@ __host__ __device__ __forceinline__ uint32_t bank_tile_log(uint32_t logN, uint32
     return lt < logN ? lt : logN;
 }
 
+// ---------------------------------------------------------------------------
+// Tensor-core layout of a Conv bank (packed for batched calls)
+//
+// Per limb l and slot block b (the s slots b*s .. b*s+s-1), the folded
+// channel sum is a dense contraction z_n[b] = sum_kk W[n][kk] X[kk][col]
+// over kk = g*s + k' (K = G*s terms), the same for every column.  The bank
+// stores, for every (l, b) and every group of 64 channels, the 64 x K weight
+// matrix as [K/4][64 channels][4 words]: [L][M][co/64][K/4][64][4].  One
+// (l, b, channel group) tile is then one contiguous region, and the thread
+// that owns channel row n reads its 4 consecutive K-words of each K/4 group
+// at consecutive 16-byte addresses of its warp.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kTcRows = 64;     // output channels per tile
+constexpr uint32_t kTcCols = 16;     // ciphertext polynomials per tile (2B <= 16)
+constexpr uint32_t kTcMaxK = 256;    // the fp32 sums of 8-bit limb products stay exact (below 2^24)
+constexpr uint32_t kTcMinBatch = 4;  // he_pack_filters_for_batch picks this layout from B = 4 up
+__host__ __device__ __forceinline__ bool tc_shape_ok(uint32_t s, uint32_t G, uint32_t co) {
+    const uint32_t K = G * s;
+    return s >= 8 && (K & 15u) == 0 && K >= 32 && K <= kTcMaxK && (co & (kTcRows - 1u)) == 0;
+}
+__host__ __device__ __forceinline__ size_t bank_index_tc(uint32_t n, uint32_t l, uint32_t g, uint32_t k,
+                                                         uint32_t logs, uint32_t M, uint32_t G, uint32_t co) {
+    const uint32_t s = 1u << logs, K = G << logs;
+    const uint32_t b = k >> logs, kk = g * s + (k & (s - 1u));
+    const size_t tile = ((size_t)l * M + b) * (co / kTcRows) + n / kTcRows;
+    return (tile * K + (kk & ~3u)) * kTcRows + (n % kTcRows) * 4u + (kk & 3u);
+}
+
+// Limb constants of the tensor-core MAC kernel's epilogue.
+struct TcLimb {
+    uint32_t q, q2, r32, r32s, ones;  // as LimbK
+    uint32_t w16, w16s;               // 2^16 mod q and its Shoup constant
+    uint32_t pad;
+};
+// One Conv call of a plan on the tensor-core MAC kernel (device table; the
+// tensor map must sit at a 64-byte boundary).
+struct alignas(64) TcCall {
+    uint64_t xmap[16];        // CUtensorMap of the NTT-domain inputs [B][G][2][L][N], box (s, 1, 2, G, B)
+    const uint32_t *bank;     // tensor-core layout, bank_index_tc
+    uint32_t *z;              // folded sums, channel-fastest: [L][2B][M][co]
+    uint32_t K, s, logs, G, co, M, ncols, xbytes;
+    TcLimb limb[HE_MAX_LIMBS];
+};
+// Work item of the tensor-core MAC kernel: blocks b0 .. b0+nb-1 of one limb.
+struct TcItem {
+    uint32_t call, l, b0, nb;
+};
+
 // One layer call inside a plan (device-resident table).
 struct CallDesc {
     ConvGeo g;
@@ -134,7 +184,8 @@ struct CallDesc {
     uint32_t *z;              // split form: folded channel sums [L][2B][co][M]
     uint32_t kind, nj, nb, cpt;
     uint32_t split;           // 1: MAC kernel + finishing kernel; 0: one fused channel kernel
-    uint32_t pad[3];
+    uint32_t zt;              // z is channel-fastest, [L][2B][M][co] (tensor-core MAC kernel)
+    uint32_t pad[2];
     LimbK limb[HE_MAX_LIMBS];
 };
 
@@ -220,12 +271,19 @@ struct he_plan_s {
     size_t smem_ntt, smem_chan[4], smem_mac, smem_fin;
     uint32_t *ws;
     size_t ws_bytes;
-    uint32_t *d_status;                 // bit 0: a bounded wait in the MAC kernel gave up
+    uint32_t n_tc, tc_ctas;             // tensor-core MAC: items, persistent CTAs
+    TcCall *d_tc_calls;
+    TcItem *d_tc_items;
+    uint32_t *d_tc_offs;                // items of CTA b at [offs[b], offs[b+1])
+    uint32_t *d_status;                 // bit 0 / bit 1: a bounded wait in the MAC / tensor-core MAC kernel gave up
     uint8_t *split;                     // host: per call, 1 if it takes the split form
     he_plan_tuning tuning;
 };
 
 cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase);
+cudaError_t he_launch_tc_mac(const he_plan_s &pl, cudaStream_t st, bool pdl);  // he_tc.cu
+cudaError_t he_tc_prepare();
+size_t he_tc_smem_bytes();
 cudaError_t he_plan_prepare(const he_plan_s &pl);
 
 struct he_filters_s {
@@ -235,6 +293,7 @@ struct he_filters_s {
     he_conv_layout lay;
     uint32_t logTS;   // conv bank tile
     uint32_t lcs;     // conv bank chunk interleave (log2)
+    uint32_t tc;      // conv bank in the tensor-core layout (bank_index_tc)
     uint32_t nc;      // split MAC: channels per work item
     he_fc_layout fl;
     uint32_t *bank;   // conv: [co][L][G][N]; fc: [P][L][N]; NTT domain, pre-scaled
@@ -250,14 +309,15 @@ he_status he_fail(he_status s, const char *msg);  // he_host.cu
 cudaError_t he_launch_ntt(const RingView &r, const uint32_t *in, uint32_t *out,
                           uint32_t npolys, bool inverse, cudaStream_t st);
 cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_conv_desc &d,
-                                const he_conv_layout &lay, uint32_t lt, uint32_t lcs, uint32_t *bank, cudaStream_t st);
+                                const he_conv_layout &lay, uint32_t lt, uint32_t lcs, uint32_t tc, uint32_t *bank,
+                                cudaStream_t st);
 cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_layout &fl,
                               uint32_t *bank, cudaStream_t st);
 uint32_t he_conv_nj(uint32_t ncols, uint32_t M, uint32_t s);
 uint32_t he_conv_cpt(uint32_t nj, uint32_t nb, uint32_t G);
 uint32_t he_ilog2(uint32_t x);
 cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt,
-                           uint32_t lcs, const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out,
+                           uint32_t lcs, uint32_t tc, const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out,
                            int mode, uint32_t B, cudaStream_t st);
 cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32_t *bank,
                          const uint32_t *bias, const uint32_t *x_ntt, uint32_t *out, int mode,

@@ -183,8 +183,13 @@ __device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K,
     const size_t tstride = (size_t)a.co * G << lt;
     // put every tile segment of this channel's weights in flight to L2 at
     // once, so the loads below wait on L2, not on DRAM
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0 && !a.tc)
         for (uint32_t t = 0; t < (N >> lt); ++t) prefetch_l2_bulk(Wb + t * tstride, (G << lt) * 4u);
+    // 4 consecutive weight words of group g from slot k (k a multiple of 4) in either bank layout
+    auto wq = [&](uint32_t g, uint32_t k) -> const uint32_t * {
+        if (a.tc) return a.bank + bank_index_tc(n, l, g, k, a.logs, M, G, a.co);
+        return Wb + (k >> lt) * tstride + (size_t)g * TS + bank_row_pos(k & (TS - 1), lt, a.lcs);
+    };
     const size_t gstride = (size_t)2 * L * N;
     const uint32_t *X[NJ];
 #pragma unroll
@@ -219,8 +224,7 @@ __device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K,
 #pragma unroll
                 for (uint32_t gg = 0; gg < kGL; ++gg) {
                     if (act[u]) {
-                        w[u][gg] = ldg4(Wb + ((4u * c[u]) >> lt) * tstride + (size_t)(g + gg) * TS +
-                                        bank_row_pos((4u * c[u]) & (TS - 1), lt, a.lcs));
+                        w[u][gg] = ldg4(wq(g + gg, 4u * c[u]));
 #pragma unroll
                         for (int jj = 0; jj < NJ; ++jj) x[u][gg][jj] = ldg4(X[jj] + (g + gg) * gstride + 4u * c[u]);
                     } else {
@@ -245,8 +249,7 @@ __device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K,
             for (int u = 0; u < CPT; ++u) {
                 if (!act[u]) continue;
                 uint4 x[NJ];
-                const uint4 w = ldg4(Wb + ((4u * c[u]) >> lt) * tstride + (size_t)g * TS +
-                                     bank_row_pos((4u * c[u]) & (TS - 1), lt, a.lcs));
+                const uint4 w = ldg4(wq(g, 4u * c[u]));
 #pragma unroll
                 for (int jj = 0; jj < NJ; ++jj) x[jj] = ldg4(X[jj] + g * gstride + 4u * c[u]);
                 mac4<NJ, NB>(acc[u], w, x);
@@ -307,7 +310,8 @@ __device__ __forceinline__ void conv_full_body(const ConvGeo &a, const LimbK &K,
         int gc = 0;
         const uint32_t *Wk = Wb + (k >> lt) * tstride + bank_row_pos(k & (TS - 1), lt, a.lcs);
         for (uint32_t g = 0; g < G; ++g) {
-            acc += (uint64_t)__ldg(Wk + (size_t)g * TS) * __ldg(Xc + g * gstride + k);
+            const uint32_t *wp = a.tc ? a.bank + bank_index_tc(n, l, g, k, a.logs, a.M, G, a.co) : Wk + (size_t)g * TS;
+            acc += (uint64_t)__ldg(wp) * __ldg(Xc + g * gstride + k);
             if (++gc == 16) {
                 gc = 0;
                 acc = reduce64(acc, K);
@@ -436,6 +440,7 @@ struct PackConvArgs {
     const int8_t *w;   // [co][ci][fh][fw]
     uint32_t *bank;    // tile-major, see bank_index
     uint32_t ci, co, fh, fw, hp, s, G, mult, lt, lcs;
+    uint32_t tc, logs, M;  // tc: tensor-core layout (bank_index_tc)
 };
 
 // Slot k of the NTT domain is the value at X_k = psi^(2 brv(k) + 1).  The
@@ -473,7 +478,8 @@ __global__ void __launch_bounds__(kThreads) k_pack_conv(const PackConvArgs a) {
         const uint32_t ex = (off * (2u * brv(k, logN) + 1u)) & mask2n;
         x = mulmod(x, __ldg(pp + ((2u * N - ex) & mask2n)), K);
         x = red_2q(shoup_lazy(x, K.ninv, K.ninvs, K.q), K.q);
-        a.bank[bank_index(n, l, g, k, logN, a.lt, a.lcs, a.co, a.G)] = x;
+        a.bank[a.tc ? bank_index_tc(n, l, g, k, a.logs, a.M, a.G, a.co)
+                    : bank_index(n, l, g, k, logN, a.lt, a.lcs, a.co, a.G)] = x;
     }
 }
 
@@ -845,6 +851,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
     if (!ok) atomicOr(status, 1u);
 }
 
+__device__ __forceinline__ uint32_t he_log2_dev(uint32_t x) { return 31u - __clz(x); }
+
 // Finishing kernel: items (call, h, l, column) run the length-M inverse
 // transforms of the s channels of output polynomial h and write the whole
 // extracted polynomial (coalesced; classes no channel uses are 0).
@@ -862,10 +870,35 @@ __global__ void __launch_bounds__(kFinThreads, 4) k_plan_fin(const CallDesc *__r
                    logM = cd.g.logM, mult = cd.g.mult, H = cd.g.H;
     const uint32_t sh = min(s, co - h * s);
     const uint32_t PS = fin_stride(M);
-    const uint32_t *zsrc = cd.z + (((size_t)l * cd.g.ncols + c) * co + h * s) * M;
     // sh*M words, 4 at a time, 8 loads in flight per thread
     const uint32_t nq = (sh << logM) >> 2;
-    for (uint32_t q0 = 0; q0 < nq; q0 += 8u * blockDim.x) {
+    if (cd.zt) {
+        // channel-fastest sums [L][2B][M][co] of the tensor-core MAC kernel:
+        // quad (e, r .. r+3), sh a multiple of 4
+        const uint32_t *zt = cd.z + ((size_t)l * cd.g.ncols + c) * M * co + h * s;
+        const uint32_t lq = he_log2_dev(sh >> 2);
+        for (uint32_t q0 = 0; q0 < nq; q0 += 8u * blockDim.x) {
+            uint4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t qi = q0 + u * blockDim.x + threadIdx.x;
+                if (qi < nq) v[u] = __ldcs(reinterpret_cast<const uint4 *>(zt + (size_t)(qi >> lq) * co) + (qi & ((sh >> 2) - 1u)));
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t qi = q0 + u * blockDim.x + threadIdx.x;
+                if (qi < nq) {
+                    const uint32_t e = qi >> lq, r = (qi & ((sh >> 2) - 1u)) << 2;
+                    Zs[r * PS + pidx(e)] = v[u].x;
+                    Zs[(r + 1) * PS + pidx(e)] = v[u].y;
+                    Zs[(r + 2) * PS + pidx(e)] = v[u].z;
+                    Zs[(r + 3) * PS + pidx(e)] = v[u].w;
+                }
+            }
+        }
+    }
+    const uint32_t *zsrc = cd.z + (((size_t)l * cd.g.ncols + c) * co + h * s) * M;
+    for (uint32_t q0 = 0; q0 < (cd.zt ? 0u : nq); q0 += 8u * blockDim.x) {
         uint4 v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -1004,11 +1037,14 @@ cudaError_t he_launch_ntt(const RingView &r, const uint32_t *in, uint32_t *out, 
 }
 
 cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_conv_desc &d,
-                                const he_conv_layout &lay, uint32_t lt, uint32_t lcs, uint32_t *bank,
+                                const he_conv_layout &lay, uint32_t lt, uint32_t lcs, uint32_t tc, uint32_t *bank,
                                 cudaStream_t st) {
     PackConvArgs a;
     a.lt = lt;
     a.lcs = lcs;
+    a.tc = tc;
+    a.logs = he_ilog2(lay.s);
+    a.M = lay.M;
     a.r = r;
     a.w = d_w;
     a.bank = bank;
@@ -1055,8 +1091,8 @@ static ConvGeo geo_of(const RingView &r) {
 }
 
 cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt,
-                           uint32_t lcs, const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out, int mode,
-                           uint32_t B, cudaStream_t st) {
+                           uint32_t lcs, uint32_t tc, const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out,
+                           int mode, uint32_t B, cudaStream_t st) {
     ConvGeo a = geo_of(r);
     a.bank = bank;
     a.x = x_ntt;
@@ -1072,6 +1108,7 @@ cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_co
     a.ncols = 2u * B;
     a.logTS = lt;
     a.lcs = lcs;
+    a.tc = tc;
     // The folded kernel keeps 2 * M words per CTA in shared memory; for
     // M = N / s above 24K words (s = 1 at N = 32768) the unfolded kernel
     // produces the same words with N words of shared memory.
@@ -1117,6 +1154,7 @@ cudaError_t he_plan_prepare(const he_plan_s &pl) {
     if (pl.n_ntt) e = set_smem(k_plan_ntt, pl.smem_ntt);
     if (e == cudaSuccess && pl.n_mac) e = set_smem(k_plan_mac, pl.smem_mac);
     if (e == cudaSuccess && pl.n_fin) e = set_smem(k_plan_fin, pl.smem_fin);
+    if (e == cudaSuccess && pl.n_tc) e = he_tc_prepare();
     if (e == cudaSuccess && pl.n_fc) e = set_smem(k_plan_fc, pl.smem_fc);
     if (e == cudaSuccess && pl.n_chan[0]) e = set_smem(k_plan_chan<2>, pl.smem_chan[0]);
     if (e == cudaSuccess && pl.n_chan[1]) e = set_smem(k_plan_chan<4>, pl.smem_chan[1]);
@@ -1179,6 +1217,9 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         e = launch_pdl(k_plan_mac, pl.mac_ctas, kThreads + 32, pl.smem_mac, st, (const MacCopy *)pl.d_mac_copy,
                        (const MacDesc *)pl.d_mac_desc, (const uint32_t *)pl.d_mac_offs, pl.d_status);
         if (e != cudaSuccess) return e;
+    }
+    if (pl.n_tc && phase != 3) {
+        if ((e = he_launch_tc_mac(pl, st, true)) != cudaSuccess) return e;
     }
     if (phase == 2) return cudaSuccess;
     if (pl.n_fin) {

@@ -1,0 +1,572 @@
+// he_tc.cu -- channel MAC of batched Conv calls on the tensor cores
+// (tcgen05, sm_103a).
+//
+// The step (Alg. 1, the product summed over input channels; Sec. III-A: only
+// the valid slots are needed) is, per limb l and slot block b of s slots,
+//   z_n^(col)[b] = sum_{kk < K} W[n][kk] * X^(col)[kk]   mod q_l,
+// kk = g*s + k' (K = G*s), W the resident bank pre-multiplied by the fold
+// factor, X the NTT-domain ciphertext polynomials: a dense [co x K] x
+// [K x 2B] product per block.  The tensor cores evaluate it exactly on
+// 8-bit limbs: a residue a < 2^30 is sum_i a_i 2^(8i) with a_i < 256, every
+// a_i is an exact fp16 value, and sum_kk a_i x_j <= K * 255^2 < 2^24 for
+// K <= 256, so the fp32 accumulators hold exact integers.  The epilogue
+// recombines sum_{i,j} 2^(8(i+j)) D_ij and reduces mod q_l.
+//
+// One tile = (limb, block, 64 output channels) x 16 columns:
+//   A (TMEM, M = 128 rows): rows 0..63 hold limbs {0, 1} of the 64 channels'
+//     weights, rows 64..127 limbs {2, 3}; two MMAs per K-step (p = 0, 1)
+//     take limb p from the low rows and limb p + 2 from the high rows.
+//   B (shared memory, N = 64 rows, K-major, no swizzle): row j*16 + col is
+//     limb j of ciphertext polynomial col.
+//   D_p (TMEM, fp32, 128 lanes x 64 columns, double-buffered).
+//
+// Warp roles (384 threads, one CTA per SM, persistent over a list of
+// items = (call, limb, range of blocks)):
+//   warp 0       producer: bulk copies of the weight tiles into a ring of
+//                16 KB stages, one 5-D tensor copy of a block's inputs;
+//                allocates and frees the tensor memory
+//   warp 1       MMA issuer (one thread)
+//   warps 2..5   A builders: weight words from the ring -> fp16 limbs ->
+//                tcgen05.st into an A slot of tensor memory
+//   warps 6..9   epilogue: tcgen05.ld of D, exact recombination, mod q,
+//                the high rows' share through shared memory, z stores
+//   warps 10..11 B builders: a block's input words -> fp16 limb rows
+// Every wait is bounded; a wait that gives up raises an abort flag that
+// every other wait sees, sets bit 1 of the plan status, and the CTA winds
+// down, with its copies and MMAs drained before the tensor memory is freed.
+
+#include "he_internal.h"
+
+namespace {
+
+constexpr uint32_t kTcThreads = 384;
+constexpr uint32_t kWStageBytes = 16384;
+constexpr uint32_t kWStages = 6;
+constexpr uint32_t kASlots = 16;               // A slots of 16 TMEM columns (one K-step)
+constexpr uint32_t kTmemCols = 512;            // D: 2 x 2 x 64 columns; A: 16 x 16 columns
+constexpr uint32_t kXRawBytes = kTcMaxK * kTcCols * 4;      // 16 KB
+constexpr uint32_t kBOpBytes = 64 * kTcMaxK * 2;            // 32 KB
+constexpr uint32_t kXchgBytes = kTcCols * kTcRows * 4;      // 4 KB
+constexpr uint32_t kTcSpin = 1u << 20;
+constexpr uint32_t kMagic = 0x4B000000u;       // bits of 2^23 as fp32
+
+struct TcBars {
+    uint64_t w_full[kWStages], w_empty[kWStages];
+    uint64_t x_full[2], x_empty[2];
+    uint64_t b_full[2], b_empty[2];
+    uint64_t a_full[kASlots], a_empty[kASlots];
+    uint64_t d_full[2], d_empty[2];
+    uint64_t fin;
+    uint32_t tmem;
+    uint32_t abort;
+};
+constexpr uint32_t kHdrBytes = 1024;
+static_assert(sizeof(TcBars) <= kHdrBytes, "barrier header");
+constexpr uint32_t kOffW = kHdrBytes;
+constexpr uint32_t kOffX = kOffW + kWStages * kWStageBytes;
+constexpr uint32_t kOffB = kOffX + 2 * kXRawBytes;
+constexpr uint32_t kOffXchg = kOffB + 2 * kBOpBytes;
+constexpr uint32_t kTcSmem = kOffXchg + 2 * kXchgBytes;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void bar_init(uint64_t *b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; false once any role of the CTA has given up.
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity, volatile uint32_t *abort) {
+    for (uint32_t it = 0; it < kTcSpin; ++it) {
+        if (bar_try(b, parity)) return true;
+        if (*abort) return false;
+    }
+    *abort = 1u;
+    return false;
+}
+
+// Bounded wait that ignores the abort flag: copies and MMAs already issued
+// must land before the CTA releases shared and tensor memory.
+__device__ __forceinline__ void bar_drain(uint64_t *b, uint32_t parity) {
+    for (uint32_t it = 0; it < kTcSpin; ++it)
+        if (bar_try(b, parity)) return;
+}
+
+__device__ __forceinline__ void pdl_wait_tc() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     su32(dst)),
+                 "l"(src), "r"(bytes), "r"(su32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void tensor5_g2s(void *dst, const void *tmap, uint32_t c0, uint32_t c1, uint64_t *b) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(su32(dst)),
+        "l"(tmap), "r"(c0), "r"(c1), "r"(0u), "r"(0u), "r"(0u), "r"(su32(b))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint64_t *b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+                 : "memory");
+}
+// D[tmem d] (+)= A[tmem a] * B[smem desc]^T, fp16 inputs, fp32 accumulators
+__device__ __forceinline__ void tc_mma(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
+        "r"(a), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Shared-memory operand descriptor: K-major, no swizzle; core matrices of
+// 8 rows x 16 bytes, lbo = byte distance between core matrices along K,
+// sbo = along the rows.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// fp16 pair (a byte i, b byte i) as exact values 0..255: the bytes go under
+// the exponent of 1024 (0x64XX = 1024 + XX), then 1024 is subtracted.
+template <int I>
+__device__ __forceinline__ uint32_t limb_pair(uint32_t a, uint32_t b) {
+    constexpr uint32_t sel = I | (I << 4) | ((4 + I) << 8) | ((4 + I) << 12);
+    const uint32_t t = (__byte_perm(a, b, sel) & 0x00FF00FFu) | 0x64006400u;
+    uint32_t r;
+    asm("sub.f16x2 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(0x64006400u));
+    return r;
+}
+__device__ __forceinline__ uint32_t limb_pair_rt(uint32_t a, uint32_t b, uint32_t i) {
+    switch (i) {
+        case 0: return limb_pair<0>(a, b);
+        case 1: return limb_pair<1>(a, b);
+        case 2: return limb_pair<2>(a, b);
+        default: return limb_pair<3>(a, b);
+    }
+}
+
+#define TC_LD8(base, v)                                                                                   \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"                  \
+                 : "=r"((v)[0]), "=r"((v)[1]), "=r"((v)[2]), "=r"((v)[3]), "=r"((v)[4]), "=r"((v)[5]), \
+                   "=r"((v)[6]), "=r"((v)[7])                                                              \
+                 : "r"(base))
+
+// exact integer of an fp32 accumulator (< 2^23 with the magic add, else F2I)
+template <bool kBig>
+__device__ __forceinline__ uint32_t acc_int(uint32_t bits) {
+    if constexpr (kBig) return __float2uint_rz(__uint_as_float(bits));
+    return __float_as_uint(__uint_as_float(bits) + 8388608.0f) - kMagic;
+}
+
+// The epilogue of one tile for this thread's row: 8 columns (c0 .. c0+7) of
+// its two limbs; v[p][j][c] = D_p[(j, c0 + c)].
+template <bool kBig>
+__device__ __forceinline__ void recombine8(const uint32_t (&v)[2][4][8], const TcLimb &K, bool high,
+                                           uint32_t *res) {
+    LimbK k;
+    k.q = K.q;
+    k.q2 = K.q2;
+    k.r32 = K.r32;
+    k.r32s = K.r32s;
+    k.ones = K.ones;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint32_t u[2][4];
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) u[p][j] = acc_int<kBig>(v[p][j][c]);
+        const uint32_t S1 = u[0][1] + u[1][0], S2 = u[0][2] + u[1][1], S3 = u[0][3] + u[1][2];
+        const uint64_t val = (uint64_t)u[0][0] + ((uint64_t)S1 << 8) + ((uint64_t)S2 << 16) + ((uint64_t)S3 << 24) +
+                             ((uint64_t)u[1][3] << 32);
+        uint32_t r = reduce64(val, k);
+        if (high) r = red_2q(shoup_lazy(r, K.w16, K.w16s, K.q), K.q);  // limbs 2, 3 carry 2^16
+        res[c] = r;
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restrict__ calls,
+                                                          const TcItem *__restrict__ items,
+                                                          const uint32_t *__restrict__ offs,
+                                                          uint32_t *__restrict__ status) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    TcBars &bars = *reinterpret_cast<TcBars *>(smem);
+    uint8_t *wring = smem + kOffW;
+    uint8_t *xraw = smem + kOffX;
+    uint8_t *bop = smem + kOffB;
+    uint32_t *xchg = reinterpret_cast<uint32_t *>(smem + kOffXchg);
+    volatile uint32_t *abort = &bars.abort;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
+    const uint32_t ib = offs[blockIdx.x], ie = offs[blockIdx.x + 1];
+    if (ib >= ie) return;
+
+    if (tid == 0) {
+        for (uint32_t i = 0; i < kWStages; ++i) {
+            bar_init(&bars.w_full[i], 1);
+            bar_init(&bars.w_empty[i], 4);
+        }
+        for (uint32_t i = 0; i < 2; ++i) {
+            bar_init(&bars.x_full[i], 1);
+            bar_init(&bars.x_empty[i], 2);
+            bar_init(&bars.b_full[i], 2);
+            bar_init(&bars.b_empty[i], 1);
+            bar_init(&bars.d_full[i], 1);
+            bar_init(&bars.d_empty[i], 4);
+        }
+        for (uint32_t i = 0; i < kASlots; ++i) {
+            bar_init(&bars.a_full[i], 4);
+            bar_init(&bars.a_empty[i], 1);
+        }
+        bar_init(&bars.fin, 1);
+        bars.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&bars.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bars.tmem;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        // Per block: its inputs, then the weight tiles of its channel groups.
+        // The first stages of weights (they do not depend on the input-NTT
+        // kernel) go out before the wait for that kernel.
+        if (lane == 0) {
+            uint32_t ws = 0, xs = 0, pre = 0;
+            bool ok = true;
+            {
+                const TcItem item = items[ib];
+                const TcCall &C = calls[item.call];
+                const uint32_t tile_words = C.K * kTcRows, nch = C.co / kTcRows;
+                const uint32_t *src = C.bank + ((size_t)item.l * C.M + item.b0) * nch * tile_words;
+                const uint32_t nst = min(kWStages, (nch * tile_words + kWStageBytes / 4u - 1u) / (kWStageBytes / 4u));
+                for (uint32_t ch = 0; ch < nch && pre < nst; ++ch)
+                    for (uint32_t off = 0; off < tile_words && pre < nst; off += kWStageBytes / 4u, ++pre) {
+                        const uint32_t bytes = min(kWStageBytes, (tile_words - off) * 4u);
+                        bar_expect(&bars.w_full[pre], bytes);
+                        bulk_g2s(wring + pre * kWStageBytes, src + (size_t)ch * tile_words + off, bytes,
+                                 &bars.w_full[pre]);
+                    }
+            }
+            pdl_wait_tc();
+            uint32_t skip = pre;
+            ws = pre;
+            for (uint32_t it = ib; ok && it < ie; ++it) {
+                const TcItem item = items[it];
+                const TcCall &C = calls[item.call];
+                const uint32_t nch = C.co / kTcRows, tile_words = C.K * kTcRows;
+                for (uint32_t b = item.b0; ok && b < item.b0 + item.nb; ++b) {
+                    const uint32_t xb = xs & 1u;
+                    if (xs >= 2 && !bar_wait(&bars.x_empty[xb], ((xs >> 1) - 1u) & 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bar_expect(&bars.x_full[xb], C.xbytes);
+                    tensor5_g2s(xraw + xb * kXRawBytes, C.xmap, b * C.s, item.l, &bars.x_full[xb]);
+                    ++xs;
+                    for (uint32_t ch = 0; ok && ch < nch; ++ch) {
+                        const uint32_t *src = C.bank + (((size_t)item.l * C.M + b) * nch + ch) * tile_words;
+                        for (uint32_t off = 0; off < tile_words; off += kWStageBytes / 4u) {
+                            if (skip) {  // issued before the wait
+                                --skip;
+                                continue;
+                            }
+                            const uint32_t st = ws % kWStages;
+                            if (ws >= kWStages &&
+                                !bar_wait(&bars.w_empty[st], ((ws / kWStages) - 1u) & 1u, abort)) {
+                                ok = false;
+                                break;
+                            }
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            const uint32_t bytes = min(kWStageBytes, (tile_words - off) * 4u);
+                            bar_expect(&bars.w_full[st], bytes);
+                            bulk_g2s(wring + st * kWStageBytes, src + off, bytes, &bars.w_full[st]);
+                            ++ws;
+                        }
+                    }
+                }
+            }
+            // every copy lands before shared memory is released (only the
+            // last two input copies and the last kWStages stages can be in flight)
+            for (uint32_t i = xs > 2 ? xs - 2 : 0; i < xs; ++i) bar_drain(&bars.x_full[i & 1u], (i >> 1) & 1u);
+            for (uint32_t i = ws > kWStages ? ws - kWStages : 0; i < ws; ++i)
+                bar_drain(&bars.w_full[i % kWStages], (i / kWStages) & 1u);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            // fp32 D (bit 4), fp16 A and B, both K-major, N = 64 (bits 17..22), M = 128 (bits 24..28)
+            const uint32_t idesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+            uint32_t as = 0, ds = 0, bs = 0;
+            bool ok = true;
+            for (uint32_t it = ib; ok && it < ie; ++it) {
+                const TcItem item = items[it];
+                const TcCall &C = calls[item.call];
+                const uint32_t nch = C.co / kTcRows, nks = C.K / 16u;
+                for (uint32_t b = item.b0; ok && b < item.b0 + item.nb; ++b) {
+                    const uint32_t bb = bs & 1u;
+                    if (!bar_wait(&bars.b_full[bb], (bs >> 1) & 1u, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t baddr = su32(bop + bb * kBOpBytes);
+                    for (uint32_t ch = 0; ok && ch < nch; ++ch) {
+                        const uint32_t db = ds & 1u;
+                        if (ds >= 2 && !bar_wait(&bars.d_empty[db], ((ds >> 1) - 1u) & 1u, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        for (uint32_t ks = 0; ks < nks; ++ks) {
+                            const uint32_t slot = as % kASlots;
+                            if (!bar_wait(&bars.a_full[slot], (as / kASlots) & 1u, abort)) {
+                                ok = false;
+                                break;
+                            }
+                            tc_fence_after();
+                            const uint64_t bdesc = smem_desc(baddr + ks * 2048u, 1024u, 128u);
+#pragma unroll
+                            for (uint32_t p = 0; p < 2; ++p)
+                                tc_mma(tmem + 128u * db + 64u * p, tmem + 256u + 16u * slot + 8u * p, bdesc, idesc,
+                                       ks > 0 ? 1u : 0u);
+                            tc_commit(&bars.a_empty[slot]);
+                            ++as;
+                        }
+                        if (!ok) break;
+                        tc_commit(&bars.d_full[db]);
+                        ++ds;
+                    }
+                    if (!ok) break;
+                    tc_commit(&bars.b_empty[bb]);
+                    ++bs;
+                }
+            }
+            // every MMA issued has completed before the tensor memory is freed
+            tc_commit(&bars.fin);
+            bar_drain(&bars.fin, 0);
+        }
+    } else if (warp < 6) {
+        // ------------------------------------------------------------ A builders
+        const uint32_t sp = warp & 3u, tl = 32u * sp + lane, n = tl & 63u, high = tl >> 6;
+        const uint32_t taddr = tmem + ((32u * sp) << 16) + 256u;
+        uint32_t ws = 0, as = 0;
+        bool ok = true;
+        for (uint32_t it = ib; ok && it < ie; ++it) {
+            const TcItem item = items[it];
+            const TcCall &C = calls[item.call];
+            const uint32_t nch = C.co / kTcRows, nks = C.K / 16u;
+            for (uint32_t b = item.b0; ok && b < item.b0 + item.nb; ++b)
+                for (uint32_t ch = 0; ok && ch < nch; ++ch)
+                    for (uint32_t ks = 0; ks < nks; ++ks) {
+                        const uint32_t st = ws % kWStages;
+                        if ((ks & 3u) == 0 && !bar_wait(&bars.w_full[st], (ws / kWStages) & 1u, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t slot = as % kASlots;
+                        if (as >= kASlots && !bar_wait(&bars.a_empty[slot], ((as / kASlots) - 1u) & 1u, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        // this K-step's 16 words of row n: [kq][64 rows][4 words], kq = 4 (ks % 4) .. + 3
+                        const uint4 *src =
+                            reinterpret_cast<const uint4 *>(wring + st * kWStageBytes + (ks & 3u) * 4096u) + n;
+                        uint32_t w[16];
+#pragma unroll
+                        for (int kq = 0; kq < 4; ++kq) {
+                            const uint4 v = src[kq * 64];
+                            w[4 * kq] = v.x;
+                            w[4 * kq + 1] = v.y;
+                            w[4 * kq + 2] = v.z;
+                            w[4 * kq + 3] = v.w;
+                        }
+                        uint32_t r[16];
+                        const uint32_t i0 = 2u * high;
+#pragma unroll
+                        for (int pp = 0; pp < 8; ++pp) {
+                            r[pp] = limb_pair_rt(w[2 * pp], w[2 * pp + 1], i0);
+                            r[8 + pp] = limb_pair_rt(w[2 * pp], w[2 * pp + 1], i0 + 1u);
+                        }
+                        asm volatile(
+                            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+                            "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr + 16u * slot),
+                            "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                            "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+                            "r"(r[15])
+                            : "memory");
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) bar_arrive(&bars.a_full[slot]);
+                        ++as;
+                        if ((ks & 3u) == 3u || ks + 1u == nks) {
+                            if (lane == 0) bar_arrive(&bars.w_empty[st]);
+                            ++ws;
+                        }
+                    }
+        }
+    } else if (warp < 10) {
+        // ------------------------------------------------------------ epilogue
+        // Every warp passes the named barrier once per tile, also after an
+        // abort, so that no warp waits there for one that has left.
+        const uint32_t sp = warp & 3u, tl = 32u * sp + lane, n = tl & 63u;
+        const bool high = tl >= 64u;
+        const uint32_t lrow = tmem + ((32u * sp) << 16);
+        uint32_t ds = 0;
+        bool ok = true;
+        for (uint32_t it = ib; it < ie; ++it) {
+            const TcItem item = items[it];
+            const TcCall &C = calls[item.call];
+            const uint32_t nch = C.co / kTcRows, ncols = C.ncols, M = C.M, co = C.co;
+            const TcLimb K = C.limb[item.l];
+            const bool big = C.K > 128u;
+            uint32_t *zb = C.z + (size_t)item.l * ncols * M * co + n;
+            const size_t cstride = (size_t)M * co;
+            for (uint32_t b = item.b0; b < item.b0 + item.nb; ++b)
+                for (uint32_t ch = 0; ch < nch; ++ch) {
+                    const uint32_t db = ds & 1u;
+                    ok = ok && bar_wait(&bars.d_full[db], (ds >> 1) & 1u, abort);
+                    uint32_t res[16];
+                    if (ok) {
+                        tc_fence_after();
+#pragma unroll
+                        for (uint32_t half = 0; half < 2; ++half) {
+                            uint32_t v[2][4][8];
+#pragma unroll
+                            for (uint32_t p = 0; p < 2; ++p)
+#pragma unroll
+                                for (uint32_t j = 0; j < 4; ++j)
+                                    TC_LD8(lrow + 128u * db + 64u * p + 16u * j + 8u * half, v[p][j]);
+                            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            if (half == 1) {
+                                tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) bar_arrive(&bars.d_empty[db]);
+                            }
+                            if (big)
+                                recombine8<true>(v, K, high, res + 8 * half);
+                            else
+                                recombine8<false>(v, K, high, res + 8 * half);
+                        }
+                    }
+                    uint32_t *xc = xchg + db * (kTcCols * kTcRows);
+                    if (ok && high)
+#pragma unroll
+                        for (uint32_t c = 0; c < kTcCols; ++c) xc[c * kTcRows + n] = res[c];
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (ok && !high) {
+                        uint32_t *z = zb + (size_t)b * co + ch * kTcRows;
+#pragma unroll
+                        for (uint32_t c = 0; c < kTcCols; ++c)
+                            if (c < ncols) z[c * cstride] = red_2q(res[c] + xc[c * kTcRows + n], K.q);
+                    }
+                    ++ds;
+                }
+        }
+    } else {
+        // ------------------------------------------------------------ B builders
+        const uint32_t xt = tid - 320u;
+        uint32_t xs = 0, bs = 0;
+        bool ok = true;
+        for (uint32_t it = ib; ok && it < ie; ++it) {
+            const TcItem item = items[it];
+            const TcCall &C = calls[item.call];
+            const uint32_t kgn = C.K / 8u, total = C.ncols * kgn, s = C.s, logs = C.logs, G = C.G;
+            for (uint32_t b = item.b0; b < item.b0 + item.nb; ++b) {
+                const uint32_t xb = xs & 1u, bb = bs & 1u;
+                if (!bar_wait(&bars.x_full[xb], (xs >> 1) & 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                if (bs >= 2 && !bar_wait(&bars.b_empty[bb], ((bs >> 1) - 1u) & 1u, abort)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t *raw = reinterpret_cast<const uint32_t *>(xraw + xb * kXRawBytes);
+                uint8_t *B = bop + bb * kBOpBytes;
+                for (uint32_t q = xt; q < total; q += 64u) {
+                    const uint32_t c = q / kgn, kg = q - c * kgn, kk0 = kg * 8u;
+                    const uint32_t g = kk0 >> logs, kp0 = kk0 & (s - 1u);
+                    // the tensor copy's box is [B][G][2][s]: column c = (c / 2, c % 2)
+                    const uint4 *src = reinterpret_cast<const uint4 *>(raw + (((c >> 1) * G + g) * 2u + (c & 1u)) * s + kp0);
+                    const uint4 x0 = src[0], x1 = src[1];
+#pragma unroll
+                    for (uint32_t j = 0; j < 4; ++j) {
+                        const uint32_t row = j * 16u + c;
+                        uint4 h;
+                        h.x = limb_pair_rt(x0.x, x0.y, j);
+                        h.y = limb_pair_rt(x0.z, x0.w, j);
+                        h.z = limb_pair_rt(x1.x, x1.y, j);
+                        h.w = limb_pair_rt(x1.z, x1.w, j);
+                        *reinterpret_cast<uint4 *>(B + (kg * 8u + (row >> 3)) * 128u + (row & 7u) * 16u) = h;
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    bar_arrive(&bars.b_full[bb]);
+                    bar_arrive(&bars.x_empty[xb]);
+                }
+                ++xs;
+                ++bs;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0 && *abort) atomicOr(status, 2u);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace
+
+size_t he_tc_smem_bytes() { return kTcSmem; }
+
+cudaError_t he_launch_tc_mac(const he_plan_s &pl, cudaStream_t st, bool pdl) {
+    if (!pl.n_tc) return cudaSuccess;
+    static_assert(kTcSmem <= 227u * 1024u, "shared memory of the tensor-core MAC kernel");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(pl.tc_ctas);
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = kTcSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_tc_mac, (const TcCall *)pl.d_tc_calls, (const TcItem *)pl.d_tc_items,
+                              (const uint32_t *)pl.d_tc_offs, pl.d_status);
+}
+
+cudaError_t he_tc_prepare() {
+    return cudaFuncSetAttribute(k_tc_mac, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+}

@@ -58,7 +58,8 @@ class he_plan_tuning(ctypes.Structure):
 class he_plan_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("kernels_per_run", "ntt_items", "mac_items", "mac_ctas",
                                                "finish_items", "fused_items", "fc_items", "split_calls")] + \
-               [("workspace_bytes", ctypes.c_uint64), ("tuning", he_plan_tuning)]
+               [("workspace_bytes", ctypes.c_uint64), ("tuning", he_plan_tuning)] + \
+               [(n, ctypes.c_uint32) for n in ("tc_items", "tc_ctas", "tc_calls")]
 
 
 class he_server_config(ctypes.Structure):
@@ -89,6 +90,8 @@ _SIGS = {
     "he_conv_layout_query": [_vp, ctypes.POINTER(he_conv_desc), ctypes.POINTER(he_conv_layout)],
     "he_fc_layout_query": [_vp, _u32, _u32, ctypes.POINTER(he_fc_layout)],
     "he_pack_filters": [_vp, ctypes.POINTER(he_conv_desc), _vp, ctypes.POINTER(_vp)],
+    "he_pack_filters_for_batch": [_vp, ctypes.POINTER(he_conv_desc), _vp, _u32, ctypes.POINTER(_vp)],
+    "he_filters_tensor_core": [_vp, ctypes.POINTER(_u32)],
     "he_pack_fc": [_vp, _u32, _u32, _vp, _vp, ctypes.POINTER(_vp)],
     "he_filters_destroy": [_vp],
     "he_conv_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
@@ -239,6 +242,21 @@ def he_pack_filters(p: int, desc, w: np.ndarray) -> int:
     return out.value
 
 
+def he_pack_filters_for_batch(p: int, desc, w: np.ndarray, B: int) -> int:
+    d = _desc(desc)
+    w = np.ascontiguousarray(w, dtype=np.int8)
+    assert w.size == d.co * d.ci * d.fh * d.fw
+    out = _vp()
+    _check(lib().he_pack_filters_for_batch(p, ctypes.byref(d), w.ctypes.data, B, ctypes.byref(out)))
+    return out.value
+
+
+def he_filters_tensor_core(f: int) -> int:
+    tc = _u32()
+    _check(lib().he_filters_tensor_core(f, ctypes.byref(tc)))
+    return tc.value
+
+
 def he_pack_fc(p: int, n_in: int, n_out: int, W: np.ndarray, bias: np.ndarray | None = None) -> int:
     W = np.ascontiguousarray(W, dtype=np.int8)
     assert W.shape == (n_out, n_in)
@@ -334,14 +352,17 @@ def he_plan_run_phase(plan: int, phase: int, stream=None) -> None:
 
 def he_plan_query(plan: int, ncalls: int | None = None) -> dict:
     """The plan's he_plan_info as a dict; with ncalls, also "split": the
-    per-call split-form flags."""
+    per-call split-form (scalar MAC kernel) flags, and "form": per call 0
+    (fused channel kernel), 1 (split form, scalar MAC kernel) or 2
+    (tensor-core MAC kernel)."""
     info = he_plan_info()
     sp = None if ncalls is None else np.zeros(ncalls, dtype=np.uint8)
     _check(lib().he_plan_query(plan, ctypes.byref(info), None if sp is None else sp.ctypes.data))
     out = {n: getattr(info, n) for n, _ in he_plan_info._fields_ if n != "tuning"}
     out["tuning"] = _tuning_dict(info.tuning)
     if sp is not None:
-        out["split"] = [bool(x) for x in sp]
+        out["split"] = [int(x) == 1 for x in sp]
+        out["form"] = [int(x) for x in sp]
     return out
 
 
