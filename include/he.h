@@ -159,7 +159,7 @@ he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w,
  * memory differs.  For B >= 4 and a layer whose per-block contraction
  * (Sec. III-A: channel n's valid slots of one block of s NTT slots are
  * sum over the G*s input words of that block of weight x input) has
- * K = G*s in [32, 256], a multiple of 16, with s >= 8 and co a multiple of
+ * K = G*s in [32, 256], a multiple of 32, with s >= 8 and co a multiple of
  * 64, the bank is laid out per (limb, block, 64 channels) as a K-major
  * matrix, and plan calls of up to 8 ciphertexts on it run the channel sum
  * on the tensor cores (exact: 8-bit limbs in fp16, fp32 sums below 2^24).

@@ -668,15 +668,14 @@ cudaError_t build_tc_tables(he_plan_s *pl, const std::vector<CallDesc> &descs, c
             tl.r32 = K.r32;
             tl.r32s = K.r32s;
             tl.ones = K.ones;
-            tl.w16 = (uint32_t)((1ull << 16) % K.q);
-            tl.w16s = (uint32_t)(((uint64_t)tl.w16 << 32) / K.q);
         }
-        // inputs [B][G][2][L][N] as a 5-D tensor, innermost first; one box is
-        // the s slots of one block of one limb for every (b, g, j)
-        const cuuint64_t dims[5] = {g.N, g.L, 2, g.G, B};
+        // inputs [B][G][2][L][N] as a 5-D tensor with dimensions (slot, limb,
+        // j, b, g), innermost first; one box is the s slots of one block of
+        // one limb for every (g, b, j), landing as [g][b][j][s]
+        const cuuint64_t dims[5] = {g.N, g.L, 2, B, g.G};
         const cuuint64_t strides[4] = {(cuuint64_t)g.N * 4u, (cuuint64_t)g.L * g.N * 4u,
-                                       (cuuint64_t)2u * g.L * g.N * 4u, (cuuint64_t)g.G * 2u * g.L * g.N * 4u};
-        const cuuint32_t box[5] = {g.s, 1, 2, g.G, B};
+                                       (cuuint64_t)g.G * 2u * g.L * g.N * 4u, (cuuint64_t)2u * g.L * g.N * 4u};
+        const cuuint32_t box[5] = {g.s, 1, 2, B, g.G};
         const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
         CUtensorMap m;
         const CUresult r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, const_cast<uint32_t *>(g.x), dims, strides,

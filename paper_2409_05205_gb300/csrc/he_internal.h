@@ -146,7 +146,7 @@ constexpr uint32_t kTcMaxK = 256;    // the fp32 sums of 8-bit limb products sta
 constexpr uint32_t kTcMinBatch = 4;  // he_pack_filters_for_batch picks this layout from B = 4 up
 __host__ __device__ __forceinline__ bool tc_shape_ok(uint32_t s, uint32_t G, uint32_t co) {
     const uint32_t K = G * s;
-    return s >= 8 && (K & 15u) == 0 && K >= 32 && K <= kTcMaxK && (co & (kTcRows - 1u)) == 0;
+    return s >= 8 && (K & 31u) == 0 && K >= 32 && K <= kTcMaxK && (co & (kTcRows - 1u)) == 0;
 }
 __host__ __device__ __forceinline__ size_t bank_index_tc(uint32_t n, uint32_t l, uint32_t g, uint32_t k,
                                                          uint32_t logs, uint32_t M, uint32_t G, uint32_t co) {
@@ -159,13 +159,12 @@ __host__ __device__ __forceinline__ size_t bank_index_tc(uint32_t n, uint32_t l,
 // Limb constants of the tensor-core MAC kernel's epilogue.
 struct TcLimb {
     uint32_t q, q2, r32, r32s, ones;  // as LimbK
-    uint32_t w16, w16s;               // 2^16 mod q and its Shoup constant
-    uint32_t pad;
+    uint32_t pad[3];
 };
 // One Conv call of a plan on the tensor-core MAC kernel (device table; the
 // tensor map must sit at a 64-byte boundary).
 struct alignas(64) TcCall {
-    uint64_t xmap[16];        // CUtensorMap of the NTT-domain inputs [B][G][2][L][N], box (s, 1, 2, G, B)
+    uint64_t xmap[16];        // CUtensorMap of the NTT-domain inputs [B][G][2][L][N], dims (slot, l, j, b, g), box (s, 1, 2, B, G)
     const uint32_t *bank;     // tensor-core layout, bank_index_tc
     uint32_t *z;              // folded sums, channel-fastest: [L][2B][M][co]
     uint32_t K, s, logs, G, co, M, ncols, xbytes;

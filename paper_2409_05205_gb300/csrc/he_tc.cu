@@ -8,29 +8,33 @@
 // factor, X the NTT-domain ciphertext polynomials: a dense [co x K] x
 // [K x 2B] product per block.  The tensor cores evaluate it exactly on
 // 8-bit limbs: a residue a < 2^30 is sum_i a_i 2^(8i) with a_i < 256, every
-// a_i is an exact fp16 value, and sum_kk a_i x_j <= K * 255^2 < 2^24 for
-// K <= 256, so the fp32 accumulators hold exact integers.  The epilogue
+// a_i is an exact fp16 value (the subnormal a_i 2^-24), and
+// sum_kk a_i x_j <= K * 255^2 < 2^24 for K <= 256, so the fp32 accumulators
+// hold exact integers (in units of 2^-48).  The epilogue
 // recombines sum_{i,j} 2^(8(i+j)) D_ij and reduces mod q_l.
 //
 // One tile = (limb, block, 64 output channels) x 16 columns:
 //   A (TMEM, M = 128 rows): rows 0..63 hold limbs {0, 1} of the 64 channels'
 //     weights, rows 64..127 limbs {2, 3}; two MMAs per K-step (p = 0, 1)
 //     take limb p from the low rows and limb p + 2 from the high rows.
-//   B (shared memory, N = 64 rows, K-major, no swizzle): row j*16 + col is
-//     limb j of ciphertext polynomial col.
+//   B (shared memory, N = 64 rows, K-major, no swizzle): row
+//     32 (col / 8) + 4 (col % 8) + j is limb j of ciphertext polynomial col.
 //   D_p (TMEM, fp32, 128 lanes x 64 columns, double-buffered).
 //
-// Warp roles (384 threads, one CTA per SM, persistent over a list of
+// Warp roles (512 threads, one CTA per SM, persistent over a list of
 // items = (call, limb, range of blocks)):
 //   warp 0       producer: bulk copies of the weight tiles into a ring of
-//                16 KB stages, one 5-D tensor copy of a block's inputs;
+//                16 KB stages, one 5-D tensor copy of a block's inputs
+//                (box (s, 1, 2, B, G): [g][col][k'] in shared memory);
 //                allocates and frees the tensor memory
 //   warp 1       MMA issuer (one thread)
-//   warps 2..5   A builders: weight words from the ring -> fp16 limbs ->
-//                tcgen05.st into an A slot of tensor memory
-//   warps 6..9   epilogue: tcgen05.ld of D, exact recombination, mod q,
-//                the high rows' share through shared memory, z stores
-//   warps 10..11 B builders: a block's input words -> fp16 limb rows
+//   warps 2..5   A builders, one per sub-partition: weight words from the
+//                ring -> fp16 limbs -> tcgen05.st into an A slot of tensor
+//                memory
+//   warps 6..13  epilogue, two per sub-partition (columns 0..7 / 8..15):
+//                tcgen05.ld of D, exact recombination, mod q, the high
+//                rows' share through shared memory, z stores
+//   warps 14..15 B builders: a block's input words -> fp16 limb rows
 // Every wait is bounded; a wait that gives up raises an abort flag that
 // every other wait sees, sets bit 1 of the plan status, and the CTA winds
 // down, with its copies and MMAs drained before the tensor memory is freed.
@@ -39,7 +43,8 @@
 
 namespace {
 
-constexpr uint32_t kTcThreads = 384;
+constexpr uint32_t kTcThreads = 512;         // 16 warps
+constexpr uint32_t kWarpE0 = 6, kWarpB0 = 14;  // first epilogue / B-builder warp (A builders: warps 2..5)
 constexpr uint32_t kWStageBytes = 16384;
 constexpr uint32_t kWStages = 6;
 constexpr uint32_t kASlots = 16;               // A slots of 16 TMEM columns (one K-step)
@@ -47,8 +52,8 @@ constexpr uint32_t kTmemCols = 512;            // D: 2 x 2 x 64 columns; A: 16 x
 constexpr uint32_t kXRawBytes = kTcMaxK * kTcCols * 4;      // 16 KB
 constexpr uint32_t kBOpBytes = 64 * kTcMaxK * 2;            // 32 KB
 constexpr uint32_t kXchgBytes = kTcCols * kTcRows * 4;      // 4 KB
-constexpr uint32_t kTcSpin = 1u << 20;
-constexpr uint32_t kMagic = 0x4B000000u;       // bits of 2^23 as fp32
+constexpr uint32_t kTcSpin = 1u << 16;   // tests of a phase before a wait gives up (each up to kSuspendNs)
+constexpr uint32_t kMagic = 0x33000000u;       // bits of 2^-25 as fp32: 2^23 units of 2^-48
 
 struct TcBars {
     uint64_t w_full[kWStages], w_empty[kWStages];
@@ -79,12 +84,16 @@ __device__ __forceinline__ void bar_arrive(uint64_t *b) {
 __device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
 }
+// One test of the phase; a waiting thread is suspended for up to
+// kSuspendNs (or until the phase completes) instead of spinning, so that
+// waiting warps leave the issue slots to the working ones.
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
+        : "r"(su32(b)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -121,6 +130,15 @@ __device__ __forceinline__ void tensor5_g2s(void *dst, const void *tmap, uint32_
         : "memory");
 }
 
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_commit(uint64_t *b) {
@@ -143,62 +161,66 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
-// fp16 pair (a byte i, b byte i) as exact values 0..255: the bytes go under
-// the exponent of 1024 (0x64XX = 1024 + XX), then 1024 is subtracted.
+// fp16 pair (a byte i, b byte i): a byte XX as the fp16 bits 0x00XX is the
+// subnormal XX * 2^-24, exact; the tensor cores take fp16 subnormals as they
+// are, so every product is an exact multiple of 2^-48 and the fp32 sums of
+// a tile stay exact integers times 2^-48 (below 2^24 of them).
 template <int I>
 __device__ __forceinline__ uint32_t limb_pair(uint32_t a, uint32_t b) {
     constexpr uint32_t sel = I | (I << 4) | ((4 + I) << 8) | ((4 + I) << 12);
-    const uint32_t t = (__byte_perm(a, b, sel) & 0x00FF00FFu) | 0x64006400u;
-    uint32_t r;
-    asm("sub.f16x2 %0, %1, %2;" : "=r"(r) : "r"(t), "r"(0x64006400u));
-    return r;
-}
-__device__ __forceinline__ uint32_t limb_pair_rt(uint32_t a, uint32_t b, uint32_t i) {
-    switch (i) {
-        case 0: return limb_pair<0>(a, b);
-        case 1: return limb_pair<1>(a, b);
-        case 2: return limb_pair<2>(a, b);
-        default: return limb_pair<3>(a, b);
-    }
+    return __byte_perm(a, b, sel) & 0x00FF00FFu;
 }
 
-#define TC_LD8(base, v)                                                                                   \
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"                  \
-                 : "=r"((v)[0]), "=r"((v)[1]), "=r"((v)[2]), "=r"((v)[3]), "=r"((v)[4]), "=r"((v)[5]), \
-                   "=r"((v)[6]), "=r"((v)[7])                                                              \
+#define TC_ST32_CONST(base, k)                                                                     \
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "                                             \
+                 "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" \
+                 ::"r"(base), "r"(k)                                                                        \
+                 : "memory")
+
+#define TC_LD16(base, v)                                                                                 \
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
+                 : "=r"((v)[0]), "=r"((v)[1]), "=r"((v)[2]), "=r"((v)[3]), "=r"((v)[4]), "=r"((v)[5]),    \
+                   "=r"((v)[6]), "=r"((v)[7]), "=r"((v)[8]), "=r"((v)[9]), "=r"((v)[10]), "=r"((v)[11]),   \
+                   "=r"((v)[12]), "=r"((v)[13]), "=r"((v)[14]), "=r"((v)[15])                              \
                  : "r"(base))
 
-// exact integer of an fp32 accumulator (< 2^23 with the magic add, else F2I)
+// The epilogue of one tile for this thread's row: 4 columns of its two
+// limbs p (limb 2*high + p), v[p][4c + j] = D_p for (column c, limb j) in units of
+// 2^-48, become val = sum_{p,j} 2^(8(p+j)) D_pj < 2^57 (not reduced).  Tiles
+// with K <= 128 accumulate on top of 2^-25 = 2^23 units (the tensor memory is
+// prefilled), where the fp32 step is exactly one unit: the bits are 2^-25's
+// bits + D and need no conversion; the 2^-25 terms are removed once from the
+// recombined value (kMagicSum).  Longer tiles accumulate from 0 (D < 2^24)
+// and convert with a multiplication by 2^48 and F2I.
+constexpr uint64_t kMagicSum = (uint64_t)kMagic * (1ull + (2ull << 8) + (2ull << 16) + (2ull << 24) + (1ull << 32));
 template <bool kBig>
-__device__ __forceinline__ uint32_t acc_int(uint32_t bits) {
-    if constexpr (kBig) return __float2uint_rz(__uint_as_float(bits));
-    return __float_as_uint(__uint_as_float(bits) + 8388608.0f) - kMagic;
-}
-
-// The epilogue of one tile for this thread's row: 8 columns (c0 .. c0+7) of
-// its two limbs; v[p][j][c] = D_p[(j, c0 + c)].
-template <bool kBig>
-__device__ __forceinline__ void recombine8(const uint32_t (&v)[2][4][8], const TcLimb &K, bool high,
-                                           uint32_t *res) {
-    LimbK k;
-    k.q = K.q;
-    k.q2 = K.q2;
-    k.r32 = K.r32;
-    k.r32s = K.r32s;
-    k.ones = K.ones;
+__device__ __forceinline__ void recombine4(const uint32_t (&v)[2][16], uint64_t *val) {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < 4; ++c) {
         uint32_t u[2][4];
 #pragma unroll
         for (int p = 0; p < 2; ++p)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) u[p][j] = acc_int<kBig>(v[p][j][c]);
+            for (int j = 0; j < 4; ++j)
+                u[p][j] = kBig ? __float2uint_rz(__uint_as_float(v[p][4 * c + j]) * 281474976710656.0f) : v[p][4 * c + j];
         const uint32_t S1 = u[0][1] + u[1][0], S2 = u[0][2] + u[1][1], S3 = u[0][3] + u[1][2];
-        const uint64_t val = (uint64_t)u[0][0] + ((uint64_t)S1 << 8) + ((uint64_t)S2 << 16) + ((uint64_t)S3 << 24) +
-                             ((uint64_t)u[1][3] << 32);
-        uint32_t r = reduce64(val, k);
-        if (high) r = red_2q(shoup_lazy(r, K.w16, K.w16s, K.q), K.q);  // limbs 2, 3 carry 2^16
-        res[c] = r;
+        // u00 + S1 2^8 + S2 2^16 + S3 2^24 (wide multiply-adds) + u13 2^32
+        uint64_t x = (uint64_t)S1 * 256u + u[0][0];
+        x = (uint64_t)S2 * 65536u + x;
+        x = (uint64_t)S3 * 16777216u + x;
+        x += (uint64_t)u[1][3] << 32;
+        if (!kBig) x -= kMagicSum;
+        val[c] = x;
+    }
+}
+
+// A operand words of one K-step for limbs I and I + 1 of 16 weight words
+template <int I>
+__device__ __forceinline__ void limbs16(const uint32_t (&w)[16], uint32_t (&r)[16]) {
+#pragma unroll
+    for (int pp = 0; pp < 8; ++pp) {
+        r[pp] = limb_pair<I>(w[2 * pp], w[2 * pp + 1]);
+        r[8 + pp] = limb_pair<I + 1>(w[2 * pp], w[2 * pp + 1]);
     }
 }
 
@@ -228,7 +250,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
             bar_init(&bars.b_full[i], 2);
             bar_init(&bars.b_empty[i], 1);
             bar_init(&bars.d_full[i], 1);
-            bar_init(&bars.d_empty[i], 4);
+            bar_init(&bars.d_empty[i], 8);
         }
         for (uint32_t i = 0; i < kASlots; ++i) {
             bar_init(&bars.a_full[i], 4);
@@ -336,12 +358,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                     tc_fence_after();
                     const uint32_t baddr = su32(bop + bb * kBOpBytes);
                     for (uint32_t ch = 0; ok && ch < nch; ++ch) {
+                        // the epilogue refills a buffer with 2^23 (and frees it) after
+                        // reading it, and fills both once at the start
                         const uint32_t db = ds & 1u;
-                        if (ds >= 2 && !bar_wait(&bars.d_empty[db], ((ds >> 1) - 1u) & 1u, abort)) {
+                        if (!bar_wait(&bars.d_empty[db], (ds >> 1) & 1u, abort)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
+                        const uint32_t acc0 = C.K > 128u ? 0u : 1u;
                         for (uint32_t ks = 0; ks < nks; ++ks) {
                             const uint32_t slot = as % kASlots;
                             if (!bar_wait(&bars.a_full[slot], (as / kASlots) & 1u, abort)) {
@@ -353,7 +378,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
 #pragma unroll
                             for (uint32_t p = 0; p < 2; ++p)
                                 tc_mma(tmem + 128u * db + 64u * p, tmem + 256u + 16u * slot + 8u * p, bdesc, idesc,
-                                       ks > 0 ? 1u : 0u);
+                                       ks > 0 ? 1u : acc0);
                             tc_commit(&bars.a_empty[slot]);
                             ++as;
                         }
@@ -370,11 +395,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
             tc_commit(&bars.fin);
             bar_drain(&bars.fin, 0);
         }
-    } else if (warp < 6) {
+    } else if (warp < kWarpE0) {
         // ------------------------------------------------------------ A builders
-        const uint32_t sp = warp & 3u, tl = 32u * sp + lane, n = tl & 63u, high = tl >> 6;
+        // Software-pipelined: K-step k+1 is read and converted while the
+        // tensor-memory store of K-step k completes; then k is signalled.
+        const uint32_t sp = warp & 3u;
+        const uint32_t tl = 32u * sp + lane, n = tl & 63u;
+        const bool high = tl >= 64u;
         const uint32_t taddr = tmem + ((32u * sp) << 16) + 256u;
-        uint32_t ws = 0, as = 0;
+        uint32_t ws = 0, as = 0, pend = kASlots;  // pend: slot stored but not yet signalled
         bool ok = true;
         for (uint32_t it = ib; ok && it < ie; ++it) {
             const TcItem item = items[it];
@@ -382,7 +411,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
             const uint32_t nch = C.co / kTcRows, nks = C.K / 16u;
             for (uint32_t b = item.b0; ok && b < item.b0 + item.nb; ++b)
                 for (uint32_t ch = 0; ok && ch < nch; ++ch)
-                    for (uint32_t ks = 0; ks < nks; ++ks) {
+                    for (uint32_t ks = 0; ks < nks; ++ks, ++as) {
                         const uint32_t st = ws % kWStages;
                         if ((ks & 3u) == 0 && !bar_wait(&bars.w_full[st], (ws / kWStages) & 1u, abort)) {
                             ok = false;
@@ -393,7 +422,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                             ok = false;
                             break;
                         }
-                        // this K-step's 16 words of row n: [kq][64 rows][4 words], kq = 4 (ks % 4) .. + 3
+                        // this K-step's 16 words of row n: [kq][64 rows][4 words]
                         const uint4 *src =
                             reinterpret_cast<const uint4 *>(wring + st * kWStageBytes + (ks & 3u) * 4096u) + n;
                         uint32_t w[16];
@@ -406,11 +435,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                             w[4 * kq + 3] = v.w;
                         }
                         uint32_t r[16];
-                        const uint32_t i0 = 2u * high;
-#pragma unroll
-                        for (int pp = 0; pp < 8; ++pp) {
-                            r[pp] = limb_pair_rt(w[2 * pp], w[2 * pp + 1], i0);
-                            r[8 + pp] = limb_pair_rt(w[2 * pp], w[2 * pp + 1], i0 + 1u);
+                        if (high)
+                            limbs16<2>(w, r);
+                        else
+                            limbs16<0>(w, r);
+                        // the stage's words are in registers: its last K-step frees it
+                        if ((ks & 3u) == 3u || ks + 1u == nks) {
+                            __syncwarp();
+                            if (lane == 0) bar_arrive(&bars.w_empty[st]);
+                            ++ws;
+                        }
+                        if (pend < kASlots) {  // K-step as-1 has landed in tensor memory
+                            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) bar_arrive(&bars.a_full[pend]);
                         }
                         asm volatile(
                             "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
@@ -419,84 +458,129 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                             "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
                             "r"(r[15])
                             : "memory");
-                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) bar_arrive(&bars.a_full[slot]);
-                        ++as;
-                        if ((ks & 3u) == 3u || ks + 1u == nks) {
-                            if (lane == 0) bar_arrive(&bars.w_empty[st]);
-                            ++ws;
-                        }
+                        pend = slot;
                     }
         }
-    } else if (warp < 10) {
+        if (pend < kASlots) {
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            __syncwarp();
+            if (ok && lane == 0) bar_arrive(&bars.a_full[pend]);
+        }
+    } else if (warp < kWarpB0) {
         // ------------------------------------------------------------ epilogue
-        // Every warp passes the named barrier once per tile, also after an
+        // Warp (sub-partition sp, column half hc) takes columns 8 hc .. 8 hc + 7
+        // of its 32 rows.  The high rows (limbs 2, 3) reduce their share and
+        // pass it through shared memory; the low rows add it times 2^16 to
+        // their own sum, reduce once and store.  The four warps of a column
+        // half meet at named barrier 1 + hc once per tile, also after an
         // abort, so that no warp waits there for one that has left.
-        const uint32_t sp = warp & 3u, tl = 32u * sp + lane, n = tl & 63u;
+        const uint32_t sp = warp & 3u, hc = (warp - kWarpE0) >> 2;
+        const uint32_t tl = 32u * sp + lane, n = tl & 63u;
         const bool high = tl >= 64u;
-        const uint32_t lrow = tmem + ((32u * sp) << 16);
+        // B rows (and so D columns) are ordered (hc, column c % 8, limb j): this
+        // warp's accumulators are D_p columns 32 hc .. 32 hc + 31
+        const uint32_t lrow = tmem + ((32u * sp) << 16) + 32u * hc;
+        // prefill both accumulator buffers with 2^23 and free them
+#pragma unroll
+        for (uint32_t db = 0; db < 2; ++db)
+#pragma unroll
+            for (uint32_t p = 0; p < 2; ++p) TC_ST32_CONST(lrow + 128u * db + 64u * p, kMagic);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) {
+            bar_arrive(&bars.d_empty[0]);
+            bar_arrive(&bars.d_empty[1]);
+        }
         uint32_t ds = 0;
         bool ok = true;
         for (uint32_t it = ib; it < ie; ++it) {
             const TcItem item = items[it];
             const TcCall &C = calls[item.call];
             const uint32_t nch = C.co / kTcRows, ncols = C.ncols, M = C.M, co = C.co;
-            const TcLimb K = C.limb[item.l];
+            LimbK K;
+            K.q = C.limb[item.l].q;
+            K.q2 = C.limb[item.l].q2;
+            K.r32 = C.limb[item.l].r32;
+            K.r32s = C.limb[item.l].r32s;
+            K.ones = C.limb[item.l].ones;
             const bool big = C.K > 128u;
-            uint32_t *zb = C.z + (size_t)item.l * ncols * M * co + n;
+            uint32_t *zb = C.z + ((size_t)item.l * ncols + 8u * hc) * M * co + n;
             const size_t cstride = (size_t)M * co;
             for (uint32_t b = item.b0; b < item.b0 + item.nb; ++b)
                 for (uint32_t ch = 0; ch < nch; ++ch) {
                     const uint32_t db = ds & 1u;
                     ok = ok && bar_wait(&bars.d_full[db], (ds >> 1) & 1u, abort);
-                    uint32_t res[16];
+                    uint64_t val[8];
+                    // this lane's word of column 0 of its half in the exchange buffer
+                    const uint32_t xa = su32(xchg + db * (kTcCols * kTcRows) + 8u * hc * kTcRows + n);
                     if (ok) {
                         tc_fence_after();
+                        // two groups of 4 columns keep 32 accumulators live at a time
 #pragma unroll
-                        for (uint32_t half = 0; half < 2; ++half) {
-                            uint32_t v[2][4][8];
+                        for (uint32_t g4 = 0; g4 < 2; ++g4) {
+                            uint32_t v[2][16];
 #pragma unroll
-                            for (uint32_t p = 0; p < 2; ++p)
-#pragma unroll
-                                for (uint32_t j = 0; j < 4; ++j)
-                                    TC_LD8(lrow + 128u * db + 64u * p + 16u * j + 8u * half, v[p][j]);
+                            for (uint32_t p = 0; p < 2; ++p) TC_LD16(lrow + 128u * db + 64u * p + 16u * g4, v[p]);
                             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                            if (half == 1) {
-                                tc_fence_before();
-                                __syncwarp();
-                                if (lane == 0) bar_arrive(&bars.d_empty[db]);
-                            }
                             if (big)
-                                recombine8<true>(v, K, high, res + 8 * half);
+                                recombine4<true>(v, val + 4 * g4);
                             else
-                                recombine8<false>(v, K, high, res + 8 * half);
+                                recombine4<false>(v, val + 4 * g4);
+                        }
+                        // refill with 2^-25 and free the buffer
+#pragma unroll
+                        for (uint32_t p = 0; p < 2; ++p) TC_ST32_CONST(lrow + 128u * db + 64u * p, kMagic);
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) bar_arrive(&bars.d_empty[db]);
+                        if (high) {  // all 8 reductions, then the 8 shared stores
+                            uint32_t r[8];
+#pragma unroll
+                            for (uint32_t c = 0; c < 8; ++c) r[c] = reduce64(val[c], K);
+#pragma unroll
+                            for (uint32_t c = 0; c < 8; ++c) sts32(xa + 4u * (c * kTcRows), r[c]);
                         }
                     }
-                    uint32_t *xc = xchg + db * (kTcCols * kTcRows);
-                    if (ok && high)
+                    if (hc == 0)
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                    else
+                        asm volatile("bar.sync 2, 128;" ::: "memory");
+                    if (ok && !high) {  // the 8 shares, the 8 reductions, then the stores
+                        uint32_t hx[8], r[8];
 #pragma unroll
-                        for (uint32_t c = 0; c < kTcCols; ++c) xc[c * kTcRows + n] = res[c];
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                    if (ok && !high) {
+                        for (uint32_t c = 0; c < 8; ++c) hx[c] = lds32(xa + 4u * (c * kTcRows));
+#pragma unroll
+                        for (uint32_t c = 0; c < 8; ++c) r[c] = reduce64(val[c] + ((uint64_t)hx[c] << 16), K);
                         uint32_t *z = zb + (size_t)b * co + ch * kTcRows;
 #pragma unroll
-                        for (uint32_t c = 0; c < kTcCols; ++c)
-                            if (c < ncols) z[c * cstride] = red_2q(res[c] + xc[c * kTcRows + n], K.q);
+                        for (uint32_t c = 0; c < 8; ++c)
+                            if (8u * hc + c < ncols) z[c * cstride] = r[c];
                     }
                     ++ds;
                 }
         }
     } else {
         // ------------------------------------------------------------ B builders
-        const uint32_t xt = tid - 320u;
+        // B row r = 32 hc + 4 (c % 8) + j holds limb j of column c = 8 hc + c % 8.
+        // A block's inputs arrive as [g][col][k'] (the tensor map's box is
+        // (s, 1, 2, B, G)).  One pass of a warp builds 8 elements (kk0 .. kk0+7,
+        // kk0 = 8 kg) of the 32 rows of one half hc: lane = r % 32 reads its
+        // column's 8 words (the 4 lanes of a column read the same words) and
+        // stores its limb's 16 bytes, so a warp's stores fill 512 contiguous
+        // bytes (four core matrices).
+        const uint32_t wb = warp - kWarpB0;
+        const uint32_t cl = lane >> 2, j = lane & 3u;
+        const uint32_t sel = j * 0x1111u + 0x4400u;  // bytes j of the two words, in the low byte of each half
         uint32_t xs = 0, bs = 0;
         bool ok = true;
         for (uint32_t it = ib; ok && it < ie; ++it) {
             const TcItem item = items[it];
             const TcCall &C = calls[item.call];
-            const uint32_t kgn = C.K / 8u, total = C.ncols * kgn, s = C.s, logs = C.logs, G = C.G;
+            const uint32_t kgn = C.K / 8u, ncols = C.ncols, s = C.s, logs = C.logs;
+            const uint32_t lnh = ncols > 8u ? 1u : 0u, npass = kgn << lnh;  // halves of 8 columns: 1 or 2
             for (uint32_t b = item.b0; b < item.b0 + item.nb; ++b) {
                 const uint32_t xb = xs & 1u, bb = bs & 1u;
                 if (!bar_wait(&bars.x_full[xb], (xs >> 1) & 1u, abort)) {
@@ -509,21 +593,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                 }
                 const uint32_t *raw = reinterpret_cast<const uint32_t *>(xraw + xb * kXRawBytes);
                 uint8_t *B = bop + bb * kBOpBytes;
-                for (uint32_t q = xt; q < total; q += 64u) {
-                    const uint32_t c = q / kgn, kg = q - c * kgn, kk0 = kg * 8u;
-                    const uint32_t g = kk0 >> logs, kp0 = kk0 & (s - 1u);
-                    // the tensor copy's box is [B][G][2][s]: column c = (c / 2, c % 2)
-                    const uint4 *src = reinterpret_cast<const uint4 *>(raw + (((c >> 1) * G + g) * 2u + (c & 1u)) * s + kp0);
-                    const uint4 x0 = src[0], x1 = src[1];
+                // passes wb, wb + 2, ..., four at a time (npass is a multiple of 4)
+                for (uint32_t p0 = wb; p0 < npass; p0 += 8u) {
+                    uint4 x[4][2];
+                    bool on[4];
 #pragma unroll
-                    for (uint32_t j = 0; j < 4; ++j) {
-                        const uint32_t row = j * 16u + c;
+                    for (uint32_t u = 0; u < 4; ++u) {
+                        const uint32_t ps = p0 + 2u * u, hc = ps & lnh, kg = ps >> lnh, c = 8u * hc + cl;
+                        on[u] = ps < npass && c < ncols;
+                        const uint32_t kk0 = kg * 8u, g = kk0 >> logs, kp0 = kk0 & (s - 1u);
+                        const uint4 *src = reinterpret_cast<const uint4 *>(raw + (g * ncols + c) * s + kp0);
+                        if (on[u]) {
+                            x[u][0] = src[0];
+                            x[u][1] = src[1];
+                        }
+                    }
+#pragma unroll
+                    for (uint32_t u = 0; u < 4; ++u) {
+                        const uint32_t ps = p0 + 2u * u, hc = ps & lnh, kg = ps >> lnh;
+                        if (!on[u]) continue;
                         uint4 h;
-                        h.x = limb_pair_rt(x0.x, x0.y, j);
-                        h.y = limb_pair_rt(x0.z, x0.w, j);
-                        h.z = limb_pair_rt(x1.x, x1.y, j);
-                        h.w = limb_pair_rt(x1.z, x1.w, j);
-                        *reinterpret_cast<uint4 *>(B + (kg * 8u + (row >> 3)) * 128u + (row & 7u) * 16u) = h;
+                        h.x = __byte_perm(x[u][0].x, x[u][0].y, sel) & 0x00FF00FFu;
+                        h.y = __byte_perm(x[u][0].z, x[u][0].w, sel) & 0x00FF00FFu;
+                        h.z = __byte_perm(x[u][1].x, x[u][1].y, sel) & 0x00FF00FFu;
+                        h.w = __byte_perm(x[u][1].z, x[u][1].w, sel) & 0x00FF00FFu;
+                        *reinterpret_cast<uint4 *>(B + (kg * 8u + 4u * hc + (lane >> 3)) * 128u + (lane & 7u) * 16u) = h;
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

@@ -153,6 +153,10 @@ WORKLOADS = {
     "plain20_c100_wide4": dict(N=16384, L=6, t=65537, B=8, conv=plain20_conv_layers(4),
                                fc=dict(n_in=256, n_out=100), wlo=-128, whi=127),
     "batched64": dict(t=65537, calls=batched_calls(3, 64), wlo=-128, whi=127),
+    # one layer of the wide x4 network (64 -> 64 channels at 32x32, N = 16384,
+    # 6 limbs, B = 8): a small case of its MAC kernel for profiling
+    "wide4_64x64": dict(N=16384, L=6, t=65537, B=8, conv=[dict(ci=64, co=64, h=32, w=32, stride=1, fh=3, fw=3, pad=1)],
+                        fc=None, wlo=-128, whi=127),
 }
 
 
