@@ -23,7 +23,10 @@ Contents, each citing the passage it follows:
     (``tier="ntt"``), both in he_oracle.c;
   * a BFV-style RLWE encrypt/decrypt over the same ring with CRT
     recombination (Sec. II-A encryption / decryption, restated for an
-    integer plaintext modulus t).
+    integer plaintext modulus t);
+  * the paper's whole Conv protocol (Alg. 1): the masked server step, the
+    server's p1 / p2 for the client, the client's c1 share and the
+    key-free decode of c0^r + c1^r.
 
 Parity pins (tests/test_oracle_*.py) tie every function here to something
 other than itself: library routines (numpy.convolve, scipy.signal.correlate2d,
@@ -529,6 +532,97 @@ def conv_layer_sampled(cts: np.ndarray, F: np.ndarray, primes: list[int],
         w = to_residues(fh[n], q)
         out[i] = sum_products_coeffs(a, w, q, np.array([k]))[0]
     return out
+
+
+# ----------------------------------------------------------------------------
+# The paper's whole Conv protocol (Alg. 1): the server's masks rho, the
+# client's c1 share, the random output share sh'.  Read for an integer
+# plaintext modulus t: no rescale, every plaintext term scaled by
+# Delta_Q = floor(Q / t), masks and shares drawn in [0, t) by the caller.
+# ----------------------------------------------------------------------------
+
+def conv_layer_masked(c0: np.ndarray, sh: np.ndarray, rho: np.ndarray, F: np.ndarray,
+                      shp: np.ndarray, primes: list[int], psis: list[int], t: int,
+                      lay: dict, tier: str = "schoolbook") -> np.ndarray:
+    """Server evaluation of Alg. 1 (the evaluation loop, the slot-copy loop
+    and the share addition):
+        y_n = sum_g c0_g * rho_{g,n} - Delta_Q * sh_g * fhat_{g,n}   (mod q_l)
+        out_h = extract(y)_h + Delta_Q * sh'_h
+    c0:  [B][G][L][N] residues, the c0 part of Enc(-(i + sh)) per input group;
+    sh:  [B][G][N] integers in [0, t), the server's share of this layer's
+         (packed) input;
+    rho: [co][G][N] integers in [0, t), the masks rho_{g,n};
+    shp: [B][H][N] integers in [0, t), the share sh' added to the output.
+    Returns [B][H][L][N] residues."""
+    B, G, L, N = c0.shape
+    assert G == lay["G"] and N == lay["N"] and L == len(primes)
+    fh = pack_filters(F, lay)
+    co, H = lay["co"], lay["H"]
+    D = delta_q(primes, t)
+    out = np.zeros((B, H, L, N), dtype=np.uint32)
+    for l, (q, psi) in enumerate(zip(primes, psis)):
+        Dq = D % q
+        dsh = (np.asarray(sh, dtype=np.uint64) % q) * Dq % q                  # Delta sh  [B][G][N]
+        x = np.concatenate([c0[:, :, l, :].astype(np.uint32), dsh.astype(np.uint32)], axis=1)
+        x = np.ascontiguousarray(x.transpose(1, 0, 2))                          # [2G][B][N]
+        w = np.concatenate([to_residues(rho, q), to_residues(-fh, q)], axis=1)  # [co][2G][N]
+        y = _sum_products(x, w, q, psi, tier)                                   # [co][B][N]
+        for b in range(B):
+            ex = extract_conv(y[:, b, :], lay).astype(np.uint64)               # [H][N]
+            out[b, :, l, :] = ((ex + Dq * (np.asarray(shp[b], np.uint64) % q)) % q).astype(np.uint32)
+    return out
+
+
+def masked_server_init(F: np.ndarray, rho: np.ndarray, b_pk: np.ndarray, e1: np.ndarray,
+                       e2: np.ndarray, primes: list[int], t: int, lay: dict) -> tuple:
+    """Alg. 1 server initialisation, per group g and output channel n:
+        p1_{g,n} = rho_{g,n} * b + e1_{g,n},
+        p2_{g,n} = Delta_Q * (fhat_{g,n} + rho_{g,n}) + e2_{g,n}     (mod q_l).
+    b_pk: [L][N] residues of the public key's b = -a*s + e; e1, e2: [co][G][N]
+    small integers.  Returns p1, p2: [co][G][L][N]."""
+    fh = pack_filters(F, lay)
+    co, G, N = fh.shape
+    L = len(primes)
+    D = delta_q(primes, t)
+    p1 = np.zeros((co, G, L, N), dtype=np.uint32)
+    p2 = np.zeros((co, G, L, N), dtype=np.uint32)
+    for l, q in enumerate(primes):
+        for n in range(co):
+            for g in range(G):
+                p1[n, g, l] = ((negacyclic_mul(to_residues(rho[n, g], q), b_pk[l], q).astype(np.int64)
+                                + np.asarray(e1[n, g], np.int64)) % q).astype(np.uint32)
+                m = (np.asarray(fh[n, g], np.int64) + np.asarray(rho[n, g], np.int64)) % q
+                p2[n, g, l] = (((D % q) * m + np.asarray(e2[n, g], np.int64)) % q).astype(np.uint32)
+    return p1, p2
+
+
+def client_c1_masked(v: np.ndarray, ish: np.ndarray, p1: np.ndarray, p2: np.ndarray,
+                     primes: list[int], lay: dict) -> np.ndarray:
+    """Client side of Alg. 1 (the loop after the server's reply), with the
+    sign that cancels the server's mask term v rho b:
+        c1^(n) = sum_g -v_g * p1_{g,n} + (i + sh)_g * p2_{g,n},
+    then the same slot copy as the server's.  v: [G][N] the client's
+    encryption randomness of each group; ish: [G][N] integers, the packed
+    layer input plus the share.  Returns [H][L][N]."""
+    co, G, L, N = p1.shape
+    out = np.zeros((lay["H"], L, N), dtype=np.uint32)
+    for l, q in enumerate(primes):
+        y = np.zeros((co, N), dtype=np.uint64)
+        for n in range(co):
+            acc = np.zeros(N, dtype=np.uint64)
+            for g in range(G):
+                acc += negacyclic_mul(to_residues(-np.asarray(v[g], np.int64), q), p1[n, g, l], q)
+                acc += negacyclic_mul(to_residues(ish[g], q), p2[n, g, l], q)
+            y[n] = acc % q
+        out[:, l, :] = extract_conv(y, lay).astype(np.uint32)
+    return out
+
+
+def decode_scaled(r: np.ndarray, primes: list[int], t: int) -> np.ndarray:
+    """round(t [r]_Q / Q) mod t, centered: the plaintext of a sum c0^r + c1^r,
+    which needs no secret key (Alg. 1's last line).  r: [L][N] -> int64 [N]."""
+    L, N = r.shape
+    return decrypt(np.stack([r, np.zeros_like(r)]), np.zeros(N, np.int64), primes, t)
 
 
 def fc_layer(ct: np.ndarray, W: np.ndarray, Bv: np.ndarray | None,
