@@ -222,6 +222,40 @@ he_status he_conv_layer_noalloc(he_params_t p, he_filters_t f, const uint32_t *d
                                 int in_domain, uint32_t *d_out, int out_mode, uint32_t B,
                                 void *stream);
 
+/* Server model load for the paper's whole Conv protocol (Alg. 1, server
+ * initialisation): the filters of he_pack_filters and the server's masks
+ * rho_{g,n}, one random polynomial per input group g and output channel n.
+ *   w:   HOST int8 [co][ci][fh][fw], as for he_pack_filters.
+ *   rho: HOST uint32 [co][G][N], integers in [0, t) (G = the layout's input
+ *        groups).  The caller draws them (uniformly); the library keeps no copy.
+ * The bank holds, for every limb, NTT(rho_{g,n}) and NTT(-Delta_Q fhat_{g,n})
+ * (co * 2G * L * N * 4 bytes).  The matching client material p1 = rho b + e1,
+ * p2 = Delta_Q (fhat + rho) + e2 (Alg. 1, server initialisation) involves the
+ * client's public key and is not computed here.  Values of rho at or above t
+ * fail with HE_ERR_ARG.  Blocking. */
+he_status he_pack_masked(he_params_t p, const he_conv_desc *d, const int8_t *w, const uint32_t *rho,
+                         he_filters_t *out);
+
+/* Server evaluation of Alg. 1 for B ciphertexts (the evaluation loop, the
+ * slot-copy loop and the share addition), with an integer plaintext modulus
+ * t (every plaintext term scaled by Delta_Q = floor(Q/t), no rescale):
+ *   c0^(n) = sum_g c0_g * rho_{g,n} - Delta_Q * sh_g * fhat_{g,n},
+ *   out_h  = extract(c0^(n)) + Delta_Q * sh'_h.
+ *   d_c0:  DEVICE uint32 [B][G][L][N], the c0 part of Enc(-(i + sh)) of each
+ *          input group, in `in_domain` (HE_COEFF or HE_NTT).
+ *   d_sh:  DEVICE uint32 [B][G][N], the server's share of the (packed) layer
+ *          input, integers in [0, t), coefficient domain.
+ *   d_shp: DEVICE uint32 [B][H][N], the new share sh' (integers in [0, t))
+ *          that the server keeps as next layer's sh.
+ *   d_out: DEVICE uint32 [B][H][L][N], c0^r of Alg. 1, every word written.
+ * The client adds its own c1^r (computed from v, p1, p2) and decodes
+ * round(t (c0^r + c1^r) / Q) mod t: no secret key is involved.  f must come
+ * from he_pack_masked (other banks fail with HE_ERR_ARG; masked banks do
+ * not run in plans).  Asynchronous on `stream`. */
+he_status he_conv_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0,
+                               const uint32_t *d_sh, const uint32_t *d_shp, int in_domain,
+                               uint32_t *d_out, uint32_t B, void *stream);
+
 /* Server evaluation of one FC layer for B ciphertexts (Alg. 2 in
  * ciphertext x plaintext form, Theorem 1):
  *   y_j^(c) = c^(c) * w_j, plus Delta_Q * d_j(X) on c0 (c = 0).

@@ -299,6 +299,7 @@ he_status he_params_create(uint32_t N, uint32_t L, const uint32_t *primes, uint3
         k.ones = shoup(1u, q);
         k.ninv = pow_mod(N % q, q - 2, q);
         k.ninvs = shoup(k.ninv, q);
+        k.delta = p->delta[l];
         for (uint32_t i = 0; i < N; ++i) {
             const uint32_t e = bitrev(i, logN);
             const uint32_t wf = pow_mod(psi, e, q), wi = pow_mod(psi_inv, e, q);
@@ -449,6 +450,60 @@ he_status he_pack_filters_for_batch(he_params_t p, const he_conv_desc *d, const 
     return pack_conv(p, d, w, B, out);
 }
 
+he_status he_pack_masked(he_params_t p, const he_conv_desc *d, const int8_t *w, const uint32_t *rho,
+                         he_filters_t *out) {
+    if (!p || !d || !w || !rho || !out) return fail(HE_ERR_ARG, "NULL argument");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    *out = nullptr;
+    he_conv_layout lay{};
+    he_status st = conv_layout(p, d, &lay);
+    if (st != HE_OK) return st;
+    if (lay.s > HE_MAX_INTERLEAVE)
+        return fail(HE_ERR_UNSUPPORTED, "interleave s = %u above %d", lay.s, HE_MAX_INTERLEAVE);
+    if (fold_smem_bytes(1, lay.M) > 192u * 1024u)
+        return fail(HE_ERR_UNSUPPORTED, "N/s = %u too long for the masked step", lay.M);
+    const size_t nrho = (size_t)d->co * lay.G * p->N;
+    for (size_t i = 0; i < nrho; ++i)
+        if (rho[i] >= p->t) return fail(HE_ERR_ARG, "rho[%zu] = %u is not below t = %u", i, rho[i], p->t);
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    he_filters_s *f = new (std::nothrow) he_filters_s();
+    if (!f) return fail(HE_ERR_NOMEM, "filters");
+    f->p = p;
+    f->kind = HE_KIND_CONV;
+    f->desc = *d;
+    f->lay = lay;
+    f->masked = 1;
+    f->logTS = bank_tile_log(p->logN, lay.s, 2u * lay.G);
+    f->lcs = bank_chunk_log(f->logTS, lay.s, 2u * lay.G);
+    f->bank_bytes = (size_t)d->co * p->L * 2u * lay.G * p->N * sizeof(uint32_t);
+    const size_t wbytes = (size_t)d->co * d->ci * d->fh * d->fw;
+    int8_t *d_w = nullptr;
+    uint32_t *d_rho = nullptr;
+    cudaError_t e = cudaMalloc(&f->bank, f->bank_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const size_t nb = f->bank_bytes;
+        delete f;
+        return fail(HE_ERR_NOMEM, "masked bank of %zu bytes", nb);
+    }
+    e = cudaMalloc(&d_w, wbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d_rho, nrho * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(d_w, w, wbytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_rho, rho, nrho * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = he_launch_pack_conv_masked(p->ring, d_w, d_rho, *d, lay, f->logTS, f->lcs, f->bank, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_w);
+    cudaFree(d_rho);
+    if (e != cudaSuccess) {
+        he_filters_destroy(f);
+        return cuda_fail(e, "pack masked bank");
+    }
+    *out = f;
+    return HE_OK;
+}
+
 he_status he_filters_tensor_core(he_filters_t f, uint32_t *tc) {
     if (!f || !tc) return fail(HE_ERR_ARG, "NULL argument");
     *tc = f->kind == HE_KIND_CONV ? f->tc : 0u;
@@ -518,6 +573,7 @@ he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int
                         int out_mode, uint32_t B, void *stream) {
     if (!p || !f || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (f->kind != HE_KIND_CONV || f->p != p) return fail(HE_ERR_ARG, "filters are not a Conv bank of these params");
+    if (f->masked) return fail(HE_ERR_ARG, "a masked bank is evaluated by he_conv_layer_masked");
     if (in_domain != HE_COEFF && in_domain != HE_NTT) return fail(HE_ERR_ARG, "bad in_domain %d", in_domain);
     if (out_mode != HE_OUT_EXTRACTED && out_mode != HE_OUT_PER_CHANNEL && out_mode != HE_OUT_EXTRACTED_UNFOLDED)
         return fail(HE_ERR_ARG, "bad out_mode %d", out_mode);
@@ -541,6 +597,27 @@ he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int
     cudaError_t e = he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, f->tc, f->bank, x, d_out, out_mode, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "conv kernel");
     return HE_OK;
+}
+
+he_status he_conv_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0, const uint32_t *d_sh,
+                               const uint32_t *d_shp, int in_domain, uint32_t *d_out, uint32_t B, void *stream) {
+    if (!p || !f || !d_c0 || !d_sh || !d_shp || !d_out) return fail(HE_ERR_ARG, "NULL argument");
+    if (f->kind != HE_KIND_CONV || !f->masked) return fail(HE_ERR_ARG, "filters are not a masked Conv bank");
+    if (f->p != p) return fail(HE_ERR_ARG, "filters belong to other params");
+    if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
+    if (in_domain != HE_COEFF && in_domain != HE_NTT) return fail(HE_ERR_ARG, "bad in_domain");
+    if (!aligned16(d_c0) || !aligned16(d_sh) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    const he_conv_layout &lay = f->lay;
+    const size_t ws_words = (size_t)B * 2u * lay.G * p->L * p->N;
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    if (ensure_ws(p, ws_words * 4u) != HE_OK) return HE_ERR_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *ws = static_cast<uint32_t *>(p->ws);
+    cudaError_t e = he_launch_ntt_masked_in(p->ring, d_c0, d_sh, ws, B, lay.G, in_domain == HE_NTT, st);
+    if (e == cudaSuccess) e = he_launch_conv_masked(p->ring, f->desc, lay, f->logTS, f->lcs, f->bank, ws, d_shp, d_out, B, st);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "masked conv layer");
 }
 
 he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain, uint32_t *d_out,
@@ -764,6 +841,8 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         const he_layer_call &c = calls[i];
         const he_filters_s *f = c.filters;
         if (!f || !c.d_in || !c.d_out) return fail(HE_ERR_ARG, "call %u: NULL argument", i);
+        if (f->kind == HE_KIND_CONV && f->masked)
+            return fail(HE_ERR_UNSUPPORTED, "call %u: masked banks run through he_conv_layer_masked", i);
         const he_params_s *p = f->p;
         if (p->device != device) return fail(HE_ERR_ARG, "call %u: params on another device", i);
         if (c.B == 0) return fail(HE_ERR_ARG, "call %u: B must be >= 1", i);

@@ -27,7 +27,7 @@ struct LimbK {
     uint32_t ones;   // Shoup constant of 1 = floor(2^32 / q)
     uint32_t ninv;   // N^-1 mod q
     uint32_t ninvs;  // Shoup constant of ninv
-    uint32_t pad;
+    uint32_t delta;  // Delta_Q mod q
 };
 
 // Everything a kernel needs to know about the ring; passed by value.
@@ -76,7 +76,10 @@ struct ConvGeo {
     uint32_t lcs;             // conv bank chunk interleave (log2)
     uint32_t cs, n0, nc;      // split MAC: chunks per thread; (per item) channel range
     uint32_t tc;              // conv bank in the tensor-core layout (bank_index_tc)
-    uint32_t pad_geo[3];
+    uint32_t masked;          // the masked server step (Alg. 1): one column per ciphertext,
+                              // inputs [B][G][L][N], outputs [B][H][L][N] + Delta_Q sh'
+    uint32_t pad_geo[2];
+    const uint32_t *shp;      // masked: the output share sh' [B][H][N], integers in [0, t)
 };
 
 // Conv filter bank layout: [L][N/TS][co][G][TS] (TS = 2^lt slots, a
@@ -293,6 +296,7 @@ struct he_filters_s {
     uint32_t logTS;   // conv bank tile
     uint32_t lcs;     // conv bank chunk interleave (log2)
     uint32_t tc;      // conv bank in the tensor-core layout (bank_index_tc)
+    uint32_t masked;  // bank of the masked server step: 2G groups (rho_{g,n}, then -Delta_Q fhat_{g,n})
     uint32_t nc;      // split MAC: channels per work item
     he_fc_layout fl;
     uint32_t *bank;   // conv: [co][L][G][N]; fc: [P][L][N]; NTT domain, pre-scaled
@@ -318,6 +322,14 @@ uint32_t he_ilog2(uint32_t x);
 cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt,
                            uint32_t lcs, uint32_t tc, const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out,
                            int mode, uint32_t B, cudaStream_t st);
+cudaError_t he_launch_pack_conv_masked(const RingView &r, const int8_t *d_w, const uint32_t *d_rho,
+                                       const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt, uint32_t lcs,
+                                       uint32_t *bank, cudaStream_t st);
+cudaError_t he_launch_ntt_masked_in(const RingView &r, const uint32_t *c0, const uint32_t *sh, uint32_t *ws,
+                                    uint32_t B, uint32_t G, bool c0_ntt, cudaStream_t st);
+cudaError_t he_launch_conv_masked(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt,
+                                  uint32_t lcs, const uint32_t *bank, const uint32_t *x_ntt, const uint32_t *shp,
+                                  uint32_t *out, uint32_t B, cudaStream_t st);
 cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32_t *bank,
                          const uint32_t *bias, const uint32_t *x_ntt, uint32_t *out, int mode,
                          uint32_t B, cudaStream_t st);

@@ -111,18 +111,40 @@ __device__ __forceinline__ void ntt_body(const uint32_t *__restrict__ src, uint3
     }
 }
 
+// Column c of a Conv call: ciphertext c / 2, polynomial c % 2 ([B][G][2][L][N]
+// inputs, [B][H][2][L][N] outputs), or in the masked form ciphertext c with
+// one polynomial ([B][G][L][N] inputs, G counting the 2G groups of the
+// masked bank; [B][H][L][N] outputs).
+__device__ __forceinline__ const uint32_t *x_col(const ConvGeo &a, uint32_t c, uint32_t l) {
+    if (a.masked) return a.x + ((size_t)c * a.G * a.L + l) * a.N;
+    return a.x + ((size_t)((c >> 1) * a.G * 2 + (c & 1)) * a.L + l) * a.N;
+}
+__device__ __forceinline__ size_t x_gstride(const ConvGeo &a) {
+    return (size_t)(a.masked ? 1u : 2u) * a.L * a.N;
+}
+__device__ __forceinline__ uint32_t *out_poly(const ConvGeo &a, uint32_t c, uint32_t h, uint32_t l) {
+    if (a.masked) return a.out + ((size_t)(c * a.H + h) * a.L + l) * a.N;
+    return a.out + ((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * a.L + l) * a.N;
+}
+// Delta_Q sh'_h[k] mod q in the masked form (Alg. 1: c0^r + sh'), else 0
+__device__ __forceinline__ uint32_t share_term(const ConvGeo &a, const LimbK &K, uint32_t c, uint32_t h, uint32_t k) {
+    if (!a.masked) return 0u;
+    return mulmod(__ldg(a.shp + ((size_t)c * a.H + h) * a.N + k), K.delta, K);
+}
+
 // Zero the residue classes of output polynomial h that no channel uses
-// (c_o < s, or a last polynomial with fewer than s channels).
-__device__ __forceinline__ void zero_unused_classes(const ConvGeo &a, uint32_t h, uint32_t l, uint32_t col0,
-                                                    uint32_t ncol) {
+// (c_o < s, or a last polynomial with fewer than s channels); in the
+// masked form they hold Delta_Q sh'.
+__device__ __forceinline__ void zero_unused_classes(const ConvGeo &a, const LimbK &K, uint32_t h, uint32_t l,
+                                                    uint32_t col0, uint32_t ncol) {
     const uint32_t cnt = min(a.s, a.co - h * a.s);
     if (a.mult == 1 && cnt == a.s) return;
-    const uint32_t N = a.N, L = a.L;
+    const uint32_t N = a.N;
     for (uint32_t idx = threadIdx.x; idx < ncol * N; idx += blockDim.x) {
         const uint32_t jj = idx / N, k = idx % N, c = col0 + jj;
         const uint32_t r = k & (a.s - 1);
         const bool used = (r % a.mult == 0) && (r / a.mult < cnt);
-        if (!used) a.out[((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N + k] = 0;
+        if (!used) out_poly(a, c, h, l)[k] = share_term(a, K, c, h, k);
     }
 }
 
@@ -175,7 +197,7 @@ template <int NJ, int NB, int CPT>
 __device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K, uint32_t n, uint32_t l,
                                                uint32_t col0, uint4 *smem4) {
     uint32_t *Z = reinterpret_cast<uint32_t *>(smem4);  // NJ padded polynomials of M words
-    const uint32_t N = a.N, L = a.L, G = a.G, s = a.s, M = a.M;
+    const uint32_t N = a.N, G = a.G, s = a.s, M = a.M;
     const uint32_t PS = padded_words(M);
     const uint32_t lt = a.logTS, TS = 1u << lt;
     // channel n's weights for tile t: G rows of TS words at W(t)
@@ -190,13 +212,10 @@ __device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K,
         if (a.tc) return a.bank + bank_index_tc(n, l, g, k, a.logs, M, G, a.co);
         return Wb + (k >> lt) * tstride + (size_t)g * TS + bank_row_pos(k & (TS - 1), lt, a.lcs);
     };
-    const size_t gstride = (size_t)2 * L * N;
+    const size_t gstride = x_gstride(a);
     const uint32_t *X[NJ];
 #pragma unroll
-    for (int jj = 0; jj < NJ; ++jj) {
-        const uint32_t c = col0 + jj;
-        X[jj] = a.x + ((size_t)((c >> 1) * G * 2 + (c & 1)) * L + l) * N;
-    }
+    for (int jj = 0; jj < NJ; ++jj) X[jj] = x_col(a, col0 + jj, l);
     constexpr uint32_t kU = NB == 1 ? 4 : (NB == 2 ? 8 : 16);  // groups per reduction (16 products)
     // groups per load batch: 6 128-bit loads in flight per thread for NJ = 2
     constexpr uint32_t kGL = (NJ == 2 && CPT == 1) ? 2u : 1u;
@@ -284,11 +303,11 @@ __device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K,
     intt_c(Z, NJ, PS, a.logM, a.tw_inv + (size_t)l * N, K.q);
     const uint32_t h = n >> a.logs, off = (n & (s - 1)) * a.mult;
     for (uint32_t idx = threadIdx.x; idx < NJ * M; idx += blockDim.x) {
-        const uint32_t jj = idx >> a.logM, e = idx & (M - 1), c = col0 + jj;
-        uint32_t *o = a.out + ((size_t)(((c >> 1) * a.H + h) * 2 + (c & 1)) * L + l) * N;
-        o[(e << a.logs) + off] = red_2q(Z[jj * PS + pidx(e)], K.q);
+        const uint32_t jj = idx >> a.logM, e = idx & (M - 1), c = col0 + jj, k = (e << a.logs) + off;
+        const uint32_t v = red_2q(Z[jj * PS + pidx(e)], K.q);
+        out_poly(a, c, h, l)[k] = a.masked ? red_2q(v + share_term(a, K, c, h, k), K.q) : v;
     }
-    if ((n & (s - 1)) == 0) zero_unused_classes(a, h, l, col0, NJ);
+    if ((n & (s - 1)) == 0) zero_unused_classes(a, K, h, l, col0, NJ);
 }
 
 // Plain form: full products, length-N INTT, one column.  The bank holds
@@ -333,7 +352,7 @@ __device__ __forceinline__ void conv_full_body(const ConvGeo &a, const LimbK &K,
             const uint32_t k = (e << a.logs) + off;
             o[k] = red_2q(Y[pidx(k)], K.q);
         }
-        if ((n & (s - 1)) == 0) zero_unused_classes(a, h, l, c, 1);
+        if ((n & (s - 1)) == 0) zero_unused_classes(a, K, h, l, c, 1);
     }
 }
 
@@ -435,12 +454,35 @@ __global__ void __launch_bounds__(kThreads, 3) k_ntt(const RingView r, const uin
              (inverse ? r.tw_inv : r.tw_fwd) + (size_t)l * N, K, inverse != 0, smem4);
 }
 
+// Inputs of the masked server step into the workspace [B][2G][L][N]:
+// groups g < G are the NTT of c0_g (or a copy when c0 is already in the NTT
+// domain), groups G + g the NTT of the share sh_g, the same integers (below
+// t) in every limb.
+__global__ void __launch_bounds__(kThreads, 3) k_ntt_masked_in(const RingView r, const uint32_t *__restrict__ c0,
+                                                           const uint32_t *__restrict__ sh, uint32_t *__restrict__ ws,
+                                                           uint32_t G, int c0_ntt) {
+    extern __shared__ uint4 smem4[];
+    const uint32_t P = blockIdx.x, N = r.N, L = r.L;
+    const uint32_t l = P % L, gz = (P / L) % (2u * G), b = P / (L * 2u * G);
+    uint32_t *dst = ws + (size_t)P * N;
+    if (gz < G && c0_ntt) {
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(c0 + ((size_t)(b * G + gz) * L + l) * N);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) d4[i] = __ldg(s4 + i);
+        return;
+    }
+    const uint32_t *src = gz < G ? c0 + ((size_t)(b * G + gz) * L + l) * N : sh + (size_t)(b * G + gz - G) * N;
+    ntt_body(src, dst, r.logN, r.tw_fwd + (size_t)l * N, r.limb[l], false, smem4);
+}
+
 struct PackConvArgs {
     RingView r;
     const int8_t *w;   // [co][ci][fh][fw]
     uint32_t *bank;    // tile-major, see bank_index
     uint32_t ci, co, fh, fw, hp, s, G, mult, lt, lcs;
     uint32_t tc, logs, M;  // tc: tensor-core layout (bank_index_tc)
+    uint32_t masked, Gm;   // masked bank: groups g < Gm hold rho (from `rho`), g >= Gm hold -Delta_Q fhat_{g - Gm}
+    const uint32_t *rho;   // masked: [co][Gm][N] integers in [0, t)
 };
 
 // Slot k of the NTT domain is the value at X_k = psi^(2 brv(k) + 1).  The
@@ -455,19 +497,31 @@ __global__ void __launch_bounds__(kThreads) k_pack_conv(const PackConvArgs a) {
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = 0;
     __syncthreads();
     const uint32_t off = (n % s) * a.mult;
-    const uint32_t sg = min(s, a.ci - g * s);
-    const uint32_t taps = a.fh * a.fw;
-    for (uint32_t idx = threadIdx.x; idx < sg * taps; idx += blockDim.x) {
-        const uint32_t mp = idx / taps, rem = idx % taps;
-        const uint32_t kp = rem / a.fw, lp = rem % a.fw;
-        const uint32_t m = g * s + mp;
-        int v = a.w[((size_t)(n * a.ci + m) * a.fh + kp) * a.fw + lp];
-        int e = (int)off - (int)mp - (int)(s * (kp * a.hp + lp));
-        if (e < 0) {
-            e += (int)N;
-            v = -v;
+    if (a.masked && g < a.Gm) {
+        // the mask rho_{g,n} (below t < q: already a residue)
+        const uint32_t *rs = a.rho + ((size_t)n * a.Gm + g) * N;
+        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = __ldg(rs + i);
+    } else {
+        const uint32_t gf = a.masked ? g - a.Gm : g;
+        const uint32_t sg = min(s, a.ci - gf * s);
+        const uint32_t taps = a.fh * a.fw;
+        for (uint32_t idx = threadIdx.x; idx < sg * taps; idx += blockDim.x) {
+            const uint32_t mp = idx / taps, rem = idx % taps;
+            const uint32_t kp = rem / a.fw, lp = rem % a.fw;
+            const uint32_t m = gf * s + mp;
+            int v = a.w[((size_t)(n * a.ci + m) * a.fh + kp) * a.fw + lp];
+            int e = (int)off - (int)mp - (int)(s * (kp * a.hp + lp));
+            if (e < 0) {
+                e += (int)N;
+                v = -v;
+            }
+            A[e] = v >= 0 ? (uint32_t)v : K.q - (uint32_t)(-v);
         }
-        A[e] = v >= 0 ? (uint32_t)v : K.q - (uint32_t)(-v);
+        if (a.masked) {  // -Delta_Q fhat
+            __syncthreads();
+            const uint32_t md = K.delta ? K.q - K.delta : 0u;
+            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = mulmod(A[i], md, K);
+        }
     }
     __syncthreads();
     ntt_fwd_smem(A, logN, a.r.tw_fwd + (size_t)l * N, K.q);
@@ -1045,6 +1099,9 @@ cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_c
     a.tc = tc;
     a.logs = he_ilog2(lay.s);
     a.M = lay.M;
+    a.masked = 0;
+    a.Gm = 0;
+    a.rho = nullptr;
     a.r = r;
     a.w = d_w;
     a.bank = bank;
@@ -1060,6 +1117,45 @@ cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_c
     cudaError_t e = set_smem(k_pack_conv, smem);
     if (e != cudaSuccess) return e;
     k_pack_conv<<<dim3(d.co, r.L, lay.G), kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t he_launch_pack_conv_masked(const RingView &r, const int8_t *d_w, const uint32_t *d_rho,
+                                       const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt, uint32_t lcs,
+                                       uint32_t *bank, cudaStream_t st) {
+    PackConvArgs a;
+    a.lt = lt;
+    a.lcs = lcs;
+    a.tc = 0;
+    a.logs = he_ilog2(lay.s);
+    a.M = lay.M;
+    a.masked = 1;
+    a.Gm = lay.G;
+    a.rho = d_rho;
+    a.r = r;
+    a.w = d_w;
+    a.bank = bank;
+    a.ci = d.ci;
+    a.co = d.co;
+    a.fh = d.fh;
+    a.fw = d.fw;
+    a.hp = lay.hp;
+    a.s = lay.s;
+    a.G = 2u * lay.G;
+    a.mult = lay.off_mult;
+    const size_t smem = (size_t)r.N * 4u;
+    cudaError_t e = set_smem(k_pack_conv, smem);
+    if (e != cudaSuccess) return e;
+    k_pack_conv<<<dim3(d.co, r.L, 2u * lay.G), kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t he_launch_ntt_masked_in(const RingView &r, const uint32_t *c0, const uint32_t *sh, uint32_t *ws,
+                                    uint32_t B, uint32_t G, bool c0_ntt, cudaStream_t st) {
+    const size_t smem = (size_t)padded_words(r.N) * 4u;
+    cudaError_t e = set_smem(k_ntt_masked_in, smem);
+    if (e != cudaSuccess) return e;
+    k_ntt_masked_in<<<B * 2u * G * r.L, kThreads, smem, st>>>(r, c0, sh, ws, G, c0_ntt ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1128,6 +1224,43 @@ cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_co
     if (e != cudaSuccess) return e;
     k_conv_full<<<dim3(d.co, r.L, a.ncols), kThreads, smem, st>>>(a, r);
     return cudaGetLastError();
+}
+
+// The masked server step: one column per ciphertext over the 2G groups of
+// the masked bank, the folded form (valid slots only) with Delta_Q sh' added.
+cudaError_t he_launch_conv_masked(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt,
+                                  uint32_t lcs, const uint32_t *bank, const uint32_t *x_ntt, const uint32_t *shp,
+                                  uint32_t *out, uint32_t B, cudaStream_t st) {
+    ConvGeo a = geo_of(r);
+    a.bank = bank;
+    a.x = x_ntt;
+    a.out = out;
+    a.shp = shp;
+    a.masked = 1;
+    a.G = 2u * lay.G;
+    a.H = lay.H;
+    a.s = lay.s;
+    a.logs = he_ilog2(lay.s);
+    a.M = lay.M;
+    a.logM = he_ilog2(lay.M);
+    a.co = d.co;
+    a.mult = lay.off_mult;
+    a.ncols = B;
+    a.logTS = lt;
+    a.lcs = lcs;
+    a.tc = 0;
+    a.mode = HE_OUT_EXTRACTED;
+    // columns per CTA: the largest power of two <= 16 dividing B whose
+    // block vectors fit (1 for odd B)
+    uint32_t nj = lay.s >= 4 ? 16u : (lay.s == 2 ? 8u : 4u);
+    while (nj > 1 && ((B % nj) != 0 || fold_smem_bytes(nj, lay.M) > 160u * 1024u)) nj >>= 1;
+    switch (nj) {
+        case 16: return launch_fold_nb<16>(a, r, st);
+        case 8: return launch_fold_nb<8>(a, r, st);
+        case 4: return launch_fold_nb<4>(a, r, st);
+        case 2: return launch_fold_nb<2>(a, r, st);
+        default: return launch_fold_nb<1>(a, r, st);
+    }
 }
 
 cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32_t *bank, const uint32_t *bias,

@@ -46,6 +46,7 @@ extern "C" he_status he_conv_layer_noalloc(he_params_t p, he_filters_t f, const 
     if (p->device == HE_DEVICE_NONE) return he_fail(HE_ERR_ARG, "params were created without a device");
     if (p->device < 0 || p->device >= 64) return he_fail(HE_ERR_ARG, "device ordinal out of range");
     if (f->kind != HE_KIND_CONV || f->p != p) return he_fail(HE_ERR_ARG, "filters are not a Conv bank of these params");
+    if (f->masked) return he_fail(HE_ERR_ARG, "a masked bank is evaluated by he_conv_layer_masked");
     if (in_domain != HE_COEFF && in_domain != HE_NTT) return he_fail(HE_ERR_ARG, "bad in_domain");
     if (out_mode != HE_OUT_EXTRACTED && out_mode != HE_OUT_PER_CHANNEL && out_mode != HE_OUT_EXTRACTED_UNFOLDED)
         return he_fail(HE_ERR_ARG, "bad out_mode");

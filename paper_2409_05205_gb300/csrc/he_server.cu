@@ -116,28 +116,33 @@ uint32_t bucket_of(uint32_t n, uint32_t max_batch) {
     return b;
 }
 
+// Frees one idle lane (another shape's buffers and plan); false if none is idle.
+bool free_idle_lane(Server *s) {
+    for (size_t i = 0; i < s->lanes.size(); ++i) {
+        Lane *l = s->lanes[i];
+        if (l->busy) continue;
+        he_plan_destroy(l->plan);
+        cudaFree(l->d_in);
+        cudaFree(l->d_out);
+        s->bytes_in_use -= l->bytes;
+        delete l;
+        s->lanes.erase(s->lanes.begin() + (long)i);
+        return true;
+    }
+    return false;
+}
+
 // a free lane for (model, layer, bucket), allocating one if the budget
-// allows; nullptr when none can be had now.  Called with s->mu held.
+// allows -- idle lanes of other shapes are freed until the new lane's
+// buffers and its plan's workspace fit; nullptr when none can be had now.
+// Called with s->mu held.
 Lane *get_lane(Server *s, uint32_t model, uint32_t layer, uint32_t bucket) {
     for (Lane *l : s->lanes)
         if (!l->busy && l->model == model && l->layer == layer && l->bucket == bucket) return l;
     const ModelLayer &ml = s->models[model].layers[layer];
     const size_t io = (ml.in_words + ml.out_words) * bucket * sizeof(uint32_t);
-    if (s->bytes_in_use + io > s->cfg.hbm_budget_bytes) {
-        // free an idle lane of another shape to make room
-        for (size_t i = 0; i < s->lanes.size(); ++i) {
-            Lane *l = s->lanes[i];
-            if (l->busy) continue;
-            he_plan_destroy(l->plan);
-            cudaFree(l->d_in);
-            cudaFree(l->d_out);
-            s->bytes_in_use -= l->bytes;
-            delete l;
-            s->lanes.erase(s->lanes.begin() + (long)i);
-            break;
-        }
-        if (s->bytes_in_use + io > s->cfg.hbm_budget_bytes) return nullptr;
-    }
+    while (s->bytes_in_use + io > s->cfg.hbm_budget_bytes)
+        if (!free_idle_lane(s)) return nullptr;
     Lane *l = new (std::nothrow) Lane();
     if (!l) return nullptr;
     l->model = model;
@@ -161,7 +166,9 @@ Lane *get_lane(Server *s, uint32_t model, uint32_t layer, uint32_t bucket) {
     he_plan_info info{};
     he_plan_query(l->plan, &info, nullptr);
     l->bytes = io + info.workspace_bytes;
-    if (s->bytes_in_use + l->bytes > s->cfg.hbm_budget_bytes) {  // the workspace did not fit after all
+    bool fits = true;
+    while (fits && s->bytes_in_use + l->bytes > s->cfg.hbm_budget_bytes) fits = free_idle_lane(s);
+    if (!fits) {  // the workspace does not fit while other lanes are busy
         he_plan_destroy(l->plan);
         cudaFree(l->d_in);
         cudaFree(l->d_out);

@@ -92,6 +92,8 @@ _SIGS = {
     "he_pack_filters": [_vp, ctypes.POINTER(he_conv_desc), _vp, ctypes.POINTER(_vp)],
     "he_pack_filters_for_batch": [_vp, ctypes.POINTER(he_conv_desc), _vp, _u32, ctypes.POINTER(_vp)],
     "he_filters_tensor_core": [_vp, ctypes.POINTER(_u32)],
+    "he_pack_masked": [_vp, ctypes.POINTER(he_conv_desc), _vp, _vp, ctypes.POINTER(_vp)],
+    "he_conv_layer_masked": [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _u32, _vp],
     "he_pack_fc": [_vp, _u32, _u32, _vp, _vp, ctypes.POINTER(_vp)],
     "he_filters_destroy": [_vp],
     "he_conv_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
@@ -249,6 +251,21 @@ def he_pack_filters_for_batch(p: int, desc, w: np.ndarray, B: int) -> int:
     out = _vp()
     _check(lib().he_pack_filters_for_batch(p, ctypes.byref(d), w.ctypes.data, B, ctypes.byref(out)))
     return out.value
+
+
+def he_pack_masked(p: int, desc, w: np.ndarray, rho: np.ndarray) -> int:
+    d = _desc(desc)
+    w = np.ascontiguousarray(w, dtype=np.int8)
+    assert w.size == d.co * d.ci * d.fh * d.fw
+    rho = np.ascontiguousarray(rho, dtype=np.uint32)
+    out = _vp()
+    _check(lib().he_pack_masked(p, ctypes.byref(d), w.ctypes.data, rho.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
+def he_conv_layer_masked(p: int, f: int, d_c0, d_sh, d_shp, in_domain: int, d_out, B: int, stream=None) -> None:
+    _check(lib().he_conv_layer_masked(p, f, _ptr(d_c0), _ptr(d_sh), _ptr(d_shp), in_domain, _ptr(d_out), B,
+                                      _stream(stream)))
 
 
 def he_filters_tensor_core(f: int) -> int:
