@@ -110,6 +110,30 @@ def plain20_conv_layers(width: int = 1) -> list[dict]:
     return L
 
 
+def f5_d8_w3_conv_layers() -> list[dict]:
+    """The f5-d8-w3 variant's Conv layers, shapes only: 5x5 filters with same
+    padding, widths 48 / 96 / 192 (three times plain-20's), 7 Conv layers
+    (the eighth layer is the FC): 3->48 and 48->48 at 32x32, 48->96 (stride
+    2, on 32x32), 96->96 at 16x16, 96->192 (stride 2, on 16x16), 2x
+    192->192 at 8x8."""
+    L = [dict(ci=3, co=48, h=32, w=32, stride=1), dict(ci=48, co=48, h=32, w=32, stride=1),
+         dict(ci=48, co=96, h=32, w=32, stride=2), dict(ci=96, co=96, h=16, w=16, stride=1),
+         dict(ci=96, co=192, h=16, w=16, stride=2), dict(ci=192, co=192, h=8, w=8, stride=1),
+         dict(ci=192, co=192, h=8, w=8, stride=1)]
+    for d in L:
+        d.update(fh=5, fw=5, pad=2)
+    return L
+
+
+def resnet_bottleneck_conv_layers() -> list[dict]:
+    """Shapes of ResNet-50 bottleneck blocks at 14x14 (its third stage),
+    shapes only: 1x1 1024->256 (c_o < c_i), 3x3 256->256, 1x1 256->1024, twice."""
+    blk = [dict(ci=1024, co=256, h=14, w=14, stride=1, fh=1, fw=1, pad=0),
+           dict(ci=256, co=256, h=14, w=14, stride=1, fh=3, fw=3, pad=1),
+           dict(ci=256, co=1024, h=14, w=14, stride=1, fh=1, fw=1, pad=0)]
+    return [dict(d) for d in blk + blk]
+
+
 # distinct Conv shapes of plain-20 (width 1) and the CIFAR-100 FC layer
 PLAIN20_DISTINCT = [dict(ci=3, co=16, h=32, w=32), dict(ci=16, co=16, h=32, w=32), dict(ci=16, co=32, h=32, w=32),
                     dict(ci=32, co=32, h=16, w=16), dict(ci=32, co=64, h=16, w=16), dict(ci=64, co=64, h=8, w=8)]
@@ -153,6 +177,10 @@ WORKLOADS = {
     "plain20_c100_wide4": dict(N=16384, L=6, t=65537, B=8, conv=plain20_conv_layers(4),
                                fc=dict(n_in=256, n_out=100), wlo=-128, whi=127),
     "batched64": dict(t=65537, calls=batched_calls(3, 64), wlo=-128, whi=127),
+    "f5_d8_w3": dict(N=8192, L=3, t=65537, B=1, conv=f5_d8_w3_conv_layers(), fc=dict(n_in=192, n_out=10),
+                     wlo=-128, whi=127),
+    "resnet50_bottleneck": dict(N=8192, L=3, t=65537, B=1, conv=resnet_bottleneck_conv_layers(), fc=None,
+                                wlo=-128, whi=127),
     # one layer of the wide x4 network (64 -> 64 channels at 32x32, N = 16384,
     # 6 limbs, B = 8): a small case of its MAC kernel for profiling
     "wide4_64x64": dict(N=16384, L=6, t=65537, B=8, conv=[dict(ci=64, co=64, h=32, w=32, stride=1, fh=3, fw=3, pad=1)],

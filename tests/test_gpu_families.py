@@ -1,0 +1,74 @@
+"""Other layer families (5x5 filters of the f5 variant, ResNet-style 1x1
+layers with c_o < c_i and c_o > c_i, and their 3x3 layers at 14x14) at full
+size, N = 8192 and 3 limbs: a plan, single calls and the oracle give the
+same words (every word of one limb by the oracle's NTT tier, sampled words
+of every limb by its schoolbook dot products)."""
+
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2409_05205_gb300 import synth
+import _gpu_helpers as U
+
+pytestmark = pytest.mark.gpu
+
+# (ci, co, hw, f, pad)
+SHAPES = [(48, 48, 32, 5, 2), (96, 192, 16, 5, 2), (192, 192, 8, 5, 2), (3, 48, 32, 5, 2),
+          (1024, 256, 14, 1, 0), (256, 1024, 14, 1, 0), (256, 256, 14, 3, 1)]
+
+
+@pytest.mark.parametrize("ci,co,hw,f,pad", SHAPES)
+def test_layer_family_full_size(ci, co, hw, f, pad):
+    H = U.he()
+    torch = U.torch_cuda()
+    N, L, B = 8192, 3, 1
+    ps, psis, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, B, seed=ci + co + f, fh=f, fw=f, pad=pad)
+    with U.params(N, L) as p, U.conv_bank(p, desc, F) as fb:
+        single = U.run_conv(p, fb, cts, H.HE_OUT_EXTRACTED, lay["H"])
+        d_in, d_out = U.to_dev(cts), U.empty_dev(single.shape)
+        plan = H.he_plan_create([(fb, d_in, H.HE_COEFF, d_out, B)])
+        try:
+            H.he_plan_run(plan, torch.cuda.current_stream())
+            H.he_sync(torch.cuda.current_stream())
+            H.he_plan_check(plan)
+        finally:
+            H.he_plan_destroy(plan)
+        got = U.from_dev(d_out).reshape(single.shape)
+    np.testing.assert_array_equal(got, single)
+    l = (ci + co) % L
+    ref = O.conv_layer(np.ascontiguousarray(cts[:, :, :, l:l + 1]), F, [ps[l]], [psis[l]], lay, O.OUT_EXTRACTED,
+                       tier="ntt")
+    np.testing.assert_array_equal(got[:, :, :, l:l + 1], ref)
+    rng = np.random.default_rng(co)
+    picks = [(0, int(rng.integers(lay["H"])), int(rng.integers(2)), int(rng.integers(L)), int(rng.integers(N)))
+             for _ in range(16)]
+    np.testing.assert_array_equal(O.conv_layer_sampled(cts, F, ps, lay, picks),
+                                  np.array([got[pk] for pk in picks], dtype=np.uint32))
+
+
+def test_f5_workload_decrypts_to_the_convolution():
+    """One 5x5 layer through real RLWE: secret-key encryption of a packed
+    image, the GPU layer in per-channel mode, decryption equals the direct
+    convolution mod t at every output position (N = 4096, 3 limbs)."""
+    H = U.he()
+    N, L, ci, co, hw = 4096, 3, 6, 4, 8
+    ps, psis = U.ring(N, L)
+    lay = O.conv_layout(N, ci, co, hw, hw, 5, 5, 2)
+    I = synth.ints(91, "f5/I", (ci, hw, hw), -8, 7)
+    F = synth.conv_weights(91, "f5/F", co, ci, 5, 5, -128, 127)
+    s = synth.ternary(91, "f5/s", N)
+    ip = O.pack_input(I, lay)
+    cts = np.zeros((1, lay["G"], 2, L, N), np.uint32)
+    for g in range(lay["G"]):
+        a = synth.residues(91, f"f5/a{g}", (L, N), ps)
+        cts[0, g] = O.encrypt_sk(ip[g], s, a, synth.cbd(91, f"f5/e{g}", N), ps, U.T)
+    with U.params(N, L) as p, U.conv_bank(p, dict(ci=ci, co=co, h=hw, w=hw, fh=5, fw=5, pad=2), F) as fb:
+        y = U.run_conv(p, fb, cts, H.HE_OUT_PER_CHANNEL, co)
+    ref = O.centered(O.direct_conv(I, F, 2), U.T)
+    for n in range(co):
+        m = O.decrypt(y[0, n], s, ps, U.T)
+        got = np.array([[m[O.output_slot(lay, n, k, l)[1]] for l in range(lay["w_out"])] for k in range(lay["h_out"])])
+        np.testing.assert_array_equal(got, ref[n])

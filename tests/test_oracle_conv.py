@@ -63,6 +63,11 @@ def _check_packing(N, ci, co, h, w, fh, fw, pad, seed, pack_filters=O.pack_filte
     (512, 16, 6, 4, 4, 3, 3, 1),   # G > 1 groups, c_o not a multiple of s
     (1024, 5, 7, 6, 5, 3, 3, 1),   # non-square input, odd channel counts
     (128, 2, 3, 8, 8, 3, 3, 1),    # s*P close to N
+    (1024, 6, 4, 6, 6, 5, 5, 2),   # 5x5 filters, same padding 2 (the f5 family)
+    (2048, 12, 8, 5, 5, 5, 5, 2),  # 5x5, G > 1
+    (512, 32, 8, 4, 4, 1, 1, 0),   # 1x1, c_o < c_i (a ResNet bottleneck's reduction)
+    (1024, 8, 24, 4, 4, 1, 1, 0),  # 1x1, c_o > c_i (its expansion), several output polynomials
+    (4096, 3, 8, 7, 7, 7, 7, 3),   # 7x7 filters, padding 3 (a ResNet stem shape, small)
 ])
 def test_packing_and_extraction_slots_hold_the_convolution(N, ci, co, h, w, fh, fw, pad):
     _check_packing(N, ci, co, h, w, fh, fw, pad, seed=N + ci + co)
