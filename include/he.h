@@ -256,6 +256,28 @@ he_status he_conv_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_
                                const uint32_t *d_sh, const uint32_t *d_shp, int in_domain,
                                uint32_t *d_out, uint32_t B, void *stream);
 
+/* The client's step of Alg. 1 (the loop after the server's reply), on the
+ * same kernels as the server's: the client loads the server's p1_{g,n} =
+ * rho_{g,n} b + e1 and p2_{g,n} = Delta_Q (fhat_{g,n} + rho_{g,n}) + e2 once.
+ *   p1, p2: HOST uint32 [co][G][L][N], residues of each limb (words at or
+ *           above q_l fail with HE_ERR_ARG).
+ * The bank holds NTT(p1) and NTT(p2) (co * 2G * L * N * 4 bytes).  Blocking. */
+he_status he_pack_client(he_params_t p, const he_conv_desc *d, const uint32_t *p1, const uint32_t *p2,
+                         he_filters_t *out);
+
+/* Client evaluation for B ciphertexts:
+ *   c1^(n) = sum_g -v_g * p1_{g,n} + (i + sh)_g * p2_{g,n},  c1^r = extract(c1^(n)),
+ * with the sign on v that cancels the server's mask term.
+ *   d_v:   DEVICE int32 [B][G][N], the randomness v of the client's encryption
+ *          of -(i + sh), one ternary polynomial per input group.
+ *   d_ish: DEVICE int32 [B][G][N], the packed layer input plus the share
+ *          (|value| < q_l).
+ *   d_out: DEVICE uint32 [B][H][L][N], c1^r; every word written.
+ * The plaintext of the layer is then round(t (c0^r + c1^r) / Q) mod t minus
+ * sh'.  f must come from he_pack_client.  Asynchronous on `stream`. */
+he_status he_conv_client(he_params_t p, he_filters_t f, const int32_t *d_v, const int32_t *d_ish,
+                         uint32_t *d_out, uint32_t B, void *stream);
+
 /* Server evaluation of one FC layer for B ciphertexts (Alg. 2 in
  * ciphertext x plaintext form, Theorem 1):
  *   y_j^(c) = c^(c) * w_j, plus Delta_Q * d_j(X) on c0 (c = 0).

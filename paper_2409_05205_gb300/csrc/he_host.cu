@@ -492,7 +492,7 @@ he_status he_pack_masked(he_params_t p, const he_conv_desc *d, const int8_t *w, 
     if (e == cudaSuccess) e = cudaMemcpy(d_w, w, wbytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(d_rho, rho, nrho * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = he_launch_pack_conv_masked(p->ring, d_w, d_rho, *d, lay, f->logTS, f->lcs, f->bank, 0);
+        e = he_launch_pack_conv_masked(p->ring, d_w, d_rho, nullptr, *d, lay, f->logTS, f->lcs, f->bank, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_w);
     cudaFree(d_rho);
@@ -502,6 +502,81 @@ he_status he_pack_masked(he_params_t p, const he_conv_desc *d, const int8_t *w, 
     }
     *out = f;
     return HE_OK;
+}
+
+he_status he_pack_client(he_params_t p, const he_conv_desc *d, const uint32_t *p1, const uint32_t *p2,
+                         he_filters_t *out) {
+    if (!p || !d || !p1 || !p2 || !out) return fail(HE_ERR_ARG, "NULL argument");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    *out = nullptr;
+    he_conv_layout lay{};
+    he_status st = conv_layout(p, d, &lay);
+    if (st != HE_OK) return st;
+    if (lay.s > HE_MAX_INTERLEAVE)
+        return fail(HE_ERR_UNSUPPORTED, "interleave s = %u above %d", lay.s, HE_MAX_INTERLEAVE);
+    if (fold_smem_bytes(1, lay.M) > 192u * 1024u)
+        return fail(HE_ERR_UNSUPPORTED, "N/s = %u too long for the client step", lay.M);
+    const size_t np = (size_t)d->co * lay.G * p->L * p->N;
+    for (size_t i = 0; i < np; ++i) {
+        const uint32_t q = p->q[(i / p->N) % p->L];
+        if (p1[i] >= q || p2[i] >= q) return fail(HE_ERR_ARG, "p1 / p2 word %zu is not a residue of its limb", i);
+    }
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    he_filters_s *f = new (std::nothrow) he_filters_s();
+    if (!f) return fail(HE_ERR_NOMEM, "filters");
+    f->p = p;
+    f->kind = HE_KIND_CONV;
+    f->desc = *d;
+    f->lay = lay;
+    f->masked = 2;
+    f->logTS = bank_tile_log(p->logN, lay.s, 2u * lay.G);
+    f->lcs = bank_chunk_log(f->logTS, lay.s, 2u * lay.G);
+    f->bank_bytes = (size_t)d->co * p->L * 2u * lay.G * p->N * sizeof(uint32_t);
+    uint32_t *d_p1 = nullptr, *d_p2 = nullptr;
+    cudaError_t e = cudaMalloc(&f->bank, f->bank_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const size_t nb = f->bank_bytes;
+        delete f;
+        return fail(HE_ERR_NOMEM, "client bank of %zu bytes", nb);
+    }
+    e = cudaMalloc(&d_p1, np * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&d_p2, np * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(d_p1, p1, np * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d_p2, p2, np * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = he_launch_pack_conv_masked(p->ring, nullptr, d_p1, d_p2, *d, lay, f->logTS, f->lcs, f->bank, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_p1);
+    cudaFree(d_p2);
+    if (e != cudaSuccess) {
+        he_filters_destroy(f);
+        return cuda_fail(e, "pack client bank");
+    }
+    *out = f;
+    return HE_OK;
+}
+
+he_status he_conv_client(he_params_t p, he_filters_t f, const int32_t *d_v, const int32_t *d_ish, uint32_t *d_out,
+                         uint32_t B, void *stream) {
+    if (!p || !f || !d_v || !d_ish || !d_out) return fail(HE_ERR_ARG, "NULL argument");
+    if (f->kind != HE_KIND_CONV || f->masked != 2) return fail(HE_ERR_ARG, "filters are not a client bank");
+    if (f->p != p) return fail(HE_ERR_ARG, "filters belong to other params");
+    if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
+    if (!aligned16(d_out)) return fail(HE_ERR_ARG, "d_out must be 16-byte aligned");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    const he_conv_layout &lay = f->lay;
+    const size_t ws_words = (size_t)B * 2u * lay.G * p->L * p->N;
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    if (ensure_ws(p, ws_words * 4u) != HE_OK) return HE_ERR_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *ws = static_cast<uint32_t *>(p->ws);
+    cudaError_t e = he_launch_client_in(p->ring, d_v, d_ish, ws, B, lay.G, st);
+    if (e == cudaSuccess)
+        e = he_launch_conv_masked(p->ring, f->desc, lay, f->logTS, f->lcs, f->bank, ws, nullptr, d_out, B, st);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "client conv step");
 }
 
 he_status he_filters_tensor_core(he_filters_t f, uint32_t *tc) {
@@ -602,7 +677,7 @@ he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int
 he_status he_conv_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0, const uint32_t *d_sh,
                                const uint32_t *d_shp, int in_domain, uint32_t *d_out, uint32_t B, void *stream) {
     if (!p || !f || !d_c0 || !d_sh || !d_shp || !d_out) return fail(HE_ERR_ARG, "NULL argument");
-    if (f->kind != HE_KIND_CONV || !f->masked) return fail(HE_ERR_ARG, "filters are not a masked Conv bank");
+    if (f->kind != HE_KIND_CONV || f->masked != 1) return fail(HE_ERR_ARG, "filters are not a masked (server) Conv bank");
     if (f->p != p) return fail(HE_ERR_ARG, "filters belong to other params");
     if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
     if (in_domain != HE_COEFF && in_domain != HE_NTT) return fail(HE_ERR_ARG, "bad in_domain");

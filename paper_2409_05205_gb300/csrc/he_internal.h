@@ -296,7 +296,8 @@ struct he_filters_s {
     uint32_t logTS;   // conv bank tile
     uint32_t lcs;     // conv bank chunk interleave (log2)
     uint32_t tc;      // conv bank in the tensor-core layout (bank_index_tc)
-    uint32_t masked;  // bank of the masked server step: 2G groups (rho_{g,n}, then -Delta_Q fhat_{g,n})
+    uint32_t masked;  // 1: bank of the masked server step, 2G groups (rho_{g,n}, then -Delta_Q fhat_{g,n});
+                      // 2: bank of the client step, 2G groups (p1_{g,n}, then p2_{g,n})
     uint32_t nc;      // split MAC: channels per work item
     he_fc_layout fl;
     uint32_t *bank;   // conv: [co][L][G][N]; fc: [P][L][N]; NTT domain, pre-scaled
@@ -323,8 +324,10 @@ cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_co
                            uint32_t lcs, uint32_t tc, const uint32_t *bank, const uint32_t *x_ntt, uint32_t *out,
                            int mode, uint32_t B, cudaStream_t st);
 cudaError_t he_launch_pack_conv_masked(const RingView &r, const int8_t *d_w, const uint32_t *d_rho,
-                                       const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt, uint32_t lcs,
-                                       uint32_t *bank, cudaStream_t st);
+                                       const uint32_t *d_p2, const he_conv_desc &d, const he_conv_layout &lay,
+                                       uint32_t lt, uint32_t lcs, uint32_t *bank, cudaStream_t st);
+cudaError_t he_launch_client_in(const RingView &r, const int32_t *v, const int32_t *ish, uint32_t *ws, uint32_t B,
+                                uint32_t G, cudaStream_t st);
 cudaError_t he_launch_ntt_masked_in(const RingView &r, const uint32_t *c0, const uint32_t *sh, uint32_t *ws,
                                     uint32_t B, uint32_t G, bool c0_ntt, cudaStream_t st);
 cudaError_t he_launch_conv_masked(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt,

@@ -128,7 +128,7 @@ __device__ __forceinline__ uint32_t *out_poly(const ConvGeo &a, uint32_t c, uint
 }
 // Delta_Q sh'_h[k] mod q in the masked form (Alg. 1: c0^r + sh'), else 0
 __device__ __forceinline__ uint32_t share_term(const ConvGeo &a, const LimbK &K, uint32_t c, uint32_t h, uint32_t k) {
-    if (!a.masked) return 0u;
+    if (!a.masked || !a.shp) return 0u;
     return mulmod(__ldg(a.shp + ((size_t)c * a.H + h) * a.N + k), K.delta, K);
 }
 
@@ -475,14 +475,36 @@ __global__ void __launch_bounds__(kThreads, 3) k_ntt_masked_in(const RingView r,
     ntt_body(src, dst, r.logN, r.tw_fwd + (size_t)l * N, r.limb[l], false, smem4);
 }
 
+// Inputs of the client step of Alg. 1 into the workspace [B][2G][L][N] as
+// residues: groups g < G hold -v_g, groups G + g hold (i + sh)_g; both are
+// small signed integers, the same in every limb.  The NTT follows in place.
+__global__ void __launch_bounds__(kThreads) k_client_in(const RingView r, const int32_t *__restrict__ v,
+                                                    const int32_t *__restrict__ ish, uint32_t *__restrict__ ws,
+                                                    uint32_t G) {
+    const uint32_t P = blockIdx.x, N = r.N, L = r.L;
+    const uint32_t l = P % L, gz = (P / L) % (2u * G), b = P / (L * 2u * G);
+    const uint32_t q = r.limb[l].q;
+    const int32_t *src = gz < G ? v + (size_t)(b * G + gz) * N : ish + (size_t)(b * G + gz - G) * N;
+    const bool neg = gz < G;
+    uint32_t *dst = ws + (size_t)P * N;
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+        int64_t x = __ldg(src + i);
+        if (neg) x = -x;
+        x %= (int64_t)q;
+        dst[i] = (uint32_t)(x < 0 ? x + q : x);
+    }
+}
+
 struct PackConvArgs {
     RingView r;
     const int8_t *w;   // [co][ci][fh][fw]
     uint32_t *bank;    // tile-major, see bank_index
     uint32_t ci, co, fh, fw, hp, s, G, mult, lt, lcs;
     uint32_t tc, logs, M;  // tc: tensor-core layout (bank_index_tc)
-    uint32_t masked, Gm;   // masked bank: groups g < Gm hold rho (from `rho`), g >= Gm hold -Delta_Q fhat_{g - Gm}
-    const uint32_t *rho;   // masked: [co][Gm][N] integers in [0, t)
+    uint32_t masked, Gm;   // 1: server bank, groups g < Gm hold rho (from `rho`), g >= Gm hold -Delta_Q fhat_{g - Gm};
+                           // 2: client bank, groups g < Gm hold p1 (from `rho`), g >= Gm hold p2 (from `p2`)
+    const uint32_t *rho;   // masked 1: [co][Gm][N] integers in [0, t); masked 2: p1 [co][Gm][L][N] residues
+    const uint32_t *p2;    // masked 2: [co][Gm][L][N] residues
 };
 
 // Slot k of the NTT domain is the value at X_k = psi^(2 brv(k) + 1).  The
@@ -497,7 +519,12 @@ __global__ void __launch_bounds__(kThreads) k_pack_conv(const PackConvArgs a) {
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = 0;
     __syncthreads();
     const uint32_t off = (n % s) * a.mult;
-    if (a.masked && g < a.Gm) {
+    if (a.masked == 2) {
+        // the server's p1_{g,n} / p2_{g,n}, residues of limb l
+        const uint32_t *src = (g < a.Gm ? a.rho + (((size_t)n * a.Gm + g) * a.r.L + l) * N
+                                        : a.p2 + (((size_t)n * a.Gm + (g - a.Gm)) * a.r.L + l) * N);
+        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = __ldg(src + i);
+    } else if (a.masked && g < a.Gm) {
         // the mask rho_{g,n} (below t < q: already a residue)
         const uint32_t *rs = a.rho + ((size_t)n * a.Gm + g) * N;
         for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = __ldg(rs + i);
@@ -1102,6 +1129,7 @@ cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_c
     a.masked = 0;
     a.Gm = 0;
     a.rho = nullptr;
+    a.p2 = nullptr;
     a.r = r;
     a.w = d_w;
     a.bank = bank;
@@ -1121,17 +1149,18 @@ cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_c
 }
 
 cudaError_t he_launch_pack_conv_masked(const RingView &r, const int8_t *d_w, const uint32_t *d_rho,
-                                       const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt, uint32_t lcs,
-                                       uint32_t *bank, cudaStream_t st) {
+                                       const uint32_t *d_p2, const he_conv_desc &d, const he_conv_layout &lay,
+                                       uint32_t lt, uint32_t lcs, uint32_t *bank, cudaStream_t st) {
     PackConvArgs a;
     a.lt = lt;
     a.lcs = lcs;
     a.tc = 0;
     a.logs = he_ilog2(lay.s);
     a.M = lay.M;
-    a.masked = 1;
+    a.masked = d_p2 ? 2u : 1u;
     a.Gm = lay.G;
     a.rho = d_rho;
+    a.p2 = d_p2;
     a.r = r;
     a.w = d_w;
     a.bank = bank;
@@ -1157,6 +1186,15 @@ cudaError_t he_launch_ntt_masked_in(const RingView &r, const uint32_t *c0, const
     if (e != cudaSuccess) return e;
     k_ntt_masked_in<<<B * 2u * G * r.L, kThreads, smem, st>>>(r, c0, sh, ws, G, c0_ntt ? 1 : 0);
     return cudaGetLastError();
+}
+
+cudaError_t he_launch_client_in(const RingView &r, const int32_t *v, const int32_t *ish, uint32_t *ws, uint32_t B,
+                                uint32_t G, cudaStream_t st) {
+    const uint32_t np = B * 2u * G * r.L;
+    k_client_in<<<np, kThreads, 0, st>>>(r, v, ish, ws, G);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return he_launch_ntt(r, ws, ws, np, false, st);
 }
 
 cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_layout &fl, uint32_t *bank,

@@ -94,6 +94,8 @@ _SIGS = {
     "he_filters_tensor_core": [_vp, ctypes.POINTER(_u32)],
     "he_pack_masked": [_vp, ctypes.POINTER(he_conv_desc), _vp, _vp, ctypes.POINTER(_vp)],
     "he_conv_layer_masked": [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _u32, _vp],
+    "he_pack_client": [_vp, ctypes.POINTER(he_conv_desc), _vp, _vp, ctypes.POINTER(_vp)],
+    "he_conv_client": [_vp, _vp, _vp, _vp, _vp, _u32, _vp],
     "he_pack_fc": [_vp, _u32, _u32, _vp, _vp, ctypes.POINTER(_vp)],
     "he_filters_destroy": [_vp],
     "he_conv_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
@@ -266,6 +268,19 @@ def he_pack_masked(p: int, desc, w: np.ndarray, rho: np.ndarray) -> int:
 def he_conv_layer_masked(p: int, f: int, d_c0, d_sh, d_shp, in_domain: int, d_out, B: int, stream=None) -> None:
     _check(lib().he_conv_layer_masked(p, f, _ptr(d_c0), _ptr(d_sh), _ptr(d_shp), in_domain, _ptr(d_out), B,
                                       _stream(stream)))
+
+
+def he_pack_client(p: int, desc, p1: np.ndarray, p2: np.ndarray) -> int:
+    d = _desc(desc)
+    p1 = np.ascontiguousarray(p1, dtype=np.uint32)
+    p2 = np.ascontiguousarray(p2, dtype=np.uint32)
+    out = _vp()
+    _check(lib().he_pack_client(p, ctypes.byref(d), p1.ctypes.data, p2.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
+def he_conv_client(p: int, f: int, d_v, d_ish, d_out, B: int, stream=None) -> None:
+    _check(lib().he_conv_client(p, f, _ptr(d_v), _ptr(d_ish), _ptr(d_out), B, _stream(stream)))
 
 
 def he_filters_tensor_core(f: int) -> int:

@@ -158,3 +158,88 @@ def test_masked_argument_errors():
         finally:
             H.he_filters_destroy(fm)
             H.he_filters_destroy(fr)
+
+
+def _protocol_case(N, L, ci, co, hw, seed):
+    ps, psis = U.ring(N, L)
+    lay = O.conv_layout(N, ci, co, hw, hw)
+    G, Hh = lay["G"], lay["H"]
+    I = synth.ints(seed, "cp/I", (ci, hw, hw), -8, 7)
+    F = synth.conv_weights(seed, "cp/F", co, ci, 3, 3, -128, 127)
+    ip = O.pack_input(I, lay)
+    sh = synth.ints(seed, "cp/sh", (1, G, N), 0, T - 1)
+    rho = synth.ints(seed, "cp/rho", (co, G, N), 0, T - 1)
+    shp = synth.ints(seed, "cp/shp", (1, Hh, N), 0, T - 1)
+    s = synth.ternary(seed, "cp/s", N)
+    a = synth.residues(seed, "cp/a", (L, N), ps)
+    e = synth.cbd(seed, "cp/e", N)
+    b_pk = np.zeros((L, N), np.uint32)
+    for l, q in enumerate(ps):
+        b_pk[l] = ((-O.negacyclic_mul(a[l], O.to_residues(s, q), q).astype(np.int64) + e) % q).astype(np.uint32)
+    ish = ip + sh[0]
+    c0 = np.zeros((1, G, L, N), np.uint32)
+    v = np.zeros((G, N), np.int64)
+    z = np.zeros(N, np.int64)
+    for g in range(G):
+        v[g] = synth.v_poly(seed, f"cp/v{g}", N)
+        c0[0, g] = O.encrypt_pk(-ish[g], s, a, e, v[g], synth.cbd(seed, f"cp/e0{g}", N), z, ps, T)[0]
+    e1 = np.stack([[synth.cbd(seed, f"cp/e1{n}{g}", N) for g in range(G)] for n in range(co)])
+    e2 = np.stack([[synth.cbd(seed, f"cp/e2{n}{g}", N) for g in range(G)] for n in range(co)])
+    p1, p2 = O.masked_server_init(F, rho, b_pk, e1, e2, ps, T, lay)
+    return dict(ps=ps, psis=psis, lay=lay, I=I, F=F, sh=sh, rho=rho, shp=shp, c0=c0, v=v, ish=ish, p1=p1, p2=p2)
+
+
+def _run_client(p, f, v, ish, B, Hh, L, N):
+    H = U.he()
+    torch = U.torch_cuda()
+    d_out = U.empty_dev((B, Hh, L, N))
+    H.he_conv_client(p, f, torch.from_numpy(np.ascontiguousarray(v, np.int32).ravel()).cuda(),
+                     torch.from_numpy(np.ascontiguousarray(ish, np.int32).ravel()).cuda(), d_out, B,
+                     torch.cuda.current_stream())
+    H.he_sync(torch.cuda.current_stream())
+    return U.from_dev(d_out).reshape(B, Hh, L, N)
+
+
+def test_client_step_matches_oracle():
+    H = U.he()
+    c = _protocol_case(512, 2, 12, 8, 4, seed=91)
+    lay, ps = c["lay"], c["ps"]
+    N, L = lay["N"], len(ps)
+    ref = O.client_c1_masked(c["v"], c["ish"], c["p1"], c["p2"], ps, lay)
+    with U.params(N, L) as p:
+        f = H.he_pack_client(p, dict(ci=12, co=8, h=4, w=4), c["p1"], c["p2"])
+        try:
+            got = _run_client(p, f, c["v"][None], c["ish"][None], 1, lay["H"], L, N)[0]
+        finally:
+            H.he_filters_destroy(f)
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_whole_protocol_on_gpu_decodes_to_the_convolution():
+    """Server step and client step both on the GPU (he_conv_layer_masked,
+    he_conv_client); the oracle only encrypts, prepares p1 / p2 and decodes."""
+    H = U.he()
+    ci, co, hw = 5, 6, 4
+    c = _protocol_case(256, 3, ci, co, hw, seed=92)
+    lay, ps = c["lay"], c["ps"]
+    N, L, Hh = lay["N"], len(ps), lay["H"]
+    desc = dict(ci=ci, co=co, h=hw, w=hw)
+    with U.params(N, L) as p:
+        fs = H.he_pack_masked(p, desc, c["F"], c["rho"].astype(np.uint32))
+        fc = H.he_pack_client(p, desc, c["p1"], c["p2"])
+        try:
+            c0r = _run_masked(p, fs, c["c0"], c["sh"].astype(np.uint32), c["shp"].astype(np.uint32), H.HE_COEFF, 1, Hh)[0]
+            c1r = _run_client(p, fc, c["v"][None], c["ish"][None], 1, Hh, L, N)[0]
+        finally:
+            H.he_filters_destroy(fs)
+            H.he_filters_destroy(fc)
+    r = np.stack([((c0r[:, l].astype(np.uint64) + c1r[:, l]) % q).astype(np.uint32) for l, q in enumerate(ps)], 1)
+    ref = O.centered(O.direct_conv(c["I"], c["F"], 1), T)
+    for h in range(Hh):
+        m = O.centered(O.decode_scaled(r[h], ps, T) - c["shp"][0, h], T)
+        for n in range(co):
+            if n // lay["s"] != h:
+                continue
+            for k in range(lay["h_out"]):
+                for l in range(lay["w_out"]):
+                    assert m[O.output_slot(lay, n, k, l)[1]] == ref[n, k, l]
