@@ -630,7 +630,11 @@ __global__ void __launch_bounds__(kThreads) k_fc(const ConvGeo a, const RingView
 // ---------------------------------------------------------------------------
 // plan kernels (one CTA per item; items are ordered longest first on the host)
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads, 3) k_plan_ntt(const CallDesc *__restrict__ calls,
+// 512 threads: a polynomial's transform is the CTA's work, and its passes
+// have 512 .. 2048 groups, so more threads shorten every pass; two CTAs per SM
+// keep a plain-20 inference's 276 transforms resident at once.
+constexpr int kNttThreads = 512;
+__global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__restrict__ calls,
                                                       const NttItem *__restrict__ items) {
     extern __shared__ uint4 smem4[];
     pdl_trigger();  // the MAC kernel may start streaming weights now
@@ -1371,7 +1375,7 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     if (pl.n_ntt && (phase == -1 || phase == 0)) {
         e = set_smem(k_plan_ntt, pl.smem_ntt);
         if (e != cudaSuccess) return e;
-        k_plan_ntt<<<pl.n_ntt, kThreads, pl.smem_ntt, st>>>(pl.d_calls, pl.d_ntt);
+        k_plan_ntt<<<pl.n_ntt, kNttThreads, pl.smem_ntt, st>>>(pl.d_calls, pl.d_ntt);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
