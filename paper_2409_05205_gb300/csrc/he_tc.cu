@@ -214,15 +214,20 @@ __device__ __forceinline__ void recombine4(const uint32_t (&v)[2][16], uint64_t 
     }
 }
 
-// A operand words of one K-step for limbs I and I + 1 of 16 weight words
+// A operand words of two K-steps for limbs I and I + 1 of 32 weight words
+// (slot 2m: columns 0..7 limb I, 8..15 limb I + 1; slot 2m + 1 the same for
+// words 16..31)
 template <int I>
-__device__ __forceinline__ void limbs16(const uint32_t (&w)[16], uint32_t (&r)[16]) {
+__device__ __forceinline__ void limbs32(const uint32_t (&w)[32], uint32_t (&r)[32]) {
 #pragma unroll
-    for (int pp = 0; pp < 8; ++pp) {
-        r[pp] = limb_pair<I>(w[2 * pp], w[2 * pp + 1]);
-        r[8 + pp] = limb_pair<I + 1>(w[2 * pp], w[2 * pp + 1]);
-    }
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int pp = 0; pp < 8; ++pp) {
+            r[16 * h + pp] = limb_pair<I>(w[16 * h + 2 * pp], w[16 * h + 2 * pp + 1]);
+            r[16 * h + 8 + pp] = limb_pair<I + 1>(w[16 * h + 2 * pp], w[16 * h + 2 * pp + 1]);
+        }
 }
+
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restrict__ calls,
                                                           const TcItem *__restrict__ items,
@@ -397,13 +402,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
         }
     } else if (warp < kWarpE0) {
         // ------------------------------------------------------------ A builders
-        // Software-pipelined: K-step k+1 is read and converted while the
-        // tensor-memory store of K-step k completes; then k is signalled.
+        // K-steps go in pairs (every tile and stage has an even number of
+        // them, so a pair never straddles a tile, a stage or the end of the
+        // slot ring): 32 weight words of row n -> two slots' limbs -> one
+        // 32-column tensor-memory store.  Software-pipelined: pair p+1 is
+        // read and converted while the store of pair p completes.
         const uint32_t sp = warp & 3u;
         const uint32_t tl = 32u * sp + lane, n = tl & 63u;
         const bool high = tl >= 64u;
         const uint32_t taddr = tmem + ((32u * sp) << 16) + 256u;
-        uint32_t ws = 0, as = 0, pend = kASlots;  // pend: slot stored but not yet signalled
+        uint32_t ws = 0, as = 0, pend = kASlots;  // pend: first slot of the pair stored but not yet signalled
         bool ok = true;
         for (uint32_t it = ib; ok && it < ie; ++it) {
             const TcItem item = items[it];
@@ -411,52 +419,59 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
             const uint32_t nch = C.co / kTcRows, nks = C.K / 16u;
             for (uint32_t b = item.b0; ok && b < item.b0 + item.nb; ++b)
                 for (uint32_t ch = 0; ok && ch < nch; ++ch)
-                    for (uint32_t ks = 0; ks < nks; ++ks, ++as) {
+                    for (uint32_t ks = 0; ks < nks; ks += 2u, as += 2u) {
                         const uint32_t st = ws % kWStages;
                         if ((ks & 3u) == 0 && !bar_wait(&bars.w_full[st], (ws / kWStages) & 1u, abort)) {
                             ok = false;
                             break;
                         }
                         const uint32_t slot = as % kASlots;
-                        if (as >= kASlots && !bar_wait(&bars.a_empty[slot], ((as / kASlots) - 1u) & 1u, abort)) {
+                        if (as >= kASlots && (!bar_wait(&bars.a_empty[slot], ((as / kASlots) - 1u) & 1u, abort) ||
+                                              !bar_wait(&bars.a_empty[slot + 1u], ((as / kASlots) - 1u) & 1u, abort))) {
                             ok = false;
                             break;
                         }
-                        // this K-step's 16 words of row n: [kq][64 rows][4 words]
+                        // the pair's 32 words of row n: [kq][64 rows][4 words], kq = 4 (ks % 4) .. + 7
                         const uint4 *src =
                             reinterpret_cast<const uint4 *>(wring + st * kWStageBytes + (ks & 3u) * 4096u) + n;
-                        uint32_t w[16];
+                        uint32_t w[32];
 #pragma unroll
-                        for (int kq = 0; kq < 4; ++kq) {
+                        for (int kq = 0; kq < 8; ++kq) {
                             const uint4 v = src[kq * 64];
                             w[4 * kq] = v.x;
                             w[4 * kq + 1] = v.y;
                             w[4 * kq + 2] = v.z;
                             w[4 * kq + 3] = v.w;
                         }
-                        uint32_t r[16];
+                        uint32_t r[32];
                         if (high)
-                            limbs16<2>(w, r);
+                            limbs32<2>(w, r);
                         else
-                            limbs16<0>(w, r);
-                        // the stage's words are in registers: its last K-step frees it
-                        if ((ks & 3u) == 3u || ks + 1u == nks) {
+                            limbs32<0>(w, r);
+                        // the stage's words are in registers: its last pair frees it
+                        if ((ks & 3u) == 2u || ks + 2u == nks) {
                             __syncwarp();
                             if (lane == 0) bar_arrive(&bars.w_empty[st]);
                             ++ws;
                         }
-                        if (pend < kASlots) {  // K-step as-1 has landed in tensor memory
+                        if (pend < kASlots) {  // the previous pair has landed in tensor memory
                             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                             tc_fence_before();
                             __syncwarp();
-                            if (lane == 0) bar_arrive(&bars.a_full[pend]);
+                            if (lane == 0) {
+                                bar_arrive(&bars.a_full[pend]);
+                                bar_arrive(&bars.a_full[pend + 1u]);
+                            }
                         }
                         asm volatile(
-                            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-                            "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr + 16u * slot),
+                            "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+                            "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                            "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr + 16u * slot),
                             "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
                             "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
-                            "r"(r[15])
+                            "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+                            "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+                            "r"(r[29]), "r"(r[30]), "r"(r[31])
                             : "memory");
                         pend = slot;
                     }
@@ -465,16 +480,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             __syncwarp();
-            if (ok && lane == 0) bar_arrive(&bars.a_full[pend]);
+            if (ok && lane == 0) {
+                bar_arrive(&bars.a_full[pend]);
+                bar_arrive(&bars.a_full[pend + 1u]);
+            }
         }
     } else if (warp < kWarpB0) {
         // ------------------------------------------------------------ epilogue
         // Warp (sub-partition sp, column half hc) takes columns 8 hc .. 8 hc + 7
-        // of its 32 rows.  The high rows (limbs 2, 3) reduce their share and
-        // pass it through shared memory; the low rows add it times 2^16 to
-        // their own sum, reduce once and store.  The four warps of a column
-        // half meet at named barrier 1 + hc once per tile, also after an
-        // abort, so that no warp waits there for one that has left.
+        // of its 32 rows.  Each output needs the low rows' sum (limbs 0, 1)
+        // plus 2^16 times the high rows' (limbs 2, 3): the low rows finish
+        // columns 0..3 of the half and the high rows 4..7, each receiving the
+        // other side's reduced share through shared memory.  The four warps
+        // of a column half meet at named barrier 1 + hc once per tile, also
+        // after an abort, so that no warp waits there for one that has left.
         const uint32_t sp = warp & 3u, hc = (warp - kWarpE0) >> 2;
         const uint32_t tl = 32u * sp + lane, n = tl & 63u;
         const bool high = tl >= 64u;
@@ -536,28 +555,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) bar_arrive(&bars.d_empty[db]);
-                        if (high) {  // all 8 reductions, then the 8 shared stores
-                            uint32_t r[8];
+                        // columns 0..3 are finished by the low rows, 4..7 by the high
+                        // rows: each side sends its reduced share of the other four
+                        {
+                            const uint32_t o = high ? 0u : 4u;
+                            uint32_t r[4];
 #pragma unroll
-                            for (uint32_t c = 0; c < 8; ++c) r[c] = reduce64(val[c], K);
+                            for (uint32_t c = 0; c < 4; ++c) r[c] = reduce64(high ? val[c] : val[4 + c], K);
 #pragma unroll
-                            for (uint32_t c = 0; c < 8; ++c) sts32(xa + 4u * (c * kTcRows), r[c]);
+                            for (uint32_t c = 0; c < 4; ++c) sts32(xa + 4u * ((o + c) * kTcRows), r[c]);
                         }
                     }
                     if (hc == 0)
                         asm volatile("bar.sync 1, 128;" ::: "memory");
                     else
                         asm volatile("bar.sync 2, 128;" ::: "memory");
-                    if (ok && !high) {  // the 8 shares, the 8 reductions, then the stores
-                        uint32_t hx[8], r[8];
+                    if (ok) {  // the other side's 4 shares, 4 reductions, then the stores
+                        const uint32_t o = high ? 4u : 0u;
+                        uint32_t hx[4], r[4];
 #pragma unroll
-                        for (uint32_t c = 0; c < 8; ++c) hx[c] = lds32(xa + 4u * (c * kTcRows));
+                        for (uint32_t c = 0; c < 4; ++c) hx[c] = lds32(xa + 4u * ((o + c) * kTcRows));
+                        // low rows: own sum + 2^16 (high share); high rows: 2^16 own sum + low share
 #pragma unroll
-                        for (uint32_t c = 0; c < 8; ++c) r[c] = reduce64(val[c] + ((uint64_t)hx[c] << 16), K);
+                        for (uint32_t c = 0; c < 4; ++c) {
+                            const uint32_t mine = reduce64(high ? val[4 + c] : val[c], K);
+                            r[c] = high ? reduce64(((uint64_t)mine << 16) + hx[c], K)
+                                        : reduce64(((uint64_t)hx[c] << 16) + mine, K);
+                        }
                         uint32_t *z = zb + (size_t)b * co + ch * kTcRows;
 #pragma unroll
-                        for (uint32_t c = 0; c < 8; ++c)
-                            if (8u * hc + c < ncols) z[c * cstride] = r[c];
+                        for (uint32_t c = 0; c < 4; ++c)
+                            if (8u * hc + o + c < ncols) z[(o + c) * cstride] = r[c];
                     }
                     ++ds;
                 }
