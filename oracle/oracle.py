@@ -697,6 +697,29 @@ def encrypt_pk(m: np.ndarray, s: np.ndarray, a: np.ndarray, e: np.ndarray,
     return out
 
 
+def rescale_last_limb(x: np.ndarray, primes: list[int]) -> np.ndarray:
+    """The RNS rescale of the paper's Delta^-1 step (Alg. 1, the line after
+    the product; Sec. IV-A: Q' after rescale), read as dropping the last
+    prime with rounding: for every coefficient X in [0, Q) (CRT of its
+    residues), X' = floor((X + floor(q_L / 2)) / q_L), given as residues of
+    the first L - 1 primes.  By its definition, with Python integers.
+    x: [..., L, N] residues -> [..., L - 1, N]."""
+    L = len(primes)
+    assert x.shape[-2] == L and L >= 2
+    qL = primes[-1]
+    lead = x.shape[:-2]
+    N = x.shape[-1]
+    flat = x.reshape(-1, L, N)
+    out = np.zeros((flat.shape[0], L - 1, N), dtype=np.uint32)
+    for i in range(flat.shape[0]):
+        X = crt([flat[i, l] for l in range(L)], primes)
+        for k, v in enumerate(X):
+            xr = (v + qL // 2) // qL
+            for l in range(L - 1):
+                out[i, l, k] = xr % primes[l]
+    return out.reshape(lead + (L - 1, N))
+
+
 def decrypt(ct: np.ndarray, s: np.ndarray, primes: list[int], t: int) -> np.ndarray:
     """m = round(t * [c0 + c1*s]_Q / Q) mod t, centered to (-t/2, t/2]
     (eq. (decryption) with the BFV scale t/Q; ties round up).
