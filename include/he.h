@@ -292,6 +292,19 @@ he_status he_conv_client(he_params_t p, he_filters_t f, const int32_t *d_v, cons
 he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain,
                       uint32_t *d_out, int out_mode, uint32_t B, void *stream);
 
+/* The RNS rescale of `count` polynomials: the paper's Delta^-1 step (Alg. 1,
+ * after the product; Sec. IV-A: Q' after rescale), read for an integer
+ * plaintext modulus as modulus switching by the last prime: every
+ * coefficient X in [0, Q) becomes X' = floor((X + floor(q_L / 2)) / q_L) in
+ * [0, Q / q_L), which keeps the plaintext mod t (with noise below about
+ * (1 + |s|_1) / 2) and drops one limb.
+ *   d_in:  DEVICE uint32 [count][L][N], coefficient domain.
+ *   d_out: DEVICE uint32 [count][L-1][N], residues of the first L - 1 primes
+ *          (the ring of he_params_create(N, L - 1, those primes, ...)).
+ * L >= 2; buffers 16-byte aligned and not overlapping.  Asynchronous. */
+he_status he_rescale(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count,
+                     void *stream);
+
 /* The forward negacyclic NTT of `count` RNS polynomials (the input
  * transform of the server step, Sec. IV-A).  d_in, d_out: DEVICE uint32
  * [count][L][N]; in place if equal.  Output in the canonical NTT order

@@ -723,6 +723,19 @@ he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int i
     return HE_OK;
 }
 
+he_status he_rescale(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count, void *stream) {
+    if (!p || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
+    if (p->L < 2) return fail(HE_ERR_ARG, "rescaling needs at least 2 limbs (L = %u)", p->L);
+    if (!aligned16(d_in) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    const size_t nin = (size_t)count * p->L * p->N, nout = (size_t)count * (p->L - 1) * p->N;
+    if (d_in < d_out + nout && d_out < d_in + nin) return fail(HE_ERR_ARG, "d_in and d_out overlap");
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    cudaError_t e = he_launch_rescale(p->ring, d_in, d_out, count, (cudaStream_t)stream);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "rescale");
+}
+
 he_status he_ntt_forward(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count, void *stream) {
     if (!p || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (need_device(p) != HE_OK) return HE_ERR_ARG;

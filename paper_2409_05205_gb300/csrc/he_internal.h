@@ -326,6 +326,8 @@ cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_co
 cudaError_t he_launch_pack_conv_masked(const RingView &r, const int8_t *d_w, const uint32_t *d_rho,
                                        const uint32_t *d_p2, const he_conv_desc &d, const he_conv_layout &lay,
                                        uint32_t lt, uint32_t lcs, uint32_t *bank, cudaStream_t st);
+cudaError_t he_launch_rescale(const RingView &r, const uint32_t *in, uint32_t *out, uint32_t npoly,
+                              cudaStream_t st);
 cudaError_t he_launch_client_in(const RingView &r, const int32_t *v, const int32_t *ish, uint32_t *ws, uint32_t B,
                                 uint32_t G, cudaStream_t st);
 cudaError_t he_launch_ntt_masked_in(const RingView &r, const uint32_t *c0, const uint32_t *sh, uint32_t *ws,

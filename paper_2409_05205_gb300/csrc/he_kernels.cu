@@ -495,6 +495,49 @@ __global__ void __launch_bounds__(kThreads) k_client_in(const RingView r, const 
     }
 }
 
+// RNS rescale by the last prime with rounding: X' = floor((X + h) / q_L),
+// h = floor(q_L / 2), from the residues alone: with y = (x_L + h) mod q_L,
+// X + h - y is a multiple of q_L, so x'_l = (x_l + h - y) q_L^-1 mod q_l.
+struct RescaleLimb {
+    uint32_t q, h, qinv, qinvs;  // q_l, h mod q_l, q_L^-1 mod q_l and its Shoup constant
+};
+struct RescaleArgs {
+    RescaleLimb limb[HE_MAX_LIMBS];
+    uint32_t qL, hL, N, L;  // last prime, floor(q_L / 2), ring degree, limbs of the input
+};
+
+__global__ void __launch_bounds__(kThreads) k_rescale(const RescaleArgs a, const uint32_t *__restrict__ in,
+                                                      uint32_t *__restrict__ out, uint32_t npoly) {
+    const uint32_t nq = a.N >> 2;
+    const size_t total = (size_t)npoly * nq;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t pi = i / nq;
+        const uint32_t k4 = (uint32_t)(i % nq);
+        const uint32_t *src = in + pi * a.L * a.N;
+        uint32_t *dst = out + pi * (a.L - 1u) * a.N;
+        const uint4 xl = __ldcs(reinterpret_cast<const uint4 *>(src + (size_t)(a.L - 1u) * a.N) + k4);
+        uint32_t y[4] = {xl.x + a.hL, xl.y + a.hL, xl.z + a.hL, xl.w + a.hL};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[u] = min(y[u], y[u] - a.qL);  // (x_L + h) mod q_L
+        for (uint32_t l = 0; l + 1u < a.L; ++l) {
+            const RescaleLimb &R = a.limb[l];
+            const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src + (size_t)l * a.N) + k4);
+            const uint32_t xv[4] = {x.x, x.y, x.z, x.w};
+            uint32_t r[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t ym = min(y[u], y[u] - R.q);          // y mod q_l (q_L < 2 q_l)
+                uint32_t v = xv[u] + R.h;                           // < 2 q_l
+                v = min(v, v - R.q);
+                v = v + R.q - ym;                                    // (x_l + h - y) mod q_l, in [1, 2 q_l)
+                v = min(v, v - R.q);
+                r[u] = red_2q(shoup_lazy(v, R.qinv, R.qinvs, R.q), R.q);
+            }
+            __stcs(reinterpret_cast<uint4 *>(dst + (size_t)l * a.N) + k4, make_uint4(r[0], r[1], r[2], r[3]));
+        }
+    }
+}
+
 struct PackConvArgs {
     RingView r;
     const int8_t *w;   // [co][ci][fh][fw]
@@ -1199,6 +1242,39 @@ cudaError_t he_launch_client_in(const RingView &r, const int32_t *v, const int32
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return he_launch_ntt(r, ws, ws, np, false, st);
+}
+
+cudaError_t he_launch_rescale(const RingView &r, const uint32_t *in, uint32_t *out, uint32_t npoly,
+                              cudaStream_t st) {
+    if (npoly == 0) return cudaSuccess;
+    RescaleArgs a{};
+    const uint32_t qL = r.limb[r.L - 1].q;
+    a.qL = qL;
+    a.hL = qL / 2u;
+    a.N = r.N;
+    a.L = r.L;
+    for (uint32_t l = 0; l + 1u < r.L; ++l) {
+        const uint32_t q = r.limb[l].q;
+        RescaleLimb &R = a.limb[l];
+        R.q = q;
+        R.h = (qL / 2u) % q;
+        // q_L^-1 mod q by Fermat (q prime)
+        uint64_t base = qL % q, e = q - 2u, acc = 1;
+        while (e) {
+            if (e & 1u) acc = acc * base % q;
+            base = base * base % q;
+            e >>= 1;
+        }
+        R.qinv = (uint32_t)acc;
+        R.qinvs = (uint32_t)(((uint64_t)R.qinv << 32) / q);
+    }
+    int sms = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    if (e != cudaSuccess) return e;
+    const size_t work = (size_t)npoly * (r.N >> 2);
+    const uint32_t grid = (uint32_t)std::min<size_t>((work + kThreads - 1) / kThreads, (size_t)sms * 8u);
+    k_rescale<<<grid, kThreads, 0, st>>>(a, in, out, npoly);
+    return cudaGetLastError();
 }
 
 cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_layout &fl, uint32_t *bank,

@@ -95,6 +95,7 @@ _SIGS = {
     "he_pack_masked": [_vp, ctypes.POINTER(he_conv_desc), _vp, _vp, ctypes.POINTER(_vp)],
     "he_conv_layer_masked": [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _u32, _vp],
     "he_pack_client": [_vp, ctypes.POINTER(he_conv_desc), _vp, _vp, ctypes.POINTER(_vp)],
+    "he_rescale": [_vp, _vp, _vp, _u32, _vp],
     "he_conv_client": [_vp, _vp, _vp, _vp, _vp, _u32, _vp],
     "he_pack_fc": [_vp, _u32, _u32, _vp, _vp, ctypes.POINTER(_vp)],
     "he_filters_destroy": [_vp],
@@ -281,6 +282,10 @@ def he_pack_client(p: int, desc, p1: np.ndarray, p2: np.ndarray) -> int:
 
 def he_conv_client(p: int, f: int, d_v, d_ish, d_out, B: int, stream=None) -> None:
     _check(lib().he_conv_client(p, f, _ptr(d_v), _ptr(d_ish), _ptr(d_out), B, _stream(stream)))
+
+
+def he_rescale(p: int, d_in, d_out, count: int, stream=None) -> None:
+    _check(lib().he_rescale(p, _ptr(d_in), _ptr(d_out), count, _stream(stream)))
 
 
 def he_filters_tensor_core(f: int) -> int:
