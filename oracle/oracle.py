@@ -618,6 +618,85 @@ def client_c1_masked(v: np.ndarray, ish: np.ndarray, p1: np.ndarray, p2: np.ndar
     return out
 
 
+def _fc_window(y: np.ndarray, lay: dict) -> np.ndarray:
+    """Theorem 1's output window: coefficients k < rows_j of block j are kept,
+    the others set to 0.  y: [P][N] -> [P][N]."""
+    y = y.copy()
+    for j in range(lay["P"]):
+        y[j, lay["rows"][j]:] = 0
+    return y
+
+
+def fc_layer_masked(c0: np.ndarray, sh: np.ndarray, rho: np.ndarray, W: np.ndarray,
+                    Bv: np.ndarray | None, shp: np.ndarray, primes: list[int], psis: list[int],
+                    t: int, lay: dict, tier: str = "schoolbook") -> np.ndarray:
+    """Server evaluation of Alg. 2 with an integer plaintext modulus (every
+    plaintext term scaled by Delta_Q, no rescale), per weight block j:
+        y_j     = c0 * rho_j - Delta_Q * sh * w_j                (mod q_l)
+        c0^r_j  = window(y_j) + Delta_Q * (d_j + sh'_j)
+    where window keeps Theorem 1's coefficients k < rows_j.
+    c0:  [B][L][N] residues, the c0 part of Enc(-(i + sh));
+    sh:  [B][N] integers in [0, t), the server's share of the packed input;
+    rho: [P][N] integers in [0, t), the masks rho_j;
+    shp: [B][P][N] integers in [0, t), the share sh' added to the output.
+    Returns [B][P][L][N] residues."""
+    B, L, N = c0.shape
+    assert N == lay["N"] and L == len(primes)
+    wpk = pack_fc_weights(W, lay)
+    dpk = pack_fc_bias(Bv if Bv is not None else np.zeros(lay["n_out"], np.int64), lay)
+    D = delta_q(primes, t)
+    P = lay["P"]
+    out = np.zeros((B, P, L, N), dtype=np.uint32)
+    for l, (q, psi) in enumerate(zip(primes, psis)):
+        Dq = D % q
+        dsh = (np.asarray(sh, dtype=np.uint64) % q) * Dq % q                    # Delta sh  [B][N]
+        x = np.stack([c0[:, l, :].astype(np.uint32), dsh.astype(np.uint32)])    # [2][B][N]
+        w = np.stack([to_residues(rho, q), to_residues(-wpk, q)], axis=1)       # [P][2][N]
+        y = _sum_products(x, w, q, psi, tier)                                   # [P][B][N]
+        for b in range(B):
+            win = _fc_window(y[:, b, :].astype(np.uint64), lay)
+            add = Dq * ((to_residues(dpk, q).astype(np.uint64) + np.asarray(shp[b], np.uint64)) % q) % q
+            out[b, :, l, :] = ((win + add) % q).astype(np.uint32)
+    return out
+
+
+def masked_fc_server_init(W: np.ndarray, rho: np.ndarray, b_pk: np.ndarray, e1: np.ndarray,
+                          e2: np.ndarray, primes: list[int], t: int, lay: dict) -> tuple:
+    """Alg. 2 server initialisation, per weight block j:
+        p1_j = rho_j * b + e1_j,   p2_j = Delta_Q * (w_j + rho_j) + e2_j   (mod q_l).
+    b_pk: [L][N] residues of the public key's b; e1, e2: [P][N] small
+    integers.  Returns p1, p2: [P][L][N]."""
+    wpk = pack_fc_weights(W, lay)
+    P, N = wpk.shape
+    D = delta_q(primes, t)
+    p1 = np.zeros((P, len(primes), N), dtype=np.uint32)
+    p2 = np.zeros((P, len(primes), N), dtype=np.uint32)
+    for l, q in enumerate(primes):
+        for j in range(P):
+            p1[j, l] = ((negacyclic_mul(to_residues(rho[j], q), b_pk[l], q).astype(np.int64)
+                         + np.asarray(e1[j], np.int64)) % q).astype(np.uint32)
+            m = (np.asarray(wpk[j], np.int64) + np.asarray(rho[j], np.int64)) % q
+            p2[j, l] = (((D % q) * m + np.asarray(e2[j], np.int64)) % q).astype(np.uint32)
+    return p1, p2
+
+
+def client_c1_fc_masked(v: np.ndarray, ish: np.ndarray, p1: np.ndarray, p2: np.ndarray,
+                        primes: list[int], lay: dict) -> np.ndarray:
+    """Client side of Alg. 2, with the sign on v that cancels the server's
+    mask term (as for Alg. 1): c1_j = window(-v * p1_j + (i + sh) * p2_j).
+    v: [N] the client's encryption randomness; ish: [N] the packed FC input
+    plus the share.  Returns [P][L][N]."""
+    P, L, N = p1.shape
+    out = np.zeros((P, L, N), dtype=np.uint32)
+    for l, q in enumerate(primes):
+        y = np.zeros((P, N), dtype=np.uint64)
+        for j in range(P):
+            y[j] = (negacyclic_mul(to_residues(-np.asarray(v, np.int64), q), p1[j, l], q).astype(np.uint64)
+                    + negacyclic_mul(to_residues(ish, q), p2[j, l], q)) % q
+        out[:, l, :] = _fc_window(y, lay).astype(np.uint32)
+    return out
+
+
 def decode_scaled(r: np.ndarray, primes: list[int], t: int) -> np.ndarray:
     """round(t [r]_Q / Q) mod t, centered: the plaintext of a sum c0^r + c1^r,
     which needs no secret key (Alg. 1's last line).  r: [L][N] -> int64 [N]."""
