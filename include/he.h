@@ -292,6 +292,47 @@ he_status he_conv_client(he_params_t p, he_filters_t f, const int32_t *d_v, cons
 he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain,
                       uint32_t *d_out, int out_mode, uint32_t B, void *stream);
 
+/* Server model load for the masked FC step of Alg. 2 (its initialisation,
+ * read for an integer plaintext modulus t like the Conv step's):
+ *   W, bias: as for he_pack_fc (bias may be NULL);
+ *   rho: HOST uint32 [P_fc][N], the masks rho_j, integers in [0, t) drawn by
+ *        the caller (words at or above t fail with HE_ERR_ARG).
+ * The bank holds NTT(rho_j) and NTT(-Delta_Q w_j) per weight block
+ * (P_fc * 2 * L * N * 4 bytes) plus Delta_Q d(X).  Such a bank runs only
+ * through he_fc_layer_masked.  Blocking. */
+he_status he_pack_fc_masked(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t *W,
+                            const int32_t *bias, const uint32_t *rho, he_filters_t *out);
+
+/* Server evaluation of Alg. 2 for B ciphertexts, per weight block j:
+ *   c0^r_j = window(c0 * rho_j - Delta_Q * sh * w_j) + Delta_Q * (d_j + sh'_j),
+ * window keeping Theorem 1's output coefficients k < rows_j (the others 0).
+ *   d_c0:  DEVICE uint32 [B][L][N], the c0 part of Enc(-(i + sh)), in
+ *          `in_domain` (HE_COEFF or HE_NTT).
+ *   d_sh:  DEVICE uint32 [B][N], the server's share of the packed input,
+ *          integers in [0, t), coefficient domain.
+ *   d_shp: DEVICE uint32 [B][P_fc][N], the new share sh', integers in [0, t).
+ *   d_out: DEVICE uint32 [B][P_fc][L][N], every word written.
+ * round(t (c0^r + c1^r) / Q) mod t minus sh' is then W I + B on each window.
+ * Asynchronous on `stream`. */
+he_status he_fc_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0,
+                             const uint32_t *d_sh, const uint32_t *d_shp, int in_domain,
+                             uint32_t *d_out, uint32_t B, void *stream);
+
+/* The client's FC bank: p1_j = rho_j b + e1_j and p2_j = Delta_Q (w_j + rho_j)
+ * + e2_j from the server, HOST uint32 [P_fc][L][N] residues of each limb
+ * (other words fail with HE_ERR_ARG).  Blocking. */
+he_status he_pack_fc_client(he_params_t p, uint32_t n_in, uint32_t n_out, const uint32_t *p1,
+                            const uint32_t *p2, he_filters_t *out);
+
+/* Client evaluation of Alg. 2 for B ciphertexts, with the sign on v that
+ * cancels the server's mask term:  c1^r_j = window(-v * p1_j + (i + sh) * p2_j).
+ *   d_v:   DEVICE int32 [B][N], the randomness v of the client's encryption.
+ *   d_ish: DEVICE int32 [B][N], the packed FC input plus the share.
+ *   d_out: DEVICE uint32 [B][P_fc][L][N]; every word written.
+ * f must come from he_pack_fc_client.  Asynchronous on `stream`. */
+he_status he_fc_client(he_params_t p, he_filters_t f, const int32_t *d_v, const int32_t *d_ish,
+                       uint32_t *d_out, uint32_t B, void *stream);
+
 /* The RNS rescale of `count` polynomials: the paper's Delta^-1 step (Alg. 1,
  * after the product; Sec. IV-A: Q' after rescale), read for an integer
  * plaintext modulus as modulus switching by the last prime: every

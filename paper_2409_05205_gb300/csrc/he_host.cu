@@ -585,6 +585,22 @@ he_status he_filters_tensor_core(he_filters_t f, uint32_t *tc) {
     return HE_OK;
 }
 
+// Delta_Q * d(X) residues [L][n_out] of an FC bias (Theorem 1), on the device.
+static cudaError_t upload_fc_bias(const he_params_s *p, const int32_t *bias, uint32_t n_out, uint32_t **d_bias) {
+    std::vector<uint32_t> hb((size_t)p->L * n_out);
+    for (uint32_t l = 0; l < p->L; ++l) {
+        const uint32_t q = p->q[l];
+        for (uint32_t k = 0; k < n_out; ++k) {
+            const int64_t b = bias[k];
+            const uint32_t br = (uint32_t)(((b % (int64_t)q) + (int64_t)q) % (int64_t)q);
+            hb[(size_t)l * n_out + k] = mul_mod(br, p->delta[l], q);
+        }
+    }
+    cudaError_t e = cudaMalloc(d_bias, hb.size() * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(*d_bias, hb.data(), hb.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    return e;
+}
+
 he_status he_pack_fc(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t *W, const int32_t *bias,
                      he_filters_t *out) {
     if (!p || !W || !out) return fail(HE_ERR_ARG, "NULL argument");
@@ -610,19 +626,7 @@ he_status he_pack_fc(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t 
         delete f;
         return fail(HE_ERR_NOMEM, "FC bank of %zu bytes", nb);
     }
-    if (bias) {
-        std::vector<uint32_t> hb((size_t)p->L * n_out);
-        for (uint32_t l = 0; l < p->L; ++l) {
-            const uint32_t q = p->q[l];
-            for (uint32_t k = 0; k < n_out; ++k) {
-                const int64_t b = bias[k];
-                const uint32_t br = (uint32_t)(((b % (int64_t)q) + (int64_t)q) % (int64_t)q);
-                hb[(size_t)l * n_out + k] = mul_mod(br, p->delta[l], q);
-            }
-        }
-        e = cudaMalloc(&f->bias, hb.size() * sizeof(uint32_t));
-        if (e == cudaSuccess) e = cudaMemcpy(f->bias, hb.data(), hb.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
-    }
+    if (bias) e = upload_fc_bias(p, bias, n_out, &f->bias);
     if (e == cudaSuccess) e = cudaMalloc(&d_W, wbytes);
     if (e == cudaSuccess) e = cudaMemcpy(d_W, W, wbytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = he_launch_pack_fc(p->ring, d_W, fl, f->bank, 0);
@@ -699,6 +703,7 @@ he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int i
                       int out_mode, uint32_t B, void *stream) {
     if (!p || !f || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (f->kind != HE_KIND_FC || f->p != p) return fail(HE_ERR_ARG, "filters are not an FC bank of these params");
+    if (f->masked) return fail(HE_ERR_ARG, "a masked FC bank is evaluated by he_fc_layer_masked / he_fc_client");
     if (in_domain != HE_COEFF && in_domain != HE_NTT) return fail(HE_ERR_ARG, "bad in_domain %d", in_domain);
     if (out_mode != HE_OUT_EXTRACTED && out_mode != HE_OUT_PER_CHANNEL)
         return fail(HE_ERR_ARG, "bad out_mode %d for an FC layer", out_mode);
@@ -721,6 +726,111 @@ he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int i
     cudaError_t e = he_launch_fc(p->ring, f->fl, f->bank, f->bias, x, d_out, out_mode, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "fc kernel");
     return HE_OK;
+}
+
+// Shared by he_pack_fc_masked (mode 1) and he_pack_fc_client (mode 2).
+static he_status pack_fc_masked(he_params_t p, uint32_t n_in, uint32_t n_out, int mode, const int8_t *W,
+                                const int32_t *bias, const uint32_t *m0, const uint32_t *m1, he_filters_t *out) {
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    *out = nullptr;
+    he_fc_layout fl{};
+    he_status st = fc_layout(p, n_in, n_out, &fl);
+    if (st != HE_OK) return st;
+    const size_t nm0 = mode == 1 ? (size_t)fl.P_fc * p->N : (size_t)fl.P_fc * p->L * p->N;
+    if (mode == 1) {
+        for (size_t i = 0; i < nm0; ++i)
+            if (m0[i] >= p->t) return fail(HE_ERR_ARG, "rho[%zu] = %u is not below t = %u", i, m0[i], p->t);
+    } else {
+        for (size_t i = 0; i < nm0; ++i) {
+            const uint32_t q = p->q[(i / p->N) % p->L];
+            if (m0[i] >= q || m1[i] >= q) return fail(HE_ERR_ARG, "p1 / p2 word %zu is not a residue of its limb", i);
+        }
+    }
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    he_filters_s *f = new (std::nothrow) he_filters_s();
+    if (!f) return fail(HE_ERR_NOMEM, "filters");
+    f->p = p;
+    f->kind = HE_KIND_FC;
+    f->fl = fl;
+    f->masked = (uint32_t)mode;
+    f->bank_bytes = (size_t)fl.P_fc * 2u * p->L * p->N * sizeof(uint32_t);
+    cudaError_t e = cudaMalloc(&f->bank, f->bank_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const size_t nb = f->bank_bytes;
+        delete f;
+        return fail(HE_ERR_NOMEM, "masked FC bank of %zu bytes", nb);
+    }
+    int8_t *d_W = nullptr;
+    uint32_t *d_m0 = nullptr, *d_m1 = nullptr;
+    if (bias) e = upload_fc_bias(p, bias, n_out, &f->bias);
+    if (e == cudaSuccess && W) e = cudaMalloc(&d_W, (size_t)n_out * n_in);
+    if (e == cudaSuccess && W) e = cudaMemcpy(d_W, W, (size_t)n_out * n_in, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&d_m0, nm0 * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(d_m0, m0, nm0 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && m1) e = cudaMalloc(&d_m1, nm0 * sizeof(uint32_t));
+    if (e == cudaSuccess && m1) e = cudaMemcpy(d_m1, m1, nm0 * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = he_launch_pack_fc_masked(p->ring, d_W, d_m0, d_m1, fl, mode, f->bank, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_W);
+    cudaFree(d_m0);
+    cudaFree(d_m1);
+    if (e != cudaSuccess) {
+        he_filters_destroy(f);
+        return cuda_fail(e, mode == 1 ? "pack masked FC bank" : "pack client FC bank");
+    }
+    *out = f;
+    return HE_OK;
+}
+
+he_status he_pack_fc_masked(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t *W, const int32_t *bias,
+                            const uint32_t *rho, he_filters_t *out) {
+    if (!p || !W || !rho || !out) return fail(HE_ERR_ARG, "NULL argument");
+    return pack_fc_masked(p, n_in, n_out, 1, W, bias, rho, nullptr, out);
+}
+
+he_status he_pack_fc_client(he_params_t p, uint32_t n_in, uint32_t n_out, const uint32_t *p1, const uint32_t *p2,
+                            he_filters_t *out) {
+    if (!p || !p1 || !p2 || !out) return fail(HE_ERR_ARG, "NULL argument");
+    return pack_fc_masked(p, n_in, n_out, 2, nullptr, nullptr, p1, p2, out);
+}
+
+he_status he_fc_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0, const uint32_t *d_sh,
+                             const uint32_t *d_shp, int in_domain, uint32_t *d_out, uint32_t B, void *stream) {
+    if (!p || !f || !d_c0 || !d_sh || !d_shp || !d_out) return fail(HE_ERR_ARG, "NULL argument");
+    if (f->kind != HE_KIND_FC || f->masked != 1) return fail(HE_ERR_ARG, "filters are not a masked (server) FC bank");
+    if (f->p != p) return fail(HE_ERR_ARG, "filters belong to other params");
+    if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
+    if (in_domain != HE_COEFF && in_domain != HE_NTT) return fail(HE_ERR_ARG, "bad in_domain");
+    if (!aligned16(d_c0) || !aligned16(d_sh) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    if (ensure_ws(p, (size_t)B * 2u * p->L * p->N * 4u) != HE_OK) return HE_ERR_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *ws = static_cast<uint32_t *>(p->ws);
+    cudaError_t e = he_launch_ntt_masked_in(p->ring, d_c0, d_sh, ws, B, 1u, in_domain == HE_NTT, st);
+    if (e == cudaSuccess) e = he_launch_fc_masked(p->ring, f->fl, f->bank, f->bias, ws, d_shp, d_out, B, st);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "masked FC layer");
+}
+
+he_status he_fc_client(he_params_t p, he_filters_t f, const int32_t *d_v, const int32_t *d_ish, uint32_t *d_out,
+                       uint32_t B, void *stream) {
+    if (!p || !f || !d_v || !d_ish || !d_out) return fail(HE_ERR_ARG, "NULL argument");
+    if (f->kind != HE_KIND_FC || f->masked != 2) return fail(HE_ERR_ARG, "filters are not a client FC bank");
+    if (f->p != p) return fail(HE_ERR_ARG, "filters belong to other params");
+    if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
+    if (!aligned16(d_out)) return fail(HE_ERR_ARG, "d_out must be 16-byte aligned");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    if (ensure_ws(p, (size_t)B * 2u * p->L * p->N * 4u) != HE_OK) return HE_ERR_NOMEM;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *ws = static_cast<uint32_t *>(p->ws);
+    cudaError_t e = he_launch_client_in(p->ring, d_v, d_ish, ws, B, 1u, st);
+    if (e == cudaSuccess) e = he_launch_fc_masked(p->ring, f->fl, f->bank, nullptr, ws, nullptr, d_out, B, st);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "client FC step");
 }
 
 he_status he_rescale(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count, void *stream) {
@@ -929,8 +1039,8 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         const he_layer_call &c = calls[i];
         const he_filters_s *f = c.filters;
         if (!f || !c.d_in || !c.d_out) return fail(HE_ERR_ARG, "call %u: NULL argument", i);
-        if (f->kind == HE_KIND_CONV && f->masked)
-            return fail(HE_ERR_UNSUPPORTED, "call %u: masked banks run through he_conv_layer_masked", i);
+        if (f->masked)
+            return fail(HE_ERR_UNSUPPORTED, "call %u: masked banks run through the masked entry points", i);
         const he_params_s *p = f->p;
         if (p->device != device) return fail(HE_ERR_ARG, "call %u: params on another device", i);
         if (c.B == 0) return fail(HE_ERR_ARG, "call %u: B must be >= 1", i);

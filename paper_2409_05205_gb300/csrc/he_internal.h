@@ -297,7 +297,8 @@ struct he_filters_s {
     uint32_t lcs;     // conv bank chunk interleave (log2)
     uint32_t tc;      // conv bank in the tensor-core layout (bank_index_tc)
     uint32_t masked;  // 1: bank of the masked server step, 2G groups (rho_{g,n}, then -Delta_Q fhat_{g,n});
-                      // 2: bank of the client step, 2G groups (p1_{g,n}, then p2_{g,n})
+                      // 2: bank of the client step, 2G groups (p1_{g,n}, then p2_{g,n});
+                      // FC banks: [P][2][L][N] pairs (rho_j, -Delta_Q w_j) or (p1_j, p2_j)
     uint32_t nc;      // split MAC: channels per work item
     he_fc_layout fl;
     uint32_t *bank;   // conv: [co][L][G][N]; fc: [P][L][N]; NTT domain, pre-scaled
@@ -338,6 +339,11 @@ cudaError_t he_launch_conv_masked(const RingView &r, const he_conv_desc &d, cons
 cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32_t *bank,
                          const uint32_t *bias, const uint32_t *x_ntt, uint32_t *out, int mode,
                          uint32_t B, cudaStream_t st);
+cudaError_t he_launch_pack_fc_masked(const RingView &r, const int8_t *d_W, const uint32_t *d_m0, const uint32_t *d_m1,
+                                     const he_fc_layout &fl, int mode, uint32_t *bank, cudaStream_t st);
+cudaError_t he_launch_fc_masked(const RingView &r, const he_fc_layout &fl, const uint32_t *bank, const uint32_t *bias,
+                                const uint32_t *x_ntt, const uint32_t *shp, uint32_t *out, uint32_t B,
+                                cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // device arithmetic

@@ -614,37 +614,126 @@ struct PackFcArgs {
     uint32_t n_in, n_in_p, n_out, rpp;
 };
 
+// w_j(X) of weight block jp (Sec. III-B eq. (w(x) formula) on the zero-padded
+// n_o' x n_i' matrix) into A as residues of q times `scale` (scale < q).
+__device__ __forceinline__ void fc_weight_poly(uint32_t *A, const int8_t *__restrict__ W, uint32_t jp, uint32_t N,
+                                               uint32_t n_in, uint32_t n_in_p, uint32_t n_out, uint32_t rpp,
+                                               uint32_t scale, const LimbK &K) {
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = 0;
+    __syncthreads();
+    const uint32_t rows = min(rpp, n_out - jp * rpp);
+    for (uint32_t idx = threadIdx.x; idx < rows * n_in_p; idx += blockDim.x) {
+        const uint32_t k = idx / n_in_p, li = idx % n_in_p;
+        const uint32_t R = jp * rpp + k;
+        int v;
+        uint32_t pos;
+        if (li == 0) {
+            v = W[(size_t)R * n_in];
+            pos = k;
+        } else {
+            const uint32_t col = n_in_p - li;
+            if (col >= n_in) continue;
+            v = -(int)W[(size_t)R * n_in + col];
+            pos = li * rpp + k;
+        }
+        const uint32_t x = v >= 0 ? (uint32_t)v : K.q - (uint32_t)(-v);
+        A[pos] = scale == 1u ? x : mulmod(x, scale, K);
+    }
+    __syncthreads();
+}
+
+// NTT of the polynomial in A, times N^-1 (the inverse transform of the
+// layer then needs no scaling), to dst.
+__device__ __forceinline__ void fc_bank_store(uint32_t *A, uint32_t *dst, uint32_t logN, const uint2 *tw,
+                                              const LimbK &K) {
+    const uint32_t N = 1u << logN;
+    ntt_fwd_smem(A, logN, tw, K.q);
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+        const uint32_t x = red_4q(A[k], K.q2, K.q);
+        dst[k] = red_2q(shoup_lazy(x, K.ninv, K.ninvs, K.q), K.q);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_pack_fc(const PackFcArgs a) {
     extern __shared__ uint4 smem4[];
     uint32_t *A = reinterpret_cast<uint32_t *>(smem4);
     const uint32_t jp = blockIdx.x, l = blockIdx.y;
     const uint32_t N = a.r.N;
     const LimbK K = a.r.limb[l];
-    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = 0;
-    __syncthreads();
-    const uint32_t rows = min(a.rpp, a.n_out - jp * a.rpp);
-    for (uint32_t idx = threadIdx.x; idx < rows * a.n_in_p; idx += blockDim.x) {
-        const uint32_t k = idx / a.n_in_p, li = idx % a.n_in_p;
-        const uint32_t R = jp * a.rpp + k;
-        int v;
-        uint32_t pos;
-        if (li == 0) {
-            v = a.W[(size_t)R * a.n_in];
-            pos = k;
-        } else {
-            const uint32_t col = a.n_in_p - li;
-            if (col >= a.n_in) continue;
-            v = -(int)a.W[(size_t)R * a.n_in + col];
-            pos = li * a.rpp + k;
-        }
-        A[pos] = v >= 0 ? (uint32_t)v : K.q - (uint32_t)(-v);
+    fc_weight_poly(A, a.W, jp, N, a.n_in, a.n_in_p, a.n_out, a.rpp, 1u, K);
+    fc_bank_store(A, a.bank + (size_t)(jp * a.r.L + l) * N, a.r.logN, a.r.tw_fwd + (size_t)l * N, K);
+}
+
+// Bank of the masked FC step (Alg. 2), [P][2][L][N], every polynomial as
+// NTT(.) * N^-1.  mode 1 (server): u = 0 holds rho_j, u = 1 holds
+// -Delta_Q w_j.  mode 2 (client): u = 0 holds p1_j, u = 1 holds p2_j.
+struct PackFcMaskedArgs {
+    RingView r;
+    const int8_t *W;      // mode 1: [n_out][n_in]
+    const uint32_t *m0;   // mode 1: rho [P][N] (integers below t); mode 2: p1 [P][L][N] residues
+    const uint32_t *m1;   // mode 2: p2 [P][L][N] residues
+    uint32_t *bank;
+    uint32_t n_in, n_in_p, n_out, rpp, mode;
+};
+
+__global__ void __launch_bounds__(kThreads) k_pack_fc_masked(const PackFcMaskedArgs a) {
+    extern __shared__ uint4 smem4[];
+    uint32_t *A = reinterpret_cast<uint32_t *>(smem4);
+    const uint32_t jp = blockIdx.x, l = blockIdx.y, u = blockIdx.z;
+    const uint32_t N = a.r.N, L = a.r.L;
+    const LimbK K = a.r.limb[l];
+    if (a.mode == 1u && u == 1u) {
+        fc_weight_poly(A, a.W, jp, N, a.n_in, a.n_in_p, a.n_out, a.rpp, K.delta ? K.q - K.delta : 0u, K);
+    } else {
+        const uint32_t *src = a.mode == 1u ? a.m0 + (size_t)jp * N : (u ? a.m1 : a.m0) + (size_t)(jp * L + l) * N;
+        for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = __ldg(src + i);
+        __syncthreads();
+    }
+    fc_bank_store(A, a.bank + (size_t)((jp * 2u + u) * L + l) * N, a.r.logN, a.r.tw_fwd + (size_t)l * N, K);
+}
+
+// The masked FC step for weight block jp, limb l, ciphertext b (Alg. 2, the
+// server's or the client's evaluation line): with the two input
+// polynomials x_0, x_1 of column b ([B][2][L][N], NTT domain) and the bank's
+// pair of block jp,
+//   y = INTT(x_0 * bank_{jp,0} + x_1 * bank_{jp,1}),
+//   out = window(y) + bias (server) + Delta_Q sh'_{b,jp} (server),
+// the window keeping Theorem 1's coefficients k < rows_j.  Client: no bias
+// and no share (bias, shp null).
+__global__ void __launch_bounds__(kThreads) k_fc_masked(const ConvGeo a, const RingView r,
+                                                       const uint32_t *__restrict__ shp) {
+    extern __shared__ uint4 smem4[];
+    uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
+    const uint32_t jp = blockIdx.x, l = blockIdx.y, b = blockIdx.z;
+    const uint32_t N = a.N, L = a.L;
+    const LimbK K = r.limb[l];
+    const uint4 *X0 = reinterpret_cast<const uint4 *>(a.x + (size_t)((b * 2u) * L + l) * N);
+    const uint4 *X1 = reinterpret_cast<const uint4 *>(a.x + (size_t)((b * 2u + 1u) * L + l) * N);
+    const uint4 *W0 = reinterpret_cast<const uint4 *>(a.bank + (size_t)((jp * 2u) * L + l) * N);
+    const uint4 *W1 = reinterpret_cast<const uint4 *>(a.bank + (size_t)((jp * 2u + 1u) * L + l) * N);
+    for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) {
+        const uint4 x0 = __ldg(X0 + i), x1 = __ldg(X1 + i), w0 = __ldg(W0 + i), w1 = __ldg(W1 + i);
+        Y[pidx(4u * i)] = reduce64((uint64_t)x0.x * w0.x + (uint64_t)x1.x * w1.x, K);
+        Y[pidx(4u * i + 1u)] = reduce64((uint64_t)x0.y * w0.y + (uint64_t)x1.y * w1.y, K);
+        Y[pidx(4u * i + 2u)] = reduce64((uint64_t)x0.z * w0.z + (uint64_t)x1.z * w1.z, K);
+        Y[pidx(4u * i + 3u)] = reduce64((uint64_t)x0.w * w0.w + (uint64_t)x1.w * w1.w, K);
     }
     __syncthreads();
-    ntt_fwd_smem(A, a.r.logN, a.r.tw_fwd + (size_t)l * N, K.q);
-    uint32_t *dst = a.bank + (size_t)(jp * a.r.L + l) * N;
+    intt_c(Y, 1, padded_words(N), a.logN, a.tw_inv + (size_t)l * N, K.q);
+    const uint32_t rows = min(a.rpp, a.n_out - jp * a.rpp);
+    uint32_t *o = a.out + (size_t)((b * a.P + jp) * L + l) * N;
+    const uint32_t *sp = shp ? shp + (size_t)(b * a.P + jp) * N : nullptr;
     for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
-        const uint32_t x = red_4q(A[k], K.q2, K.q);
-        dst[k] = red_2q(shoup_lazy(x, K.ninv, K.ninvs, K.q), K.q);
+        uint32_t v = k < rows ? red_2q(Y[pidx(k)], K.q) : 0u;
+        if (k < rows && a.bias) {
+            v += __ldg(a.bias + (size_t)l * a.n_out + jp * a.rpp + k);
+            v = min(v, v - K.q);
+        }
+        if (sp) {
+            v += mulmod(__ldg(sp + k), K.delta, K);
+            v = min(v, v - K.q);
+        }
+        o[k] = v;
     }
 }
 
@@ -1302,6 +1391,44 @@ static ConvGeo geo_of(const RingView &r) {
     a.logN = r.logN;
     a.L = r.L;
     return a;
+}
+
+cudaError_t he_launch_pack_fc_masked(const RingView &r, const int8_t *d_W, const uint32_t *d_m0, const uint32_t *d_m1,
+                                     const he_fc_layout &fl, int mode, uint32_t *bank, cudaStream_t st) {
+    PackFcMaskedArgs a;
+    a.r = r;
+    a.W = d_W;
+    a.m0 = d_m0;
+    a.m1 = d_m1;
+    a.bank = bank;
+    a.n_in = fl.n_in;
+    a.n_in_p = fl.n_in_p;
+    a.n_out = fl.n_out;
+    a.rpp = fl.rows_per_poly;
+    a.mode = (uint32_t)mode;
+    const size_t smem = (size_t)r.N * 4u;
+    cudaError_t e = set_smem(k_pack_fc_masked, smem);
+    if (e != cudaSuccess) return e;
+    k_pack_fc_masked<<<dim3(fl.P_fc, r.L, 2), kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t he_launch_fc_masked(const RingView &r, const he_fc_layout &fl, const uint32_t *bank, const uint32_t *bias,
+                                const uint32_t *x_ntt, const uint32_t *shp, uint32_t *out, uint32_t B,
+                                cudaStream_t st) {
+    ConvGeo a = geo_of(r);
+    a.bank = bank;
+    a.bias = bias;
+    a.x = x_ntt;
+    a.out = out;
+    a.P = fl.P_fc;
+    a.rpp = fl.rows_per_poly;
+    a.n_out = fl.n_out;
+    const size_t smem = (size_t)padded_words(r.N) * 4u;
+    cudaError_t e = set_smem(k_fc_masked, smem);
+    if (e != cudaSuccess) return e;
+    k_fc_masked<<<dim3(fl.P_fc, r.L, B), kThreads, smem, st>>>(a, r, shp);
+    return cudaGetLastError();
 }
 
 cudaError_t he_launch_conv(const RingView &r, const he_conv_desc &d, const he_conv_layout &lay, uint32_t lt,

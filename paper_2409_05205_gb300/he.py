@@ -98,6 +98,10 @@ _SIGS = {
     "he_rescale": [_vp, _vp, _vp, _u32, _vp],
     "he_conv_client": [_vp, _vp, _vp, _vp, _vp, _u32, _vp],
     "he_pack_fc": [_vp, _u32, _u32, _vp, _vp, ctypes.POINTER(_vp)],
+    "he_pack_fc_masked": [_vp, _u32, _u32, _vp, _vp, _vp, ctypes.POINTER(_vp)],
+    "he_fc_layer_masked": [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _u32, _vp],
+    "he_pack_fc_client": [_vp, _u32, _u32, _vp, _vp, ctypes.POINTER(_vp)],
+    "he_fc_client": [_vp, _vp, _vp, _vp, _vp, _u32, _vp],
     "he_filters_destroy": [_vp],
     "he_conv_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
     "he_conv_layer_noalloc": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
@@ -302,6 +306,35 @@ def he_pack_fc(p: int, n_in: int, n_out: int, W: np.ndarray, bias: np.ndarray | 
     _check(lib().he_pack_fc(p, n_in, n_out, W.ctypes.data, None if b is None else b.ctypes.data,
                             ctypes.byref(out)))
     return out.value
+
+
+def he_pack_fc_masked(p: int, n_in: int, n_out: int, W: np.ndarray, bias: np.ndarray | None,
+                      rho: np.ndarray) -> int:
+    W = np.ascontiguousarray(W, dtype=np.int8)
+    assert W.shape == (n_out, n_in)
+    b = None if bias is None else np.ascontiguousarray(bias, dtype=np.int32)
+    rho = np.ascontiguousarray(rho, dtype=np.uint32)
+    out = _vp()
+    _check(lib().he_pack_fc_masked(p, n_in, n_out, W.ctypes.data, None if b is None else b.ctypes.data,
+                                   rho.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
+def he_fc_layer_masked(p: int, f: int, d_c0, d_sh, d_shp, in_domain: int, d_out, B: int, stream=None) -> None:
+    _check(lib().he_fc_layer_masked(p, f, _ptr(d_c0), _ptr(d_sh), _ptr(d_shp), in_domain, _ptr(d_out), B,
+                                    _stream(stream)))
+
+
+def he_pack_fc_client(p: int, n_in: int, n_out: int, p1: np.ndarray, p2: np.ndarray) -> int:
+    p1 = np.ascontiguousarray(p1, dtype=np.uint32)
+    p2 = np.ascontiguousarray(p2, dtype=np.uint32)
+    out = _vp()
+    _check(lib().he_pack_fc_client(p, n_in, n_out, p1.ctypes.data, p2.ctypes.data, ctypes.byref(out)))
+    return out.value
+
+
+def he_fc_client(p: int, f: int, d_v, d_ish, d_out, B: int, stream=None) -> None:
+    _check(lib().he_fc_client(p, f, _ptr(d_v), _ptr(d_ish), _ptr(d_out), B, _stream(stream)))
 
 
 def he_filters_destroy(f: int) -> None:
