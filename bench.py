@@ -542,6 +542,340 @@ def run_e2e(arm, args, stream):
 
 
 # ----------------------------------------------------------------------------
+# the masked protocol (Alg. 1 / Alg. 2): server step, client step, rescale
+# ----------------------------------------------------------------------------
+
+class MaskedArm:
+    """Per replica: the server banks (he_pack_masked / he_pack_fc_masked, masks
+    rho below t), the client banks (he_pack_client / he_pack_fc_client, p1 and
+    p2 uniform residues: their values do not change the work) and the
+    device-resident inputs and outputs of every layer's server step, client
+    step and rescale."""
+
+    def __init__(self, wl, device: int, replicas: int = 2):
+        import torch
+        from paper_2409_05205_gb300 import build
+        from paper_2409_05205_gb300 import he as H
+        from paper_2409_05205_gb300 import synth
+        build.build()
+        self.torch, self.H, self.wl = torch, H, wl
+        self.calls = synth.call_list(wl)
+        t = wl["t"]
+        self.params, primes = {}, {}
+        for c in self.calls:
+            key = (c["N"], c["L"])
+            if key not in self.params:
+                self.params[key] = H.he_params_create(c["N"], c["L"], None, t, device)
+                primes[key] = H.he_params_primes(self.params[key], c["L"])
+        self.geo, ws = [], {}
+        for c in self.calls:
+            p, N, L, B = self.params[(c["N"], c["L"])], c["N"], c["L"], c["B"]
+            if c["kind"] == "conv":
+                lay = H.he_conv_layout_query(p, c)
+                G, Hh = lay["G"], lay["H"]
+                g = dict(G=G, Hh=Hh, M=lay["M"], c0=(B, G, L, N), sh=(B, G, N), shp=(B, Hh, N), out=(B, Hh, L, N),
+                         rho=(c["co"], G, N), pp=(c["co"], G, L, N), bank=c["co"] * 2 * G * L * N * 4)
+            else:
+                fl = H.he_fc_layout_query(p, c["n_in"], c["n_out"])
+                P = fl["P_fc"]
+                g = dict(G=1, Hh=P, c0=(B, L, N), sh=(B, N), shp=(B, P, N), out=(B, P, L, N),
+                         rho=(P, N), pp=(P, L, N), bank=P * 2 * L * N * 4)
+            g["ws"] = B * 2 * g["G"] * L * N * 4
+            g["npoly_out"] = B * g["Hh"]
+            ws[(N, L)] = max(ws.get((N, L), 0), g["ws"])
+            self.geo.append(g)
+        for key, b in ws.items():
+            H.he_params_reserve(self.params[key], b)
+
+        def dev(a):
+            return torch.from_numpy(np.ascontiguousarray(a).view(np.int32).ravel()).cuda()
+
+        self.R = replicas
+        self.srv, self.cli, self.io = [], [], []
+        for r in range(replicas):
+            srv, cli, io = [], [], []
+            for i, (c, g) in enumerate(zip(self.calls, self.geo)):
+                p, ps = self.params[(c["N"], c["L"])], primes[(c["N"], c["L"])]
+                rho = synth.ints(SEED + r, f"rho{i}", g["rho"], 0, t - 1).astype(np.uint32)
+                p1 = synth.residues(SEED + r, f"p1_{i}", g["pp"], ps)
+                p2 = synth.residues(SEED + r, f"p2_{i}", g["pp"], ps)
+                if c["kind"] == "conv":
+                    F = synth.conv_weights(SEED + r, f"w{i}", c["co"], c["ci"], c["fh"], c["fw"], wl["wlo"], wl["whi"])
+                    srv.append(H.he_pack_masked(p, c, F, rho))
+                    cli.append(H.he_pack_client(p, c, p1, p2))
+                else:
+                    W = synth.fc_weights(SEED + r, f"w{i}", c["n_out"], c["n_in"], wl["wlo"], wl["whi"])
+                    srv.append(H.he_pack_fc_masked(p, c["n_in"], c["n_out"], W, None, rho))
+                    cli.append(H.he_pack_fc_client(p, c["n_in"], c["n_out"], p1, p2))
+                L, N = c["L"], c["N"]
+                o_l1 = (g["npoly_out"], L - 1, N)
+                io.append(dict(
+                    c0=dev(synth.residues(SEED + 10 * r, f"c0_{i}", g["c0"], ps)),
+                    sh=dev(synth.ints(SEED + 10 * r, f"sh{i}", g["sh"], 0, t - 1).astype(np.uint32)),
+                    shp=dev(synth.ints(SEED + 10 * r, f"shp{i}", g["shp"], 0, t - 1).astype(np.uint32)),
+                    v=dev(synth.ints(SEED + 10 * r, f"v{i}", g["sh"], -1, 1).astype(np.int32)),
+                    ish=dev(synth.ints(SEED + 10 * r, f"ish{i}", g["sh"], -8, t).astype(np.int32)),
+                    out=torch.empty(int(np.prod(g["out"])), dtype=torch.int32, device="cuda"),
+                    out1=torch.empty(int(np.prod(g["out"])), dtype=torch.int32, device="cuda"),
+                    outr=torch.empty(int(np.prod(o_l1)), dtype=torch.int32, device="cuda")))
+            self.srv.append(srv)
+            self.cli.append(cli)
+            self.io.append(io)
+        self.units = sum(c["B"] for c in self.calls)
+        torch.cuda.synchronize()
+
+    def server(self, r, stream, evs=None):
+        H = self.H
+        for i, c in enumerate(self.calls):
+            p, x = self.params[(c["N"], c["L"])], self.io[r][i]
+            if evs is not None:
+                evs[i][0].record(stream)
+            f = H.he_conv_layer_masked if c["kind"] == "conv" else H.he_fc_layer_masked
+            f(p, self.srv[r][i], x["c0"], x["sh"], x["shp"], H.HE_COEFF, x["out"], c["B"], stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    def client(self, r, stream):
+        H = self.H
+        for i, c in enumerate(self.calls):
+            p, x = self.params[(c["N"], c["L"])], self.io[r][i]
+            f = H.he_conv_client if c["kind"] == "conv" else H.he_fc_client
+            f(p, self.cli[r][i], x["v"], x["ish"], x["out1"], c["B"], stream)
+
+    def rescale(self, r, stream):
+        for i, (c, g) in enumerate(zip(self.calls, self.geo)):
+            x = self.io[r][i]
+            self.H.he_rescale(self.params[(c["N"], c["L"])], x["out"], x["outr"], g["npoly_out"], stream)
+
+    def make_plans(self):
+        """Per replica: one plan over every layer's masked server call, one over
+        every layer's client call."""
+        H = self.H
+        self.srv_plans, self.cli_plans = [], []
+        for r in range(self.R):
+            sc, cc = [], []
+            for i, c in enumerate(self.calls):
+                x = self.io[r][i]
+                sc.append((self.srv[r][i], x["c0"], H.HE_COEFF, x["out"], c["B"], x["sh"], x["shp"]))
+                cc.append((self.cli[r][i], x["v"], H.HE_COEFF, x["out1"], c["B"], x["ish"]))
+            self.srv_plans.append(H.he_plan_create(sc))
+            self.cli_plans.append(H.he_plan_create(cc))
+
+    def server_plan(self, r, stream):
+        self.H.he_plan_run(self.srv_plans[r], stream)
+
+    def client_plan(self, r, stream):
+        self.H.he_plan_run(self.cli_plans[r], stream)
+
+    def mac_bytes(self, form):
+        """Algorithmic bytes of one k_plan_mac launch of the server plan: for
+        every split-form Conv call, its masked bank (co * 2G * L * N words) and
+        its transformed inputs (2G * L * N words per ciphertext) read once, its
+        folded channel sums (L * co * N/s words per ciphertext) written once."""
+        tot = 0
+        for c, g, f in zip(self.calls, self.geo, form):
+            if f == 1 and c["kind"] == "conv":
+                L, N, B = c["L"], c["N"], c["B"]
+                tot += g["bank"] + B * 2 * g["G"] * L * N * 4 + B * L * c["co"] * g["M"] * 4
+        return tot
+
+    def server_bytes(self, conv_only=False):
+        """Algorithmic bytes of one server step: c0, sh, sh' and the bank read
+        once, c0^r written once (per layer call)."""
+        tot = 0
+        for c, g in zip(self.calls, self.geo):
+            if conv_only and c["kind"] != "conv":
+                continue
+            tot += g["bank"] + 4 * (int(np.prod(g["c0"])) + int(np.prod(g["sh"])) + int(np.prod(g["shp"]))
+                                    + int(np.prod(g["out"])))
+        return tot
+
+    def rescale_bytes(self):
+        """Per step: every c0^r word read (L limbs), L - 1 limbs written."""
+        return sum(g["npoly_out"] * (2 * c["L"] - 1) * c["N"] * 4 for c, g in zip(self.calls, self.geo))
+
+    def capture(self, fn):
+        torch = self.torch
+        s = torch.cuda.Stream()
+        graphs = []
+        for r in range(self.R):
+            with torch.cuda.stream(s):
+                fn(r, s)                      # warm-up outside capture
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                fn(r, s)
+            graphs.append(g)
+        torch.cuda.synchronize()
+        return graphs
+
+    def free(self):
+        for pl in getattr(self, "srv_plans", []) + getattr(self, "cli_plans", []):
+            self.H.he_plan_destroy(pl)
+        for banks in self.srv + self.cli:
+            for f in banks:
+                self.H.he_filters_destroy(f)
+        for p in self.params.values():
+            self.H.he_params_destroy(p)
+
+
+def _replay_rate(torch, graphs, stream, K, W):
+    """K replays (replicas rotated) after W warm-up ones, CUDA events on the
+    stream; returns the total ms and per-replay ms of a separate run."""
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            graphs[k % len(graphs)].replay()
+    torch.cuda.synchronize()
+    t0, t1 = _events(2)
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for k in range(K):
+            graphs[k % len(graphs)].replay()
+        t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1)
+
+
+def run_masked(args, rank, world, device):
+    import torch
+    wl = workload(args.workload)
+    arm = MaskedArm(wl, device)
+    H = arm.H
+    nl = len(arm.calls)
+    stream = torch.cuda.Stream()
+    K, W = args.steps, args.warmup
+    hbm, peak_src = _peaks()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # single-call form: the masked entry points one layer at a time (a CUDA
+    # graph of the 20 calls), for comparison with the plan
+    k2 = min(K, 2000)
+    g_single = arm.capture(arm.server)
+    single_ms = _replay_rate(torch, g_single, stream, k2, W)
+
+    # plans: server and client steps, each one graph replay per step
+    arm.make_plans()
+    info = H.he_plan_query(arm.srv_plans[0], nl)
+    g_srv, g_cli, g_rs = arm.capture(arm.server_plan), arm.capture(arm.client_plan), arm.capture(arm.rescale)
+    barrier()
+    clocks = ClockSampler(device)
+    clocks.start()
+    time.sleep(0.3)
+    srv_ms = _replay_rate(torch, g_srv, stream, K, W)
+    clk = clocks.stop()
+    barrier()
+    k_lat = min(K, 2000)
+    with torch.cuda.stream(stream):
+        ev = [_events(2) for _ in range(k_lat)]
+        for k in range(k_lat):
+            ev[k][0].record(stream)
+            g_srv[k % arm.R].replay()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    lat = [a.elapsed_time(b) for a, b in ev]
+    cli_ms = _replay_rate(torch, g_cli, stream, k2, W)
+    rs_ms = _replay_rate(torch, g_rs, stream, k2, W)
+    # the MAC kernel of the server plan alone, back to back over the replicas
+    k_phase = min(K, 500)
+    m0, m1 = _events(2)
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            H.he_plan_run(arm.srv_plans[k % arm.R], stream)
+        for k in range(W):
+            H.he_plan_run_phase(arm.srv_plans[k % arm.R], H.HE_PHASE_MAC, stream)
+        m0.record(stream)
+        for k in range(k_phase):
+            H.he_plan_run_phase(arm.srv_plans[k % arm.R], H.HE_PHASE_MAC, stream)
+        m1.record(stream)
+    torch.cuda.synchronize()
+    mac_ms = m0.elapsed_time(m1) / k_phase
+    if world > 1:
+        srv_ms, = max_over_ranks([srv_ms], "cuda")
+
+    # e2e: per step H2D of every layer's c0, sh and sh' from pinned host
+    # memory, the server plan (graph), D2H of every c0^r
+    keys = ("c0", "sh", "shp")
+    hx = [{k: torch.empty_like(x[k], device="cpu").pin_memory() for k in keys} for x in arm.io[0]]
+    hy = [torch.empty_like(x["out"], device="cpu").pin_memory() for x in arm.io[0]]
+    for i, x in enumerate(arm.io[0]):
+        for k in keys:
+            hx[i][k].copy_(x[k].cpu())
+    h2d = sum(hx[i][k].numel() * 4 for i in range(nl) for k in keys)
+    d2h = sum(y.numel() * 4 for y in hy)
+
+    def e2e_step(r):
+        for i, x in enumerate(arm.io[r]):
+            for k in keys:
+                x[k].copy_(hx[i][k], non_blocking=True)
+        g_srv[r].replay()
+        for i, x in enumerate(arm.io[r]):
+            hy[i].copy_(x["out"], non_blocking=True)
+
+    with torch.cuda.stream(stream):
+        for k in range(3):
+            e2e_step(k % arm.R)
+    torch.cuda.synchronize()
+    ke = max(20, min(K, 2000))
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(ke):
+            e2e_step(k % arm.R)
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+
+    mac_bytes = arm.mac_bytes(info["form"])
+    mac_gbs = mac_bytes / (mac_ms * 1e-3) / 1e9
+    rs_bytes = arm.rescale_bytes()
+    rs_gbs = rs_bytes / (rs_ms / k2 * 1e-3) / 1e9
+    step_bytes = arm.server_bytes()
+    res = {
+        "metric": METRIC, "value": whole_job_rate(arm.units, K, world, srv_ms), "unit": "layers/s",
+        "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": srv_ms / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u32 (exact residues mod 30-bit primes)", "data": "synthetic",
+        "config": {"workload": wl["name"], **Arm.describe(arm),
+                   "form": f"masked server step of Alg. 1 / Alg. 2 for every layer: one plan of {nl} calls "
+                           f"({info['kernels_per_run']} kernels) replayed as a CUDA graph",
+                   "l2": f"rotates {arm.R} model replicas + input sets (masked banks > 2x L2); no flush",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "steps": k_lat, "how": "CUDA events around each server-plan graph replay"},
+        "single_call_form": {"value": arm.units * k2 / (single_ms * 1e-3), "unit": "layers/s", "steps": k2,
+                             "ms_per_step": single_ms / k2,
+                             "what": "he_conv_layer_masked / he_fc_layer_masked per layer, the 20 calls "
+                                     "captured as a CUDA graph"},
+        "client_step": {"value": arm.units * k2 / (cli_ms * 1e-3), "unit": "layers/s", "steps": k2,
+                        "ms_per_step": cli_ms / k2,
+                        "what": "c1^r = extract(sum -v p1 + (i + sh) p2) of every layer: one plan of the "
+                                "client calls, a CUDA graph per step"},
+        "rescale": {"value": arm.units * k2 / (rs_ms * 1e-3), "unit": "layers/s", "steps": k2,
+                    "ms_per_step": rs_ms / k2, "bytes_per_step": rs_bytes, "achieved_gbs": rs_gbs,
+                    "frac": rs_gbs / hbm,
+                    "what": f"k_rescale of every c0^r from {arm.calls[0]['L']} to {arm.calls[0]['L'] - 1} limbs "
+                            f"({nl} launches per step in a CUDA graph; L limbs read, L - 1 written)"},
+        "roofline": {"kernel": "k_plan_mac: one-column masked channel MAC of every Conv layer (masked banks "
+                               "+ transformed c0 and sh read once, folded sums written once)",
+                     "bound": "hbm", "achieved": mac_gbs, "peak": hbm, "unit": "GB/s", "frac": mac_gbs / hbm,
+                     "peak_source": peak_src + " (hbm_gbs burst copy)", "algorithmic_bytes": mac_bytes,
+                     "avg_launch_ms": mac_ms, "launches": k_phase, "traffic": None},
+        "kernels": {"step_bytes": step_bytes, "step_gbs_graph": step_bytes / (srv_ms / K * 1e-3) / 1e9},
+        "plan": {k: v for k, v in info.items() if k not in ("split", "form")},
+        "e2e": {"value": arm.units * ke / e2e_dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": ke,
+                "how": "per step: H2D of every layer's c0, sh and sh' from pinned host memory, the server "
+                       "plan (CUDA graph), D2H of every c0^r; one stream, wall clock"},
+        "gpu_launches": info["kernels_per_run"] * K,
+        "clocks": clk,
+    }
+    arm.free()
+    return res
+
+
+# ----------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # ----------------------------------------------------------------------------
 
@@ -562,7 +896,25 @@ def oracle_layers_per_s(wl, budget_s: float, max_calls: int | None = None, start
             ps = O.select_primes(N, L)
             rings[(N, L)] = (ps, [O.root_2n(q, N) for q in ps])
         ps, psis = rings[(N, L)]
-        if c["kind"] == "conv":
+        t = wl["t"]
+        if wl.get("masked") and c["kind"] == "conv":
+            lay = O.conv_layout(N, c["ci"], c["co"], c["h"], c["w"], c["fh"], c["fw"], c["pad"])
+            G, Hh = lay["G"], lay["H"]
+            F = synth.conv_weights(SEED, f"cpuw{done}", c["co"], c["ci"], c["fh"], c["fw"], wl["wlo"], wl["whi"])
+            O.conv_layer_masked(synth.residues(SEED, f"cpu{done}", (B, G, L, N), ps),
+                                synth.ints(SEED, f"cpush{done}", (B, G, N), 0, t - 1),
+                                synth.ints(SEED, f"cpurho{done}", (c["co"], G, N), 0, t - 1), F,
+                                synth.ints(SEED, f"cpushp{done}", (B, Hh, N), 0, t - 1), ps, psis, t, lay,
+                                tier="ntt")
+        elif wl.get("masked"):
+            fl = O.fc_layout(N, c["n_in"], c["n_out"])
+            W = synth.fc_weights(SEED, f"cpuw{done}", c["n_out"], c["n_in"], wl["wlo"], wl["whi"])
+            O.fc_layer_masked(synth.residues(SEED, f"cpu{done}", (B, L, N), ps),
+                              synth.ints(SEED, f"cpush{done}", (B, N), 0, t - 1),
+                              synth.ints(SEED, f"cpurho{done}", (fl["P"], N), 0, t - 1), W, None,
+                              synth.ints(SEED, f"cpushp{done}", (B, fl["P"], N), 0, t - 1), ps, psis, t, fl,
+                              tier="ntt")
+        elif c["kind"] == "conv":
             lay = O.conv_layout(N, c["ci"], c["co"], c["h"], c["w"], c["fh"], c["fw"], c["pad"])
             cts = synth.residues(SEED, f"cpu{done}", (B, lay["G"], 2, L, N), ps)
             F = synth.conv_weights(SEED, f"cpuw{done}", c["co"], c["ci"], c["fh"], c["fw"], wl["wlo"], wl["whi"])
@@ -824,7 +1176,8 @@ def main():
         if rank == 0:
             print(json.dumps(res))
         return
-    res = run_ours(args, rank, world, local)
+    wl = workload(args.workload)
+    res = (run_masked if wl.get("masked") else run_ours)(args, rank, world, local)
     if rank == 0:
         if not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(workload(args.workload))

@@ -362,12 +362,16 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
  * A plan fixes a list of Conv / FC layer calls (any mix of ring degrees,
  * limb counts, shapes and batch sizes whose params live on one device) and
  * their buffers.  Each call computes the words that he_conv_layer /
- * he_fc_layer with HE_OUT_EXTRACTED would write.  he_plan_run issues, in
- * order on `stream`:
+ * he_fc_layer with HE_OUT_EXTRACTED would write, or, for a masked or client
+ * bank, the words of he_conv_layer_masked / he_fc_layer_masked /
+ * he_conv_client / he_fc_client (a masked or client Conv call needs B = 1
+ * and the split form below, or an even B).  he_plan_run issues, in order
+ * on `stream`:
  *   1. one kernel computing every coefficient-domain input NTT of every
- *      Conv call;
+ *      Conv call (for masked and client calls: of both input sources);
  *   2. for the Conv calls in the split form (B = 1, interleave s >= 4, G in
- *      {1, 2, 4}): a persistent kernel that streams each slot tile's
+ *      {1, 2, 4}, or 2G in {2, 4, 8} for masked and client banks): a
+ *      persistent kernel that streams each slot tile's
  *      weights for every output channel into shared memory with bulk copies
  *      and stores the folded channel sums (Sec. III-A, valid slots only) in
  *      the plan's workspace, then a kernel that runs the length-N/s inverse
@@ -386,11 +390,16 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
 typedef struct he_plan_s *he_plan_t;
 
 typedef struct {
-    he_filters_t filters;   /* a Conv bank (he_pack_filters) or FC bank (he_pack_fc) */
-    const uint32_t *d_in;   /* DEVICE input, the layout of he_conv_layer / he_fc_layer */
-    int in_domain;          /* HE_COEFF or HE_NTT */
-    uint32_t *d_out;        /* DEVICE output, the HE_OUT_EXTRACTED layout */
+    he_filters_t filters;   /* a Conv or FC bank: ordinary, masked (server) or client */
+    const uint32_t *d_in;   /* DEVICE input, the layout of he_conv_layer / he_fc_layer;
+                               masked banks: c0 (he_conv_layer_masked / he_fc_layer_masked);
+                               client banks: v (int32, he_conv_client / he_fc_client) */
+    int in_domain;          /* HE_COEFF or HE_NTT (client banks: HE_COEFF) */
+    uint32_t *d_out;        /* DEVICE output, the HE_OUT_EXTRACTED layout, or the masked
+                               entry points' output layout */
     uint32_t B;             /* ciphertexts in this call, >= 1 */
+    const uint32_t *d_share;     /* masked banks: sh; client banks: i + sh (int32); else NULL */
+    const uint32_t *d_share_out; /* masked banks: sh'; else NULL */
 } he_layer_call;
 
 /* Validates every call (shapes, alignment, one device, no output overlapping

@@ -1039,8 +1039,14 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         const he_layer_call &c = calls[i];
         const he_filters_s *f = c.filters;
         if (!f || !c.d_in || !c.d_out) return fail(HE_ERR_ARG, "call %u: NULL argument", i);
-        if (f->masked)
-            return fail(HE_ERR_UNSUPPORTED, "call %u: masked banks run through the masked entry points", i);
+        // 0: ciphertext x plaintext; 1: masked server step; 2: client step (Alg. 1 / Alg. 2)
+        const uint32_t msrc = f->masked;
+        if (msrc == 1 && (!c.d_share || !c.d_share_out))
+            return fail(HE_ERR_ARG, "call %u: a masked bank needs d_share (sh) and d_share_out (sh')", i);
+        if (msrc == 2 && !c.d_share) return fail(HE_ERR_ARG, "call %u: a client bank needs d_share (i + sh)", i);
+        if (msrc == 2 && c.in_domain != HE_COEFF)
+            return fail(HE_ERR_ARG, "call %u: client inputs are coefficient-domain integers (HE_COEFF)", i);
+        if (msrc && !aligned16(c.d_share)) return fail(HE_ERR_ARG, "call %u: d_share must be 16-byte aligned", i);
         const he_params_s *p = f->p;
         if (p->device != device) return fail(HE_ERR_ARG, "call %u: params on another device", i);
         if (c.B == 0) return fail(HE_ERR_ARG, "call %u: B must be >= 1", i);
@@ -1057,17 +1063,22 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         g.N = r.N;
         g.logN = r.logN;
         g.L = r.L;
-        g.ncols = 2u * c.B;
+        g.ncols = msrc ? c.B : 2u * c.B;  // masked and client steps: one column per ciphertext
         g.mode = HE_OUT_EXTRACTED;
+        g.masked = msrc ? 1u : 0u;
+        g.shp = msrc == 1 ? c.d_share_out : nullptr;
+        cd.msrc = msrc;
+        cd.src_b = msrc ? c.d_share : nullptr;
+        cd.a_ntt = msrc == 1 && c.in_domain == HE_NTT ? 1u : 0u;
         cd.tw_fwd = r.tw_fwd;
         for (uint32_t l = 0; l < r.L; ++l) cd.limb[l] = r.limb[l];
-        size_t nin, nout;
+        size_t nin, nout, nsh = 0, nshp = 0;
         if (f->kind == HE_KIND_CONV) {
             const he_conv_layout &lay = f->lay;
             if (fold_smem_bytes(2, lay.M) > 192u * 1024u)
                 return fail(HE_ERR_UNSUPPORTED, "call %u: N/s = %u too long for a plan", i, lay.M);
             cd.kind = HE_KIND_CONV;
-            g.G = lay.G;
+            g.G = msrc ? 2u * lay.G : lay.G;  // groups the channel sum runs over
             g.H = lay.H;
             g.s = lay.s;
             g.logs = he_ilog2(lay.s);
@@ -1079,15 +1090,19 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             g.lcs = f->lcs;
             cd.nj = std::min(he_conv_nj(g.ncols, lay.M, lay.s), tu.fused_max_nj);
             cd.nb = lay.s >= 4 ? 1 : (lay.s == 2 ? 2 : 4);
-            cd.cpt = he_conv_cpt(cd.nj, cd.nb, lay.G);
-            // split form for one ciphertext per call with s >= 4 and G in
-            // {1, 2, 4} whose output polynomials fit shared memory
-            cd.split = (tu.split && c.B == 1 && split_mac_ok(lay.s, lay.G) &&
+            cd.cpt = he_conv_cpt(cd.nj, cd.nb, g.G);
+            // split form for one ciphertext per call with s >= 4, G in
+            // {1, 2, 4} (2G in {2, 4, 8} for the one-column masked and client
+            // steps) whose inputs fit one MAC input buffer and whose output
+            // polynomials fit shared memory
+            const uint32_t ncol = msrc ? 1u : 2u;
+            cd.split = (tu.split && c.B == 1 && split_mac_ok(lay.s, g.G) &&
+                        ((ncol * g.G) << f->logTS) <= kMacXWords &&
                         (size_t)std::min(lay.s, f->desc.co) * fin_stride(lay.M) * 4u <= 200u * 1024u)
                            ? 1u
                            : 0u;
-            g.cs = split_cs(lay.s, lay.G);
-            g.nc = std::min(f->desc.co, std::max(1u, (tu.mac_item_kb * 256u) / (lay.G << f->logTS)));
+            g.cs = split_cs(lay.s, g.G);
+            g.nc = std::min(f->desc.co, std::max(1u, (tu.mac_item_kb * 256u) / (g.G << f->logTS)));
             // bank interleave and tile must match the MAC kernel's
             if (cd.split && ((1u << f->lcs) != g.cs || f->logTS != split_tile_log(f->lcs))) cd.split = 0;
             // a tensor-core bank: the tensor-core MAC kernel for up to 16
@@ -1097,8 +1112,15 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
                 cd.split = 0;
                 cd.zt = g.ncols <= kTcCols ? 1u : 0u;
             }
-            nin = (size_t)c.B * lay.G * 2u * r.L * r.N;
-            nout = (size_t)c.B * lay.H * 2u * r.L * r.N;
+            // the fused form covers columns in tiles of nj >= 2 (plain calls have 2B columns)
+            if (msrc && !cd.split && (g.ncols % cd.nj) != 0)
+                return fail(HE_ERR_UNSUPPORTED,
+                            "call %u: a masked or client Conv call in a plan needs B = 1 in the split form or an even B", i);
+            nin = msrc == 2 ? (size_t)c.B * lay.G * r.N
+                            : (size_t)c.B * lay.G * (msrc ? 1u : 2u) * r.L * r.N;
+            nsh = (size_t)c.B * lay.G * r.N;
+            nshp = (size_t)c.B * lay.H * r.N;
+            nout = (size_t)c.B * lay.H * (msrc ? 1u : 2u) * r.L * r.N;
         } else {
             cd.kind = HE_KIND_FC;
             g.bias = f->bias;
@@ -1106,10 +1128,24 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             g.rpp = f->fl.rows_per_poly;
             g.n_out = f->fl.n_out;
             cd.nj = 2;
-            nin = (size_t)c.B * 2u * r.L * r.N;
-            nout = (size_t)c.B * f->fl.P_fc * 2u * r.L * r.N;
+            if (msrc && 2u * padded_words(r.N) * 4u > 227u * 1024u)
+                return fail(HE_ERR_UNSUPPORTED, "call %u: N = %u too long for a masked FC item", i, r.N);
+            nin = msrc == 2 ? (size_t)c.B * r.N : (size_t)c.B * (msrc ? 1u : 2u) * r.L * r.N;
+            nsh = (size_t)c.B * r.N;
+            nshp = (size_t)c.B * f->fl.P_fc * r.N;
+            nout = (size_t)c.B * f->fl.P_fc * (msrc ? 1u : 2u) * r.L * r.N;
         }
-        if (c.in_domain == HE_COEFF) {
+        if (msrc) {
+            // both input sources are staged by the input-transform kernel
+            // (Conv) or transformed inside the FC item
+            cd.x_coeff = c.d_in;
+            if (cd.kind == HE_KIND_CONV) {
+                ws_off[i] = ws_words;
+                ws_words += (size_t)c.B * g.G * r.L * r.N;
+            }
+            ranges.push_back({(uintptr_t)c.d_share, (uintptr_t)(c.d_share + nsh), false, i});
+            if (msrc == 1) ranges.push_back({(uintptr_t)c.d_share_out, (uintptr_t)(c.d_share_out + nshp), false, i});
+        } else if (c.in_domain == HE_COEFF) {
             cd.x_coeff = c.d_in;
             if (cd.kind == HE_KIND_CONV) {  // FC items transform their input in shared memory
                 ws_off[i] = ws_words;
@@ -1178,7 +1214,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         }
         if (cd.x_coeff) {
             g.x = pl->ws + ws_off[i];
-            const size_t npoly = (size_t)calls[i].B * g.G * 2u * g.L;
+            const size_t npoly = (size_t)calls[i].B * g.G * (cd.msrc ? 1u : 2u) * g.L;
             for (size_t pidx_ = 0; pidx_ < npoly; ++pidx_) ntt_cost.push_back({N * logN, NttItem{i, (uint32_t)pidx_}});
         }
         if (cd.zt) {
@@ -1220,7 +1256,8 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
     std::stable_sort(fc_cost.begin(), fc_cost.end(), by_cost);
     for (auto &it : fc_cost) {
         fcs.push_back(it.second);
-        pl->smem_fc = std::max(pl->smem_fc, (size_t)padded_words(descs[it.second.call].g.N) * 4u);
+        const CallDesc &cd = descs[it.second.call];
+        pl->smem_fc = std::max(pl->smem_fc, (size_t)padded_words(cd.g.N) * 4u * (cd.msrc ? 2u : 1u));
     }
     pl->n_fc = (uint32_t)fcs.size();
     auto upload = [&](ChanItem **dst, const std::vector<ChanItem> &v) -> cudaError_t {
@@ -1296,11 +1333,14 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             c.x = g.x + (size_t)it.l * g.N + ((size_t)it.a << lt);
             c.nwords = (nc * g.G) << lt;
             c.xstride = g.L * g.N;
-            c.xrows = 2 * g.G;
+            c.ncol = cd.msrc ? 1u : 2u;
+            c.xrows = c.ncol * g.G;
             c.xwords = 1u << lt;
+            c.pad = 0;
             copies.push_back(c);
             MacDesc d{};
-            d.z = cd.z + ((size_t)it.l * 2u * g.co + it.b) * g.M + (((size_t)it.a << lt) >> g.logs);
+            d.ncol = c.ncol;
+            d.z = cd.z + ((size_t)it.l * g.ncols * g.co + it.b) * g.M + (((size_t)it.a << lt) >> g.logs);
             d.colstride = g.co * g.M;
             d.M = g.M;
             d.nch = nc;

@@ -104,13 +104,13 @@ __host__ __device__ __forceinline__ size_t bank_index(uint32_t n, uint32_t l, ui
 // a channel's products per column are at most 16.  Other layers use a
 // 512-slot tile.
 __host__ __device__ __forceinline__ uint32_t split_cs(uint32_t s, uint32_t G) {
-    const uint32_t a = 4u / G, b = s / 4u;
+    const uint32_t a = G >= 4 ? 1u : 4u / G, b = s / 4u;
     return a < b ? a : b;
 }
 // The s-slot block of one output value must lie within one warp's lanes
 // (s / (4 CS) <= 32) for the block sum.
 __host__ __device__ __forceinline__ bool split_mac_ok(uint32_t s, uint32_t G) {
-    return s >= 4 && (G == 1 || G == 2 || G == 4) && s <= 128u * split_cs(s, G);
+    return s >= 4 && (G == 1 || G == 2 || G == 4 || G == 8) && s <= 128u * split_cs(s, G);
 }
 // log2 of the chunk interleave of a bank: log2(split_cs) for split layers,
 // else 0 (no interleave); never more than the tile allows
@@ -181,22 +181,25 @@ struct TcItem {
 // One layer call inside a plan (device-resident table).
 struct CallDesc {
     ConvGeo g;
-    const uint32_t *x_coeff;  // coefficient-domain input (nullptr when the call's input is in NTT form)
+    const uint32_t *x_coeff;  // coefficient-domain input (nullptr when the call's input is in NTT form);
+                              // masked server calls: c0 in either domain (a_ntt); client calls: v (int32)
     const uint2 *tw_fwd;      // [L][N]
-    uint32_t *z;              // split form: folded channel sums [L][2B][co][M]
+    uint32_t *z;              // split form: folded channel sums [L][ncols][co][M]
+    const uint32_t *src_b;    // masked server calls: sh [B][G][N]; client calls: i + sh (int32 [B][G][N])
     uint32_t kind, nj, nb, cpt;
     uint32_t split;           // 1: MAC kernel + finishing kernel; 0: one fused channel kernel
     uint32_t zt;              // z is channel-fastest, [L][2B][M][co] (tensor-core MAC kernel)
-    uint32_t pad[2];
+    uint32_t msrc;            // 0: ciphertext x plaintext; 1: masked server step; 2: client step (Alg. 1 / 2)
+    uint32_t a_ntt;           // masked server calls: c0 is already in the NTT domain
     LimbK limb[HE_MAX_LIMBS];
 };
 
-// split MAC kernel classes by (G, CS): (1,1) (1,2) (1,4) (2,1) (2,2) (4,1)
-constexpr int kMacClasses = 6;
+// split MAC kernel classes by (G, CS): (1,1) (1,2) (1,4) (2,1) (2,2) (4,1) (8,1)
+constexpr int kMacClasses = 7;
 __host__ __device__ __forceinline__ int he_mac_class(uint32_t G, uint32_t cs) {
     if (G == 1) return cs == 1 ? 0 : (cs == 2 ? 1 : 2);
     if (G == 2) return cs == 1 ? 3 : 4;
-    return 5;
+    return G == 4 ? 5 : 6;
 }
 
 // split form: bulk-copy ring of the MAC kernel
@@ -219,8 +222,10 @@ struct MacCopy {
     const uint32_t *x;       // input row (g = 0, column 0); row (g, jj) at x + (2g + jj) * xstride
     uint32_t nwords;         // weight words
     uint32_t xstride;        // words between input rows
-    uint32_t xrows;          // 2 * G
+    uint32_t xrows;          // input rows: 2 * G (two columns), or G (one column, ncol = 1)
     uint32_t xwords;         // words per input row (TS)
+    uint32_t ncol;           // 2: columns c0, c1 of one ciphertext; 1: one column (masked and client steps)
+    uint32_t pad;
 };
 
 // What the compute warps need about one MAC item, built on the host and
@@ -234,7 +239,8 @@ struct alignas(16) MacDesc {
     uint32_t logs;           // log2 s
     uint32_t nst;            // weight stages of the item
     uint32_t q, q2, r32, r32s, ones;  // limb constants
-    uint32_t pad[3];
+    uint32_t ncol;           // columns whose sums are stored (1 or 2)
+    uint32_t pad[2];
 };
 static_assert(sizeof(MacDesc) == 64, "MacDesc is one 64-byte bulk copy");
 
@@ -774,8 +780,9 @@ struct InvStageC<K, LO, LOG, K> {
 };
 
 // Forward pass PASS of a length-2^LOG transform.  The first pass reads the
-// global source, the last one reduces to [0, q) and writes the global
-// destination (2^K consecutive words per group, 128-bit stores).
+// global source (or, with src null, the padded shared buffer), the last one
+// reduces to [0, q) and writes the global destination (2^K consecutive words
+// per group, 128-bit stores), or the shared buffer with dst null.
 template <int LOG, int PASS>
 struct FwdPassC {
     using Plan = PassPlan<LOG, false>;
@@ -791,7 +798,7 @@ struct FwdPassC {
             uint32_t v[1 << K];
 #pragma unroll
             for (int r = 0; r < (1 << K); ++r)
-                v[r] = kFirst ? __ldg(src + base + ((uint32_t)r << LO)) : sm[pb + sm_off<LO>(r)];
+                v[r] = kFirst && src ? __ldg(src + base + ((uint32_t)r << LO)) : sm[pb + sm_off<LO>(r)];
             FwdStageC<K, LO, LOG, 0>::run(v, base, tw, q, q2);
             if (kLast) {
 #pragma unroll

@@ -475,6 +475,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_ntt_masked_in(const RingView r,
     ntt_body(src, dst, r.logN, r.tw_fwd + (size_t)l * N, r.limb[l], false, smem4);
 }
 
+// x (or -x when neg) mod q for |x| < q.
+__device__ __forceinline__ uint32_t small_residue(int32_t x, bool neg, uint32_t q) {
+    const int32_t y = neg ? -x : x;
+    return y < 0 ? (uint32_t)(y + (int32_t)q) : (uint32_t)y;
+}
+
 // Inputs of the client step of Alg. 1 into the workspace [B][2G][L][N] as
 // residues: groups g < G hold -v_g, groups G + g hold (i + sh)_g; both are
 // small signed integers, the same in every limb.  The NTT follows in place.
@@ -487,12 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_client_in(const RingView r, const 
     const int32_t *src = gz < G ? v + (size_t)(b * G + gz) * N : ish + (size_t)(b * G + gz - G) * N;
     const bool neg = gz < G;
     uint32_t *dst = ws + (size_t)P * N;
-    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
-        int64_t x = __ldg(src + i);
-        if (neg) x = -x;
-        x %= (int64_t)q;
-        dst[i] = (uint32_t)(x < 0 ? x + q : x);
-    }
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) dst[i] = small_residue(__ldg(src + i), neg, q);
 }
 
 // RNS rescale by the last prime with rounding: X' = floor((X + h) / q_L),
@@ -692,16 +693,36 @@ __global__ void __launch_bounds__(kThreads) k_pack_fc_masked(const PackFcMaskedA
     fc_bank_store(A, a.bank + (size_t)((jp * 2u + u) * L + l) * N, a.r.logN, a.r.tw_fwd + (size_t)l * N, K);
 }
 
-// The masked FC step for weight block jp, limb l, ciphertext b (Alg. 2, the
-// server's or the client's evaluation line): with the two input
-// polynomials x_0, x_1 of column b ([B][2][L][N], NTT domain) and the bank's
-// pair of block jp,
-//   y = INTT(x_0 * bank_{jp,0} + x_1 * bank_{jp,1}),
-//   out = window(y) + bias (server) + Delta_Q sh'_{b,jp} (server),
-// the window keeping Theorem 1's coefficients k < rows_j.  Client: no bias
-// and no share (bias, shp null).
-__global__ void __launch_bounds__(kThreads) k_fc_masked(const ConvGeo a, const RingView r,
-                                                       const uint32_t *__restrict__ shp) {
+// The inverse transform and output window of the masked FC step (Alg. 2)
+// for weight block jp, limb l, ciphertext b, from Y = x_0 * bank_{jp,0} +
+// x_1 * bank_{jp,1} (NTT domain, padded layout in shared memory):
+//   out = window(INTT(Y)) + bias (server) + Delta_Q sh'_{b,jp} (server),
+// the window keeping Theorem 1's coefficients k < rows_j; the client's
+// calls have no bias and no share (bias, shp null).
+__device__ __forceinline__ void fc_masked_out(const ConvGeo &a, const LimbK &K, uint32_t jp, uint32_t l, uint32_t b,
+                                              uint32_t *Y) {
+    const uint32_t N = a.N, L = a.L;
+    intt_c(Y, 1, padded_words(N), a.logN, a.tw_inv + (size_t)l * N, K.q);
+    const uint32_t rows = min(a.rpp, a.n_out - jp * a.rpp);
+    uint32_t *o = a.out + (size_t)((b * a.P + jp) * L + l) * N;
+    const uint32_t *sp = a.shp ? a.shp + (size_t)(b * a.P + jp) * N : nullptr;
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+        uint32_t v = k < rows ? red_2q(Y[pidx(k)], K.q) : 0u;
+        if (k < rows && a.bias) {
+            v += __ldg(a.bias + (size_t)l * a.n_out + jp * a.rpp + k);
+            v = min(v, v - K.q);
+        }
+        if (sp) {
+            v += mulmod(__ldg(sp + k), K.delta, K);
+            v = min(v, v - K.q);
+        }
+        o[k] = v;
+    }
+}
+
+// Single-call masked FC step: the two NTT-domain inputs of column b come
+// from the workspace [B][2][L][N].
+__global__ void __launch_bounds__(kThreads) k_fc_masked(const ConvGeo a, const RingView r) {
     extern __shared__ uint4 smem4[];
     uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
     const uint32_t jp = blockIdx.x, l = blockIdx.y, b = blockIdx.z;
@@ -719,22 +740,43 @@ __global__ void __launch_bounds__(kThreads) k_fc_masked(const ConvGeo a, const R
         Y[pidx(4u * i + 3u)] = reduce64((uint64_t)x0.w * w0.w + (uint64_t)x1.w * w1.w, K);
     }
     __syncthreads();
-    intt_c(Y, 1, padded_words(N), a.logN, a.tw_inv + (size_t)l * N, K.q);
-    const uint32_t rows = min(a.rpp, a.n_out - jp * a.rpp);
-    uint32_t *o = a.out + (size_t)((b * a.P + jp) * L + l) * N;
-    const uint32_t *sp = shp ? shp + (size_t)(b * a.P + jp) * N : nullptr;
-    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
-        uint32_t v = k < rows ? red_2q(Y[pidx(k)], K.q) : 0u;
-        if (k < rows && a.bias) {
-            v += __ldg(a.bias + (size_t)l * a.n_out + jp * a.rpp + k);
-            v = min(v, v - K.q);
+    fc_masked_out(a, K, jp, l, b, Y);
+}
+
+// A masked FC item of a plan in one CTA: both inputs of ciphertext b
+// transformed in shared memory (server: c0 and sh; client: -v and i + sh),
+// the product with block jp's pair, then fc_masked_out.
+__device__ __forceinline__ void fc_masked_fused_body(const CallDesc &cd, const LimbK &K, uint32_t jp, uint32_t l,
+                                                     uint32_t b, uint4 *smem4) {
+    const ConvGeo &a = cd.g;
+    const uint32_t N = a.N, L = a.L;
+    uint32_t *Y0 = reinterpret_cast<uint32_t *>(smem4), *Y1 = Y0 + padded_words(N);
+    const uint2 *tw = cd.tw_fwd + (size_t)l * N;
+    if (cd.msrc == 1u) {
+        const uint32_t *c0 = cd.x_coeff + ((size_t)b * L + l) * N;
+        if (cd.a_ntt) {
+            for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) Y0[pidx(k)] = __ldg(c0 + k);
+            __syncthreads();
+        } else {
+            ntt_fwd_c(c0, nullptr, Y0, a.logN, tw, K.q);
         }
-        if (sp) {
-            v += mulmod(__ldg(sp + k), K.delta, K);
-            v = min(v, v - K.q);
+        ntt_fwd_c(cd.src_b + (size_t)b * N, nullptr, Y1, a.logN, tw, K.q);
+    } else {
+        const int32_t *v = reinterpret_cast<const int32_t *>(cd.x_coeff) + (size_t)b * N;
+        const int32_t *ish = reinterpret_cast<const int32_t *>(cd.src_b) + (size_t)b * N;
+        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+            Y0[pidx(k)] = small_residue(__ldg(v + k), true, K.q);
+            Y1[pidx(k)] = small_residue(__ldg(ish + k), false, K.q);
         }
-        o[k] = v;
+        __syncthreads();
+        ntt_fwd_c(nullptr, nullptr, Y0, a.logN, tw, K.q);
+        ntt_fwd_c(nullptr, nullptr, Y1, a.logN, tw, K.q);
     }
+    const uint32_t *W0 = a.bank + (size_t)((jp * 2u) * L + l) * N, *W1 = a.bank + (size_t)((jp * 2u + 1u) * L + l) * N;
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x)
+        Y0[pidx(k)] = reduce64((uint64_t)Y0[pidx(k)] * __ldg(W0 + k) + (uint64_t)Y1[pidx(k)] * __ldg(W1 + k), K);
+    __syncthreads();
+    fc_masked_out(a, K, jp, l, b, Y0);
 }
 
 // resident CTAs per SM the register budget is set for, by column tile width
@@ -775,8 +817,29 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
     const uint32_t N = cd.g.N, L = cd.g.L;
     const uint32_t l = it.poly % L;
     const LimbK K = cd.limb[l];
-    ntt_body(cd.x_coeff + (size_t)it.poly * N, const_cast<uint32_t *>(cd.g.x) + (size_t)it.poly * N, cd.g.logN,
-             cd.tw_fwd + (size_t)l * N, K, false, smem4);
+    uint32_t *dst = const_cast<uint32_t *>(cd.g.x) + (size_t)it.poly * N;
+    if (cd.msrc) {
+        // masked / client calls: polynomial (b, gz, l) of the [B][2G][L][N]
+        // workspace from its two sources (Alg. 1: c0 and sh, or -v and i + sh)
+        const uint32_t G = cd.g.G >> 1, gz = (it.poly / L) % (2u * G), b = it.poly / (L * 2u * G);
+        const size_t row = (size_t)b * G + (gz < G ? gz : gz - G);
+        if (cd.msrc == 1u && gz >= G) {
+            ntt_body(cd.src_b + row * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, false, smem4);
+        } else if (cd.msrc == 1u && cd.a_ntt) {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(cd.x_coeff + (row * L + l) * N);
+            for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) reinterpret_cast<uint4 *>(dst)[i] = __ldg(s4 + i);
+        } else if (cd.msrc == 1u) {
+            ntt_body(cd.x_coeff + (row * L + l) * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, false, smem4);
+        } else {
+            const int32_t *src = reinterpret_cast<const int32_t *>(gz < G ? cd.x_coeff : cd.src_b) + row * N;
+            uint32_t *a = reinterpret_cast<uint32_t *>(smem4);
+            for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) a[pidx(i)] = small_residue(__ldg(src + i), gz < G, K.q);
+            __syncthreads();
+            ntt_fwd_c(nullptr, dst, a, cd.g.logN, cd.tw_fwd + (size_t)l * N, K.q);
+        }
+        return;
+    }
+    ntt_body(cd.x_coeff + (size_t)it.poly * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, false, smem4);
 }
 
 // Fused FC items of a plan: item.poly = (jp * L + l) * ncols + column.
@@ -787,6 +850,10 @@ __global__ void __launch_bounds__(kThreads) k_plan_fc(const CallDesc *__restrict
     const CallDesc &cd = calls[it.call];
     const uint32_t L = cd.g.L, col = it.poly % cd.g.ncols, l = (it.poly / cd.g.ncols) % L,
                    jp = it.poly / (cd.g.ncols * L);
+    if (cd.msrc) {
+        fc_masked_fused_body(cd, cd.limb[l], jp, l, col, smem4);
+        return;
+    }
     const ConvGeo g = cd.g;
     fc_fused_body(g, cd.x_coeff, cd.tw_fwd, cd.limb[l], jp, l, col, smem4);
 }
@@ -878,7 +945,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // Thread (column jj, slot group c) owns the CS*4 consecutive slots
 // t*TS + 4*CS*c ..; its inputs for the item sit in registers.  With
 // G*CS <= 4 a channel adds at most 16 products of (q-1)^2 per column, so
-// two 64-bit accumulators per column need a single reduction per channel.
+// two 64-bit accumulators per column need a single reduction per channel;
+// with G*CS = 8 each accumulator holds 16 products (< 2^64) and is reduced
+// on its own.  One-column items (the masked and client steps: 2G groups of
+// one polynomial) leave column 1's threads computing column 0 again without
+// storing it: the kernel is bound by the weight stream, not by the MACs.
 // The per-thread sum covers CS*4 slots of one s-slot block; the block sum
 // (the valid-slot-only fold, see conv_fold_body) adds s/(4*CS) neighbouring
 // lanes and goes to the folded buffer z[l][jj][n][block].
@@ -892,12 +963,13 @@ __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, ui
     static_assert(NCH >= 1 && NCH * G == ROWS, "a stage holds whole channels");
     const uint32_t tid = threadIdx.x, lane = tid & 31u;
     const uint32_t jj = tid >> 7, c = tid & 127u;  // 128 slot groups per column
+    const uint32_t jx = d.ncol == 2u ? jj : 0u;    // the input column this thread reads
     uint4 x[G][CS];
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
         for (int u = 0; u < CS; ++u)
-            x[g][u] = *reinterpret_cast<const uint4 *>(X + ((jj * G + g) << LT) + 4u * CS * c + 4u * u);
+            x[g][u] = *reinterpret_cast<const uint4 *>(X + ((jx * G + g) << LT) + 4u * CS * c + 4u * u);
     __syncwarp();
     if (lane == 0) mbar_arrive(xempty);  // the producer may refill this input buffer
     LimbK K;
@@ -909,7 +981,7 @@ __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, ui
     uint32_t *zc = d.z + jj * d.colstride + ((4u * CS * c) >> d.logs);
     const uint32_t M = d.M, nch = d.nch, nst = d.nst;
     const uint32_t lanes = max(1u, (1u << d.logs) / (4u * CS));  // threads whose sums make one block
-    const bool lead = (lane & (lanes - 1u)) == 0;
+    const bool lead = (lane & (lanes - 1u)) == 0 && jj < d.ncol;
     uint32_t n = 0;
     for (uint32_t st = 0; st < nst; ++st, n += NCH) {
         if (!mbar_wait(full + buf, ph)) return false;
@@ -929,7 +1001,13 @@ __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, ui
                         a0 += (uint64_t)w.z * x[g][u].z;
                         a1 += (uint64_t)w.w * x[g][u].w;
                     }
-                uint32_t v = reduce64(a0 + a1, K);
+                uint32_t v;
+                if constexpr (G * CS > 4) {
+                    v = reduce64(a0, K) + reduce64(a1, K);
+                    v = min(v, v - K.q);
+                } else {
+                    v = reduce64(a0 + a1, K);
+                }
                 for (uint32_t o = 1; o < lanes; o <<= 1) {
                     v += __shfl_xor_sync(0xffffffffu, v, o);
                     v = min(v, v - K.q);
@@ -953,9 +1031,9 @@ __device__ __forceinline__ void mac_issue_inputs(const MacCopy &c, const MacDesc
     mbar_expect(xbar, c.xrows * c.xwords * 4u + (uint32_t)sizeof(MacDesc));
     bulk_load(dslot, desc, (uint32_t)sizeof(MacDesc), xbar);
     for (uint32_t r = 0; r < c.xrows; ++r) {
-        // buffer row order [jj][g]: input row (g, jj) = 2g + jj
-        const uint32_t g = r >> 1, jj = r & 1u;
-        bulk_load(X + (jj * (c.xrows >> 1) + g) * c.xwords, c.x + (size_t)r * c.xstride, c.xwords * 4u, xbar);
+        // buffer row order [jj][g]: input row (g, jj) = 2g + jj; one column: row g
+        const uint32_t g = c.ncol == 2u ? r >> 1 : r, jj = c.ncol == 2u ? r & 1u : 0u;
+        bulk_load(X + (jj * (c.xrows / c.ncol) + g) * c.xwords, c.x + (size_t)r * c.xstride, c.xwords * 4u, xbar);
     }
 }
 
@@ -1062,7 +1140,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
             case 2: ok = mac_item<1, 4>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
             case 3: ok = mac_item<2, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
             case 4: ok = mac_item<2, 2>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
-            default: ok = mac_item<4, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
+            case 5: ok = mac_item<4, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
+            default: ok = mac_item<8, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
         }
     }
     if (!ok) atomicOr(status, 1u);
@@ -1083,8 +1162,8 @@ __global__ void __launch_bounds__(kFinThreads, 4) k_plan_fin(const CallDesc *__r
     const LimbK K = cd.limb[it.l];
     uint32_t *Zs = reinterpret_cast<uint32_t *>(smem4);
     const uint32_t h = it.a, l = it.l, c = it.b;
-    const uint32_t N = cd.g.N, L = cd.g.L, co = cd.g.co, s = cd.g.s, logs = cd.g.logs, M = cd.g.M,
-                   logM = cd.g.logM, mult = cd.g.mult, H = cd.g.H;
+    const uint32_t N = cd.g.N, co = cd.g.co, s = cd.g.s, logs = cd.g.logs, M = cd.g.M, logM = cd.g.logM,
+                   mult = cd.g.mult;
     const uint32_t sh = min(s, co - h * s);
     const uint32_t PS = fin_stride(M);
     // sh*M words, 4 at a time, 8 loads in flight per thread
@@ -1137,8 +1216,19 @@ __global__ void __launch_bounds__(kFinThreads, 4) k_plan_fin(const CallDesc *__r
     }
     __syncthreads();
     intt_c(Zs, sh, PS, logM, cd.g.tw_inv + (size_t)l * N, K.q);
-    uint32_t *o = cd.g.out + ((size_t)(((c >> 1) * H + h) * 2 + (c & 1)) * L + l) * N;
-    if (mult == 1 && sh == s) {
+    uint32_t *o = out_poly(cd.g, c, h, l);
+    if (cd.g.masked) {
+        // masked server / client step: [B][H][L][N] output, + Delta_Q sh'_h on every slot (server)
+        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+            const uint32_t r = k & (s - 1), rr = r / mult;
+            uint32_t v = share_term(cd.g, K, c, h, k);
+            if (r == rr * mult && rr < sh) {
+                v += red_2q(Zs[rr * PS + pidx(k >> logs)], K.q);
+                v = min(v, v - K.q);
+            }
+            o[k] = v;
+        }
+    } else if (mult == 1 && sh == s) {
         for (uint32_t k = threadIdx.x; k < N; k += blockDim.x)
             o[k] = red_2q(Zs[(k & (s - 1)) * PS + pidx(k >> logs)], K.q);
     } else {
@@ -1424,10 +1514,11 @@ cudaError_t he_launch_fc_masked(const RingView &r, const he_fc_layout &fl, const
     a.P = fl.P_fc;
     a.rpp = fl.rows_per_poly;
     a.n_out = fl.n_out;
+    a.shp = shp;
     const size_t smem = (size_t)padded_words(r.N) * 4u;
     cudaError_t e = set_smem(k_fc_masked, smem);
     if (e != cudaSuccess) return e;
-    k_fc_masked<<<dim3(fl.P_fc, r.L, B), kThreads, smem, st>>>(a, r, shp);
+    k_fc_masked<<<dim3(fl.P_fc, r.L, B), kThreads, smem, st>>>(a, r);
     return cudaGetLastError();
 }
 

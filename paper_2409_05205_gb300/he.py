@@ -48,7 +48,8 @@ class he_fc_layout(ctypes.Structure):
 
 class he_layer_call(ctypes.Structure):
     _fields_ = [("filters", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("in_domain", ctypes.c_int),
-                ("d_out", ctypes.c_void_p), ("B", ctypes.c_uint32)]
+                ("d_out", ctypes.c_void_p), ("B", ctypes.c_uint32), ("d_share", ctypes.c_void_p),
+                ("d_share_out", ctypes.c_void_p)]
 
 
 class he_plan_tuning(ctypes.Structure):
@@ -370,12 +371,18 @@ def he_ntt_inverse(p: int, d_in, d_out, count: int, stream=None) -> None:
 
 
 def _calls(calls):
+    """(filters, d_in, in_domain, d_out, B[, d_share[, d_share_out]]) tuples
+    or dicts with those keys."""
     arr = (he_layer_call * len(calls))()
     for i, c in enumerate(calls):
         if isinstance(c, dict):
-            c = (c["filters"], c["d_in"], c.get("in_domain", HE_COEFF), c["d_out"], c["B"])
-        f, d_in, dom, d_out, B = c
-        arr[i] = he_layer_call(f, _ptr(d_in), dom, _ptr(d_out), B)
+            c = (c["filters"], c["d_in"], c.get("in_domain", HE_COEFF), c["d_out"], c["B"], c.get("d_share"),
+                 c.get("d_share_out"))
+        f, d_in, dom, d_out, B = c[:5]
+        sh = c[5] if len(c) > 5 else None
+        shp = c[6] if len(c) > 6 else None
+        arr[i] = he_layer_call(f, _ptr(d_in), dom, _ptr(d_out), B, None if sh is None else _ptr(sh),
+                               None if shp is None else _ptr(shp))
     return arr
 
 
@@ -384,7 +391,8 @@ def _tuning_dict(t: he_plan_tuning) -> dict:
 
 
 def he_plan_create(calls) -> int:
-    """calls: sequence of (filters, d_in, in_domain, d_out, B) tuples or dicts."""
+    """calls: sequence of (filters, d_in, in_domain, d_out, B[, d_share[,
+    d_share_out]]) tuples or dicts (the shares for masked and client banks)."""
     out = _vp()
     _check(lib().he_plan_create(_calls(calls), len(calls), ctypes.byref(out)))
     return out.value

@@ -177,6 +177,10 @@ WORKLOADS = {
     "plain20_c100_wide4": dict(N=16384, L=6, t=65537, B=8, conv=plain20_conv_layers(4),
                                fc=dict(n_in=256, n_out=100), wlo=-128, whi=127),
     "batched64": dict(t=65537, calls=batched_calls(3, 64), wlo=-128, whi=127),
+    # the same network through the masked protocol of Alg. 1 / Alg. 2 (server
+    # step c0 rho - Delta sh fhat + Delta sh', client step, rescale)
+    "plain20_c10_masked": dict(N=8192, L=3, t=65537, B=1, conv=plain20_conv_layers(1),
+                               fc=dict(n_in=64, n_out=10), wlo=-128, whi=127, masked=True),
     "f5_d8_w3": dict(N=8192, L=3, t=65537, B=1, conv=f5_d8_w3_conv_layers(), fc=dict(n_in=192, n_out=10),
                      wlo=-128, whi=127),
     "resnet50_bottleneck": dict(N=8192, L=3, t=65537, B=1, conv=resnet_bottleneck_conv_layers(), fc=None,
