@@ -34,6 +34,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -79,11 +80,11 @@ class ClockSampler:
     def __init__(self, device: int):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="he_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
@@ -114,6 +115,10 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         return {"sm_mhz": float(np.median(sms)) if sms else None, "sm_max_mhz": mx,
                 "reasons": sorted(reasons), "samples": len(sms)}
 
@@ -298,7 +303,8 @@ class Arm:
 # DRAM bytes (read + write) of one k_plan_mac launch, from an ncu capture of
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where no
 # capture of the current kernel exists.
-TRAFFIC = {"plain20_c10": 140.87e6}  # ncu --set full of one launch: read 136.60 MB + write 4.27 MB
+TRAFFIC = {"plain20_c10": 141.15e6,          # ncu --set full of one launch: read 136.62 MB + write 4.54 MB
+           "plain20_c10_masked": 269.85e6}   # read 264.15 MB + write 5.70 MB
 
 
 def _traffic(name):
@@ -651,15 +657,20 @@ class MaskedArm:
         """Per replica: one plan over every layer's masked server call, one over
         every layer's client call."""
         H = self.H
-        self.srv_plans, self.cli_plans = [], []
+        self.srv_plans, self.cli_plans, self.rs_plans = [], [], []
         for r in range(self.R):
-            sc, cc = [], []
+            sc, cc, rc = [], [], []
             for i, c in enumerate(self.calls):
                 x = self.io[r][i]
                 sc.append((self.srv[r][i], x["c0"], H.HE_COEFF, x["out"], c["B"], x["sh"], x["shp"]))
+                rc.append((self.srv[r][i], x["c0"], H.HE_COEFF, x["out"], c["B"], x["sh"], x["shp"], x["outr"]))
                 cc.append((self.cli[r][i], x["v"], H.HE_COEFF, x["out1"], c["B"], x["ish"]))
             self.srv_plans.append(H.he_plan_create(sc))
             self.cli_plans.append(H.he_plan_create(cc))
+            self.rs_plans.append(H.he_plan_create(rc))
+
+    def server_rescale_plan(self, r, stream):
+        self.H.he_plan_run(self.rs_plans[r], stream)
 
     def server_plan(self, r, stream):
         self.H.he_plan_run(self.srv_plans[r], stream)
@@ -710,7 +721,7 @@ class MaskedArm:
         return graphs
 
     def free(self):
-        for pl in getattr(self, "srv_plans", []) + getattr(self, "cli_plans", []):
+        for pl in getattr(self, "srv_plans", []) + getattr(self, "cli_plans", []) + getattr(self, "rs_plans", []):
             self.H.he_plan_destroy(pl)
         for banks in self.srv + self.cli:
             for f in banks:
@@ -761,6 +772,7 @@ def run_masked(args, rank, world, device):
     arm.make_plans()
     info = H.he_plan_query(arm.srv_plans[0], nl)
     g_srv, g_cli, g_rs = arm.capture(arm.server_plan), arm.capture(arm.client_plan), arm.capture(arm.rescale)
+    g_srs = arm.capture(arm.server_rescale_plan)
     barrier()
     clocks = ClockSampler(device)
     clocks.start()
@@ -779,6 +791,18 @@ def run_masked(args, rank, world, device):
     lat = [a.elapsed_time(b) for a, b in ev]
     cli_ms = _replay_rate(torch, g_cli, stream, k2, W)
     rs_ms = _replay_rate(torch, g_rs, stream, k2, W)
+    srs_ms = _replay_rate(torch, g_srs, stream, k2, W)
+    # the plan's rescale kernel alone, back to back over the replicas
+    r0, r1 = _events(2)
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            H.he_plan_run_phase(arm.rs_plans[k % arm.R], H.HE_PHASE_RESCALE, stream)
+        r0.record(stream)
+        for k in range(k2):
+            H.he_plan_run_phase(arm.rs_plans[k % arm.R], H.HE_PHASE_RESCALE, stream)
+        r1.record(stream)
+    torch.cuda.synchronize()
+    prs_ms = r0.elapsed_time(r1) / k2
     # the MAC kernel of the server plan alone, back to back over the replicas
     k_phase = min(K, 500)
     m0, m1 = _events(2)
@@ -852,16 +876,20 @@ def run_masked(args, rank, world, device):
                         "ms_per_step": cli_ms / k2,
                         "what": "c1^r = extract(sum -v p1 + (i + sh) p2) of every layer: one plan of the "
                                 "client calls, a CUDA graph per step"},
-        "rescale": {"value": arm.units * k2 / (rs_ms * 1e-3), "unit": "layers/s", "steps": k2,
-                    "ms_per_step": rs_ms / k2, "bytes_per_step": rs_bytes, "achieved_gbs": rs_gbs,
-                    "frac": rs_gbs / hbm,
-                    "what": f"k_rescale of every c0^r from {arm.calls[0]['L']} to {arm.calls[0]['L'] - 1} limbs "
-                            f"({nl} launches per step in a CUDA graph; L limbs read, L - 1 written)"},
+        "rescale": {"server_step_with_rescale_ms": srs_ms / k2,
+                    "k_plan_rescale": {"avg_launch_ms": prs_ms, "bytes": rs_bytes,
+                                       "achieved_gbs": rs_bytes / (prs_ms * 1e-3) / 1e9,
+                                       "frac": rs_bytes / (prs_ms * 1e-3) / 1e9 / hbm, "launches": k2,
+                                       "what": f"every c0^r of the step from {arm.calls[0]['L']} to "
+                                               f"{arm.calls[0]['L'] - 1} limbs in one launch (L limbs read, "
+                                               "L - 1 written), back to back over the replicas"},
+                    "single_calls": {"ms_per_step": rs_ms / k2, "achieved_gbs": rs_gbs, "frac": rs_gbs / hbm,
+                                     "what": f"he_rescale per layer output ({nl} launches per step, a CUDA graph)"}},
         "roofline": {"kernel": "k_plan_mac: one-column masked channel MAC of every Conv layer (masked banks "
                                "+ transformed c0 and sh read once, folded sums written once)",
                      "bound": "hbm", "achieved": mac_gbs, "peak": hbm, "unit": "GB/s", "frac": mac_gbs / hbm,
                      "peak_source": peak_src + " (hbm_gbs burst copy)", "algorithmic_bytes": mac_bytes,
-                     "avg_launch_ms": mac_ms, "launches": k_phase, "traffic": None},
+                     "avg_launch_ms": mac_ms, "launches": k_phase, "traffic": _traffic(wl["name"])},
         "kernels": {"step_bytes": step_bytes, "step_gbs_graph": step_bytes / (srv_ms / K * 1e-3) / 1e9},
         "plan": {k: v for k, v in info.items() if k not in ("split", "form")},
         "e2e": {"value": arm.units * ke / e2e_dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,

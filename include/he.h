@@ -182,7 +182,7 @@ he_status he_pack_fc(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t 
                      const int32_t *bias, he_filters_t *out);
 void he_filters_destroy(he_filters_t f);
 
-/* Server evaluation of one Conv layer for B ciphertexts (Alg. 1 line 16 and
+/* Server evaluation of one Conv layer for B ciphertexts (Alg. 1's evaluation step and
  * the slot-copy loop that follows, in ciphertext x plaintext form):
  *   y_n^(j) = sum_{g<G} c_g^(j) * fhat_{g,n}  in Z_q[X]/(X^N+1), j = 0, 1,
  * then output polynomial h takes from each channel n it holds the
@@ -380,7 +380,9 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
  *      (MAC, folded inverse transform and extraction per output channel);
  *   4. every FC call's work (input transform, product, inverse transform,
  *      bias, output) in one kernel on a side stream that forks off `stream`
- *      at the start and joins it again before the run completes.
+ *      at the start and joins it again before the run completes;
+ *   5. for the calls with d_rescaled: one kernel rescaling all their
+ *      outputs (the RNS rescale of he_rescale).
  * Work items are ordered longest first.  The plan owns its workspace and
  * descriptor tables, so he_plan_run allocates nothing and can be captured
  * into a CUDA graph.  Runs of one plan must not overlap on the GPU;
@@ -400,6 +402,8 @@ typedef struct {
     uint32_t B;             /* ciphertexts in this call, >= 1 */
     const uint32_t *d_share;     /* masked banks: sh; client banks: i + sh (int32); else NULL */
     const uint32_t *d_share_out; /* masked banks: sh'; else NULL */
+    uint32_t *d_rescaled;        /* NULL, or DEVICE [..][L-1][N]: every [L][N] polynomial of d_out
+                                    rescaled by the last prime, the words of he_rescale (L >= 2) */
 } he_layer_call;
 
 /* Validates every call (shapes, alignment, one device, no output overlapping
@@ -450,13 +454,16 @@ he_status he_plan_run(he_plan_t plan, void *stream);
  *   HE_PHASE_NTT (0)   the input-NTT kernel (step 1 above);
  *   HE_PHASE_REST (1)  everything after it (steps 2-4);
  *   HE_PHASE_MAC (2)   the split-form MAC kernel alone (first half of 2);
- *   HE_PHASE_FINISH (3) everything after the MAC kernel (rest of 2, 3, 4).
+ *   HE_PHASE_FINISH (3) everything after the MAC kernel (rest of 2, 3, 4, 5);
+ *   HE_PHASE_RESCALE (4) the rescale kernel alone (step 5; it reads the
+ *                      outputs of the phases before it).
  * A full run is phases 0, 1 or phases 0, 2, 3, in that order on one stream
  * (or otherwise ordered). */
 #define HE_PHASE_NTT 0
 #define HE_PHASE_REST 1
 #define HE_PHASE_MAC 2
 #define HE_PHASE_FINISH 3
+#define HE_PHASE_RESCALE 4
 he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream);
 
 /* What a plan launches; filled by he_plan_query. */
@@ -474,6 +481,7 @@ typedef struct {
     uint32_t tc_items;        /* tensor-core MAC items (call x limb x run of slot blocks) */
     uint32_t tc_ctas;         /* persistent CTAs of the tensor-core MAC kernel */
     uint32_t tc_calls;        /* Conv calls on the tensor-core MAC kernel */
+    uint32_t rescale_items;   /* items of the rescale kernel (0: no call has d_rescaled) */
 } he_plan_info;
 /* Fills *info; if `split` is not NULL, also split[i] for each call i (of
  * the ncalls given to he_plan_create): 1 if it takes the split form with the

@@ -204,7 +204,7 @@ void ora_ntt_inv(uint32_t *a, int count, int N, uint32_t q, uint32_t psi) {
  * x: K*C coefficient polynomials, x[k][c] at x + (k*C + c)*N
  * w: Nout*K coefficient polynomials, w[n][k] at w + (n*K + k)*N
  * y: Nout*C output polynomials, y[n][c] at y + (n*C + c)*N
- * This is the plain form of the server step (Sec. III-A, Alg. 1 line 16:
+ * This is the plain form of the server step (Sec. III-A, Alg. 1's evaluation step:
  * one product per input polynomial and output channel, summed, then INTT). */
 void ora_sum_products_ntt(const uint32_t *x, int K, int C, const uint32_t *w,
                           int Nout, uint32_t *y, int N, uint32_t q,

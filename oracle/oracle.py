@@ -12,7 +12,7 @@ Contents, each citing the passage it follows:
     eq. (k_batch_new), with the readings listed in the design notes;
   * packing of inputs, filters, FC inputs, FC weights and FC bias
     (Sec. II-C, Sec. III-A, Sec. III-B eqs. (i(x) formula), (w(x) formula));
-  * rotation-free extraction (Alg. 1, the slot-copy loop after line 16) and
+  * rotation-free extraction (Alg. 1, the slot-copy loop) and
     the FC output window (Alg. 2, Theorem 1, "only the first n_o
     coefficients");
   * the direct Conv and FC definitions (Sec. II-B eqs. (siso_conv_formula),
@@ -297,7 +297,7 @@ def output_slot(lay: dict, n: int, k: int, l: int) -> tuple[int, int]:
 
 
 def extract_conv(y: np.ndarray, lay: dict) -> np.ndarray:
-    """Rotation-free extraction (Alg. 1, the loop after line 16): for output
+    """Rotation-free extraction (Alg. 1, the slot-copy loop): for output
     polynomial h, copy from channel n's product every coefficient in its
     residue class off_n (mod s), i.e. slots s*e + off_n for all e < N/s;
     every other slot is 0.  y: [c_o][...][N] -> out: [H][...][N]."""
@@ -473,7 +473,7 @@ def _sum_products(x: np.ndarray, w: np.ndarray, q: int, psi: int,
 
 
 # ----------------------------------------------------------------------------
-# The server step (Sec. III-A, Alg. 1 line 16 + the extraction loop;
+# The server step (Sec. III-A, Alg. 1's evaluation step + the extraction loop;
 # Sec. III-B, Alg. 2), in the ciphertext x plaintext form
 # ----------------------------------------------------------------------------
 

@@ -1034,6 +1034,8 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
     std::vector<Range> ranges;
     std::vector<CallDesc> descs(ncalls);
     std::vector<size_t> ws_off(ncalls, 0), z_off(ncalls, 0);
+    std::vector<RescaleCall> rs_calls;
+    std::vector<RsItem> rs_items;
     size_t ws_words = 0;
     for (uint32_t i = 0; i < ncalls; ++i) {
         const he_layer_call &c = calls[i];
@@ -1156,6 +1158,20 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         }
         ranges.push_back({(uintptr_t)c.d_in, (uintptr_t)(c.d_in + nin), false, i});
         ranges.push_back({(uintptr_t)c.d_out, (uintptr_t)(c.d_out + nout), true, i});
+        if (c.d_rescaled) {
+            if (r.L < 2) return fail(HE_ERR_ARG, "call %u: d_rescaled needs at least 2 limbs", i);
+            if (!aligned16(c.d_rescaled)) return fail(HE_ERR_ARG, "call %u: d_rescaled must be 16-byte aligned", i);
+            const size_t npoly = nout / ((size_t)r.L * r.N);
+            ranges.push_back({(uintptr_t)c.d_rescaled, (uintptr_t)(c.d_rescaled + npoly * (r.L - 1u) * r.N), true, i});
+            RescaleCall rc;
+            rc.a = he_rescale_args(r);
+            rc.in = c.d_out;
+            rc.out = c.d_rescaled;
+            const size_t total = npoly * (r.N >> 2);
+            for (size_t b = 0; b < total; b += kRsItemU4)
+                rs_items.push_back({(uint32_t)rs_calls.size(), (uint32_t)b, (uint32_t)std::min(total, b + kRsItemU4), 0u});
+            rs_calls.push_back(rc);
+        }
     }
     for (uint32_t i = 0; i < ncalls; ++i)
         if (descs[i].split || descs[i].zt) {
@@ -1374,6 +1390,15 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         }
     }
     if (e == cudaSuccess && !tc_calls.empty()) e = build_tc_tables(pl, descs, calls, tc_calls);
+    if (e == cudaSuccess && !rs_items.empty()) {
+        e = cudaMalloc(&pl->d_rs_calls, sizeof(RescaleCall) * rs_calls.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(pl->d_rs_calls, rs_calls.data(), sizeof(RescaleCall) * rs_calls.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&pl->d_rs_items, sizeof(RsItem) * rs_items.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(pl->d_rs_items, rs_items.data(), sizeof(RsItem) * rs_items.size(), cudaMemcpyHostToDevice);
+        pl->n_rs = (uint32_t)rs_items.size();
+    }
     if (e == cudaSuccess) {
         std::stable_sort(fin.begin(), fin.end(), by_cost);
         std::vector<ChanItem> items;
@@ -1421,7 +1446,7 @@ he_status he_plan_run(he_plan_t plan, void *stream) {
 
 he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream) {
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
-    if (phase < HE_PHASE_NTT || phase > HE_PHASE_FINISH) return fail(HE_ERR_ARG, "phase must be 0, 1, 2 or 3");
+    if (phase < HE_PHASE_NTT || phase > HE_PHASE_RESCALE) return fail(HE_ERR_ARG, "phase must be 0 .. 4");
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
     cudaError_t e = he_launch_plan(*plan, (cudaStream_t)stream, phase);
@@ -1438,7 +1463,8 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
     for (int c = 0; c < 4; ++c) r.fused_items += plan->n_chan[c];
     r.fc_items = plan->n_fc;
     r.kernels_per_run = (plan->n_ntt > 0) + (plan->n_mac > 0) + (plan->n_fin > 0) + (plan->n_fc > 0) +
-                        (plan->n_tc > 0);
+                        (plan->n_tc > 0) + (plan->n_rs > 0);
+    r.rescale_items = plan->n_rs;
     r.tc_items = plan->n_tc;
     r.tc_ctas = plan->n_tc ? plan->tc_ctas : 0;
     for (uint32_t i = 0; i < plan->ncalls; ++i) r.tc_calls += plan->split[i] == 2;
@@ -1468,6 +1494,8 @@ void he_plan_destroy(he_plan_t plan) {
     cudaFree(plan->d_tc_items);
     cudaFree(plan->d_tc_offs);
     cudaFree(plan->d_status);
+    cudaFree(plan->d_rs_calls);
+    cudaFree(plan->d_rs_items);
     cudaFree(plan->d_fc);
     if (plan->side) cudaStreamDestroy(plan->side);
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);

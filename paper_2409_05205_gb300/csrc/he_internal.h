@@ -259,6 +259,26 @@ struct ChanItem {
     uint32_t call, a, l, b;   // conv: (channel n, limb, column tile); fc: (weight poly, limb, column)
 };                            // split MAC: (tile, limb, first channel); finishing: (output poly, limb, column)
 
+// RNS rescale by the last prime (he_rescale; k_rescale, k_plan_rescale)
+struct RescaleLimb {
+    uint32_t q, h, qinv, qinvs;  // q_l, floor(q_L / 2) mod q_l, q_L^-1 mod q_l and its Shoup constant
+};
+struct RescaleArgs {
+    RescaleLimb limb[HE_MAX_LIMBS];
+    uint32_t qL, hL, N, L;  // last prime, floor(q_L / 2), ring degree, limbs of the input
+};
+RescaleArgs he_rescale_args(const RingView &r);
+// One plan call's rescale: npoly polynomials [L][N] at in -> [L-1][N] at out.
+struct RescaleCall {
+    RescaleArgs a;
+    const uint32_t *in;
+    uint32_t *out;
+};
+struct RsItem {
+    uint32_t call, begin, end, pad;  // uint4 groups [begin, end) of the call's npoly * N / 4
+};
+constexpr uint32_t kRsItemU4 = 256;  // uint4 groups per rescale item: one per thread (1024 coefficients)
+
 struct he_plan_s {
     int device;
     uint32_t ncalls, n_ntt, n_chan[4];  // fused channel items per NJ class (2, 4, 8, 16)
@@ -283,6 +303,9 @@ struct he_plan_s {
     TcCall *d_tc_calls;
     TcItem *d_tc_items;
     uint32_t *d_tc_offs;                // items of CTA b at [offs[b], offs[b+1])
+    uint32_t n_rs;                      // rescale items (calls with d_rescaled)
+    RescaleCall *d_rs_calls;
+    RsItem *d_rs_items;
     uint32_t *d_status;                 // bit 0 / bit 1: a bounded wait in the MAC / tensor-core MAC kernel gave up
     uint8_t *split;                     // host: per call, 1 if it takes the split form
     he_plan_tuning tuning;

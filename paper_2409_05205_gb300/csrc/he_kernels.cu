@@ -8,10 +8,10 @@
 //                 factor that turns the channel sum below into the valid-slot-
 //                 only inverse transform (derivation at conv_fold_body).
 //  k_pack_fc      model load: packs w_j (Sec. III-B eq. (w(x) formula)).
-//  k_conv_fold    the hot kernel: NTT-domain channel MAC (Alg. 1 line 16,
+//  k_conv_fold    the hot kernel: NTT-domain channel MAC (Alg. 1's evaluation step,
 //                 summed over input groups), folded to the N/s slots one
 //                 output channel keeps, inverse transform of length N/s, and
-//                 the rotation-free slot copy (Alg. 1, the loop after line 16).
+//                 the rotation-free slot copy (Alg. 1, the slot-copy loop).
 //  k_conv_full    the plain form: MAC, full length-N INTT, then either the
 //                 whole product (per-channel output) or the slot copy.
 //  k_fc           FC server step (Alg. 2): product, INTT, first n_o
@@ -496,47 +496,54 @@ __global__ void __launch_bounds__(kThreads) k_client_in(const RingView r, const 
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) dst[i] = small_residue(__ldg(src + i), neg, q);
 }
 
+// The rescale of uint4 group i (4 coefficients) of polynomial i / (N/4):
+// reads its L limbs, writes L - 1.
+__device__ __forceinline__ void rescale_u4(const RescaleArgs &a, const uint32_t *__restrict__ in,
+                                           uint32_t *__restrict__ out, size_t i) {
+    const uint32_t nq = a.N >> 2;
+    const size_t pi = i / nq;
+    const uint32_t k4 = (uint32_t)(i % nq);
+    const uint32_t *src = in + pi * a.L * a.N;
+    uint32_t *dst = out + pi * (a.L - 1u) * a.N;
+    const uint4 xl = __ldcs(reinterpret_cast<const uint4 *>(src + (size_t)(a.L - 1u) * a.N) + k4);
+    uint32_t y[4] = {xl.x + a.hL, xl.y + a.hL, xl.z + a.hL, xl.w + a.hL};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) y[u] = min(y[u], y[u] - a.qL);  // (x_L + h) mod q_L
+    for (uint32_t l = 0; l + 1u < a.L; ++l) {
+        const RescaleLimb &R = a.limb[l];
+        const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src + (size_t)l * a.N) + k4);
+        const uint32_t xv[4] = {x.x, x.y, x.z, x.w};
+        uint32_t r[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t ym = min(y[u], y[u] - R.q);          // y mod q_l (q_L < 2 q_l)
+            uint32_t v = xv[u] + R.h;                           // < 2 q_l
+            v = min(v, v - R.q);
+            v = v + R.q - ym;                                    // (x_l + h - y) mod q_l, in [1, 2 q_l)
+            v = min(v, v - R.q);
+            r[u] = red_2q(shoup_lazy(v, R.qinv, R.qinvs, R.q), R.q);
+        }
+        __stcs(reinterpret_cast<uint4 *>(dst + (size_t)l * a.N) + k4, make_uint4(r[0], r[1], r[2], r[3]));
+    }
+}
+
 // RNS rescale by the last prime with rounding: X' = floor((X + h) / q_L),
 // h = floor(q_L / 2), from the residues alone: with y = (x_L + h) mod q_L,
 // X + h - y is a multiple of q_L, so x'_l = (x_l + h - y) q_L^-1 mod q_l.
-struct RescaleLimb {
-    uint32_t q, h, qinv, qinvs;  // q_l, h mod q_l, q_L^-1 mod q_l and its Shoup constant
-};
-struct RescaleArgs {
-    RescaleLimb limb[HE_MAX_LIMBS];
-    uint32_t qL, hL, N, L;  // last prime, floor(q_L / 2), ring degree, limbs of the input
-};
-
 __global__ void __launch_bounds__(kThreads) k_rescale(const RescaleArgs a, const uint32_t *__restrict__ in,
                                                       uint32_t *__restrict__ out, uint32_t npoly) {
-    const uint32_t nq = a.N >> 2;
-    const size_t total = (size_t)npoly * nq;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t pi = i / nq;
-        const uint32_t k4 = (uint32_t)(i % nq);
-        const uint32_t *src = in + pi * a.L * a.N;
-        uint32_t *dst = out + pi * (a.L - 1u) * a.N;
-        const uint4 xl = __ldcs(reinterpret_cast<const uint4 *>(src + (size_t)(a.L - 1u) * a.N) + k4);
-        uint32_t y[4] = {xl.x + a.hL, xl.y + a.hL, xl.z + a.hL, xl.w + a.hL};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) y[u] = min(y[u], y[u] - a.qL);  // (x_L + h) mod q_L
-        for (uint32_t l = 0; l + 1u < a.L; ++l) {
-            const RescaleLimb &R = a.limb[l];
-            const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src + (size_t)l * a.N) + k4);
-            const uint32_t xv[4] = {x.x, x.y, x.z, x.w};
-            uint32_t r[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const uint32_t ym = min(y[u], y[u] - R.q);          // y mod q_l (q_L < 2 q_l)
-                uint32_t v = xv[u] + R.h;                           // < 2 q_l
-                v = min(v, v - R.q);
-                v = v + R.q - ym;                                    // (x_l + h - y) mod q_l, in [1, 2 q_l)
-                v = min(v, v - R.q);
-                r[u] = red_2q(shoup_lazy(v, R.qinv, R.qinvs, R.q), R.q);
-            }
-            __stcs(reinterpret_cast<uint4 *>(dst + (size_t)l * a.N) + k4, make_uint4(r[0], r[1], r[2], r[3]));
-        }
-    }
+    const size_t total = (size_t)npoly * (a.N >> 2);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+        rescale_u4(a, in, out, i);
+}
+
+// The rescale step of a plan: one item per run of kRsItemU4 uint4 groups of
+// one call's output.
+__global__ void __launch_bounds__(kThreads) k_plan_rescale(const RescaleCall *__restrict__ calls,
+                                                           const RsItem *__restrict__ items) {
+    const RsItem it = items[blockIdx.x];
+    const RescaleCall &c = calls[it.call];
+    for (uint32_t i = it.begin + threadIdx.x; i < it.end; i += blockDim.x) rescale_u4(c.a, c.in, c.out, i);
 }
 
 struct PackConvArgs {
@@ -1423,9 +1430,7 @@ cudaError_t he_launch_client_in(const RingView &r, const int32_t *v, const int32
     return he_launch_ntt(r, ws, ws, np, false, st);
 }
 
-cudaError_t he_launch_rescale(const RingView &r, const uint32_t *in, uint32_t *out, uint32_t npoly,
-                              cudaStream_t st) {
-    if (npoly == 0) return cudaSuccess;
+RescaleArgs he_rescale_args(const RingView &r) {
     RescaleArgs a{};
     const uint32_t qL = r.limb[r.L - 1].q;
     a.qL = qL;
@@ -1447,8 +1452,16 @@ cudaError_t he_launch_rescale(const RingView &r, const uint32_t *in, uint32_t *o
         R.qinv = (uint32_t)acc;
         R.qinvs = (uint32_t)(((uint64_t)R.qinv << 32) / q);
     }
-    int sms = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    return a;
+}
+
+cudaError_t he_launch_rescale(const RingView &r, const uint32_t *in, uint32_t *out, uint32_t npoly,
+                              cudaStream_t st) {
+    if (npoly == 0) return cudaSuccess;
+    const RescaleArgs a = he_rescale_args(r);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
     const size_t work = (size_t)npoly * (r.N >> 2);
     const uint32_t grid = (uint32_t)std::min<size_t>((work + kThreads - 1) / kThreads, (size_t)sms * 8u);
@@ -1658,6 +1671,10 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     // work, joined back before the last channel kernel's completion
     // phase: -1 whole run, 0 input NTTs, 1 everything after them, 2 the MAC
     // kernel alone, 3 everything after the MAC kernel
+    if (phase == 4) {  // the rescale kernel alone
+        if (pl.n_rs) k_plan_rescale<<<pl.n_rs, kThreads, 0, st>>>(pl.d_rs_calls, pl.d_rs_items);
+        return cudaGetLastError();
+    }
     const bool fc = pl.n_fc && (phase == -1 || phase == 1 || phase == 3);
     if (fc) {
         if ((e = cudaEventRecord(pl.ev_fork, st)) != cudaSuccess) return e;
@@ -1699,5 +1716,13 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     if ((e = plan_chan_launch<2>(pl, 0, st)) != cudaSuccess) return e;
     if ((e = plan_chan_launch<4>(pl, 1, st)) != cudaSuccess) return e;
     if ((e = plan_chan_launch<8>(pl, 2, st)) != cudaSuccess) return e;
-    return plan_chan_launch<16>(pl, 3, st);
+    if ((e = plan_chan_launch<16>(pl, 3, st)) != cudaSuccess) return e;
+    if (pl.n_rs) {
+        // the rescale reads every output, FC outputs included: join first
+        if (join.on && (e = cudaStreamWaitEvent(st, pl.ev_join, 0)) != cudaSuccess) return e;
+        join.on = false;
+        k_plan_rescale<<<pl.n_rs, kThreads, 0, st>>>(pl.d_rs_calls, pl.d_rs_items);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }

@@ -22,7 +22,7 @@ HE_OUT_EXTRACTED, HE_OUT_PER_CHANNEL, HE_OUT_EXTRACTED_UNFOLDED = 0, 1, 2
 HE_MAX_LIMBS = 16
 HE_MAX_INTERLEAVE = 128
 HE_DEVICE_NONE = -1
-HE_PHASE_NTT, HE_PHASE_REST, HE_PHASE_MAC, HE_PHASE_FINISH = range(4)
+HE_PHASE_NTT, HE_PHASE_REST, HE_PHASE_MAC, HE_PHASE_FINISH, HE_PHASE_RESCALE = range(5)
 
 _STATUS = {0: "HE_OK", 1: "HE_ERR_ARG", 2: "HE_ERR_SHAPE", 3: "HE_ERR_UNSUPPORTED",
            4: "HE_ERR_NOMEM", 5: "HE_ERR_CUDA", 6: "HE_ERR_TIMEOUT"}
@@ -49,7 +49,7 @@ class he_fc_layout(ctypes.Structure):
 class he_layer_call(ctypes.Structure):
     _fields_ = [("filters", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("in_domain", ctypes.c_int),
                 ("d_out", ctypes.c_void_p), ("B", ctypes.c_uint32), ("d_share", ctypes.c_void_p),
-                ("d_share_out", ctypes.c_void_p)]
+                ("d_share_out", ctypes.c_void_p), ("d_rescaled", ctypes.c_void_p)]
 
 
 class he_plan_tuning(ctypes.Structure):
@@ -60,7 +60,7 @@ class he_plan_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("kernels_per_run", "ntt_items", "mac_items", "mac_ctas",
                                                "finish_items", "fused_items", "fc_items", "split_calls")] + \
                [("workspace_bytes", ctypes.c_uint64), ("tuning", he_plan_tuning)] + \
-               [(n, ctypes.c_uint32) for n in ("tc_items", "tc_ctas", "tc_calls")]
+               [(n, ctypes.c_uint32) for n in ("tc_items", "tc_ctas", "tc_calls", "rescale_items")]
 
 
 class he_server_config(ctypes.Structure):
@@ -371,18 +371,16 @@ def he_ntt_inverse(p: int, d_in, d_out, count: int, stream=None) -> None:
 
 
 def _calls(calls):
-    """(filters, d_in, in_domain, d_out, B[, d_share[, d_share_out]]) tuples
-    or dicts with those keys."""
+    """(filters, d_in, in_domain, d_out, B[, d_share[, d_share_out[,
+    d_rescaled]]]) tuples or dicts with those keys."""
     arr = (he_layer_call * len(calls))()
     for i, c in enumerate(calls):
         if isinstance(c, dict):
             c = (c["filters"], c["d_in"], c.get("in_domain", HE_COEFF), c["d_out"], c["B"], c.get("d_share"),
-                 c.get("d_share_out"))
+                 c.get("d_share_out"), c.get("d_rescaled"))
         f, d_in, dom, d_out, B = c[:5]
-        sh = c[5] if len(c) > 5 else None
-        shp = c[6] if len(c) > 6 else None
-        arr[i] = he_layer_call(f, _ptr(d_in), dom, _ptr(d_out), B, None if sh is None else _ptr(sh),
-                               None if shp is None else _ptr(shp))
+        extra = [(_ptr(c[k]) if len(c) > k else None) for k in (5, 6, 7)]
+        arr[i] = he_layer_call(f, _ptr(d_in), dom, _ptr(d_out), B, *extra)
     return arr
 
 
@@ -392,7 +390,8 @@ def _tuning_dict(t: he_plan_tuning) -> dict:
 
 def he_plan_create(calls) -> int:
     """calls: sequence of (filters, d_in, in_domain, d_out, B[, d_share[,
-    d_share_out]]) tuples or dicts (the shares for masked and client banks)."""
+    d_share_out[, d_rescaled]]]) tuples or dicts (the shares for masked and
+    client banks; d_rescaled for an output rescaled by the last prime)."""
     out = _vp()
     _check(lib().he_plan_create(_calls(calls), len(calls), ctypes.byref(out)))
     return out.value

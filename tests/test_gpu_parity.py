@@ -419,8 +419,11 @@ def test_plan_split_form_plain20_shapes_bit_exact():
                 H.he_plan_check(plan)
                 for c, ref in zip(calls, refs):
                     np.testing.assert_array_equal(U.from_dev(c[3]).reshape(ref.shape), ref)
-            with pytest.raises(H.HEError):
-                H.he_plan_run_phase(plan, 4, s)
+            H.he_plan_run_phase(plan, H.HE_PHASE_RESCALE, s)   # no call asks for a rescale: nothing runs
+            H.he_sync(s)
+            for bad in (-1, 5):
+                with pytest.raises(H.HEError):
+                    H.he_plan_run_phase(plan, bad, s)
         finally:
             H.he_plan_destroy(plan)
             for f in banks:

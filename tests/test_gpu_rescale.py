@@ -74,3 +74,67 @@ def test_rescale_argument_errors():
         with pytest.raises(RuntimeError):
             H.he_rescale(p, U.to_dev(np.zeros((1, 1, 256), np.uint32)), U.empty_dev((1, 1, 256)), 1,
                          torch.cuda.current_stream())
+
+
+def test_plan_rescales_every_output_in_one_kernel():
+    """d_rescaled on plain, masked Conv and FC calls of one plan: the words of
+    the oracle's rescale of each call's output (FC outputs come from the side
+    stream, so the rescale also checks the join); HE_PHASE_RESCALE reruns
+    the rescale kernel alone."""
+    H = U.he()
+    torch = U.torch_cuda()
+    N, L, T = 4096, 3, U.T
+    ps, psis = U.ring(N, L)
+    s = torch.cuda.current_stream()
+    conv = dict(ci=16, co=32, h=16, w=16)
+    lay = O.conv_layout(N, 16, 32, 16, 16)
+    fl = O.fc_layout(N, 64, 10)
+    G, Hh, P = lay["G"], lay["H"], fl["P"]
+    F = synth.conv_weights(401, "rp/F", 32, 16, 3, 3, -128, 127)
+    W = synth.fc_weights(401, "rp/W", 10, 64, -128, 127)
+    rho = synth.ints(401, "rp/rho", (32, G, N), 0, T - 1).astype(np.uint32)
+    with U.params(N, L) as p:
+        banks = [H.he_pack_filters(p, conv, F), H.he_pack_masked(p, conv, F, rho), H.he_pack_fc(p, 64, 10, W)]
+        try:
+            cts = U.to_dev(synth.residues(402, "rp/ct", (1, G, 2, L, N), ps))
+            c0 = U.to_dev(synth.residues(402, "rp/c0", (1, G, L, N), ps))
+            sh = U.to_dev(synth.ints(402, "rp/sh", (1, G, N), 0, T - 1).astype(np.uint32))
+            shp = U.to_dev(synth.ints(402, "rp/shp", (1, Hh, N), 0, T - 1).astype(np.uint32))
+            fct = U.to_dev(synth.residues(402, "rp/fct", (2, 2, L, N), ps))
+            shapes = [(1 * Hh * 2, L, N), (1 * Hh, L, N), (2 * P * 2, L, N)]
+            outs = [U.empty_dev(sh_) for sh_ in shapes]
+            rsc = [U.empty_dev((sh_[0], L - 1, N)) for sh_ in shapes]
+            calls = [(banks[0], cts, H.HE_COEFF, outs[0], 1, None, None, rsc[0]),
+                     (banks[1], c0, H.HE_COEFF, outs[1], 1, sh, shp, rsc[1]),
+                     (banks[2], fct, H.HE_COEFF, outs[2], 2, None, None, rsc[2])]
+            plan = H.he_plan_create(calls)
+            try:
+                info = H.he_plan_query(plan, 3)
+                assert info["rescale_items"] > 0
+                H.he_plan_run(plan, s)
+                H.he_sync(s)
+                H.he_plan_check(plan)
+                for o, r, sh_ in zip(outs, rsc, shapes):
+                    want = O.rescale_last_limb(U.from_dev(o).reshape(sh_), ps)
+                    np.testing.assert_array_equal(U.from_dev(r).reshape(want.shape), want)
+                for r in rsc:
+                    r.fill_(-1)
+                H.he_plan_run_phase(plan, H.HE_PHASE_RESCALE, s)
+                H.he_sync(s)
+                for o, r, sh_ in zip(outs, rsc, shapes):
+                    want = O.rescale_last_limb(U.from_dev(o).reshape(sh_), ps)
+                    np.testing.assert_array_equal(U.from_dev(r).reshape(want.shape), want)
+            finally:
+                H.he_plan_destroy(plan)
+            with U.params(N, 1) as p1:
+                f1 = H.he_pack_filters(p1, conv, F)
+                try:
+                    x1 = U.to_dev(np.zeros((1, G, 2, 1, N), np.uint32))
+                    with pytest.raises(RuntimeError):   # one limb: nothing to rescale by
+                        H.he_plan_create([(f1, x1, H.HE_COEFF, U.empty_dev((1, Hh, 2, 1, N)), 1, None, None,
+                                           U.empty_dev((Hh * 2, 1, N)))])
+                finally:
+                    H.he_filters_destroy(f1)
+        finally:
+            for b in banks:
+                H.he_filters_destroy(b)
