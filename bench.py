@@ -268,6 +268,22 @@ class Arm:
             bfly += g["npoly"] * L * (N // 2) * (N.bit_length() - 1)
         return ch_bytes, ntt_bytes, bfly
 
+    def butterflies(self, form):
+        """Algorithmic butterflies of the input-NTT kernel (every Conv call's
+        input polynomials: (N/2) log2 N each) and of the finishing kernel
+        (every split-form call: one length-N/s inverse transform per output
+        channel, limb and column: (M/2) log2 M each)."""
+        ntt, fin = 0, 0
+        for c, g, f in zip(self.calls, self.geo, form):
+            if c["kind"] != "conv":
+                continue
+            N, L, B = c["N"], c["L"], c["B"]
+            ntt += g["npoly"] * L * (N // 2) * (N.bit_length() - 1)
+            if f == 1:
+                M = g["lay"]["M"]
+                fin += c["co"] * L * 2 * B * (M // 2) * (M.bit_length() - 1)
+        return ntt, fin
+
     def mac_bytes(self, split):
         """Algorithmic bytes of one launch of the MAC phase (k_plan_mac for
         split-form calls, k_tc_mac for tensor-core calls): for every such Conv
@@ -330,6 +346,27 @@ def whole_job_rate(units_per_step, steps, world, elapsed_ms):
 def _events(n):
     import torch
     return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+
+
+def bfly_peak(torch, H, p, stream, device):
+    """Measured integer-ALU peak of the transforms' butterfly: the
+    register-only kernel behind he_bench_butterflies at full occupancy (8
+    CTAs of 256 threads per SM), 5 launches timed with CUDA events after a
+    warm-up.  Returns (butterflies/s, ms per launch, butterflies per launch)."""
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks, iters = sms * 8, 2048
+    sink = torch.empty(blocks * 256, dtype=torch.int32, device="cuda")
+    e0, e1 = _events(2)
+    with torch.cuda.stream(stream):
+        H.he_bench_butterflies(p, blocks, iters, sink, stream)
+        e0.record(stream)
+        for _ in range(5):
+            H.he_bench_butterflies(p, blocks, iters, sink, stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    n = blocks * 256 * 8 * iters
+    return n / (ms * 1e-3), ms, n
 
 
 def run_ours(args, rank, world, device):
@@ -408,6 +445,19 @@ def run_ours(args, rank, world, device):
     torch.cuda.synchronize()
     barrier()
     mac_b2b_ms = m0.elapsed_time(m1) / k_phase
+    # the finishing kernel alone (it rereads the folded sums the MAC runs
+    # above left in the plan workspace)
+    f0, f1 = _events(2)
+    with torch.cuda.stream(stream):
+        for k in range(W):
+            H.he_plan_run_phase(arm.plans[k % arm.R], H.HE_PHASE_FIN, stream)
+        f0.record(stream)
+        for k in range(k_phase):
+            H.he_plan_run_phase(arm.plans[k % arm.R], H.HE_PHASE_FIN, stream)
+        f1.record(stream)
+    torch.cuda.synchronize()
+    fin_only_ms = f0.elapsed_time(f1) / k_phase
+    peak_bfly, peak_ms, _ = bfly_peak(torch, H, next(iter(arm.params.values())), stream, device)
 
     # ---------------- headline: the plan as a CUDA graph, one replay per step
     with torch.cuda.stream(stream):
@@ -444,6 +494,7 @@ def run_ours(args, rank, world, device):
     e2e = run_e2e(arm, args, stream)
 
     ch_bytes, ntt_bytes, bfly = arm.algorithmic()
+    ntt_bfly, fin_bfly = arm.butterflies(info["form"])
     mac_bytes = arm.mac_bytes(info["form"])
     kinds = sorted({int(v) for v in info["form"] if v})
     mac_name = " + ".join({1: "k_plan_mac", 2: "k_tc_mac"}[k] for k in kinds) or "none"
@@ -491,9 +542,17 @@ def run_ours(args, rank, world, device):
                      "unit": "GB/s", "frac": roof["achieved"] / hbm, "peak_source": peak_src + " (hbm_gbs burst copy)",
                      "algorithmic_bytes": roof["algorithmic_bytes"], "avg_launch_ms": roof["avg_launch_ms"],
                      "launches": roof["launches"], "traffic": traffic},
-        "kernels": {"k_plan_ntt": {"avg_launch_ms": ntt_avg, "butterflies": bfly,
-                                   "gbfly_per_s": bfly / (ntt_avg * 1e-3) / 1e9,
+        "alu_peak": {"gbfly_per_s": peak_bfly / 1e9, "ms_per_launch": peak_ms,
+                     "how": "he_bench_butterflies: 8 independent lazy-Shoup butterfly chains per thread in "
+                            "registers, 8 CTAs x 256 threads per SM, 5 launches timed with CUDA events"},
+        "kernels": {"k_plan_ntt": {"avg_launch_ms": ntt_avg, "butterflies": ntt_bfly,
+                                   "gbfly_per_s": ntt_bfly / (ntt_avg * 1e-3) / 1e9,
+                                   "alu_frac": ntt_bfly / (ntt_avg * 1e-3) / peak_bfly,
                                    "bytes": ntt_bytes, "gbs": ntt_bytes / (ntt_avg * 1e-3) / 1e9},
+                    "k_plan_fin": {"avg_launch_ms": fin_only_ms, "butterflies": fin_bfly,
+                                   "gbfly_per_s": fin_bfly / (fin_only_ms * 1e-3) / 1e9 if fin_bfly else 0.0,
+                                   "alu_frac": fin_bfly / (fin_only_ms * 1e-3) / peak_bfly if fin_bfly else 0.0,
+                                   "timing": f"{k_phase} launches back to back (HE_PHASE_FIN), CUDA events"},
                     "mac_phase": {"kernels": mac_name, "avg_launch_ms": mac_avg, "bytes": mac_bytes, "gbs": mac_gbs,
                                    "after_ntt_ms": float(np.mean(mac_ms)),
                                    "timing": f"{k_phase} launches back to back, replicas rotated, CUDA events"},
@@ -959,11 +1018,24 @@ def oracle_layers_per_s(wl, budget_s: float, max_calls: int | None = None, start
             return units / el, done, units, O.threads()
 
 
-def cpu_baseline(wl, budget_s=15.0):
+def cpu_baseline(wl, budget_s=15.0, one_thread_s=8.0):
     v, n, u, th = oracle_layers_per_s(wl, budget_s)
-    return {"value": v, "unit": "layers/s", "cores": th, "kind": "oracle",
-            "sample": f"{n} layer calls ({u} layers) of the same workload cycled in order, ~{budget_s:.0f} s "
-                      f"budget, oracle NTT tier (OpenMP, {th} threads)"}
+    res = {"value": v, "unit": "layers/s", "cores": th, "kind": "oracle",
+           "sample": f"{n} layer calls ({u} layers) of the same workload cycled in order, ~{budget_s:.0f} s "
+                     f"budget, oracle NTT tier (OpenMP, {th} threads)"}
+    # the same oracle on one thread (beside the paper's single-thread figures),
+    # in a child process so its OpenMP runtime starts with one thread
+    code = ("import json, bench; v, n, u, th = bench.oracle_layers_per_s(bench.workload(%r), %r); "
+            "print(json.dumps([v, n, u, th]))" % (wl["name"], one_thread_s))
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300,
+                           env=dict(os.environ, OMP_NUM_THREADS="1"))
+        v1, n1, u1, th1 = json.loads(r.stdout.strip().splitlines()[-1])
+        res["one_thread"] = {"value": v1, "unit": "layers/s", "cores": th1,
+                             "sample": f"{n1} layer calls ({u1} layers), ~{one_thread_s:.0f} s budget"}
+    except Exception as e:  # reported, not fatal: the all-cores figure stands
+        res["one_thread"] = {"error": str(e)[:200]}
+    return res
 
 
 def run_reference(args, rank, world):

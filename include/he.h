@@ -346,6 +346,16 @@ he_status he_fc_client(he_params_t p, he_filters_t f, const int32_t *d_v, const 
 he_status he_rescale(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count,
                      void *stream);
 
+/* Measurement aid for the integer-ALU roofline of the transforms: launches
+ * `blocks` CTAs of 256 threads, each thread running 8 independent chains of
+ * `iters` forward butterflies (one lazy Shoup product, an add, a subtract
+ * and a correction, as in every NTT kernel here) in registers, with no
+ * memory traffic.  The caller times it (events on `stream`); butterflies =
+ * blocks * 256 * 8 * iters.  d_sink: DEVICE uint32 [blocks * 256], written.
+ * Asynchronous. */
+he_status he_bench_butterflies(he_params_t p, uint32_t blocks, uint32_t iters, uint32_t *d_sink,
+                               void *stream);
+
 /* The forward negacyclic NTT of `count` RNS polynomials (the input
  * transform of the server step, Sec. IV-A).  d_in, d_out: DEVICE uint32
  * [count][L][N]; in place if equal.  Output in the canonical NTT order
@@ -456,7 +466,9 @@ he_status he_plan_run(he_plan_t plan, void *stream);
  *   HE_PHASE_MAC (2)   the split-form MAC kernel alone (first half of 2);
  *   HE_PHASE_FINISH (3) everything after the MAC kernel (rest of 2, 3, 4, 5);
  *   HE_PHASE_RESCALE (4) the rescale kernel alone (step 5; it reads the
- *                      outputs of the phases before it).
+ *                      outputs of the phases before it);
+ *   HE_PHASE_FIN (5)   the split form's finishing kernel alone (second half
+ *                      of step 2; it reads the MAC kernel's folded sums).
  * A full run is phases 0, 1 or phases 0, 2, 3, in that order on one stream
  * (or otherwise ordered). */
 #define HE_PHASE_NTT 0
@@ -464,6 +476,7 @@ he_status he_plan_run(he_plan_t plan, void *stream);
 #define HE_PHASE_MAC 2
 #define HE_PHASE_FINISH 3
 #define HE_PHASE_RESCALE 4
+#define HE_PHASE_FIN 5
 he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream);
 
 /* What a plan launches; filled by he_plan_query. */

@@ -846,6 +846,15 @@ he_status he_rescale(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint3
     return e == cudaSuccess ? HE_OK : cuda_fail(e, "rescale");
 }
 
+he_status he_bench_butterflies(he_params_t p, uint32_t blocks, uint32_t iters, uint32_t *d_sink, void *stream) {
+    if (!p || !d_sink || blocks == 0) return fail(HE_ERR_ARG, "NULL argument or no blocks");
+    if (need_device(p) != HE_OK) return HE_ERR_ARG;
+    DeviceGuard g(p->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
+    cudaError_t e = he_launch_bfly_peak(p->ring, blocks, iters, d_sink, (cudaStream_t)stream);
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "butterfly peak");
+}
+
 he_status he_ntt_forward(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count, void *stream) {
     if (!p || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (need_device(p) != HE_OK) return HE_ERR_ARG;
@@ -1446,7 +1455,7 @@ he_status he_plan_run(he_plan_t plan, void *stream) {
 
 he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream) {
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
-    if (phase < HE_PHASE_NTT || phase > HE_PHASE_RESCALE) return fail(HE_ERR_ARG, "phase must be 0 .. 4");
+    if (phase < HE_PHASE_NTT || phase > HE_PHASE_FIN) return fail(HE_ERR_ARG, "phase must be 0 .. 5");
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
     cudaError_t e = he_launch_plan(*plan, (cudaStream_t)stream, phase);

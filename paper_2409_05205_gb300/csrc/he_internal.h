@@ -268,6 +268,7 @@ struct RescaleArgs {
     uint32_t qL, hL, N, L;  // last prime, floor(q_L / 2), ring degree, limbs of the input
 };
 RescaleArgs he_rescale_args(const RingView &r);
+cudaError_t he_launch_bfly_peak(const RingView &r, uint32_t blocks, uint32_t iters, uint32_t *sink, cudaStream_t st);
 // One plan call's rescale: npoly polynomials [L][N] at in -> [L-1][N] at out.
 struct RescaleCall {
     RescaleArgs a;

@@ -546,6 +546,30 @@ __global__ void __launch_bounds__(kThreads) k_plan_rescale(const RescaleCall *__
     for (uint32_t i = it.begin + threadIdx.x; i < it.end; i += blockDim.x) rescale_u4(c.a, c.in, c.out, i);
 }
 
+// Peak rate of the transforms' butterfly (bf_fwd: one lazy Shoup product,
+// one add, one subtract, one correction) with no memory traffic: each thread
+// runs 8 independent chains for `iters` rounds, values staying in [0, 4q).
+// The integer-ALU roofline of the NTT kernels; each thread's final words go
+// to sink[thread] so no chain is optimised away.
+__global__ void __launch_bounds__(kThreads) k_bfly_peak(uint32_t q, uint2 w, uint32_t iters, uint32_t *sink) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t q2 = 2u * q;
+    uint32_t U[8], V[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        U[i] = (t * 8u + (uint32_t)i) % q;
+        V[i] = (t * 13u + 7u * (uint32_t)i + 1u) % q;
+    }
+    for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) bf_fwd(U[i], V[i], w, q, q2);
+    }
+    uint32_t x = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x ^= U[i] ^ V[i];
+    sink[t] = x;
+}
+
 struct PackConvArgs {
     RingView r;
     const int8_t *w;   // [co][ci][fh][fw]
@@ -1430,6 +1454,14 @@ cudaError_t he_launch_client_in(const RingView &r, const int32_t *v, const int32
     return he_launch_ntt(r, ws, ws, np, false, st);
 }
 
+cudaError_t he_launch_bfly_peak(const RingView &r, uint32_t blocks, uint32_t iters, uint32_t *sink, cudaStream_t st) {
+    const LimbK &K = r.limb[0];
+    // a multiplier and its Shoup constant (2^32 mod q; any w < q will do)
+    const uint2 w = make_uint2(K.r32, K.r32s);
+    k_bfly_peak<<<blocks, kThreads, 0, st>>>(K.q, w, iters, sink);
+    return cudaGetLastError();
+}
+
 RescaleArgs he_rescale_args(const RingView &r) {
     RescaleArgs a{};
     const uint32_t qL = r.limb[r.L - 1].q;
@@ -1673,6 +1705,10 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     // kernel alone, 3 everything after the MAC kernel
     if (phase == 4) {  // the rescale kernel alone
         if (pl.n_rs) k_plan_rescale<<<pl.n_rs, kThreads, 0, st>>>(pl.d_rs_calls, pl.d_rs_items);
+        return cudaGetLastError();
+    }
+    if (phase == 5) {  // the finishing kernel alone
+        if (pl.n_fin) k_plan_fin<<<pl.n_fin, kFinThreads, pl.smem_fin, st>>>(pl.d_calls, pl.d_fin);
         return cudaGetLastError();
     }
     const bool fc = pl.n_fc && (phase == -1 || phase == 1 || phase == 3);

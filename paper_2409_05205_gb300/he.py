@@ -22,7 +22,7 @@ HE_OUT_EXTRACTED, HE_OUT_PER_CHANNEL, HE_OUT_EXTRACTED_UNFOLDED = 0, 1, 2
 HE_MAX_LIMBS = 16
 HE_MAX_INTERLEAVE = 128
 HE_DEVICE_NONE = -1
-HE_PHASE_NTT, HE_PHASE_REST, HE_PHASE_MAC, HE_PHASE_FINISH, HE_PHASE_RESCALE = range(5)
+HE_PHASE_NTT, HE_PHASE_REST, HE_PHASE_MAC, HE_PHASE_FINISH, HE_PHASE_RESCALE, HE_PHASE_FIN = range(6)
 
 _STATUS = {0: "HE_OK", 1: "HE_ERR_ARG", 2: "HE_ERR_SHAPE", 3: "HE_ERR_UNSUPPORTED",
            4: "HE_ERR_NOMEM", 5: "HE_ERR_CUDA", 6: "HE_ERR_TIMEOUT"}
@@ -107,6 +107,7 @@ _SIGS = {
     "he_conv_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
     "he_conv_layer_noalloc": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
     "he_fc_layer": [_vp, _vp, _vp, _i32, _vp, _i32, _u32, _vp],
+    "he_bench_butterflies": [_vp, _u32, _u32, _vp, _vp],
     "he_ntt_forward": [_vp, _vp, _vp, _u32, _vp],
     "he_ntt_inverse": [_vp, _vp, _vp, _u32, _vp],
     "he_plan_create": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(_vp)],
@@ -287,6 +288,12 @@ def he_pack_client(p: int, desc, p1: np.ndarray, p2: np.ndarray) -> int:
 
 def he_conv_client(p: int, f: int, d_v, d_ish, d_out, B: int, stream=None) -> None:
     _check(lib().he_conv_client(p, f, _ptr(d_v), _ptr(d_ish), _ptr(d_out), B, _stream(stream)))
+
+
+def he_bench_butterflies(p: int, blocks: int, iters: int, d_sink, stream=None) -> None:
+    """Launches the butterfly-peak kernel (blocks * 256 * 8 * iters forward
+    butterflies in registers); the caller times it."""
+    _check(lib().he_bench_butterflies(p, blocks, iters, _ptr(d_sink), _stream(stream)))
 
 
 def he_rescale(p: int, d_in, d_out, count: int, stream=None) -> None:

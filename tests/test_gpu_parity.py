@@ -421,7 +421,7 @@ def test_plan_split_form_plain20_shapes_bit_exact():
                     np.testing.assert_array_equal(U.from_dev(c[3]).reshape(ref.shape), ref)
             H.he_plan_run_phase(plan, H.HE_PHASE_RESCALE, s)   # no call asks for a rescale: nothing runs
             H.he_sync(s)
-            for bad in (-1, 5):
+            for bad in (-1, 6):
                 with pytest.raises(H.HEError):
                     H.he_plan_run_phase(plan, bad, s)
         finally:
