@@ -835,6 +835,93 @@ __global__ void __launch_bounds__(kThreads) k_fc(const ConvGeo a, const RingView
 // ---------------------------------------------------------------------------
 // plan kernels (one CTA per item; items are ordered longest first on the host)
 // ---------------------------------------------------------------------------
+// Forward stage on register bit B of 16 values: pairs (j, j + 2^B) with bit
+// B of j clear, pair j using twiddle t[j >> (B + 1)] (bf_fwd, as everywhere).
+template <int B>
+__device__ __forceinline__ void reg_stage16(uint32_t (&v)[16], const uint2 *__restrict__ t, uint32_t q, uint32_t q2) {
+#pragma unroll
+    for (int blk = 0; blk < (16 >> (B + 1)); ++blk) {
+        const uint2 w = __ldg(t + blk);
+#pragma unroll
+        for (int u = 0; u < (1 << B); ++u) bf_fwd(v[blk * (2 << B) + u], v[blk * (2 << B) + u + (1 << B)], w, q, q2);
+    }
+}
+
+// Forward negacyclic NTT of length 8192 by 512 threads in three register
+// phases.  Stage P (span 2^P) pairs i with i + 2^P (bit P of i clear) under
+// twiddle tw[2^(12-P) + (i >> (P+1))] -- the pairs, twiddles and butterfly
+// of ntt_fwd_c, so the output words are the same:
+//   A  thread t holds x[t + 512 j], j < 16: spans 4096 .. 512, the twiddles
+//      common to the whole CTA;
+//   one block-wide exchange through shared memory;
+//   B  warp w owns the 512-element sub-problem w (elements 512 w ..), lane l
+//      its elements l + 32 m: spans 256 .. 32, twiddles common to the warp;
+//   a transpose inside the warp's own shared memory (__syncwarp only);
+//   C  lane l holds elements 16 l + m: span 16 by a shuffle with lane l ^ 1,
+//      spans 8 .. 1 in registers; its 16 consecutive results leave as four
+//      128-bit stores.
+// The padded layout pidx keeps every shared-memory access conflict-free.
+__device__ __forceinline__ void ntt_fwd_8192_warp(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                                  uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q) {
+    const uint32_t q2 = 2u * q, t = threadIdx.x, w = t >> 5, l = t & 31u;
+    uint32_t v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __ldg(src + t + 512u * j);
+    reg_stage16<3>(v, tw + 1, q, q2);  // P = 12
+    reg_stage16<2>(v, tw + 2, q, q2);  // P = 11
+    reg_stage16<1>(v, tw + 4, q, q2);  // P = 10
+    reg_stage16<0>(v, tw + 8, q, q2);  // P = 9
+#pragma unroll
+    for (int j = 0; j < 16; ++j) sm[pidx(t + 512u * j)] = v[j];
+    __syncthreads();
+    const uint32_t b0 = 512u * w;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = sm[pidx(b0 + l + 32u * m)];
+    reg_stage16<3>(v, tw + 16 + w, q, q2);        // P = 8
+    reg_stage16<2>(v, tw + 32 + 2u * w, q, q2);   // P = 7
+    reg_stage16<1>(v, tw + 64 + 4u * w, q, q2);   // P = 6
+    reg_stage16<0>(v, tw + 128 + 8u * w, q, q2);  // P = 5
+    // each lane rewrites the words it read; then reads the transpose
+#pragma unroll
+    for (int m = 0; m < 16; ++m) sm[pidx(b0 + l + 32u * m)] = v[m];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = sm[pidx(b0 + 16u * l + m)];
+    {  // P = 4: element 16 l + m pairs with 16 (l ^ 1) + m
+        const uint2 w4 = __ldg(tw + 256 + 16u * w + (l >> 1));
+        const bool lower = (l & 1u) == 0u;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) {
+            const uint32_t o = __shfl_xor_sync(0xffffffffu, v[m], 1);
+            const uint32_t X = lower ? v[m] : o;  // the pair's first element
+            const uint32_t Y = lower ? o : v[m];  // its second
+            const uint32_t U = min(X, X - q2);
+            const uint32_t T = shoup_lazy(Y, w4.x, w4.y, q);
+            v[m] = lower ? U + T : U - T + q2;
+        }
+    }
+    reg_stage16<3>(v, tw + 512 + 32u * w + l, q, q2);          // P = 3
+    reg_stage16<2>(v, tw + 1024 + 64u * w + 2u * l, q, q2);    // P = 2
+    reg_stage16<1>(v, tw + 2048 + 128u * w + 4u * l, q, q2);   // P = 1
+    reg_stage16<0>(v, tw + 4096 + 256u * w + 8u * l, q, q2);   // P = 0
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst + b0 + 16u * l);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        d4[k] = make_uint4(red_4q(v[4 * k], q2, q), red_4q(v[4 * k + 1], q2, q), red_4q(v[4 * k + 2], q2, q),
+                           red_4q(v[4 * k + 3], q2, q));
+}
+
+// The forward transform of one plan input polynomial: the three-phase
+// kernel above for N = 8192 with 512 threads, else the pass-by-pass one.
+__device__ __forceinline__ void plan_fwd_ntt(const uint32_t *src, uint32_t *dst, uint32_t logN, const uint2 *tw,
+                                             const LimbK &K, uint4 *smem4) {
+    if (logN == 13 && blockDim.x == 512) {
+        ntt_fwd_8192_warp(src, dst, reinterpret_cast<uint32_t *>(smem4), tw, K.q);
+        return;
+    }
+    ntt_body(src, dst, logN, tw, K, false, smem4);
+}
+
 // 512 threads: a polynomial's transform is the CTA's work, and its passes
 // have 512 .. 2048 groups, so more threads shorten every pass; two CTAs per SM
 // keep a plain-20 inference's 276 transforms resident at once.
@@ -855,12 +942,12 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
         const uint32_t G = cd.g.G >> 1, gz = (it.poly / L) % (2u * G), b = it.poly / (L * 2u * G);
         const size_t row = (size_t)b * G + (gz < G ? gz : gz - G);
         if (cd.msrc == 1u && gz >= G) {
-            ntt_body(cd.src_b + row * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, false, smem4);
+            plan_fwd_ntt(cd.src_b + row * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, smem4);
         } else if (cd.msrc == 1u && cd.a_ntt) {
             const uint4 *s4 = reinterpret_cast<const uint4 *>(cd.x_coeff + (row * L + l) * N);
             for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) reinterpret_cast<uint4 *>(dst)[i] = __ldg(s4 + i);
         } else if (cd.msrc == 1u) {
-            ntt_body(cd.x_coeff + (row * L + l) * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, false, smem4);
+            plan_fwd_ntt(cd.x_coeff + (row * L + l) * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, smem4);
         } else {
             const int32_t *src = reinterpret_cast<const int32_t *>(gz < G ? cd.x_coeff : cd.src_b) + row * N;
             uint32_t *a = reinterpret_cast<uint32_t *>(smem4);
@@ -870,7 +957,7 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
         }
         return;
     }
-    ntt_body(cd.x_coeff + (size_t)it.poly * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, false, smem4);
+    plan_fwd_ntt(cd.x_coeff + (size_t)it.poly * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, smem4);
 }
 
 // Fused FC items of a plan: item.poly = (jp * L + l) * ncols + column.
