@@ -1109,7 +1109,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             const uint32_t ncol = msrc ? 1u : 2u;
             cd.split = (tu.split && c.B == 1 && split_mac_ok(lay.s, g.G) &&
                         ((ncol * g.G) << f->logTS) <= kMacXWords &&
-                        (size_t)std::min(lay.s, f->desc.co) * fin_stride(lay.M) * 4u <= 200u * 1024u)
+                        (size_t)std::min(lay.s, f->desc.co) * fin_stride(lay.M, lay.s) * 4u <= 200u * 1024u)
                            ? 1u
                            : 0u;
             g.cs = split_cs(lay.s, g.G);
@@ -1415,7 +1415,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         for (auto &it : fin) {
             items.push_back(it.second);
             const CallDesc &cd = descs[it.second.call];
-            pl->smem_fin = std::max(pl->smem_fin, (size_t)std::min(cd.g.s, cd.g.co) * fin_stride(cd.g.M) * 4u);
+            pl->smem_fin = std::max(pl->smem_fin, (size_t)std::min(cd.g.s, cd.g.co) * fin_stride(cd.g.M, cd.g.s) * 4u);
         }
         pl->n_fin = (uint32_t)items.size();
         e = upload(&pl->d_fin, items);

@@ -247,9 +247,17 @@ static_assert(sizeof(MacDesc) == 64, "MacDesc is one 64-byte bulk copy");
 __host__ __device__ __forceinline__ size_t mac_smem_bytes() {
     return kMacHdrBytes + (size_t)2 * kMacXWords * 4u + (size_t)kMacStages * kMacStageWords * 4u;
 }
-// polynomial stride (words) of the finishing kernel: padded and odd, so the
-// transposed reads of the extraction hit distinct banks
-__host__ __device__ __forceinline__ uint32_t fin_stride(uint32_t M) { return padded_words(M) | 1u; }
+// polynomial stride (words) of the finishing kernel's s rows of length M
+// (>= padded_words(M)): the extraction reads slot e of the s rows
+// interleaved (k -> row k mod s, slot k / s), so a warp touches 32/s
+// consecutive slots of each of s rows (s <= 32) or one slot of 32 rows.
+// A stride of 32/s mod 32 (odd for s >= 32) puts those reads in 32
+// distinct banks.
+__host__ __device__ __forceinline__ uint32_t fin_stride(uint32_t M, uint32_t s) {
+    const uint32_t b = padded_words(M);
+    if (s >= 32u || s <= 1u) return b | 1u;
+    return b + (((32u / s) - (b & 31u)) & 31u);
+}
 
 struct NttItem {
     uint32_t call, poly;      // conv: poly index within the call's [npoly][L][N] input;

@@ -1272,7 +1272,7 @@ __device__ __forceinline__ uint32_t he_log2_dev(uint32_t x) { return 31u - __clz
 // extracted polynomial (coalesced; classes no channel uses are 0).
 constexpr int kFinThreads = 256;
 
-__global__ void __launch_bounds__(kFinThreads, 4) k_plan_fin(const CallDesc *__restrict__ calls,
+__global__ void __launch_bounds__(kFinThreads, 3) k_plan_fin(const CallDesc *__restrict__ calls,
                                                       const ChanItem *__restrict__ items) {
     extern __shared__ uint4 smem4[];
     const ChanItem it = items[blockIdx.x];
@@ -1283,7 +1283,7 @@ __global__ void __launch_bounds__(kFinThreads, 4) k_plan_fin(const CallDesc *__r
     const uint32_t N = cd.g.N, co = cd.g.co, s = cd.g.s, logs = cd.g.logs, M = cd.g.M, logM = cd.g.logM,
                    mult = cd.g.mult;
     const uint32_t sh = min(s, co - h * s);
-    const uint32_t PS = fin_stride(M);
+    const uint32_t PS = fin_stride(M, s);
     // sh*M words, 4 at a time, 8 loads in flight per thread
     const uint32_t nq = (sh << logM) >> 2;
     if (cd.zt) {
