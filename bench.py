@@ -180,19 +180,29 @@ class Arm:
                 self.geo.append(dict(lay=fl, nin=B * 2 * L * N, nout=B * fl["P_fc"] * 2 * L * N,
                                      npoly=B * 2, wbytes=fl["P_fc"] * L * N * 4))
         self.models = [Model(H, self, r) for r in range(replicas)]
-        # inputs / NTT buffers / outputs per replica (device resident)
-        self.x, self.xn, self.y = [], [], []
+        # inputs / NTT buffers / outputs per replica (device resident); every
+        # layer's input (output) is a view into one contiguous buffer, so a
+        # step moves its inputs and outputs with one copy each way
+        self.x, self.xn, self.y, self.xall, self.yall = [], [], [], [], []
+        offs_in = np.cumsum([0] + [g["nin"] for g in self.geo])
+        offs_out = np.cumsum([0] + [g["nout"] for g in self.geo])
         for r in range(replicas):
+            xall = torch.empty(int(offs_in[-1]), dtype=torch.int32, device="cuda")
+            yall = torch.empty(int(offs_out[-1]), dtype=torch.int32, device="cuda")
             xs, xns, ys = [], [], []
             for i, (c, g) in enumerate(zip(self.calls, self.geo)):
                 N, L = c["N"], c["L"]
                 a = synth.residues(SEED + 10 * r, f"x{i}", (g["nin"] // (L * N), L, N), primes[(N, L)])
-                xs.append(torch.from_numpy(a.view(np.int32).ravel()).cuda())
+                xv = xall[int(offs_in[i]):int(offs_in[i + 1])]
+                xv.copy_(torch.from_numpy(a.view(np.int32).ravel()))
+                xs.append(xv)
                 xns.append(torch.empty(g["nin"], dtype=torch.int32, device="cuda"))
-                ys.append(torch.empty(g["nout"], dtype=torch.int32, device="cuda"))
+                ys.append(yall[int(offs_out[i]):int(offs_out[i + 1])])
             self.x.append(xs)
             self.xn.append(xns)
             self.y.append(ys)
+            self.xall.append(xall)
+            self.yall.append(yall)
         self.R = replicas
         # layers per step: one per call and ciphertext of the batch
         self.units = sum(c["B"] for c in self.calls)
@@ -571,39 +581,64 @@ def run_ours(args, rank, world, device):
     return res
 
 
-def run_e2e(arm, args, stream):
-    """Per step: H2D of the 20 layer inputs from pinned host memory, the plan
-    (graph replay), D2H of the 20 extracted outputs into pinned host memory."""
-    torch = arm.torch
-    K = max(20, min(args.steps, 2000))
-    hx = [torch.empty(g["nin"], dtype=torch.int32, pin_memory=True) for g in arm.geo]
-    hy = [torch.empty(g["nout"], dtype=torch.int32, pin_memory=True) for g in arm.geo]
-    for i in range(len(hx)):
-        hx[i].copy_(arm.x[0][i].cpu())
-    h2d = sum(g["nin"] * 4 for g in arm.geo)
-    d2h = sum(g["nout"] * 4 for g in arm.geo)
+def pipelined_steps(torch, R, K, upload, replay, download, stream):
+    """K end-to-end steps, step k on replica k % R, timed on the wall clock:
+    the upload of step k's inputs (H2D stream), its graph (`stream`) and the
+    download of its result (D2H stream) are ordered by events, so step k+1's
+    upload and step k-1's download overlap step k's graph.  A replica's input
+    buffer is rewritten only after its previous graph has read it, and its
+    output buffer only after its previous download.  Returns seconds."""
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(R)]
+    ev_comp = [torch.cuda.Event() for _ in range(R)]
+    ev_out = [torch.cuda.Event() for _ in range(R)]
 
-    def step(r):
-        for i in range(len(arm.calls)):
-            arm.x[r][i].copy_(hx[i], non_blocking=True)
-        arm.graphs[r].replay()
-        for i in range(len(arm.calls)):
-            hy[i].copy_(arm.y[r][i], non_blocking=True)
+    def run(n):
+        for k in range(n):
+            r = k % R
+            if k >= R:
+                s_in.wait_event(ev_comp[r])
+            with torch.cuda.stream(s_in):
+                upload(r)
+            ev_in[r].record(s_in)
+            stream.wait_event(ev_in[r])
+            if k >= R:
+                stream.wait_event(ev_out[r])
+            with torch.cuda.stream(stream):
+                replay(r)
+            ev_comp[r].record(stream)
+            s_out.wait_event(ev_comp[r])
+            with torch.cuda.stream(s_out):
+                download(r)
+            ev_out[r].record(s_out)
 
-    with torch.cuda.stream(stream):
-        for k in range(3):
-            step(k % arm.R)
+    run(3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for k in range(K):
-            step(k % arm.R)
+    run(K)
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def run_e2e(arm, args, stream):
+    """Per step: H2D of every layer input from pinned host memory (one copy:
+    the inputs are contiguous), the plan (graph replay), D2H of every
+    extracted output into pinned host memory (one copy)."""
+    torch = arm.torch
+    K = max(20, min(args.steps, 2000))
+    hx = torch.empty(arm.xall[0].numel(), dtype=torch.int32, pin_memory=True)
+    hy = [torch.empty(arm.yall[0].numel(), dtype=torch.int32, pin_memory=True) for _ in range(arm.R)]
+    hx.copy_(arm.xall[0].cpu())
+    h2d = hx.numel() * 4
+    d2h = hy[0].numel() * 4
+    dt = pipelined_steps(torch, arm.R, K, lambda r: arm.xall[r].copy_(hx, non_blocking=True),
+                         lambda r: arm.graphs[r].replay(), lambda r: hy[r].copy_(arm.yall[r], non_blocking=True),
+                         stream)
     return {"value": arm.units * K / dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": K,
-            "how": "per step: 20 H2D copies from pinned host memory, the plan (CUDA graph), "
-                   "20 D2H copies of the extracted outputs; one stream, wall clock"}
+            "how": "per step: one H2D copy of every layer input (contiguous) from pinned host memory, the plan "
+                   "(CUDA graph), one D2H copy of every extracted output into pinned memory; uploads, graphs and "
+                   "downloads on three streams ordered by events, so consecutive steps overlap; wall clock"}
 
 
 # ----------------------------------------------------------------------------
@@ -656,9 +691,16 @@ class MaskedArm:
             return torch.from_numpy(np.ascontiguousarray(a).view(np.int32).ravel()).cuda()
 
         self.R = replicas
-        self.srv, self.cli, self.io = [], [], []
+        self.srv, self.cli, self.io, self.inall, self.outall = [], [], [], [], []
+        # c0, sh, sh' of every layer are views into one input buffer and every
+        # c0^r into one output buffer, so a step moves each with one copy
+        in_words = [int(np.prod(g["c0"]) + np.prod(g["sh"]) + np.prod(g["shp"])) for g in self.geo]
+        out_words = [int(np.prod(g["out"])) for g in self.geo]
         for r in range(replicas):
             srv, cli, io = [], [], []
+            inall = torch.empty(sum(in_words), dtype=torch.int32, device="cuda")
+            outall = torch.empty(sum(out_words), dtype=torch.int32, device="cuda")
+            oi = oo = 0
             for i, (c, g) in enumerate(zip(self.calls, self.geo)):
                 p, ps = self.params[(c["N"], c["L"])], primes[(c["N"], c["L"])]
                 rho = synth.ints(SEED + r, f"rho{i}", g["rho"], 0, t - 1).astype(np.uint32)
@@ -674,18 +716,29 @@ class MaskedArm:
                     cli.append(H.he_pack_fc_client(p, c["n_in"], c["n_out"], p1, p2))
                 L, N = c["L"], c["N"]
                 o_l1 = (g["npoly_out"], L - 1, N)
-                io.append(dict(
-                    c0=dev(synth.residues(SEED + 10 * r, f"c0_{i}", g["c0"], ps)),
-                    sh=dev(synth.ints(SEED + 10 * r, f"sh{i}", g["sh"], 0, t - 1).astype(np.uint32)),
-                    shp=dev(synth.ints(SEED + 10 * r, f"shp{i}", g["shp"], 0, t - 1).astype(np.uint32)),
-                    v=dev(synth.ints(SEED + 10 * r, f"v{i}", g["sh"], -1, 1).astype(np.int32)),
-                    ish=dev(synth.ints(SEED + 10 * r, f"ish{i}", g["sh"], -8, t).astype(np.int32)),
-                    out=torch.empty(int(np.prod(g["out"])), dtype=torch.int32, device="cuda"),
-                    out1=torch.empty(int(np.prod(g["out"])), dtype=torch.int32, device="cuda"),
-                    outr=torch.empty(int(np.prod(o_l1)), dtype=torch.int32, device="cuda")))
+
+                def view(a):
+                    nonlocal oi
+                    v = inall[oi:oi + a.size]
+                    v.copy_(torch.from_numpy(np.ascontiguousarray(a).view(np.int32).ravel()))
+                    oi += a.size
+                    return v
+
+                x = dict(c0=view(synth.residues(SEED + 10 * r, f"c0_{i}", g["c0"], ps)),
+                         sh=view(synth.ints(SEED + 10 * r, f"sh{i}", g["sh"], 0, t - 1).astype(np.uint32)),
+                         shp=view(synth.ints(SEED + 10 * r, f"shp{i}", g["shp"], 0, t - 1).astype(np.uint32)),
+                         v=dev(synth.ints(SEED + 10 * r, f"v{i}", g["sh"], -1, 1).astype(np.int32)),
+                         ish=dev(synth.ints(SEED + 10 * r, f"ish{i}", g["sh"], -8, t).astype(np.int32)),
+                         out=outall[oo:oo + out_words[i]],
+                         out1=torch.empty(out_words[i], dtype=torch.int32, device="cuda"),
+                         outr=torch.empty(int(np.prod(o_l1)), dtype=torch.int32, device="cuda"))
+                oo += out_words[i]
+                io.append(x)
             self.srv.append(srv)
             self.cli.append(cli)
             self.io.append(io)
+            self.inall.append(inall)
+            self.outall.append(outall)
         self.units = sum(c["B"] for c in self.calls)
         torch.cuda.synchronize()
 
@@ -879,36 +932,16 @@ def run_masked(args, rank, world, device):
     if world > 1:
         srv_ms, = max_over_ranks([srv_ms], "cuda")
 
-    # e2e: per step H2D of every layer's c0, sh and sh' from pinned host
-    # memory, the server plan (graph), D2H of every c0^r
-    keys = ("c0", "sh", "shp")
-    hx = [{k: torch.empty_like(x[k], device="cpu").pin_memory() for k in keys} for x in arm.io[0]]
-    hy = [torch.empty_like(x["out"], device="cpu").pin_memory() for x in arm.io[0]]
-    for i, x in enumerate(arm.io[0]):
-        for k in keys:
-            hx[i][k].copy_(x[k].cpu())
-    h2d = sum(hx[i][k].numel() * 4 for i in range(nl) for k in keys)
-    d2h = sum(y.numel() * 4 for y in hy)
-
-    def e2e_step(r):
-        for i, x in enumerate(arm.io[r]):
-            for k in keys:
-                x[k].copy_(hx[i][k], non_blocking=True)
-        g_srv[r].replay()
-        for i, x in enumerate(arm.io[r]):
-            hy[i].copy_(x["out"], non_blocking=True)
-
-    with torch.cuda.stream(stream):
-        for k in range(3):
-            e2e_step(k % arm.R)
-    torch.cuda.synchronize()
+    # e2e: per step one H2D copy of every layer's c0, sh and sh' (contiguous)
+    # from pinned host memory, the server plan (graph), one D2H copy of every c0^r
+    hx = torch.empty(arm.inall[0].numel(), dtype=torch.int32, pin_memory=True)
+    hy = [torch.empty(arm.outall[0].numel(), dtype=torch.int32, pin_memory=True) for _ in range(arm.R)]
+    hx.copy_(arm.inall[0].cpu())
+    h2d, d2h = hx.numel() * 4, hy[0].numel() * 4
     ke = max(20, min(K, 2000))
-    t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for k in range(ke):
-            e2e_step(k % arm.R)
-    torch.cuda.synchronize()
-    e2e_dt = time.perf_counter() - t0
+    e2e_dt = pipelined_steps(torch, arm.R, ke, lambda r: arm.inall[r].copy_(hx, non_blocking=True),
+                             lambda r: g_srv[r].replay(), lambda r: hy[r].copy_(arm.outall[r], non_blocking=True),
+                             stream)
 
     mac_bytes = arm.mac_bytes(info["form"])
     mac_gbs = mac_bytes / (mac_ms * 1e-3) / 1e9
@@ -953,8 +986,9 @@ def run_masked(args, rank, world, device):
         "plan": {k: v for k, v in info.items() if k not in ("split", "form")},
         "e2e": {"value": arm.units * ke / e2e_dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": ke,
-                "how": "per step: H2D of every layer's c0, sh and sh' from pinned host memory, the server "
-                       "plan (CUDA graph), D2H of every c0^r; one stream, wall clock"},
+                "how": "per step: one H2D copy of every layer's c0, sh and sh' (contiguous) from pinned host "
+                       "memory, the server plan (CUDA graph), one D2H copy of every c0^r; uploads, graphs and "
+                       "downloads on three streams ordered by events, so consecutive steps overlap; wall clock"},
         "gpu_launches": info["kernels_per_run"] * K,
         "clocks": clk,
     }
