@@ -163,8 +163,10 @@ he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w,
  * 64, the bank is laid out per (limb, block, 64 channels) as a K-major
  * matrix, and plan calls of up to 8 ciphertexts on it run the channel sum
  * on the tensor cores (exact: 8-bit limbs in fp16, fp32 sums below 2^24).
- * Single calls (he_conv_layer) and plan calls of more than 8 ciphertexts
- * read the same bank with the scalar kernels.  Any other B or shape gives
+ * Such a bank also keeps the weights in he_pack_filters' layout (twice the
+ * memory): single calls (he_conv_layer), plan calls of more than 8
+ * ciphertexts and plan calls below the tuning's tc_min_batch read that copy
+ * with the scalar kernels.  Any other B or shape gives
  * he_pack_filters' bank.  Results are bit-identical either way.  Blocking. */
 he_status he_pack_filters_for_batch(he_params_t p, const he_conv_desc *d, const int8_t *w,
                                     uint32_t B, he_filters_t *out);
@@ -432,12 +434,17 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *   mac_ctas_per_sm  persistent MAC CTAs per SM: 1 or 2 (default 2).
  *   fused_max_nj     the most ciphertext columns one fused-form CTA handles:
  *                    2, 4, 8 or 16 (default 16; fewer also when shared
- *                    memory requires). */
+ *                    memory requires).
+ *   tc_min_batch     the fewest ciphertexts of a call on a tensor-core bank
+ *                    that take the tensor-core MAC kernel: 1, 2, 4 or 8
+ *                    (default 2); smaller calls read the bank's scalar-layout
+ *                    copy like an ordinary bank. */
 typedef struct {
     uint32_t split;
     uint32_t mac_item_kb;
     uint32_t mac_ctas_per_sm;
     uint32_t fused_max_nj;
+    uint32_t tc_min_batch;
 } he_plan_tuning;
 
 /* The default tuning. */

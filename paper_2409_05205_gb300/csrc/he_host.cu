@@ -430,6 +430,10 @@ static he_status pack_conv(he_params_t p, const he_conv_desc *d, const int8_t *w
     e = cudaMalloc(&d_w, wbytes);
     if (e == cudaSuccess) e = cudaMemcpy(d_w, w, wbytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = he_launch_pack_conv(p->ring, d_w, *d, lay, f->logTS, f->lcs, f->tc, f->bank, 0);
+    // a tensor-core bank keeps the scalar layout too: batch-1 calls stream it
+    // through the split MAC kernel at twice the tensor-core kernel's speed
+    if (e == cudaSuccess && f->tc) e = cudaMalloc(&f->bank_s, f->bank_bytes);
+    if (e == cudaSuccess && f->tc) e = he_launch_pack_conv(p->ring, d_w, *d, lay, f->logTS, f->lcs, 0u, f->bank_s, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_w);
     if (e != cudaSuccess) {
@@ -644,6 +648,7 @@ void he_filters_destroy(he_filters_t f) {
     if (!f) return;
     DeviceGuard g(f->p->device);
     cudaFree(f->bank);
+    cudaFree(f->bank_s);
     cudaFree(f->bias);
     delete f;
 }
@@ -673,7 +678,8 @@ he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int
         if (e != cudaSuccess) return cuda_fail(e, "input NTT");
         x = (const uint32_t *)p->ws;
     }
-    cudaError_t e = he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, f->tc, f->bank, x, d_out, out_mode, B, st);
+    cudaError_t e = f->bank_s ? he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, 0u, f->bank_s, x, d_out, out_mode, B, st)
+                              : he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, f->tc, f->bank, x, d_out, out_mode, B, st);
     if (e != cudaSuccess) return cuda_fail(e, "conv kernel");
     return HE_OK;
 }
@@ -881,6 +887,7 @@ he_status he_plan_tuning_default(he_plan_tuning *t) {
     t->mac_item_kb = 128;
     t->mac_ctas_per_sm = 2;
     t->fused_max_nj = 16;
+    t->tc_min_batch = 2;
     return HE_OK;
 }
 
@@ -892,6 +899,8 @@ he_status check_tuning(const he_plan_tuning &t) {
     if (t.mac_ctas_per_sm != 1 && t.mac_ctas_per_sm != 2) return fail(HE_ERR_ARG, "tuning: mac_ctas_per_sm must be 1 or 2");
     if (t.fused_max_nj != 2 && t.fused_max_nj != 4 && t.fused_max_nj != 8 && t.fused_max_nj != 16)
         return fail(HE_ERR_ARG, "tuning: fused_max_nj must be 2, 4, 8 or 16");
+    if (t.tc_min_batch != 1 && t.tc_min_batch != 2 && t.tc_min_batch != 4 && t.tc_min_batch != 8)
+        return fail(HE_ERR_ARG, "tuning: tc_min_batch must be 1, 2, 4 or 8");
     return HE_OK;
 }
 }  // namespace
@@ -1089,6 +1098,12 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             if (fold_smem_bytes(2, lay.M) > 192u * 1024u)
                 return fail(HE_ERR_UNSUPPORTED, "call %u: N/s = %u too long for a plan", i, lay.M);
             cd.kind = HE_KIND_CONV;
+            // a tensor-core bank: the tensor-core MAC kernel for tc_min_batch
+            // to 8 ciphertexts (up to 16 columns), then the finishing kernel;
+            // other batches read its scalar-layout copy like any bank
+            const bool use_tc = f->tc && g.ncols <= kTcCols && c.B >= tu.tc_min_batch;
+            if (f->tc && !use_tc && f->bank_s) g.bank = f->bank_s;
+            const uint32_t btc = f->tc && (use_tc || !f->bank_s) ? 1u : 0u;  // the layout g.bank has
             g.G = msrc ? 2u * lay.G : lay.G;  // groups the channel sum runs over
             g.H = lay.H;
             g.s = lay.s;
@@ -1116,12 +1131,10 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             g.nc = std::min(f->desc.co, std::max(1u, (tu.mac_item_kb * 256u) / (g.G << f->logTS)));
             // bank interleave and tile must match the MAC kernel's
             if (cd.split && ((1u << f->lcs) != g.cs || f->logTS != split_tile_log(f->lcs))) cd.split = 0;
-            // a tensor-core bank: the tensor-core MAC kernel for up to 16
-            // columns, then the finishing kernel; more columns take the fused form
-            g.tc = f->tc;
-            if (f->tc) {
+            g.tc = btc;
+            if (btc) {  // the tensor-core layout: its MAC kernel, or the fused form beyond 16 columns
                 cd.split = 0;
-                cd.zt = g.ncols <= kTcCols ? 1u : 0u;
+                cd.zt = use_tc ? 1u : 0u;
             }
             // the fused form covers columns in tiles of nj >= 2 (plain calls have 2B columns)
             if (msrc && !cd.split && (g.ncols % cd.nj) != 0)

@@ -340,6 +340,8 @@ struct he_filters_s {
     uint32_t nc;      // split MAC: channels per work item
     he_fc_layout fl;
     uint32_t *bank;   // conv: [co][L][G][N]; fc: [P][L][N]; NTT domain, pre-scaled
+    uint32_t *bank_s; // tensor-core banks: the same weights in the scalar layout (logTS, lcs) for single
+                      // calls and small batches; else nullptr
     uint32_t *bias;   // fc: [L][n_out] Delta_Q * B mod q_l, or nullptr
     size_t bank_bytes;
 };

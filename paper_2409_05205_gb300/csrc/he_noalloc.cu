@@ -84,7 +84,8 @@ extern "C" he_status he_conv_layer_noalloc(he_params_t p, he_filters_t f, const 
         if (e != cudaSuccess) return he_fail(HE_ERR_CUDA, cudaGetErrorString(e));
         x = scratch;
     }
-    cudaError_t e = he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, f->tc, f->bank, x, d_out, out_mode, B, st);
+    cudaError_t e = f->bank_s ? he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, 0u, f->bank_s, x, d_out, out_mode, B, st)
+                              : he_launch_conv(p->ring, f->desc, lay, f->logTS, f->lcs, f->tc, f->bank, x, d_out, out_mode, B, st);
     if (e != cudaSuccess) return he_fail(HE_ERR_CUDA, cudaGetErrorString(e));
     return HE_OK;
 }

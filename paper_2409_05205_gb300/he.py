@@ -53,7 +53,8 @@ class he_layer_call(ctypes.Structure):
 
 
 class he_plan_tuning(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_uint32) for n in ("split", "mac_item_kb", "mac_ctas_per_sm", "fused_max_nj")]
+    _fields_ = [(n, ctypes.c_uint32) for n in ("split", "mac_item_kb", "mac_ctas_per_sm", "fused_max_nj",
+                                               "tc_min_batch")]
 
 
 class he_plan_info(ctypes.Structure):

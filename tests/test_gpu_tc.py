@@ -70,21 +70,24 @@ def test_tensor_core_plan_matches_oracle(N, L, ci, co, hw, B, dom):
             d_in2, d_out2 = U.to_dev(x2), U.empty_dev(ref2.shape)
             calls = [(f, d_in, H.HE_NTT if dom == "ntt" else H.HE_COEFF, d_out, B),
                      (f2, d_in2, H.HE_COEFF, d_out2, 1)]
-            plan = H.he_plan_create(calls)
-            try:
-                info = H.he_plan_query(plan, len(calls))
-                assert info["tc_calls"] == 1 and info["tc_items"] > 0 and info["form"][0] == 2
-                s = torch.cuda.current_stream()
-                for _ in range(2):  # repeatable: every word rewritten each run
-                    d_out.fill_(-1)
-                    d_out2.fill_(-1)
-                    H.he_plan_run(plan, s)
-                    H.he_sync(s)
-                    H.he_plan_check(plan)
-                    np.testing.assert_array_equal(U.from_dev(d_out).reshape(ref.shape), ref)
-                    np.testing.assert_array_equal(U.from_dev(d_out2).reshape(ref2.shape), ref2)
-            finally:
-                H.he_plan_destroy(plan)
+            # the tensor-core kernel at every batch size (tc_min_batch = 1), then
+            # batches below 4 on the bank's scalar-layout copy (split or fused form)
+            for tmin in (1, 4):
+                plan = H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), tc_min_batch=tmin))
+                try:
+                    info = H.he_plan_query(plan, len(calls))
+                    assert (info["form"][0] == 2) == (B >= tmin) and (info["tc_calls"] == 1) == (B >= tmin)
+                    s = torch.cuda.current_stream()
+                    for _ in range(2):  # repeatable: every word rewritten each run
+                        d_out.fill_(-1)
+                        d_out2.fill_(-1)
+                        H.he_plan_run(plan, s)
+                        H.he_sync(s)
+                        H.he_plan_check(plan)
+                        np.testing.assert_array_equal(U.from_dev(d_out).reshape(ref.shape), ref)
+                        np.testing.assert_array_equal(U.from_dev(d_out2).reshape(ref2.shape), ref2)
+                finally:
+                    H.he_plan_destroy(plan)
         finally:
             H.he_filters_destroy(f)
             H.he_filters_destroy(f2)
