@@ -30,6 +30,7 @@ cores) on a bounded sample of the same layers.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import subprocess
@@ -1221,12 +1222,14 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
             H.he_server_wait(srv, t, 600000)
             models[mi]["pool"].put(outs)
     waits = [0.0]
+    late = []  # how late each submission left the load generator, s
 
     def drive(times, which):
         """Submits each request at its scheduled time (its own thread) and
         waits for them in order; returns the latencies from the scheduled
         arrivals, per model, the layers done and the first / last times."""
         done_q = queue.Queue()
+        late.clear()
 
         def submitter(t0):
             for k, (ta, mi) in enumerate(zip(times, which)):
@@ -1238,6 +1241,7 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
                 outs = m["pool"].get()
                 waits[0] = max(waits[0], time.monotonic() - w0)
                 tk = H.he_server_submit(srv, mids[int(mi)], m["ins"][k % input_sets], outs)
+                late.append(time.monotonic() - (t0 + ta))
                 done_q.put((tk, int(mi), outs, (t0 + ta) * 1e3))
             done_q.put(None)
 
@@ -1271,7 +1275,11 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
     clocks = ClockSampler(device)
     clocks.start()
     time.sleep(0.3)
-    lat_sched, per_model, layers_done, t0, t_last = drive(times, which)
+    gc.disable()  # no collector pauses inside the load generator's schedule
+    try:
+        lat_sched, per_model, layers_done, t0, t_last = drive(times, which)
+    finally:
+        gc.enable()
     clk = clocks.stop()
     elapsed_s = (t_last - t0 * 1e3) * 1e-3
     rep = H.he_server_report(srv)
@@ -1290,6 +1298,9 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
                                    "from": "entry into the layer's queue to its outputs on the host"},
               "batches": nb, "mean_batch": ncalls / max(1, nb), "hbm_bytes_peak": rep["bytes_peak"],
               "failed": rep["failed"], "max_submit_wait_s": waits[0],
+              "submit_late_ms": {"p99": pct(late, 99) * 1e3 if late else None,
+                                 "max": max(late) * 1e3 if late else None,
+                                 "what": "submission time minus scheduled arrival, in the load generator"},
               "server": {"max_batch": max_batch, "streams": streams, "max_inflight": max_inflight}}
     return {"n": n, "elapsed_s": elapsed_s, "value": layers_done / elapsed_s, "report": report, "clocks": clk,
             "warm_requests": 2 * 15 * len(models) + nw}

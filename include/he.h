@@ -565,7 +565,9 @@ he_status he_server_create(const he_server_config *cfg, he_server_t *out);
 /* Registers a model: `layers` are its banks in order (Conv and FC, one
  * params).  The banks must outlive the server.  *model_id is the handle.
  * HE_ERR_ARG if a layer's batch-1 buffers (twice its input plus output
- * words) do not fit hbm_budget_bytes. */
+ * words) do not fit hbm_budget_bytes.  Blocking: builds one lane (batch
+ * buffers and plan) per layer and batch size (powers of two up to
+ * max_batch) while the budget allows; the others are built on demand. */
 he_status he_server_add_model(he_server_t s, const he_filters_t *layers, uint32_t nlayers,
                               uint32_t *model_id);
 /* Queues one inference.  h_in[i]: HOST uint32 input of layer i, the layout

@@ -357,6 +357,12 @@ he_status he_server_add_model(he_server_t s, const he_filters_t *layers, uint32_
     std::lock_guard<std::mutex> lk(s->mu);
     *model_id = (uint32_t)s->models.size();
     s->models.push_back(std::move(m));
+    // one lane (batch buffers and plan) per layer and batch size, built now
+    // while the budget allows, so that serving does not build them on the
+    // request path (a plan build allocates and copies synchronously)
+    for (uint32_t b = 1; b <= s->cfg.max_batch; b *= 2)
+        for (uint32_t i = 0; i < nlayers; ++i)
+            if (!get_lane(s, *model_id, i, b)) return HE_OK;  // budget reached: the rest on demand
     return HE_OK;
 }
 
