@@ -143,6 +143,34 @@ void he_params_destroy(he_params_t p);
 he_status he_conv_layout_query(he_params_t p, const he_conv_desc *d, he_conv_layout *out);
 he_status he_fc_layout_query(he_params_t p, uint32_t n_in, uint32_t n_out, he_fc_layout *out);
 
+/* Operation counts of one layer call on this path, per RNS limb (the
+ * quantities of Table I (Conv) and Table III (FC)), from the same layout the
+ * kernels use; host only, no device needed.
+ *   form:      HE_FORM_PLAIN (ciphertext x plaintext, both polynomials of
+ *              each ciphertext), HE_FORM_MASKED (the masked server step of
+ *              Alg. 1 / Alg. 2), HE_FORM_CLIENT (the client step).
+ *   in_domain: HE_COEFF or HE_NTT for the input ciphertext polynomials (the
+ *              client step's inputs are always coefficient-domain integers).
+ *   B:         ciphertexts in the call.
+ * Outputs the extracted-output form (HE_OUT_EXTRACTED): Conv inverse
+ * transforms are the valid-slot-only ones of length N/s, FC ones full length.
+ * HE_ERR_SHAPE / HE_ERR_ARG as the layout queries. */
+#define HE_FORM_PLAIN 0
+#define HE_FORM_MASKED 1
+#define HE_FORM_CLIENT 2
+typedef struct {
+    uint64_t fwd_ntts;   /* forward length-N NTTs */
+    uint64_t inv_ntts;   /* inverse transforms */
+    uint32_t inv_len;    /* the length of each inverse transform */
+    uint32_t pad;
+    uint64_t cwms;       /* coefficient-wise products of two length-N polynomials */
+    uint64_t rotations;  /* ciphertext rotations: always 0 */
+} he_op_counts;
+he_status he_conv_op_counts(he_params_t p, const he_conv_desc *d, int form, int in_domain, uint32_t B,
+                            he_op_counts *out);
+he_status he_fc_op_counts(he_params_t p, uint32_t n_in, uint32_t n_out, int form, int in_domain, uint32_t B,
+                          he_op_counts *out);
+
 /* Server model load for one Conv layer (Sec. III-A eq. (k_batch_new); Sec.
  * IV-A: the NTTs of the filter polynomials are computed once and stored).
  *   w: HOST int8 weights [co][ci][fh][fw], F^(m,n)_{k',l'} at

@@ -395,6 +395,62 @@ he_status he_fc_layout_query(he_params_t p, uint32_t n_in, uint32_t n_out, he_fc
     return fc_layout(p, n_in, n_out, out);
 }
 
+// Per limb: what the kernels of each form do for one call (the extracted
+// output): plain -- transforms of c0, c1 of every group (coefficient-domain
+// input), 2G*co products and 2*co valid-slot inverse transforms per
+// ciphertext; masked -- sh always, c0 when coefficient-domain, 2G*co
+// products, co inverse transforms; client -- -v and i + sh, 2G*co products,
+// co inverse transforms.  FC: one weight block per output polynomial.
+he_status he_conv_op_counts(he_params_t p, const he_conv_desc *d, int form, int in_domain, uint32_t B,
+                            he_op_counts *out) {
+    if (!p || !out) return fail(HE_ERR_ARG, "NULL argument");
+    if (form < HE_FORM_PLAIN || form > HE_FORM_CLIENT) return fail(HE_ERR_ARG, "bad form %d", form);
+    if (in_domain != HE_COEFF && in_domain != HE_NTT) return fail(HE_ERR_ARG, "bad in_domain %d", in_domain);
+    if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
+    he_conv_layout lay{};
+    he_status st = conv_layout(p, d, &lay);
+    if (st != HE_OK) return st;
+    const uint64_t G = lay.G, co = d->co, coeff = in_domain == HE_COEFF ? 1u : 0u;
+    he_op_counts c{};
+    if (form == HE_FORM_PLAIN) {
+        c.fwd_ntts = coeff * B * G * 2u;
+        c.cwms = (uint64_t)B * 2u * G * co;
+        c.inv_ntts = (uint64_t)B * 2u * co;
+    } else {
+        c.fwd_ntts = form == HE_FORM_MASKED ? B * G * (1u + coeff) : (uint64_t)B * 2u * G;
+        c.cwms = (uint64_t)B * 2u * G * co;
+        c.inv_ntts = (uint64_t)B * co;
+    }
+    c.inv_len = lay.M;
+    *out = c;
+    return HE_OK;
+}
+
+he_status he_fc_op_counts(he_params_t p, uint32_t n_in, uint32_t n_out, int form, int in_domain, uint32_t B,
+                          he_op_counts *out) {
+    if (!p || !out) return fail(HE_ERR_ARG, "NULL argument");
+    if (form < HE_FORM_PLAIN || form > HE_FORM_CLIENT) return fail(HE_ERR_ARG, "bad form %d", form);
+    if (in_domain != HE_COEFF && in_domain != HE_NTT) return fail(HE_ERR_ARG, "bad in_domain %d", in_domain);
+    if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
+    he_fc_layout fl{};
+    he_status st = fc_layout(p, n_in, n_out, &fl);
+    if (st != HE_OK) return st;
+    const uint64_t P = fl.P_fc, coeff = in_domain == HE_COEFF ? 1u : 0u;
+    he_op_counts c{};
+    if (form == HE_FORM_PLAIN) {
+        c.fwd_ntts = coeff * B * 2u;
+        c.cwms = (uint64_t)B * 2u * P;
+        c.inv_ntts = (uint64_t)B * 2u * P;
+    } else {
+        c.fwd_ntts = form == HE_FORM_MASKED ? B * (1u + coeff) : (uint64_t)B * 2u;
+        c.cwms = (uint64_t)B * 2u * P;
+        c.inv_ntts = (uint64_t)B * P;
+    }
+    c.inv_len = p->N;
+    *out = c;
+    return HE_OK;
+}
+
 static he_status pack_conv(he_params_t p, const he_conv_desc *d, const int8_t *w, uint32_t batch,
                            he_filters_t *out) {
     if (!p || !d || !w || !out) return fail(HE_ERR_ARG, "NULL argument");

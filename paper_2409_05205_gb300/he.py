@@ -22,6 +22,7 @@ HE_OUT_EXTRACTED, HE_OUT_PER_CHANNEL, HE_OUT_EXTRACTED_UNFOLDED = 0, 1, 2
 HE_MAX_LIMBS = 16
 HE_MAX_INTERLEAVE = 128
 HE_DEVICE_NONE = -1
+HE_FORM_PLAIN, HE_FORM_MASKED, HE_FORM_CLIENT = range(3)
 HE_PHASE_NTT, HE_PHASE_REST, HE_PHASE_MAC, HE_PHASE_FINISH, HE_PHASE_RESCALE, HE_PHASE_FIN = range(6)
 
 _STATUS = {0: "HE_OK", 1: "HE_ERR_ARG", 2: "HE_ERR_SHAPE", 3: "HE_ERR_UNSUPPORTED",
@@ -50,6 +51,11 @@ class he_layer_call(ctypes.Structure):
     _fields_ = [("filters", ctypes.c_void_p), ("d_in", ctypes.c_void_p), ("in_domain", ctypes.c_int),
                 ("d_out", ctypes.c_void_p), ("B", ctypes.c_uint32), ("d_share", ctypes.c_void_p),
                 ("d_share_out", ctypes.c_void_p), ("d_rescaled", ctypes.c_void_p)]
+
+
+class he_op_counts(ctypes.Structure):
+    _fields_ = [("fwd_ntts", ctypes.c_uint64), ("inv_ntts", ctypes.c_uint64), ("inv_len", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("cwms", ctypes.c_uint64), ("rotations", ctypes.c_uint64)]
 
 
 class he_plan_tuning(ctypes.Structure):
@@ -91,6 +97,8 @@ _SIGS = {
     "he_params_destroy": [_vp],
     "he_conv_layout_query": [_vp, ctypes.POINTER(he_conv_desc), ctypes.POINTER(he_conv_layout)],
     "he_fc_layout_query": [_vp, _u32, _u32, ctypes.POINTER(he_fc_layout)],
+    "he_conv_op_counts": [_vp, ctypes.POINTER(he_conv_desc), _i32, _i32, _u32, ctypes.POINTER(he_op_counts)],
+    "he_fc_op_counts": [_vp, _u32, _u32, _i32, _i32, _u32, ctypes.POINTER(he_op_counts)],
     "he_pack_filters": [_vp, ctypes.POINTER(he_conv_desc), _vp, ctypes.POINTER(_vp)],
     "he_pack_filters_for_batch": [_vp, ctypes.POINTER(he_conv_desc), _vp, _u32, ctypes.POINTER(_vp)],
     "he_filters_tensor_core": [_vp, ctypes.POINTER(_u32)],
@@ -252,6 +260,23 @@ def he_pack_filters(p: int, desc, w: np.ndarray) -> int:
     out = _vp()
     _check(lib().he_pack_filters(p, ctypes.byref(d), w.ctypes.data, ctypes.byref(out)))
     return out.value
+
+
+def _op_counts(c: he_op_counts) -> dict:
+    return {n: getattr(c, n) for n, _ in he_op_counts._fields_ if n != "pad"}
+
+
+def he_conv_op_counts(p: int, desc, form: int, in_domain: int, B: int = 1) -> dict:
+    d = _desc(desc)
+    c = he_op_counts()
+    _check(lib().he_conv_op_counts(p, ctypes.byref(d), form, in_domain, B, ctypes.byref(c)))
+    return _op_counts(c)
+
+
+def he_fc_op_counts(p: int, n_in: int, n_out: int, form: int, in_domain: int, B: int = 1) -> dict:
+    c = he_op_counts()
+    _check(lib().he_fc_op_counts(p, n_in, n_out, form, in_domain, B, ctypes.byref(c)))
+    return _op_counts(c)
 
 
 def he_pack_filters_for_batch(p: int, desc, w: np.ndarray, B: int) -> int:
