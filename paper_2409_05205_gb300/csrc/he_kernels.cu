@@ -17,8 +17,19 @@
 //  k_fc           FC server step (Alg. 2): product, INTT, first n_o
 //                 coefficients, + Delta_Q d(X) on c0.
 //  k_plan_ntt /   a plan: every input NTT of many independent layer calls
-//  k_plan_chan    (any ring degree, limb count and shape) in one launch, then
-//                 every channel work unit of all calls in one launch.
+//  k_plan_chan    (any ring degree, limb count and shape) in one launch
+//                 (the three-phase register transform for N = 8192), then
+//                 every fused channel work unit of all calls in one launch.
+//  k_plan_mac /   a plan's split form: a persistent bulk-copy-fed channel MAC
+//  k_plan_fin     (two columns, or one for the masked and client steps), then
+//                 the valid-slot inverse transforms and the extraction.
+//  k_plan_fc      a plan's FC items (ordinary and masked) on a side stream.
+//  k_ntt_masked_in, k_client_in, k_fc_masked, k_pack_fc_masked
+//                 the masked server and client steps of Alg. 1 / Alg. 2.
+//  k_rescale /    the RNS rescale by the last prime, for one buffer or for
+//  k_plan_rescale every output of a plan.
+//  k_bfly_peak    the butterfly-rate measurement behind the ALU roofline.
+// The tensor-core channel MAC is in he_tc.cu.
 #include <algorithm>
 #include <mutex>
 
