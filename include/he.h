@@ -404,9 +404,7 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
  * their buffers.  Each call computes the words that he_conv_layer /
  * he_fc_layer with HE_OUT_EXTRACTED would write, or, for a masked or client
  * bank, the words of he_conv_layer_masked / he_fc_layer_masked /
- * he_conv_client / he_fc_client (a masked or client Conv call needs B = 1
- * and the split form below, or an even B).  he_plan_run issues, in order
- * on `stream`:
+ * he_conv_client / he_fc_client.  he_plan_run issues, in order on `stream`:
  *   1. one kernel computing every coefficient-domain input NTT of every
  *      Conv call (for masked and client calls: of both input sources);
  *   2. for the Conv calls in the split form (B = 1, interleave s >= 4, G in

@@ -1192,10 +1192,12 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
                 cd.split = 0;
                 cd.zt = use_tc ? 1u : 0u;
             }
-            // the fused form covers columns in tiles of nj >= 2 (plain calls have 2B columns)
-            if (msrc && !cd.split && (g.ncols % cd.nj) != 0)
-                return fail(HE_ERR_UNSUPPORTED,
-                            "call %u: a masked or client Conv call in a plan needs B = 1 in the split form or an even B", i);
+            // the fused form covers columns in tiles of nj (plain calls have 2B
+            // columns); one-column calls with an odd batch take tiles of one
+            if (msrc && !cd.split && (g.ncols % cd.nj) != 0) {
+                cd.nj = 1;
+                cd.cpt = he_conv_cpt(1, cd.nb, g.G);
+            }
             nin = msrc == 2 ? (size_t)c.B * lay.G * r.N
                             : (size_t)c.B * lay.G * (msrc ? 1u : 2u) * r.L * r.N;
             nsh = (size_t)c.B * lay.G * r.N;
@@ -1291,7 +1293,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
     using Costed = std::pair<double, ChanItem>;
     std::vector<std::pair<double, NttItem>> ntt_cost, fc_cost;
     std::vector<uint32_t> tc_calls;
-    std::vector<Costed> chan[4], mac[kMacClasses], fin;
+    std::vector<Costed> chan[kChanClasses], mac[kMacClasses], fin;
     for (uint32_t i = 0; i < ncalls; ++i) {
         CallDesc &cd = descs[i];
         ConvGeo &g = cd.g;
@@ -1331,7 +1333,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
                 for (uint32_t l = 0; l < g.L; ++l)
                     for (uint32_t col = 0; col < g.ncols; ++col) fin.push_back({fcost, ChanItem{i, h, l, col}});
         } else {
-            const int cls = cd.nj == 2 ? 0 : cd.nj == 4 ? 1 : cd.nj == 8 ? 2 : 3;
+            const int cls = cd.nj == 1 ? 4 : cd.nj == 2 ? 0 : cd.nj == 4 ? 1 : cd.nj == 8 ? 2 : 3;
             const double cost = (double)g.G * N * cd.nj + 3.0 * cd.nj * (g.M / 2.0) * g.logM;
             for (uint32_t n = 0; n < g.co; ++n)
                 for (uint32_t l = 0; l < g.L; ++l)
@@ -1373,11 +1375,11 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
     }
-    for (int cls = 0; cls < 4 && e == cudaSuccess; ++cls) {
+    for (int cls = 0; cls < kChanClasses && e == cudaSuccess; ++cls) {
         std::stable_sort(chan[cls].begin(), chan[cls].end(), by_cost);
         std::vector<ChanItem> items;
         size_t smem = 16;
-        const uint32_t nj = 2u << cls;
+        const uint32_t nj = chan_class_nj(cls);
         for (auto &it : chan[cls]) {
             items.push_back(it.second);
             smem = std::max(smem, fold_smem_bytes(nj, descs[it.second.call].g.M));
@@ -1538,7 +1540,7 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
     r.mac_items = plan->n_mac;
     r.mac_ctas = plan->n_mac ? plan->mac_ctas : 0;
     r.finish_items = plan->n_fin;
-    for (int c = 0; c < 4; ++c) r.fused_items += plan->n_chan[c];
+    for (int c = 0; c < kChanClasses; ++c) r.fused_items += plan->n_chan[c];
     r.fc_items = plan->n_fc;
     r.kernels_per_run = (plan->n_ntt > 0) + (plan->n_mac > 0) + (plan->n_fin > 0) + (plan->n_fc > 0) +
                         (plan->n_tc > 0) + (plan->n_rs > 0);
@@ -1546,7 +1548,7 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
     r.tc_items = plan->n_tc;
     r.tc_ctas = plan->n_tc ? plan->tc_ctas : 0;
     for (uint32_t i = 0; i < plan->ncalls; ++i) r.tc_calls += plan->split[i] == 2;
-    for (int c = 0; c < 4; ++c) r.kernels_per_run += plan->n_chan[c] > 0;
+    for (int c = 0; c < kChanClasses; ++c) r.kernels_per_run += plan->n_chan[c] > 0;
     for (uint32_t i = 0; i < plan->ncalls; ++i) r.split_calls += plan->split[i] == 1;
     r.workspace_bytes = plan->ws_bytes;
     r.tuning = plan->tuning;
@@ -1562,7 +1564,7 @@ void he_plan_destroy(he_plan_t plan) {
     cudaFree(plan->ws);
     cudaFree(plan->d_calls);
     cudaFree(plan->d_ntt);
-    for (int c = 0; c < 4; ++c) cudaFree(plan->d_chan[c]);
+    for (int c = 0; c < kChanClasses; ++c) cudaFree(plan->d_chan[c]);
     cudaFree(plan->d_mac);
     cudaFree(plan->d_mac_offs);
     cudaFree(plan->d_mac_copy);

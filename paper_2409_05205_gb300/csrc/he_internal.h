@@ -288,13 +288,18 @@ struct RsItem {
 };
 constexpr uint32_t kRsItemU4 = 256;  // uint4 groups per rescale item: one per thread (1024 coefficients)
 
+// fused-form column-tile classes of a plan: NJ = 2, 4, 8, 16 columns per
+// CTA, and 1 for the one-column masked and client calls with an odd batch
+constexpr int kChanClasses = 5;
+__host__ __device__ __forceinline__ constexpr uint32_t chan_class_nj(int cls) { return cls < 4 ? 2u << cls : 1u; }
+
 struct he_plan_s {
     int device;
-    uint32_t ncalls, n_ntt, n_chan[4];  // fused channel items per NJ class (2, 4, 8, 16)
+    uint32_t ncalls, n_ntt, n_chan[kChanClasses];  // fused channel items per NJ class (2, 4, 8, 16, 1)
     uint32_t n_mac, n_fin;              // split form: MAC items, finishing items (and every FC item)
     CallDesc *d_calls;
     NttItem *d_ntt;
-    ChanItem *d_chan[4];
+    ChanItem *d_chan[kChanClasses];
     ChanItem *d_mac, *d_fin;
     uint32_t *d_mac_offs;               // persistent MAC CTAs: items of CTA b at [offs[b], offs[b+1])
     MacCopy *d_mac_copy;                // per item, same order as d_mac
@@ -305,7 +310,7 @@ struct he_plan_s {
     size_t smem_fc;
     cudaStream_t side;                  // FC work forks off the caller's stream and joins it again
     cudaEvent_t ev_fork, ev_join;
-    size_t smem_ntt, smem_chan[4], smem_mac, smem_fin;
+    size_t smem_ntt, smem_chan[kChanClasses], smem_mac, smem_fin;
     uint32_t *ws;
     size_t ws_bytes;
     uint32_t n_tc, tc_ctas;             // tensor-core MAC: items, persistent CTAs

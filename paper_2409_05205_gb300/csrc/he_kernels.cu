@@ -1772,6 +1772,7 @@ cudaError_t he_plan_prepare(const he_plan_s &pl) {
     if (e == cudaSuccess && pl.n_chan[1]) e = set_smem(k_plan_chan<4>, pl.smem_chan[1]);
     if (e == cudaSuccess && pl.n_chan[2]) e = set_smem(k_plan_chan<8>, pl.smem_chan[2]);
     if (e == cudaSuccess && pl.n_chan[3]) e = set_smem(k_plan_chan<16>, pl.smem_chan[3]);
+    if (e == cudaSuccess && pl.n_chan[4]) e = set_smem(k_plan_chan<1>, pl.smem_chan[4]);
     return e;
 }
 
@@ -1851,6 +1852,7 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     if ((e = plan_chan_launch<4>(pl, 1, st)) != cudaSuccess) return e;
     if ((e = plan_chan_launch<8>(pl, 2, st)) != cudaSuccess) return e;
     if ((e = plan_chan_launch<16>(pl, 3, st)) != cudaSuccess) return e;
+    if ((e = plan_chan_launch<1>(pl, 4, st)) != cudaSuccess) return e;
     if (pl.n_rs) {
         // the rescale reads every output, FC outputs included: join first
         if (join.on && (e = cudaStreamWaitEvent(st, pl.ev_join, 0)) != cudaSuccess) return e;

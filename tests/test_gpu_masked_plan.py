@@ -208,20 +208,23 @@ def test_masked_plan_matches_the_oracle():
             H.he_filters_destroy(ff)
 
 
-def test_even_batch_masked_calls_take_the_fused_form_and_graph_capture():
+def test_batched_masked_calls_take_the_fused_form_and_graph_capture():
     H = U.he()
     torch = U.torch_cuda()
     N, L = 4096, 2
     ps, psis = U.ring(N, L)
     s = torch.cuda.Stream()
     with U.params(N, L) as p:
+        # even batches in column tiles of 2 and more, odd ones in tiles of one
         cases = [_Case(H, p, N, ps, psis, "server", SHAPES[2], 2, 330),
                  _Case(H, p, N, ps, psis, "client", SHAPES[3], 4, 331),
-                 _Case(H, p, N, ps, psis, "server", dict(fc=True, n_in=100, n_out=40), 3, 332)]
+                 _Case(H, p, N, ps, psis, "server", dict(fc=True, n_in=100, n_out=40), 3, 332),
+                 _Case(H, p, N, ps, psis, "server", SHAPES[1], 3, 333),
+                 _Case(H, p, N, ps, psis, "client", SHAPES[2], 5, 334)]
         try:
             with torch.cuda.stream(s):
                 info, outs = _run_plan(H, cases, s, graph=True)
-            assert info["form"][0] == 0 and info["form"][1] == 0
+            assert info["form"][0] == 0 and info["form"][1] == 0 and info["form"][3] == 0 and info["form"][4] == 0
             for c, got in zip(cases, outs[0]):
                 np.testing.assert_array_equal(got, c.single(H, p, s), err_msg=f"{c.kind} {c.shape}")
         finally:
@@ -234,15 +237,15 @@ def test_masked_plan_argument_errors():
     N, L = 4096, 2
     ps, psis = U.ring(N, L)
     with U.params(N, L) as p:
-        c = _Case(H, p, N, ps, psis, "server", SHAPES[2], 3, 340)      # odd B > 1: no form for it
         c1 = _Case(H, p, N, ps, psis, "server", SHAPES[2], 1, 341)
+        cc = _Case(H, p, N, ps, psis, "client", SHAPES[2], 1, 342)
         try:
-            with pytest.raises(RuntimeError):
-                H.he_plan_create([c.call()])
+            with pytest.raises(RuntimeError):                        # a client call with NTT-domain inputs
+                H.he_plan_create([(cc.f, cc.d_in, H.HE_NTT, cc.d_out, 1, cc.d_sh)])
             with pytest.raises(RuntimeError):                        # no shares
                 H.he_plan_create([(c1.f, c1.d_in, H.HE_COEFF, c1.d_out, 1)])
             with pytest.raises(RuntimeError):                        # output overlapping a share
                 H.he_plan_create([(c1.f, c1.d_in, H.HE_COEFF, c1.d_sh, 1, c1.d_sh, c1.d_shp)])
         finally:
-            H.he_filters_destroy(c.f)
             H.he_filters_destroy(c1.f)
+            H.he_filters_destroy(cc.f)
