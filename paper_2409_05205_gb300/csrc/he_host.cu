@@ -1179,7 +1179,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             // polynomials fit shared memory
             const uint32_t ncol = msrc ? 1u : 2u;
             cd.split = (tu.split && c.B == 1 && split_mac_ok(lay.s, g.G) &&
-                        ((ncol * g.G) << f->logTS) <= kMacXWords &&
+                        ((ncol * g.G) << f->logTS) <= kMacXWordsBig &&
                         (size_t)std::min(lay.s, f->desc.co) * fin_stride(lay.M, lay.s) * 4u <= 200u * 1024u)
                            ? 1u
                            : 0u;
@@ -1419,6 +1419,8 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         }
         offs[nctas] = (uint32_t)items.size();
         std::vector<MacCopy> copies;
+        pl->mac_xw = kMacXWords;
+        pl->mac_nst = kMacStages;
         std::vector<MacDesc> mdescs;
         for (const ChanItem &it : items) {
             const CallDesc &cd = descs[it.call];
@@ -1432,6 +1434,10 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             c.ncol = cd.msrc ? 1u : 2u;
             c.xrows = c.ncol * g.G;
             c.xwords = 1u << lt;
+            if (c.xrows * c.xwords > kMacXWords) {  // 2 columns x 8 groups: the larger input buffers
+                pl->mac_xw = kMacXWordsBig;
+                pl->mac_nst = kMacStagesBig;
+            }
             c.pad = 0;
             copies.push_back(c);
             MacDesc d{};
@@ -1453,7 +1459,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
         }
         pl->n_mac = (uint32_t)items.size();
         pl->mac_ctas = nctas;
-        pl->smem_mac = mac_smem_bytes();
+        pl->smem_mac = mac_smem_bytes(pl->mac_xw, pl->mac_nst);
         if (e == cudaSuccess) e = upload(&pl->d_mac, items);
         if (e == cudaSuccess && !copies.empty()) {
             e = cudaMalloc(&pl->d_mac_copy, sizeof(MacCopy) * copies.size());

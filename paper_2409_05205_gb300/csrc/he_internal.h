@@ -204,13 +204,17 @@ __host__ __device__ __forceinline__ int he_mac_class(uint32_t G, uint32_t cs) {
 
 // split form: bulk-copy ring of the MAC kernel
 constexpr uint32_t kMacStageWords = 4096;   // 16 KB per stage
-constexpr uint32_t kMacStages = 5;
+constexpr uint32_t kMacStages = 5;          // stages of the ring (the most; barriers for this many)
 // shared-memory header: mbarriers xfull[2], xempty[2], full[S], empty[S],
 // then two 64-byte item descriptors
 constexpr uint32_t kMacBarBytes = ((4u + 2u * kMacStages) * 8u + 15u) / 16u * 16u;
 constexpr uint32_t kMacHdrBytes = kMacBarBytes + 128u;
 constexpr uint32_t kMacItemWords = 32768;   // weights per work item (128 KB)
 constexpr uint32_t kMacXWords = 4096;       // one input buffer: 2 columns x G*TS <= 2048 words
+// plans with a split-form call of 2 columns x G = 8 groups take input buffers
+// of 8192 words and a 3-stage ring: the same 112 KB, two CTAs per SM
+constexpr uint32_t kMacXWordsBig = 8192;
+constexpr uint32_t kMacStagesBig = 3;
 // the split MAC kernel's slot tile: TS = 2^(9 + log2 CS) slots, so that its
 // 256 compute threads own 4*CS slots of one column each
 __host__ __device__ __forceinline__ constexpr uint32_t split_tile_log(uint32_t lcs) { return 9u + lcs; }
@@ -244,8 +248,8 @@ struct alignas(16) MacDesc {
 };
 static_assert(sizeof(MacDesc) == 64, "MacDesc is one 64-byte bulk copy");
 
-__host__ __device__ __forceinline__ size_t mac_smem_bytes() {
-    return kMacHdrBytes + (size_t)2 * kMacXWords * 4u + (size_t)kMacStages * kMacStageWords * 4u;
+__host__ __device__ __forceinline__ size_t mac_smem_bytes(uint32_t xw, uint32_t nstages) {
+    return kMacHdrBytes + (size_t)2 * xw * 4u + (size_t)nstages * kMacStageWords * 4u;
 }
 // polynomial stride (words) of the finishing kernel's s rows of length M
 // (>= padded_words(M)): the extraction reads slot e of the s rows
@@ -305,6 +309,7 @@ struct he_plan_s {
     MacCopy *d_mac_copy;                // per item, same order as d_mac
     MacDesc *d_mac_desc;                // per item, same order as d_mac
     uint32_t mac_ctas;
+    uint32_t mac_xw, mac_nst;           // MAC kernel: words per input buffer, stages of the weight ring
     uint32_t n_fc;                      // fused FC items, run on a side stream
     NttItem *d_fc;
     size_t smem_fc;

@@ -1085,7 +1085,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 template <int G, int CS>
 __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, uint64_t *xempty,
                                          const uint32_t *ring, uint64_t *full, uint64_t *empty, uint32_t &buf,
-                                         uint32_t &ph) {
+                                         uint32_t &ph, uint32_t nstages) {
     constexpr uint32_t LT = split_tile_log(CS == 4 ? 2 : (CS == 2 ? 1 : 0));
     constexpr uint32_t ROWS = kMacStageWords >> LT;  // weight rows of TS words per stage
     constexpr uint32_t NCH = ROWS / G;               // channels per full stage
@@ -1146,7 +1146,7 @@ __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, ui
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty + buf);
-        if (++buf == kMacStages) {
+        if (++buf == nstages) {
             buf = 0;
             ph ^= 1u;
         }
@@ -1169,7 +1169,8 @@ __device__ __forceinline__ void mac_issue_inputs(const MacCopy &c, const MacDesc
 __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__restrict__ copies,
                                                               const MacDesc *__restrict__ descs,
                                                               const uint32_t *__restrict__ offs,
-                                                              uint32_t *__restrict__ status) {
+                                                              uint32_t *__restrict__ status, uint32_t xw,
+                                                              uint32_t nring) {
     extern __shared__ uint4 smem4[];
     uint64_t *xfull = reinterpret_cast<uint64_t *>(smem4);  // [2]
     uint64_t *xempty = xfull + 2;                            // [2]
@@ -1177,7 +1178,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
     uint64_t *empty = full + kMacStages;                     // [kMacStages]
     MacDesc *dslot = reinterpret_cast<MacDesc *>(reinterpret_cast<char *>(smem4) + kMacBarBytes);  // [2]
     uint32_t *Xb = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(smem4) + kMacHdrBytes);
-    uint32_t *ring = Xb + 2 * kMacXWords;
+    uint32_t *ring = Xb + 2 * xw;  // xw words per input buffer, nring <= kMacStages weight stages
     constexpr uint32_t kWarps = kThreads / 32;  // compute warps
     const uint32_t ib = offs[blockIdx.x], ie = offs[blockIdx.x + 1];
     const uint32_t tid = threadIdx.x;
@@ -1202,7 +1203,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
         MacCopy c = copies[ib];
         // the weights do not depend on the input-NTT kernel: the first ring
         // stages go out before waiting for it
-        uint32_t st0 = min(kMacStages, (c.nwords + kMacStageWords - 1) / kMacStageWords);
+        uint32_t st0 = min(nring, (c.nwords + kMacStageWords - 1) / kMacStageWords);
         for (uint32_t st = 0; st < st0; ++st, ++issued) {
             const uint32_t w = min(kMacStageWords, c.nwords - st * kMacStageWords);
             mbar_expect(full + st, w * 4u);
@@ -1210,16 +1211,16 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
         }
         pdl_wait();
         for (uint32_t k = ib; k < ie && k < ib + 2; ++k, ++xiss)
-            mac_issue_inputs(copies[k], descs + k, dslot + (xiss & 1u), Xb + (xiss & 1u) * kMacXWords,
+            mac_issue_inputs(copies[k], descs + k, dslot + (xiss & 1u), Xb + (xiss & 1u) * xw,
                              xfull + (xiss & 1u));
         for (uint32_t k = ib; ok && k < ie; ++k) {
             MacCopy cn;
             if (k + 1 < ie) cn = copies[k + 1];  // in flight while this item's stages go out
             const uint32_t nst = (c.nwords + kMacStageWords - 1) / kMacStageWords;
             for (uint32_t st = (k == ib ? st0 : 0u); st < nst; ++st, ++issued) {
-                const uint32_t b = issued % kMacStages;
-                if (issued >= kMacStages) {
-                    if (!mbar_wait(empty + b, ((issued / kMacStages) - 1u) & 1u)) {
+                const uint32_t b = issued % nring;
+                if (issued >= nring) {
+                    if (!mbar_wait(empty + b, ((issued / nring) - 1u) & 1u)) {
                         ok = false;
                         break;
                     }
@@ -1237,7 +1238,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
                     break;
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mac_issue_inputs(copies[k + 2], descs + k + 2, dslot + xb, Xb + xb * kMacXWords, xfull + xb);
+                mac_issue_inputs(copies[k + 2], descs + k + 2, dslot + xb, Xb + xb * xw, xfull + xb);
                 ++xiss;
             }
             c = cn;
@@ -1247,8 +1248,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
         // the last two input loads and the last kMacStages stages can still
         // be in flight (an older phase of a barrier must not be waited for)
         for (uint32_t i = xiss > 2 ? xiss - 2 : 0; i < xiss; ++i) mbar_wait(xfull + (i & 1u), (i >> 1) & 1u);
-        for (uint32_t i = issued > kMacStages ? issued - kMacStages : 0; i < issued; ++i)
-            mbar_wait(full + i % kMacStages, (i / kMacStages) & 1u);
+        for (uint32_t i = issued > nring ? issued - nring : 0; i < issued; ++i)
+            mbar_wait(full + i % nring, (i / nring) & 1u);
         return;
     }
     // ---- compute warps: blocked (not polling) until the input-NTT kernel is done
@@ -1262,15 +1263,15 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
             break;
         }
         const MacDesc d = dslot[xb];
-        const uint32_t *X = Xb + xb * kMacXWords;
+        const uint32_t *X = Xb + xb * xw;
         switch (d.cls) {
-            case 0: ok = mac_item<1, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
-            case 1: ok = mac_item<1, 2>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
-            case 2: ok = mac_item<1, 4>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
-            case 3: ok = mac_item<2, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
-            case 4: ok = mac_item<2, 2>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
-            case 5: ok = mac_item<4, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
-            default: ok = mac_item<8, 1>(d, X, xempty + xb, ring, full, empty, buf, ph); break;
+            case 0: ok = mac_item<1, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
+            case 1: ok = mac_item<1, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
+            case 2: ok = mac_item<1, 4>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
+            case 3: ok = mac_item<2, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
+            case 4: ok = mac_item<2, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
+            case 5: ok = mac_item<4, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
+            default: ok = mac_item<8, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
         }
     }
     if (!ok) atomicOr(status, 1u);
@@ -1836,7 +1837,8 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     } join{pl, st, fc};
     if (pl.n_mac && phase != 3) {
         e = launch_pdl(k_plan_mac, pl.mac_ctas, kThreads + 32, pl.smem_mac, st, (const MacCopy *)pl.d_mac_copy,
-                       (const MacDesc *)pl.d_mac_desc, (const uint32_t *)pl.d_mac_offs, pl.d_status);
+                       (const MacDesc *)pl.d_mac_desc, (const uint32_t *)pl.d_mac_offs, pl.d_status, pl.mac_xw,
+                       pl.mac_nst);
         if (e != cudaSuccess) return e;
     }
     if (pl.n_tc && phase != 3) {

@@ -15,21 +15,26 @@ import _gpu_helpers as U
 
 pytestmark = pytest.mark.gpu
 
-# (ci, co, hw, f, pad)
-SHAPES = [(48, 48, 32, 5, 2), (96, 192, 16, 5, 2), (192, 192, 8, 5, 2), (3, 48, 32, 5, 2),
-          (1024, 256, 14, 1, 0), (256, 1024, 14, 1, 0), (256, 256, 14, 3, 1)]
+# (ci, co, hw, f, pad, N, L)
+SHAPES = [(48, 48, 32, 5, 2, 8192, 3), (96, 192, 16, 5, 2, 8192, 3), (192, 192, 8, 5, 2, 8192, 3),
+          (3, 48, 32, 5, 2, 8192, 3), (1024, 256, 14, 1, 0, 8192, 3), (256, 1024, 14, 1, 0, 8192, 3),
+          (256, 256, 14, 3, 1, 8192, 3), (64, 64, 32, 3, 1, 16384, 2)]
 
 
-@pytest.mark.parametrize("ci,co,hw,f,pad", SHAPES)
-def test_layer_family_full_size(ci, co, hw, f, pad):
+@pytest.mark.parametrize("ci,co,hw,f,pad,N,L", SHAPES)
+def test_layer_family_full_size(ci, co, hw, f, pad, N, L):
     H = U.he()
     torch = U.torch_cuda()
-    N, L, B = 8192, 3, 1
+    B = 1
     ps, psis, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, B, seed=ci + co + f, fh=f, fw=f, pad=pad)
     with U.params(N, L) as p, U.conv_bank(p, desc, F) as fb:
         single = U.run_conv(p, fb, cts, H.HE_OUT_EXTRACTED, lay["H"])
         d_in, d_out = U.to_dev(cts), U.empty_dev(single.shape)
         plan = H.he_plan_create([(fb, d_in, H.HE_COEFF, d_out, B)])
+        # G = 8 at s >= 4 (two columns of 8 groups) takes the split form with
+        # the larger input buffers
+        if lay["G"] == 8 and lay["s"] >= 4:
+            assert H.he_plan_query(plan, 1)["form"][0] == 1
         try:
             H.he_plan_run(plan, torch.cuda.current_stream())
             H.he_sync(torch.cuda.current_stream())
