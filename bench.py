@@ -352,8 +352,8 @@ class Arm:
 # DRAM bytes (read + write) of one k_plan_mac launch, from an ncu capture of
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where no
 # capture of the current kernel exists.
-TRAFFIC = {"plain20_c10": 141.15e6,          # ncu --set full of one launch: read 136.62 MB + write 4.54 MB
-           "plain20_c10_masked": 269.85e6}   # read 264.15 MB + write 5.70 MB
+TRAFFIC = {"plain20_c10": 141.38e6,          # ncu --set full of one launch: read 136.62 MB + write 4.77 MB
+           "plain20_c10_masked": 269.45e6}   # read 264.17 MB + write 5.28 MB
 
 
 def _traffic(name):
