@@ -199,29 +199,28 @@ void ora_ntt_inv(uint32_t *a, int count, int N, uint32_t q, uint32_t psi) {
     free(ipw);
 }
 
-/* Sum of products through the NTT for one limb:
- *   y[n][c] = INTT( sum_{k<K} NTT(x[k][c]) (.) NTT(w[n][k]) )
+/* Sum of products through the NTT for one limb, per request, with the
+ * weights already in the NTT domain (Sec. IV-A: the server computes the NTTs
+ * of its plaintext polynomials once and stores them):
+ *   y[n][c] = INTT( sum_{k<K} NTT(x[k][c]) (.) w_ntt[n][k] )
  * x: K*C coefficient polynomials, x[k][c] at x + (k*C + c)*N
- * w: Nout*K coefficient polynomials, w[n][k] at w + (n*K + k)*N
+ * w_ntt: Nout*K NTT-domain polynomials, w_ntt[n][k] at w_ntt + (n*K + k)*N
  * y: Nout*C output polynomials, y[n][c] at y + (n*C + c)*N
- * This is the plain form of the server step (Sec. III-A, Alg. 1's evaluation step:
- * one product per input polynomial and output channel, summed, then INTT). */
-void ora_sum_products_ntt(const uint32_t *x, int K, int C, const uint32_t *w,
-                          int Nout, uint32_t *y, int N, uint32_t q,
-                          uint32_t psi) {
+ * This is the plain form of the server step (Sec. III-A, Alg. 1's evaluation
+ * step: one product per input polynomial and output channel, summed, then
+ * INTT). */
+void ora_sum_products_ntt_w(const uint32_t *x, int K, int C, const uint32_t *w_ntt,
+                            int Nout, uint32_t *y, int N, uint32_t q,
+                            uint32_t psi) {
     uint32_t *pw = (uint32_t *)malloc(sizeof(uint32_t) * N);
     uint32_t *ipw = (uint32_t *)malloc(sizeof(uint32_t) * N);
     make_tables(N, q, psi, pw, ipw);
     uint32_t ninv = powmod((uint32_t)N % q, (uint64_t)q - 2, q);
-    size_t nx = (size_t)K * C, nw = (size_t)Nout * K;
+    size_t nx = (size_t)K * C;
     uint32_t *X = (uint32_t *)malloc(sizeof(uint32_t) * nx * N);
-    uint32_t *W = (uint32_t *)malloc(sizeof(uint32_t) * nw * N);
     memcpy(X, x, sizeof(uint32_t) * nx * N);
-    memcpy(W, w, sizeof(uint32_t) * nw * N);
 #pragma omp parallel for schedule(dynamic, 1)
     for (long p = 0; p < (long)nx; p++) ntt_fwd_one(X + (size_t)p * N, N, q, pw);
-#pragma omp parallel for schedule(dynamic, 1)
-    for (long p = 0; p < (long)nw; p++) ntt_fwd_one(W + (size_t)p * N, N, q, pw);
 #pragma omp parallel for schedule(dynamic, 1) collapse(2)
     for (int n = 0; n < Nout; n++) {
         for (int c = 0; c < C; c++) {
@@ -229,7 +228,7 @@ void ora_sum_products_ntt(const uint32_t *x, int K, int C, const uint32_t *w,
             for (int i = 0; i < N; i++) yy[i] = 0;
             for (int k = 0; k < K; k++) {
                 const uint32_t *xa = X + ((size_t)k * C + c) * N;
-                const uint32_t *wa = W + ((size_t)n * K + k) * N;
+                const uint32_t *wa = w_ntt + ((size_t)n * K + k) * N;
                 for (int i = 0; i < N; i++)
                     yy[i] = addmod(yy[i], mulmod(xa[i], wa[i], q), q);
             }
@@ -237,7 +236,19 @@ void ora_sum_products_ntt(const uint32_t *x, int K, int C, const uint32_t *w,
         }
     }
     free(X);
-    free(W);
     free(pw);
     free(ipw);
+}
+
+/* The same with coefficient-domain weights w[n][k] (at w + (n*K + k)*N):
+ * their NTTs first, then the per-request part above. */
+void ora_sum_products_ntt(const uint32_t *x, int K, int C, const uint32_t *w,
+                          int Nout, uint32_t *y, int N, uint32_t q,
+                          uint32_t psi) {
+    size_t nw = (size_t)Nout * K;
+    uint32_t *W = (uint32_t *)malloc(sizeof(uint32_t) * nw * N);
+    memcpy(W, w, sizeof(uint32_t) * nw * N);
+    ora_ntt_fwd(W, (int)nw, N, q, psi);
+    ora_sum_products_ntt_w(x, K, C, W, Nout, y, N, q, psi);
+    free(W);
 }

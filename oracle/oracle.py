@@ -84,6 +84,7 @@ def _c():
             lib.ora_sum_products_ntt.argtypes = [
                 u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int, u32p,
                 ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32]
+            lib.ora_sum_products_ntt_w.argtypes = lib.ora_sum_products_ntt.argtypes
             lib.ora_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -449,11 +450,14 @@ def ntt_direct(a: np.ndarray, q: int, psi: int) -> np.ndarray:
 
 
 def _sum_products(x: np.ndarray, w: np.ndarray, q: int, psi: int,
-                  tier: str) -> np.ndarray:
+                  tier: str, w_ntt: bool = False) -> np.ndarray:
     """y[n][c] = sum_k x[k][c] * w[n][k] in Z_q[X]/(X^N+1).
-    x: [K][C][N], w: [Nout][K][N] residues -> y: [Nout][C][N]."""
+    x: [K][C][N], w: [Nout][K][N] residues -> y: [Nout][C][N].
+    w_ntt: w holds the NTTs of the weight polynomials (NTT tier only)."""
     K, C, N = x.shape
     Nout = w.shape[0]
+    if w_ntt and tier != "ntt":
+        raise ValueError("NTT-domain weights need the NTT tier")
     if tier == "schoolbook":
         y = np.zeros((Nout, C, N), dtype=np.uint32)
         for n in range(Nout):
@@ -467,7 +471,8 @@ def _sum_products(x: np.ndarray, w: np.ndarray, q: int, psi: int,
         x = np.ascontiguousarray(x, dtype=np.uint32)
         w = np.ascontiguousarray(w, dtype=np.uint32)
         y = np.zeros((Nout, C, N), dtype=np.uint32)
-        _c().ora_sum_products_ntt(_p32(x), K, C, _p32(w), Nout, _p32(y), N, q, psi)
+        fn = _c().ora_sum_products_ntt_w if w_ntt else _c().ora_sum_products_ntt
+        fn(_p32(x), K, C, _p32(w), Nout, _p32(y), N, q, psi)
         return y
     raise ValueError(tier)
 
@@ -493,16 +498,22 @@ def conv_layer(cts: np.ndarray, F: np.ndarray, primes: list[int],
     (the ciphertext-plaintext product of Sec. II-A summed over groups).
     mode OUT_EXTRACTED: extract_conv(y) -> [B][H][2][L][N];
     mode OUT_PER_CHANNEL: y itself    -> [B][c_o][2][L][N]."""
+    fh = pack_filters(F, lay)
+    return _conv_products(cts, [to_residues(fh, q) for q in primes], primes, psis, lay, mode, tier, False)
+
+
+def _conv_products(cts: np.ndarray, wl: list, primes: list[int], psis: list[int], lay: dict, mode: int,
+                   tier: str, w_ntt: bool) -> np.ndarray:
+    """conv_layer's products and extraction; wl[l]: [co][G][N] filter
+    residues of limb l (their NTTs with w_ntt)."""
     B, G, J, L, N = cts.shape
     assert J == 2 and G == lay["G"] and N == lay["N"] and L == len(primes)
-    fh = pack_filters(F, lay)
     co = lay["co"]
     y = np.zeros((B, co, 2, L, N), dtype=np.uint32)
     for l, (q, psi) in enumerate(zip(primes, psis)):
-        wr = to_residues(fh, q)                                   # [co][G][N]
         x = np.ascontiguousarray(
             cts[:, :, :, l, :].transpose(1, 0, 2, 3).reshape(G, B * 2, N))
-        yl = _sum_products(x, wr, q, psi, tier)                   # [co][2B][N]
+        yl = _sum_products(x, wl[l], q, psi, tier, w_ntt)         # [co][2B][N]
         y[:, :, :, l, :] = yl.reshape(co, B, 2, N).transpose(1, 0, 2, 3)
     if mode == OUT_PER_CHANNEL:
         return y
@@ -554,10 +565,19 @@ def conv_layer_masked(c0: np.ndarray, sh: np.ndarray, rho: np.ndarray, F: np.nda
     rho: [co][G][N] integers in [0, t), the masks rho_{g,n};
     shp: [B][H][N] integers in [0, t), the share sh' added to the output.
     Returns [B][H][L][N] residues."""
+    fh = pack_filters(F, lay)
+    wl = [np.concatenate([to_residues(rho, q), to_residues(-fh, q)], axis=1) for q in primes]  # [co][2G][N]
+    return _conv_masked_products(c0, sh, wl, shp, primes, psis, t, lay, tier, False)
+
+
+def _conv_masked_products(c0: np.ndarray, sh: np.ndarray, wl: list, shp: np.ndarray, primes: list[int],
+                          psis: list[int], t: int, lay: dict, tier: str, w_ntt: bool) -> np.ndarray:
+    """conv_layer_masked's products, extraction and share; wl[l]: the masks
+    rho and the negated filters -fhat of limb l side by side, [co][2G][N]
+    (their NTTs with w_ntt)."""
     B, G, L, N = c0.shape
     assert G == lay["G"] and N == lay["N"] and L == len(primes)
-    fh = pack_filters(F, lay)
-    co, H = lay["co"], lay["H"]
+    H = lay["H"]
     D = delta_q(primes, t)
     out = np.zeros((B, H, L, N), dtype=np.uint32)
     for l, (q, psi) in enumerate(zip(primes, psis)):
@@ -565,8 +585,7 @@ def conv_layer_masked(c0: np.ndarray, sh: np.ndarray, rho: np.ndarray, F: np.nda
         dsh = (np.asarray(sh, dtype=np.uint64) % q) * Dq % q                  # Delta sh  [B][G][N]
         x = np.concatenate([c0[:, :, l, :].astype(np.uint32), dsh.astype(np.uint32)], axis=1)
         x = np.ascontiguousarray(x.transpose(1, 0, 2))                          # [2G][B][N]
-        w = np.concatenate([to_residues(rho, q), to_residues(-fh, q)], axis=1)  # [co][2G][N]
-        y = _sum_products(x, w, q, psi, tier)                                   # [co][B][N]
+        y = _sum_products(x, wl[l], q, psi, tier, w_ntt)                        # [co][B][N]
         for b in range(B):
             ex = extract_conv(y[:, b, :], lay).astype(np.uint64)               # [H][N]
             out[b, :, l, :] = ((ex + Dq * (np.asarray(shp[b], np.uint64) % q)) % q).astype(np.uint32)
@@ -640,10 +659,20 @@ def fc_layer_masked(c0: np.ndarray, sh: np.ndarray, rho: np.ndarray, W: np.ndarr
     rho: [P][N] integers in [0, t), the masks rho_j;
     shp: [B][P][N] integers in [0, t), the share sh' added to the output.
     Returns [B][P][L][N] residues."""
-    B, L, N = c0.shape
-    assert N == lay["N"] and L == len(primes)
     wpk = pack_fc_weights(W, lay)
     dpk = pack_fc_bias(Bv if Bv is not None else np.zeros(lay["n_out"], np.int64), lay)
+    wl = [np.stack([to_residues(rho, q), to_residues(-wpk, q)], axis=1) for q in primes]  # [P][2][N]
+    return _fc_masked_products(c0, sh, wl, dpk, shp, primes, psis, t, lay, tier, False)
+
+
+def _fc_masked_products(c0: np.ndarray, sh: np.ndarray, wl: list, dpk: np.ndarray, shp: np.ndarray,
+                        primes: list[int], psis: list[int], t: int, lay: dict, tier: str,
+                        w_ntt: bool) -> np.ndarray:
+    """fc_layer_masked's products, window, bias and share; wl[l]: [P][2][N]
+    the masks rho_j and the negated weights -w_j of limb l (their NTTs with
+    w_ntt); dpk: [P][N] the packed bias d_j."""
+    B, L, N = c0.shape
+    assert N == lay["N"] and L == len(primes)
     D = delta_q(primes, t)
     P = lay["P"]
     out = np.zeros((B, P, L, N), dtype=np.uint32)
@@ -651,8 +680,7 @@ def fc_layer_masked(c0: np.ndarray, sh: np.ndarray, rho: np.ndarray, W: np.ndarr
         Dq = D % q
         dsh = (np.asarray(sh, dtype=np.uint64) % q) * Dq % q                    # Delta sh  [B][N]
         x = np.stack([c0[:, l, :].astype(np.uint32), dsh.astype(np.uint32)])    # [2][B][N]
-        w = np.stack([to_residues(rho, q), to_residues(-wpk, q)], axis=1)       # [P][2][N]
-        y = _sum_products(x, w, q, psi, tier)                                   # [P][B][N]
+        y = _sum_products(x, wl[l], q, psi, tier, w_ntt)                        # [P][B][N]
         for b in range(B):
             win = _fc_window(y[:, b, :].astype(np.uint64), lay)
             add = Dq * ((to_residues(dpk, q).astype(np.uint64) + np.asarray(shp[b], np.uint64)) % q) % q
@@ -714,16 +742,23 @@ def fc_layer(ct: np.ndarray, W: np.ndarray, Bv: np.ndarray | None,
     any message).  OUT_EXTRACTED keeps coefficients k < rows_j of each block
     (Theorem 1: they hold W I + B), zero elsewhere -> [B][P][2][L][N];
     OUT_PER_CHANNEL keeps every coefficient."""
-    B, J, L, N = ct.shape
     wpk = pack_fc_weights(W, lay)
     dpk = pack_fc_bias(Bv if Bv is not None else np.zeros(lay["n_out"], np.int64), lay)
+    return _fc_products(ct, [to_residues(wpk, q)[:, None, :] for q in primes], dpk, primes, psis, t, lay, mode,
+                        tier, False)
+
+
+def _fc_products(ct: np.ndarray, wl: list, dpk: np.ndarray, primes: list[int], psis: list[int], t: int,
+                 lay: dict, mode: int, tier: str, w_ntt: bool) -> np.ndarray:
+    """fc_layer's products, bias and window; wl[l]: [P][1][N] the packed
+    weights of limb l (their NTTs with w_ntt); dpk: [P][N] the packed bias."""
+    B, J, L, N = ct.shape
     D = delta_q(primes, t)
     P = lay["P"]
     out = np.zeros((B, P, 2, L, N), dtype=np.uint32)
     for l, (q, psi) in enumerate(zip(primes, psis)):
-        wr = to_residues(wpk, q)[:, None, :]                      # [P][1][N]
         x = np.ascontiguousarray(ct[:, :, l, :].reshape(1, B * 2, N))
-        yl = _sum_products(x, wr, q, psi, tier).reshape(P, B, 2, N)
+        yl = _sum_products(x, wl[l], q, psi, tier, w_ntt).reshape(P, B, 2, N)
         dres = to_residues(dpk, q).astype(np.uint64)
         yl[:, :, 0, :] = ((yl[:, :, 0, :].astype(np.uint64)
                            + (D % q) * dres[:, None, :]) % q).astype(np.uint32)
@@ -732,6 +767,77 @@ def fc_layer(ct: np.ndarray, W: np.ndarray, Bv: np.ndarray | None,
                 yl[j, :, :, lay["rows"][j]:] = 0
         out[:, :, :, l, :] = yl.transpose(1, 0, 2, 3)
     return out
+
+
+# ----------------------------------------------------------------------------
+# The server step split as the server runs it: model load, then requests
+# (Sec. IV-A: the NTTs of the server's plaintext polynomials are computed once
+# and stored, so a request pays only for its input transforms, the
+# coefficient-wise products, the inverse transforms and the slot copy).  The
+# "_load" functions pack and transform the weights once; the "_loaded" layer
+# functions are the NTT tier of the functions above on those transforms, with
+# the same results.
+# ----------------------------------------------------------------------------
+
+def _ntt_per_limb(wl: list, primes: list[int], psis: list[int]) -> list:
+    return [ntt_fwd(w, q, psi) for w, q, psi in zip(wl, primes, psis)]
+
+
+def conv_load(F: np.ndarray, primes: list[int], psis: list[int], lay: dict) -> list:
+    """Per limb, the NTTs of the packed filters fhat_{g,n}: [co][G][N]."""
+    fh = pack_filters(F, lay)
+    return _ntt_per_limb([to_residues(fh, q) for q in primes], primes, psis)
+
+
+def conv_layer_loaded(cts: np.ndarray, wn: list, primes: list[int], psis: list[int], lay: dict,
+                      mode: int = OUT_EXTRACTED) -> np.ndarray:
+    """conv_layer(..., tier="ntt") on weights from conv_load."""
+    return _conv_products(cts, wn, primes, psis, lay, mode, "ntt", True)
+
+
+def conv_masked_load(F: np.ndarray, rho: np.ndarray, primes: list[int], psis: list[int], lay: dict) -> list:
+    """Per limb, the NTTs of the masks rho_{g,n} and of -fhat_{g,n}: [co][2G][N]."""
+    fh = pack_filters(F, lay)
+    return _ntt_per_limb([np.concatenate([to_residues(rho, q), to_residues(-fh, q)], axis=1) for q in primes],
+                         primes, psis)
+
+
+def conv_layer_masked_loaded(c0: np.ndarray, sh: np.ndarray, wn: list, shp: np.ndarray, primes: list[int],
+                             psis: list[int], t: int, lay: dict) -> np.ndarray:
+    """conv_layer_masked(..., tier="ntt") on weights from conv_masked_load."""
+    return _conv_masked_products(c0, sh, wn, shp, primes, psis, t, lay, "ntt", True)
+
+
+def fc_load(W: np.ndarray, Bv: np.ndarray | None, primes: list[int], psis: list[int], lay: dict) -> tuple:
+    """Per limb, the NTTs of the packed weight blocks w_j ([P][1][N]), and
+    the packed bias d(X) ([P][N])."""
+    wpk = pack_fc_weights(W, lay)
+    dpk = pack_fc_bias(Bv if Bv is not None else np.zeros(lay["n_out"], np.int64), lay)
+    return _ntt_per_limb([to_residues(wpk, q)[:, None, :] for q in primes], primes, psis), dpk
+
+
+def fc_layer_loaded(ct: np.ndarray, loaded: tuple, primes: list[int], psis: list[int], t: int, lay: dict,
+                    mode: int = OUT_EXTRACTED) -> np.ndarray:
+    """fc_layer(..., tier="ntt") on weights from fc_load."""
+    wn, dpk = loaded
+    return _fc_products(ct, wn, dpk, primes, psis, t, lay, mode, "ntt", True)
+
+
+def fc_masked_load(W: np.ndarray, Bv: np.ndarray | None, rho: np.ndarray, primes: list[int], psis: list[int],
+                   lay: dict) -> tuple:
+    """Per limb, the NTTs of the masks rho_j and of -w_j ([P][2][N]), and
+    the packed bias d(X) ([P][N])."""
+    wpk = pack_fc_weights(W, lay)
+    dpk = pack_fc_bias(Bv if Bv is not None else np.zeros(lay["n_out"], np.int64), lay)
+    wl = [np.stack([to_residues(rho, q), to_residues(-wpk, q)], axis=1) for q in primes]
+    return _ntt_per_limb(wl, primes, psis), dpk
+
+
+def fc_layer_masked_loaded(c0: np.ndarray, sh: np.ndarray, loaded: tuple, shp: np.ndarray, primes: list[int],
+                           psis: list[int], t: int, lay: dict) -> np.ndarray:
+    """fc_layer_masked(..., tier="ntt") on weights from fc_masked_load."""
+    wn, dpk = loaded
+    return _fc_masked_products(c0, sh, wn, dpk, shp, primes, psis, t, lay, "ntt", True)
 
 
 # ----------------------------------------------------------------------------
