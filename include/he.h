@@ -31,10 +31,12 @@
  *    unspecified (but memory-safe) results.
  *  - Ownership: params and filter banks are created and freed by the
  *    library; activation buffers (inputs, outputs) are caller-owned device
- *    memory.  The layer calls allocate nothing, except that a call whose
- *    forward NTT workspace exceeds the params' current workspace grows it
- *    once (cudaMalloc, which synchronizes the device); he_params_reserve
- *    pre-sizes it so that later calls, and stream capture, never allocate.
+ *    memory.  The layer calls never allocate.  Their forward-NTT workspace
+ *    lives in the params and is sized at model load: each packing call
+ *    reserves what one call on its bank needs at the batch it was packed
+ *    for (B = 1, or he_pack_filters_for_batch's B), and he_params_reserve
+ *    reserves more.  A call that needs more workspace than the params hold
+ *    fails with HE_ERR_NOMEM before anything is launched.
  *    Calls that share one params handle share its workspace and must not
  *    overlap on the GPU (issue them on one stream).
  */
@@ -133,11 +135,18 @@ he_status he_params_primes(he_params_t p, uint32_t *primes_out);
 he_status he_params_psi(he_params_t p, uint32_t *psi_out);
 /* delta_out[L] <- floor(Q / t) mod q_l. */
 he_status he_params_delta(he_params_t p, uint32_t *delta_out);
-/* Grow the forward-NTT workspace to at least `bytes` now (blocking). */
+/* Grow the forward-NTT workspace to at least `bytes` now (blocking; a
+ * model-load step: it may free and reallocate the workspace, so no call on
+ * these params may be in flight).  HE_ERR_NOMEM if the device has no room. */
 he_status he_params_reserve(he_params_t p, size_t bytes);
-/* Workspace bytes a he_conv_layer / he_fc_layer call with these arguments needs. */
+/* Workspace bytes a he_conv_layer call on a bank of this layer with B
+ * ciphertexts needs (B * G * 2 * L * N words with HE_COEFF inputs; the
+ * masked and client Conv steps need the same); HE_NTT inputs need none. */
 he_status he_conv_workspace_bytes(he_params_t p, const he_conv_desc *d, uint32_t B,
                                   size_t *bytes);
+/* Workspace bytes a he_fc_layer call with B ciphertexts needs (B * 2 * L * N
+ * words; the masked and client FC steps need the same). */
+he_status he_fc_workspace_bytes(he_params_t p, uint32_t B, size_t *bytes);
 void he_params_destroy(he_params_t p);
 
 he_status he_conv_layout_query(he_params_t p, const he_conv_desc *d, he_conv_layout *out);
@@ -223,7 +232,10 @@ void he_filters_destroy(he_filters_t f);
  *          HE_OUT_EXTRACTED / HE_OUT_EXTRACTED_UNFOLDED: [B][H][2][L][N];
  *          HE_OUT_PER_CHANNEL: [B][co][2][L][N] (y_n itself).
  *          Every word is written.  Must not overlap d_in.
- *   B >= 1.  Asynchronous on `stream`. */
+ *   B >= 1.  Asynchronous on `stream`.
+ * HE_COEFF inputs are transformed into the params' workspace, which must
+ * hold he_conv_workspace_bytes(B) (HE_ERR_NOMEM otherwise, nothing
+ * launched). */
 he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain,
                         uint32_t *d_out, int out_mode, uint32_t B, void *stream);
 
@@ -231,10 +243,11 @@ he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int
  * counterpart: this is a library-side variant for callers that must never
  * see a layer call allocate, such as a server that has divided its whole HBM
  * budget between requests before it starts, or a process whose device memory
- * belongs to an outside allocator.  he_conv_layer grows the params'
- * workspace with cudaMalloc when a call needs more; this entry point instead
- * transforms coefficient-domain inputs into a fixed 8 MiB scratch array
- * compiled into the library (one per device), so a call never allocates.
+ * belongs to an outside allocator.  he_conv_layer transforms
+ * coefficient-domain inputs into the params' workspace, which the library
+ * allocates at model load and which bounds the batch a call may have; this
+ * entry point instead uses a fixed 8 MiB scratch array compiled into the
+ * library (one per device), so it needs no workspace reservation at all.
  *   Arguments, layouts, results and asynchrony are those of he_conv_layer,
  *   which this call matches word for word.
  *   Limit: with in_domain == HE_COEFF, B * G * 2 * L * N must be at most
@@ -281,7 +294,8 @@ he_status he_pack_masked(he_params_t p, const he_conv_desc *d, const int8_t *w, 
  * The client adds its own c1^r (computed from v, p1, p2) and decodes
  * round(t (c0^r + c1^r) / Q) mod t: no secret key is involved.  f must come
  * from he_pack_masked (other banks fail with HE_ERR_ARG; masked banks do
- * not run in plans).  Asynchronous on `stream`. */
+ * not run in plans).  Asynchronous on `stream`.  Uses
+ * he_conv_workspace_bytes(B) of params workspace (HE_ERR_NOMEM otherwise). */
 he_status he_conv_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0,
                                const uint32_t *d_sh, const uint32_t *d_shp, int in_domain,
                                uint32_t *d_out, uint32_t B, void *stream);
@@ -304,7 +318,8 @@ he_status he_pack_client(he_params_t p, const he_conv_desc *d, const uint32_t *p
  *          (|value| < q_l).
  *   d_out: DEVICE uint32 [B][H][L][N], c1^r; every word written.
  * The plaintext of the layer is then round(t (c0^r + c1^r) / Q) mod t minus
- * sh'.  f must come from he_pack_client.  Asynchronous on `stream`. */
+ * sh'.  f must come from he_pack_client.  Asynchronous on `stream`.  Uses
+ * he_conv_workspace_bytes(B) of params workspace (HE_ERR_NOMEM otherwise). */
 he_status he_conv_client(he_params_t p, he_filters_t f, const int32_t *d_v, const int32_t *d_ish,
                          uint32_t *d_out, uint32_t B, void *stream);
 
@@ -318,7 +333,9 @@ he_status he_conv_client(he_params_t p, he_filters_t f, const int32_t *d_v, cons
  *          j*rows_per_poly + k of W I + B ("only the first n_o coefficients
  *          need to be computed", Sec. III-B); the rest are 0.
  *          HE_OUT_PER_CHANNEL: every coefficient of the product (+ bias).
- *   Asynchronous on `stream`. */
+ *   Asynchronous on `stream`.  HE_COEFF inputs need
+ *   he_fc_workspace_bytes(B) of params workspace (HE_ERR_NOMEM otherwise,
+ *   nothing launched). */
 he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain,
                       uint32_t *d_out, int out_mode, uint32_t B, void *stream);
 
@@ -343,7 +360,8 @@ he_status he_pack_fc_masked(he_params_t p, uint32_t n_in, uint32_t n_out, const 
  *   d_shp: DEVICE uint32 [B][P_fc][N], the new share sh', integers in [0, t).
  *   d_out: DEVICE uint32 [B][P_fc][L][N], every word written.
  * round(t (c0^r + c1^r) / Q) mod t minus sh' is then W I + B on each window.
- * Asynchronous on `stream`. */
+ * Asynchronous on `stream`.  Uses he_fc_workspace_bytes(B) of params
+ * workspace (HE_ERR_NOMEM otherwise). */
 he_status he_fc_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0,
                              const uint32_t *d_sh, const uint32_t *d_shp, int in_domain,
                              uint32_t *d_out, uint32_t B, void *stream);
@@ -359,7 +377,8 @@ he_status he_pack_fc_client(he_params_t p, uint32_t n_in, uint32_t n_out, const 
  *   d_v:   DEVICE int32 [B][N], the randomness v of the client's encryption.
  *   d_ish: DEVICE int32 [B][N], the packed FC input plus the share.
  *   d_out: DEVICE uint32 [B][P_fc][L][N]; every word written.
- * f must come from he_pack_fc_client.  Asynchronous on `stream`. */
+ * f must come from he_pack_fc_client.  Asynchronous on `stream`.  Uses
+ * he_fc_workspace_bytes(B) of params workspace (HE_ERR_NOMEM otherwise). */
 he_status he_fc_client(he_params_t p, he_filters_t f, const int32_t *d_v, const int32_t *d_ish,
                        uint32_t *d_out, uint32_t B, void *stream);
 
@@ -479,6 +498,11 @@ he_status he_plan_tuning_default(he_plan_tuning *t);
  * for a knob outside the values listed above.  Blocking. */
 he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *t,
                                he_plan_t *out);
+/* Device workspace bytes he_plan_create would allocate for these calls (the
+ * default tuning), without allocating anything: lets a caller that admits
+ * work under a memory budget check it first.  d_in / d_out may be NULL here;
+ * every other field is validated as he_plan_create does. */
+he_status he_plan_workspace_bytes(const he_layer_call *calls, uint32_t ncalls, size_t *bytes);
 /* Autotuner: finds the fastest tuning for these calls by timing whole plan
  * runs on `stream` (CUDA events; per candidate 2 warm-up runs, then the
  * best of three batches of `iters` timed runs; one knob at a time in the
@@ -556,8 +580,10 @@ void he_plan_destroy(he_plan_t plan);
  * the next batch of its layer as soon as it is there, while other batches
  * run on other streams), copies host->device, runs, copies device->host.
  * Device buffers for a batch (its inputs, outputs and plan workspace) are
- * allocated on demand while their total stays within hbm_budget_bytes and
- * are reused; when the budget is spent, requests wait.  Each request's
+ * sized before anything is allocated and allocated only while their total
+ * stays within hbm_budget_bytes; they are reused.  When the budget is spent,
+ * idle buffers of other shapes are retired and freed once no batch is in
+ * flight (freeing synchronizes the device), and requests wait.  Each request's
  * words are those of he_conv_layer / he_fc_layer (HE_OUT_EXTRACTED) on its
  * own, whatever it was batched with.  Host buffers in page-locked memory
  * let the copies overlap; they must stay valid until the request finishes.
@@ -584,14 +610,17 @@ typedef struct {
     uint64_t batches, batched_calls;  /* plan runs; layer calls (ciphertexts) in them */
     uint64_t lanes;                   /* batch buffers allocated now */
     uint64_t bytes_in_use, bytes_peak;
+    uint64_t evictions;               /* idle lanes freed to make room for another shape */
+    uint64_t batch_hist[4];           /* batches of 1, 2, 4 and 8 ciphertexts */
 } he_server_report_t;
 
 /* Starts the scheduler thread.  Blocking. */
 he_status he_server_create(const he_server_config *cfg, he_server_t *out);
 /* Registers a model: `layers` are its banks in order (Conv and FC, one
  * params).  The banks must outlive the server.  *model_id is the handle.
- * HE_ERR_ARG if a layer's batch-1 buffers (twice its input plus output
- * words) do not fit hbm_budget_bytes.  Blocking: builds one lane (batch
+ * HE_ERR_ARG if a layer's batch-1 lane (its input and output words and
+ * its one-call plan's workspace) does not fit hbm_budget_bytes.  Blocking:
+ * builds one lane (batch
  * buffers and plan) per layer and batch size (powers of two up to
  * max_batch) while the budget allows; the others are built on demand. */
 he_status he_server_add_model(he_server_t s, const he_filters_t *layers, uint32_t nlayers,

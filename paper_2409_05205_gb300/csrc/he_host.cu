@@ -208,6 +208,19 @@ he_status ensure_ws(he_params_s *p, size_t bytes) {
     return HE_OK;
 }
 
+// A layer call takes its forward-transform workspace from the params.  The
+// workspace is sized at model load (each packing call reserves what its
+// bank needs at the batch it was packed for; he_params_reserve reserves
+// more), so a call never allocates: one that needs more than the params
+// hold fails before any launch.
+he_status need_ws(const he_params_s *p, size_t bytes) {
+    if (bytes <= p->ws_bytes) return HE_OK;
+    return fail(HE_ERR_NOMEM,
+                "the call needs %zu bytes of workspace and the params hold %zu; reserve them at model load "
+                "(he_params_reserve with he_conv_workspace_bytes / he_fc_workspace_bytes)",
+                bytes, p->ws_bytes);
+}
+
 }  // namespace
 
 // Sets the thread-local message of he_last_error for code outside this file.
@@ -371,6 +384,12 @@ he_status he_conv_workspace_bytes(he_params_t p, const he_conv_desc *d, uint32_t
     return HE_OK;
 }
 
+he_status he_fc_workspace_bytes(he_params_t p, uint32_t B, size_t *bytes) {
+    if (!p || !bytes) return fail(HE_ERR_ARG, "NULL argument");
+    *bytes = (size_t)B * 2u * p->L * p->N * sizeof(uint32_t);
+    return HE_OK;
+}
+
 void he_params_destroy(he_params_t p) {
     if (!p) return;
     if (p->device == HE_DEVICE_NONE) {
@@ -496,6 +515,12 @@ static he_status pack_conv(he_params_t p, const he_conv_desc *d, const int8_t *w
         he_filters_destroy(f);
         return cuda_fail(e, "pack filters");
     }
+    // the workspace of a call at the packed batch with coefficient-domain inputs
+    st = ensure_ws(p, (size_t)batch * lay.G * 2u * p->L * p->N * sizeof(uint32_t));
+    if (st != HE_OK) {
+        he_filters_destroy(f);
+        return st;
+    }
     *out = f;
     return HE_OK;
 }
@@ -560,6 +585,11 @@ he_status he_pack_masked(he_params_t p, const he_conv_desc *d, const int8_t *w, 
         he_filters_destroy(f);
         return cuda_fail(e, "pack masked bank");
     }
+    st = ensure_ws(p, (size_t)2u * lay.G * p->L * p->N * sizeof(uint32_t));  // one ciphertext: c0 and sh
+    if (st != HE_OK) {
+        he_filters_destroy(f);
+        return st;
+    }
     *out = f;
     return HE_OK;
 }
@@ -614,6 +644,11 @@ he_status he_pack_client(he_params_t p, const he_conv_desc *d, const uint32_t *p
         he_filters_destroy(f);
         return cuda_fail(e, "pack client bank");
     }
+    st = ensure_ws(p, (size_t)2u * lay.G * p->L * p->N * sizeof(uint32_t));  // one ciphertext: -v and i + sh
+    if (st != HE_OK) {
+        he_filters_destroy(f);
+        return st;
+    }
     *out = f;
     return HE_OK;
 }
@@ -630,7 +665,7 @@ he_status he_conv_client(he_params_t p, he_filters_t f, const int32_t *d_v, cons
     const size_t ws_words = (size_t)B * 2u * lay.G * p->L * p->N;
     DeviceGuard g(p->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
-    if (ensure_ws(p, ws_words * 4u) != HE_OK) return HE_ERR_NOMEM;
+    if (need_ws(p, ws_words * 4u) != HE_OK) return HE_ERR_NOMEM;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t *ws = static_cast<uint32_t *>(p->ws);
     cudaError_t e = he_launch_client_in(p->ring, d_v, d_ish, ws, B, lay.G, st);
@@ -696,6 +731,11 @@ he_status he_pack_fc(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t 
         he_filters_destroy(f);
         return cuda_fail(e, "pack FC");
     }
+    st = ensure_ws(p, (size_t)2u * p->L * p->N * sizeof(uint32_t));  // one ciphertext
+    if (st != HE_OK) {
+        he_filters_destroy(f);
+        return st;
+    }
     *out = f;
     return HE_OK;
 }
@@ -728,7 +768,7 @@ he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t *x = d_in;
     if (in_domain == HE_COEFF) {
-        he_status s = ensure_ws(p, nin * sizeof(uint32_t));
+        he_status s = need_ws(p, nin * sizeof(uint32_t));
         if (s != HE_OK) return s;
         cudaError_t e = he_launch_ntt(p->ring, d_in, (uint32_t *)p->ws, (uint32_t)(nin / ((size_t)p->L * p->N) * p->L), false, st);
         if (e != cudaSuccess) return cuda_fail(e, "input NTT");
@@ -753,7 +793,7 @@ he_status he_conv_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_
     const size_t ws_words = (size_t)B * 2u * lay.G * p->L * p->N;
     DeviceGuard g(p->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
-    if (ensure_ws(p, ws_words * 4u) != HE_OK) return HE_ERR_NOMEM;
+    if (need_ws(p, ws_words * 4u) != HE_OK) return HE_ERR_NOMEM;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t *ws = static_cast<uint32_t *>(p->ws);
     cudaError_t e = he_launch_ntt_masked_in(p->ring, d_c0, d_sh, ws, B, lay.G, in_domain == HE_NTT, st);
@@ -779,7 +819,7 @@ he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int i
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t *x = d_in;
     if (in_domain == HE_COEFF) {
-        he_status s = ensure_ws(p, nin * sizeof(uint32_t));
+        he_status s = need_ws(p, nin * sizeof(uint32_t));
         if (s != HE_OK) return s;
         cudaError_t e = he_launch_ntt(p->ring, d_in, (uint32_t *)p->ws, 2u * B * p->L, false, st);
         if (e != cudaSuccess) return cuda_fail(e, "input NTT");
@@ -842,6 +882,11 @@ static he_status pack_fc_masked(he_params_t p, uint32_t n_in, uint32_t n_out, in
         he_filters_destroy(f);
         return cuda_fail(e, mode == 1 ? "pack masked FC bank" : "pack client FC bank");
     }
+    st = ensure_ws(p, (size_t)2u * p->L * p->N * sizeof(uint32_t));  // one ciphertext: c0 and sh (or -v, i + sh)
+    if (st != HE_OK) {
+        he_filters_destroy(f);
+        return st;
+    }
     *out = f;
     return HE_OK;
 }
@@ -869,7 +914,7 @@ he_status he_fc_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0
     if (need_device(p) != HE_OK) return HE_ERR_ARG;
     DeviceGuard g(p->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
-    if (ensure_ws(p, (size_t)B * 2u * p->L * p->N * 4u) != HE_OK) return HE_ERR_NOMEM;
+    if (need_ws(p, (size_t)B * 2u * p->L * p->N * 4u) != HE_OK) return HE_ERR_NOMEM;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t *ws = static_cast<uint32_t *>(p->ws);
     cudaError_t e = he_launch_ntt_masked_in(p->ring, d_c0, d_sh, ws, B, 1u, in_domain == HE_NTT, st);
@@ -887,7 +932,7 @@ he_status he_fc_client(he_params_t p, he_filters_t f, const int32_t *d_v, const 
     if (need_device(p) != HE_OK) return HE_ERR_ARG;
     DeviceGuard g(p->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", p->device);
-    if (ensure_ws(p, (size_t)B * 2u * p->L * p->N * 4u) != HE_OK) return HE_ERR_NOMEM;
+    if (need_ws(p, (size_t)B * 2u * p->L * p->N * 4u) != HE_OK) return HE_ERR_NOMEM;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t *ws = static_cast<uint32_t *>(p->ws);
     cudaError_t e = he_launch_client_in(p->ring, d_v, d_ish, ws, B, 1u, st);
@@ -1089,13 +1134,33 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
     return he_plan_create_tuned(calls, ncalls, &t, out);
 }
 
+namespace {
+he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning, he_plan_t *out,
+                     size_t *ws_only);
+}  // namespace
+
 he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning,
                                he_plan_t *out) {
+    return plan_build(calls, ncalls, tuning, out, nullptr);
+}
+
+he_status he_plan_workspace_bytes(const he_layer_call *calls, uint32_t ncalls, size_t *bytes) {
+    if (!bytes) return fail(HE_ERR_ARG, "NULL argument");
+    he_plan_tuning t;
+    he_plan_tuning_default(&t);
+    return plan_build(calls, ncalls, &t, nullptr, bytes);
+}
+
+namespace {
+// Builds a plan, or with ws_only set only validates the calls and returns the
+// workspace the plan would own (nothing allocated; d_in / d_out may be NULL).
+he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning, he_plan_t *out,
+                     size_t *ws_only) {
     if (!tuning) return fail(HE_ERR_ARG, "NULL tuning");
     if (check_tuning(*tuning) != HE_OK) return HE_ERR_ARG;
     const he_plan_tuning tu = *tuning;
-    if (!calls || !out || ncalls == 0) return fail(HE_ERR_ARG, "NULL argument or empty plan");
-    *out = nullptr;
+    if (!calls || (!out && !ws_only) || ncalls == 0) return fail(HE_ERR_ARG, "NULL argument or empty plan");
+    if (out) *out = nullptr;
     const he_params_s *p0 = calls[0].filters ? calls[0].filters->p : nullptr;
     if (!p0) return fail(HE_ERR_ARG, "call 0 has no filters");
     const int device = p0->device;
@@ -1114,7 +1179,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
     for (uint32_t i = 0; i < ncalls; ++i) {
         const he_layer_call &c = calls[i];
         const he_filters_s *f = c.filters;
-        if (!f || !c.d_in || !c.d_out) return fail(HE_ERR_ARG, "call %u: NULL argument", i);
+        if (!f || (!ws_only && (!c.d_in || !c.d_out))) return fail(HE_ERR_ARG, "call %u: NULL argument", i);
         // 0: ciphertext x plaintext; 1: masked server step; 2: client step (Alg. 1 / Alg. 2)
         const uint32_t msrc = f->masked;
         if (msrc == 1 && (!c.d_share || !c.d_share_out))
@@ -1259,6 +1324,10 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
             z_off[i] = ws_words;
             ws_words += (size_t)g.L * g.ncols * g.co * g.M;
         }
+    if (ws_only) {
+        *ws_only = ws_words * sizeof(uint32_t);
+        return HE_OK;
+    }
     for (size_t a = 0; a < ranges.size(); ++a)
         for (size_t b = a + 1; b < ranges.size(); ++b) {
             if (!ranges[a].is_out && !ranges[b].is_out) continue;  // inputs may be shared
@@ -1505,6 +1574,7 @@ he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, cons
     *out = pl;
     return HE_OK;
 }
+}  // namespace
 
 he_status he_plan_check(he_plan_t plan) {
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");

@@ -8,7 +8,8 @@
 //    for every 32-bit a.
 //  * Harvey's lazy butterflies: forward (Cooley-Tukey) values stay in
 //    [0, 4q), inverse (Gentleman-Sande) values in [0, 2q); 4q < 2^32.
-//  * 64-bit accumulators of up to 15 products (< 2^64) reduced by
+//  * 64-bit accumulators of up to 16 products of fully reduced residues
+//    (each below (q-1)^2 < 2^60, so the sum stays below 2^64) reduced by
 //    x = hi 2^32 + lo -> (hi * (2^32 mod q) + lo) with two Shoup products.
 #pragma once
 

@@ -1,14 +1,15 @@
 // he_noalloc.cu -- he_conv_layer_noalloc: the Conv layer call with no device
 // allocation on its path.
 //
-// he_conv_layer transforms coefficient-domain inputs into a workspace that
-// the params handle grows with cudaMalloc when a call needs more room.  Some
-// callers cannot let a layer call allocate: a serving loop that has split its
-// whole HBM budget between requests up front, or a process whose device
-// memory is owned by an outside allocator, must not see cudaMalloc (which can
-// fail under memory pressure at an arbitrary call, and can synchronize the
-// device) appear in the middle of their work.  This entry point keeps that
-// transform's scratch in a fixed array compiled into the library instead.
+// he_conv_layer transforms coefficient-domain inputs into the params'
+// workspace, which the library cudaMallocs at model load and which caps the
+// batch of a call.  Some callers cannot have the library allocate device
+// memory for them at all: a serving loop that has split its whole HBM budget
+// between requests up front, or a process whose device memory is owned by an
+// outside allocator, must not see cudaMalloc (which can fail under memory
+// pressure, and can synchronize the device) when a larger batch comes in.
+// This entry point keeps that transform's scratch in a fixed array compiled
+// into the library instead.
 #include <cstdio>
 #include <mutex>
 

@@ -11,9 +11,12 @@
 // as a slot is free, while other batches run -- and runs each batch on one
 // of several streams: host->device copies, the layer as a one-call plan,
 // device->host copies, then a host callback.  Device buffers ("lanes": the
-// batch's inputs and outputs and the plan's workspace) are allocated on
-// demand under an HBM budget and reused; when the budget is spent, requests
-// wait for a lane to free up.
+// batch's inputs and outputs and the plan's workspace) are allocated under an
+// HBM budget and reused.  A lane's size is known before anything is
+// allocated, so device memory never exceeds the budget; when the budget is
+// spent, idle lanes of other shapes are retired, and their memory is freed
+// once no batch is in flight (cudaFree waits for the whole device, so
+// freeing earlier would stall every stream); requests wait meanwhile.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -84,8 +87,10 @@ struct Server {
     std::map<std::pair<uint32_t, uint32_t>, std::deque<Req *>> queues;  // (model, layer) -> waiting
     std::vector<Batch *> failed_launch;
     std::vector<Lane *> lanes;
+    std::vector<Lane *> retired;  // evicted idle lanes, counted in bytes_in_use until freed
     size_t bytes_in_use = 0, bytes_peak = 0;
     uint64_t next_id = 1, submitted = 0, finished = 0, batches = 0, batched_calls = 0, failed = 0;
+    uint64_t evictions = 0, batch_hist[4] = {0, 0, 0, 0};
     uint32_t inflight = 0;
     std::vector<double> lat_layer, lat_net;
     bool stop = false;
@@ -116,33 +121,56 @@ uint32_t bucket_of(uint32_t n, uint32_t max_batch) {
     return b;
 }
 
-// Frees one idle lane (another shape's buffers and plan); false if none is idle.
-bool free_idle_lane(Server *s) {
+void free_lane(Server *s, Lane *l) {
+    he_plan_destroy(l->plan);
+    cudaFree(l->d_in);
+    cudaFree(l->d_out);
+    s->bytes_in_use -= l->bytes;
+    delete l;
+}
+
+// Retires one idle lane (another shape's buffers and plan); false if none is
+// idle.  Its bytes stay counted until free_retired releases them.
+bool retire_idle_lane(Server *s) {
     for (size_t i = 0; i < s->lanes.size(); ++i) {
         Lane *l = s->lanes[i];
         if (l->busy) continue;
-        he_plan_destroy(l->plan);
-        cudaFree(l->d_in);
-        cudaFree(l->d_out);
-        s->bytes_in_use -= l->bytes;
-        delete l;
+        s->retired.push_back(l);
         s->lanes.erase(s->lanes.begin() + (long)i);
+        ++s->evictions;
         return true;
     }
     return false;
 }
 
+// Frees the retired lanes, only while no batch is in flight: cudaFree
+// synchronizes the device, which then stalls nothing.
+void free_retired(Server *s) {
+    if (s->inflight != 0 || s->retired.empty()) return;
+    for (Lane *l : s->retired) free_lane(s, l);
+    s->retired.clear();
+}
+
 // a free lane for (model, layer, bucket), allocating one if the budget
-// allows -- idle lanes of other shapes are freed until the new lane's
-// buffers and its plan's workspace fit; nullptr when none can be had now.
-// Called with s->mu held.
-Lane *get_lane(Server *s, uint32_t model, uint32_t layer, uint32_t bucket) {
+// allows.  The lane's bytes (batch buffers plus its plan's workspace) are
+// computed first; idle lanes of other shapes are retired until they fit,
+// and nothing is allocated unless they do.  nullptr when none can be had
+// now.  At model load (may_retire false) no lane is retired.  Called with
+// s->mu held.
+Lane *get_lane(Server *s, uint32_t model, uint32_t layer, uint32_t bucket, bool may_retire = true) {
     for (Lane *l : s->lanes)
         if (!l->busy && l->model == model && l->layer == layer && l->bucket == bucket) return l;
     const ModelLayer &ml = s->models[model].layers[layer];
     const size_t io = (ml.in_words + ml.out_words) * bucket * sizeof(uint32_t);
-    while (s->bytes_in_use + io > s->cfg.hbm_budget_bytes)
-        if (!free_idle_lane(s)) return nullptr;
+    he_layer_call c{ml.f, nullptr, HE_COEFF, nullptr, bucket};
+    size_t ws = 0;
+    if (he_plan_workspace_bytes(&c, 1, &ws) != HE_OK) return nullptr;
+    const size_t need = io + ws;
+    if (need > s->cfg.hbm_budget_bytes) return nullptr;
+    while (may_retire && s->bytes_in_use + need > s->cfg.hbm_budget_bytes && retire_idle_lane(s)) {
+    }
+    if (s->bytes_in_use + need > s->cfg.hbm_budget_bytes) free_retired(s);
+    if (s->bytes_in_use + need > s->cfg.hbm_budget_bytes) return nullptr;
     Lane *l = new (std::nothrow) Lane();
     if (!l) return nullptr;
     l->model = model;
@@ -156,25 +184,15 @@ Lane *get_lane(Server *s, uint32_t model, uint32_t layer, uint32_t bucket) {
         delete l;
         return nullptr;
     }
-    he_layer_call c{ml.f, l->d_in, HE_COEFF, l->d_out, bucket};
+    c.d_in = l->d_in;
+    c.d_out = l->d_out;
     if (he_plan_create(&c, 1, &l->plan) != HE_OK) {
         cudaFree(l->d_in);
         cudaFree(l->d_out);
         delete l;
         return nullptr;
     }
-    he_plan_info info{};
-    he_plan_query(l->plan, &info, nullptr);
-    l->bytes = io + info.workspace_bytes;
-    bool fits = true;
-    while (fits && s->bytes_in_use + l->bytes > s->cfg.hbm_budget_bytes) fits = free_idle_lane(s);
-    if (!fits) {  // the workspace does not fit while other lanes are busy
-        he_plan_destroy(l->plan);
-        cudaFree(l->d_in);
-        cudaFree(l->d_out);
-        delete l;
-        return nullptr;
-    }
+    l->bytes = need;
     s->bytes_in_use += l->bytes;
     s->bytes_peak = std::max(s->bytes_peak, s->bytes_in_use);
     s->lanes.push_back(l);
@@ -210,6 +228,7 @@ bool launch(Server *s, Lane *lane, std::vector<Req *> &rs) {
     ++s->inflight;
     ++s->batches;
     s->batched_calls += rs.size();
+    ++s->batch_hist[rs.size() >= 8 ? 3 : (rs.size() >= 4 ? 2 : (rs.size() >= 2 ? 1 : 0))];
     return true;
 }
 
@@ -256,6 +275,7 @@ void scheduler(Server *s) {
         s->failed_launch.clear();
         for (Batch *b : done) finish_batch(s, b);
         if (!done.empty()) s->cv_done.notify_all();
+        free_retired(s);
         if (s->stop && s->inflight == 0) break;
         // dispatch: oldest waiting request first, each batch from one queue
         bool progress = true;
@@ -348,9 +368,13 @@ he_status he_server_add_model(he_server_t s, const he_filters_t *layers, uint32_
             ml.in_words = 2u * LN;
             ml.out_words = (size_t)f->fl.P_fc * 2u * LN;
         }
-        // a batch-1 buffer set (inputs, outputs, and a workspace of about
-        // the same size) must fit the budget, or the layer could never run
-        if (2u * (ml.in_words + ml.out_words) * sizeof(uint32_t) > s->cfg.hbm_budget_bytes)
+        // a batch-1 lane (inputs, outputs and its plan's workspace) must fit
+        // the budget, or the layer could never run
+        he_layer_call c{layers[i], nullptr, HE_COEFF, nullptr, 1};
+        size_t ws = 0;
+        const he_status st = he_plan_workspace_bytes(&c, 1, &ws);
+        if (st != HE_OK) return st;
+        if ((ml.in_words + ml.out_words) * sizeof(uint32_t) + ws > s->cfg.hbm_budget_bytes)
             return he_fail(HE_ERR_ARG, "hbm_budget_bytes is too small for one of the model's layers");
         m.layers.push_back(ml);
     }
@@ -362,7 +386,7 @@ he_status he_server_add_model(he_server_t s, const he_filters_t *layers, uint32_
     // request path (a plan build allocates and copies synchronously)
     for (uint32_t b = 1; b <= s->cfg.max_batch; b *= 2)
         for (uint32_t i = 0; i < nlayers; ++i)
-            if (!get_lane(s, *model_id, i, b)) return HE_OK;  // budget reached: the rest on demand
+            if (!get_lane(s, *model_id, i, b, false)) return HE_OK;  // budget reached: the rest on demand
     return HE_OK;
 }
 
@@ -422,6 +446,8 @@ he_status he_server_report(he_server_t s, he_server_report_t *rep) {
     rep->lanes = s->lanes.size();
     rep->bytes_in_use = s->bytes_in_use;
     rep->bytes_peak = s->bytes_peak;
+    rep->evictions = s->evictions;
+    for (int i = 0; i < 4; ++i) rep->batch_hist[i] = s->batch_hist[i];
     return HE_OK;
 }
 
@@ -452,12 +478,8 @@ void he_server_destroy(he_server_t s) {
         cudaStreamSynchronize(st);
         cudaStreamDestroy(st);
     }
-    for (Lane *l : s->lanes) {
-        he_plan_destroy(l->plan);
-        cudaFree(l->d_in);
-        cudaFree(l->d_out);
-        delete l;
-    }
+    for (Lane *l : s->lanes) free_lane(s, l);
+    for (Lane *l : s->retired) free_lane(s, l);
     for (auto &kv : s->reqs) delete kv.second;
     cudaSetDevice(prev);
     delete s;

@@ -81,7 +81,8 @@ class he_request_stats(ctypes.Structure):
 
 class he_server_report_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "finished", "failed", "batches", "batched_calls",
-                                               "lanes", "bytes_in_use", "bytes_peak")]
+                                               "lanes", "bytes_in_use", "bytes_peak", "evictions")] + \
+               [("batch_hist", ctypes.c_uint64 * 4)]
 
 
 _lib = None
@@ -94,6 +95,7 @@ _SIGS = {
     "he_params_delta": [_vp, _vp],
     "he_params_reserve": [_vp, _sz],
     "he_conv_workspace_bytes": [_vp, ctypes.POINTER(he_conv_desc), _u32, ctypes.POINTER(_sz)],
+    "he_fc_workspace_bytes": [_vp, _u32, ctypes.POINTER(_sz)],
     "he_params_destroy": [_vp],
     "he_conv_layout_query": [_vp, ctypes.POINTER(he_conv_desc), ctypes.POINTER(he_conv_layout)],
     "he_fc_layout_query": [_vp, _u32, _u32, ctypes.POINTER(he_fc_layout)],
@@ -122,6 +124,7 @@ _SIGS = {
     "he_plan_create": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(_vp)],
     "he_plan_tuning_default": [ctypes.POINTER(he_plan_tuning)],
     "he_plan_create_tuned": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(he_plan_tuning), ctypes.POINTER(_vp)],
+    "he_plan_workspace_bytes": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(_sz)],
     "he_plan_autotune": [ctypes.POINTER(he_layer_call), _u32, _u32, _vp, ctypes.POINTER(he_plan_tuning),
                          ctypes.POINTER(_vp)],
     "he_plan_run": [_vp, _vp],
@@ -233,6 +236,12 @@ def he_conv_workspace_bytes(p: int, desc, B: int) -> int:
     out = _sz()
     d = _desc(desc)
     _check(lib().he_conv_workspace_bytes(p, ctypes.byref(d), B, ctypes.byref(out)))
+    return out.value
+
+
+def he_fc_workspace_bytes(p: int, B: int) -> int:
+    out = _sz()
+    _check(lib().he_fc_workspace_bytes(p, B, ctypes.byref(out)))
     return out.value
 
 
@@ -443,6 +452,14 @@ def he_plan_create_tuned(calls, tuning: dict) -> int:
     return out.value
 
 
+def he_plan_workspace_bytes(calls) -> int:
+    """Workspace he_plan_create would allocate for these calls (d_in / d_out
+    may be None); allocates nothing."""
+    out = _sz()
+    _check(lib().he_plan_workspace_bytes(_calls(calls), len(calls), ctypes.byref(out)))
+    return out.value
+
+
 def he_plan_autotune(calls, iters: int = 5, stream=None) -> tuple[int, dict]:
     """(plan, chosen tuning).  Runs the calls while timing candidates."""
     t = he_plan_tuning()
@@ -518,7 +535,9 @@ def he_server_wait(s: int, ticket: int, timeout_ms: int = 60000) -> dict:
 def he_server_report(s: int) -> dict:
     r = he_server_report_t()
     _check(lib().he_server_report(s, ctypes.byref(r)))
-    return {n: getattr(r, n) for n, _ in he_server_report_t._fields_}
+    d = {n: getattr(r, n) for n, _ in he_server_report_t._fields_}
+    d["batch_hist"] = {str(1 << i): int(r.batch_hist[i]) for i in range(4)}
+    return d
 
 
 def he_server_latencies(s: int, which: int) -> np.ndarray:

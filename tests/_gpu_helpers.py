@@ -77,11 +77,18 @@ def ring(N, L):
     return ps, [O.root_2n(q, N) for q in ps]
 
 
+def reserve(p, nbytes: int) -> None:
+    """The model-load step before calls of a larger batch than a bank was
+    packed for: the layer calls never grow the params' workspace."""
+    he().he_params_reserve(p, int(nbytes))
+
+
 def run_conv(p, f, cts: np.ndarray, mode: int, out_polys: int, in_domain=None):
     """cts: [B][G][2][L][N] coefficient-domain residues."""
     H = he()
     torch = torch_cuda()
     B, G, _, L, N = cts.shape
+    reserve(p, cts.size * 4)
     x = cts
     if in_domain == H.HE_NTT:
         ps, psis = ring(N, L)
@@ -100,6 +107,7 @@ def run_fc(p, f, ct: np.ndarray, mode: int, P: int):
     H = he()
     torch = torch_cuda()
     B, _, L, N = ct.shape
+    reserve(p, ct.size * 4)
     d_in = to_dev(ct)
     d_out = empty_dev((B, P, 2, L, N))
     H.he_fc_layer(p, f, d_in, H.HE_COEFF, d_out, mode, B, torch.cuda.current_stream())

@@ -82,6 +82,7 @@ def test_fc_with_the_widest_input():
         f = H.he_pack_fc(p, n_in, n_out, W, Bv)
         try:
             d_out = U.empty_dev(ref.shape)
+            U.reserve(p, H.he_fc_workspace_bytes(p, B))
             H.he_fc_layer(p, f, U.to_dev(ct), H.HE_COEFF, d_out, H.HE_OUT_EXTRACTED, B, torch.cuda.current_stream())
             H.he_sync(torch.cuda.current_stream())
             np.testing.assert_array_equal(U.from_dev(d_out).reshape(ref.shape), ref)

@@ -33,6 +33,7 @@ def _run_masked(p, f, c0, sh, shp, dom, B, H):
     H_ = U.he()
     torch = U.torch_cuda()
     _, _, L, N = c0.shape
+    U.reserve(p, 2 * c0.size * 4)  # c0 and sh transformed side by side
     d_out = U.empty_dev((B, H, L, N))
     H_.he_conv_layer_masked(p, f, U.to_dev(c0), U.to_dev(sh), U.to_dev(shp), dom, d_out, B,
                             torch.cuda.current_stream())
@@ -192,6 +193,7 @@ def _protocol_case(N, L, ci, co, hw, seed):
 def _run_client(p, f, v, ish, B, Hh, L, N):
     H = U.he()
     torch = U.torch_cuda()
+    U.reserve(p, 2 * np.asarray(v).size * L * 4)  # -v and i + sh in every limb
     d_out = U.empty_dev((B, Hh, L, N))
     H.he_conv_client(p, f, torch.from_numpy(np.ascontiguousarray(v, np.int32).ravel()).cuda(),
                      torch.from_numpy(np.ascontiguousarray(ish, np.int32).ravel()).cuda(), d_out, B,

@@ -28,6 +28,7 @@ def _server(p, f, c0, sh, shp, dom, B, P):
     H = U.he()
     torch = U.torch_cuda()
     _, L, N = c0.shape
+    U.reserve(p, U.he().he_fc_workspace_bytes(p, B))
     d_out = U.empty_dev((B, P, L, N))
     H.he_fc_layer_masked(p, f, U.to_dev(c0), U.to_dev(sh), U.to_dev(shp), dom, d_out, B,
                          torch.cuda.current_stream())
@@ -38,6 +39,7 @@ def _server(p, f, c0, sh, shp, dom, B, P):
 def _client(p, f, v, ish, B, P, L, N):
     H = U.he()
     torch = U.torch_cuda()
+    U.reserve(p, H.he_fc_workspace_bytes(p, B))
     d_out = U.empty_dev((B, P, L, N))
     H.he_fc_client(p, f, torch.from_numpy(np.ascontiguousarray(v, np.int32).ravel()).cuda(),
                    torch.from_numpy(np.ascontiguousarray(ish, np.int32).ravel()).cuda(), d_out, B,

@@ -77,6 +77,9 @@ class _Case:
             self.d_in = U.to_dev(cts)
             self.d_sh = self.d_shp = None
         self.d_out = U.empty_dev(self.out_shape)
+        # every form transforms B * (G or 2G) * 2 * L * N / 2 ... words: the
+        # most any of them needs is B * 2G * L * N (G = 1 for an FC layer)
+        U.reserve(p, B * 2 * G * L * N * 4)
 
     def call(self):
         return (self.f, self.d_in, self.dom, self.d_out, self.B, self.d_sh, self.d_shp)

@@ -25,6 +25,7 @@ def _both(H, p, f, cts, mode, out_polys, in_domain):
     d_in = U.to_dev(cts)
     ref = U.empty_dev((B, out_polys, 2, L, N))
     got = U.empty_dev((B, out_polys, 2, L, N), fill=0x5A5A5A5A)
+    U.reserve(p, cts.size * 4)  # he_conv_layer's workspace, sized before its call
     H.he_conv_layer(p, f, d_in, in_domain, ref, mode, B, st)
     H.he_conv_layer_noalloc(p, f, d_in, in_domain, got, mode, B, st)
     H.he_sync(st)
@@ -49,6 +50,38 @@ def test_noalloc_matches_conv_layer_on_consecutive_calls(case):
                 np.testing.assert_array_equal(got, ref)
         ref, got = _both(H, p, f, cts, H.HE_OUT_EXTRACTED, lay["H"], H.HE_NTT)
         np.testing.assert_array_equal(got, ref)
+
+
+def test_noalloc_needs_no_workspace_and_allocates_nothing():
+    """On fresh params whose workspace only covers one ciphertext, a call of
+    three runs through the scratch alone (he_conv_layer refuses the same call
+    until it is reserved), and a second call leaves the device's free memory
+    unchanged."""
+    H = U.he()
+    torch = U.torch_cuda()
+    N, L, ci, co, h, w, B = 1024, 3, 16, 8, 8, 8, 3
+    ps, psis, lay, cts, F, desc = U.conv_case(N, L, ci, co, h, w, B, seed=25)
+    cts2 = U.synth.residues(26, "noalloc/fresh2", cts.shape, ps)
+    st = torch.cuda.current_stream()
+    with U.params(N, L) as p, U.conv_bank(p, desc, F) as f:
+        d_in, d_in2 = U.to_dev(cts), U.to_dev(cts2)
+        got = U.empty_dev((B, lay["H"], 2, L, N), fill=0x5A5A5A5A)
+        got2 = U.empty_dev((B, lay["H"], 2, L, N), fill=0x5A5A5A5A)
+        H.he_conv_layer_noalloc(p, f, d_in, H.HE_COEFF, got, H.HE_OUT_EXTRACTED, B, st)  # first call: set-up
+        H.he_sync(st)
+        free0 = torch.cuda.mem_get_info()[0]
+        H.he_conv_layer_noalloc(p, f, d_in2, H.HE_COEFF, got2, H.HE_OUT_EXTRACTED, B, st)
+        H.he_sync(st)
+        assert torch.cuda.mem_get_info()[0] == free0
+        ref = U.empty_dev((B, lay["H"], 2, L, N))
+        with pytest.raises(H.HEError) as ei:
+            H.he_conv_layer(p, f, d_in, H.HE_COEFF, ref, H.HE_OUT_EXTRACTED, B, st)
+        assert ei.value.status == H.HE_ERR_NOMEM
+        U.reserve(p, cts.size * 4)
+        for x, g in ((d_in, got), (d_in2, got2)):
+            H.he_conv_layer(p, f, x, H.HE_COEFF, ref, H.HE_OUT_EXTRACTED, B, st)
+            H.he_sync(st)
+            np.testing.assert_array_equal(U.from_dev(g), U.from_dev(ref))
 
 
 def test_noalloc_matches_the_oracle():
