@@ -11,9 +11,10 @@ inference = the 20 server-side layer calls.
 Forms measured (same model, same inputs, same output words):
   graph  a plan of the 20 independent layer calls (he_plan_create): one
          kernel for every input NTT, a persistent MAC kernel over every
-         Conv layer's weights, a finishing kernel (inverse transforms and
-         extraction) and the FC kernel on a forked stream, captured once in
-         a CUDA graph and replayed once per step -- the headline `value`
+         Conv layer's weights and a finishing kernel (inverse transforms and
+         extraction, and the FC layer's product, inverse transform and
+         window), captured once in a CUDA graph and replayed once per step
+         -- the headline `value`
          and its p50/p99 per-inference latency;
   phases the same plan run without the graph in three phases (input NTTs,
          MAC, the rest) with CUDA events between them -- the MAC kernel's
@@ -290,17 +291,19 @@ class Arm:
         return ch_bytes, ntt_bytes, bfly
 
     def butterflies(self, form):
-        """Algorithmic butterflies of the input-NTT kernel (every Conv call's
-        input polynomials: (N/2) log2 N each) and of the finishing kernel
-        (every split-form call: one length-N/s inverse transform per output
-        channel, limb and column: (M/2) log2 M each)."""
+        """Algorithmic butterflies of the input-NTT kernel (every Conv and FC
+        call's input polynomials: (N/2) log2 N each) and of the finishing
+        kernel (every split-form Conv call: one length-N/s inverse transform
+        per output channel, limb and column, (M/2) log2 M each; every FC
+        call: one length-N inverse transform per weight block, limb and
+        column)."""
         ntt, fin = 0, 0
         for c, g, f in zip(self.calls, self.geo, form):
-            if c["kind"] != "conv":
-                continue
             N, L, B = c["N"], c["L"], c["B"]
             ntt += g["npoly"] * L * (N // 2) * (N.bit_length() - 1)
-            if f == 1:
+            if c["kind"] != "conv":
+                fin += g["lay"]["P_fc"] * L * 2 * B * (N // 2) * (N.bit_length() - 1)
+            elif f == 1:
                 M = g["lay"]["M"]
                 fin += c["co"] * L * 2 * B * (M // 2) * (M.bit_length() - 1)
         return ntt, fin
@@ -510,6 +513,16 @@ def run_ours(args, rank, world, device):
     barrier()
     clk = clocks.stop()
     graph_ms = t0.elapsed_time(t1)
+    # the same K-step window repeated: its spread (the headline is the first)
+    windows = [graph_ms]
+    for _ in range(4):
+        with torch.cuda.stream(stream):
+            t0.record(stream)
+            for k in range(K):
+                arm.graphs[k % arm.R].replay()
+            t1.record(stream)
+        torch.cuda.synchronize()
+        windows.append(t0.elapsed_time(t1))
     # per-inference latency: the same replays, one at a time between events
     k_lat = min(K, 2000)
     g_ev = [_events(2) for _ in range(k_lat)]
@@ -546,7 +559,7 @@ def run_ours(args, rank, world, device):
                 "achieved": mac_gbs, "algorithmic_bytes": mac_bytes, "avg_launch_ms": mac_avg, "launches": k_phase}
     else:
         # every Conv call takes the fused form: the phase after the input
-        # transforms (k_plan_chan, with k_plan_fc on the side stream) is the
+        # transforms (k_plan_chan, with the FC items in k_plan_fin) is the
         # channel step; its bytes are the weights and transformed inputs read
         # once and the extracted outputs written once
         fb = arm.fused_bytes(info["form"])
@@ -591,8 +604,9 @@ def run_ours(args, rank, world, device):
                     "mac_phase": {"kernels": mac_name, "avg_launch_ms": mac_avg, "bytes": mac_bytes, "gbs": mac_gbs,
                                    "after_ntt_ms": float(np.mean(mac_ms)),
                                    "timing": f"{k_phase} launches back to back, replicas rotated, CUDA events"},
-                    "finish_and_fc": {"avg_launch_ms": fin_avg,
-                                      "what": "k_plan_fin on the stream, k_plan_fc on the side stream"},
+                    "after_mac": {"avg_launch_ms": fin_avg,
+                                  "what": "everything after the MAC kernel: k_plan_fin (Conv finishing items and "
+                                          "every FC item)"},
                     "step_bytes": ch_bytes,
                     "step_gbs_graph": ch_bytes / (graph_ms / K * 1e-3) / 1e9},
         "tensor_pipe": ({"kernel": "k_tc_mac", "flops": tc_fl, "avg_launch_ms": mac_avg,
@@ -607,6 +621,9 @@ def run_ours(args, rank, world, device):
         "e2e": e2e,
         "gpu_launches": info["kernels_per_run"] * K,
         "clocks": clk,
+        "windows": {"layers_per_s": [arm.units * K / (w * 1e-3) for w in windows],
+                    "median": float(np.median([arm.units * K / (w * 1e-3) for w in windows])),
+                    "how": f"the timed window of {K} graph replays run 5 times back to back; value is the first"},
     }
     arm.free()
     return res
@@ -1379,6 +1396,59 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
 
 
 # ----------------------------------------------------------------------------
+# the other configurations, summarised beside the headline
+
+EXTRAS = (("batched64", dict(steps=200, warmup=5)),
+          ("plain20_c100_wide4", dict(steps=20, warmup=3)),
+          ("serving", dict(serve_seconds=10.0)))
+
+
+def _summary(r):
+    """The figures of one configuration's line that the headline line carries."""
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "latency_ms", "speedup_vs_plain_form", "config",
+            "clocks", "gpu_launches", "windows")
+    out = {k: r[k] for k in keep if k in r}
+    if r.get("plain_form"):
+        pf = r["plain_form"]
+        out["plain_form"] = {k: pf[k] for k in ("value", "unit", "ms_per_step", "latency_ms", "network_latency_ms",
+                                                "inferences_per_s", "how") if k in pf}
+    if r.get("roofline"):
+        out["roofline"] = {k: r["roofline"][k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac",
+                                                         "algorithmic_bytes", "avg_launch_ms")}
+    if r.get("tensor_pipe"):
+        out["tensor_pipe"] = {k: r["tensor_pipe"][k] for k in ("achieved_tflops", "peak_tflops", "frac")}
+    if r.get("kernels"):
+        out["kernels"] = {k: {kk: v[kk] for kk in ("avg_launch_ms", "alu_frac", "gbs") if kk in v}
+                          for k, v in r["kernels"].items() if isinstance(v, dict)}
+    if r.get("e2e"):
+        out["e2e"] = {k: r["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
+    if r.get("serving"):
+        out["serving"] = r["serving"]
+    return out
+
+
+def run_extras(args, rank, world, device):
+    """Runs each configuration of EXTRAS after the headline, on the same GPU,
+    with its own steps (the headline's K and W are for plain-20), and returns
+    their summaries; a configuration that fails is reported, not fatal."""
+    import torch
+    out = {}
+    for name, kw in EXTRAS:
+        a = argparse.Namespace(**vars(args))
+        a.workload = name
+        for k, v in kw.items():
+            setattr(a, k, v)
+        t0 = time.perf_counter()
+        try:
+            r = run_serving(a, rank, world, device) if name == "serving" else run_ours(a, rank, world, device)
+            out[name] = _summary(r)
+        except Exception as e:  # reported beside the headline, which stands
+            out[name] = {"error": f"{type(e).__name__}: {e}"[:400]}
+        out[name]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return out
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -1390,6 +1460,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, wide and serving configurations after the plain-20 headline")
     args = ap.parse_args()
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     rank = int(os.environ.get("RANK", 0))
@@ -1412,6 +1484,8 @@ def main():
         return
     wl = workload(args.workload)
     res = (run_masked if wl.get("masked") else run_ours)(args, rank, world, local)
+    if args.workload == "plain20_c10" and world == 1 and not args.no_extras:
+        res["extras"] = run_extras(args, rank, world, local)
     if rank == 0:
         if not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(workload(args.workload))

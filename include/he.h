@@ -425,20 +425,20 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
  * bank, the words of he_conv_layer_masked / he_fc_layer_masked /
  * he_conv_client / he_fc_client.  he_plan_run issues, in order on `stream`:
  *   1. one kernel computing every coefficient-domain input NTT of every
- *      Conv call (for masked and client calls: of both input sources);
+ *      Conv and FC call (for masked and client calls: of both input
+ *      sources);
  *   2. for the Conv calls in the split form (B = 1, interleave s >= 4, G in
  *      {1, 2, 4}, or 2G in {2, 4, 8} for masked and client banks): a
  *      persistent kernel that streams each slot tile's
  *      weights for every output channel into shared memory with bulk copies
  *      and stores the folded channel sums (Sec. III-A, valid slots only) in
  *      the plan's workspace, then a kernel that runs the length-N/s inverse
- *      transforms and writes each extracted output polynomial;
+ *      transforms and writes each extracted output polynomial; the same
+ *      kernel runs every FC call's product with its weight blocks, inverse
+ *      transform, window and bias;
  *   3. for the other Conv calls: one fused kernel per column-tile class
  *      (MAC, folded inverse transform and extraction per output channel);
- *   4. every FC call's work (input transform, product, inverse transform,
- *      bias, output) in one kernel on a side stream that forks off `stream`
- *      at the start and joins it again before the run completes;
- *   5. for the calls with d_rescaled: one kernel rescaling all their
+ *   4. for the calls with d_rescaled: one kernel rescaling all their
  *      outputs (the RNS rescale of he_rescale).
  * Work items are ordered longest first.  The plan owns its workspace and
  * descriptor tables, so he_plan_run allocates nothing and can be captured
@@ -483,13 +483,20 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *   tc_min_batch     the fewest ciphertexts of a call on a tensor-core bank
  *                    that take the tensor-core MAC kernel: 1, 2, 4 or 8
  *                    (default 2); smaller calls read the bank's scalar-layout
- *                    copy like an ordinary bank. */
+ *                    copy like an ordinary bank.
+ *   fc_direct        1: an FC call with coefficient-domain inputs whose
+ *                    output window (Theorem 1's first rows_j coefficients)
+ *                    costs fewer products than two length-N transforms
+ *                    computes that window directly from the coefficient
+ *                    forms (default); 0: every FC call takes the transform
+ *                    path (input NTT, product, inverse NTT, window). */
 typedef struct {
     uint32_t split;
     uint32_t mac_item_kb;
     uint32_t mac_ctas_per_sm;
     uint32_t fused_max_nj;
     uint32_t tc_min_batch;
+    uint32_t fc_direct;
 } he_plan_tuning;
 
 /* The default tuning. */
@@ -538,13 +545,13 @@ he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream);
 
 /* What a plan launches; filled by he_plan_query. */
 typedef struct {
-    uint32_t kernels_per_run; /* kernels he_plan_run launches (both streams) */
+    uint32_t kernels_per_run; /* kernels he_plan_run launches */
     uint32_t ntt_items;       /* polynomials the input-NTT kernel transforms */
     uint32_t mac_items;       /* split-form MAC items (channels x limb x tile) */
     uint32_t mac_ctas;        /* persistent CTAs of the MAC kernel */
     uint32_t finish_items;    /* output polynomial x limb x column items */
     uint32_t fused_items;     /* non-split Conv channel items, all classes */
-    uint32_t fc_items;        /* FC items on the side stream */
+    uint32_t fc_items;        /* FC items (run by the finishing kernel) */
     uint32_t split_calls;     /* Conv calls in the split form */
     uint64_t workspace_bytes; /* device workspace the plan owns */
     he_plan_tuning tuning;    /* the tuning the plan was built with */
@@ -563,6 +570,18 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split);
  * the flag.  Blocking; call it after the streams the plan ran on are
  * synchronized. */
 he_status he_plan_check(he_plan_t plan);
+/* How many times the split-form MAC kernel of this plan polls a barrier
+ * (a bulk copy landing, or the compute warps releasing a buffer) before it
+ * gives up, sets the status that he_plan_check reports as HE_ERR_TIMEOUT and
+ * returns.  HE_WAIT_POLLS_DEFAULT (the value a plan starts with) is far
+ * above any wait of a healthy run; a small value (0: give up at the first
+ * wait) makes the failure path run on purpose, for tests.  Whatever the
+ * limit, the kernel still waits (with the default limit) for its own copies
+ * in flight before it exits.  Applies to later runs (and graph captures);
+ * the outputs of a run that gave up are unspecified.  (Library-side; the
+ * paper has no counterpart.) */
+#define HE_WAIT_POLLS_DEFAULT (1u << 20)
+he_status he_plan_set_wait_limit(he_plan_t plan, uint32_t polls);
 void he_plan_destroy(he_plan_t plan);
 
 /* ------------------------------------------------------------------------

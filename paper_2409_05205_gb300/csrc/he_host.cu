@@ -715,16 +715,17 @@ he_status he_pack_fc(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t 
     const size_t wbytes = (size_t)n_out * n_in;
     int8_t *d_W = nullptr;
     cudaError_t e = cudaMalloc(&f->bank, f->bank_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&f->bank_s, f->bank_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         const size_t nb = f->bank_bytes;
-        delete f;
-        return fail(HE_ERR_NOMEM, "FC bank of %zu bytes", nb);
+        he_filters_destroy(f);
+        return fail(HE_ERR_NOMEM, "FC bank of %zu bytes", 2 * nb);
     }
     if (bias) e = upload_fc_bias(p, bias, n_out, &f->bias);
     if (e == cudaSuccess) e = cudaMalloc(&d_W, wbytes);
     if (e == cudaSuccess) e = cudaMemcpy(d_W, W, wbytes, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = he_launch_pack_fc(p->ring, d_W, fl, f->bank, 0);
+    if (e == cudaSuccess) e = he_launch_pack_fc(p->ring, d_W, fl, f->bank, f->bank_s, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_W);
     if (e != cudaSuccess) {
@@ -858,11 +859,12 @@ static he_status pack_fc_masked(he_params_t p, uint32_t n_in, uint32_t n_out, in
     f->masked = (uint32_t)mode;
     f->bank_bytes = (size_t)fl.P_fc * 2u * p->L * p->N * sizeof(uint32_t);
     cudaError_t e = cudaMalloc(&f->bank, f->bank_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&f->bank_s, f->bank_bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         const size_t nb = f->bank_bytes;
-        delete f;
-        return fail(HE_ERR_NOMEM, "masked FC bank of %zu bytes", nb);
+        he_filters_destroy(f);
+        return fail(HE_ERR_NOMEM, "masked FC bank of %zu bytes", 2 * nb);
     }
     int8_t *d_W = nullptr;
     uint32_t *d_m0 = nullptr, *d_m1 = nullptr;
@@ -873,7 +875,7 @@ static he_status pack_fc_masked(he_params_t p, uint32_t n_in, uint32_t n_out, in
     if (e == cudaSuccess) e = cudaMemcpy(d_m0, m0, nm0 * sizeof(uint32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && m1) e = cudaMalloc(&d_m1, nm0 * sizeof(uint32_t));
     if (e == cudaSuccess && m1) e = cudaMemcpy(d_m1, m1, nm0 * sizeof(uint32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = he_launch_pack_fc_masked(p->ring, d_W, d_m0, d_m1, fl, mode, f->bank, 0);
+    if (e == cudaSuccess) e = he_launch_pack_fc_masked(p->ring, d_W, d_m0, d_m1, fl, mode, f->bank, f->bank_s, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_W);
     cudaFree(d_m0);
@@ -989,6 +991,7 @@ he_status he_plan_tuning_default(he_plan_tuning *t) {
     t->mac_ctas_per_sm = 2;
     t->fused_max_nj = 16;
     t->tc_min_batch = 2;
+    t->fc_direct = 1;
     return HE_OK;
 }
 
@@ -1002,6 +1005,7 @@ he_status check_tuning(const he_plan_tuning &t) {
         return fail(HE_ERR_ARG, "tuning: fused_max_nj must be 2, 4, 8 or 16");
     if (t.tc_min_batch != 1 && t.tc_min_batch != 2 && t.tc_min_batch != 4 && t.tc_min_batch != 8)
         return fail(HE_ERR_ARG, "tuning: tc_min_batch must be 1, 2, 4 or 8");
+    if (t.fc_direct > 1) return fail(HE_ERR_ARG, "tuning: fc_direct must be 0 or 1");
     return HE_OK;
 }
 }  // namespace
@@ -1274,9 +1278,18 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             g.P = f->fl.P_fc;
             g.rpp = f->fl.rows_per_poly;
             g.n_out = f->fl.n_out;
+            g.G = msrc ? 2u : 1u;  // masked and client calls stage two input polynomials per ciphertext
             cd.nj = 2;
-            if (msrc && 2u * padded_words(r.N) * 4u > 227u * 1024u)
-                return fail(HE_ERR_UNSUPPORTED, "call %u: N = %u too long for a masked FC item", i, r.N);
+            // the output window computed directly when the inputs are in the
+            // coefficient domain and its products cost less than two
+            // length-N transforms: rows * (N for each dense term, n_in' * rows
+            // for the sparse packed weights)
+            const bool coef_in = msrc == 2 || (msrc == 1 && c.in_domain == HE_COEFF) ||
+                                 (msrc == 0 && c.in_domain == HE_COEFF);
+            const size_t rows = std::min(g.rpp, g.n_out), sparse = (size_t)(r.N / g.rpp) * rows;
+            const size_t terms = msrc == 0 ? sparse : (msrc == 1 ? r.N + sparse : 2u * (size_t)r.N);
+            cd.fc_direct = tu.fc_direct && coef_in && f->bank_s && rows * terms <= 2u * (size_t)r.N * r.logN ? 1u : 0u;
+            cd.wc = f->bank_s;
             nin = msrc == 2 ? (size_t)c.B * r.N : (size_t)c.B * (msrc ? 1u : 2u) * r.L * r.N;
             nsh = (size_t)c.B * r.N;
             nshp = (size_t)c.B * f->fl.P_fc * r.N;
@@ -1284,9 +1297,9 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         }
         if (msrc) {
             // both input sources are staged by the input-transform kernel
-            // (Conv) or transformed inside the FC item
+            // into [B][2G][L][N] (G = 1 for FC), unless the FC window is direct
             cd.x_coeff = c.d_in;
-            if (cd.kind == HE_KIND_CONV) {
+            if (!cd.fc_direct) {
                 ws_off[i] = ws_words;
                 ws_words += (size_t)c.B * g.G * r.L * r.N;
             }
@@ -1294,7 +1307,7 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             if (msrc == 1) ranges.push_back({(uintptr_t)c.d_share_out, (uintptr_t)(c.d_share_out + nshp), false, i});
         } else if (c.in_domain == HE_COEFF) {
             cd.x_coeff = c.d_in;
-            if (cd.kind == HE_KIND_CONV) {  // FC items transform their input in shared memory
+            if (!cd.fc_direct) {
                 ws_off[i] = ws_words;
                 ws_words += nin;
             }
@@ -1349,6 +1362,7 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
     }
     for (uint32_t i = 0; i < ncalls; ++i) pl->split[i] = descs[i].split ? 1 : (descs[i].zt ? 2 : 0);
     pl->tuning = tu;
+    pl->wait_polls = HE_WAIT_POLLS_DEFAULT;
     pl->ws_bytes = ws_words * sizeof(uint32_t);
     if (ws_words) e = cudaMalloc(&pl->ws, ws_words * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMalloc(&pl->d_status, sizeof(uint32_t));
@@ -1360,27 +1374,43 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
     }
     // work items, each list ordered longest first
     using Costed = std::pair<double, ChanItem>;
-    std::vector<std::pair<double, NttItem>> ntt_cost, fc_cost;
+    std::vector<std::pair<double, NttItem>> ntt_cost;
     std::vector<uint32_t> tc_calls;
     std::vector<Costed> chan[kChanClasses], mac[kMacClasses], fin;
+    uint32_t n_fc = 0;
     for (uint32_t i = 0; i < ncalls; ++i) {
         CallDesc &cd = descs[i];
         ConvGeo &g = cd.g;
         const double N = g.N, logN = g.logN;
-        if (cd.kind == HE_KIND_FC) {
-            // fused FC items (input transform, product, inverse, output) run
-            // in the input-transform kernel, ahead of the conv transforms
-            const double cost = 3.0 * N * logN;
+        if (cd.fc_direct) {
+            // direct FC items run in the input-NTT kernel, ahead of its
+            // transforms (their loads are latency-bound): no transforms
+            const double cost = 4.0 * N * logN;
             for (uint32_t jp = 0; jp < g.P; ++jp)
                 for (uint32_t l = 0; l < g.L; ++l)
-                    for (uint32_t col = 0; col < g.ncols; ++col)
-                        fc_cost.push_back({cost, NttItem{i, (jp * g.L + l) * g.ncols + col}});
+                    for (uint32_t col = 0; col < g.ncols; ++col) {
+                        ntt_cost.push_back({cost, NttItem{i, (jp * g.L + l) * g.ncols + col}});
+                        ++n_fc;
+                    }
             continue;
         }
         if (cd.x_coeff) {
+            // the input-NTT kernel transforms (or stages) every input polynomial
             g.x = pl->ws + ws_off[i];
             const size_t npoly = (size_t)calls[i].B * g.G * (cd.msrc ? 1u : 2u) * g.L;
             for (size_t pidx_ = 0; pidx_ < npoly; ++pidx_) ntt_cost.push_back({N * logN, NttItem{i, (uint32_t)pidx_}});
+        }
+        if (cd.kind == HE_KIND_FC) {
+            // FC items (product, length-N inverse transform, window) run in
+            // the finishing kernel
+            const double cost = 3.0 * (N / 2.0) * logN + N;
+            for (uint32_t jp = 0; jp < g.P; ++jp)
+                for (uint32_t l = 0; l < g.L; ++l)
+                    for (uint32_t col = 0; col < g.ncols; ++col) {
+                        fin.push_back({cost, ChanItem{i, jp, l, col}});
+                        ++n_fc;
+                    }
+            continue;
         }
         if (cd.zt) {
             cd.z = pl->ws + z_off[i];
@@ -1414,17 +1444,13 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
     std::stable_sort(ntt_cost.begin(), ntt_cost.end(), by_cost);
     for (auto &it : ntt_cost) {
         ntt.push_back(it.second);
-        pl->smem_ntt = std::max(pl->smem_ntt, (size_t)padded_words(descs[it.second.call].g.N) * 4u);
+        const ConvGeo &g = descs[it.second.call].g;
+        const size_t sm = descs[it.second.call].fc_direct ? (size_t)std::min(g.rpp, g.n_out) * 4u
+                                                          : (size_t)padded_words(g.N) * 4u;
+        pl->smem_ntt = std::max(pl->smem_ntt, sm);
     }
     pl->n_ntt = (uint32_t)ntt.size();
-    std::vector<NttItem> fcs;
-    std::stable_sort(fc_cost.begin(), fc_cost.end(), by_cost);
-    for (auto &it : fc_cost) {
-        fcs.push_back(it.second);
-        const CallDesc &cd = descs[it.second.call];
-        pl->smem_fc = std::max(pl->smem_fc, (size_t)padded_words(cd.g.N) * 4u * (cd.msrc ? 2u : 1u));
-    }
-    pl->n_fc = (uint32_t)fcs.size();
+    pl->n_fc = n_fc;
     auto upload = [&](ChanItem **dst, const std::vector<ChanItem> &v) -> cudaError_t {
         if (v.empty()) return cudaSuccess;
         cudaError_t err = cudaMalloc(dst, sizeof(ChanItem) * v.size());
@@ -1436,13 +1462,6 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
     if (e == cudaSuccess && !ntt.empty()) {
         e = cudaMalloc(&pl->d_ntt, sizeof(NttItem) * ntt.size());
         if (e == cudaSuccess) e = cudaMemcpy(pl->d_ntt, ntt.data(), sizeof(NttItem) * ntt.size(), cudaMemcpyHostToDevice);
-    }
-    if (e == cudaSuccess && !fcs.empty()) {
-        e = cudaMalloc(&pl->d_fc, sizeof(NttItem) * fcs.size());
-        if (e == cudaSuccess) e = cudaMemcpy(pl->d_fc, fcs.data(), sizeof(NttItem) * fcs.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->side, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming);
     }
     for (int cls = 0; cls < kChanClasses && e == cudaSuccess; ++cls) {
         std::stable_sort(chan[cls].begin(), chan[cls].end(), by_cost);
@@ -1561,7 +1580,9 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         for (auto &it : fin) {
             items.push_back(it.second);
             const CallDesc &cd = descs[it.second.call];
-            pl->smem_fin = std::max(pl->smem_fin, (size_t)std::min(cd.g.s, cd.g.co) * fin_stride(cd.g.M, cd.g.s) * 4u);
+            const size_t sm = cd.kind == HE_KIND_FC ? (size_t)padded_words(cd.g.N) * 4u
+                                                    : (size_t)std::min(cd.g.s, cd.g.co) * fin_stride(cd.g.M, cd.g.s) * 4u;
+            pl->smem_fin = std::max(pl->smem_fin, sm);
         }
         pl->n_fin = (uint32_t)items.size();
         e = upload(&pl->d_fin, items);
@@ -1575,6 +1596,12 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
     return HE_OK;
 }
 }  // namespace
+
+he_status he_plan_set_wait_limit(he_plan_t plan, uint32_t polls) {
+    if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
+    plan->wait_polls = polls;
+    return HE_OK;
+}
 
 he_status he_plan_check(he_plan_t plan) {
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
@@ -1618,8 +1645,8 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
     r.finish_items = plan->n_fin;
     for (int c = 0; c < kChanClasses; ++c) r.fused_items += plan->n_chan[c];
     r.fc_items = plan->n_fc;
-    r.kernels_per_run = (plan->n_ntt > 0) + (plan->n_mac > 0) + (plan->n_fin > 0) + (plan->n_fc > 0) +
-                        (plan->n_tc > 0) + (plan->n_rs > 0);
+    r.kernels_per_run = (plan->n_ntt > 0) + (plan->n_mac > 0) + (plan->n_fin > 0) + (plan->n_tc > 0) +
+                        (plan->n_rs > 0);
     r.rescale_items = plan->n_rs;
     r.tc_items = plan->n_tc;
     r.tc_ctas = plan->n_tc ? plan->tc_ctas : 0;
@@ -1652,10 +1679,6 @@ void he_plan_destroy(he_plan_t plan) {
     cudaFree(plan->d_status);
     cudaFree(plan->d_rs_calls);
     cudaFree(plan->d_rs_items);
-    cudaFree(plan->d_fc);
-    if (plan->side) cudaStreamDestroy(plan->side);
-    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
-    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
     delete[] plan->split;
     delete plan;
 }

@@ -192,6 +192,9 @@ struct CallDesc {
     uint32_t zt;              // z is channel-fastest, [L][2B][M][co] (tensor-core MAC kernel)
     uint32_t msrc;            // 0: ciphertext x plaintext; 1: masked server step; 2: client step (Alg. 1 / 2)
     uint32_t a_ntt;           // masked server calls: c0 is already in the NTT domain
+    uint32_t fc_direct;       // FC: the output window computed directly from the coefficient-domain
+                              // inputs and weights (fc_direct_body), no transforms
+    const uint32_t *wc;       // FC: the bank's polynomials in the coefficient domain
     LimbK limb[HE_MAX_LIMBS];
 };
 
@@ -265,8 +268,8 @@ __host__ __device__ __forceinline__ uint32_t fin_stride(uint32_t M, uint32_t s) 
 }
 
 struct NttItem {
-    uint32_t call, poly;      // conv: poly index within the call's [npoly][L][N] input;
-};                            // fc: poly = (jp * L + l) * ncols + column of a fused FC item
+    uint32_t call, poly;      // poly index within the call's [npoly][L][N] input (Conv and FC)
+};
 
 struct ChanItem {
     uint32_t call, a, l, b;   // conv: (channel n, limb, column tile); fc: (weight poly, limb, column)
@@ -311,11 +314,7 @@ struct he_plan_s {
     MacDesc *d_mac_desc;                // per item, same order as d_mac
     uint32_t mac_ctas;
     uint32_t mac_xw, mac_nst;           // MAC kernel: words per input buffer, stages of the weight ring
-    uint32_t n_fc;                      // fused FC items, run on a side stream
-    NttItem *d_fc;
-    size_t smem_fc;
-    cudaStream_t side;                  // FC work forks off the caller's stream and joins it again
-    cudaEvent_t ev_fork, ev_join;
+    uint32_t n_fc;                      // FC items (among the finishing kernel's items)
     size_t smem_ntt, smem_chan[kChanClasses], smem_mac, smem_fin;
     uint32_t *ws;
     size_t ws_bytes;
@@ -327,6 +326,7 @@ struct he_plan_s {
     RescaleCall *d_rs_calls;
     RsItem *d_rs_items;
     uint32_t *d_status;                 // bit 0 / bit 1: a bounded wait in the MAC / tensor-core MAC kernel gave up
+    uint32_t wait_polls;                // polls of the split MAC kernel's waits before it gives up (he_plan_set_wait_limit)
     uint8_t *split;                     // host: per call, 1 if it takes the split form
     he_plan_tuning tuning;
 };
@@ -352,7 +352,8 @@ struct he_filters_s {
     he_fc_layout fl;
     uint32_t *bank;   // conv: [co][L][G][N]; fc: [P][L][N]; NTT domain, pre-scaled
     uint32_t *bank_s; // tensor-core banks: the same weights in the scalar layout (logTS, lcs) for single
-                      // calls and small batches; else nullptr
+                      // calls and small batches; FC banks: the same polynomials in the coefficient domain
+                      // (the direct output window of plan calls); else nullptr
     uint32_t *bias;   // fc: [L][n_out] Delta_Q * B mod q_l, or nullptr
     size_t bank_bytes;
 };
@@ -368,7 +369,7 @@ cudaError_t he_launch_pack_conv(const RingView &r, const int8_t *d_w, const he_c
                                 const he_conv_layout &lay, uint32_t lt, uint32_t lcs, uint32_t tc, uint32_t *bank,
                                 cudaStream_t st);
 cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_layout &fl,
-                              uint32_t *bank, cudaStream_t st);
+                              uint32_t *bank, uint32_t *coef, cudaStream_t st);
 uint32_t he_conv_nj(uint32_t ncols, uint32_t M, uint32_t s);
 uint32_t he_conv_cpt(uint32_t nj, uint32_t nb, uint32_t G);
 uint32_t he_ilog2(uint32_t x);
@@ -391,7 +392,8 @@ cudaError_t he_launch_fc(const RingView &r, const he_fc_layout &fl, const uint32
                          const uint32_t *bias, const uint32_t *x_ntt, uint32_t *out, int mode,
                          uint32_t B, cudaStream_t st);
 cudaError_t he_launch_pack_fc_masked(const RingView &r, const int8_t *d_W, const uint32_t *d_m0, const uint32_t *d_m1,
-                                     const he_fc_layout &fl, int mode, uint32_t *bank, cudaStream_t st);
+                                     const he_fc_layout &fl, int mode, uint32_t *bank, uint32_t *coef,
+                                     cudaStream_t st);
 cudaError_t he_launch_fc_masked(const RingView &r, const he_fc_layout &fl, const uint32_t *bank, const uint32_t *bias,
                                 const uint32_t *x_ntt, const uint32_t *shp, uint32_t *out, uint32_t B,
                                 cudaStream_t st);

@@ -22,8 +22,9 @@
 //                 every fused channel work unit of all calls in one launch.
 //  k_plan_mac /   a plan's split form: a persistent bulk-copy-fed channel MAC
 //  k_plan_fin     (two columns, or one for the masked and client steps), then
-//                 the valid-slot inverse transforms and the extraction.
-//  k_plan_fc      a plan's FC items (ordinary and masked) on a side stream.
+//                 the valid-slot inverse transforms and the extraction; the
+//                 finishing kernel also runs every FC item of the plan (its
+//                 inputs transformed by k_plan_ntt).
 //  k_ntt_masked_in, k_client_in, k_fc_masked, k_pack_fc_masked
 //                 the masked server and client steps of Alg. 1 / Alg. 2.
 //  k_rescale /    the RNS rescale by the last prime, for one buffer or for
@@ -423,36 +424,6 @@ __device__ __forceinline__ void fc_body(const ConvGeo &a, const LimbK &K, uint32
     }
 }
 
-// A whole FC item in one CTA: column c's input transform (skipped for
-// NTT-domain input), the product with weight polynomial jp, the inverse
-// transform and the output window -- the words fc_body writes.
-__device__ __forceinline__ void fc_fused_body(const ConvGeo &a, const uint32_t *x_coeff, const uint2 *tw_fwd,
-                                              const LimbK &K, uint32_t jp, uint32_t l, uint32_t c, uint4 *smem4) {
-    uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
-    const uint32_t N = a.N, L = a.L;
-    const size_t off = ((size_t)c * L + l) * N;
-    if (x_coeff) {
-        ntt_fwd_c(x_coeff + off, nullptr, Y, a.logN, tw_fwd + (size_t)l * N, K.q);
-    } else {
-        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) Y[pidx(k)] = __ldg(a.x + off + k);
-        __syncthreads();
-    }
-    const uint32_t *W = a.bank + (size_t)(jp * L + l) * N;
-    mul_by_row(Y, W, N, K, true);
-    intt_c(Y, 1, padded_words(N), a.logN, a.tw_inv + (size_t)l * N, K.q);
-    const uint32_t rows = min(a.rpp, a.n_out - jp * a.rpp);
-    uint32_t *o = a.out + ((size_t)(((c >> 1) * a.P + jp) * 2 + (c & 1)) * L + l) * N;
-    const bool c0 = (c & 1) == 0;
-    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
-        uint32_t v = k < rows ? red_2q(Y[pidx(k)], K.q) : 0u;
-        if (k < rows && c0 && a.bias) {
-            v += __ldg(a.bias + (size_t)l * a.n_out + jp * a.rpp + k);
-            v = min(v, v - K.q);
-        }
-        o[k] = v;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // single-call kernels
 // ---------------------------------------------------------------------------
@@ -654,6 +625,7 @@ struct PackFcArgs {
     RingView r;
     const int8_t *W;   // [n_out][n_in]
     uint32_t *bank;    // [P][L][N]
+    uint32_t *coef;    // [P][L][N] the same polynomials in the coefficient domain, or nullptr
     uint32_t n_in, n_in_p, n_out, rpp;
 };
 
@@ -686,10 +658,15 @@ __device__ __forceinline__ void fc_weight_poly(uint32_t *A, const int8_t *__rest
 }
 
 // NTT of the polynomial in A, times N^-1 (the inverse transform of the
-// layer then needs no scaling), to dst.
-__device__ __forceinline__ void fc_bank_store(uint32_t *A, uint32_t *dst, uint32_t logN, const uint2 *tw,
-                                              const LimbK &K) {
+// layer then needs no scaling), to dst; the polynomial itself (residues in
+// [0, q)) to coef when it is given.
+__device__ __forceinline__ void fc_bank_store(uint32_t *A, uint32_t *dst, uint32_t *coef, uint32_t logN,
+                                              const uint2 *tw, const LimbK &K) {
     const uint32_t N = 1u << logN;
+    if (coef) {
+        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) coef[k] = A[k];
+        __syncthreads();
+    }
     ntt_fwd_smem(A, logN, tw, K.q);
     for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
         const uint32_t x = red_4q(A[k], K.q2, K.q);
@@ -704,7 +681,8 @@ __global__ void __launch_bounds__(kThreads) k_pack_fc(const PackFcArgs a) {
     const uint32_t N = a.r.N;
     const LimbK K = a.r.limb[l];
     fc_weight_poly(A, a.W, jp, N, a.n_in, a.n_in_p, a.n_out, a.rpp, 1u, K);
-    fc_bank_store(A, a.bank + (size_t)(jp * a.r.L + l) * N, a.r.logN, a.r.tw_fwd + (size_t)l * N, K);
+    const size_t off = (size_t)(jp * a.r.L + l) * N;
+    fc_bank_store(A, a.bank + off, a.coef ? a.coef + off : nullptr, a.r.logN, a.r.tw_fwd + (size_t)l * N, K);
 }
 
 // Bank of the masked FC step (Alg. 2), [P][2][L][N], every polynomial as
@@ -716,6 +694,7 @@ struct PackFcMaskedArgs {
     const uint32_t *m0;   // mode 1: rho [P][N] (integers below t); mode 2: p1 [P][L][N] residues
     const uint32_t *m1;   // mode 2: p2 [P][L][N] residues
     uint32_t *bank;
+    uint32_t *coef;       // the same polynomials in the coefficient domain, or nullptr
     uint32_t n_in, n_in_p, n_out, rpp, mode;
 };
 
@@ -732,7 +711,8 @@ __global__ void __launch_bounds__(kThreads) k_pack_fc_masked(const PackFcMaskedA
         for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) A[i] = __ldg(src + i);
         __syncthreads();
     }
-    fc_bank_store(A, a.bank + (size_t)((jp * 2u + u) * L + l) * N, a.r.logN, a.r.tw_fwd + (size_t)l * N, K);
+    const size_t off = (size_t)((jp * 2u + u) * L + l) * N;
+    fc_bank_store(A, a.bank + off, a.coef ? a.coef + off : nullptr, a.r.logN, a.r.tw_fwd + (size_t)l * N, K);
 }
 
 // The inverse transform and output window of the masked FC step (Alg. 2)
@@ -762,14 +742,12 @@ __device__ __forceinline__ void fc_masked_out(const ConvGeo &a, const LimbK &K, 
     }
 }
 
-// Single-call masked FC step: the two NTT-domain inputs of column b come
-// from the workspace [B][2][L][N].
-__global__ void __launch_bounds__(kThreads) k_fc_masked(const ConvGeo a, const RingView r) {
-    extern __shared__ uint4 smem4[];
+// Masked / client FC step of block jp, limb l, ciphertext b: the two
+// NTT-domain inputs of ciphertext b come from a.x = [B][2][L][N].
+__device__ __forceinline__ void fc_masked_body(const ConvGeo &a, const LimbK &K, uint32_t jp, uint32_t l, uint32_t b,
+                                               uint4 *smem4) {
     uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
-    const uint32_t jp = blockIdx.x, l = blockIdx.y, b = blockIdx.z;
     const uint32_t N = a.N, L = a.L;
-    const LimbK K = r.limb[l];
     const uint4 *X0 = reinterpret_cast<const uint4 *>(a.x + (size_t)((b * 2u) * L + l) * N);
     const uint4 *X1 = reinterpret_cast<const uint4 *>(a.x + (size_t)((b * 2u + 1u) * L + l) * N);
     const uint4 *W0 = reinterpret_cast<const uint4 *>(a.bank + (size_t)((jp * 2u) * L + l) * N);
@@ -785,40 +763,10 @@ __global__ void __launch_bounds__(kThreads) k_fc_masked(const ConvGeo a, const R
     fc_masked_out(a, K, jp, l, b, Y);
 }
 
-// A masked FC item of a plan in one CTA: both inputs of ciphertext b
-// transformed in shared memory (server: c0 and sh; client: -v and i + sh),
-// the product with block jp's pair, then fc_masked_out.
-__device__ __forceinline__ void fc_masked_fused_body(const CallDesc &cd, const LimbK &K, uint32_t jp, uint32_t l,
-                                                     uint32_t b, uint4 *smem4) {
-    const ConvGeo &a = cd.g;
-    const uint32_t N = a.N, L = a.L;
-    uint32_t *Y0 = reinterpret_cast<uint32_t *>(smem4), *Y1 = Y0 + padded_words(N);
-    const uint2 *tw = cd.tw_fwd + (size_t)l * N;
-    if (cd.msrc == 1u) {
-        const uint32_t *c0 = cd.x_coeff + ((size_t)b * L + l) * N;
-        if (cd.a_ntt) {
-            for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) Y0[pidx(k)] = __ldg(c0 + k);
-            __syncthreads();
-        } else {
-            ntt_fwd_c(c0, nullptr, Y0, a.logN, tw, K.q);
-        }
-        ntt_fwd_c(cd.src_b + (size_t)b * N, nullptr, Y1, a.logN, tw, K.q);
-    } else {
-        const int32_t *v = reinterpret_cast<const int32_t *>(cd.x_coeff) + (size_t)b * N;
-        const int32_t *ish = reinterpret_cast<const int32_t *>(cd.src_b) + (size_t)b * N;
-        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
-            Y0[pidx(k)] = small_residue(__ldg(v + k), true, K.q);
-            Y1[pidx(k)] = small_residue(__ldg(ish + k), false, K.q);
-        }
-        __syncthreads();
-        ntt_fwd_c(nullptr, nullptr, Y0, a.logN, tw, K.q);
-        ntt_fwd_c(nullptr, nullptr, Y1, a.logN, tw, K.q);
-    }
-    const uint32_t *W0 = a.bank + (size_t)((jp * 2u) * L + l) * N, *W1 = a.bank + (size_t)((jp * 2u + 1u) * L + l) * N;
-    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x)
-        Y0[pidx(k)] = reduce64((uint64_t)Y0[pidx(k)] * __ldg(W0 + k) + (uint64_t)Y1[pidx(k)] * __ldg(W1 + k), K);
-    __syncthreads();
-    fc_masked_out(a, K, jp, l, b, Y0);
+// Single-call masked FC step (grid: blocks x limbs x ciphertexts).
+__global__ void __launch_bounds__(kThreads) k_fc_masked(const ConvGeo a, const RingView r) {
+    extern __shared__ uint4 smem4[];
+    fc_masked_body(a, r.limb[blockIdx.y], blockIdx.x, blockIdx.y, blockIdx.z, smem4);
 }
 
 // resident CTAs per SM the register budget is set for, by column tile width
@@ -922,6 +870,118 @@ __device__ __forceinline__ void ntt_fwd_8192_warp(const uint32_t *__restrict__ s
                            red_4q(v[4 * k + 3], q2, q));
 }
 
+// ---------------------------------------------------------------------------
+// FC output window computed directly (Sec. III-B: only the first n_o
+// coefficients of the product are needed).  Coefficient k of a negacyclic
+// product x * w is sum_{b <= k} x_{k-b} w_b - sum_{b > k} x_{k-b+N} w_b.  For
+// the window k < rows_j that is rows_j dot products over the support of w:
+// the packed weights w_j(X) (eq. (w(x) formula)) are nonzero only at
+// exponents b with b mod rows_per_poly < rows_j, so an ordinary FC layer
+// with few outputs costs n_in' * rows_j^2 products instead of a forward and
+// an inverse length-N transform.  The masked server step adds the dense
+// product c0 * rho_j, the client step two dense products (-v p1_j and
+// (i + sh) p2_j).  Exact: every sum is reduced mod q_l; the words equal
+// those of the transform path.
+// ---------------------------------------------------------------------------
+
+// One term of coefficient k: sum over b of sgn(k, b) x_{(k-b) mod N} w_b by
+// the 32 lanes of a warp (b over the support: all N exponents, or only
+// b mod rpp < rows), every lane returning the sum in [0, q).  X holds
+// residues (or, for the client step, small signed integers, negated when
+// xneg) read through L1; W residues.  Each lane loads 8 terms at a time
+// (16 loads in flight) and sums their products (< 2^60 each) in two 64-bit
+// accumulators, one per sign, reduced after every 8.
+template <bool SMALL>
+__device__ __forceinline__ uint32_t window_term(const uint32_t *__restrict__ X, bool xneg,
+                                                const uint32_t *__restrict__ W, uint32_t k, uint32_t N,
+                                                uint32_t rpp, uint32_t rows, bool sparse, const LimbK &K) {
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t cnt = sparse ? (N / rpp) * rows : N;
+    uint32_t sp = 0, sn = 0;
+    for (uint32_t i0 = 0; i0 < cnt; i0 += 256u) {
+        uint32_t x[8], w[8], bb[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint32_t idx = i0 + 32u * u + lane;
+            const uint32_t b = sparse ? (idx / rows) * rpp + idx % rows : idx;
+            bb[u] = idx < cnt ? b : 0xFFFFFFFFu;
+            const uint32_t xi = b <= k ? k - b : k + N - b;
+            x[u] = idx < cnt ? __ldg(X + xi) : 0u;
+            w[u] = idx < cnt ? __ldg(W + b) : 0u;
+        }
+        uint64_t pos = 0, neg = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            uint32_t xv = x[u];
+            if (SMALL) xv = small_residue((int32_t)xv, xneg, K.q);
+            const uint64_t prod = (uint64_t)xv * w[u];
+            if (bb[u] <= k)
+                pos += prod;
+            else
+                neg += prod;
+        }
+        sp = red_2q(sp + reduce64(pos, K), K.q);
+        sn = red_2q(sn + reduce64(neg, K), K.q);
+    }
+    uint32_t v = red_2q(sp + K.q - sn, K.q);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v = red_2q(v + __shfl_xor_sync(0xffffffffu, v, o), K.q);
+    return v;
+}
+
+// One direct FC item of a plan: weight block jp, limb l, column col (plain
+// calls: ciphertext col / 2, polynomial col % 2; masked and client calls:
+// ciphertext col), coefficient-domain inputs; writes the whole output
+// polynomial (the window, zeros beyond it, bias and Delta_Q sh' as the
+// transform path does).  `sm` holds rows_j words.
+__device__ __forceinline__ void fc_direct_body(const CallDesc &cd, const LimbK &K, uint32_t jp, uint32_t l,
+                                               uint32_t col, uint32_t *sm) {
+    const ConvGeo &a = cd.g;
+    const uint32_t N = a.N, L = a.L, P = a.P, rpp = a.rpp;
+    const uint32_t rows = min(rpp, a.n_out - jp * rpp);
+    const uint32_t warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (uint32_t k = warp; k < rows; k += nwarps) {
+        uint32_t v;
+        if (cd.msrc == 0u) {
+            const uint32_t *X = cd.x_coeff + ((size_t)col * L + l) * N;
+            v = window_term<false>(X, false, cd.wc + ((size_t)jp * L + l) * N, k, N, rpp, rows, true, K);
+        } else if (cd.msrc == 1u) {  // c0 rho_j - Delta_Q sh w_j
+            const uint32_t *c0 = cd.x_coeff + ((size_t)col * L + l) * N, *sh = cd.src_b + (size_t)col * N;
+            v = window_term<false>(c0, false, cd.wc + ((size_t)(jp * 2u) * L + l) * N, k, N, rpp, rows, false, K);
+            v += window_term<false>(sh, false, cd.wc + ((size_t)(jp * 2u + 1u) * L + l) * N, k, N, rpp, rows,
+                                    true, K);
+            v = red_2q(v, K.q);
+        } else {  // -v p1_j + (i + sh) p2_j
+            const uint32_t *vv = cd.x_coeff + (size_t)col * N, *ish = cd.src_b + (size_t)col * N;
+            v = window_term<true>(vv, true, cd.wc + ((size_t)(jp * 2u) * L + l) * N, k, N, rpp, rows, false, K);
+            v += window_term<true>(ish, false, cd.wc + ((size_t)(jp * 2u + 1u) * L + l) * N, k, N, rpp, rows,
+                                   false, K);
+            v = red_2q(v, K.q);
+        }
+        if ((threadIdx.x & 31u) == 0u) sm[k] = v;
+    }
+    __syncthreads();
+    uint32_t *o;
+    const uint32_t *bias = nullptr, *shp = nullptr;
+    if (cd.msrc == 0u) {
+        o = a.out + ((size_t)(((col >> 1) * P + jp) * 2u + (col & 1u)) * L + l) * N;
+        if ((col & 1u) == 0u) bias = a.bias;
+    } else {
+        o = a.out + ((size_t)(col * P + jp) * L + l) * N;
+        bias = a.bias;
+        shp = a.shp ? a.shp + (size_t)(col * P + jp) * N : nullptr;
+    }
+    for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+        uint32_t v = 0;
+        if (k < rows) {
+            v = sm[k];
+            if (bias) v = red_2q(v + __ldg(bias + (size_t)l * a.n_out + jp * rpp + k), K.q);
+        }
+        if (shp) v = red_2q(v + mulmod(__ldg(shp + k), K.delta, K), K.q);
+        o[k] = v;
+    }
+}
+
 // The forward transform of one plan input polynomial: the three-phase
 // kernel above for N = 8192 with 512 threads, else the pass-by-pass one.
 __device__ __forceinline__ void plan_fwd_ntt(const uint32_t *src, uint32_t *dst, uint32_t logN, const uint2 *tw,
@@ -944,6 +1004,11 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
     const NttItem it = items[blockIdx.x];
     const CallDesc &cd = calls[it.call];
     const uint32_t N = cd.g.N, L = cd.g.L;
+    if (cd.fc_direct) {  // item poly = (jp * L + l) * ncols + column
+        const uint32_t col = it.poly % cd.g.ncols, l = (it.poly / cd.g.ncols) % L, jp = it.poly / (cd.g.ncols * L);
+        fc_direct_body(cd, cd.limb[l], jp, l, col, reinterpret_cast<uint32_t *>(smem4));
+        return;
+    }
     const uint32_t l = it.poly % L;
     const LimbK K = cd.limb[l];
     uint32_t *dst = const_cast<uint32_t *>(cd.g.x) + (size_t)it.poly * N;
@@ -969,22 +1034,6 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
         return;
     }
     plan_fwd_ntt(cd.x_coeff + (size_t)it.poly * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, smem4);
-}
-
-// Fused FC items of a plan: item.poly = (jp * L + l) * ncols + column.
-__global__ void __launch_bounds__(kThreads) k_plan_fc(const CallDesc *__restrict__ calls,
-                                                     const NttItem *__restrict__ items) {
-    extern __shared__ uint4 smem4[];
-    const NttItem it = items[blockIdx.x];
-    const CallDesc &cd = calls[it.call];
-    const uint32_t L = cd.g.L, col = it.poly % cd.g.ncols, l = (it.poly / cd.g.ncols) % L,
-                   jp = it.poly / (cd.g.ncols * L);
-    if (cd.msrc) {
-        fc_masked_fused_body(cd, cd.limb[l], jp, l, col, smem4);
-        return;
-    }
-    const ConvGeo g = cd.g;
-    fc_fused_body(g, cd.x_coeff, cd.tw_fwd, cd.limb[l], jp, l, col, smem4);
 }
 
 template <int NJ>
@@ -1016,7 +1065,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<NJ>::value) k_plan_chan(co
 // split form of the channel step (plans): a MAC kernel per slot tile, then a
 // finishing kernel per output polynomial
 // ---------------------------------------------------------------------------
-constexpr uint32_t kSpinLimit = 1u << 20;  // bounded mbarrier waits
+constexpr uint32_t kSpinLimit = HE_WAIT_POLLS_DEFAULT;  // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -1039,10 +1088,10 @@ __device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// Waits for phase `parity` of `bar`; gives up after kSpinLimit polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Waits for phase `parity` of `bar`; gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kSpinLimit) {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
@@ -1085,7 +1134,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 template <int G, int CS>
 __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, uint64_t *xempty,
                                          const uint32_t *ring, uint64_t *full, uint64_t *empty, uint32_t &buf,
-                                         uint32_t &ph, uint32_t nstages) {
+                                         uint32_t &ph, uint32_t nstages, uint32_t spin) {
     constexpr uint32_t LT = split_tile_log(CS == 4 ? 2 : (CS == 2 ? 1 : 0));
     constexpr uint32_t ROWS = kMacStageWords >> LT;  // weight rows of TS words per stage
     constexpr uint32_t NCH = ROWS / G;               // channels per full stage
@@ -1113,7 +1162,7 @@ __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, ui
     const bool lead = (lane & (lanes - 1u)) == 0 && jj < d.ncol;
     uint32_t n = 0;
     for (uint32_t st = 0; st < nst; ++st, n += NCH) {
-        if (!mbar_wait(full + buf, ph)) return false;
+        if (!mbar_wait(full + buf, ph, spin)) return false;
         // the bank interleaves chunks: this thread's u-th chunk is uint4 u*128 + c
         const uint32_t *W = ring + buf * kMacStageWords + 4u * c;
 #pragma unroll
@@ -1170,7 +1219,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
                                                               const MacDesc *__restrict__ descs,
                                                               const uint32_t *__restrict__ offs,
                                                               uint32_t *__restrict__ status, uint32_t xw,
-                                                              uint32_t nring) {
+                                                              uint32_t nring, uint32_t spin) {
     extern __shared__ uint4 smem4[];
     uint64_t *xfull = reinterpret_cast<uint64_t *>(smem4);  // [2]
     uint64_t *xempty = xfull + 2;                            // [2]
@@ -1220,7 +1269,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
             for (uint32_t st = (k == ib ? st0 : 0u); st < nst; ++st, ++issued) {
                 const uint32_t b = issued % nring;
                 if (issued >= nring) {
-                    if (!mbar_wait(empty + b, ((issued / nring) - 1u) & 1u)) {
+                    if (!mbar_wait(empty + b, ((issued / nring) - 1u) & 1u, spin)) {
                         ok = false;
                         break;
                     }
@@ -1233,7 +1282,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
             // inputs of item k + 2 once the compute warps hold item k's in registers
             if (ok && k + 2 < ie) {
                 const uint32_t xb = xiss & 1u;
-                if (!mbar_wait(xempty + xb, ((xiss >> 1) - 1u) & 1u)) {
+                if (!mbar_wait(xempty + xb, ((xiss >> 1) - 1u) & 1u, spin)) {
                     ok = false;
                     break;
                 }
@@ -1246,7 +1295,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
         if (!ok) atomicOr(status, 1u);
         // every copy lands before the CTA's shared memory is released; only
         // the last two input loads and the last kMacStages stages can still
-        // be in flight (an older phase of a barrier must not be waited for)
+        // be in flight (an older phase of a barrier must not be waited for).
+        // These waits keep the full limit whatever `spin` is.
         for (uint32_t i = xiss > 2 ? xiss - 2 : 0; i < xiss; ++i) mbar_wait(xfull + (i & 1u), (i >> 1) & 1u);
         for (uint32_t i = issued > nring ? issued - nring : 0; i < issued; ++i)
             mbar_wait(full + i % nring, (i / nring) & 1u);
@@ -1258,20 +1308,20 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
     bool ok = true;
     for (uint32_t k = ib; ok && k < ie; ++k) {
         const uint32_t xb = (k - ib) & 1u;
-        if (!mbar_wait(xfull + xb, ((k - ib) >> 1) & 1u)) {
+        if (!mbar_wait(xfull + xb, ((k - ib) >> 1) & 1u, spin)) {
             ok = false;
             break;
         }
         const MacDesc d = dslot[xb];
         const uint32_t *X = Xb + xb * xw;
         switch (d.cls) {
-            case 0: ok = mac_item<1, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
-            case 1: ok = mac_item<1, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
-            case 2: ok = mac_item<1, 4>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
-            case 3: ok = mac_item<2, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
-            case 4: ok = mac_item<2, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
-            case 5: ok = mac_item<4, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
-            default: ok = mac_item<8, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring); break;
+            case 0: ok = mac_item<1, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
+            case 1: ok = mac_item<1, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
+            case 2: ok = mac_item<1, 4>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
+            case 3: ok = mac_item<2, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
+            case 4: ok = mac_item<2, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
+            case 5: ok = mac_item<4, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
+            default: ok = mac_item<8, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
         }
     }
     if (!ok) atomicOr(status, 1u);
@@ -1281,7 +1331,11 @@ __device__ __forceinline__ uint32_t he_log2_dev(uint32_t x) { return 31u - __clz
 
 // Finishing kernel: items (call, h, l, column) run the length-M inverse
 // transforms of the s channels of output polynomial h and write the whole
-// extracted polynomial (coalesced; classes no channel uses are 0).
+// extracted polynomial (coalesced; classes no channel uses are 0).  FC
+// items (call, weight block j, l, column) take their input transformed by
+// the input-NTT kernel, multiply it by block j's weights, run the length-N
+// inverse transform and write Theorem 1's window (Alg. 2; masked and client
+// calls: the two-term product, the window, the bias and Delta_Q sh').
 constexpr int kFinThreads = 256;
 
 __global__ void __launch_bounds__(kFinThreads, 3) k_plan_fin(const CallDesc *__restrict__ calls,
@@ -1290,6 +1344,13 @@ __global__ void __launch_bounds__(kFinThreads, 3) k_plan_fin(const CallDesc *__r
     const ChanItem it = items[blockIdx.x];
     const CallDesc &cd = calls[it.call];
     const LimbK K = cd.limb[it.l];
+    if (cd.kind == HE_KIND_FC) {
+        if (cd.msrc)
+            fc_masked_body(cd.g, K, it.a, it.l, it.b, smem4);
+        else
+            fc_body(cd.g, K, it.a, it.l, it.b, smem4);
+        return;
+    }
     uint32_t *Zs = reinterpret_cast<uint32_t *>(smem4);
     const uint32_t h = it.a, l = it.l, c = it.b;
     const uint32_t N = cd.g.N, co = cd.g.co, s = cd.g.s, logs = cd.g.logs, M = cd.g.M, logM = cd.g.logM,
@@ -1601,11 +1662,12 @@ cudaError_t he_launch_rescale(const RingView &r, const uint32_t *in, uint32_t *o
 }
 
 cudaError_t he_launch_pack_fc(const RingView &r, const int8_t *d_W, const he_fc_layout &fl, uint32_t *bank,
-                              cudaStream_t st) {
+                              uint32_t *coef, cudaStream_t st) {
     PackFcArgs a;
     a.r = r;
     a.W = d_W;
     a.bank = bank;
+    a.coef = coef;
     a.n_in = fl.n_in;
     a.n_in_p = fl.n_in_p;
     a.n_out = fl.n_out;
@@ -1628,13 +1690,15 @@ static ConvGeo geo_of(const RingView &r) {
 }
 
 cudaError_t he_launch_pack_fc_masked(const RingView &r, const int8_t *d_W, const uint32_t *d_m0, const uint32_t *d_m1,
-                                     const he_fc_layout &fl, int mode, uint32_t *bank, cudaStream_t st) {
+                                     const he_fc_layout &fl, int mode, uint32_t *bank, uint32_t *coef,
+                                     cudaStream_t st) {
     PackFcMaskedArgs a;
     a.r = r;
     a.W = d_W;
     a.m0 = d_m0;
     a.m1 = d_m1;
     a.bank = bank;
+    a.coef = coef;
     a.n_in = fl.n_in;
     a.n_in_p = fl.n_in_p;
     a.n_out = fl.n_out;
@@ -1768,7 +1832,6 @@ cudaError_t he_plan_prepare(const he_plan_s &pl) {
     if (e == cudaSuccess && pl.n_mac) e = set_smem(k_plan_mac, pl.smem_mac);
     if (e == cudaSuccess && pl.n_fin) e = set_smem(k_plan_fin, pl.smem_fin);
     if (e == cudaSuccess && pl.n_tc) e = he_tc_prepare();
-    if (e == cudaSuccess && pl.n_fc) e = set_smem(k_plan_fc, pl.smem_fc);
     if (e == cudaSuccess && pl.n_chan[0]) e = set_smem(k_plan_chan<2>, pl.smem_chan[0]);
     if (e == cudaSuccess && pl.n_chan[1]) e = set_smem(k_plan_chan<4>, pl.smem_chan[1]);
     if (e == cudaSuccess && pl.n_chan[2]) e = set_smem(k_plan_chan<8>, pl.smem_chan[2]);
@@ -1799,8 +1862,6 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), uint32_t grid, uint32_t block, si
 
 cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     cudaError_t e = cudaSuccess;
-    // fused FC items: forked onto the plan's side stream with the channel
-    // work, joined back before the last channel kernel's completion
     // phase: -1 whole run, 0 input NTTs, 1 everything after them, 2 the MAC
     // kernel alone, 3 everything after the MAC kernel
     if (phase == 4) {  // the rescale kernel alone
@@ -1811,14 +1872,6 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         if (pl.n_fin) k_plan_fin<<<pl.n_fin, kFinThreads, pl.smem_fin, st>>>(pl.d_calls, pl.d_fin);
         return cudaGetLastError();
     }
-    const bool fc = pl.n_fc && (phase == -1 || phase == 1 || phase == 3);
-    if (fc) {
-        if ((e = cudaEventRecord(pl.ev_fork, st)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(pl.side, pl.ev_fork, 0)) != cudaSuccess) return e;
-        k_plan_fc<<<pl.n_fc, kThreads, pl.smem_fc, pl.side>>>(pl.d_calls, pl.d_fc);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = cudaEventRecord(pl.ev_join, pl.side)) != cudaSuccess) return e;
-    }
     if (pl.n_ntt && (phase == -1 || phase == 0)) {
         e = set_smem(k_plan_ntt, pl.smem_ntt);
         if (e != cudaSuccess) return e;
@@ -1827,18 +1880,10 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         if (e != cudaSuccess) return e;
     }
     if (phase == 0) return cudaSuccess;
-    struct Join {
-        const he_plan_s &pl;
-        cudaStream_t st;
-        bool on;
-        ~Join() {
-            if (on) cudaStreamWaitEvent(st, pl.ev_join, 0);
-        }
-    } join{pl, st, fc};
     if (pl.n_mac && phase != 3) {
         e = launch_pdl(k_plan_mac, pl.mac_ctas, kThreads + 32, pl.smem_mac, st, (const MacCopy *)pl.d_mac_copy,
                        (const MacDesc *)pl.d_mac_desc, (const uint32_t *)pl.d_mac_offs, pl.d_status, pl.mac_xw,
-                       pl.mac_nst);
+                       pl.mac_nst, pl.wait_polls);
         if (e != cudaSuccess) return e;
     }
     if (pl.n_tc && phase != 3) {
@@ -1856,9 +1901,6 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     if ((e = plan_chan_launch<16>(pl, 3, st)) != cudaSuccess) return e;
     if ((e = plan_chan_launch<1>(pl, 4, st)) != cudaSuccess) return e;
     if (pl.n_rs) {
-        // the rescale reads every output, FC outputs included: join first
-        if (join.on && (e = cudaStreamWaitEvent(st, pl.ev_join, 0)) != cudaSuccess) return e;
-        join.on = false;
         k_plan_rescale<<<pl.n_rs, kThreads, 0, st>>>(pl.d_rs_calls, pl.d_rs_items);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

@@ -60,7 +60,7 @@ class he_op_counts(ctypes.Structure):
 
 class he_plan_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("split", "mac_item_kb", "mac_ctas_per_sm", "fused_max_nj",
-                                               "tc_min_batch")]
+                                               "tc_min_batch", "fc_direct")]
 
 
 class he_plan_info(ctypes.Structure):
@@ -125,6 +125,7 @@ _SIGS = {
     "he_plan_tuning_default": [ctypes.POINTER(he_plan_tuning)],
     "he_plan_create_tuned": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(he_plan_tuning), ctypes.POINTER(_vp)],
     "he_plan_workspace_bytes": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(_sz)],
+    "he_plan_set_wait_limit": [_vp, _u32],
     "he_plan_autotune": [ctypes.POINTER(he_layer_call), _u32, _u32, _vp, ctypes.POINTER(he_plan_tuning),
                          ctypes.POINTER(_vp)],
     "he_plan_run": [_vp, _vp],
@@ -458,6 +459,13 @@ def he_plan_workspace_bytes(calls) -> int:
     out = _sz()
     _check(lib().he_plan_workspace_bytes(_calls(calls), len(calls), ctypes.byref(out)))
     return out.value
+
+
+HE_WAIT_POLLS_DEFAULT = 1 << 20
+
+
+def he_plan_set_wait_limit(plan: int, polls: int) -> None:
+    _check(lib().he_plan_set_wait_limit(plan, polls))
 
 
 def he_plan_autotune(calls, iters: int = 5, stream=None) -> tuple[int, dict]:

@@ -99,9 +99,9 @@ class _Case:
         return U.from_dev(d).reshape(self.out_shape)
 
 
-def _run_plan(H, cases, stream, graph=False):
+def _run_plan(H, cases, stream, graph=False, fc_direct=1):
     torch = U.torch_cuda()
-    plan = H.he_plan_create([c.call() for c in cases])
+    plan = H.he_plan_create_tuned([c.call() for c in cases], dict(H.he_plan_tuning_default(), fc_direct=fc_direct))
     try:
         info = H.he_plan_query(plan, len(cases))
         outs = []
@@ -141,8 +141,10 @@ def _mixed(H, p, N, ps, psis, B=1, in_ntt=False):
     return cases
 
 
-@pytest.mark.parametrize("in_ntt", [False, True])
-def test_masked_and_client_calls_in_one_plan_match_single_calls(in_ntt):
+# fc_direct: the FC windows computed directly (coefficient-domain inputs)
+# or through the transforms; the words are the same
+@pytest.mark.parametrize("in_ntt,fc_direct", [(False, 1), (True, 1), (False, 0)])
+def test_masked_and_client_calls_in_one_plan_match_single_calls(in_ntt, fc_direct):
     H = U.he()
     torch = U.torch_cuda()
     N, L = 8192, 3
@@ -151,7 +153,7 @@ def test_masked_and_client_calls_in_one_plan_match_single_calls(in_ntt):
     with U.params(N, L) as p:
         cases = _mixed(H, p, N, ps, psis, in_ntt=in_ntt)
         try:
-            info, outs = _run_plan(H, cases, s)
+            info, outs = _run_plan(H, cases, s, fc_direct=fc_direct)
             # B = 1 masked and client Conv calls run in the split form
             for i, c in enumerate(cases):
                 if c.kind != "plain" and not c.shape.get("fc"):
@@ -165,9 +167,11 @@ def test_masked_and_client_calls_in_one_plan_match_single_calls(in_ntt):
                 H.he_filters_destroy(c.f)
 
 
-def test_masked_plan_matches_the_oracle():
+@pytest.mark.parametrize("fc_direct", [1, 0])
+def test_masked_plan_matches_the_oracle(fc_direct):
     """One masked Conv call (16 -> 16 at 32x32: 2G = 8) and one masked FC call
-    in a plan, against the oracle's words directly."""
+    in a plan, against the oracle's words directly (the FC window computed
+    directly, or through the transforms)."""
     H = U.he()
     torch = U.torch_cuda()
     N, L = 8192, 3
@@ -197,7 +201,7 @@ def test_masked_plan_matches_the_oracle():
             d_out, fd_out = U.empty_dev(ref.shape), U.empty_dev(fref.shape)
             calls = [(f, U.to_dev(c0), H.HE_COEFF, d_out, 1, U.to_dev(sh), U.to_dev(shp)),
                      (ff, U.to_dev(fc0), H.HE_COEFF, fd_out, 1, U.to_dev(fsh), U.to_dev(fshp))]
-            plan = H.he_plan_create(calls)
+            plan = H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), fc_direct=fc_direct))
             try:
                 H.he_plan_run(plan, s)
                 H.he_sync(s)

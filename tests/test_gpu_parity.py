@@ -226,7 +226,7 @@ def test_fc_encrypt_eval_decrypt():
 # argument errors, workspace growth, repeatability
 # ----------------------------------------------------------------------------
 
-def test_argument_errors_and_workspace_growth():
+def test_argument_errors_and_larger_batches():
     H = U.he()
     torch = U.torch_cuda()
     ps, psis, lay, cts, F, desc = U.conv_case(1024, 1, 8, 8, 6, 6, 4, seed=11)
@@ -245,7 +245,7 @@ def test_argument_errors_and_workspace_growth():
         with pytest.raises(H.HEError) as ei:
             H.he_conv_layer(p, f, buf, 7, U.empty_dev((1 << 16,)), H.HE_OUT_EXTRACTED, 1)
         assert ei.value.status == H.HE_ERR_ARG
-        # the workspace grows from B = 1 to B = 4; results stay exact and repeatable
+        # B = 1, then B = 4 with its workspace reserved; results stay exact and repeatable
         ref = O.conv_layer(cts, F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt")
         got1 = U.run_conv(p, f, cts[:1], H.HE_OUT_EXTRACTED, lay["H"])
         np.testing.assert_array_equal(got1, ref[:1])
@@ -280,14 +280,15 @@ def _plan_case(H, p, N, L, shape, B, seed, fc=False):
 
 def test_plan_mixed_rings_and_shapes_bit_exact():
     """A plan over independent calls with N in {1024, 2048, 4096}, 1-3 limbs,
-    B in {1, 2, 8}, Conv shapes with s = 2 .. 64 and FC layers (one of them
-    split over 2 weight polynomials), some inputs already in the NTT domain."""
+    B in {1, 2, 8}, Conv shapes with s = 2 .. 64 and FC layers (split over 2
+    and 3 weight polynomials; the last one's window computed directly), some
+    inputs already in the NTT domain."""
     H = U.he()
     torch = U.torch_cuda()
     specs = [(1024, 2, (16, 16, 8), 1, False), (2048, 1, (3, 4, 16), 1, False),
              (4096, 3, (16, 16, 32), 1, False), (4096, 2, (64, 100), 1, True),
              (2048, 3, (32, 64, 4), 2, False), (1024, 1, (64, 10), 2, True),
-             (4096, 2, (8, 16, 8), 8, False)]
+             (4096, 2, (8, 16, 8), 8, False), (2048, 2, (200, 20), 2, True)]
     pars = {}
     calls, refs, outs, keep = [], [], [], []
     try:
@@ -402,7 +403,7 @@ def test_plan_split_form_plain20_shapes_bit_exact():
             info = H.he_plan_query(plan, len(calls))
             assert info["split"] == [True] * len(PLAIN20_SHAPES) + [False]
             assert info["split_calls"] == len(PLAIN20_SHAPES)
-            assert info["kernels_per_run"] == 4        # NTT, MAC, finish, FC
+            assert info["kernels_per_run"] == 3        # NTT (and the FC window), MAC, finish
             assert info["fc_items"] > 0 and info["fused_items"] == 0
             s = torch.cuda.current_stream()
             # the whole run, then the same run in phases 0 + 1 and 0 + 2 + 3

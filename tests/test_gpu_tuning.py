@@ -42,11 +42,12 @@ def _check(H, calls, refs):
         np.testing.assert_array_equal(U.from_dev(c[3]).reshape(ref.shape), ref)
 
 
-TUNINGS = [dict(split=1, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=4),
-           dict(split=0, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=1),
-           dict(split=1, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=2, tc_min_batch=8),
-           dict(split=1, mac_item_kb=64, mac_ctas_per_sm=2, fused_max_nj=4, tc_min_batch=2),
-           dict(split=0, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=8, tc_min_batch=4)]
+# fc_direct = 1 computes the FC 64 -> 10 window directly, 0 through the transforms
+TUNINGS = [dict(split=1, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=4, fc_direct=1),
+           dict(split=0, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=1, fc_direct=0),
+           dict(split=1, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=2, tc_min_batch=8, fc_direct=1),
+           dict(split=1, mac_item_kb=64, mac_ctas_per_sm=2, fused_max_nj=4, tc_min_batch=2, fc_direct=0),
+           dict(split=0, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=8, tc_min_batch=4, fc_direct=1)]
 
 
 def test_every_tuning_gives_the_oracle_words():
