@@ -505,6 +505,8 @@ def run_ours(args, rank, world, device):
     clocks.start()
     time.sleep(0.3)
     with torch.cuda.stream(stream):
+        for k in range(W):  # the GPU idled while the sampler started: warm it up again
+            arm.graphs[k % arm.R].replay()
         t0.record(stream)
         for k in range(K):
             arm.graphs[k % arm.R].replay()
@@ -1386,6 +1388,9 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
               "layer_latency_ms": {"p50": pct(lat_layer, 50), "p99": pct(lat_layer, 99),
                                    "from": "entry into the layer's queue to its outputs on the host"},
               "batches": nb, "mean_batch": ncalls / max(1, nb), "hbm_bytes_peak": rep["bytes_peak"],
+              "batch_hist": {k: v - warm["batch_hist"][k] for k, v in rep["batch_hist"].items()},
+              "lanes_built_timed": rep["lanes"] + rep["evictions"] - warm["lanes"] - warm["evictions"],
+              "evictions_timed": rep["evictions"] - warm["evictions"],
               "failed": rep["failed"], "max_submit_wait_s": waits[0],
               "submit_late_ms": {"p99": pct(late, 99) * 1e3 if late else None,
                                  "max": max(late) * 1e3 if late else None,

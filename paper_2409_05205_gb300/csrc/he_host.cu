@@ -18,6 +18,7 @@
 #include <cuda.h>
 
 #include "he_internal.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace {
 
@@ -181,6 +182,13 @@ he_status fc_layout(const he_params_s *p, uint32_t n_in, uint32_t n_out, he_fc_l
     fl->P_fc = (n_out + fl->rows_per_poly - 1) / fl->rows_per_poly;
     return HE_OK;
 }
+
+// Names an entry point's host-side work (and so the GPU work it enqueues) in
+// a profiler's timeline; costs nothing when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 he_status need_device(const he_params_s *p) {
     if (p->device == HE_DEVICE_NONE) return fail(HE_ERR_ARG, "params were created without a device");
@@ -526,17 +534,20 @@ static he_status pack_conv(he_params_t p, const he_conv_desc *d, const int8_t *w
 }
 
 he_status he_pack_filters(he_params_t p, const he_conv_desc *d, const int8_t *w, he_filters_t *out) {
+    NvtxRange nvtx_("he_pack_filters");
     return pack_conv(p, d, w, 1, out);
 }
 
 he_status he_pack_filters_for_batch(he_params_t p, const he_conv_desc *d, const int8_t *w, uint32_t B,
                                     he_filters_t *out) {
+    NvtxRange nvtx_("he_pack_filters_for_batch");
     if (B == 0) return fail(HE_ERR_ARG, "B must be >= 1");
     return pack_conv(p, d, w, B, out);
 }
 
 he_status he_pack_masked(he_params_t p, const he_conv_desc *d, const int8_t *w, const uint32_t *rho,
                          he_filters_t *out) {
+    NvtxRange nvtx_("he_pack_masked");
     if (!p || !d || !w || !rho || !out) return fail(HE_ERR_ARG, "NULL argument");
     if (need_device(p) != HE_OK) return HE_ERR_ARG;
     *out = nullptr;
@@ -596,6 +607,7 @@ he_status he_pack_masked(he_params_t p, const he_conv_desc *d, const int8_t *w, 
 
 he_status he_pack_client(he_params_t p, const he_conv_desc *d, const uint32_t *p1, const uint32_t *p2,
                          he_filters_t *out) {
+    NvtxRange nvtx_("he_pack_client");
     if (!p || !d || !p1 || !p2 || !out) return fail(HE_ERR_ARG, "NULL argument");
     if (need_device(p) != HE_OK) return HE_ERR_ARG;
     *out = nullptr;
@@ -655,6 +667,7 @@ he_status he_pack_client(he_params_t p, const he_conv_desc *d, const uint32_t *p
 
 he_status he_conv_client(he_params_t p, he_filters_t f, const int32_t *d_v, const int32_t *d_ish, uint32_t *d_out,
                          uint32_t B, void *stream) {
+    NvtxRange nvtx_("he_conv_client");
     if (!p || !f || !d_v || !d_ish || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (f->kind != HE_KIND_CONV || f->masked != 2) return fail(HE_ERR_ARG, "filters are not a client bank");
     if (f->p != p) return fail(HE_ERR_ARG, "filters belong to other params");
@@ -698,6 +711,7 @@ static cudaError_t upload_fc_bias(const he_params_s *p, const int32_t *bias, uin
 
 he_status he_pack_fc(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t *W, const int32_t *bias,
                      he_filters_t *out) {
+    NvtxRange nvtx_("he_pack_fc");
     if (!p || !W || !out) return fail(HE_ERR_ARG, "NULL argument");
     if (need_device(p) != HE_OK) return HE_ERR_ARG;
     *out = nullptr;
@@ -752,6 +766,7 @@ void he_filters_destroy(he_filters_t f) {
 
 he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain, uint32_t *d_out,
                         int out_mode, uint32_t B, void *stream) {
+    NvtxRange nvtx_("he_conv_layer");
     if (!p || !f || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (f->kind != HE_KIND_CONV || f->p != p) return fail(HE_ERR_ARG, "filters are not a Conv bank of these params");
     if (f->masked) return fail(HE_ERR_ARG, "a masked bank is evaluated by he_conv_layer_masked");
@@ -783,6 +798,7 @@ he_status he_conv_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int
 
 he_status he_conv_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0, const uint32_t *d_sh,
                                const uint32_t *d_shp, int in_domain, uint32_t *d_out, uint32_t B, void *stream) {
+    NvtxRange nvtx_("he_conv_layer_masked");
     if (!p || !f || !d_c0 || !d_sh || !d_shp || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (f->kind != HE_KIND_CONV || f->masked != 1) return fail(HE_ERR_ARG, "filters are not a masked (server) Conv bank");
     if (f->p != p) return fail(HE_ERR_ARG, "filters belong to other params");
@@ -804,6 +820,7 @@ he_status he_conv_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_
 
 he_status he_fc_layer(he_params_t p, he_filters_t f, const uint32_t *d_in, int in_domain, uint32_t *d_out,
                       int out_mode, uint32_t B, void *stream) {
+    NvtxRange nvtx_("he_fc_layer");
     if (!p || !f || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (f->kind != HE_KIND_FC || f->p != p) return fail(HE_ERR_ARG, "filters are not an FC bank of these params");
     if (f->masked) return fail(HE_ERR_ARG, "a masked FC bank is evaluated by he_fc_layer_masked / he_fc_client");
@@ -895,18 +912,21 @@ static he_status pack_fc_masked(he_params_t p, uint32_t n_in, uint32_t n_out, in
 
 he_status he_pack_fc_masked(he_params_t p, uint32_t n_in, uint32_t n_out, const int8_t *W, const int32_t *bias,
                             const uint32_t *rho, he_filters_t *out) {
+    NvtxRange nvtx_("he_pack_fc_masked");
     if (!p || !W || !rho || !out) return fail(HE_ERR_ARG, "NULL argument");
     return pack_fc_masked(p, n_in, n_out, 1, W, bias, rho, nullptr, out);
 }
 
 he_status he_pack_fc_client(he_params_t p, uint32_t n_in, uint32_t n_out, const uint32_t *p1, const uint32_t *p2,
                             he_filters_t *out) {
+    NvtxRange nvtx_("he_pack_fc_client");
     if (!p || !p1 || !p2 || !out) return fail(HE_ERR_ARG, "NULL argument");
     return pack_fc_masked(p, n_in, n_out, 2, nullptr, nullptr, p1, p2, out);
 }
 
 he_status he_fc_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0, const uint32_t *d_sh,
                              const uint32_t *d_shp, int in_domain, uint32_t *d_out, uint32_t B, void *stream) {
+    NvtxRange nvtx_("he_fc_layer_masked");
     if (!p || !f || !d_c0 || !d_sh || !d_shp || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (f->kind != HE_KIND_FC || f->masked != 1) return fail(HE_ERR_ARG, "filters are not a masked (server) FC bank");
     if (f->p != p) return fail(HE_ERR_ARG, "filters belong to other params");
@@ -926,6 +946,7 @@ he_status he_fc_layer_masked(he_params_t p, he_filters_t f, const uint32_t *d_c0
 
 he_status he_fc_client(he_params_t p, he_filters_t f, const int32_t *d_v, const int32_t *d_ish, uint32_t *d_out,
                        uint32_t B, void *stream) {
+    NvtxRange nvtx_("he_fc_client");
     if (!p || !f || !d_v || !d_ish || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (f->kind != HE_KIND_FC || f->masked != 2) return fail(HE_ERR_ARG, "filters are not a client FC bank");
     if (f->p != p) return fail(HE_ERR_ARG, "filters belong to other params");
@@ -943,6 +964,7 @@ he_status he_fc_client(he_params_t p, he_filters_t f, const int32_t *d_v, const 
 }
 
 he_status he_rescale(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count, void *stream) {
+    NvtxRange nvtx_("he_rescale");
     if (!p || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (p->L < 2) return fail(HE_ERR_ARG, "rescaling needs at least 2 limbs (L = %u)", p->L);
     if (!aligned16(d_in) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
@@ -965,6 +987,7 @@ he_status he_bench_butterflies(he_params_t p, uint32_t blocks, uint32_t iters, u
 }
 
 he_status he_ntt_forward(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count, void *stream) {
+    NvtxRange nvtx_("he_ntt_forward");
     if (!p || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (need_device(p) != HE_OK) return HE_ERR_ARG;
     if (!aligned16(d_in) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
@@ -975,6 +998,7 @@ he_status he_ntt_forward(he_params_t p, const uint32_t *d_in, uint32_t *d_out, u
 }
 
 he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out, uint32_t count, void *stream) {
+    NvtxRange nvtx_("he_ntt_inverse");
     if (!p || !d_in || !d_out) return fail(HE_ERR_ARG, "NULL argument");
     if (need_device(p) != HE_OK) return HE_ERR_ARG;
     if (!aligned16(d_in) || !aligned16(d_out)) return fail(HE_ERR_ARG, "buffers must be 16-byte aligned");
@@ -1242,18 +1266,20 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             cd.nj = std::min(he_conv_nj(g.ncols, lay.M, lay.s), tu.fused_max_nj);
             cd.nb = lay.s >= 4 ? 1 : (lay.s == 2 ? 2 : 4);
             cd.cpt = he_conv_cpt(cd.nj, cd.nb, g.G);
-            // split form for one ciphertext per call with s >= 4, G in
-            // {1, 2, 4} (2G in {2, 4, 8} for the one-column masked and client
-            // steps) whose inputs fit one MAC input buffer and whose output
-            // polynomials fit shared memory
+            // split form for one ciphertext per call with s >= 4 (the groups,
+            // 2G for the one-column masked and client steps, taken in parts
+            // of gp <= 8) whose part inputs fit one MAC input buffer and
+            // whose output polynomials fit shared memory
             const uint32_t ncol = msrc ? 1u : 2u;
+            g.gp = group_part(g.G);
+            g.parts = g.G / g.gp;
             cd.split = (tu.split && c.B == 1 && split_mac_ok(lay.s, g.G) &&
-                        ((ncol * g.G) << f->logTS) <= kMacXWordsBig &&
+                        ((ncol * g.gp) << f->logTS) <= kMacXWordsBig &&
                         (size_t)std::min(lay.s, f->desc.co) * fin_stride(lay.M, lay.s) * 4u <= 200u * 1024u)
                            ? 1u
                            : 0u;
             g.cs = split_cs(lay.s, g.G);
-            g.nc = std::min(f->desc.co, std::max(1u, (tu.mac_item_kb * 256u) / (g.G << f->logTS)));
+            g.nc = std::min(f->desc.co, std::max(1u, (tu.mac_item_kb * 256u) / (g.gp << f->logTS)));
             // bank interleave and tile must match the MAC kernel's
             if (cd.split && ((1u << f->lcs) != g.cs || f->logTS != split_tile_log(f->lcs))) cd.split = 0;
             g.tc = btc;
@@ -1335,7 +1361,7 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         if (descs[i].split || descs[i].zt) {
             const ConvGeo &g = descs[i].g;
             z_off[i] = ws_words;
-            ws_words += (size_t)g.L * g.ncols * g.co * g.M;
+            ws_words += (size_t)(descs[i].split ? g.parts : 1u) * g.L * g.ncols * g.co * g.M;
         }
     if (ws_only) {
         *ws_only = ws_words * sizeof(uint32_t);
@@ -1389,7 +1415,10 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             for (uint32_t jp = 0; jp < g.P; ++jp)
                 for (uint32_t l = 0; l < g.L; ++l)
                     for (uint32_t col = 0; col < g.ncols; ++col) {
-                        ntt_cost.push_back({cost, NttItem{i, (jp * g.L + l) * g.ncols + col}});
+                        NttItem it{};
+                        it.call = i;
+                        it.poly = (jp * g.L + l) * g.ncols + col;
+                        ntt_cost.push_back({cost, it});
                         ++n_fc;
                     }
             continue;
@@ -1398,7 +1427,20 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             // the input-NTT kernel transforms (or stages) every input polynomial
             g.x = pl->ws + ws_off[i];
             const size_t npoly = (size_t)calls[i].B * g.G * (cd.msrc ? 1u : 2u) * g.L;
-            for (size_t pidx_ = 0; pidx_ < npoly; ++pidx_) ntt_cost.push_back({N * logN, NttItem{i, (uint32_t)pidx_}});
+            for (size_t pidx_ = 0; pidx_ < npoly; ++pidx_) {
+                NttItem it{};
+                it.call = i;
+                it.poly = (uint32_t)pidx_;
+                if (!cd.msrc) {  // plain inputs: poly p of [npoly][L][N], limb p % L
+                    const uint32_t l = (uint32_t)(pidx_ % g.L);
+                    it.src = cd.x_coeff + pidx_ * g.N;
+                    it.dst = const_cast<uint32_t *>(g.x) + pidx_ * g.N;
+                    it.tw = cd.tw_fwd + (size_t)l * g.N;
+                    it.q = cd.limb[l].q;
+                    it.logN = g.logN;
+                }
+                ntt_cost.push_back({N * logN, it});
+            }
         }
         if (cd.kind == HE_KIND_FC) {
             // FC items (product, length-N inverse transform, window) run in
@@ -1421,12 +1463,15 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
                     for (uint32_t col = 0; col < g.ncols; ++col) fin.push_back({fcost, ChanItem{i, h, l, col}});
         } else if (cd.split) {
             cd.z = pl->ws + z_off[i];
-            const int cls = he_mac_class(g.G, g.cs);
+            const int cls = he_mac_class(g.gp, g.cs);
             const uint32_t T = g.N >> g.logTS;
-            const double mcost = (double)std::min(g.nc, g.co) * g.G * (1u << g.logTS);
-            for (uint32_t t = 0; t < T; ++t)
-                for (uint32_t l = 0; l < g.L; ++l)
-                    for (uint32_t n0 = 0; n0 < g.co; n0 += g.nc) mac[cls].push_back({mcost, ChanItem{i, t, l, n0}});
+            const double mcost = (double)std::min(g.nc, g.co) * g.gp * (1u << g.logTS);
+            // MAC items (call, part * T + tile, limb, first channel)
+            for (uint32_t pt = 0; pt < g.parts; ++pt)
+                for (uint32_t t = 0; t < T; ++t)
+                    for (uint32_t l = 0; l < g.L; ++l)
+                        for (uint32_t n0 = 0; n0 < g.co; n0 += g.nc)
+                            mac[cls].push_back({mcost, ChanItem{i, pt * T + t, l, n0}});
             const double fcost = 3.0 * (N / 2.0) * g.logM + N;
             for (uint32_t h = 0; h < g.H; ++h)
                 for (uint32_t l = 0; l < g.L; ++l)
@@ -1514,13 +1559,14 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             const CallDesc &cd = descs[it.call];
             const ConvGeo &g = cd.g;
             const uint32_t lt = g.logTS, nc = std::min(g.nc, g.co - it.b);
+            const uint32_t T = g.N >> lt, part = it.a / T, tile = it.a % T;
             MacCopy c;
-            c.w = g.bank + bank_index(it.b, it.l, 0, it.a << lt, g.logN, lt, g.lcs, g.co, g.G);
-            c.x = g.x + (size_t)it.l * g.N + ((size_t)it.a << lt);
-            c.nwords = (nc * g.G) << lt;
-            c.xstride = g.L * g.N;
             c.ncol = cd.msrc ? 1u : 2u;
-            c.xrows = c.ncol * g.G;
+            c.w = g.bank + bank_index(it.b, it.l, part * g.gp, tile << lt, g.logN, lt, g.lcs, g.co, g.G);
+            c.x = g.x + (size_t)part * g.gp * c.ncol * g.L * g.N + (size_t)it.l * g.N + ((size_t)tile << lt);
+            c.nwords = (nc * g.gp) << lt;
+            c.xstride = g.L * g.N;
+            c.xrows = c.ncol * g.gp;
             c.xwords = 1u << lt;
             if (c.xrows * c.xwords > kMacXWords) {  // 2 columns x 8 groups: the larger input buffers
                 pl->mac_xw = kMacXWordsBig;
@@ -1530,11 +1576,12 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             copies.push_back(c);
             MacDesc d{};
             d.ncol = c.ncol;
-            d.z = cd.z + ((size_t)it.l * g.ncols * g.co + it.b) * g.M + (((size_t)it.a << lt) >> g.logs);
+            d.z = cd.z + (size_t)part * g.L * g.ncols * g.co * g.M + ((size_t)it.l * g.ncols * g.co + it.b) * g.M +
+                  (((size_t)tile << lt) >> g.logs);
             d.colstride = g.co * g.M;
             d.M = g.M;
             d.nch = nc;
-            d.cls = (uint32_t)he_mac_class(g.G, g.cs);
+            d.cls = (uint32_t)he_mac_class(g.gp, g.cs);
             d.logs = g.logs;
             d.nst = (c.nwords + kMacStageWords - 1) / kMacStageWords;
             const LimbK &K = cd.limb[it.l];
@@ -1620,6 +1667,7 @@ he_status he_plan_check(he_plan_t plan) {
 }
 
 he_status he_plan_run(he_plan_t plan, void *stream) {
+    NvtxRange nvtx_("he_plan_run");
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
@@ -1628,6 +1676,7 @@ he_status he_plan_run(he_plan_t plan, void *stream) {
 }
 
 he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream) {
+    NvtxRange nvtx_("he_plan_run_phase");
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
     if (phase < HE_PHASE_NTT || phase > HE_PHASE_FIN) return fail(HE_ERR_ARG, "phase must be 0 .. 5");
     DeviceGuard g(plan->device);

@@ -79,39 +79,57 @@ struct ConvGeo {
     uint32_t tc;              // conv bank in the tensor-core layout (bank_index_tc)
     uint32_t masked;          // the masked server step (Alg. 1): one column per ciphertext,
                               // inputs [B][G][L][N], outputs [B][H][L][N] + Delta_Q sh'
-    uint32_t pad_geo[2];
+    uint32_t gp, parts;       // groups per part (group_part(G)) and G / gp
     const uint32_t *shp;      // masked: the output share sh' [B][H][N], integers in [0, t)
 };
 
-// Conv filter bank layout: [L][N/TS][co][G][TS] (TS = 2^lt slots, a
-// power of two <= N chosen per bank), so the weights one slot tile of one
-// limb needs, for any range of channels, are one contiguous region.  Inside
-// a row of TS words the 4-word chunks are interleaved by CS = 2^lcs: chunk
-// j sits at chunk position (j mod CS) * (TS / 4CS) + j / CS, so the threads
-// that each own CS consecutive chunks read consecutive 16-byte words.
+// Input groups are taken in parts of gp = group_part(G) groups, the largest
+// of 8, 4, 2, 1 that divides G (G = 12: three parts of 4; G = 6: three of 2;
+// G in {1, 2, 4, 8}: one part).  The split-form MAC kernel sums one part of
+// a channel's groups per work item, so its register and accumulator budget
+// (at most 8 groups, at most 16 products per 64-bit sum) holds for any G;
+// the finishing kernel adds the parts' sums.
+__host__ __device__ __forceinline__ uint32_t group_part(uint32_t G) {
+    return (G & 7u) == 0 ? 8u : ((G & 3u) == 0 ? 4u : ((G & 1u) == 0 ? 2u : 1u));
+}
+
+// Conv filter bank layout: [L][N/TS][parts][co][gp][TS] (TS = 2^lt slots, a
+// power of two <= N chosen per bank; gp groups per part, see group_part), so
+// the weights one slot tile of one limb and one part need, for any range of
+// channels, are one contiguous region.  With one part this is
+// [L][N/TS][co][G][TS].  Inside a row of TS words the 4-word chunks are
+// interleaved by CS = 2^lcs: chunk j sits at chunk position
+// (j mod CS) * (TS / 4CS) + j / CS, so the threads that each own CS
+// consecutive chunks read consecutive 16-byte words.
 __host__ __device__ __forceinline__ uint32_t bank_row_pos(uint32_t kk, uint32_t lt, uint32_t lcs) {
     const uint32_t chunk = kk >> 2, lng = lt - 2 - lcs;
     return ((((chunk & ((1u << lcs) - 1u)) << lng) + (chunk >> lcs)) << 2) + (kk & 3u);
 }
 __host__ __device__ __forceinline__ size_t bank_index(uint32_t n, uint32_t l, uint32_t g, uint32_t k, uint32_t logN,
                                                       uint32_t lt, uint32_t lcs, uint32_t co, uint32_t G) {
+    const uint32_t gp = group_part(G), parts = G / gp;
     const size_t tile = ((size_t)l << (logN - lt)) + (k >> lt);
-    return (((tile * co + n) * G + g) << lt) + bank_row_pos(k & ((1u << lt) - 1u), lt, lcs);
+    return ((((tile * parts + g / gp) * co + n) * gp + g % gp) << lt) + bank_row_pos(k & ((1u << lt) - 1u), lt, lcs);
+}
+// words between two parts of one channel's weights in one slot tile
+__host__ __device__ __forceinline__ size_t bank_part_stride(uint32_t lt, uint32_t co, uint32_t G) {
+    return ((size_t)co * group_part(G)) << lt;
 }
 
 // Split-form MAC geometry of a Conv layer: chunks of 4 slots per thread
-// (cs) and bank tile log2 (lt).  The split form needs s >= 4 and G in
-// {1, 2, 4}; then cs = min(4 / G, s / 4), so a thread's inputs are 8 uint4 and
-// a channel's products per column are at most 16.  Other layers use a
-// 512-slot tile.
+// (cs) and bank tile log2 (lt).  The split form needs s >= 4; with gp
+// groups per part, cs = min(4 / gp, s / 4), so a thread's inputs are 8 uint4
+// and a channel's products per column and part are at most 16.  Other
+// layers use a 512-slot tile.
 __host__ __device__ __forceinline__ uint32_t split_cs(uint32_t s, uint32_t G) {
-    const uint32_t a = G >= 4 ? 1u : 4u / G, b = s / 4u;
+    const uint32_t gp = group_part(G);
+    const uint32_t a = gp >= 4 ? 1u : 4u / gp, b = s / 4u;
     return a < b ? a : b;
 }
 // The s-slot block of one output value must lie within one warp's lanes
 // (s / (4 CS) <= 32) for the block sum.
 __host__ __device__ __forceinline__ bool split_mac_ok(uint32_t s, uint32_t G) {
-    return s >= 4 && (G == 1 || G == 2 || G == 4 || G == 8) && s <= 128u * split_cs(s, G);
+    return s >= 4 && s <= 128u * split_cs(s, G);
 }
 // log2 of the chunk interleave of a bank: log2(split_cs) for split layers,
 // else 0 (no interleave); never more than the tile allows
@@ -185,7 +203,7 @@ struct CallDesc {
     const uint32_t *x_coeff;  // coefficient-domain input (nullptr when the call's input is in NTT form);
                               // masked server calls: c0 in either domain (a_ntt); client calls: v (int32)
     const uint2 *tw_fwd;      // [L][N]
-    uint32_t *z;              // split form: folded channel sums [L][ncols][co][M]
+    uint32_t *z;              // split form: folded channel sums [parts][L][ncols][co][M]
     const uint32_t *src_b;    // masked server calls: sh [B][G][N]; client calls: i + sh (int32 [B][G][N])
     uint32_t kind, nj, nb, cpt;
     uint32_t split;           // 1: MAC kernel + finishing kernel; 0: one fused channel kernel
@@ -269,6 +287,12 @@ __host__ __device__ __forceinline__ uint32_t fin_stride(uint32_t M, uint32_t s) 
 
 struct NttItem {
     uint32_t call, poly;      // poly index within the call's [npoly][L][N] input (Conv and FC)
+    // ordinary transforms (src != nullptr) carry what the kernel needs, so it
+    // starts its loads without first reading the call table
+    const uint32_t *src;      // coefficient-domain polynomial, or nullptr (the call table decides)
+    uint32_t *dst;            // its NTT-domain image
+    const uint2 *tw;          // forward twiddles of its limb
+    uint32_t q, logN;
 };
 
 struct ChanItem {

@@ -212,17 +212,20 @@ __device__ __forceinline__ void conv_fold_body(const ConvGeo &a, const LimbK &K,
     const uint32_t N = a.N, G = a.G, s = a.s, M = a.M;
     const uint32_t PS = padded_words(M);
     const uint32_t lt = a.logTS, TS = 1u << lt;
-    // channel n's weights for tile t: G rows of TS words at W(t)
+    // channel n's weights for tile t: per part, gp rows of TS words
     const uint32_t *Wb = a.bank + bank_index(n, l, 0, 0, a.logN, a.logTS, a.lcs, a.co, G);
-    const size_t tstride = (size_t)a.co * G << lt;
+    const size_t tstride = (size_t)a.co * G << lt, pstride = bank_part_stride(lt, a.co, G);
+    const uint32_t gp = group_part(G);
     // put every tile segment of this channel's weights in flight to L2 at
     // once, so the loads below wait on L2, not on DRAM
     if (threadIdx.x == 0 && !a.tc)
-        for (uint32_t t = 0; t < (N >> lt); ++t) prefetch_l2_bulk(Wb + t * tstride, (G << lt) * 4u);
+        for (uint32_t t = 0; t < (N >> lt); ++t)
+            for (uint32_t pt = 0; pt < G / gp; ++pt) prefetch_l2_bulk(Wb + t * tstride + pt * pstride, (gp << lt) * 4u);
     // 4 consecutive weight words of group g from slot k (k a multiple of 4) in either bank layout
     auto wq = [&](uint32_t g, uint32_t k) -> const uint32_t * {
         if (a.tc) return a.bank + bank_index_tc(n, l, g, k, a.logs, M, G, a.co);
-        return Wb + (k >> lt) * tstride + (size_t)g * TS + bank_row_pos(k & (TS - 1), lt, a.lcs);
+        return Wb + (k >> lt) * tstride + (g / gp) * pstride + (size_t)(g % gp) * TS +
+               bank_row_pos(k & (TS - 1), lt, a.lcs);
     };
     const size_t gstride = x_gstride(a);
     const uint32_t *X[NJ];
@@ -329,8 +332,8 @@ __device__ __forceinline__ void conv_full_body(const ConvGeo &a, const LimbK &K,
     uint32_t *Y = reinterpret_cast<uint32_t *>(smem4);
     const uint32_t N = a.N, L = a.L, G = a.G, s = a.s, logN = a.logN;
     const uint32_t *Wb = a.bank + bank_index(n, l, 0, 0, logN, a.logTS, a.lcs, a.co, G);
-    const uint32_t lt = a.logTS, TS = 1u << lt;
-    const size_t tstride = (size_t)a.co * G << lt;
+    const uint32_t lt = a.logTS, TS = 1u << lt, gp = group_part(G);
+    const size_t tstride = (size_t)a.co * G << lt, pstride = bank_part_stride(lt, a.co, G);
     const uint32_t *Xc = a.x + ((size_t)((c >> 1) * G * 2 + (c & 1)) * L + l) * N;
     const size_t gstride = (size_t)2 * L * N;
     const uint32_t off = (n & (s - 1)) * a.mult;
@@ -341,7 +344,8 @@ __device__ __forceinline__ void conv_full_body(const ConvGeo &a, const LimbK &K,
         int gc = 0;
         const uint32_t *Wk = Wb + (k >> lt) * tstride + bank_row_pos(k & (TS - 1), lt, a.lcs);
         for (uint32_t g = 0; g < G; ++g) {
-            const uint32_t *wp = a.tc ? a.bank + bank_index_tc(n, l, g, k, a.logs, a.M, G, a.co) : Wk + (size_t)g * TS;
+            const uint32_t *wp = a.tc ? a.bank + bank_index_tc(n, l, g, k, a.logs, a.M, G, a.co)
+                                      : Wk + (g / gp) * pstride + (size_t)(g % gp) * TS;
             acc += (uint64_t)__ldg(wp) * __ldg(Xc + g * gstride + k);
             if (++gc == 16) {
                 gc = 0;
@@ -1002,6 +1006,13 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
     extern __shared__ uint4 smem4[];
     pdl_trigger();  // the MAC kernel may start streaming weights now
     const NttItem it = items[blockIdx.x];
+    if (it.src) {  // an ordinary input transform
+        if (it.logN == 13 && blockDim.x == 512)
+            ntt_fwd_8192_warp(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.tw, it.q);
+        else
+            ntt_fwd_c(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.logN, it.tw, it.q);
+        return;
+    }
     const CallDesc &cd = calls[it.call];
     const uint32_t N = cd.g.N, L = cd.g.L;
     if (cd.fc_direct) {  // item poly = (jp * L + l) * ncols + column
@@ -1384,13 +1395,26 @@ __global__ void __launch_bounds__(kFinThreads, 3) k_plan_fin(const CallDesc *__r
             }
         }
     }
+    // split form: the parts' folded sums [parts][L][ncols][co][M], added
     const uint32_t *zsrc = cd.z + (((size_t)l * cd.g.ncols + c) * co + h * s) * M;
+    const size_t zpart4 = ((size_t)cd.g.L * cd.g.ncols * co * M) >> 2;
     for (uint32_t q0 = 0; q0 < (cd.zt ? 0u : nq); q0 += 8u * blockDim.x) {
         uint4 v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const uint32_t qi = q0 + u * blockDim.x + threadIdx.x;
             if (qi < nq) v[u] = __ldcs(reinterpret_cast<const uint4 *>(zsrc) + qi);
+        }
+        for (uint32_t pt = 1; pt < cd.g.parts; ++pt) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t qi = q0 + u * blockDim.x + threadIdx.x;
+                if (qi < nq) {
+                    const uint4 w = __ldcs(reinterpret_cast<const uint4 *>(zsrc) + pt * zpart4 + qi);
+                    v[u] = make_uint4(red_2q(v[u].x + w.x, K.q), red_2q(v[u].y + w.y, K.q), red_2q(v[u].z + w.z, K.q),
+                                      red_2q(v[u].w + w.w, K.q));
+                }
+            }
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {

@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "he_internal.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace {
 
@@ -201,6 +202,10 @@ Lane *get_lane(Server *s, uint32_t model, uint32_t layer, uint32_t bucket, bool 
 
 // issue one batch on a stream.  Called with s->mu held.
 bool launch(Server *s, Lane *lane, std::vector<Req *> &rs) {
+    nvtxRangePushA("he_server batch");  // one range per batch launch on the scheduler thread
+    struct Pop {
+        ~Pop() { nvtxRangePop(); }
+    } pop;
     const ModelLayer &ml = s->models[lane->model].layers[lane->layer];
     cudaStream_t st = s->streams[s->next_stream++ % s->streams.size()];
     Batch *b = new (std::nothrow) Batch{s, lane, rs, true};

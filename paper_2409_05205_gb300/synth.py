@@ -93,21 +93,33 @@ def v_poly(seed: int, stream, n: int) -> np.ndarray:
 # Workload shapes (plain-20 on CIFAR-shaped inputs, only the shapes are used)
 # ----------------------------------------------------------------------------
 
+def plain_conv_layers(width: int = 1, depth: int = 20) -> list[dict]:
+    """The 3x3 Conv layers of a plain network of depth 6n + 2 on 32x32x3
+    inputs (the last layer is the FC): 3->16w @32x32, then three stages of
+    2n layers: 2n x 16w->16w @32x32; 16w->32w stride 2 (evaluated on
+    32x32) and 2n-1 x 32w->32w @16x16; 32w->64w stride 2 (on 16x16) and
+    2n-1 x 64w->64w @8x8.  Depth 20 is plain-20 (19 Conv layers), depth 14
+    has 13."""
+    assert depth >= 8 and (depth - 2) % 6 == 0
+    n2 = (depth - 2) // 3
+    c1, c2, c3 = 16 * width, 32 * width, 64 * width
+    L = [dict(ci=3, co=c1, h=32, w=32, stride=1)]
+    L += [dict(ci=c1, co=c1, h=32, w=32, stride=1) for _ in range(n2)]
+    L += [dict(ci=c1, co=c2, h=32, w=32, stride=2)]
+    L += [dict(ci=c2, co=c2, h=16, w=16, stride=1) for _ in range(n2 - 1)]
+    L += [dict(ci=c2, co=c3, h=16, w=16, stride=2)]
+    L += [dict(ci=c3, co=c3, h=8, w=8, stride=1) for _ in range(n2 - 1)]
+    for d in L:
+        d.update(fh=3, fw=3, pad=1)
+    return L
+
+
 def plain20_conv_layers(width: int = 1) -> list[dict]:
     """The 19 3x3 Conv layers of a plain-20 network on 32x32x3 inputs:
     3->16w @32x32, 6x 16w->16w @32x32, 16w->32w stride 2 (evaluated on
     32x32), 5x 32w->32w @16x16, 32w->64w stride 2 (on 16x16),
     5x 64w->64w @8x8."""
-    c1, c2, c3 = 16 * width, 32 * width, 64 * width
-    L = [dict(ci=3, co=c1, h=32, w=32, stride=1)]
-    L += [dict(ci=c1, co=c1, h=32, w=32, stride=1) for _ in range(6)]
-    L += [dict(ci=c1, co=c2, h=32, w=32, stride=2)]
-    L += [dict(ci=c2, co=c2, h=16, w=16, stride=1) for _ in range(5)]
-    L += [dict(ci=c2, co=c3, h=16, w=16, stride=2)]
-    L += [dict(ci=c3, co=c3, h=8, w=8, stride=1) for _ in range(5)]
-    for d in L:
-        d.update(fh=3, fw=3, pad=1)
-    return L
+    return plain_conv_layers(width, 20)
 
 
 def f5_d8_w3_conv_layers() -> list[dict]:
@@ -183,6 +195,12 @@ WORKLOADS = {
                                fc=dict(n_in=64, n_out=10), wlo=-128, whi=127, masked=True),
     "f5_d8_w3": dict(N=8192, L=3, t=65537, B=1, conv=f5_d8_w3_conv_layers(), fc=dict(n_in=192, n_out=10),
                      wlo=-128, whi=127),
+    # the f3-d20-w3 and f3-d14-w3 variants: plain-20 / plain-14 at three
+    # times the width (48 / 96 / 192 channels), CIFAR-10 classifier
+    "f3_d20_w3": dict(N=8192, L=3, t=65537, B=1, conv=plain_conv_layers(3, 20), fc=dict(n_in=192, n_out=10),
+                      wlo=-128, whi=127),
+    "f3_d14_w3": dict(N=8192, L=3, t=65537, B=1, conv=plain_conv_layers(3, 14), fc=dict(n_in=192, n_out=10),
+                      wlo=-128, whi=127),
     "resnet50_bottleneck": dict(N=8192, L=3, t=65537, B=1, conv=resnet_bottleneck_conv_layers(), fc=None,
                                 wlo=-128, whi=127),
     # one layer of the wide x4 network (64 -> 64 channels at 32x32, N = 16384,

@@ -1,8 +1,11 @@
-"""Other layer families (5x5 filters of the f5 variant, ResNet-style 1x1
-layers with c_o < c_i and c_o > c_i, and their 3x3 layers at 14x14) at full
-size, N = 8192 and 3 limbs: a plan, single calls and the oracle give the
-same words (every word of one limb by the oracle's NTT tier, sampled words
-of every limb by its schoolbook dot products)."""
+"""Other layer families (5x5 filters of the f5 variant, the 3x3 layers of
+the w3 variants at 48 / 96 / 192 channels, ResNet-style 1x1 layers with
+c_o < c_i and c_o > c_i, and their 3x3 layers at 14x14) at full size,
+N = 8192 and 3 limbs: a plan, single calls and the oracle give the same
+words (every word of one limb by the oracle's NTT tier, sampled words of
+every limb by its schoolbook dot products).  Every layer with an interleave
+s >= 4 takes the split form in the plan, its input groups taken in parts of
+8, 4, 2 or 1 (G = 12, 6, 3, 32 have 3, 3, 3, 4 parts)."""
 
 from __future__ import annotations
 
@@ -18,7 +21,9 @@ pytestmark = pytest.mark.gpu
 # (ci, co, hw, f, pad, N, L)
 SHAPES = [(48, 48, 32, 5, 2, 8192, 3), (96, 192, 16, 5, 2, 8192, 3), (192, 192, 8, 5, 2, 8192, 3),
           (3, 48, 32, 5, 2, 8192, 3), (1024, 256, 14, 1, 0, 8192, 3), (256, 1024, 14, 1, 0, 8192, 3),
-          (256, 256, 14, 3, 1, 8192, 3), (64, 64, 32, 3, 1, 16384, 2)]
+          (256, 256, 14, 3, 1, 8192, 3), (64, 64, 32, 3, 1, 16384, 2),
+          (3, 48, 32, 3, 1, 8192, 3), (48, 48, 32, 3, 1, 8192, 3), (48, 96, 32, 3, 1, 8192, 3),
+          (96, 96, 16, 3, 1, 8192, 3), (96, 192, 16, 3, 1, 8192, 3), (192, 192, 8, 3, 1, 8192, 3)]
 
 
 @pytest.mark.parametrize("ci,co,hw,f,pad,N,L", SHAPES)
@@ -31,9 +36,8 @@ def test_layer_family_full_size(ci, co, hw, f, pad, N, L):
         single = U.run_conv(p, fb, cts, H.HE_OUT_EXTRACTED, lay["H"])
         d_in, d_out = U.to_dev(cts), U.empty_dev(single.shape)
         plan = H.he_plan_create([(fb, d_in, H.HE_COEFF, d_out, B)])
-        # G = 8 at s >= 4 (two columns of 8 groups) takes the split form with
-        # the larger input buffers
-        if lay["G"] == 8 and lay["s"] >= 4:
+        # s >= 4: the split form, groups in parts (G = 8: the larger input buffers)
+        if lay["s"] >= 4:
             assert H.he_plan_query(plan, 1)["form"][0] == 1
         try:
             H.he_plan_run(plan, torch.cuda.current_stream())
