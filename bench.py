@@ -293,17 +293,21 @@ class Arm:
     def butterflies(self, form):
         """Algorithmic butterflies of the input-NTT kernel (every Conv and FC
         call's input polynomials: (N/2) log2 N each) and of the finishing
-        kernel (every split-form Conv call: one length-N/s inverse transform
-        per output channel, limb and column, (M/2) log2 M each; every FC
-        call: one length-N inverse transform per weight block, limb and
-        column)."""
+        kernel (every Conv call whose MAC is the split or the tensor-core
+        kernel: one length-N/s inverse transform per output channel, limb and
+        column, (M/2) log2 M each; every FC call: one length-N inverse
+        transform per weight block, limb and column; an FC call whose window
+        is computed directly does neither, and is counted as the transforms
+        it replaces)."""
         ntt, fin = 0, 0
         for c, g, f in zip(self.calls, self.geo, form):
             N, L, B = c["N"], c["L"], c["B"]
+            if f == 3:  # FC window computed directly: no transforms
+                continue
             ntt += g["npoly"] * L * (N // 2) * (N.bit_length() - 1)
             if c["kind"] != "conv":
                 fin += g["lay"]["P_fc"] * L * 2 * B * (N // 2) * (N.bit_length() - 1)
-            elif f == 1:
+            elif f in (1, 2):  # split form, scalar or tensor-core MAC: the finishing kernel's transforms
                 M = g["lay"]["M"]
                 fin += c["co"] * L * 2 * B * (M // 2) * (M.bit_length() - 1)
         return ntt, fin
@@ -546,7 +550,7 @@ def run_ours(args, rank, world, device):
     mac_bytes = arm.mac_bytes(info["form"])
     tc_fl = arm.tc_flops(info["form"])
     tpeak, tsrc = _tensor_peak()
-    kinds = sorted({int(v) for v in info["form"] if v})
+    kinds = sorted({int(v) for v in info["form"] if v in (1, 2)})
     mac_name = " + ".join({1: "k_plan_mac", 2: "k_tc_mac"}[k] for k in kinds) or "none"
     mac_what = " / ".join({1: "split-form (scalar)", 2: "tensor-core"}[k] for k in kinds) or "split-form"
     hbm, peak_src = _peaks()

@@ -562,11 +562,14 @@ typedef struct {
 } he_plan_info;
 /* Fills *info; if `split` is not NULL, also split[i] for each call i (of
  * the ncalls given to he_plan_create): 1 if it takes the split form with the
- * scalar MAC kernel, 2 if it takes the tensor-core MAC kernel, else 0 (one
- * fused channel kernel).  Host only, non-blocking. */
+ * scalar MAC kernel, 2 if it takes the tensor-core MAC kernel, 3 for an FC
+ * call whose output window is computed directly (fc_direct), else 0 (one
+ * fused channel kernel, or an FC call on the transform path).  Host only,
+ * non-blocking. */
 he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split);
 /* Reports whether a bounded device-side wait of an earlier run gave up
- * (HE_ERR_TIMEOUT; the outputs of that run are then unspecified) and clears
+ * (HE_ERR_TIMEOUT) or, with checks on (he_plan_set_checks), a bounds check
+ * failed (HE_ERR_ARG); the outputs of that run are then unspecified.  Clears
  * the flag.  Blocking; call it after the streams the plan ran on are
  * synchronized. */
 he_status he_plan_check(he_plan_t plan);
@@ -582,6 +585,15 @@ he_status he_plan_check(he_plan_t plan);
  * paper has no counterpart.) */
 #define HE_WAIT_POLLS_DEFAULT (1u << 20)
 he_status he_plan_set_wait_limit(he_plan_t plan, uint32_t polls);
+/* Device-side bounds checks for later runs of this plan (on != 0; off by
+ * default).  Every work item of the input-NTT, split MAC and finishing
+ * kernels first checks that the memory it will read and write lies inside
+ * its call's buffers (inputs, NTT-domain inputs, bank, folded sums,
+ * outputs); an item that fails skips its work and sets a status that
+ * he_plan_check reports as HE_ERR_ARG.  The words of a run that passes are
+ * those of a run without checks.  (A debugging aid standing in for a
+ * memory checker; library-side, the paper has no counterpart.) */
+he_status he_plan_set_checks(he_plan_t plan, int on);
 void he_plan_destroy(he_plan_t plan);
 
 /* ------------------------------------------------------------------------
@@ -639,9 +651,10 @@ he_status he_server_create(const he_server_config *cfg, he_server_t *out);
  * params).  The banks must outlive the server.  *model_id is the handle.
  * HE_ERR_ARG if a layer's batch-1 lane (its input and output words and
  * its one-call plan's workspace) does not fit hbm_budget_bytes.  Blocking:
- * builds one lane (batch
- * buffers and plan) per layer and batch size (powers of two up to
- * max_batch) while the budget allows; the others are built on demand. */
+ * builds lanes (batch buffers and plan) while the budget allows -- per layer
+ * three of batch 1 (at most max_inflight) and one of every larger batch
+ * size (powers of two up to max_batch) -- so that serving rarely builds one
+ * on the request path; the others are built on demand. */
 he_status he_server_add_model(he_server_t s, const he_filters_t *layers, uint32_t nlayers,
                               uint32_t *model_id);
 /* Queues one inference.  h_in[i]: HOST uint32 input of layer i, the layout

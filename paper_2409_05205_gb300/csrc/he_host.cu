@@ -1327,7 +1327,8 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             cd.x_coeff = c.d_in;
             if (!cd.fc_direct) {
                 ws_off[i] = ws_words;
-                ws_words += (size_t)c.B * g.G * r.L * r.N;
+                cd.x_words = (size_t)c.B * g.G * r.L * r.N;
+                ws_words += cd.x_words;
             }
             ranges.push_back({(uintptr_t)c.d_share, (uintptr_t)(c.d_share + nsh), false, i});
             if (msrc == 1) ranges.push_back({(uintptr_t)c.d_share_out, (uintptr_t)(c.d_share_out + nshp), false, i});
@@ -1335,13 +1336,17 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             cd.x_coeff = c.d_in;
             if (!cd.fc_direct) {
                 ws_off[i] = ws_words;
+                cd.x_words = nin;
                 ws_words += nin;
             }
         } else {
             g.x = c.d_in;
+            cd.x_words = nin;
         }
         ranges.push_back({(uintptr_t)c.d_in, (uintptr_t)(c.d_in + nin), false, i});
         ranges.push_back({(uintptr_t)c.d_out, (uintptr_t)(c.d_out + nout), true, i});
+        cd.in_words = nin;
+        cd.out_words = nout;
         if (c.d_rescaled) {
             if (r.L < 2) return fail(HE_ERR_ARG, "call %u: d_rescaled needs at least 2 limbs", i);
             if (!aligned16(c.d_rescaled)) return fail(HE_ERR_ARG, "call %u: d_rescaled must be 16-byte aligned", i);
@@ -1361,7 +1366,8 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         if (descs[i].split || descs[i].zt) {
             const ConvGeo &g = descs[i].g;
             z_off[i] = ws_words;
-            ws_words += (size_t)(descs[i].split ? g.parts : 1u) * g.L * g.ncols * g.co * g.M;
+            descs[i].z_words = (size_t)(descs[i].split ? g.parts : 1u) * g.L * g.ncols * g.co * g.M;
+            ws_words += descs[i].z_words;
         }
     if (ws_only) {
         *ws_only = ws_words * sizeof(uint32_t);
@@ -1386,7 +1392,8 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         delete pl;
         return fail(HE_ERR_NOMEM, "plan");
     }
-    for (uint32_t i = 0; i < ncalls; ++i) pl->split[i] = descs[i].split ? 1 : (descs[i].zt ? 2 : 0);
+    for (uint32_t i = 0; i < ncalls; ++i)
+        pl->split[i] = descs[i].split ? 1 : (descs[i].zt ? 2 : (descs[i].fc_direct ? 3 : 0));
     pl->tuning = tu;
     pl->wait_polls = HE_WAIT_POLLS_DEFAULT;
     pl->ws_bytes = ws_words * sizeof(uint32_t);
@@ -1568,6 +1575,10 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             c.xstride = g.L * g.N;
             c.xrows = c.ncol * g.gp;
             c.xwords = 1u << lt;
+            c.w_lo = g.bank;
+            c.w_hi = g.bank + (size_t)g.co * g.L * g.G * g.N;
+            c.x_lo = g.x;
+            c.x_hi = g.x + cd.x_words;
             if (c.xrows * c.xwords > kMacXWords) {  // 2 columns x 8 groups: the larger input buffers
                 pl->mac_xw = kMacXWordsBig;
                 pl->mac_nst = kMacStagesBig;
@@ -1582,6 +1593,11 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             d.M = g.M;
             d.nch = nc;
             d.cls = (uint32_t)he_mac_class(g.gp, g.cs);
+            {   // every folded sum the item writes lies in its call's z region
+                const size_t last = (size_t)(c.ncol - 1u) * d.colstride + (size_t)(nc - 1u) * g.M +
+                                    (((1u << lt) - 1u) >> g.logs);
+                if (!in_range(d.z, last + 1u, cd.z, cd.z_words)) e = cudaErrorInvalidValue;
+            }
             d.logs = g.logs;
             d.nst = (c.nwords + kMacStageWords - 1) / kMacStageWords;
             const LimbK &K = cd.limb[it.l];
@@ -1644,6 +1660,12 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
 }
 }  // namespace
 
+he_status he_plan_set_checks(he_plan_t plan, int on) {
+    if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
+    plan->checks = on ? 1u : 0u;
+    return HE_OK;
+}
+
 he_status he_plan_set_wait_limit(he_plan_t plan, uint32_t polls) {
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
     plan->wait_polls = polls;
@@ -1660,6 +1682,9 @@ he_status he_plan_check(he_plan_t plan) {
     if (st) {
         const uint32_t zero = 0;
         cudaMemcpy(plan->d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        if (st & kStatusBounds)
+            return fail(HE_ERR_ARG, "a device-side bounds check failed: a work item addresses memory outside its "
+                                    "call's buffers (status 0x%x)", st);
         return fail(HE_ERR_TIMEOUT, "a bounded wait of a MAC kernel gave up (status 0x%x: bit 0 scalar, bit 1 tensor-core)",
                     st);
     }

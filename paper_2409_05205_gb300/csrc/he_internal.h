@@ -213,8 +213,20 @@ struct CallDesc {
     uint32_t fc_direct;       // FC: the output window computed directly from the coefficient-domain
                               // inputs and weights (fc_direct_body), no transforms
     const uint32_t *wc;       // FC: the bank's polynomials in the coefficient domain
+    // word counts of the call's buffers, for the device-side bounds checks
+    // (he_plan_set_checks): inputs at x_coeff, NTT-domain inputs at g.x,
+    // outputs at g.out, folded sums at z
+    size_t in_words, x_words, out_words, z_words;
     LimbK limb[HE_MAX_LIMBS];
 };
+// status bits of a plan run: 1, 2: a bounded wait of the split / tensor-core
+// MAC kernel gave up; 4: a device-side bounds check failed (checks mode)
+constexpr uint32_t kStatusBounds = 4u;
+// does [p, p + n) lie within [lo, lo + words)?
+__host__ __device__ __forceinline__ bool in_range(const void *p, size_t n, const void *lo, size_t words) {
+    const uintptr_t a = (uintptr_t)p, b = (uintptr_t)lo;
+    return a >= b && a + 4u * n <= b + 4u * words;
+}
 
 // split MAC kernel classes by (G, CS): (1,1) (1,2) (1,4) (2,1) (2,2) (4,1) (8,1)
 constexpr int kMacClasses = 7;
@@ -252,6 +264,8 @@ struct MacCopy {
     uint32_t xwords;         // words per input row (TS)
     uint32_t ncol;           // 2: columns c0, c1 of one ciphertext; 1: one column (masked and client steps)
     uint32_t pad;
+    // the call's bank and NTT-domain inputs, for the device-side bounds checks
+    const uint32_t *w_lo, *w_hi, *x_lo, *x_hi;
 };
 
 // What the compute warps need about one MAC item, built on the host and
@@ -351,6 +365,7 @@ struct he_plan_s {
     RsItem *d_rs_items;
     uint32_t *d_status;                 // bit 0 / bit 1: a bounded wait in the MAC / tensor-core MAC kernel gave up
     uint32_t wait_polls;                // polls of the split MAC kernel's waits before it gives up (he_plan_set_wait_limit)
+    uint32_t checks;                    // device-side bounds checks on (he_plan_set_checks)
     uint8_t *split;                     // host: per call, 1 if it takes the split form
     he_plan_tuning tuning;
 };

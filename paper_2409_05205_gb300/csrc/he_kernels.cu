@@ -1001,11 +1001,31 @@ __device__ __forceinline__ void plan_fwd_ntt(const uint32_t *src, uint32_t *dst,
 // have 512 .. 2048 groups, so more threads shorten every pass; two CTAs per SM
 // keep a plain-20 inference's 276 transforms resident at once.
 constexpr int kNttThreads = 512;
+// Checks mode: does item `it` touch only its call's buffers?  (The input it
+// reads, the NTT-domain image it writes; a direct FC item's output.)
+__device__ __forceinline__ bool ntt_item_in_bounds(const CallDesc &cd, const NttItem &it) {
+    const uint32_t N = cd.g.N;
+    if (it.src) return in_range(it.src, N, cd.x_coeff, cd.in_words) && in_range(it.dst, N, cd.g.x, cd.x_words);
+    if (cd.fc_direct) {
+        const uint32_t col = it.poly % cd.g.ncols, l = (it.poly / cd.g.ncols) % cd.g.L,
+                       jp = it.poly / (cd.g.ncols * cd.g.L);
+        const size_t o = cd.msrc ? (size_t)(col * cd.g.P + jp) * cd.g.L + l
+                                 : (size_t)(((col >> 1) * cd.g.P + jp) * 2u + (col & 1u)) * cd.g.L + l;
+        return jp < cd.g.P && in_range(cd.g.out + o * N, N, cd.g.out, cd.out_words);
+    }
+    return in_range(cd.g.x + (size_t)it.poly * N, N, cd.g.x, cd.x_words);
+}
+
 __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__restrict__ calls,
-                                                      const NttItem *__restrict__ items) {
+                                                      const NttItem *__restrict__ items,
+                                                      uint32_t *__restrict__ status, uint32_t checks) {
     extern __shared__ uint4 smem4[];
     pdl_trigger();  // the MAC kernel may start streaming weights now
     const NttItem it = items[blockIdx.x];
+    if (checks && !ntt_item_in_bounds(calls[it.call], it)) {
+        if (threadIdx.x == 0) atomicOr(status, kStatusBounds);
+        return;
+    }
     if (it.src) {  // an ordinary input transform
         if (it.logN == 13 && blockDim.x == 512)
             ntt_fwd_8192_warp(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.tw, it.q);
@@ -1230,7 +1250,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
                                                               const MacDesc *__restrict__ descs,
                                                               const uint32_t *__restrict__ offs,
                                                               uint32_t *__restrict__ status, uint32_t xw,
-                                                              uint32_t nring, uint32_t spin) {
+                                                              uint32_t nring, uint32_t spin, uint32_t checks) {
     extern __shared__ uint4 smem4[];
     uint64_t *xfull = reinterpret_cast<uint64_t *>(smem4);  // [2]
     uint64_t *xempty = xfull + 2;                            // [2]
@@ -1243,6 +1263,22 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
     const uint32_t ib = offs[blockIdx.x], ie = offs[blockIdx.x + 1];
     const uint32_t tid = threadIdx.x;
     if (ib >= ie) return;
+    if (checks) {
+        // every copy of the CTA's items reads inside its call's bank and
+        // NTT-domain inputs, and a stage holds at most kMacStageWords words
+        bool bad = false;
+        for (uint32_t k = ib + tid; k < ie; k += blockDim.x) {
+            const MacCopy c = copies[k];
+            bad |= !in_range(c.w, c.nwords, c.w_lo, (size_t)(c.w_hi - c.w_lo));
+            bad |= c.xrows * c.xwords > xw;
+            for (uint32_t r = 0; r < c.xrows; ++r)
+                bad |= !in_range(c.x + (size_t)r * c.xstride, c.xwords, c.x_lo, (size_t)(c.x_hi - c.x_lo));
+        }
+        if (__syncthreads_or(bad)) {
+            if (tid == 0) atomicOr(status, kStatusBounds);
+            return;
+        }
+    }
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
             mbar_init(xfull + i, 1);
@@ -1349,12 +1385,42 @@ __device__ __forceinline__ uint32_t he_log2_dev(uint32_t x) { return 31u - __clz
 // calls: the two-term product, the window, the bias and Delta_Q sh').
 constexpr int kFinThreads = 256;
 
+// Checks mode: does finishing item `it` read and write only its call's
+// folded sums (or NTT-domain FC inputs) and outputs?
+__device__ __forceinline__ bool fin_item_in_bounds(const CallDesc &cd, const ChanItem &it) {
+    const ConvGeo &g = cd.g;
+    const uint32_t N = g.N, L = g.L;
+    if (cd.kind == HE_KIND_FC) {
+        const uint32_t jp = it.a, l = it.l, c = it.b;
+        if (cd.msrc) {
+            const size_t x0 = ((size_t)(c * 2u) * L + l) * N, o = ((size_t)(c * g.P + jp) * L + l) * N;
+            return in_range(g.x + x0, (size_t)L * N + N, g.x, cd.x_words) && in_range(g.out + o, N, g.out, cd.out_words);
+        }
+        const size_t o = ((size_t)(((c >> 1) * g.P + jp) * 2u + (c & 1u)) * L + l) * N;
+        return in_range(g.x + ((size_t)c * L + l) * N, N, g.x, cd.x_words) && in_range(g.out + o, N, g.out, cd.out_words);
+    }
+    const uint32_t h = it.a, l = it.l, c = it.b, sh = min(g.s, g.co - h * g.s);
+    const size_t zs = (((size_t)l * g.ncols + c) * g.co + h * g.s) * g.M;
+    const size_t zlast = cd.zt ? 0 : zs + (size_t)(cd.g.parts - 1u) * L * g.ncols * g.co * g.M;
+    const bool zok = cd.zt ? in_range(cd.z, (size_t)L * g.ncols * g.M * g.co, cd.z, cd.z_words)
+                           : in_range(cd.z + zs, (size_t)sh * g.M, cd.z, cd.z_words) &&
+                                 in_range(cd.z + zlast, (size_t)sh * g.M, cd.z, cd.z_words);
+    const size_t o = g.masked ? ((size_t)(c * g.H + h) * L + l) * N
+                              : ((size_t)(((c >> 1) * g.H + h) * 2u + (c & 1u)) * L + l) * N;
+    return zok && in_range(g.out + o, N, g.out, cd.out_words);
+}
+
 __global__ void __launch_bounds__(kFinThreads, 3) k_plan_fin(const CallDesc *__restrict__ calls,
-                                                      const ChanItem *__restrict__ items) {
+                                                      const ChanItem *__restrict__ items,
+                                                      uint32_t *__restrict__ status, uint32_t checks) {
     extern __shared__ uint4 smem4[];
     const ChanItem it = items[blockIdx.x];
     const CallDesc &cd = calls[it.call];
     const LimbK K = cd.limb[it.l];
+    if (checks && !fin_item_in_bounds(cd, it)) {
+        if (threadIdx.x == 0) atomicOr(status, kStatusBounds);
+        return;
+    }
     if (cd.kind == HE_KIND_FC) {
         if (cd.msrc)
             fc_masked_body(cd.g, K, it.a, it.l, it.b, smem4);
@@ -1893,13 +1959,13 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         return cudaGetLastError();
     }
     if (phase == 5) {  // the finishing kernel alone
-        if (pl.n_fin) k_plan_fin<<<pl.n_fin, kFinThreads, pl.smem_fin, st>>>(pl.d_calls, pl.d_fin);
+        if (pl.n_fin) k_plan_fin<<<pl.n_fin, kFinThreads, pl.smem_fin, st>>>(pl.d_calls, pl.d_fin, pl.d_status, pl.checks);
         return cudaGetLastError();
     }
     if (pl.n_ntt && (phase == -1 || phase == 0)) {
         e = set_smem(k_plan_ntt, pl.smem_ntt);
         if (e != cudaSuccess) return e;
-        k_plan_ntt<<<pl.n_ntt, kNttThreads, pl.smem_ntt, st>>>(pl.d_calls, pl.d_ntt);
+        k_plan_ntt<<<pl.n_ntt, kNttThreads, pl.smem_ntt, st>>>(pl.d_calls, pl.d_ntt, pl.d_status, pl.checks);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -1907,7 +1973,7 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     if (pl.n_mac && phase != 3) {
         e = launch_pdl(k_plan_mac, pl.mac_ctas, kThreads + 32, pl.smem_mac, st, (const MacCopy *)pl.d_mac_copy,
                        (const MacDesc *)pl.d_mac_desc, (const uint32_t *)pl.d_mac_offs, pl.d_status, pl.mac_xw,
-                       pl.mac_nst, pl.wait_polls);
+                       pl.mac_nst, pl.wait_polls, pl.checks);
         if (e != cudaSuccess) return e;
     }
     if (pl.n_tc && phase != 3) {
@@ -1916,7 +1982,7 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     if (phase == 2) return cudaSuccess;
     if (pl.n_fin) {
         // an ordinary launch: started early, its blocks only wait (measured slower)
-        k_plan_fin<<<pl.n_fin, kFinThreads, pl.smem_fin, st>>>(pl.d_calls, pl.d_fin);
+        k_plan_fin<<<pl.n_fin, kFinThreads, pl.smem_fin, st>>>(pl.d_calls, pl.d_fin, pl.d_status, pl.checks);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if ((e = plan_chan_launch<2>(pl, 0, st)) != cudaSuccess) return e;

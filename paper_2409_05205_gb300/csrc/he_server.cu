@@ -386,12 +386,26 @@ he_status he_server_add_model(he_server_t s, const he_filters_t *layers, uint32_
     std::lock_guard<std::mutex> lk(s->mu);
     *model_id = (uint32_t)s->models.size();
     s->models.push_back(std::move(m));
-    // one lane (batch buffers and plan) per layer and batch size, built now
-    // while the budget allows, so that serving does not build them on the
-    // request path (a plan build allocates and copies synchronously)
-    for (uint32_t b = 1; b <= s->cfg.max_batch; b *= 2)
-        for (uint32_t i = 0; i < nlayers; ++i)
-            if (!get_lane(s, *model_id, i, b, false)) return HE_OK;  // budget reached: the rest on demand
+    // lanes (batch buffers and plan) built now while the budget allows, so
+    // that serving does not build them on the request path (a plan build
+    // allocates and copies synchronously, stalling every stream): per layer
+    // kLanesBatch1 of batch 1 -- requests of one model reach the same layer
+    // at nearly the same time -- and one of every larger batch size
+    constexpr uint32_t kLanesBatch1 = 3;
+    std::vector<Lane *> held;  // built lanes are marked busy so get_lane builds new ones
+    bool room = true;
+    for (uint32_t b = 1; room && b <= s->cfg.max_batch; b *= 2)
+        for (uint32_t i = 0; room && i < nlayers; ++i)
+            for (uint32_t k = 0; room && k < (b == 1 ? std::min(kLanesBatch1, s->cfg.max_inflight) : 1u); ++k) {
+                Lane *l = get_lane(s, *model_id, i, b, false);
+                if (!l) {
+                    room = false;  // budget reached: the rest on demand
+                    break;
+                }
+                l->busy = true;
+                held.push_back(l);
+            }
+    for (Lane *l : held) l->busy = false;
     return HE_OK;
 }
 

@@ -126,6 +126,7 @@ _SIGS = {
     "he_plan_create_tuned": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(he_plan_tuning), ctypes.POINTER(_vp)],
     "he_plan_workspace_bytes": [ctypes.POINTER(he_layer_call), _u32, ctypes.POINTER(_sz)],
     "he_plan_set_wait_limit": [_vp, _u32],
+    "he_plan_set_checks": [_vp, _i32],
     "he_plan_autotune": [ctypes.POINTER(he_layer_call), _u32, _u32, _vp, ctypes.POINTER(he_plan_tuning),
                          ctypes.POINTER(_vp)],
     "he_plan_run": [_vp, _vp],
@@ -466,6 +467,10 @@ HE_WAIT_POLLS_DEFAULT = 1 << 20
 
 def he_plan_set_wait_limit(plan: int, polls: int) -> None:
     _check(lib().he_plan_set_wait_limit(plan, polls))
+
+
+def he_plan_set_checks(plan: int, on: bool) -> None:
+    _check(lib().he_plan_set_checks(plan, 1 if on else 0))
 
 
 def he_plan_autotune(calls, iters: int = 5, stream=None) -> tuple[int, dict]:

@@ -5,6 +5,11 @@
   every CTA gives up at once.  The kernel lets its own copies land, returns,
   and he_plan_check reports HE_ERR_TIMEOUT; with the default limit restored
   the same plan runs again on the same context and gives the oracle's words.
+* Device-side bounds checks (he_plan_set_checks): every work item of a plan
+  with Conv calls in the split form (one and several group parts), a direct
+  and a transform-path FC call, and masked and client calls checks its
+  memory ranges first; the run reports no violation and gives the words of
+  the run without checks.
 * The 64-bit accumulators at their worst case: a client bank whose words are
   all q - 1 (p = -N X^{off_n}: the bank stores NTT(p) X_k^{-off_n} / N) and
   inputs whose transforms are all q - 1 (-v = i + sh = -1 at coefficient 0),
@@ -95,3 +100,41 @@ def test_accumulators_at_their_worst_case_client_bank_of_q_minus_1():
             np.testing.assert_array_equal(U.from_dev(d_plan).reshape(Hh, L, N), want)
         finally:
             H.he_filters_destroy(f)
+
+
+def test_bounds_checked_plan_reports_nothing_and_gives_the_same_words():
+    import test_gpu_masked_plan as MP
+    H = U.he()
+    torch = U.torch_cuda()
+    st = torch.cuda.current_stream()
+    N, L = 8192, 3
+    ps, psis = U.ring(N, L)
+    with U.params(N, L) as p:
+        cases = MP._mixed(H, p, N, ps, psis)
+        ci, co, hw = 48, 48, 32  # G = 12: three group parts
+        _, _, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, 1, seed=43)
+        fb = H.he_pack_filters(p, desc, F)
+        d_in, d_out = U.to_dev(cts), U.empty_dev((1, lay["H"], 2, L, N))
+        calls = [c.call() for c in cases] + [(fb, d_in, H.HE_COEFF, d_out, 1)]
+        outs = [c.d_out for c in cases] + [d_out]
+        try:
+            got = []
+            for checks, fc_direct in ((False, 1), (True, 1), (True, 0)):
+                plan = H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), fc_direct=fc_direct))
+                try:
+                    H.he_plan_set_checks(plan, checks)
+                    for o in outs:
+                        o.fill_(-1)
+                    H.he_plan_run(plan, st)
+                    H.he_sync(st)
+                    H.he_plan_check(plan)
+                    got.append([U.from_dev(o) for o in outs])
+                finally:
+                    H.he_plan_destroy(plan)
+            for run in got[1:]:
+                for a, b in zip(got[0], run):
+                    np.testing.assert_array_equal(a, b)
+        finally:
+            for c in cases:
+                H.he_filters_destroy(c.f)
+            H.he_filters_destroy(fb)
