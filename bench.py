@@ -264,8 +264,12 @@ class Arm:
         for r in range(self.R):
             calls = [(self.models[r].banks[i], self.x[r][i], H.HE_COEFF, self.y[r][i], c["B"])
                      for i, c in enumerate(self.calls)]
-            # autotuned once (replicas share the signature, so 1 and 2 reuse it)
-            pl, self.tuning = H.he_plan_autotune(calls, 30, s)
+            if NO_AUTOTUNE:
+                self.tuning = H.he_plan_tuning_default()
+                pl = H.he_plan_create_tuned(calls, self.tuning)
+            else:
+                # autotuned once (replicas share the signature, so 1 and 2 reuse it)
+                pl, self.tuning = H.he_plan_autotune(calls, 30, s)
             self.plans.append(pl)
         torch.cuda.synchronize()
         for r in range(self.R):
@@ -1379,6 +1383,8 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
     elapsed_s = (t_last - t0 * 1e3) * 1e-3
     rep = H.he_server_report(srv)
     lat_layer = H.he_server_latencies(srv, 1)[lat_layer0:]
+    lat_wait = H.he_server_latencies(srv, 2)[lat_layer0:]
+    lat_run = H.he_server_latencies(srv, 3)[lat_layer0:]
     H.he_server_destroy(srv)
     n = len(lat_sched)
     pct = lambda v, q: float(np.percentile(v, q)) if len(v) else None
@@ -1390,7 +1396,10 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
               "network_latency_ms_by_model": {m["name"]: {"p50": pct(v, 50), "p99": pct(v, 99)}
                                               for m, v in zip(models, per_model)},
               "layer_latency_ms": {"p50": pct(lat_layer, 50), "p99": pct(lat_layer, 99),
-                                   "from": "entry into the layer's queue to its outputs on the host"},
+                                   "from": "entry into the layer's queue to its outputs on the host",
+                                   "queue_wait": {"p50": pct(lat_wait, 50), "p99": pct(lat_wait, 99)},
+                                   "run": {"p50": pct(lat_run, 50), "p99": pct(lat_run, 99),
+                                           "what": "batch launch to outputs on the host"}},
               "batches": nb, "mean_batch": ncalls / max(1, nb), "hbm_bytes_peak": rep["bytes_peak"],
               "batch_hist": {k: v - warm["batch_hist"][k] for k, v in rep["batch_hist"].items()},
               "lanes_built_timed": rep["lanes"] + rep["evictions"] - warm["lanes"] - warm["evictions"],
@@ -1402,6 +1411,12 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
               "server": {"max_batch": max_batch, "streams": streams, "max_inflight": max_inflight}}
     return {"n": n, "elapsed_s": elapsed_s, "value": layers_done / elapsed_s, "report": report, "clocks": clk,
             "warm_requests": 2 * 15 * len(models) + nw}
+
+
+# the plans take the default tuning instead of the autotuner's choice
+# (--no-autotune: under a profiler every launch is slower, which skews the
+# autotuner's timings)
+NO_AUTOTUNE = False
 
 
 # ----------------------------------------------------------------------------
@@ -1471,7 +1486,11 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched, wide and serving configurations after the plain-20 headline")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="plans take the default tuning (for profiling runs, whose timings skew the autotuner)")
     args = ap.parse_args()
+    global NO_AUTOTUNE
+    NO_AUTOTUNE = args.no_autotune
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

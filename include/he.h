@@ -668,7 +668,9 @@ he_status he_server_wait(he_server_t s, uint64_t ticket, uint32_t timeout_ms, he
 he_status he_server_report(he_server_t s, he_server_report_t *rep);
 /* Recorded latencies in ms: which = 0 per inference (arrival to the last
  * layer's outputs on the host), 1 per layer call (entry into the layer's
- * queue to its outputs on the host).  Copies min(n, cap) values. */
+ * queue to its outputs on the host), and the two parts of a layer call's:
+ * 2 its wait in the queue (entry to its batch's launch), 3 its run (launch
+ * to its outputs on the host).  Copies min(n, cap) values. */
 he_status he_server_latencies(he_server_t s, int which, double *out_ms, uint64_t cap, uint64_t *n);
 /* Stops the scheduler (queued requests that have not started are dropped;
  * running batches finish), frees the server's buffers.  Blocking. */

@@ -54,6 +54,7 @@ struct Req {
     std::vector<const uint32_t *> in;
     std::vector<uint32_t *> out;
     double t_arrive, t_layer;  // arrival; entry into the current layer's queue
+    double t_launch = 0.0;     // the current layer's batch launch
     bool done = false, failed = false;
     double t_done = 0.0;
 };
@@ -93,7 +94,7 @@ struct Server {
     uint64_t next_id = 1, submitted = 0, finished = 0, batches = 0, batched_calls = 0, failed = 0;
     uint64_t evictions = 0, batch_hist[4] = {0, 0, 0, 0};
     uint32_t inflight = 0;
-    std::vector<double> lat_layer, lat_net;
+    std::vector<double> lat_layer, lat_net, lat_wait, lat_run;
     bool stop = false;
     char error[256] = {0};
     std::thread sched;
@@ -229,6 +230,8 @@ bool launch(Server *s, Lane *lane, std::vector<Req *> &rs) {
         snprintf(s->error, sizeof(s->error), "batch launch failed");
         return false;
     }
+    const double t = now_ms();
+    for (Req *r : rs) r->t_launch = t;
     lane->busy = true;
     ++s->inflight;
     ++s->batches;
@@ -253,6 +256,8 @@ void finish_batch(Server *s, Batch *b) {
             continue;
         }
         s->lat_layer.push_back(t - r->t_layer);
+        s->lat_wait.push_back(r->t_launch - r->t_layer);
+        s->lat_run.push_back(t - r->t_launch);
         if (++r->layer == s->models[r->model].layers.size()) {
             r->done = true;
             r->t_done = t;
@@ -471,9 +476,10 @@ he_status he_server_report(he_server_t s, he_server_report_t *rep) {
 }
 
 he_status he_server_latencies(he_server_t s, int which, double *out_ms, uint64_t cap, uint64_t *n) {
-    if (!s || !n || (which != 0 && which != 1)) return he_fail(HE_ERR_ARG, "bad argument");
+    if (!s || !n || which < 0 || which > 3) return he_fail(HE_ERR_ARG, "bad argument");
     std::lock_guard<std::mutex> lk(s->mu);
-    const std::vector<double> &v = which == 0 ? s->lat_net : s->lat_layer;
+    const std::vector<double> &v =
+        which == 0 ? s->lat_net : (which == 1 ? s->lat_layer : (which == 2 ? s->lat_wait : s->lat_run));
     *n = v.size();
     if (out_ms)
         for (size_t i = 0; i < v.size() && i < cap; ++i) out_ms[i] = v[i];
