@@ -363,8 +363,8 @@ class Arm:
 # DRAM bytes (read + write) of one k_plan_mac launch, from an ncu capture of
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where no
 # capture of the current kernel exists.
-TRAFFIC = {"plain20_c10": 141.38e6,          # ncu --set full of one launch: read 136.62 MB + write 4.77 MB
-           "plain20_c10_masked": 269.45e6}   # read 264.17 MB + write 5.28 MB
+TRAFFIC = {"plain20_c10": 140.93e6,          # ncu --set full of one launch: read 136.63 MB + write 4.30 MB
+           "f3_d20_w3": 1250.86e6}           # read 1168.25 MB + write 82.60 MB
 
 
 def _traffic(name):
@@ -941,6 +941,7 @@ def run_masked(args, rank, world, device):
     # plans: server and client steps, each one graph replay per step
     arm.make_plans()
     info = H.he_plan_query(arm.srv_plans[0], nl)
+    rs_info = H.he_plan_query(arm.rs_plans[0], nl)
     g_srv, g_cli, g_rs = arm.capture(arm.server_plan), arm.capture(arm.client_plan), arm.capture(arm.rescale)
     g_srs = arm.capture(arm.server_rescale_plan)
     barrier()
@@ -1027,12 +1028,18 @@ def run_masked(args, rank, world, device):
                         "what": "c1^r = extract(sum -v p1 + (i + sh) p2) of every layer: one plan of the "
                                 "client calls, a CUDA graph per step"},
         "rescale": {"server_step_with_rescale_ms": srs_ms / k2,
+                    "in_finishing_kernel": {"calls": rs_info["rescale_fused_calls"], "of": nl,
+                                            "rescale_kernel_items_left": rs_info["rescale_items"],
+                                            "what": "calls whose outputs k_plan_fin writes are rescaled in its "
+                                                    "epilogue (the last limb item of each output polynomial); "
+                                                    "the rest by k_plan_rescale after the channel kernels"},
                     "k_plan_rescale": {"avg_launch_ms": prs_ms, "bytes": rs_bytes,
                                        "achieved_gbs": rs_bytes / (prs_ms * 1e-3) / 1e9,
                                        "frac": rs_bytes / (prs_ms * 1e-3) / 1e9 / hbm, "launches": k2,
                                        "what": f"every c0^r of the step from {arm.calls[0]['L']} to "
-                                               f"{arm.calls[0]['L'] - 1} limbs in one launch (L limbs read, "
-                                               "L - 1 written), back to back over the replicas"},
+                                               f"{arm.calls[0]['L'] - 1} limbs in one launch of the standalone "
+                                               "kernel (HE_PHASE_RESCALE; L limbs read, L - 1 written), back to "
+                                               "back over the replicas"},
                     "single_calls": {"ms_per_step": rs_ms / k2, "achieved_gbs": rs_gbs, "frac": rs_gbs / hbm,
                                      "what": f"he_rescale per layer output ({nl} launches per step, a CUDA graph)"}},
         "roofline": {"kernel": "k_plan_mac: one-column masked channel MAC of every Conv layer (masked banks "

@@ -426,20 +426,25 @@ he_status he_ntt_inverse(he_params_t p, const uint32_t *d_in, uint32_t *d_out,
  * he_conv_client / he_fc_client.  he_plan_run issues, in order on `stream`:
  *   1. one kernel computing every coefficient-domain input NTT of every
  *      Conv and FC call (for masked and client calls: of both input
- *      sources);
- *   2. for the Conv calls in the split form (B = 1, interleave s >= 4, G in
- *      {1, 2, 4}, or 2G in {2, 4, 8} for masked and client banks): a
- *      persistent kernel that streams each slot tile's
- *      weights for every output channel into shared memory with bulk copies
- *      and stores the folded channel sums (Sec. III-A, valid slots only) in
- *      the plan's workspace, then a kernel that runs the length-N/s inverse
- *      transforms and writes each extracted output polynomial; the same
- *      kernel runs every FC call's product with its weight blocks, inverse
- *      transform, window and bias;
+ *      sources), and the output window of every FC call computed directly
+ *      from coefficient-domain inputs (fc_direct);
+ *   2. for the Conv calls in the split form (B = 1, interleave s >= 4; the
+ *      G groups, 2G for masked and client banks, taken in parts of up to
+ *      8): a persistent kernel that streams each slot tile's weights for
+ *      every output channel into shared memory with bulk copies and stores
+ *      the folded channel sums (Sec. III-A, valid slots only) in the plan's
+ *      workspace (tensor-core banks at batch >= tc_min_batch: the
+ *      tensor-core MAC kernel instead), then a finishing kernel that runs
+ *      the length-N/s inverse transforms and writes each extracted output
+ *      polynomial; the same kernel runs every other FC call's product with
+ *      its weight blocks, inverse transform, window and bias.  For the
+ *      calls with d_rescaled whose outputs it writes, the last of an output
+ *      polynomial's L limb items to finish rescales that polynomial (the
+ *      RNS rescale of he_rescale) while its words are still in L2;
  *   3. for the other Conv calls: one fused kernel per column-tile class
  *      (MAC, folded inverse transform and extraction per output channel);
- *   4. for the calls with d_rescaled: one kernel rescaling all their
- *      outputs (the RNS rescale of he_rescale).
+ *   4. for the other calls with d_rescaled: one kernel rescaling their
+ *      outputs.
  * Work items are ordered longest first.  The plan owns its workspace and
  * descriptor tables, so he_plan_run allocates nothing and can be captured
  * into a CUDA graph.  Runs of one plan must not overlap on the GPU;
@@ -529,8 +534,11 @@ he_status he_plan_run(he_plan_t plan, void *stream);
  *   HE_PHASE_REST (1)  everything after it (steps 2-4);
  *   HE_PHASE_MAC (2)   the split-form MAC kernel alone (first half of 2);
  *   HE_PHASE_FINISH (3) everything after the MAC kernel (rest of 2, 3, 4, 5);
- *   HE_PHASE_RESCALE (4) the rescale kernel alone (step 5; it reads the
- *                      outputs of the phases before it);
+ *   HE_PHASE_RESCALE (4) the rescale kernel alone, over every call with
+ *                      d_rescaled (it reads the outputs of the phases
+ *                      before it; in a full run the calls whose outputs
+ *                      the finishing kernel writes are rescaled by that
+ *                      kernel instead);
  *   HE_PHASE_FIN (5)   the split form's finishing kernel alone (second half
  *                      of step 2; it reads the MAC kernel's folded sums).
  * A full run is phases 0, 1 or phases 0, 2, 3, in that order on one stream
@@ -558,7 +566,9 @@ typedef struct {
     uint32_t tc_items;        /* tensor-core MAC items (call x limb x run of slot blocks) */
     uint32_t tc_ctas;         /* persistent CTAs of the tensor-core MAC kernel */
     uint32_t tc_calls;        /* Conv calls on the tensor-core MAC kernel */
-    uint32_t rescale_items;   /* items of the rescale kernel (0: no call has d_rescaled) */
+    uint32_t rescale_items;   /* items of the rescale kernel a full run launches (0: none; calls
+                                 whose outputs the finishing kernel writes are rescaled there) */
+    uint32_t rescale_fused_calls; /* calls with d_rescaled rescaled in the finishing kernel's epilogue */
 } he_plan_info;
 /* Fills *info; if `split` is not NULL, also split[i] for each call i (of
  * the ncalls given to he_plan_create): 1 if it takes the split form with the

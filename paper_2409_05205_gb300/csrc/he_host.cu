@@ -1202,7 +1202,13 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
     std::vector<CallDesc> descs(ncalls);
     std::vector<size_t> ws_off(ncalls, 0), z_off(ncalls, 0);
     std::vector<RescaleCall> rs_calls;
-    std::vector<RsItem> rs_items;
+    // rescale items: calls the finishing kernel does not write go first (the
+    // full run's k_plan_rescale), the fused calls' after them (for
+    // HE_PHASE_RESCALE, which rescales every call in that kernel alone)
+    std::vector<RsItem> rs_items, rs_items_fused;
+    std::vector<int32_t> rs_idx(ncalls, -1);
+    std::vector<size_t> rs_cnt_off(ncalls, 0);
+    size_t rs_cnt_words = 0;
     size_t ws_words = 0;
     for (uint32_t i = 0; i < ncalls; ++i) {
         const he_layer_call &c = calls[i];
@@ -1356,9 +1362,18 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             rc.a = he_rescale_args(r);
             rc.in = c.d_out;
             rc.out = c.d_rescaled;
+            // outputs written by the finishing kernel are rescaled in its
+            // epilogue, by the last of each polynomial's limb items
+            const bool fused = f->kind == HE_KIND_CONV ? (cd.split || cd.zt) : !cd.fc_direct;
+            std::vector<RsItem> &dst = fused ? rs_items_fused : rs_items;
             const size_t total = npoly * (r.N >> 2);
             for (size_t b = 0; b < total; b += kRsItemU4)
-                rs_items.push_back({(uint32_t)rs_calls.size(), (uint32_t)b, (uint32_t)std::min(total, b + kRsItemU4), 0u});
+                dst.push_back({(uint32_t)rs_calls.size(), (uint32_t)b, (uint32_t)std::min(total, b + kRsItemU4), 0u});
+            if (fused) {
+                rs_idx[i] = (int32_t)rs_calls.size();
+                rs_cnt_off[i] = rs_cnt_words;
+                rs_cnt_words += npoly;
+            }
             rs_calls.push_back(rc);
         }
     }
@@ -1509,7 +1524,29 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         if (err == cudaSuccess) err = cudaMemcpy(*dst, v.data(), sizeof(ChanItem) * v.size(), cudaMemcpyHostToDevice);
         return err;
     };
-    e = cudaMalloc(&pl->d_calls, sizeof(CallDesc) * ncalls);
+    pl->n_rs_run = (uint32_t)rs_items.size();
+    rs_items.insert(rs_items.end(), rs_items_fused.begin(), rs_items_fused.end());
+    if (!rs_items.empty()) {
+        e = cudaMalloc(&pl->d_rs_calls, sizeof(RescaleCall) * rs_calls.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(pl->d_rs_calls, rs_calls.data(), sizeof(RescaleCall) * rs_calls.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMalloc(&pl->d_rs_items, sizeof(RsItem) * rs_items.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(pl->d_rs_items, rs_items.data(), sizeof(RsItem) * rs_items.size(), cudaMemcpyHostToDevice);
+        pl->n_rs = (uint32_t)rs_items.size();
+    }
+    if (e == cudaSuccess && rs_cnt_words) {
+        e = cudaMalloc(&pl->d_rs_cnt, sizeof(uint32_t) * rs_cnt_words);
+        if (e == cudaSuccess) e = cudaMemset(pl->d_rs_cnt, 0, sizeof(uint32_t) * rs_cnt_words);
+        pl->rs_cnt_words = rs_cnt_words;
+    }
+    for (uint32_t i = 0; i < ncalls && e == cudaSuccess; ++i)
+        if (rs_idx[i] >= 0) {
+            descs[i].rs = pl->d_rs_calls + rs_idx[i];
+            descs[i].rs_cnt = pl->d_rs_cnt + rs_cnt_off[i];
+            ++pl->n_rs_fused;
+        }
+    if (e == cudaSuccess) e = cudaMalloc(&pl->d_calls, sizeof(CallDesc) * ncalls);
     if (e == cudaSuccess) e = cudaMemcpy(pl->d_calls, descs.data(), sizeof(CallDesc) * ncalls, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !ntt.empty()) {
         e = cudaMalloc(&pl->d_ntt, sizeof(NttItem) * ntt.size());
@@ -1627,15 +1664,6 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         }
     }
     if (e == cudaSuccess && !tc_calls.empty()) e = build_tc_tables(pl, descs, calls, tc_calls);
-    if (e == cudaSuccess && !rs_items.empty()) {
-        e = cudaMalloc(&pl->d_rs_calls, sizeof(RescaleCall) * rs_calls.size());
-        if (e == cudaSuccess)
-            e = cudaMemcpy(pl->d_rs_calls, rs_calls.data(), sizeof(RescaleCall) * rs_calls.size(), cudaMemcpyHostToDevice);
-        if (e == cudaSuccess) e = cudaMalloc(&pl->d_rs_items, sizeof(RsItem) * rs_items.size());
-        if (e == cudaSuccess)
-            e = cudaMemcpy(pl->d_rs_items, rs_items.data(), sizeof(RsItem) * rs_items.size(), cudaMemcpyHostToDevice);
-        pl->n_rs = (uint32_t)rs_items.size();
-    }
     if (e == cudaSuccess) {
         std::stable_sort(fin.begin(), fin.end(), by_cost);
         std::vector<ChanItem> items;
@@ -1682,6 +1710,8 @@ he_status he_plan_check(he_plan_t plan) {
     if (st) {
         const uint32_t zero = 0;
         cudaMemcpy(plan->d_status, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        // items that stopped early left the fused rescale's counters part-way
+        if (plan->d_rs_cnt) cudaMemset(plan->d_rs_cnt, 0, sizeof(uint32_t) * plan->rs_cnt_words);
         if (st & kStatusBounds)
             return fail(HE_ERR_ARG, "a device-side bounds check failed: a work item addresses memory outside its "
                                     "call's buffers (status 0x%x)", st);
@@ -1720,8 +1750,9 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
     for (int c = 0; c < kChanClasses; ++c) r.fused_items += plan->n_chan[c];
     r.fc_items = plan->n_fc;
     r.kernels_per_run = (plan->n_ntt > 0) + (plan->n_mac > 0) + (plan->n_fin > 0) + (plan->n_tc > 0) +
-                        (plan->n_rs > 0);
-    r.rescale_items = plan->n_rs;
+                        (plan->n_rs_run > 0);
+    r.rescale_items = plan->n_rs_run;
+    r.rescale_fused_calls = plan->n_rs_fused;
     r.tc_items = plan->n_tc;
     r.tc_ctas = plan->n_tc ? plan->tc_ctas : 0;
     for (uint32_t i = 0; i < plan->ncalls; ++i) r.tc_calls += plan->split[i] == 2;
@@ -1753,6 +1784,7 @@ void he_plan_destroy(he_plan_t plan) {
     cudaFree(plan->d_status);
     cudaFree(plan->d_rs_calls);
     cudaFree(plan->d_rs_items);
+    cudaFree(plan->d_rs_cnt);
     delete[] plan->split;
     delete plan;
 }

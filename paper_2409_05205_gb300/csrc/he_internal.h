@@ -198,6 +198,7 @@ struct TcItem {
 };
 
 // One layer call inside a plan (device-resident table).
+struct RescaleCall;
 struct CallDesc {
     ConvGeo g;
     const uint32_t *x_coeff;  // coefficient-domain input (nullptr when the call's input is in NTT form);
@@ -213,6 +214,11 @@ struct CallDesc {
     uint32_t fc_direct;       // FC: the output window computed directly from the coefficient-domain
                               // inputs and weights (fc_direct_body), no transforms
     const uint32_t *wc;       // FC: the bank's polynomials in the coefficient domain
+    // the rescale of the call's outputs done by the finishing kernel (calls
+    // with d_rescaled whose outputs that kernel writes; else nullptr): the
+    // last of an output polynomial's L limb items to finish rescales it
+    const RescaleCall *rs;
+    uint32_t *rs_cnt;         // per output polynomial: limb items finished in this run
     // word counts of the call's buffers, for the device-side bounds checks
     // (he_plan_set_checks): inputs at x_coeff, NTT-domain inputs at g.x,
     // outputs at g.out, folded sums at z
@@ -360,9 +366,14 @@ struct he_plan_s {
     TcCall *d_tc_calls;
     TcItem *d_tc_items;
     uint32_t *d_tc_offs;                // items of CTA b at [offs[b], offs[b+1])
-    uint32_t n_rs;                      // rescale items (calls with d_rescaled)
+    uint32_t n_rs;                      // rescale items of every call with d_rescaled (HE_PHASE_RESCALE)
+    uint32_t n_rs_run;                  // the first n_rs_run of them: calls whose outputs the finishing
+                                        // kernel does not write, rescaled by k_plan_rescale in a full run
+    uint32_t n_rs_fused;                // calls rescaled in the finishing kernel's epilogue
     RescaleCall *d_rs_calls;
     RsItem *d_rs_items;
+    uint32_t *d_rs_cnt;                 // the fused calls' per-polynomial counters (CallDesc::rs_cnt)
+    size_t rs_cnt_words;
     uint32_t *d_status;                 // bit 0 / bit 1: a bounded wait in the MAC / tensor-core MAC kernel gave up
     uint32_t wait_polls;                // polls of the split MAC kernel's waits before it gives up (he_plan_set_wait_limit)
     uint32_t checks;                    // device-side bounds checks on (he_plan_set_checks)

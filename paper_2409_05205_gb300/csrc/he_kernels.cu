@@ -23,12 +23,13 @@
 //  k_plan_mac /   a plan's split form: a persistent bulk-copy-fed channel MAC
 //  k_plan_fin     (two columns, or one for the masked and client steps), then
 //                 the valid-slot inverse transforms and the extraction; the
-//                 finishing kernel also runs every FC item of the plan (its
-//                 inputs transformed by k_plan_ntt).
+//                 finishing kernel also runs the FC items of the plan (their
+//                 inputs transformed by k_plan_ntt) and rescales the outputs
+//                 it writes when the call asks for it.
 //  k_ntt_masked_in, k_client_in, k_fc_masked, k_pack_fc_masked
 //                 the masked server and client steps of Alg. 1 / Alg. 2.
 //  k_rescale /    the RNS rescale by the last prime, for one buffer or for
-//  k_plan_rescale every output of a plan.
+//  k_plan_rescale the outputs of a plan the finishing kernel does not write.
 //  k_bfly_peak    the butterfly-rate measurement behind the ALU roofline.
 // The tensor-core channel MAC is in he_tc.cu.
 #include <algorithm>
@@ -483,7 +484,14 @@ __global__ void __launch_bounds__(kThreads) k_client_in(const RingView r, const 
 }
 
 // The rescale of uint4 group i (4 coefficients) of polynomial i / (N/4):
-// reads its L limbs, writes L - 1.
+// reads its L limbs, writes L - 1.  kL2: the limbs were written by other
+// CTAs of the running kernel, so they are read through L2 (ld.global.cg),
+// else streamed (ld.global.cs).
+template <bool kL2 = false>
+__device__ __forceinline__ uint4 rs_load(const uint4 *p) {
+    return kL2 ? __ldcg(p) : __ldcs(p);
+}
+template <bool kL2 = false>
 __device__ __forceinline__ void rescale_u4(const RescaleArgs &a, const uint32_t *__restrict__ in,
                                            uint32_t *__restrict__ out, size_t i) {
     const uint32_t nq = a.N >> 2;
@@ -491,13 +499,13 @@ __device__ __forceinline__ void rescale_u4(const RescaleArgs &a, const uint32_t 
     const uint32_t k4 = (uint32_t)(i % nq);
     const uint32_t *src = in + pi * a.L * a.N;
     uint32_t *dst = out + pi * (a.L - 1u) * a.N;
-    const uint4 xl = __ldcs(reinterpret_cast<const uint4 *>(src + (size_t)(a.L - 1u) * a.N) + k4);
+    const uint4 xl = rs_load<kL2>(reinterpret_cast<const uint4 *>(src + (size_t)(a.L - 1u) * a.N) + k4);
     uint32_t y[4] = {xl.x + a.hL, xl.y + a.hL, xl.z + a.hL, xl.w + a.hL};
 #pragma unroll
     for (int u = 0; u < 4; ++u) y[u] = min(y[u], y[u] - a.qL);  // (x_L + h) mod q_L
     for (uint32_t l = 0; l + 1u < a.L; ++l) {
         const RescaleLimb &R = a.limb[l];
-        const uint4 x = __ldcs(reinterpret_cast<const uint4 *>(src + (size_t)l * a.N) + k4);
+        const uint4 x = rs_load<kL2>(reinterpret_cast<const uint4 *>(src + (size_t)l * a.N) + k4);
         const uint32_t xv[4] = {x.x, x.y, x.z, x.w};
         uint32_t r[4];
 #pragma unroll
@@ -1410,24 +1418,40 @@ __device__ __forceinline__ bool fin_item_in_bounds(const CallDesc &cd, const Cha
     return zok && in_range(g.out + o, N, g.out, cd.out_words);
 }
 
-__global__ void __launch_bounds__(kFinThreads, 3) k_plan_fin(const CallDesc *__restrict__ calls,
-                                                      const ChanItem *__restrict__ items,
-                                                      uint32_t *__restrict__ status, uint32_t checks) {
-    extern __shared__ uint4 smem4[];
-    const ChanItem it = items[blockIdx.x];
-    const CallDesc &cd = calls[it.call];
-    const LimbK K = cd.limb[it.l];
-    if (checks && !fin_item_in_bounds(cd, it)) {
-        if (threadIdx.x == 0) atomicOr(status, kStatusBounds);
-        return;
+// The rescale fused into the finishing kernel: once a CTA has written limb
+// l of output polynomial `poly`, it counts itself in; the last of the
+// polynomial's L limb items rescales the whole polynomial (all L limbs are
+// then written and, just written, still in L2) and resets the counter for
+// the next run.  No CTA waits on another.
+__device__ __forceinline__ void fin_rescale(const CallDesc &cd, size_t poly) {
+    __shared__ uint32_t last;
+    __threadfence();  // this CTA's output words, visible before it counts in
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t prior = atomicAdd(cd.rs_cnt + poly, 1u);
+        last = prior + 1u == cd.g.L ? 1u : 0u;
+        if (last) cd.rs_cnt[poly] = 0u;
     }
-    if (cd.kind == HE_KIND_FC) {
-        if (cd.msrc)
-            fc_masked_body(cd.g, K, it.a, it.l, it.b, smem4);
-        else
-            fc_body(cd.g, K, it.a, it.l, it.b, smem4);
-        return;
-    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const RescaleCall &rc = *cd.rs;
+    const size_t nq = rc.a.N >> 2, i0 = poly * nq;
+    for (uint32_t k = threadIdx.x; k < nq; k += blockDim.x) rescale_u4<true>(rc.a, rc.in, rc.out, i0 + k);
+}
+
+// index of the output polynomial finishing item (h or block jp, column c)
+// writes: [B][H][L][N] masked and client, else [B][H][2][L][N] (P for FC)
+__device__ __forceinline__ size_t fin_out_poly(const CallDesc &cd, uint32_t a, uint32_t c) {
+    const uint32_t H = cd.kind == HE_KIND_FC ? cd.g.P : cd.g.H;
+    return cd.g.masked ? (size_t)c * H + a : ((size_t)(c >> 1) * H + a) * 2u + (c & 1u);
+}
+
+// Conv finishing item (call, h, l, column): the parts' folded sums of the
+// s channels of output polynomial h, their length-M inverse transforms,
+// and the extracted polynomial's limb l.
+__device__ __forceinline__ void fin_conv_body(const CallDesc &cd, const LimbK &K, const ChanItem &it,
+                                              uint4 *smem4) {
     uint32_t *Zs = reinterpret_cast<uint32_t *>(smem4);
     const uint32_t h = it.a, l = it.l, c = it.b;
     const uint32_t N = cd.g.N, co = cd.g.co, s = cd.g.s, logs = cd.g.logs, M = cd.g.M, logM = cd.g.logM,
@@ -1520,6 +1544,28 @@ __global__ void __launch_bounds__(kFinThreads, 3) k_plan_fin(const CallDesc *__r
             o[k] = v;
         }
     }
+}
+
+__global__ void __launch_bounds__(kFinThreads, 3) k_plan_fin(const CallDesc *__restrict__ calls,
+                                                      const ChanItem *__restrict__ items,
+                                                      uint32_t *__restrict__ status, uint32_t checks) {
+    extern __shared__ uint4 smem4[];
+    const ChanItem it = items[blockIdx.x];
+    const CallDesc &cd = calls[it.call];
+    const LimbK K = cd.limb[it.l];
+    if (checks && !fin_item_in_bounds(cd, it)) {
+        if (threadIdx.x == 0) atomicOr(status, kStatusBounds);
+        return;
+    }
+    if (cd.kind == HE_KIND_FC) {
+        if (cd.msrc)
+            fc_masked_body(cd.g, K, it.a, it.l, it.b, smem4);
+        else
+            fc_body(cd.g, K, it.a, it.l, it.b, smem4);
+    } else {
+        fin_conv_body(cd, K, it, smem4);
+    }
+    if (cd.rs) fin_rescale(cd, fin_out_poly(cd, it.a, it.b));
 }
 
 // Opt a kernel in to `bytes` of dynamic shared memory once per (kernel,
@@ -1954,7 +2000,7 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     cudaError_t e = cudaSuccess;
     // phase: -1 whole run, 0 input NTTs, 1 everything after them, 2 the MAC
     // kernel alone, 3 everything after the MAC kernel
-    if (phase == 4) {  // the rescale kernel alone
+    if (phase == 4) {  // the rescale kernel alone, over every call with d_rescaled
         if (pl.n_rs) k_plan_rescale<<<pl.n_rs, kThreads, 0, st>>>(pl.d_rs_calls, pl.d_rs_items);
         return cudaGetLastError();
     }
@@ -1990,8 +2036,8 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     if ((e = plan_chan_launch<8>(pl, 2, st)) != cudaSuccess) return e;
     if ((e = plan_chan_launch<16>(pl, 3, st)) != cudaSuccess) return e;
     if ((e = plan_chan_launch<1>(pl, 4, st)) != cudaSuccess) return e;
-    if (pl.n_rs) {
-        k_plan_rescale<<<pl.n_rs, kThreads, 0, st>>>(pl.d_rs_calls, pl.d_rs_items);
+    if (pl.n_rs_run) {  // calls the finishing kernel does not write (their items come first)
+        k_plan_rescale<<<pl.n_rs_run, kThreads, 0, st>>>(pl.d_rs_calls, pl.d_rs_items);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

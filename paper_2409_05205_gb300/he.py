@@ -67,7 +67,8 @@ class he_plan_info(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("kernels_per_run", "ntt_items", "mac_items", "mac_ctas",
                                                "finish_items", "fused_items", "fc_items", "split_calls")] + \
                [("workspace_bytes", ctypes.c_uint64), ("tuning", he_plan_tuning)] + \
-               [(n, ctypes.c_uint32) for n in ("tc_items", "tc_ctas", "tc_calls", "rescale_items")]
+               [(n, ctypes.c_uint32) for n in ("tc_items", "tc_ctas", "tc_calls", "rescale_items",
+                                              "rescale_fused_calls")]
 
 
 class he_server_config(ctypes.Structure):

@@ -76,11 +76,15 @@ def test_rescale_argument_errors():
                          torch.cuda.current_stream())
 
 
-def test_plan_rescales_every_output_in_one_kernel():
-    """d_rescaled on plain, masked Conv and FC calls of one plan: the words of
-    the oracle's rescale of each call's output (FC outputs come from the side
-    stream, so the rescale also checks the join); HE_PHASE_RESCALE reruns
-    the rescale kernel alone."""
+def test_plan_rescales_every_output():
+    """d_rescaled on plain and masked Conv calls of the split form, a Conv
+    call of the fused form, an FC call whose window is computed directly and
+    one on the transform path, in one plan: the words of the oracle's
+    rescale of each call's output, on two runs in a row (the finishing
+    kernel's per-polynomial counters reset themselves).  The outputs the
+    finishing kernel writes are rescaled in its epilogue, the others by the
+    rescale kernel; HE_PHASE_RESCALE reruns every call's rescale in that
+    kernel alone."""
     H = U.he()
     torch = U.torch_cuda()
     N, L, T = 4096, 3, U.T
@@ -97,26 +101,36 @@ def test_plan_rescales_every_output_in_one_kernel():
         banks = [H.he_pack_filters(p, conv, F), H.he_pack_masked(p, conv, F, rho), H.he_pack_fc(p, 64, 10, W)]
         try:
             cts = U.to_dev(synth.residues(402, "rp/ct", (1, G, 2, L, N), ps))
+            cts2 = U.to_dev(synth.residues(402, "rp/ct2", (2, G, 2, L, N), ps))
             c0 = U.to_dev(synth.residues(402, "rp/c0", (1, G, L, N), ps))
             sh = U.to_dev(synth.ints(402, "rp/sh", (1, G, N), 0, T - 1).astype(np.uint32))
             shp = U.to_dev(synth.ints(402, "rp/shp", (1, Hh, N), 0, T - 1).astype(np.uint32))
             fct = U.to_dev(synth.residues(402, "rp/fct", (2, 2, L, N), ps))
-            shapes = [(1 * Hh * 2, L, N), (1 * Hh, L, N), (2 * P * 2, L, N)]
+            fcn = U.to_dev(synth.residues(402, "rp/fcn", (2, 2, L, N), ps))
+            shapes = [(1 * Hh * 2, L, N), (1 * Hh, L, N), (2 * Hh * 2, L, N), (2 * P * 2, L, N), (2 * P * 2, L, N)]
             outs = [U.empty_dev(sh_) for sh_ in shapes]
             rsc = [U.empty_dev((sh_[0], L - 1, N)) for sh_ in shapes]
             calls = [(banks[0], cts, H.HE_COEFF, outs[0], 1, None, None, rsc[0]),
                      (banks[1], c0, H.HE_COEFF, outs[1], 1, sh, shp, rsc[1]),
-                     (banks[2], fct, H.HE_COEFF, outs[2], 2, None, None, rsc[2])]
+                     (banks[0], cts2, H.HE_COEFF, outs[2], 2, None, None, rsc[2]),
+                     (banks[2], fct, H.HE_COEFF, outs[3], 2, None, None, rsc[3]),
+                     (banks[2], fcn, H.HE_NTT, outs[4], 2, None, None, rsc[4])]
             plan = H.he_plan_create(calls)
             try:
-                info = H.he_plan_query(plan, 3)
-                assert info["rescale_items"] > 0
-                H.he_plan_run(plan, s)
-                H.he_sync(s)
-                H.he_plan_check(plan)
-                for o, r, sh_ in zip(outs, rsc, shapes):
-                    want = O.rescale_last_limb(U.from_dev(o).reshape(sh_), ps)
-                    np.testing.assert_array_equal(U.from_dev(r).reshape(want.shape), want)
+                info = H.he_plan_query(plan, len(calls))
+                # split Conv (scalar MAC), fused-form Conv, direct FC, FC on the transform path
+                assert info["form"] == [1, 1, 0, 3, 0]
+                assert info["rescale_fused_calls"] == 3          # calls 0, 1 and 4
+                assert info["rescale_items"] > 0                 # calls 2 and 3
+                for run in range(2):
+                    for r in rsc:
+                        r.fill_(-1)
+                    H.he_plan_run(plan, s)
+                    H.he_sync(s)
+                    H.he_plan_check(plan)
+                    for o, r, sh_ in zip(outs, rsc, shapes):
+                        want = O.rescale_last_limb(U.from_dev(o).reshape(sh_), ps)
+                        np.testing.assert_array_equal(U.from_dev(r).reshape(want.shape), want)
                 for r in rsc:
                     r.fill_(-1)
                 H.he_plan_run_phase(plan, H.HE_PHASE_RESCALE, s)
