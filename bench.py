@@ -413,13 +413,42 @@ def bfly_peak(torch, H, p, stream, device):
     return n / (ms * 1e-3), ms, n
 
 
+# Inferences in flight in the timed windows: step k's graph replays on
+# stream k % STREAMS (replica k % R, R a multiple of STREAMS, so a replica's
+# steps never overlap one another).  Independent inferences on two streams let
+# one step's bandwidth-bound MAC kernel run beside another step's transform
+# kernels; the per-inference latency is timed one step at a time.
+STREAMS = 2
+
+
+def replay_window(torch, graphs, K, streams, k0=0):
+    """Events around K replays, step k on streams[k % len(streams)]; returns
+    (start, end) events recorded on streams[0] after every stream joined."""
+    t0, t1 = _events(2)
+    s0 = streams[0]
+    t0.record(s0)
+    for st in streams[1:]:
+        st.wait_event(t0)
+    for k in range(k0, k0 + K):
+        st = streams[k % len(streams)]
+        with torch.cuda.stream(st):
+            graphs[k % len(graphs)].replay()
+    for st in streams[1:]:
+        e = torch.cuda.Event()
+        e.record(st)
+        s0.wait_event(e)
+    t1.record(s0)
+    return t0, t1
+
+
 def run_ours(args, rank, world, device):
     import torch
     wl = workload(args.workload)
-    arm = Arm(wl, device)
+    arm = Arm(wl, device, replicas=2 * STREAMS)
     H = arm.H
     nl = len(arm.calls)
     stream = torch.cuda.Stream()
+    streams = [stream] + [torch.cuda.Stream() for _ in range(STREAMS - 1)]
     K, W = args.steps, args.warmup
     k_plain, k_phase = min(K, 200), min(K, 500)
 
@@ -503,22 +532,16 @@ def run_ours(args, rank, world, device):
     fin_only_ms = f0.elapsed_time(f1) / k_phase
     peak_bfly, peak_ms, _ = bfly_peak(torch, H, next(iter(arm.params.values())), stream, device)
 
-    # ---------------- headline: the plan as a CUDA graph, one replay per step
-    with torch.cuda.stream(stream):
-        for k in range(W):
-            arm.graphs[k % arm.R].replay()
+    # ---------------- headline: the plan as a CUDA graph, one replay per step,
+    # STREAMS inferences in flight
+    replay_window(torch, arm.graphs, W, streams)
     torch.cuda.synchronize()
     barrier()
     clocks = ClockSampler(device)
     clocks.start()
     time.sleep(0.3)
-    with torch.cuda.stream(stream):
-        for k in range(W):  # the GPU idled while the sampler started: warm it up again
-            arm.graphs[k % arm.R].replay()
-        t0.record(stream)
-        for k in range(K):
-            arm.graphs[k % arm.R].replay()
-        t1.record(stream)
+    replay_window(torch, arm.graphs, W, streams)  # the GPU idled while the sampler started: warm it up again
+    t0, t1 = replay_window(torch, arm.graphs, K, streams)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
@@ -526,13 +549,13 @@ def run_ours(args, rank, world, device):
     # the same K-step window repeated: its spread (the headline is the first)
     windows = [graph_ms]
     for _ in range(4):
-        with torch.cuda.stream(stream):
-            t0.record(stream)
-            for k in range(K):
-                arm.graphs[k % arm.R].replay()
-            t1.record(stream)
+        t0, t1 = replay_window(torch, arm.graphs, K, streams)
         torch.cuda.synchronize()
         windows.append(t0.elapsed_time(t1))
+    # the same window with one inference in flight (one stream)
+    t0, t1 = replay_window(torch, arm.graphs, K, [stream])
+    torch.cuda.synchronize()
+    one_ms = t0.elapsed_time(t1)
     # per-inference latency: the same replays, one at a time between events
     k_lat = min(K, 2000)
     g_ev = [_events(2) for _ in range(k_lat)]
@@ -547,7 +570,7 @@ def run_ours(args, rank, world, device):
         graph_ms, plain_ms = max_over_ranks([graph_ms, plain_ms], "cuda")
 
     # ---------------- e2e: pinned host buffers, H2D + plan + D2H every step
-    e2e = run_e2e(arm, args, stream)
+    e2e = run_e2e(arm, args, streams)
 
     ch_bytes, ntt_bytes, bfly = arm.algorithmic()
     ntt_bfly, fin_bfly = arm.butterflies(info["form"])
@@ -584,8 +607,13 @@ def run_ours(args, rank, world, device):
         "dtype": "u32 (exact residues mod 30-bit primes)", "data": "synthetic",
         "config": {"workload": wl["name"], **arm.describe(),
                    "form": f"plan of {nl} layer calls ({info['kernels_per_run']} kernels) replayed as a CUDA graph",
-                   "l2": "rotates 3 model replicas + 3 input sets (> 2x L2); no flush",
+                   "l2": f"rotates {arm.R} model replicas + {arm.R} input sets (> 2x L2); no flush",
+                   "in_flight": f"{STREAMS} inferences: step k's graph replays on stream k % {STREAMS} "
+                                f"(replica k % {arm.R})",
                    "parallelism": f"replicas x{world}"},
+        "one_in_flight": {"value": whole_job_rate(arm.units, K, world, one_ms), "unit": "layers/s",
+                          "ms_per_step": one_ms / K,
+                          "how": f"the same {K}-step window with every replay on one stream"},
         "latency_ms": {"p50": float(np.percentile(graph_steps, 50)),
                        "p99": float(np.percentile(graph_steps, 99)), "steps": k_lat,
                        "how": "CUDA events around each graph replay, a separate run of the same replays"},
@@ -633,7 +661,8 @@ def run_ours(args, rank, world, device):
         "clocks": clk,
         "windows": {"layers_per_s": [arm.units * K / (w * 1e-3) for w in windows],
                     "median": float(np.median([arm.units * K / (w * 1e-3) for w in windows])),
-                    "how": f"the timed window of {K} graph replays run 5 times back to back; value is the first"},
+                    "how": f"the timed window of {K} graph replays ({STREAMS} in flight) run 5 times back to "
+                           "back; value is the first"},
     }
     arm.free()
     return res
@@ -641,11 +670,13 @@ def run_ours(args, rank, world, device):
 
 def pipelined_steps(torch, R, K, upload, replay, download, stream):
     """K end-to-end steps, step k on replica k % R, timed on the wall clock:
-    the upload of step k's inputs (H2D stream), its graph (`stream`) and the
-    download of its result (D2H stream) are ordered by events, so step k+1's
-    upload and step k-1's download overlap step k's graph.  A replica's input
+    the upload of step k's inputs (H2D stream), its graph (`stream`, or with
+    a list of streams stream[k % len], R a multiple of len) and the download
+    of its result (D2H stream) are ordered by events, so step k+1's upload
+    and step k-1's download overlap step k's graph.  A replica's input
     buffer is rewritten only after its previous graph has read it, and its
     output buffer only after its previous download.  Returns seconds."""
+    comp = stream if isinstance(stream, (list, tuple)) else [stream]
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     ev_in = [torch.cuda.Event() for _ in range(R)]
     ev_comp = [torch.cuda.Event() for _ in range(R)]
@@ -654,17 +685,18 @@ def pipelined_steps(torch, R, K, upload, replay, download, stream):
     def run(n):
         for k in range(n):
             r = k % R
+            cs = comp[k % len(comp)]
             if k >= R:
                 s_in.wait_event(ev_comp[r])
             with torch.cuda.stream(s_in):
                 upload(r)
             ev_in[r].record(s_in)
-            stream.wait_event(ev_in[r])
+            cs.wait_event(ev_in[r])
             if k >= R:
-                stream.wait_event(ev_out[r])
-            with torch.cuda.stream(stream):
+                cs.wait_event(ev_out[r])
+            with torch.cuda.stream(cs):
                 replay(r)
-            ev_comp[r].record(stream)
+            ev_comp[r].record(cs)
             s_out.wait_event(ev_comp[r])
             with torch.cuda.stream(s_out):
                 download(r)
@@ -695,8 +727,9 @@ def run_e2e(arm, args, stream):
     return {"value": arm.units * K / dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": K,
             "how": "per step: one H2D copy of every layer input (contiguous) from pinned host memory, the plan "
-                   "(CUDA graph), one D2H copy of every extracted output into pinned memory; uploads, graphs and "
-                   "downloads on three streams ordered by events, so consecutive steps overlap; wall clock"}
+                   "(CUDA graph), one D2H copy of every extracted output into pinned memory; uploads, graphs (on "
+                   f"{len(stream) if isinstance(stream, list) else 1} streams, step k on stream k % that) and "
+                   "downloads ordered by events, so consecutive steps overlap; wall clock"}
 
 
 # ----------------------------------------------------------------------------

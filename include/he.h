@@ -494,7 +494,15 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *                    costs fewer products than two length-N transforms
  *                    computes that window directly from the coefficient
  *                    forms (default); 0: every FC call takes the transform
- *                    path (input NTT, product, inverse NTT, window). */
+ *                    path (input NTT, product, inverse NTT, window).
+ *   groups           1, 2 or 3 (default 1): the calls are split into that
+ *                    many groups of about equal weight bytes, each with
+ *                    its own kernels; group g + 1 runs on a stream of the
+ *                    plan's own, started once group g's input transforms
+ *                    are done, so that one group's bandwidth-bound MAC
+ *                    overlaps the next group's transforms and the previous
+ *                    group's finishing kernel; the run joins back onto the
+ *                    caller's stream (graph capture included). */
 typedef struct {
     uint32_t split;
     uint32_t mac_item_kb;
@@ -502,6 +510,7 @@ typedef struct {
     uint32_t fused_max_nj;
     uint32_t tc_min_batch;
     uint32_t fc_direct;
+    uint32_t groups;
 } he_plan_tuning;
 
 /* The default tuning. */
@@ -617,9 +626,12 @@ void he_plan_destroy(he_plan_t plan);
  * paper's protocol where the client's non-linear step sits between layers
  * (Sec. III, Alg. 1; the client's time is taken as zero here).  A
  * scheduler thread batches up to max_batch requests waiting for the same
- * (model, layer) into one plan run (continuous batching: a request joins
- * the next batch of its layer as soon as it is there, while other batches
- * run on other streams), copies host->device, runs, copies device->host.
+ * (model, layer) into one plan run (continuous batching: while a batch of
+ * a layer runs, the requests reaching that layer wait and form its next
+ * batch, issued when the running one completes or as soon as max_batch of
+ * them wait; a layer with nothing running is issued at once, oldest waiting
+ * request first; batches of different layers run on several streams),
+ * copies host->device, runs, copies device->host.
  * Device buffers for a batch (its inputs, outputs and plan workspace) are
  * sized before anything is allocated and allocated only while their total
  * stays within hbm_budget_bytes; they are reused.  When the budget is spent,

@@ -1016,6 +1016,7 @@ he_status he_plan_tuning_default(he_plan_tuning *t) {
     t->fused_max_nj = 16;
     t->tc_min_batch = 2;
     t->fc_direct = 1;
+    t->groups = 1;
     return HE_OK;
 }
 
@@ -1030,6 +1031,7 @@ he_status check_tuning(const he_plan_tuning &t) {
     if (t.tc_min_batch != 1 && t.tc_min_batch != 2 && t.tc_min_batch != 4 && t.tc_min_batch != 8)
         return fail(HE_ERR_ARG, "tuning: tc_min_batch must be 1, 2, 4 or 8");
     if (t.fc_direct > 1) return fail(HE_ERR_ARG, "tuning: fc_direct must be 0 or 1");
+    if (t.groups < 1 || t.groups > kPlanMaxGroups) return fail(HE_ERR_ARG, "tuning: groups must be 1, 2 or 3");
     return HE_OK;
 }
 }  // namespace
@@ -1164,7 +1166,7 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
 
 namespace {
 he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning, he_plan_t *out,
-                     size_t *ws_only);
+                     size_t *ws_only, bool check_overlaps = false);
 }  // namespace
 
 he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning,
@@ -1180,15 +1182,21 @@ he_status he_plan_workspace_bytes(const he_layer_call *calls, uint32_t ncalls, s
 }
 
 namespace {
+he_status plan_build_grouped(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning &tu, he_plan_t *out);
+
 // Builds a plan, or with ws_only set only validates the calls and returns the
-// workspace the plan would own (nothing allocated; d_in / d_out may be NULL).
+// workspace the plan would own (nothing allocated; d_in / d_out may be NULL;
+// with check_overlaps, the buffers are also checked for overlaps).
 he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning, he_plan_t *out,
-                     size_t *ws_only) {
+                     size_t *ws_only, bool check_overlaps) {
     if (!tuning) return fail(HE_ERR_ARG, "NULL tuning");
     if (check_tuning(*tuning) != HE_OK) return HE_ERR_ARG;
     const he_plan_tuning tu = *tuning;
     if (!calls || (!out && !ws_only) || ncalls == 0) return fail(HE_ERR_ARG, "NULL argument or empty plan");
     if (out) *out = nullptr;
+    // a grouped plan owns the same workspace as the ungrouped one (the sum
+    // of its calls' shares)
+    if (tu.groups > 1 && !ws_only) return plan_build_grouped(calls, ncalls, tu, out);
     const he_params_s *p0 = calls[0].filters ? calls[0].filters->p : nullptr;
     if (!p0) return fail(HE_ERR_ARG, "call 0 has no filters");
     const int device = p0->device;
@@ -1384,10 +1392,8 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             descs[i].z_words = (size_t)(descs[i].split ? g.parts : 1u) * g.L * g.ncols * g.co * g.M;
             ws_words += descs[i].z_words;
         }
-    if (ws_only) {
-        *ws_only = ws_words * sizeof(uint32_t);
-        return HE_OK;
-    }
+    if (ws_only) *ws_only = ws_words * sizeof(uint32_t);
+    if (ws_only && !check_overlaps) return HE_OK;
     for (size_t a = 0; a < ranges.size(); ++a)
         for (size_t b = a + 1; b < ranges.size(); ++b) {
             if (!ranges[a].is_out && !ranges[b].is_out) continue;  // inputs may be shared
@@ -1395,6 +1401,7 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
                 return fail(HE_ERR_ARG, "calls %u and %u: an output overlaps another buffer", ranges[a].call,
                             ranges[b].call);
         }
+    if (ws_only) return HE_OK;
     DeviceGuard dg(device);
     if (!dg.ok) return fail(HE_ERR_CUDA, "cannot select device %d", device);
     he_plan_s *pl = new (std::nothrow) he_plan_s();
@@ -1686,22 +1693,105 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
     *out = pl;
     return HE_OK;
 }
+// Device words a call streams through the MAC (its bank) and moves in and
+// out (inputs, outputs): the weight by which calls are spread over groups.
+double call_weight(const he_layer_call &c) {
+    const he_filters_s *f = c.filters;
+    const double LN = (double)f->p->L * f->p->N, k = f->masked ? 2.0 : 1.0;
+    if (f->kind == HE_KIND_CONV)
+        return LN * ((double)f->desc.co * f->lay.G * k + (double)c.B * 2.0 * (f->lay.G + f->lay.H));
+    return LN * ((double)f->fl.P_fc * k + (double)c.B * 2.0 * (1.0 + f->fl.P_fc));
+}
+
+// A plan over `groups` groups of the calls (about equal weight each, heaviest
+// call first onto the lightest group; calls keep their order within a
+// group), each an ordinary plan, run as a pipeline (he_plan_run).
+he_status plan_build_grouped(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning &tu, he_plan_t *out) {
+    he_plan_tuning t1 = tu;
+    t1.groups = 1;
+    size_t ws = 0;
+    he_status st = plan_build(calls, ncalls, &t1, nullptr, &ws, true);  // validates every call, overlaps included
+    if (st != HE_OK) return st;
+    const uint32_t ng = std::min(tu.groups, ncalls);
+    if (ng == 1) return plan_build(calls, ncalls, &t1, out, nullptr);
+    std::vector<uint32_t> order(ncalls), grp(ncalls);
+    for (uint32_t i = 0; i < ncalls; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t a, uint32_t b) { return call_weight(calls[a]) > call_weight(calls[b]); });
+    std::vector<double> load(ng, 0.0);
+    for (uint32_t i : order) {
+        const uint32_t g = (uint32_t)(std::min_element(load.begin(), load.end()) - load.begin());
+        grp[i] = g;
+        load[g] += call_weight(calls[i]);
+    }
+    const int device = calls[0].filters->p->device;
+    DeviceGuard dg(device);
+    if (!dg.ok) return fail(HE_ERR_CUDA, "cannot select device %d", device);
+    he_plan_s *pl = new (std::nothrow) he_plan_s();
+    if (!pl) return fail(HE_ERR_NOMEM, "plan");
+    pl->device = device;
+    pl->ncalls = ncalls;
+    pl->tuning = tu;
+    pl->wait_polls = HE_WAIT_POLLS_DEFAULT;
+    pl->split = new (std::nothrow) uint8_t[ncalls];
+    if (!pl->split) {
+        delete pl;
+        return fail(HE_ERR_NOMEM, "plan");
+    }
+    pl->ngroups = ng;
+    for (uint32_t g = 0; g < ng; ++g) {
+        std::vector<he_layer_call> gc;
+        std::vector<uint32_t> idx;
+        for (uint32_t i = 0; i < ncalls; ++i)
+            if (grp[i] == g) {
+                gc.push_back(calls[i]);
+                idx.push_back(i);
+            }
+        st = plan_build(gc.data(), (uint32_t)gc.size(), &t1, &pl->sub[g], nullptr);
+        if (st != HE_OK) {
+            he_plan_destroy(pl);
+            return st;
+        }
+        for (size_t k = 0; k < idx.size(); ++k) pl->split[idx[k]] = pl->sub[g]->split[k];
+        pl->ws_bytes += pl->sub[g]->ws_bytes;
+        cudaError_t e = cudaEventCreateWithFlags(&pl->ev_ntt[g], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->ev_end[g], cudaEventDisableTiming);
+        if (e == cudaSuccess && g > 0) e = cudaStreamCreateWithFlags(&pl->side[g - 1], cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            he_plan_destroy(pl);
+            return cuda_fail(e, "plan streams and events");
+        }
+    }
+    *out = pl;
+    return HE_OK;
+}
 }  // namespace
 
 he_status he_plan_set_checks(he_plan_t plan, int on) {
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
     plan->checks = on ? 1u : 0u;
+    for (uint32_t g = 0; g < plan->ngroups; ++g) plan->sub[g]->checks = plan->checks;
     return HE_OK;
 }
 
 he_status he_plan_set_wait_limit(he_plan_t plan, uint32_t polls) {
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
     plan->wait_polls = polls;
+    for (uint32_t g = 0; g < plan->ngroups; ++g) plan->sub[g]->wait_polls = polls;
     return HE_OK;
 }
 
 he_status he_plan_check(he_plan_t plan) {
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
+    if (plan->ngroups) {  // every group's flags are read and cleared; the first error is returned
+        he_status first = HE_OK;
+        for (uint32_t g = 0; g < plan->ngroups; ++g) {
+            const he_status st = he_plan_check(plan->sub[g]);
+            if (first == HE_OK) first = st;
+        }
+        return first;
+    }
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
     uint32_t st = 0;
@@ -1721,12 +1811,32 @@ he_status he_plan_check(he_plan_t plan) {
     return HE_OK;
 }
 
+namespace {
+// The pipeline of a grouped plan: group 0's kernels on the caller's stream;
+// group g > 0 on its side stream, started after group g - 1's input
+// transforms; then the caller's stream waits for every side stream.
+cudaError_t run_grouped(const he_plan_s &pl, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (uint32_t g = 0; g < pl.ngroups && e == cudaSuccess; ++g) {
+        const cudaStream_t sg = g == 0 ? st : pl.side[g - 1];
+        if (g > 0) e = cudaStreamWaitEvent(sg, pl.ev_ntt[g - 1], 0);
+        if (e == cudaSuccess) e = he_launch_plan(*pl.sub[g], sg, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(pl.ev_ntt[g], sg);
+        if (e == cudaSuccess) e = he_launch_plan(*pl.sub[g], sg, 1);
+        if (e == cudaSuccess && g > 0) e = cudaEventRecord(pl.ev_end[g], sg);
+    }
+    for (uint32_t g = 1; g < pl.ngroups && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(st, pl.ev_end[g], 0);
+    return e;
+}
+}  // namespace
+
 he_status he_plan_run(he_plan_t plan, void *stream) {
     NvtxRange nvtx_("he_plan_run");
     if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
-    cudaError_t e = he_launch_plan(*plan, (cudaStream_t)stream, -1);
+    cudaError_t e = plan->ngroups ? run_grouped(*plan, (cudaStream_t)stream)
+                                  : he_launch_plan(*plan, (cudaStream_t)stream, -1);
     return e == cudaSuccess ? HE_OK : cuda_fail(e, "plan run");
 }
 
@@ -1736,12 +1846,43 @@ he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream) {
     if (phase < HE_PHASE_NTT || phase > HE_PHASE_FIN) return fail(HE_ERR_ARG, "phase must be 0 .. 5");
     DeviceGuard g(plan->device);
     if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
-    cudaError_t e = he_launch_plan(*plan, (cudaStream_t)stream, phase);
+    cudaError_t e = cudaSuccess;
+    if (plan->ngroups)  // the groups' kernels of this phase, one group after the other on `stream`
+        for (uint32_t k = 0; k < plan->ngroups && e == cudaSuccess; ++k)
+            e = he_launch_plan(*plan->sub[k], (cudaStream_t)stream, phase);
+    else
+        e = he_launch_plan(*plan, (cudaStream_t)stream, phase);
     return e == cudaSuccess ? HE_OK : cuda_fail(e, "plan run phase");
 }
 
 he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
     if (!plan || !info) return fail(HE_ERR_ARG, "NULL argument");
+    if (plan->ngroups) {  // the groups' kernels and items, added up
+        he_plan_info r{};
+        for (uint32_t g = 0; g < plan->ngroups; ++g) {
+            he_plan_info q{};
+            he_plan_query(plan->sub[g], &q, nullptr);
+            r.kernels_per_run += q.kernels_per_run;
+            r.ntt_items += q.ntt_items;
+            r.mac_items += q.mac_items;
+            r.mac_ctas = std::max(r.mac_ctas, q.mac_ctas);
+            r.finish_items += q.finish_items;
+            r.fused_items += q.fused_items;
+            r.fc_items += q.fc_items;
+            r.split_calls += q.split_calls;
+            r.tc_items += q.tc_items;
+            r.tc_ctas = std::max(r.tc_ctas, q.tc_ctas);
+            r.tc_calls += q.tc_calls;
+            r.rescale_items += q.rescale_items;
+            r.rescale_fused_calls += q.rescale_fused_calls;
+        }
+        r.workspace_bytes = plan->ws_bytes;
+        r.tuning = plan->tuning;
+        *info = r;
+        if (split)
+            for (uint32_t i = 0; i < plan->ncalls; ++i) split[i] = plan->split[i];
+        return HE_OK;
+    }
     he_plan_info r{};
     r.ntt_items = plan->n_ntt;
     r.mac_items = plan->n_mac;
@@ -1769,6 +1910,12 @@ he_status he_plan_query(he_plan_t plan, he_plan_info *info, uint8_t *split) {
 void he_plan_destroy(he_plan_t plan) {
     if (!plan) return;
     DeviceGuard g(plan->device);
+    for (uint32_t k = 0; k < plan->ngroups; ++k) {
+        he_plan_destroy(plan->sub[k]);
+        if (plan->ev_ntt[k]) cudaEventDestroy(plan->ev_ntt[k]);
+        if (plan->ev_end[k]) cudaEventDestroy(plan->ev_end[k]);
+        if (plan->side[k]) cudaStreamDestroy(plan->side[k]);
+    }
     cudaFree(plan->ws);
     cudaFree(plan->d_calls);
     cudaFree(plan->d_ntt);
@@ -1898,6 +2045,7 @@ he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t
             }
         };
         if (has_split) try_knob(&he_plan_tuning::split, {1u, 0u});
+        if (ncalls > 1) try_knob(&he_plan_tuning::groups, {1u, 2u, 3u});
         if (has_split && cur.split) {
             try_knob(&he_plan_tuning::mac_item_kb, {128u, 64u, 32u});
             try_knob(&he_plan_tuning::mac_ctas_per_sm, {2u, 1u});

@@ -345,6 +345,7 @@ constexpr uint32_t kRsItemU4 = 256;  // uint4 groups per rescale item: one per t
 constexpr int kChanClasses = 5;
 __host__ __device__ __forceinline__ constexpr uint32_t chan_class_nj(int cls) { return cls < 4 ? 2u << cls : 1u; }
 
+constexpr uint32_t kPlanMaxGroups = 3;  // call groups of a pipelined plan (he_plan_tuning::groups)
 struct he_plan_s {
     int device;
     uint32_t ncalls, n_ntt, n_chan[kChanClasses];  // fused channel items per NJ class (2, 4, 8, 16, 1)
@@ -379,6 +380,14 @@ struct he_plan_s {
     uint32_t checks;                    // device-side bounds checks on (he_plan_set_checks)
     uint8_t *split;                     // host: per call, 1 if it takes the split form
     he_plan_tuning tuning;
+    // grouped plan (tuning.groups > 1): no kernels of its own; sub-plan g
+    // holds group g's calls, and runs on side[g - 1] (g > 0) once group
+    // g - 1's input transforms are done (ev_ntt[g - 1]); ev_end[g] joins it
+    // back onto the caller's stream
+    uint32_t ngroups;
+    he_plan_s *sub[kPlanMaxGroups];
+    cudaStream_t side[kPlanMaxGroups];
+    cudaEvent_t ev_ntt[kPlanMaxGroups], ev_end[kPlanMaxGroups];
 };
 
 cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase);

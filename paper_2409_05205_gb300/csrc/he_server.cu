@@ -7,9 +7,11 @@
 // in the protocol where the client's non-linear step sits between layers
 // (taken here as zero time).  A scheduler thread forms batches of up to
 // max_batch requests waiting for the same (model, layer) -- continuous
-// batching: a request is admitted into the next batch of its layer as soon
-// as a slot is free, while other batches run -- and runs each batch on one
-// of several streams: host->device copies, the layer as a one-call plan,
+// batching: while a batch of a layer runs, the requests that reach that
+// layer wait and form its next batch, which is issued when the running one
+// completes (or at once when max_batch of them wait); layers with nothing
+// running are issued at once, oldest waiting request first -- and runs
+// each batch on one of several streams: host->device copies, the layer as a one-call plan,
 // device->host copies, then a host callback.  Device buffers ("lanes": the
 // batch's inputs and outputs and the plan's workspace) are allocated under an
 // HBM budget and reused.  A lane's size is known before anything is
@@ -87,6 +89,7 @@ struct Server {
     std::condition_variable cv_done;
     std::map<uint64_t, Req *> reqs;
     std::map<std::pair<uint32_t, uint32_t>, std::deque<Req *>> queues;  // (model, layer) -> waiting
+    std::map<std::pair<uint32_t, uint32_t>, uint32_t> running;          // (model, layer) -> batches in flight
     std::vector<Batch *> failed_launch;
     std::vector<Lane *> lanes;
     std::vector<Lane *> retired;  // evicted idle lanes, counted in bytes_in_use until freed
@@ -234,6 +237,7 @@ bool launch(Server *s, Lane *lane, std::vector<Req *> &rs) {
     for (Req *r : rs) r->t_launch = t;
     lane->busy = true;
     ++s->inflight;
+    ++s->running[{lane->model, lane->layer}];
     ++s->batches;
     s->batched_calls += rs.size();
     ++s->batch_hist[rs.size() >= 8 ? 3 : (rs.size() >= 4 ? 2 : (rs.size() >= 2 ? 1 : 0))];
@@ -245,6 +249,7 @@ void finish_batch(Server *s, Batch *b) {
     if (b->lane->busy) {
         b->lane->busy = false;
         --s->inflight;
+        --s->running[{b->lane->model, b->lane->layer}];
     }
     for (Req *r : b->reqs) {
         if (!b->ok) {
@@ -287,19 +292,25 @@ void scheduler(Server *s) {
         if (!done.empty()) s->cv_done.notify_all();
         free_retired(s);
         if (s->stop && s->inflight == 0) break;
-        // dispatch: oldest waiting request first, each batch from one queue
+        // dispatch: oldest waiting request first, each batch from one queue;
+        // a queue whose layer has a batch in flight keeps collecting
+        // requests until it completes, unless a full batch waits
         bool progress = true;
         while (!s->stop && progress && s->inflight < s->cfg.max_inflight) {
             progress = false;
             std::deque<Req *> *best = nullptr;
             std::pair<uint32_t, uint32_t> key{0, 0};
             double oldest = 0.0;
-            for (auto &kv : s->queues)
-                if (!kv.second.empty() && (!best || kv.second.front()->t_layer < oldest)) {
+            for (auto &kv : s->queues) {
+                if (kv.second.empty()) continue;
+                auto run = s->running.find(kv.first);
+                if (run != s->running.end() && run->second > 0 && kv.second.size() < s->cfg.max_batch) continue;
+                if (!best || kv.second.front()->t_layer < oldest) {
                     best = &kv.second;
                     key = kv.first;
                     oldest = kv.second.front()->t_layer;
                 }
+            }
             if (!best) break;
             const uint32_t bucket = bucket_of((uint32_t)best->size(), s->cfg.max_batch);
             Lane *lane = nullptr;

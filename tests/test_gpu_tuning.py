@@ -42,12 +42,14 @@ def _check(H, calls, refs):
         np.testing.assert_array_equal(U.from_dev(c[3]).reshape(ref.shape), ref)
 
 
-# fc_direct = 1 computes the FC 64 -> 10 window directly, 0 through the transforms
-TUNINGS = [dict(split=1, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=4, fc_direct=1),
-           dict(split=0, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=1, fc_direct=0),
-           dict(split=1, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=2, tc_min_batch=8, fc_direct=1),
-           dict(split=1, mac_item_kb=64, mac_ctas_per_sm=2, fused_max_nj=4, tc_min_batch=2, fc_direct=0),
-           dict(split=0, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=8, tc_min_batch=4, fc_direct=1)]
+# fc_direct = 1 computes the FC 64 -> 10 window directly, 0 through the
+# transforms; groups > 1 runs the calls in that many groups on the plan's own
+# streams
+TUNINGS = [dict(split=1, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=4, fc_direct=1, groups=1),
+           dict(split=0, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=1, fc_direct=0, groups=2),
+           dict(split=1, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=2, tc_min_batch=8, fc_direct=1, groups=3),
+           dict(split=1, mac_item_kb=64, mac_ctas_per_sm=2, fused_max_nj=4, tc_min_batch=2, fc_direct=0, groups=2),
+           dict(split=0, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=8, tc_min_batch=4, fc_direct=1, groups=3)]
 
 
 def test_every_tuning_gives_the_oracle_words():
@@ -109,6 +111,58 @@ def test_autotune_picks_a_valid_tuning_and_caches_it():
             assert t2 == t
             assert all((U.from_dev(c[3]) == 0xFFFFFFFF).all() for c in calls)
             assert dt < 5.0
+        finally:
+            for f in banks:
+                H.he_filters_destroy(f)
+
+
+@pytest.mark.parametrize("groups", [2, 3])
+def test_grouped_plan_in_a_graph_and_by_phases(groups):
+    """A grouped plan forks onto its own streams and joins back: captured
+    into a CUDA graph and replayed, and run phase by phase on one stream, it
+    gives the oracle's words; the calls' forms are those of the ungrouped
+    plan."""
+    H = U.he()
+    torch = U.torch_cuda()
+    with U.params(N, L) as p:
+        banks, calls, refs = _setup(H, p)
+        try:
+            s = torch.cuda.Stream()
+            flat = H.he_plan_create(calls)
+            plan = H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), groups=groups))
+            try:
+                qf, qg = H.he_plan_query(flat, len(calls)), H.he_plan_query(plan, len(calls))
+                assert qg["form"] == qf["form"] and qg["tuning"]["groups"] == groups
+                assert qg["workspace_bytes"] == qf["workspace_bytes"]
+                assert qg["ntt_items"] == qf["ntt_items"] and qg["finish_items"] == qf["finish_items"]
+                H.he_plan_set_checks(plan, 1)
+                with torch.cuda.stream(s):
+                    H.he_plan_run(plan, s)          # warm-up outside capture
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    H.he_plan_run(plan, s)
+                for c in calls:
+                    c[3].fill_(-1)
+                torch.cuda.synchronize()
+                with torch.cuda.stream(s):
+                    g.replay()
+                    g.replay()
+                torch.cuda.synchronize()
+                H.he_plan_check(plan)
+                _check(H, calls, refs)
+                for c in calls:
+                    c[3].fill_(-1)
+                torch.cuda.synchronize()
+                for ph in (H.HE_PHASE_NTT, H.HE_PHASE_MAC, H.HE_PHASE_FINISH):
+                    H.he_plan_run_phase(plan, ph, s)
+                H.he_sync(s)
+                H.he_plan_check(plan)
+                _check(H, calls, refs)
+                del g
+            finally:
+                H.he_plan_destroy(plan)
+                H.he_plan_destroy(flat)
         finally:
             for f in banks:
                 H.he_filters_destroy(f)
