@@ -132,6 +132,8 @@ class ClockSampler:
         except OSError:
             pass
         return {"sm_mhz": float(np.median(sms)) if sms else None, "sm_max_mhz": mx,
+                "sm_mhz_p10": float(np.percentile(sms, 10)) if sms else None,
+                "sm_mhz_min": float(np.min(sms)) if sms else None,
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
@@ -418,7 +420,7 @@ def bfly_peak(torch, H, p, stream, device):
 # steps never overlap one another).  Independent inferences on two streams let
 # one step's bandwidth-bound MAC kernel run beside another step's transform
 # kernels; the per-inference latency is timed one step at a time.
-STREAMS = 2
+STREAMS = 3
 
 
 def replay_window(torch, graphs, K, streams, k0=0):
@@ -1470,7 +1472,7 @@ EXTRAS = (("batched64", dict(steps=200, warmup=5)),
 def _summary(r):
     """The figures of one configuration's line that the headline line carries."""
     keep = ("value", "unit", "ms_per_step", "steps", "warmup", "latency_ms", "speedup_vs_plain_form", "config",
-            "clocks", "gpu_launches", "windows")
+            "clocks", "gpu_launches", "windows", "one_in_flight")
     out = {k: r[k] for k in keep if k in r}
     if r.get("plain_form"):
         pf = r["plain_form"]
@@ -1488,6 +1490,8 @@ def _summary(r):
         out["e2e"] = {k: r["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
     if r.get("serving"):
         out["serving"] = r["serving"]
+    if r.get("tuning"):
+        out["tuning"] = r["tuning"]["chosen"]
     return out
 
 

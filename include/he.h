@@ -502,7 +502,13 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *                    are done, so that one group's bandwidth-bound MAC
  *                    overlaps the next group's transforms and the previous
  *                    group's finishing kernel; the run joins back onto the
- *                    caller's stream (graph capture included). */
+ *                    caller's stream (graph capture included).
+ *   fin_parts        1, 2 or 4 (default 1): finishing items per output
+ *                    polynomial, limb and column of a split-form Conv call,
+ *                    each over that share of the s residue classes (its
+ *                    channels' inverse transforms and those classes'
+ *                    coefficients); fewer where a share would hold under 4
+ *                    classes.  More, smaller items fill more of the GPU. */
 typedef struct {
     uint32_t split;
     uint32_t mac_item_kb;
@@ -511,6 +517,7 @@ typedef struct {
     uint32_t tc_min_batch;
     uint32_t fc_direct;
     uint32_t groups;
+    uint32_t fin_parts;
 } he_plan_tuning;
 
 /* The default tuning. */

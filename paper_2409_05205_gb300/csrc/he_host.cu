@@ -1017,6 +1017,7 @@ he_status he_plan_tuning_default(he_plan_tuning *t) {
     t->tc_min_batch = 2;
     t->fc_direct = 1;
     t->groups = 1;
+    t->fin_parts = 1;
     return HE_OK;
 }
 
@@ -1032,6 +1033,8 @@ he_status check_tuning(const he_plan_tuning &t) {
         return fail(HE_ERR_ARG, "tuning: tc_min_batch must be 1, 2, 4 or 8");
     if (t.fc_direct > 1) return fail(HE_ERR_ARG, "tuning: fc_direct must be 0 or 1");
     if (t.groups < 1 || t.groups > kPlanMaxGroups) return fail(HE_ERR_ARG, "tuning: groups must be 1, 2 or 3");
+    if (t.fin_parts != 1 && t.fin_parts != 2 && t.fin_parts != 4)
+        return fail(HE_ERR_ARG, "tuning: fin_parts must be 1, 2 or 4");
     return HE_OK;
 }
 }  // namespace
@@ -1184,6 +1187,14 @@ he_status he_plan_workspace_bytes(const he_layer_call *calls, uint32_t ncalls, s
 namespace {
 he_status plan_build_grouped(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning &tu, he_plan_t *out);
 
+// finishing items per output polynomial of a split-form Conv call: the
+// tuning's fin_parts, fewer where a part would hold under 4 residue classes
+uint32_t fin_parts_of(const he_plan_tuning &tu, uint32_t s) {
+    uint32_t np = tu.fin_parts;
+    while (np > 1 && s / np < 4u) np >>= 1;
+    return np;
+}
+
 // Builds a plan, or with ws_only set only validates the calls and returns the
 // workspace the plan would own (nothing allocated; d_in / d_out may be NULL;
 // with check_overlaps, the buffers are also checked for overlaps).
@@ -1237,6 +1248,7 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         if (!aligned16(c.d_in) || !aligned16(c.d_out)) return fail(HE_ERR_ARG, "call %u: buffers must be 16-byte aligned", i);
         CallDesc &cd = descs[i];
         memset(&cd, 0, sizeof(cd));
+        cd.fin_parts = 1;
         const RingView &r = p->ring;
         ConvGeo &g = cd.g;
         g.bank = f->bank;
@@ -1491,6 +1503,7 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
                 for (uint32_t l = 0; l < g.L; ++l)
                     for (uint32_t col = 0; col < g.ncols; ++col) fin.push_back({fcost, ChanItem{i, h, l, col}});
         } else if (cd.split) {
+            cd.fin_parts = fin_parts_of(tu, g.s);
             cd.z = pl->ws + z_off[i];
             const int cls = he_mac_class(g.gp, g.cs);
             const uint32_t T = g.N >> g.logTS;
@@ -1501,10 +1514,13 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
                     for (uint32_t l = 0; l < g.L; ++l)
                         for (uint32_t n0 = 0; n0 < g.co; n0 += g.nc)
                             mac[cls].push_back({mcost, ChanItem{i, pt * T + t, l, n0}});
-            const double fcost = 3.0 * (N / 2.0) * g.logM + N;
+            // finishing items (call, h | part << 16, limb, column)
+            const double fcost = (3.0 * (N / 2.0) * g.logM + N) / cd.fin_parts;
             for (uint32_t h = 0; h < g.H; ++h)
-                for (uint32_t l = 0; l < g.L; ++l)
-                    for (uint32_t col = 0; col < g.ncols; ++col) fin.push_back({fcost, ChanItem{i, h, l, col}});
+                for (uint32_t pt = 0; pt < cd.fin_parts; ++pt)
+                    for (uint32_t l = 0; l < g.L; ++l)
+                        for (uint32_t col = 0; col < g.ncols; ++col)
+                            fin.push_back({fcost, ChanItem{i, h | (pt << 16), l, col}});
         } else {
             const int cls = cd.nj == 1 ? 4 : cd.nj == 2 ? 0 : cd.nj == 4 ? 1 : cd.nj == 8 ? 2 : 3;
             const double cost = (double)g.G * N * cd.nj + 3.0 * cd.nj * (g.M / 2.0) * g.logM;
@@ -1678,8 +1694,9 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         for (auto &it : fin) {
             items.push_back(it.second);
             const CallDesc &cd = descs[it.second.call];
+            const uint32_t sp = cd.g.s / std::max(1u, cd.fin_parts);
             const size_t sm = cd.kind == HE_KIND_FC ? (size_t)padded_words(cd.g.N) * 4u
-                                                    : (size_t)std::min(cd.g.s, cd.g.co) * fin_stride(cd.g.M, cd.g.s) * 4u;
+                                                    : (size_t)std::min(sp, cd.g.co) * fin_stride(cd.g.M, sp) * 4u;
             pl->smem_fin = std::max(pl->smem_fin, sm);
         }
         pl->n_fin = (uint32_t)items.size();
@@ -2046,6 +2063,7 @@ he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t
         };
         if (has_split) try_knob(&he_plan_tuning::split, {1u, 0u});
         if (ncalls > 1) try_knob(&he_plan_tuning::groups, {1u, 2u, 3u});
+        if (has_split && cur.split) try_knob(&he_plan_tuning::fin_parts, {1u, 2u, 4u});
         if (has_split && cur.split) {
             try_knob(&he_plan_tuning::mac_item_kb, {128u, 64u, 32u});
             try_knob(&he_plan_tuning::mac_ctas_per_sm, {2u, 1u});

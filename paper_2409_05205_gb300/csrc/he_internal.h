@@ -219,6 +219,10 @@ struct CallDesc {
     // last of an output polynomial's L limb items to finish rescales it
     const RescaleCall *rs;
     uint32_t *rs_cnt;         // per output polynomial: limb items finished in this run
+    // split-form Conv: finishing items per (output polynomial, limb, column),
+    // each over 1 / fin_parts of the s residue classes (item field a = h |
+    // part << 16); 1 for every other call
+    uint32_t fin_parts;
     // word counts of the call's buffers, for the device-side bounds checks
     // (he_plan_set_checks): inputs at x_coeff, NTT-domain inputs at g.x,
     // outputs at g.out, folded sums at z

@@ -1407,7 +1407,7 @@ __device__ __forceinline__ bool fin_item_in_bounds(const CallDesc &cd, const Cha
         const size_t o = ((size_t)(((c >> 1) * g.P + jp) * 2u + (c & 1u)) * L + l) * N;
         return in_range(g.x + ((size_t)c * L + l) * N, N, g.x, cd.x_words) && in_range(g.out + o, N, g.out, cd.out_words);
     }
-    const uint32_t h = it.a, l = it.l, c = it.b, sh = min(g.s, g.co - h * g.s);
+    const uint32_t h = it.a & 0xFFFFu, l = it.l, c = it.b, sh = min(g.s, g.co - h * g.s);
     const size_t zs = (((size_t)l * g.ncols + c) * g.co + h * g.s) * g.M;
     const size_t zlast = cd.zt ? 0 : zs + (size_t)(cd.g.parts - 1u) * L * g.ncols * g.co * g.M;
     const bool zok = cd.zt ? in_range(cd.z, (size_t)L * g.ncols * g.M * g.co, cd.z, cd.z_words)
@@ -1419,8 +1419,8 @@ __device__ __forceinline__ bool fin_item_in_bounds(const CallDesc &cd, const Cha
 }
 
 // The rescale fused into the finishing kernel: once a CTA has written limb
-// l of output polynomial `poly`, it counts itself in; the last of the
-// polynomial's L limb items rescales the whole polynomial (all L limbs are
+// l of output polynomial `poly` (or its part of it), it counts itself in; the
+// last of the polynomial's L x fin_parts items rescales the whole polynomial (all L limbs are
 // then written and, just written, still in L2) and resets the counter for
 // the next run.  No CTA waits on another.
 __device__ __forceinline__ void fin_rescale(const CallDesc &cd, size_t poly) {
@@ -1429,7 +1429,7 @@ __device__ __forceinline__ void fin_rescale(const CallDesc &cd, size_t poly) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t prior = atomicAdd(cd.rs_cnt + poly, 1u);
-        last = prior + 1u == cd.g.L ? 1u : 0u;
+        last = prior + 1u == cd.g.L * cd.fin_parts ? 1u : 0u;
         if (last) cd.rs_cnt[poly] = 0u;
     }
     __syncthreads();
@@ -1447,17 +1447,23 @@ __device__ __forceinline__ size_t fin_out_poly(const CallDesc &cd, uint32_t a, u
     return cd.g.masked ? (size_t)c * H + a : ((size_t)(c >> 1) * H + a) * 2u + (c & 1u);
 }
 
-// Conv finishing item (call, h, l, column): the parts' folded sums of the
-// s channels of output polynomial h, their length-M inverse transforms,
-// and the extracted polynomial's limb l.
+// Conv finishing item (call, h | part << 16, l, column): the group parts'
+// folded sums of the channels of output polynomial h whose residue classes
+// fall in this item's part (classes r in [part sp, part sp + sp), sp =
+// s / fin_parts; all s with one part), their length-M inverse transforms,
+// and those classes' coefficients of the extracted polynomial's limb l.
 __device__ __forceinline__ void fin_conv_body(const CallDesc &cd, const LimbK &K, const ChanItem &it,
                                               uint4 *smem4) {
     uint32_t *Zs = reinterpret_cast<uint32_t *>(smem4);
-    const uint32_t h = it.a, l = it.l, c = it.b;
+    const uint32_t h = it.a & 0xFFFFu, part = it.a >> 16, l = it.l, c = it.b;
     const uint32_t N = cd.g.N, co = cd.g.co, s = cd.g.s, logs = cd.g.logs, M = cd.g.M, logM = cd.g.logM,
                    mult = cd.g.mult;
-    const uint32_t sh = min(s, co - h * s);
-    const uint32_t PS = fin_stride(M, s);
+    const uint32_t sh0 = min(s, co - h * s);
+    const uint32_t np = cd.fin_parts, sp = s / np, lsp = he_log2_dev(sp);
+    // channels rr (class rr * mult) of this part: [lo, hi)
+    const uint32_t lo = min(sh0, (part * sp + mult - 1u) / mult), hi = min(sh0, (part * sp + sp + mult - 1u) / mult);
+    const uint32_t sh = hi - lo;
+    const uint32_t PS = fin_stride(M, sp);
     // sh*M words, 4 at a time, 8 loads in flight per thread
     const uint32_t nq = (sh << logM) >> 2;
     if (cd.zt) {
@@ -1485,8 +1491,8 @@ __device__ __forceinline__ void fin_conv_body(const CallDesc &cd, const LimbK &K
             }
         }
     }
-    // split form: the parts' folded sums [parts][L][ncols][co][M], added
-    const uint32_t *zsrc = cd.z + (((size_t)l * cd.g.ncols + c) * co + h * s) * M;
+    // split form: the group parts' folded sums [parts][L][ncols][co][M], added
+    const uint32_t *zsrc = cd.z + (((size_t)l * cd.g.ncols + c) * co + h * s + lo) * M;
     const size_t zpart4 = ((size_t)cd.g.L * cd.g.ncols * co * M) >> 2;
     for (uint32_t q0 = 0; q0 < (cd.zt ? 0u : nq); q0 += 8u * blockDim.x) {
         uint4 v[8];
@@ -1522,25 +1528,32 @@ __device__ __forceinline__ void fin_conv_body(const CallDesc &cd, const LimbK &K
     __syncthreads();
     intt_c(Zs, sh, PS, logM, cd.g.tw_inv + (size_t)l * N, K.q);
     uint32_t *o = out_poly(cd.g, c, h, l);
+    // this part's coefficients: j -> k = (j / sp) s + part sp + j mod sp,
+    // runs of sp consecutive words (every coefficient with one part)
+    const uint32_t nk = N / np, kp = part * sp;
     if (cd.g.masked) {
         // masked server / client step: [B][H][L][N] output, + Delta_Q sh'_h on every slot (server)
-        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+        for (uint32_t j = threadIdx.x; j < nk; j += blockDim.x) {
+            const uint32_t k = ((j >> lsp) << logs) + kp + (j & (sp - 1u));
             const uint32_t r = k & (s - 1), rr = r / mult;
             uint32_t v = share_term(cd.g, K, c, h, k);
-            if (r == rr * mult && rr < sh) {
-                v += red_2q(Zs[rr * PS + pidx(k >> logs)], K.q);
+            if (r == rr * mult && rr >= lo && rr < hi) {
+                v += red_2q(Zs[(rr - lo) * PS + pidx(k >> logs)], K.q);
                 v = min(v, v - K.q);
             }
             o[k] = v;
         }
-    } else if (mult == 1 && sh == s) {
-        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x)
-            o[k] = red_2q(Zs[(k & (s - 1)) * PS + pidx(k >> logs)], K.q);
+    } else if (mult == 1 && sh == sp) {
+        for (uint32_t j = threadIdx.x; j < nk; j += blockDim.x) {
+            const uint32_t k = ((j >> lsp) << logs) + kp + (j & (sp - 1u));
+            o[k] = red_2q(Zs[(j & (sp - 1u)) * PS + pidx(k >> logs)], K.q);
+        }
     } else {
-        for (uint32_t k = threadIdx.x; k < N; k += blockDim.x) {
+        for (uint32_t j = threadIdx.x; j < nk; j += blockDim.x) {
+            const uint32_t k = ((j >> lsp) << logs) + kp + (j & (sp - 1u));
             const uint32_t r = k & (s - 1), rr = r / mult;
             uint32_t v = 0;
-            if (r == rr * mult && rr < sh) v = red_2q(Zs[rr * PS + pidx(k >> logs)], K.q);
+            if (r == rr * mult && rr >= lo && rr < hi) v = red_2q(Zs[(rr - lo) * PS + pidx(k >> logs)], K.q);
             o[k] = v;
         }
     }
@@ -1565,7 +1578,7 @@ __global__ void __launch_bounds__(kFinThreads, 3) k_plan_fin(const CallDesc *__r
     } else {
         fin_conv_body(cd, K, it, smem4);
     }
-    if (cd.rs) fin_rescale(cd, fin_out_poly(cd, it.a, it.b));
+    if (cd.rs) fin_rescale(cd, fin_out_poly(cd, it.a & 0xFFFFu, it.b));
 }
 
 // Opt a kernel in to `bytes` of dynamic shared memory once per (kernel,

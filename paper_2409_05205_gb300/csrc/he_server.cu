@@ -11,8 +11,11 @@
 // layer wait and form its next batch, which is issued when the running one
 // completes (or at once when max_batch of them wait); layers with nothing
 // running are issued at once, oldest waiting request first -- and runs
-// each batch on one of several streams: host->device copies, the layer as a one-call plan,
-// device->host copies, then a host callback.  Device buffers ("lanes": the
+// each batch on one of several streams: host->device copies, the layer as a
+// one-call plan, device->host copies, then an event of the batch's lane that
+// the scheduler polls (no host callbacks: the driver runs every stream's
+// callbacks on one thread, one after another, and completions waited behind
+// each other under load).  Device buffers ("lanes": the
 // batch's inputs and outputs and the plan's workspace) are allocated under an
 // HBM budget and reused.  A lane's size is known before anything is
 // allocated, so device memory never exceeds the budget; when the budget is
@@ -31,10 +34,16 @@
 #include <thread>
 #include <vector>
 
+#include <sys/prctl.h>
+
 #include "he_internal.h"
 #include <nvtx3/nvToolsExt.h>
 
 namespace {
+
+// polling period of the in-flight batches' events; the scheduler thread's
+// timer slack is set to 1 us so that the sleep is about this long
+constexpr int kPollUs = 5;
 
 double now_ms() {
     using namespace std::chrono;
@@ -65,6 +74,7 @@ struct Lane {
     uint32_t model, layer, bucket;
     uint32_t *d_in = nullptr, *d_out = nullptr;
     he_plan_t plan = nullptr;
+    cudaEvent_t done = nullptr;  // recorded after the batch's last copy
     size_t bytes = 0;
     bool busy = false;
 };
@@ -77,16 +87,10 @@ struct Server {
     std::vector<cudaStream_t> streams;
     uint32_t next_stream = 0;
 
-    // Completed batches, pushed by the CUDA callback thread.  The callback
-    // takes only cb_mu, which is never held across a CUDA call, so a CUDA
-    // call that waits for streams (cudaFree, a pageable copy) cannot wait on
-    // a callback that waits on a lock.
-    std::mutex cb_mu;
-    std::condition_variable cv_sched;
-    std::vector<Batch *> completed;
-
     std::mutex mu;  // everything below; the scheduler holds it across CUDA calls
+    std::condition_variable cv_sched;  // a submission or a stop
     std::condition_variable cv_done;
+    std::vector<Batch *> flight;       // launched batches, polled through their lane's event
     std::map<uint64_t, Req *> reqs;
     std::map<std::pair<uint32_t, uint32_t>, std::deque<Req *>> queues;  // (model, layer) -> waiting
     std::map<std::pair<uint32_t, uint32_t>, uint32_t> running;          // (model, layer) -> batches in flight
@@ -110,15 +114,6 @@ struct Batch {
     bool ok;
 };
 
-void CUDART_CB on_batch_done(void *p) {
-    // runs on a CUDA callback thread: no CUDA calls here
-    Batch *b = static_cast<Batch *>(p);
-    Server *s = b->s;
-    std::lock_guard<std::mutex> lk(s->cb_mu);
-    s->completed.push_back(b);
-    s->cv_sched.notify_one();
-}
-
 // largest power of two <= n, at most max_batch
 uint32_t bucket_of(uint32_t n, uint32_t max_batch) {
     uint32_t b = 1;
@@ -127,6 +122,7 @@ uint32_t bucket_of(uint32_t n, uint32_t max_batch) {
 }
 
 void free_lane(Server *s, Lane *l) {
+    if (l->done) cudaEventDestroy(l->done);
     he_plan_destroy(l->plan);
     cudaFree(l->d_in);
     cudaFree(l->d_out);
@@ -191,7 +187,10 @@ Lane *get_lane(Server *s, uint32_t model, uint32_t layer, uint32_t bucket, bool 
     }
     c.d_in = l->d_in;
     c.d_out = l->d_out;
-    if (he_plan_create(&c, 1, &l->plan) != HE_OK) {
+    if (cudaEventCreateWithFlags(&l->done, cudaEventDisableTiming) != cudaSuccess ||
+        he_plan_create(&c, 1, &l->plan) != HE_OK) {
+        cudaGetLastError();
+        if (l->done) cudaEventDestroy(l->done);
         cudaFree(l->d_in);
         cudaFree(l->d_out);
         delete l;
@@ -222,10 +221,9 @@ bool launch(Server *s, Lane *lane, std::vector<Req *> &rs) {
     for (size_t j = 0; j < rs.size() && ok; ++j)
         ok = cudaMemcpyAsync(rs[j]->out[lane->layer], lane->d_out + j * ml.out_words, ml.out_words * sizeof(uint32_t),
                              cudaMemcpyDeviceToHost, st) == cudaSuccess;
-    ok = ok && cudaLaunchHostFunc(st, on_batch_done, b) == cudaSuccess;
+    ok = ok && cudaEventRecord(lane->done, st) == cudaSuccess;
     if (!ok) {
-        // nothing will call back: let what was issued drain, then fail the
-        // batch here
+        // let what was issued drain, then fail the batch here
         cudaStreamSynchronize(st);
         cudaGetLastError();
         b->ok = false;
@@ -235,6 +233,7 @@ bool launch(Server *s, Lane *lane, std::vector<Req *> &rs) {
     }
     const double t = now_ms();
     for (Req *r : rs) r->t_launch = t;
+    s->flight.push_back(b);
     lane->busy = true;
     ++s->inflight;
     ++s->running[{lane->model, lane->layer}];
@@ -278,14 +277,29 @@ void finish_batch(Server *s, Batch *b) {
 
 void scheduler(Server *s) {
     cudaSetDevice(s->cfg.device);
+    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);  // 1 us: short polling sleeps stay short
+    std::unique_lock<std::mutex> lk(s->mu);
     for (;;) {
+        // completions first: they free lanes and move requests to their next
+        // layer.  A batch is done when its lane's event is; an error there
+        // fails the batch's requests.
         std::vector<Batch *> done;
-        {
-            std::lock_guard<std::mutex> ck(s->cb_mu);
-            done.swap(s->completed);
+        for (size_t i = 0; i < s->flight.size();) {
+            Batch *b = s->flight[i];
+            const cudaError_t q = cudaEventQuery(b->lane->done);
+            if (q == cudaErrorNotReady) {
+                ++i;
+                continue;
+            }
+            if (q != cudaSuccess) {
+                cudaGetLastError();
+                b->ok = false;
+                snprintf(s->error, sizeof(s->error), "batch failed on the device");
+            }
+            done.push_back(b);
+            s->flight[i] = s->flight.back();
+            s->flight.pop_back();
         }
-        std::unique_lock<std::mutex> lk(s->mu);
-        // completions first: they free lanes and move requests to their next layer
         done.insert(done.end(), s->failed_launch.begin(), s->failed_launch.end());
         s->failed_launch.clear();
         for (Batch *b : done) finish_batch(s, b);
@@ -324,11 +338,17 @@ void scheduler(Server *s) {
             launch(s, lane, rs);
             progress = true;
         }
-        const bool retry = !s->failed_launch.empty();
-        lk.unlock();
-        if (retry) continue;
-        std::unique_lock<std::mutex> ck(s->cb_mu);
-        if (s->completed.empty()) s->cv_sched.wait_for(ck, std::chrono::milliseconds(1));
+        if (!s->failed_launch.empty()) continue;
+        if (s->flight.empty()) {
+            // nothing on the GPU: sleep until a submission (or a stop)
+            s->cv_sched.wait_for(lk, std::chrono::milliseconds(1));
+        } else {
+            // batches in flight: poll again after a few microseconds, with the
+            // lock released so that submissions and waits go through
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(kPollUs));
+            lk.lock();
+        }
     }
 }
 

@@ -46,10 +46,12 @@ namespace {
 constexpr uint32_t kTcThreads = 512;         // 16 warps
 constexpr uint32_t kWarpE0 = 6, kWarpB0 = 14;  // first epilogue / B-builder warp (A builders: warps 2..5)
 constexpr uint32_t kWStageBytes = 16384;
-constexpr uint32_t kWStages = 6;
+constexpr uint32_t kWStages = 5;
 constexpr uint32_t kASlots = 16;               // A slots of 16 TMEM columns (one K-step)
 constexpr uint32_t kTmemCols = 512;            // D: 2 x 2 x 64 columns; A: 16 x 16 columns
 constexpr uint32_t kXRawBytes = kTcMaxK * kTcCols * 4;      // 16 KB
+constexpr uint32_t kXSlots = 4;  // blocks of inputs in flight: one input copy per block of one
+                                 // tile (K = 64) must not wait for the copy latency
 constexpr uint32_t kBOpBytes = 64 * kTcMaxK * 2;            // 32 KB
 constexpr uint32_t kXchgBytes = kTcCols * kTcRows * 4;      // 4 KB
 constexpr uint32_t kTcSpin = 1u << 16;   // tests of a phase before a wait gives up (each up to kSuspendNs)
@@ -57,7 +59,7 @@ constexpr uint32_t kMagic = 0x33000000u;       // bits of 2^-25 as fp32: 2^23 un
 
 struct TcBars {
     uint64_t w_full[kWStages], w_empty[kWStages];
-    uint64_t x_full[2], x_empty[2];
+    uint64_t x_full[kXSlots], x_empty[kXSlots];
     uint64_t b_full[2], b_empty[2];
     uint64_t a_full[kASlots], a_empty[kASlots];
     uint64_t d_full[2], d_empty[2];
@@ -69,7 +71,7 @@ constexpr uint32_t kHdrBytes = 1024;
 static_assert(sizeof(TcBars) <= kHdrBytes, "barrier header");
 constexpr uint32_t kOffW = kHdrBytes;
 constexpr uint32_t kOffX = kOffW + kWStages * kWStageBytes;
-constexpr uint32_t kOffB = kOffX + 2 * kXRawBytes;
+constexpr uint32_t kOffB = kOffX + kXSlots * kXRawBytes;
 constexpr uint32_t kOffXchg = kOffB + 2 * kBOpBytes;
 constexpr uint32_t kTcSmem = kOffXchg + 2 * kXchgBytes;
 
@@ -171,12 +173,6 @@ __device__ __forceinline__ uint32_t limb_pair(uint32_t a, uint32_t b) {
     return __byte_perm(a, b, sel) & 0x00FF00FFu;
 }
 
-#define TC_ST32_CONST(base, k)                                                                     \
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "                                             \
-                 "{%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" \
-                 ::"r"(base), "r"(k)                                                                        \
-                 : "memory")
-
 #define TC_LD16(base, v)                                                                                 \
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];" \
                  : "=r"((v)[0]), "=r"((v)[1]), "=r"((v)[2]), "=r"((v)[3]), "=r"((v)[4]), "=r"((v)[5]),    \
@@ -186,12 +182,12 @@ __device__ __forceinline__ uint32_t limb_pair(uint32_t a, uint32_t b) {
 
 // The epilogue of one tile for this thread's row: 4 columns of its two
 // limbs p (limb 2*high + p), v[p][4c + j] = D_p for (column c, limb j) in units of
-// 2^-48, become val = sum_{p,j} 2^(8(p+j)) D_pj < 2^57 (not reduced).  Tiles
-// with K <= 128 accumulate on top of 2^-25 = 2^23 units (the tensor memory is
-// prefilled), where the fp32 step is exactly one unit: the bits are 2^-25's
-// bits + D and need no conversion; the 2^-25 terms are removed once from the
-// recombined value (kMagicSum).  Longer tiles accumulate from 0 (D < 2^24)
-// and convert with a multiplication by 2^48 and F2I.
+// 2^-48, become val = sum_{p,j} 2^(8(p+j)) D_pj < 2^57 (not reduced).  Every
+// tile accumulates from 0.  With K <= 128, D < 2^23 units: one fp32 add of
+// 2^-25 = 2^23 units lands in [2^-25, 2^-24), where the fp32 step is exactly
+// one unit, so the sum's bits are 2^-25's bits + D (exact, no conversion);
+// the 2^-25 terms are removed once from the recombined value (kMagicSum).
+// Longer tiles (D < 2^24) convert with a multiplication by 2^48 and F2I.
 constexpr uint64_t kMagicSum = (uint64_t)kMagic * (1ull + (2ull << 8) + (2ull << 16) + (2ull << 24) + (1ull << 32));
 template <bool kBig>
 __device__ __forceinline__ void recombine4(const uint32_t (&v)[2][16], uint64_t *val) {
@@ -202,7 +198,8 @@ __device__ __forceinline__ void recombine4(const uint32_t (&v)[2][16], uint64_t 
         for (int p = 0; p < 2; ++p)
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                u[p][j] = kBig ? __float2uint_rz(__uint_as_float(v[p][4 * c + j]) * 281474976710656.0f) : v[p][4 * c + j];
+                u[p][j] = kBig ? __float2uint_rz(__uint_as_float(v[p][4 * c + j]) * 281474976710656.0f)
+                               : __float_as_uint(__uint_as_float(v[p][4 * c + j]) + __uint_as_float(kMagic));
         const uint32_t S1 = u[0][1] + u[1][0], S2 = u[0][2] + u[1][1], S3 = u[0][3] + u[1][2];
         // u00 + S1 2^8 + S2 2^16 + S3 2^24 (wide multiply-adds) + u13 2^32
         uint64_t x = (uint64_t)S1 * 256u + u[0][0];
@@ -249,9 +246,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
             bar_init(&bars.w_full[i], 1);
             bar_init(&bars.w_empty[i], 4);
         }
-        for (uint32_t i = 0; i < 2; ++i) {
+        for (uint32_t i = 0; i < kXSlots; ++i) {
             bar_init(&bars.x_full[i], 1);
             bar_init(&bars.x_empty[i], 2);
+        }
+        for (uint32_t i = 0; i < 2; ++i) {
             bar_init(&bars.b_full[i], 2);
             bar_init(&bars.b_empty[i], 1);
             bar_init(&bars.d_full[i], 1);
@@ -306,8 +305,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                 const TcCall &C = calls[item.call];
                 const uint32_t nch = C.co / kTcRows, tile_words = C.K * kTcRows;
                 for (uint32_t b = item.b0; ok && b < item.b0 + item.nb; ++b) {
-                    const uint32_t xb = xs & 1u;
-                    if (xs >= 2 && !bar_wait(&bars.x_empty[xb], ((xs >> 1) - 1u) & 1u, abort)) {
+                    const uint32_t xb = xs % kXSlots;
+                    if (xs >= kXSlots && !bar_wait(&bars.x_empty[xb], ((xs / kXSlots) - 1u) & 1u, abort)) {
                         ok = false;
                         break;
                     }
@@ -338,8 +337,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                 }
             }
             // every copy lands before shared memory is released (only the
-            // last two input copies and the last kWStages stages can be in flight)
-            for (uint32_t i = xs > 2 ? xs - 2 : 0; i < xs; ++i) bar_drain(&bars.x_full[i & 1u], (i >> 1) & 1u);
+            // last kXSlots input copies and the last kWStages stages can be in flight)
+            for (uint32_t i = xs > kXSlots ? xs - kXSlots : 0; i < xs; ++i)
+                bar_drain(&bars.x_full[i % kXSlots], (i / kXSlots) & 1u);
             for (uint32_t i = ws > kWStages ? ws - kWStages : 0; i < ws; ++i)
                 bar_drain(&bars.w_full[i % kWStages], (i / kWStages) & 1u);
         }
@@ -363,15 +363,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                     tc_fence_after();
                     const uint32_t baddr = su32(bop + bb * kBOpBytes);
                     for (uint32_t ch = 0; ok && ch < nch; ++ch) {
-                        // the epilogue refills a buffer with 2^23 (and frees it) after
-                        // reading it, and fills both once at the start
+                        // the epilogue frees a buffer once it has read it (the first
+                        // K-step overwrites it)
                         const uint32_t db = ds & 1u;
                         if (!bar_wait(&bars.d_empty[db], (ds >> 1) & 1u, abort)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t acc0 = C.K > 128u ? 0u : 1u;
                         for (uint32_t ks = 0; ks < nks; ++ks) {
                             const uint32_t slot = as % kASlots;
                             if (!bar_wait(&bars.a_full[slot], (as / kASlots) & 1u, abort)) {
@@ -383,7 +382,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
 #pragma unroll
                             for (uint32_t p = 0; p < 2; ++p)
                                 tc_mma(tmem + 128u * db + 64u * p, tmem + 256u + 16u * slot + 8u * p, bdesc, idesc,
-                                       ks > 0 ? 1u : acc0);
+                                       ks > 0 ? 1u : 0u);
                             tc_commit(&bars.a_empty[slot]);
                             ++as;
                         }
@@ -500,13 +499,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
         // B rows (and so D columns) are ordered (hc, column c % 8, limb j): this
         // warp's accumulators are D_p columns 32 hc .. 32 hc + 31
         const uint32_t lrow = tmem + ((32u * sp) << 16) + 32u * hc;
-        // prefill both accumulator buffers with 2^23 and free them
-#pragma unroll
-        for (uint32_t db = 0; db < 2; ++db)
-#pragma unroll
-            for (uint32_t p = 0; p < 2; ++p) TC_ST32_CONST(lrow + 128u * db + 64u * p, kMagic);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        tc_fence_before();
+        // both accumulator buffers start free
         __syncwarp();
         if (lane == 0) {
             bar_arrive(&bars.d_empty[0]);
@@ -543,18 +536,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
 #pragma unroll
                             for (uint32_t p = 0; p < 2; ++p) TC_LD16(lrow + 128u * db + 64u * p + 16u * g4, v[p]);
                             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                            if (g4 == 1) {  // the warp's accumulators are in registers: free the buffer
+                                tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) bar_arrive(&bars.d_empty[db]);
+                            }
                             if (big)
                                 recombine4<true>(v, val + 4 * g4);
                             else
                                 recombine4<false>(v, val + 4 * g4);
                         }
-                        // refill with 2^-25 and free the buffer
-#pragma unroll
-                        for (uint32_t p = 0; p < 2; ++p) TC_ST32_CONST(lrow + 128u * db + 64u * p, kMagic);
-                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) bar_arrive(&bars.d_empty[db]);
                         // columns 0..3 are finished by the low rows, 4..7 by the high
                         // rows: each side sends its reduced share of the other four
                         {
@@ -610,8 +601,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
             const uint32_t kgn = C.K / 8u, ncols = C.ncols, s = C.s, logs = C.logs;
             const uint32_t lnh = ncols > 8u ? 1u : 0u, npass = kgn << lnh;  // halves of 8 columns: 1 or 2
             for (uint32_t b = item.b0; b < item.b0 + item.nb; ++b) {
-                const uint32_t xb = xs & 1u, bb = bs & 1u;
-                if (!bar_wait(&bars.x_full[xb], (xs >> 1) & 1u, abort)) {
+                const uint32_t xb = xs % kXSlots, bb = bs & 1u;
+                if (!bar_wait(&bars.x_full[xb], (xs / kXSlots) & 1u, abort)) {
                     ok = false;
                     break;
                 }

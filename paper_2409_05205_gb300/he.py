@@ -60,7 +60,7 @@ class he_op_counts(ctypes.Structure):
 
 class he_plan_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("split", "mac_item_kb", "mac_ctas_per_sm", "fused_max_nj",
-                                               "tc_min_batch", "fc_direct", "groups")]
+                                               "tc_min_batch", "fc_direct", "groups", "fin_parts")]
 
 
 class he_plan_info(ctypes.Structure):

@@ -34,19 +34,23 @@ def test_layer_family_full_size(ci, co, hw, f, pad, N, L):
     ps, psis, lay, cts, F, desc = U.conv_case(N, L, ci, co, hw, hw, B, seed=ci + co + f, fh=f, fw=f, pad=pad)
     with U.params(N, L) as p, U.conv_bank(p, desc, F) as fb:
         single = U.run_conv(p, fb, cts, H.HE_OUT_EXTRACTED, lay["H"])
-        d_in, d_out = U.to_dev(cts), U.empty_dev(single.shape)
-        plan = H.he_plan_create([(fb, d_in, H.HE_COEFF, d_out, B)])
-        # s >= 4: the split form, groups in parts (G = 8: the larger input buffers)
-        if lay["s"] >= 4:
-            assert H.he_plan_query(plan, 1)["form"][0] == 1
-        try:
-            H.he_plan_run(plan, torch.cuda.current_stream())
-            H.he_sync(torch.cuda.current_stream())
-            H.he_plan_check(plan)
-        finally:
-            H.he_plan_destroy(plan)
-        got = U.from_dev(d_out).reshape(single.shape)
-    np.testing.assert_array_equal(got, single)
+        d_in = U.to_dev(cts)
+        # finishing items over all residue classes, and over quarters of them
+        for fin_parts in (1, 4):
+            d_out = U.empty_dev(single.shape)
+            plan = H.he_plan_create_tuned([(fb, d_in, H.HE_COEFF, d_out, B)],
+                                          dict(H.he_plan_tuning_default(), fin_parts=fin_parts))
+            # s >= 4: the split form, groups in parts (G = 8: the larger input buffers)
+            if lay["s"] >= 4:
+                assert H.he_plan_query(plan, 1)["form"][0] == 1
+            try:
+                H.he_plan_run(plan, torch.cuda.current_stream())
+                H.he_sync(torch.cuda.current_stream())
+                H.he_plan_check(plan)
+            finally:
+                H.he_plan_destroy(plan)
+            got = U.from_dev(d_out).reshape(single.shape)
+            np.testing.assert_array_equal(got, single, err_msg=f"fin_parts {fin_parts}")
     l = (ci + co) % L
     ref = O.conv_layer(np.ascontiguousarray(cts[:, :, :, l:l + 1]), F, [ps[l]], [psis[l]], lay, O.OUT_EXTRACTED,
                        tier="ntt")

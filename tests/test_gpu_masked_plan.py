@@ -99,9 +99,10 @@ class _Case:
         return U.from_dev(d).reshape(self.out_shape)
 
 
-def _run_plan(H, cases, stream, graph=False, fc_direct=1):
+def _run_plan(H, cases, stream, graph=False, fc_direct=1, fin_parts=1):
     torch = U.torch_cuda()
-    plan = H.he_plan_create_tuned([c.call() for c in cases], dict(H.he_plan_tuning_default(), fc_direct=fc_direct))
+    plan = H.he_plan_create_tuned([c.call() for c in cases],
+                                  dict(H.he_plan_tuning_default(), fc_direct=fc_direct, fin_parts=fin_parts))
     try:
         info = H.he_plan_query(plan, len(cases))
         outs = []
@@ -142,9 +143,10 @@ def _mixed(H, p, N, ps, psis, B=1, in_ntt=False):
 
 
 # fc_direct: the FC windows computed directly (coefficient-domain inputs)
-# or through the transforms; the words are the same
-@pytest.mark.parametrize("in_ntt,fc_direct", [(False, 1), (True, 1), (False, 0)])
-def test_masked_and_client_calls_in_one_plan_match_single_calls(in_ntt, fc_direct):
+# or through the transforms; fin_parts: finishing items over 1, 2 or 4
+# shares of the residue classes; the words are the same
+@pytest.mark.parametrize("in_ntt,fc_direct,fin_parts", [(False, 1, 1), (True, 1, 2), (False, 0, 4)])
+def test_masked_and_client_calls_in_one_plan_match_single_calls(in_ntt, fc_direct, fin_parts):
     H = U.he()
     torch = U.torch_cuda()
     N, L = 8192, 3
@@ -153,7 +155,7 @@ def test_masked_and_client_calls_in_one_plan_match_single_calls(in_ntt, fc_direc
     with U.params(N, L) as p:
         cases = _mixed(H, p, N, ps, psis, in_ntt=in_ntt)
         try:
-            info, outs = _run_plan(H, cases, s, fc_direct=fc_direct)
+            info, outs = _run_plan(H, cases, s, fc_direct=fc_direct, fin_parts=fin_parts)
             # B = 1 masked and client Conv calls run in the split form
             for i, c in enumerate(cases):
                 if c.kind != "plain" and not c.shape.get("fc"):

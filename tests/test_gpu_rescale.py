@@ -76,7 +76,8 @@ def test_rescale_argument_errors():
                          torch.cuda.current_stream())
 
 
-def test_plan_rescales_every_output():
+@pytest.mark.parametrize("fin_parts", [1, 2])
+def test_plan_rescales_every_output(fin_parts):
     """d_rescaled on plain and masked Conv calls of the split form, a Conv
     call of the fused form, an FC call whose window is computed directly and
     one on the transform path, in one plan: the words of the oracle's
@@ -84,7 +85,8 @@ def test_plan_rescales_every_output():
     kernel's per-polynomial counters reset themselves).  The outputs the
     finishing kernel writes are rescaled in its epilogue, the others by the
     rescale kernel; HE_PHASE_RESCALE reruns every call's rescale in that
-    kernel alone."""
+    kernel alone.  fin_parts = 2: each output polynomial's limbs are written
+    by two finishing items each, and the counters count all of them."""
     H = U.he()
     torch = U.torch_cuda()
     N, L, T = 4096, 3, U.T
@@ -115,7 +117,7 @@ def test_plan_rescales_every_output():
                      (banks[0], cts2, H.HE_COEFF, outs[2], 2, None, None, rsc[2]),
                      (banks[2], fct, H.HE_COEFF, outs[3], 2, None, None, rsc[3]),
                      (banks[2], fcn, H.HE_NTT, outs[4], 2, None, None, rsc[4])]
-            plan = H.he_plan_create(calls)
+            plan = H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), fin_parts=fin_parts))
             try:
                 info = H.he_plan_query(plan, len(calls))
                 # split Conv (scalar MAC), fused-form Conv, direct FC, FC on the transform path
