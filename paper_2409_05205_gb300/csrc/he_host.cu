@@ -1530,13 +1530,41 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         }
     }
     auto by_cost = [](const auto &x, const auto &y) { return x.first > y.first; };
+    {   // ordinary 4096-point transforms go two to an item (one per half of the CTA)
+        std::vector<std::pair<double, NttItem>> kept;
+        size_t open = SIZE_MAX;  // index in kept of an item waiting for its second transform
+        for (auto &c : ntt_cost) {
+            if (!c.second.src || c.second.logN != 12) {
+                kept.push_back(c);
+                continue;
+            }
+            if (open != SIZE_MAX) {
+                NttItem &o = kept[open].second;
+                o.call2 = c.second.call;
+                o.q2 = c.second.q;
+                o.src2 = c.second.src;
+                o.dst2 = c.second.dst;
+                o.tw2 = c.second.tw;
+                kept[open].first += c.first;
+                open = SIZE_MAX;
+            } else {
+                open = kept.size();
+                kept.push_back(c);
+            }
+        }
+        ntt_cost.swap(kept);
+    }
     std::vector<NttItem> ntt;
     std::stable_sort(ntt_cost.begin(), ntt_cost.end(), by_cost);
     for (auto &it : ntt_cost) {
         ntt.push_back(it.second);
         const ConvGeo &g = descs[it.second.call].g;
-        const size_t sm = descs[it.second.call].fc_direct ? (size_t)std::min(g.rpp, g.n_out) * 4u
-                                                          : (size_t)padded_words(g.N) * 4u;
+        // pairs of 4096-point transforms: two padded halves; 16384-point
+        // ordinary transforms: two padded 8192-word halves (ntt_fwd_16384)
+        const size_t words = it.second.src2 ? 2u * padded_words(4096)
+                             : (it.second.src && g.logN == 14) ? 2u * padded_words(8192)
+                                                               : padded_words(g.N);
+        const size_t sm = descs[it.second.call].fc_direct ? (size_t)std::min(g.rpp, g.n_out) * 4u : words * 4u;
         pl->smem_ntt = std::max(pl->smem_ntt, sm);
     }
     pl->n_ntt = (uint32_t)ntt.size();

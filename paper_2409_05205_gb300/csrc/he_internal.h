@@ -317,6 +317,12 @@ struct NttItem {
     uint32_t *dst;            // its NTT-domain image
     const uint2 *tw;          // forward twiddles of its limb
     uint32_t q, logN;
+    // N = 4096: a second ordinary transform in the same item (threads 256 ..
+    // 511 of the CTA), or src2 == nullptr
+    uint32_t call2, q2;
+    const uint32_t *src2;
+    uint32_t *dst2;
+    const uint2 *tw2;
 };
 
 struct ChanItem {

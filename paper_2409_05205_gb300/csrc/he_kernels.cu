@@ -818,40 +818,62 @@ __device__ __forceinline__ void reg_stage16(uint32_t (&v)[16], const uint2 *__re
     }
 }
 
-// Forward negacyclic NTT of length 8192 by 512 threads in three register
-// phases.  Stage P (span 2^P) pairs i with i + 2^P (bit P of i clear) under
-// twiddle tw[2^(12-P) + (i >> (P+1))] -- the pairs, twiddles and butterfly
-// of ntt_fwd_c, so the output words are the same:
-//   A  thread t holds x[t + 512 j], j < 16: spans 4096 .. 512, the twiddles
-//      common to the whole CTA;
-//   one block-wide exchange through shared memory;
-//   B  warp w owns the 512-element sub-problem w (elements 512 w ..), lane l
-//      its elements l + 32 m: spans 256 .. 32, twiddles common to the warp;
+// Forward negacyclic NTT of length N = 2^LOGN (8192 or 4096) by T = N / 16
+// threads (thread t = 0 .. T-1 of the group) in three register phases.
+// Stage P (span 2^P) pairs i with i + 2^P (bit P of i clear) under twiddle
+// tw[2^(LOGN-1-P) + (i >> (P+1))] -- the pairs, twiddles and butterfly of
+// ntt_fwd_c, so the output words are the same:
+//   A  thread t holds x[t + T j], j < 16: spans N/2 .. T, the twiddles
+//      common to the whole group;
+//   one group-wide exchange through shared memory (__syncthreads for
+//      N = 8192; for N = 4096 named barrier BAR over the group's 256 threads,
+//      two polynomials per 512-thread CTA);
+//   B  warp w owns elements 512 w .. 512 w + 511 (one sub-problem of 512 for
+//      N = 8192, two of 256 for N = 4096), lane l its elements l + 32 m:
+//      spans 256 (N = 8192 only), 128, 64, 32, twiddles common to the warp;
 //   a transpose inside the warp's own shared memory (__syncwarp only);
 //   C  lane l holds elements 16 l + m: span 16 by a shuffle with lane l ^ 1,
 //      spans 8 .. 1 in registers; its 16 consecutive results leave as four
 //      128-bit stores.
 // The padded layout pidx keeps every shared-memory access conflict-free.
-__device__ __forceinline__ void ntt_fwd_8192_warp(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
-                                                  uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q) {
-    const uint32_t q2 = 2u * q, t = threadIdx.x, w = t >> 5, l = t & 31u;
+// FROM_SM: the input is already in `sm` (padded layout), not at src.  S
+// scales every stage's twiddle base 2^(LOGN-1-P): S = 1 for a whole
+// transform; S = 2 + h for half h of a 16384-point transform after its first
+// stage (ntt_fwd_16384), whose stage-P twiddles are tw[2^(13-P) (2 + h) / 2 +
+// (i >> (P+1))] with i the index within the half.
+template <int LOGN, int BAR, bool FROM_SM = false>
+__device__ __forceinline__ void ntt_fwd_3ph(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                            uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q, uint32_t t,
+                                            uint32_t S = 1) {
+    static_assert(LOGN == 12 || LOGN == 13, "three-phase transform: N = 4096 or 8192");
+    constexpr uint32_t T = 1u << (LOGN - 4), C = 1u << (LOGN - 12);  // threads; phase-C twiddle scale
+    const uint32_t q2 = 2u * q, w = t >> 5, l = t & 31u, CS = C * S;
     uint32_t v[16];
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __ldg(src + t + 512u * j);
-    reg_stage16<3>(v, tw + 1, q, q2);  // P = 12
-    reg_stage16<2>(v, tw + 2, q, q2);  // P = 11
-    reg_stage16<1>(v, tw + 4, q, q2);  // P = 10
-    reg_stage16<0>(v, tw + 8, q, q2);  // P = 9
+    for (int j = 0; j < 16; ++j) v[j] = FROM_SM ? sm[pidx(t + T * j)] : __ldg(src + t + T * j);
+    reg_stage16<3>(v, tw + 1 * S, q, q2);  // P = LOGN - 1
+    reg_stage16<2>(v, tw + 2 * S, q, q2);
+    reg_stage16<1>(v, tw + 4 * S, q, q2);
+    reg_stage16<0>(v, tw + 8 * S, q, q2);  // P = LOGN - 4
 #pragma unroll
-    for (int j = 0; j < 16; ++j) sm[pidx(t + 512u * j)] = v[j];
-    __syncthreads();
+    for (int j = 0; j < 16; ++j) sm[pidx(t + T * j)] = v[j];
+    if constexpr (BAR == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(T) : "memory");
     const uint32_t b0 = 512u * w;
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = sm[pidx(b0 + l + 32u * m)];
-    reg_stage16<3>(v, tw + 16 + w, q, q2);        // P = 8
-    reg_stage16<2>(v, tw + 32 + 2u * w, q, q2);   // P = 7
-    reg_stage16<1>(v, tw + 64 + 4u * w, q, q2);   // P = 6
-    reg_stage16<0>(v, tw + 128 + 8u * w, q, q2);  // P = 5
+    if constexpr (LOGN == 13) {
+        reg_stage16<3>(v, tw + 16 * S + w, q, q2);        // P = 8
+        reg_stage16<2>(v, tw + 32 * S + 2u * w, q, q2);   // P = 7
+        reg_stage16<1>(v, tw + 64 * S + 4u * w, q, q2);   // P = 6
+        reg_stage16<0>(v, tw + 128 * S + 8u * w, q, q2);  // P = 5
+    } else {
+        reg_stage16<2>(v, tw + 16 + 2u * w, q, q2);   // P = 7
+        reg_stage16<1>(v, tw + 32 + 4u * w, q, q2);   // P = 6
+        reg_stage16<0>(v, tw + 64 + 8u * w, q, q2);   // P = 5
+    }
     // each lane rewrites the words it read; then reads the transpose
 #pragma unroll
     for (int m = 0; m < 16; ++m) sm[pidx(b0 + l + 32u * m)] = v[m];
@@ -859,7 +881,7 @@ __device__ __forceinline__ void ntt_fwd_8192_warp(const uint32_t *__restrict__ s
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = sm[pidx(b0 + 16u * l + m)];
     {  // P = 4: element 16 l + m pairs with 16 (l ^ 1) + m
-        const uint2 w4 = __ldg(tw + 256 + 16u * w + (l >> 1));
+        const uint2 w4 = __ldg(tw + 128 * CS + 16u * w + (l >> 1));
         const bool lower = (l & 1u) == 0u;
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
@@ -867,19 +889,58 @@ __device__ __forceinline__ void ntt_fwd_8192_warp(const uint32_t *__restrict__ s
             const uint32_t X = lower ? v[m] : o;  // the pair's first element
             const uint32_t Y = lower ? o : v[m];  // its second
             const uint32_t U = min(X, X - q2);
-            const uint32_t T = shoup_lazy(Y, w4.x, w4.y, q);
-            v[m] = lower ? U + T : U - T + q2;
+            const uint32_t Tw = shoup_lazy(Y, w4.x, w4.y, q);
+            v[m] = lower ? U + Tw : U - Tw + q2;
         }
     }
-    reg_stage16<3>(v, tw + 512 + 32u * w + l, q, q2);          // P = 3
-    reg_stage16<2>(v, tw + 1024 + 64u * w + 2u * l, q, q2);    // P = 2
-    reg_stage16<1>(v, tw + 2048 + 128u * w + 4u * l, q, q2);   // P = 1
-    reg_stage16<0>(v, tw + 4096 + 256u * w + 8u * l, q, q2);   // P = 0
+    reg_stage16<3>(v, tw + 256 * CS + 32u * w + l, q, q2);          // P = 3
+    reg_stage16<2>(v, tw + 512 * CS + 64u * w + 2u * l, q, q2);     // P = 2
+    reg_stage16<1>(v, tw + 1024 * CS + 128u * w + 4u * l, q, q2);   // P = 1
+    reg_stage16<0>(v, tw + 2048 * CS + 256u * w + 8u * l, q, q2);   // P = 0
     uint4 *d4 = reinterpret_cast<uint4 *>(dst + b0 + 16u * l);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         d4[k] = make_uint4(red_4q(v[4 * k], q2, q), red_4q(v[4 * k + 1], q2, q), red_4q(v[4 * k + 2], q2, q),
                            red_4q(v[4 * k + 3], q2, q));
+}
+
+__device__ __forceinline__ void ntt_fwd_8192_warp(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                                  uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q) {
+    ntt_fwd_3ph<13, 0>(src, dst, sm, tw, q, threadIdx.x);
+}
+
+// Forward negacyclic NTT of length 16384 by 512 threads: stage 13 (span
+// 8192, twiddle tw[1]) pairs i with i + 8192 -- 16 pairs per thread, in four
+// rounds of 4 -- into two padded 8192-word halves of `sm`; after it the
+// halves are independent, and each takes the three-phase scheme in place
+// with its twiddle bases scaled by 2 + h (ntt_fwd_3ph).  `sm` holds
+// 2 padded_words(8192) words.
+__device__ __forceinline__ void ntt_fwd_16384(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                                           uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q) {
+    const uint32_t t = threadIdx.x, q2 = 2u * q;
+    uint32_t *sm1 = sm + padded_words(8192);
+    const uint2 w1 = __ldg(tw + 1);
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+        uint32_t a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            a[u] = __ldg(src + t + 512u * (4 * r + u));
+            b[u] = __ldg(src + 8192u + t + 512u * (4 * r + u));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            bf_fwd(a[u], b[u], w1, q, q2);
+            sm[pidx(t + 512u * (4 * r + u))] = a[u];
+            sm1[pidx(t + 512u * (4 * r + u))] = b[u];
+        }
+    }
+    __syncthreads();
+    // one copy of the scheme for both halves (two inlined copies would not
+    // fit in the register budget)
+#pragma unroll 1
+    for (uint32_t h = 0; h < 2; ++h)
+        ntt_fwd_3ph<13, 0, true>(nullptr, dst + 8192u * h, h ? sm1 : sm, tw, q, t, 2u + h);
 }
 
 // ---------------------------------------------------------------------------
@@ -1011,8 +1072,14 @@ __device__ __forceinline__ void plan_fwd_ntt(const uint32_t *src, uint32_t *dst,
 constexpr int kNttThreads = 512;
 // Checks mode: does item `it` touch only its call's buffers?  (The input it
 // reads, the NTT-domain image it writes; a direct FC item's output.)
-__device__ __forceinline__ bool ntt_item_in_bounds(const CallDesc &cd, const NttItem &it) {
+__device__ __forceinline__ bool ntt_item_in_bounds(const CallDesc *__restrict__ calls, const NttItem &it) {
+    const CallDesc &cd = calls[it.call];
     const uint32_t N = cd.g.N;
+    if (it.src && it.src2) {  // a pair of 4096-point transforms, possibly of two calls
+        const CallDesc &c2 = calls[it.call2];
+        return in_range(it.src, N, cd.x_coeff, cd.in_words) && in_range(it.dst, N, cd.g.x, cd.x_words) &&
+               in_range(it.src2, N, c2.x_coeff, c2.in_words) && in_range(it.dst2, N, c2.g.x, c2.x_words);
+    }
     if (it.src) return in_range(it.src, N, cd.x_coeff, cd.in_words) && in_range(it.dst, N, cd.g.x, cd.x_words);
     if (cd.fc_direct) {
         const uint32_t col = it.poly % cd.g.ncols, l = (it.poly / cd.g.ncols) % cd.g.L,
@@ -1030,15 +1097,26 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
     extern __shared__ uint4 smem4[];
     pdl_trigger();  // the MAC kernel may start streaming weights now
     const NttItem it = items[blockIdx.x];
-    if (checks && !ntt_item_in_bounds(calls[it.call], it)) {
+    if (checks && !ntt_item_in_bounds(calls, it)) {
         if (threadIdx.x == 0) atomicOr(status, kStatusBounds);
         return;
     }
     if (it.src) {  // an ordinary input transform
-        if (it.logN == 13 && blockDim.x == 512)
+        if (it.logN == 13 && blockDim.x == 512) {
             ntt_fwd_8192_warp(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.tw, it.q);
-        else
+        } else if (it.logN == 14 && blockDim.x == 512) {
+            ntt_fwd_16384(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.tw, it.q);
+        } else if (it.logN == 12 && it.src2 && blockDim.x == 512) {
+            // two 4096-point transforms, one per half of the CTA, each in its
+            // own padded half of shared memory, synchronized by named barriers
+            uint32_t *sm = reinterpret_cast<uint32_t *>(smem4);
+            if (threadIdx.x < 256u)
+                ntt_fwd_3ph<12, 1>(it.src, it.dst, sm, it.tw, it.q, threadIdx.x);
+            else
+                ntt_fwd_3ph<12, 2>(it.src2, it.dst2, sm + padded_words(4096), it.tw2, it.q2, threadIdx.x - 256u);
+        } else {
             ntt_fwd_c(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.logN, it.tw, it.q);
+        }
         return;
     }
     const CallDesc &cd = calls[it.call];
