@@ -267,7 +267,7 @@ class Arm:
             calls = [(self.models[r].banks[i], self.x[r][i], H.HE_COEFF, self.y[r][i], c["B"])
                      for i, c in enumerate(self.calls)]
             if NO_AUTOTUNE:
-                self.tuning = H.he_plan_tuning_default()
+                self.tuning = dict(H.he_plan_tuning_default(), **TUNING_OVERRIDE)
                 pl = H.he_plan_create_tuned(calls, self.tuning)
             else:
                 # autotuned once (replicas share the signature, so 1 and 2 reuse it)
@@ -1459,6 +1459,7 @@ def serve_run(H, models, times, which, device, budget, max_batch, streams, max_i
 # (--no-autotune: under a profiler every launch is slower, which skews the
 # autotuner's timings)
 NO_AUTOTUNE = False
+TUNING_OVERRIDE = {}  # --tuning knob=value,...: knobs of the default tuning to change (implies --no-autotune)
 
 
 # ----------------------------------------------------------------------------
@@ -1532,9 +1533,12 @@ def main():
                     help="skip the batched, wide and serving configurations after the plain-20 headline")
     ap.add_argument("--no-autotune", action="store_true",
                     help="plans take the default tuning (for profiling runs, whose timings skew the autotuner)")
+    ap.add_argument("--tuning", default="",
+                    help="knob=value,... changed from the default tuning, no autotuner (e.g. fin_parts=2)")
     args = ap.parse_args()
-    global NO_AUTOTUNE
-    NO_AUTOTUNE = args.no_autotune
+    global NO_AUTOTUNE, TUNING_OVERRIDE
+    TUNING_OVERRIDE = {kv.split("=")[0]: int(kv.split("=")[1]) for kv in args.tuning.split(",") if kv}
+    NO_AUTOTUNE = args.no_autotune or bool(TUNING_OVERRIDE)
     assert args.warmup >= 3 or args.impl == "reference", "at least 3 warm-up steps"
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

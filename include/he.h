@@ -491,10 +491,14 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *                    copy like an ordinary bank.
  *   fc_direct        1: an FC call with coefficient-domain inputs whose
  *                    output window (Theorem 1's first rows_j coefficients)
- *                    costs fewer products than two length-N transforms
- *                    computes that window directly from the coefficient
- *                    forms (default); 0: every FC call takes the transform
- *                    path (input NTT, product, inverse NTT, window).
+ *                    costs fewer than N log2 N / 4 products computes that
+ *                    window directly from the coefficient forms (default;
+ *                    in practice the plain FC layers, whose packed weights
+ *                    are sparse); 2: every FC call with coefficient-domain
+ *                    inputs does (masked and client calls too, whose windows
+ *                    hold dense N-term products); 0: every FC call takes the
+ *                    transform path (input NTT, product, inverse NTT,
+ *                    window).
  *   groups           1, 2 or 3 (default 1): the calls are split into that
  *                    many groups of about equal weight bytes, each with
  *                    its own kernels; group g + 1 runs on a stream of the

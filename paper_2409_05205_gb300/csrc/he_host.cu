@@ -1031,7 +1031,7 @@ he_status check_tuning(const he_plan_tuning &t) {
         return fail(HE_ERR_ARG, "tuning: fused_max_nj must be 2, 4, 8 or 16");
     if (t.tc_min_batch != 1 && t.tc_min_batch != 2 && t.tc_min_batch != 4 && t.tc_min_batch != 8)
         return fail(HE_ERR_ARG, "tuning: tc_min_batch must be 1, 2, 4 or 8");
-    if (t.fc_direct > 1) return fail(HE_ERR_ARG, "tuning: fc_direct must be 0 or 1");
+    if (t.fc_direct > 2) return fail(HE_ERR_ARG, "tuning: fc_direct must be 0, 1 or 2");
     if (t.groups < 1 || t.groups > kPlanMaxGroups) return fail(HE_ERR_ARG, "tuning: groups must be 1, 2 or 3");
     if (t.fin_parts != 1 && t.fin_parts != 2 && t.fin_parts != 4)
         return fail(HE_ERR_ARG, "tuning: fin_parts must be 1, 2 or 4");
@@ -1333,14 +1333,21 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
             g.G = msrc ? 2u : 1u;  // masked and client calls stage two input polynomials per ciphertext
             cd.nj = 2;
             // the output window computed directly when the inputs are in the
-            // coefficient domain and its products cost less than two
-            // length-N transforms: rows * (N for each dense term, n_in' * rows
-            // for the sparse packed weights)
+            // coefficient domain and its products -- rows * (N for each dense
+            // term, n_in' * rows for the sparse packed weights) -- are fewer
+            // than N log2 N / 4 (a window's products run on one warp per
+            // coefficient, latency-bound, so it pays only where it is small
+            // beside the two length-N transforms it replaces: the plain FC
+            // layers; masked and client windows have dense N-term products);
+            // fc_direct = 2 takes it whenever the inputs allow
             const bool coef_in = msrc == 2 || (msrc == 1 && c.in_domain == HE_COEFF) ||
                                  (msrc == 0 && c.in_domain == HE_COEFF);
             const size_t rows = std::min(g.rpp, g.n_out), sparse = (size_t)(r.N / g.rpp) * rows;
             const size_t terms = msrc == 0 ? sparse : (msrc == 1 ? r.N + sparse : 2u * (size_t)r.N);
-            cd.fc_direct = tu.fc_direct && coef_in && f->bank_s && rows * terms <= 2u * (size_t)r.N * r.logN ? 1u : 0u;
+            cd.fc_direct = tu.fc_direct && coef_in && f->bank_s &&
+                                   (tu.fc_direct == 2u || 4u * rows * terms <= (size_t)r.N * r.logN)
+                               ? 1u
+                               : 0u;
             cd.wc = f->bank_s;
             nin = msrc == 2 ? (size_t)c.B * r.N : (size_t)c.B * (msrc ? 1u : 2u) * r.L * r.N;
             nsh = (size_t)c.B * r.N;

@@ -156,7 +156,7 @@ def test_plan_tuning_default_and_validation(he):
                      groups=1, fin_parts=1)
     # a bad knob is refused before any call is looked at or any device work
     for bad in (dict(t, split=2), dict(t, mac_item_kb=48), dict(t, mac_ctas_per_sm=3),
-                dict(t, fused_max_nj=3), dict(t, tc_min_batch=3), dict(t, fc_direct=2), dict(t, groups=0),
+                dict(t, fused_max_nj=3), dict(t, tc_min_batch=3), dict(t, fc_direct=3), dict(t, groups=0),
                 dict(t, groups=4), dict(t, fin_parts=3)):
         with pytest.raises(he.HEError) as ei:
             he.he_plan_create_tuned([(0, 16, he.HE_COEFF, 4096, 1)], bad)

@@ -119,7 +119,7 @@ def test_bounds_checked_plan_reports_nothing_and_gives_the_same_words():
         outs = [c.d_out for c in cases] + [d_out]
         try:
             got = []
-            for checks, fc_direct in ((False, 1), (True, 1), (True, 0)):
+            for checks, fc_direct in ((False, 1), (True, 2), (True, 0)):
                 plan = H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), fc_direct=fc_direct))
                 try:
                     H.he_plan_set_checks(plan, checks)

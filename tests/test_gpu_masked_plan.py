@@ -142,10 +142,12 @@ def _mixed(H, p, N, ps, psis, B=1, in_ntt=False):
     return cases
 
 
-# fc_direct: the FC windows computed directly (coefficient-domain inputs)
-# or through the transforms; fin_parts: finishing items over 1, 2 or 4
-# shares of the residue classes; the words are the same
-@pytest.mark.parametrize("in_ntt,fc_direct,fin_parts", [(False, 1, 1), (True, 1, 2), (False, 0, 4)])
+# fc_direct: the FC windows computed directly (2: every coefficient-domain
+# FC call, masked and client ones included; 1: the cost rule, which keeps the
+# masked and client windows on the transform path) or through the
+# transforms; fin_parts: finishing items over 1, 2 or 4 shares of the
+# residue classes; the words are the same
+@pytest.mark.parametrize("in_ntt,fc_direct,fin_parts", [(False, 2, 1), (True, 1, 2), (False, 0, 4)])
 def test_masked_and_client_calls_in_one_plan_match_single_calls(in_ntt, fc_direct, fin_parts):
     H = U.he()
     torch = U.torch_cuda()
@@ -169,7 +171,7 @@ def test_masked_and_client_calls_in_one_plan_match_single_calls(in_ntt, fc_direc
                 H.he_filters_destroy(c.f)
 
 
-@pytest.mark.parametrize("fc_direct", [1, 0])
+@pytest.mark.parametrize("fc_direct", [2, 1, 0])
 def test_masked_plan_matches_the_oracle(fc_direct):
     """One masked Conv call (16 -> 16 at 32x32: 2G = 8) and one masked FC call
     in a plan, against the oracle's words directly (the FC window computed

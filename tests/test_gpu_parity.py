@@ -281,8 +281,10 @@ def _plan_case(H, p, N, L, shape, B, seed, fc=False):
 def test_plan_mixed_rings_and_shapes_bit_exact():
     """A plan over independent calls with N in {1024, 2048, 4096}, 1-3 limbs,
     B in {1, 2, 8}, Conv shapes with s = 2 .. 64 and FC layers (split over 2
-    and 3 weight polynomials; the last one's window computed directly), some
-    inputs already in the NTT domain."""
+    and 3 weight polynomials), some inputs already in the NTT domain; built
+    with the default tuning and with fc_direct = 2, which computes the window
+    of every coefficient-domain FC call directly (the last call's third block
+    ragged)."""
     H = U.he()
     torch = U.torch_cuda()
     specs = [(1024, 2, (16, 16, 8), 1, False), (2048, 1, (3, 4, 16), 1, False),
@@ -309,19 +311,23 @@ def test_plan_mixed_rings_and_shapes_bit_exact():
             calls.append((f, d_in, dom, d_out, B))
             refs.append(ref)
             outs.append(d_out)
-        plan = H.he_plan_create(calls)
-        try:
-            s = torch.cuda.current_stream()
-            for _ in range(2):           # repeatable: every word rewritten each run
-                for o in outs:
-                    o.fill_(-1)
-                H.he_plan_run(plan, s)
-                H.he_sync(s)
-                H.he_plan_check(plan)
-                for o, ref in zip(outs, refs):
-                    np.testing.assert_array_equal(U.from_dev(o).reshape(ref.shape), ref)
-        finally:
-            H.he_plan_destroy(plan)
+        for fc_direct in (1, 2):
+            plan = H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), fc_direct=fc_direct))
+            try:
+                form = H.he_plan_query(plan, len(calls))["form"]
+                if fc_direct == 2:
+                    assert form[3] == 3 and form[7] == 3   # the coefficient-domain FC calls
+                s = torch.cuda.current_stream()
+                for _ in range(2):           # repeatable: every word rewritten each run
+                    for o in outs:
+                        o.fill_(-1)
+                    H.he_plan_run(plan, s)
+                    H.he_sync(s)
+                    H.he_plan_check(plan)
+                    for o, ref in zip(outs, refs):
+                        np.testing.assert_array_equal(U.from_dev(o).reshape(ref.shape), ref)
+            finally:
+                H.he_plan_destroy(plan)
     finally:
         for c in calls:
             H.he_filters_destroy(c[0])
