@@ -365,7 +365,8 @@ class Arm:
 # DRAM bytes (read + write) of one k_plan_mac launch, from an ncu capture of
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where no
 # capture of the current kernel exists.
-TRAFFIC = {"plain20_c10": 140.93e6,          # ncu --set full of one launch: read 136.63 MB + write 4.30 MB
+TRAFFIC = {"plain20_c10": 141.84e6,          # ncu --set full of one launch: read 136.78 MB + write 5.05 MB
+           "plain20_c10_masked": 269.68e6,   # read 264.23 MB + write 5.45 MB
            "f3_d20_w3": 1250.86e6}           # read 1168.25 MB + write 82.60 MB
 
 
@@ -870,9 +871,20 @@ class MaskedArm:
                 sc.append((self.srv[r][i], x["c0"], H.HE_COEFF, x["out"], c["B"], x["sh"], x["shp"]))
                 rc.append((self.srv[r][i], x["c0"], H.HE_COEFF, x["out"], c["B"], x["sh"], x["shp"], x["outr"]))
                 cc.append((self.cli[r][i], x["v"], H.HE_COEFF, x["out1"], c["B"], x["ish"]))
-            self.srv_plans.append(H.he_plan_create(sc))
-            self.cli_plans.append(H.he_plan_create(cc))
-            self.rs_plans.append(H.he_plan_create(rc))
+            self.srv_plans.append(self._plan(sc))
+            self.cli_plans.append(self._plan(cc))
+            self.rs_plans.append(self._plan(rc))
+
+    def _plan(self, calls):
+        """A plan of these calls: autotuned (the choice is cached per call
+        signature, so replicas reuse it), or the default tuning with
+        --no-autotune / --tuning."""
+        H = self.H
+        if NO_AUTOTUNE:
+            return H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), **TUNING_OVERRIDE))
+        pl, t = H.he_plan_autotune(calls, 20, self.torch.cuda.current_stream())
+        self.tunings = getattr(self, "tunings", []) + [t]
+        return pl
 
     def server_rescale_plan(self, r, stream):
         self.H.he_plan_run(self.rs_plans[r], stream)
@@ -1054,6 +1066,9 @@ def run_masked(args, rank, world, device):
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "steps": k_lat, "how": "CUDA events around each server-plan graph replay"},
+        "tuning": {"chosen": (getattr(arm, "tunings", None) or [info["tuning"]])[0],
+                   "client_and_rescale_plans": (getattr(arm, "tunings", None) or [None, None, None])[1:3],
+                   "how": "he_plan_autotune per plan signature" if not NO_AUTOTUNE else "fixed (--no-autotune / --tuning)"},
         "single_call_form": {"value": arm.units * k2 / (single_ms * 1e-3), "unit": "layers/s", "steps": k2,
                              "ms_per_step": single_ms / k2,
                              "what": "he_conv_layer_masked / he_fc_layer_masked per layer, the 20 calls "
