@@ -573,7 +573,7 @@ def run_ours(args, rank, world, device):
         graph_ms, plain_ms = max_over_ranks([graph_ms, plain_ms], "cuda")
 
     # ---------------- e2e: pinned host buffers, H2D + plan + D2H every step
-    e2e = run_e2e(arm, args, streams)
+    e2e = run_e2e(arm, args)
 
     ch_bytes, ntt_bytes, bfly = arm.algorithmic()
     ntt_bfly, fin_bfly = arm.butterflies(info["form"])
@@ -671,68 +671,42 @@ def run_ours(args, rank, world, device):
     return res
 
 
-def pipelined_steps(torch, R, K, upload, replay, download, stream):
-    """K end-to-end steps, step k on replica k % R, timed on the wall clock:
-    the upload of step k's inputs (H2D stream), its graph (`stream`, or with
-    a list of streams stream[k % len], R a multiple of len) and the download
-    of its result (D2H stream) are ordered by events, so step k+1's upload
-    and step k-1's download overlap step k's graph.  A replica's input
-    buffer is rewritten only after its previous graph has read it, and its
-    output buffer only after its previous download.  Returns seconds."""
-    comp = stream if isinstance(stream, (list, tuple)) else [stream]
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_in = [torch.cuda.Event() for _ in range(R)]
-    ev_comp = [torch.cuda.Event() for _ in range(R)]
-    ev_out = [torch.cuda.Event() for _ in range(R)]
-
-    def run(n):
-        for k in range(n):
-            r = k % R
-            cs = comp[k % len(comp)]
-            if k >= R:
-                s_in.wait_event(ev_comp[r])
-            with torch.cuda.stream(s_in):
-                upload(r)
-            ev_in[r].record(s_in)
-            cs.wait_event(ev_in[r])
-            if k >= R:
-                cs.wait_event(ev_out[r])
-            with torch.cuda.stream(cs):
-                replay(r)
-            ev_comp[r].record(cs)
-            s_out.wait_event(ev_comp[r])
-            with torch.cuda.stream(s_out):
-                download(r)
-            ev_out[r].record(s_out)
-
-    run(3)
+def run_e2e(arm, args):
+    """Per step, through the library's host-buffer entry point
+    (he_plan_run_host): the H2D copy of every layer input from pinned host
+    memory, the plan, the D2H copy of every extracted output into pinned
+    host memory -- captured per replica as one CUDA graph, replica r's
+    steps on stream r, so one step's copies overlap other steps' kernels.
+    Wall clock."""
+    torch, H = arm.torch, arm.H
+    streams = [torch.cuda.Stream() for _ in range(arm.R)]
+    K = max(20, min(args.steps, 2000))
+    w = H.he_plan_host_words(arm.plans[0])
+    assert w["in_words"] == arm.xall[0].numel() and w["out_words"] == arm.yall[0].numel()
+    hx = torch.empty(w["in_words"], dtype=torch.int32, pin_memory=True)
+    hy = [torch.empty(w["out_words"], dtype=torch.int32, pin_memory=True) for _ in range(arm.R)]
+    hx.copy_(arm.xall[0].cpu())   # the inputs are one contiguous buffer, in call order
+    graphs = []
+    cs = torch.cuda.Stream()
+    for r in range(arm.R):
+        H.he_plan_run_host(arm.plans[r], hx, hy[r], cs)   # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cs):
+            H.he_plan_run_host(arm.plans[r], hx, hy[r], cs)
+        graphs.append(g)
+    torch.cuda.synchronize()
+    replay_window(torch, graphs, 2 * arm.R, streams)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    run(K)
+    replay_window(torch, graphs, K, streams)
     torch.cuda.synchronize()
-    return time.perf_counter() - t0
-
-
-def run_e2e(arm, args, stream):
-    """Per step: H2D of every layer input from pinned host memory (one copy:
-    the inputs are contiguous), the plan (graph replay), D2H of every
-    extracted output into pinned host memory (one copy)."""
-    torch = arm.torch
-    K = max(20, min(args.steps, 2000))
-    hx = torch.empty(arm.xall[0].numel(), dtype=torch.int32, pin_memory=True)
-    hy = [torch.empty(arm.yall[0].numel(), dtype=torch.int32, pin_memory=True) for _ in range(arm.R)]
-    hx.copy_(arm.xall[0].cpu())
-    h2d = hx.numel() * 4
-    d2h = hy[0].numel() * 4
-    dt = pipelined_steps(torch, arm.R, K, lambda r: arm.xall[r].copy_(hx, non_blocking=True),
-                         lambda r: arm.graphs[r].replay(), lambda r: hy[r].copy_(arm.yall[r], non_blocking=True),
-                         stream)
-    return {"value": arm.units * K / dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "steps": K,
-            "how": "per step: one H2D copy of every layer input (contiguous) from pinned host memory, the plan "
-                   "(CUDA graph), one D2H copy of every extracted output into pinned memory; uploads, graphs (on "
-                   f"{len(stream) if isinstance(stream, list) else 1} streams, step k on stream k % that) and "
-                   "downloads ordered by events, so consecutive steps overlap; wall clock"}
+    dt = time.perf_counter() - t0
+    return {"value": arm.units * K / dt, "unit": "layers/s", "h2d_bytes_per_step": w["in_words"] * 4,
+            "d2h_bytes_per_step": w["out_words"] * 4, "steps": K, "copies_per_step": w["copies"],
+            "how": "per step: he_plan_run_host (H2D of every layer input from pinned host memory, the plan, "
+                   "D2H of every extracted output into pinned host memory), one CUDA graph per replica, replica "
+                   f"r's steps on stream r ({arm.R} streams), so consecutive steps overlap; wall clock"}
 
 
 # ----------------------------------------------------------------------------
@@ -967,7 +941,7 @@ def _replay_rate(torch, graphs, stream, K, W):
 def run_masked(args, rank, world, device):
     import torch
     wl = workload(args.workload)
-    arm = MaskedArm(wl, device)
+    arm = MaskedArm(wl, device, replicas=2 * STREAMS)
     H = arm.H
     nl = len(arm.calls)
     stream = torch.cuda.Stream()
@@ -992,12 +966,19 @@ def run_masked(args, rank, world, device):
     g_srv, g_cli, g_rs = arm.capture(arm.server_plan), arm.capture(arm.client_plan), arm.capture(arm.rescale)
     g_srs = arm.capture(arm.server_rescale_plan)
     barrier()
+    streams = [stream] + [torch.cuda.Stream() for _ in range(STREAMS - 1)]
     clocks = ClockSampler(device)
     clocks.start()
     time.sleep(0.3)
-    srv_ms = _replay_rate(torch, g_srv, stream, K, W)
+    # STREAMS server steps in flight (replica k % R on stream k % STREAMS),
+    # as in the plain arm; and the same window on one stream
+    replay_window(torch, g_srv, W, streams)
+    t0, t1 = replay_window(torch, g_srv, K, streams)
+    torch.cuda.synchronize()
+    srv_ms = t0.elapsed_time(t1)
     clk = clocks.stop()
     barrier()
+    srv_one_ms = _replay_rate(torch, g_srv, stream, K, W)
     k_lat = min(K, 2000)
     with torch.cuda.stream(stream):
         ev = [_events(2) for _ in range(k_lat)]
@@ -1038,16 +1019,32 @@ def run_masked(args, rank, world, device):
     if world > 1:
         srv_ms, = max_over_ranks([srv_ms], "cuda")
 
-    # e2e: per step one H2D copy of every layer's c0, sh and sh' (contiguous)
-    # from pinned host memory, the server plan (graph), one D2H copy of every c0^r
-    hx = torch.empty(arm.inall[0].numel(), dtype=torch.int32, pin_memory=True)
-    hy = [torch.empty(arm.outall[0].numel(), dtype=torch.int32, pin_memory=True) for _ in range(arm.R)]
+    # e2e through he_plan_run_host: per step the H2D copy of every layer's c0,
+    # sh and sh' (laid out per call in that order, so one copy) from pinned
+    # host memory, the server plan, the D2H copy of every c0^r; one graph per
+    # replica, replica r's steps on stream r
+    hw = H.he_plan_host_words(arm.srv_plans[0])
+    assert hw["in_words"] == arm.inall[0].numel() and hw["out_words"] == arm.outall[0].numel()
+    hx = torch.empty(hw["in_words"], dtype=torch.int32, pin_memory=True)
+    hy = [torch.empty(hw["out_words"], dtype=torch.int32, pin_memory=True) for _ in range(arm.R)]
     hx.copy_(arm.inall[0].cpu())
-    h2d, d2h = hx.numel() * 4, hy[0].numel() * 4
+    h2d, d2h = hw["in_words"] * 4, hw["out_words"] * 4
     ke = max(20, min(K, 2000))
-    e2e_dt = pipelined_steps(torch, arm.R, ke, lambda r: arm.inall[r].copy_(hx, non_blocking=True),
-                             lambda r: g_srv[r].replay(), lambda r: hy[r].copy_(arm.outall[r], non_blocking=True),
-                             stream)
+    g_host, cs = [], torch.cuda.Stream()
+    for r in range(arm.R):
+        H.he_plan_run_host(arm.srv_plans[r], hx, hy[r], cs)   # warm-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cs):
+            H.he_plan_run_host(arm.srv_plans[r], hx, hy[r], cs)
+        g_host.append(g)
+    e2e_streams = [torch.cuda.Stream() for _ in range(arm.R)]
+    replay_window(torch, g_host, 2 * arm.R, e2e_streams)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter()
+    replay_window(torch, g_host, ke, e2e_streams)
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t_e2e
 
     mac_bytes = arm.mac_bytes(info["form"])
     mac_gbs = mac_bytes / (mac_ms * 1e-3) / 1e9
@@ -1063,7 +1060,12 @@ def run_masked(args, rank, world, device):
                    "form": f"masked server step of Alg. 1 / Alg. 2 for every layer: one plan of {nl} calls "
                            f"({info['kernels_per_run']} kernels) replayed as a CUDA graph",
                    "l2": f"rotates {arm.R} model replicas + input sets (masked banks > 2x L2); no flush",
+                   "in_flight": f"{STREAMS} server steps: step k's graph replays on stream k % {STREAMS} "
+                                f"(replica k % {arm.R})",
                    "parallelism": f"replicas x{world}"},
+        "one_in_flight": {"value": arm.units * K / (srv_one_ms * 1e-3), "unit": "layers/s",
+                          "ms_per_step": srv_one_ms / K,
+                          "how": f"the same {K}-step window with every replay on one stream"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "steps": k_lat, "how": "CUDA events around each server-plan graph replay"},
         "tuning": {"chosen": (getattr(arm, "tunings", None) or [info["tuning"]])[0],
@@ -1101,9 +1103,11 @@ def run_masked(args, rank, world, device):
         "plan": {k: v for k, v in info.items() if k not in ("split", "form")},
         "e2e": {"value": arm.units * ke / e2e_dt, "unit": "layers/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": ke,
-                "how": "per step: one H2D copy of every layer's c0, sh and sh' (contiguous) from pinned host "
-                       "memory, the server plan (CUDA graph), one D2H copy of every c0^r; uploads, graphs and "
-                       "downloads on three streams ordered by events, so consecutive steps overlap; wall clock"},
+                "copies_per_step": hw["copies"],
+                "how": "per step: he_plan_run_host on the server plan (one H2D copy of every layer's c0, sh "
+                       "and sh' from pinned host memory, the plan, one D2H copy of every c0^r), one CUDA graph "
+                       f"per replica, replica r's steps on stream r ({arm.R} streams), so consecutive steps "
+                       "overlap; wall clock"},
         "gpu_launches": info["kernels_per_run"] * K,
         "clocks": clk,
     }

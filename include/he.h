@@ -549,6 +549,20 @@ he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t
                            he_plan_tuning *best, he_plan_t *out);
 /* Runs every call of the plan.  Asynchronous on `stream`. */
 he_status he_plan_run(he_plan_t plan, void *stream);
+/* he_plan_run with HOST input and output buffers: h_in holds, call after
+ * call, each call's d_in words, then (masked and client calls) its d_share
+ * words, then (masked calls) its d_share_out words; h_out receives each
+ * call's d_out words, then its d_rescaled words if it has them.  The words
+ * are copied into the calls' device buffers (one copy per run of calls whose
+ * device buffers follow one another in memory), the plan runs, and the
+ * outputs are copied back: all asynchronous on `stream`; the host buffers
+ * must stay valid until the stream reaches the end, and should be
+ * page-locked for the copies to overlap other work.  Sizes:
+ * he_plan_host_words.  HE_ERR_ARG for a NULL argument. */
+he_status he_plan_run_host(he_plan_t plan, const uint32_t *h_in, uint32_t *h_out, void *stream);
+/* Words of he_plan_run_host's h_in and h_out, and the copies it issues per
+ * run (any pointer may be NULL).  Host only. */
+he_status he_plan_host_words(he_plan_t plan, uint64_t *in_words, uint64_t *out_words, uint32_t *copies);
 /* Part of he_plan_run, for timing its kernels separately:
  *   HE_PHASE_NTT (0)   the input-NTT kernel (step 1 above);
  *   HE_PHASE_REST (1)  everything after it (steps 2-4);

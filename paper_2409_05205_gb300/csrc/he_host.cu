@@ -1168,8 +1168,14 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
 }
 
 namespace {
+// a call buffer that he_plan_run_host copies: device pointer and words
+struct IoSeg {
+    uint32_t *dev;
+    size_t words;
+};
 he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning, he_plan_t *out,
-                     size_t *ws_only, bool check_overlaps = false);
+                     size_t *ws_only, bool check_overlaps = false, std::vector<IoSeg> *io_in = nullptr,
+                     std::vector<IoSeg> *io_out = nullptr);
 }  // namespace
 
 he_status he_plan_create_tuned(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning,
@@ -1187,6 +1193,30 @@ he_status he_plan_workspace_bytes(const he_layer_call *calls, uint32_t ncalls, s
 namespace {
 he_status plan_build_grouped(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning &tu, he_plan_t *out);
 
+// he_plan_run_host's copies: the segments in call order, host offsets
+// cumulative, device-contiguous neighbours merged into one copy
+bool set_host_runs(he_plan_s *pl, const std::vector<IoSeg> &in, const std::vector<IoSeg> &out) {
+    auto runs = [](const std::vector<IoSeg> &segs, HostRun *&dst, uint32_t &n, size_t &total) {
+        std::vector<HostRun> v;
+        size_t off = 0;
+        for (const IoSeg &sg : segs) {
+            if (!v.empty() && v.back().dev + v.back().words == sg.dev)
+                v.back().words += sg.words;
+            else
+                v.push_back({sg.dev, off, sg.words});
+            off += sg.words;
+        }
+        total = off;
+        n = (uint32_t)v.size();
+        dst = new (std::nothrow) HostRun[std::max<size_t>(1, v.size())];
+        if (!dst) return false;
+        std::copy(v.begin(), v.end(), dst);
+        return true;
+    };
+    return runs(in, pl->h_in_runs, pl->n_in_runs, pl->host_in_words) &&
+           runs(out, pl->h_out_runs, pl->n_out_runs, pl->host_out_words);
+}
+
 // finishing items per output polynomial of a split-form Conv call: the
 // tuning's fin_parts, fewer where a part would hold under 4 residue classes
 uint32_t fin_parts_of(const he_plan_tuning &tu, uint32_t s) {
@@ -1199,7 +1229,7 @@ uint32_t fin_parts_of(const he_plan_tuning &tu, uint32_t s) {
 // workspace the plan would own (nothing allocated; d_in / d_out may be NULL;
 // with check_overlaps, the buffers are also checked for overlaps).
 he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning *tuning, he_plan_t *out,
-                     size_t *ws_only, bool check_overlaps) {
+                     size_t *ws_only, bool check_overlaps, std::vector<IoSeg> *io_in, std::vector<IoSeg> *io_out) {
     if (!tuning) return fail(HE_ERR_ARG, "NULL tuning");
     if (check_tuning(*tuning) != HE_OK) return HE_ERR_ARG;
     const he_plan_tuning tu = *tuning;
@@ -1208,6 +1238,11 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
     // a grouped plan owns the same workspace as the ungrouped one (the sum
     // of its calls' shares)
     if (tu.groups > 1 && !ws_only) return plan_build_grouped(calls, ncalls, tu, out);
+    std::vector<IoSeg> own_in, own_out;  // the host-IO segments when the caller wants none
+    if (!io_in) io_in = &own_in;
+    if (!io_out) io_out = &own_out;
+    io_in->clear();
+    io_out->clear();
     const he_params_s *p0 = calls[0].filters ? calls[0].filters->p : nullptr;
     if (!p0) return fail(HE_ERR_ARG, "call 0 has no filters");
     const int device = p0->device;
@@ -1380,11 +1415,17 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         ranges.push_back({(uintptr_t)c.d_out, (uintptr_t)(c.d_out + nout), true, i});
         cd.in_words = nin;
         cd.out_words = nout;
+        // he_plan_run_host's order: d_in, d_share, d_share_out; d_out, d_rescaled
+        io_in->push_back({const_cast<uint32_t *>(c.d_in), nin});
+        if (msrc) io_in->push_back({const_cast<uint32_t *>(c.d_share), nsh});
+        if (msrc == 1) io_in->push_back({const_cast<uint32_t *>(c.d_share_out), nshp});
+        io_out->push_back({c.d_out, nout});
         if (c.d_rescaled) {
             if (r.L < 2) return fail(HE_ERR_ARG, "call %u: d_rescaled needs at least 2 limbs", i);
             if (!aligned16(c.d_rescaled)) return fail(HE_ERR_ARG, "call %u: d_rescaled must be 16-byte aligned", i);
             const size_t npoly = nout / ((size_t)r.L * r.N);
             ranges.push_back({(uintptr_t)c.d_rescaled, (uintptr_t)(c.d_rescaled + npoly * (r.L - 1u) * r.N), true, i});
+            io_out->push_back({c.d_rescaled, npoly * (r.L - 1u) * r.N});
             RescaleCall rc;
             rc.a = he_rescale_args(r);
             rc.in = c.d_out;
@@ -1742,6 +1783,10 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         he_plan_destroy(pl);
         return cuda_fail(e, "plan tables");
     }
+    if (!set_host_runs(pl, *io_in, *io_out)) {
+        he_plan_destroy(pl);
+        return fail(HE_ERR_NOMEM, "plan");
+    }
     *out = pl;
     return HE_OK;
 }
@@ -1762,7 +1807,8 @@ he_status plan_build_grouped(const he_layer_call *calls, uint32_t ncalls, const 
     he_plan_tuning t1 = tu;
     t1.groups = 1;
     size_t ws = 0;
-    he_status st = plan_build(calls, ncalls, &t1, nullptr, &ws, true);  // validates every call, overlaps included
+    std::vector<IoSeg> io_in, io_out;
+    he_status st = plan_build(calls, ncalls, &t1, nullptr, &ws, true, &io_in, &io_out);  // validates every call
     if (st != HE_OK) return st;
     const uint32_t ng = std::min(tu.groups, ncalls);
     if (ng == 1) return plan_build(calls, ncalls, &t1, out, nullptr);
@@ -1814,6 +1860,10 @@ he_status plan_build_grouped(const he_layer_call *calls, uint32_t ncalls, const 
             he_plan_destroy(pl);
             return cuda_fail(e, "plan streams and events");
         }
+    }
+    if (!set_host_runs(pl, io_in, io_out)) {
+        he_plan_destroy(pl);
+        return fail(HE_ERR_NOMEM, "plan");
     }
     *out = pl;
     return HE_OK;
@@ -1890,6 +1940,33 @@ he_status he_plan_run(he_plan_t plan, void *stream) {
     cudaError_t e = plan->ngroups ? run_grouped(*plan, (cudaStream_t)stream)
                                   : he_launch_plan(*plan, (cudaStream_t)stream, -1);
     return e == cudaSuccess ? HE_OK : cuda_fail(e, "plan run");
+}
+
+he_status he_plan_host_words(he_plan_t plan, uint64_t *in_words, uint64_t *out_words, uint32_t *copies) {
+    if (!plan) return fail(HE_ERR_ARG, "plan is NULL");
+    if (in_words) *in_words = plan->host_in_words;
+    if (out_words) *out_words = plan->host_out_words;
+    if (copies) *copies = plan->n_in_runs + plan->n_out_runs;
+    return HE_OK;
+}
+
+he_status he_plan_run_host(he_plan_t plan, const uint32_t *h_in, uint32_t *h_out, void *stream) {
+    NvtxRange nvtx_("he_plan_run_host");
+    if (!plan || !h_in || !h_out) return fail(HE_ERR_ARG, "NULL argument");
+    DeviceGuard g(plan->device);
+    if (!g.ok) return fail(HE_ERR_CUDA, "cannot select device %d", plan->device);
+    const cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    for (uint32_t i = 0; i < plan->n_in_runs && e == cudaSuccess; ++i) {
+        const HostRun &r = plan->h_in_runs[i];
+        e = cudaMemcpyAsync(r.dev, h_in + r.host_off, r.words * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = plan->ngroups ? run_grouped(*plan, st) : he_launch_plan(*plan, st, -1);
+    for (uint32_t i = 0; i < plan->n_out_runs && e == cudaSuccess; ++i) {
+        const HostRun &r = plan->h_out_runs[i];
+        e = cudaMemcpyAsync(h_out + r.host_off, r.dev, r.words * sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    }
+    return e == cudaSuccess ? HE_OK : cuda_fail(e, "plan run with host buffers");
 }
 
 he_status he_plan_run_phase(he_plan_t plan, int phase, void *stream) {
@@ -1985,6 +2062,8 @@ void he_plan_destroy(he_plan_t plan) {
     cudaFree(plan->d_rs_items);
     cudaFree(plan->d_rs_cnt);
     delete[] plan->split;
+    delete[] plan->h_in_runs;
+    delete[] plan->h_out_runs;
     delete plan;
 }
 

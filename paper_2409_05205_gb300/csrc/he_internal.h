@@ -356,6 +356,13 @@ constexpr int kChanClasses = 5;
 __host__ __device__ __forceinline__ constexpr uint32_t chan_class_nj(int cls) { return cls < 4 ? 2u << cls : 1u; }
 
 constexpr uint32_t kPlanMaxGroups = 3;  // call groups of a pipelined plan (he_plan_tuning::groups)
+// One copy of he_plan_run_host: `words` words between device buffer `dev`
+// and the host buffer at word offset `host_off` (runs of device-contiguous
+// call buffers are merged into one copy).
+struct HostRun {
+    uint32_t *dev;
+    size_t host_off, words;
+};
 struct he_plan_s {
     int device;
     uint32_t ncalls, n_ntt, n_chan[kChanClasses];  // fused channel items per NJ class (2, 4, 8, 16, 1)
@@ -396,6 +403,11 @@ struct he_plan_s {
     // back onto the caller's stream
     uint32_t ngroups;
     he_plan_s *sub[kPlanMaxGroups];
+    // he_plan_run_host: the copies of the calls' input and output buffers,
+    // in call order (host: new[], owned)
+    HostRun *h_in_runs, *h_out_runs;
+    uint32_t n_in_runs, n_out_runs;
+    size_t host_in_words, host_out_words;
     cudaStream_t side[kPlanMaxGroups];
     cudaEvent_t ev_ntt[kPlanMaxGroups], ev_end[kPlanMaxGroups];
 };

@@ -131,6 +131,9 @@ _SIGS = {
     "he_plan_autotune": [ctypes.POINTER(he_layer_call), _u32, _u32, _vp, ctypes.POINTER(he_plan_tuning),
                          ctypes.POINTER(_vp)],
     "he_plan_run": [_vp, _vp],
+    "he_plan_run_host": [_vp, _vp, _vp, _vp],
+    "he_plan_host_words": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                           ctypes.POINTER(_u32)],
     "he_plan_run_phase": [_vp, _i32, _vp],
     "he_plan_query": [_vp, ctypes.POINTER(he_plan_info), _vp],
     "he_plan_check": [_vp],
@@ -485,6 +488,20 @@ def he_plan_autotune(calls, iters: int = 5, stream=None) -> tuple[int, dict]:
 
 def he_plan_run(plan: int, stream=None) -> None:
     _check(lib().he_plan_run(plan, _stream(stream)))
+
+
+def he_plan_run_host(plan: int, h_in, h_out, stream=None) -> None:
+    """he_plan_run with host buffers (host addresses, or objects with
+    data_ptr(), e.g. pinned torch tensors): inputs of every call in call
+    order in h_in, outputs in h_out (sizes: he_plan_host_words)."""
+    _check(lib().he_plan_run_host(plan, _ptr(h_in), _ptr(h_out), _stream(stream)))
+
+
+def he_plan_host_words(plan: int) -> dict:
+    """{"in_words", "out_words", "copies"} of he_plan_run_host."""
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), _u32()
+    _check(lib().he_plan_host_words(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"in_words": a.value, "out_words": b.value, "copies": c.value}
 
 
 def he_plan_run_phase(plan: int, phase: int, stream=None) -> None:
