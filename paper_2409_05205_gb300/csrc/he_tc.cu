@@ -14,9 +14,10 @@
 // recombines sum_{i,j} 2^(8(i+j)) D_ij and reduces mod q_l.
 //
 // One tile = (limb, block, 64 output channels) x 16 columns:
-//   A (TMEM, M = 128 rows): rows 0..63 hold limbs {0, 1} of the 64 channels'
-//     weights, rows 64..127 limbs {2, 3}; two MMAs per K-step (p = 0, 1)
-//     take limb p from the low rows and limb p + 2 from the high rows.
+//   A (TMEM, M = 128 rows): row 2n holds limbs {0, 1} of channel n's
+//     weights, row 2n + 1 limbs {2, 3} (a channel's two rows in adjacent
+//     lanes of one warp); two MMAs per K-step (p = 0, 1) take limb p from
+//     the even rows and limb p + 2 from the odd rows.
 //   B (shared memory, N = 64 rows, K-major, no swizzle): row
 //     32 (col / 8) + 4 (col % 8) + j is limb j of ciphertext polynomial col.
 //   D_p (TMEM, fp32, 128 lanes x 64 columns, double-buffered).
@@ -32,8 +33,8 @@
 //                ring -> fp16 limbs -> tcgen05.st into an A slot of tensor
 //                memory
 //   warps 6..13  epilogue, two per sub-partition (columns 0..7 / 8..15):
-//                tcgen05.ld of D, exact recombination, mod q, the high
-//                rows' share through shared memory, z stores
+//                tcgen05.ld of D, exact recombination, mod q, the shares of
+//                a channel's two rows exchanged by lane shuffles, z stores
 //   warps 14..15 B builders: a block's input words -> fp16 limb rows
 // Every wait is bounded; a wait that gives up raises an abort flag that
 // every other wait sees, sets bit 1 of the plan status, and the CTA winds
@@ -53,7 +54,6 @@ constexpr uint32_t kXRawBytes = kTcMaxK * kTcCols * 4;      // 16 KB
 constexpr uint32_t kXSlots = 4;  // blocks of inputs in flight: one input copy per block of one
                                  // tile (K = 64) must not wait for the copy latency
 constexpr uint32_t kBOpBytes = 64 * kTcMaxK * 2;            // 32 KB
-constexpr uint32_t kXchgBytes = kTcCols * kTcRows * 4;      // 4 KB
 constexpr uint32_t kTcSpin = 1u << 16;   // tests of a phase before a wait gives up (each up to kSuspendNs)
 constexpr uint32_t kMagic = 0x33000000u;       // bits of 2^-25 as fp32: 2^23 units of 2^-48
 
@@ -72,8 +72,7 @@ static_assert(sizeof(TcBars) <= kHdrBytes, "barrier header");
 constexpr uint32_t kOffW = kHdrBytes;
 constexpr uint32_t kOffX = kOffW + kWStages * kWStageBytes;
 constexpr uint32_t kOffB = kOffX + kXSlots * kXRawBytes;
-constexpr uint32_t kOffXchg = kOffB + 2 * kBOpBytes;
-constexpr uint32_t kTcSmem = kOffXchg + 2 * kXchgBytes;
+constexpr uint32_t kTcSmem = kOffB + 2 * kBOpBytes;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 
@@ -130,15 +129,6 @@ __device__ __forceinline__ void tensor5_g2s(void *dst, const void *tmap, uint32_
         "%6}], [%7];" ::"r"(su32(dst)),
         "l"(tmap), "r"(c0), "r"(c1), "r"(0u), "r"(0u), "r"(0u), "r"(su32(b))
         : "memory");
-}
-
-__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
-    uint32_t v;
-    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
-    return v;
-}
-__device__ __forceinline__ void sts32(uint32_t addr, uint32_t v) {
-    asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -235,7 +225,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
     uint8_t *wring = smem + kOffW;
     uint8_t *xraw = smem + kOffX;
     uint8_t *bop = smem + kOffB;
-    uint32_t *xchg = reinterpret_cast<uint32_t *>(smem + kOffXchg);
     volatile uint32_t *abort = &bars.abort;
     const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = tid & 31u;
     const uint32_t ib = offs[blockIdx.x], ie = offs[blockIdx.x + 1];
@@ -407,8 +396,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
         // 32-column tensor-memory store.  Software-pipelined: pair p+1 is
         // read and converted while the store of pair p completes.
         const uint32_t sp = warp & 3u;
-        const uint32_t tl = 32u * sp + lane, n = tl & 63u;
-        const bool high = tl >= 64u;
+        // row tl = 2 n + high: channel n's limbs {0, 1} (high = 0) or {2, 3}
+        const uint32_t tl = 32u * sp + lane, n = tl >> 1;
+        const bool high = (tl & 1u) != 0u;
         const uint32_t taddr = tmem + ((32u * sp) << 16) + 256u;
         uint32_t ws = 0, as = 0, pend = kASlots;  // pend: first slot of the pair stored but not yet signalled
         bool ok = true;
@@ -487,15 +477,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
     } else if (warp < kWarpB0) {
         // ------------------------------------------------------------ epilogue
         // Warp (sub-partition sp, column half hc) takes columns 8 hc .. 8 hc + 7
-        // of its 32 rows.  Each output needs the low rows' sum (limbs 0, 1)
-        // plus 2^16 times the high rows' (limbs 2, 3): the low rows finish
-        // columns 0..3 of the half and the high rows 4..7, each receiving the
-        // other side's reduced share through shared memory.  The four warps
-        // of a column half meet at named barrier 1 + hc once per tile, also
-        // after an abort, so that no warp waits there for one that has left.
+        // of its 32 rows: 16 channels, channel n in rows 2n (limbs 0, 1) and
+        // 2n + 1 (limbs 2, 3), so in lanes 2m and 2m + 1 of one warp.  Each
+        // output needs the low row's sum plus 2^16 times the high row's: the
+        // low lane finishes columns 0..3 of the half and the high lane 4..7,
+        // each receiving its partner's reduced share by a shuffle.
         const uint32_t sp = warp & 3u, hc = (warp - kWarpE0) >> 2;
-        const uint32_t tl = 32u * sp + lane, n = tl & 63u;
-        const bool high = tl >= 64u;
+        const uint32_t tl = 32u * sp + lane, n = tl >> 1;
+        const bool high = (tl & 1u) != 0u;
         // B rows (and so D columns) are ordered (hc, column c % 8, limb j): this
         // warp's accumulators are D_p columns 32 hc .. 32 hc + 31
         const uint32_t lrow = tmem + ((32u * sp) << 16) + 32u * hc;
@@ -524,9 +513,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                 for (uint32_t ch = 0; ch < nch; ++ch) {
                     const uint32_t db = ds & 1u;
                     ok = ok && bar_wait(&bars.d_full[db], (ds >> 1) & 1u, abort);
+                    ok = __all_sync(0xffffffffu, ok);  // the shuffles below need the whole warp
                     uint64_t val[8];
-                    // this lane's word of column 0 of its half in the exchange buffer
-                    const uint32_t xa = su32(xchg + db * (kTcCols * kTcRows) + 8u * hc * kTcRows + n);
                     if (ok) {
                         tc_fence_after();
                         // two groups of 4 columns keep 32 accumulators live at a time
@@ -546,33 +534,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                             else
                                 recombine4<false>(v, val + 4 * g4);
                         }
-                        // columns 0..3 are finished by the low rows, 4..7 by the high
-                        // rows: each side sends its reduced share of the other four
-                        {
-                            const uint32_t o = high ? 0u : 4u;
-                            uint32_t r[4];
+                        // each lane sends its reduced share of the partner's four
+                        // columns and receives the partner's share of its own
+                        uint32_t got[4];
 #pragma unroll
-                            for (uint32_t c = 0; c < 4; ++c) r[c] = reduce64(high ? val[c] : val[4 + c], K);
-#pragma unroll
-                            for (uint32_t c = 0; c < 4; ++c) sts32(xa + 4u * ((o + c) * kTcRows), r[c]);
-                        }
-                    }
-                    if (hc == 0)
-                        asm volatile("bar.sync 1, 128;" ::: "memory");
-                    else
-                        asm volatile("bar.sync 2, 128;" ::: "memory");
-                    if (ok) {  // the other side's 4 shares, 4 reductions, then the stores
+                        for (uint32_t c = 0; c < 4; ++c)
+                            got[c] = __shfl_xor_sync(0xffffffffu, reduce64(high ? val[c] : val[4 + c], K), 1);
+                        // low lane: own sum (< 2^57) + 2^16 (high share); high lane:
+                        // 2^16 (own sum reduced) + low share
                         const uint32_t o = high ? 4u : 0u;
-                        uint32_t hx[4], r[4];
+                        uint32_t r[4];
 #pragma unroll
-                        for (uint32_t c = 0; c < 4; ++c) hx[c] = lds32(xa + 4u * ((o + c) * kTcRows));
-                        // low rows: own sum + 2^16 (high share); high rows: 2^16 own sum + low share
-#pragma unroll
-                        for (uint32_t c = 0; c < 4; ++c) {
-                            const uint32_t mine = reduce64(high ? val[4 + c] : val[c], K);
-                            r[c] = high ? reduce64(((uint64_t)mine << 16) + hx[c], K)
-                                        : reduce64(((uint64_t)hx[c] << 16) + mine, K);
-                        }
+                        for (uint32_t c = 0; c < 4; ++c)
+                            r[c] = high ? reduce64(((uint64_t)reduce64(val[4 + c], K) << 16) + got[c], K)
+                                        : reduce64(val[c] + ((uint64_t)got[c] << 16), K);
                         uint32_t *z = zb + (size_t)b * co + ch * kTcRows;
 #pragma unroll
                         for (uint32_t c = 0; c < 4; ++c)
