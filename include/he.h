@@ -481,7 +481,10 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *   mac_item_kb      weight bytes of one split-form MAC work item: 32, 64 or
  *                    128 (default 128).  Smaller items balance the
  *                    persistent CTAs better and re-read inputs more often.
- *   mac_ctas_per_sm  persistent MAC CTAs per SM: 1 or 2 (default 2).
+ *   mac_ctas_per_sm  persistent MAC CTAs per SM: 1 or 2 (default 2).  A
+ *                    lone CTA leaves registers and shared memory for a CTA
+ *                    of another kernel beside it: slower alone, faster with
+ *                    several runs in flight.
  *   fused_max_nj     the most ciphertext columns one fused-form CTA handles:
  *                    2, 4, 8 or 16 (default 16; fewer also when shared
  *                    memory requires).
@@ -512,7 +515,14 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *                    each over that share of the s residue classes (its
  *                    channels' inverse transforms and those classes'
  *                    coefficients); fewer where a share would hold under 4
- *                    classes.  More, smaller items fill more of the GPU. */
+ *                    classes.  More, smaller items fill more of the GPU.
+ *   tw_smem          1: each 4096- and 8192-point input transform of the
+ *                    input-NTT kernel copies its forward twiddle table into
+ *                    shared memory with bulk copies issued at its start, and
+ *                    its last stages read it there (99 KB of shared memory
+ *                    per CTA instead of 34 KB); 0 (default): they read it
+ *                    from global memory (L2), in an order that makes every
+ *                    load coalesced. */
 typedef struct {
     uint32_t split;
     uint32_t mac_item_kb;
@@ -522,6 +532,7 @@ typedef struct {
     uint32_t fc_direct;
     uint32_t groups;
     uint32_t fin_parts;
+    uint32_t tw_smem;
 } he_plan_tuning;
 
 /* The default tuning. */
@@ -547,6 +558,17 @@ he_status he_plan_workspace_bytes(const he_layer_call *calls, uint32_t ncalls, s
  * runs nothing.  `best` (may be NULL) receives the tuning.  Blocking. */
 he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t iters, void *stream,
                            he_plan_tuning *best, he_plan_t *out);
+/* he_plan_autotune for a caller that keeps `in_flight` (1 .. 8) runs of
+ * plans over calls of this signature in flight at once, each on a stream of
+ * its own: every candidate is timed as `in_flight` plans, each replayed from
+ * a CUDA graph on its own stream, run k on plan k % in_flight (the
+ * throughput of that regime, where kernels of different runs share the SMs;
+ * it can pick another tuning than one run at a time does).  The first plan
+ * works on the calls' buffers; the others read the same inputs and write
+ * private output buffers, allocated and freed per candidate.  Cached per
+ * signature and in_flight; in_flight = 1 is he_plan_autotune.  Blocking. */
+he_status he_plan_autotune_inflight(const he_layer_call *calls, uint32_t ncalls, uint32_t iters,
+                                    uint32_t in_flight, void *stream, he_plan_tuning *best, he_plan_t *out);
 /* Runs every call of the plan.  Asynchronous on `stream`. */
 he_status he_plan_run(he_plan_t plan, void *stream);
 /* he_plan_run with HOST input and output buffers: h_in holds, call after

@@ -128,6 +128,22 @@ uint32_t bitrev(uint32_t x, uint32_t bits) {
     return r;
 }
 
+// Position of entry e of a length-2^logN forward table in the three-phase
+// transform's copy (RingView::tw_fwd3, logN = 12 .. 14).  In the transform's
+// last three stages (stage 0, 1, 2: the entries e >= N/8) each lane takes
+// 2^k consecutive twiddles (k = 3 - stage) of its warp's segment of 32 * 2^k
+// entries; the copy stores every such segment transposed, twiddle j of lane
+// l at 32 j + l, so that the 32 lanes' twiddle j are 32 consecutive entries
+// (one coalesced load from global memory, conflict-free from shared memory).
+// The entries of the earlier stages keep their places.
+uint32_t tw3_pos(uint32_t e, uint32_t logN) {
+    if (e < (1u << (logN - 3))) return e;
+    uint32_t lg = 0;
+    while ((2u << lg) <= e) ++lg;  // floor(log2 e)
+    const uint32_t k = lg + 4u - logN, seg = 32u << k, o = e & (seg - 1u);
+    return e - o + 32u * (o & ((1u << k) - 1u)) + (o >> k);
+}
+
 uint32_t log2_exact(uint32_t x) {
     uint32_t l = 0;
     while ((1u << l) < x) ++l;
@@ -342,8 +358,18 @@ he_status he_params_create(uint32_t N, uint32_t L, const uint32_t *primes, uint3
         delete p;
         return fail(HE_ERR_CUDA, "cannot select device %d", device);
     }
+    // the three-phase transform's copy of the forward table (N = 4096 .. 16384)
+    std::vector<uint2> twf3;
+    if (logN >= 12 && logN <= 14) {
+        twf3.resize(twf.size());
+        for (uint32_t l = 0; l < L; ++l)
+            for (uint32_t i = 0; i < N; ++i) twf3[(size_t)l * N + tw3_pos(i, logN)] = twf[(size_t)l * N + i];
+    }
     cudaError_t e = cudaMalloc(&p->d_tw_fwd, twf.size() * sizeof(uint2));
     if (e == cudaSuccess) e = cudaMalloc(&p->d_tw_inv, twi.size() * sizeof(uint2));
+    if (e == cudaSuccess && !twf3.empty()) e = cudaMalloc(&p->d_tw_fwd3, twf3.size() * sizeof(uint2));
+    if (e == cudaSuccess && !twf3.empty())
+        e = cudaMemcpy(p->d_tw_fwd3, twf3.data(), twf3.size() * sizeof(uint2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_psi_pow, pw.size() * sizeof(uint32_t));
     if (e == cudaSuccess) e = cudaMemcpy(p->d_tw_fwd, twf.data(), twf.size() * sizeof(uint2), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->d_tw_inv, twi.data(), twi.size() * sizeof(uint2), cudaMemcpyHostToDevice);
@@ -356,6 +382,7 @@ he_status he_params_create(uint32_t N, uint32_t L, const uint32_t *primes, uint3
     r.tw_fwd = p->d_tw_fwd;
     r.tw_inv = p->d_tw_inv;
     r.psi_pow = p->d_psi_pow;
+    r.tw_fwd3 = p->d_tw_fwd3;
     *out = p;
     return HE_OK;
 }
@@ -408,6 +435,7 @@ void he_params_destroy(he_params_t p) {
     cudaFree(p->d_tw_fwd);
     cudaFree(p->d_tw_inv);
     cudaFree(p->d_psi_pow);
+    cudaFree(p->d_tw_fwd3);
     cudaFree(p->ws);
     delete p;
 }
@@ -1018,6 +1046,7 @@ he_status he_plan_tuning_default(he_plan_tuning *t) {
     t->fc_direct = 1;
     t->groups = 1;
     t->fin_parts = 1;
+    t->tw_smem = 0;
     return HE_OK;
 }
 
@@ -1035,6 +1064,7 @@ he_status check_tuning(const he_plan_tuning &t) {
     if (t.groups < 1 || t.groups > kPlanMaxGroups) return fail(HE_ERR_ARG, "tuning: groups must be 1, 2 or 3");
     if (t.fin_parts != 1 && t.fin_parts != 2 && t.fin_parts != 4)
         return fail(HE_ERR_ARG, "tuning: fin_parts must be 1, 2 or 4");
+    if (t.tw_smem > 1) return fail(HE_ERR_ARG, "tuning: tw_smem must be 0 or 1");
     return HE_OK;
 }
 }  // namespace
@@ -1301,6 +1331,7 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         cd.src_b = msrc ? c.d_share : nullptr;
         cd.a_ntt = msrc == 1 && c.in_domain == HE_NTT ? 1u : 0u;
         cd.tw_fwd = r.tw_fwd;
+        cd.tw_fwd3 = r.tw_fwd3;
         for (uint32_t l = 0; l < r.L; ++l) cd.limb[l] = r.limb[l];
         size_t nin, nout, nsh = 0, nshp = 0;
         if (f->kind == HE_KIND_CONV) {
@@ -1524,7 +1555,9 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
                     const uint32_t l = (uint32_t)(pidx_ % g.L);
                     it.src = cd.x_coeff + pidx_ * g.N;
                     it.dst = const_cast<uint32_t *>(g.x) + pidx_ * g.N;
-                    it.tw = cd.tw_fwd + (size_t)l * g.N;
+                    // the three-phase transforms (N = 8192, 16384) read the
+                    // table in their own order; N = 4096 switches when paired
+                    it.tw = (g.logN == 13 || g.logN == 14 ? cd.tw_fwd3 : cd.tw_fwd) + (size_t)l * g.N;
                     it.q = cd.limb[l].q;
                     it.logN = g.logN;
                 }
@@ -1587,12 +1620,14 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
                 continue;
             }
             if (open != SIZE_MAX) {
+                // a pair runs the three-phase transform: its table order
                 NttItem &o = kept[open].second;
+                o.tw = descs[o.call].tw_fwd3 + (o.tw - descs[o.call].tw_fwd);
                 o.call2 = c.second.call;
                 o.q2 = c.second.q;
                 o.src2 = c.second.src;
                 o.dst2 = c.second.dst;
-                o.tw2 = c.second.tw;
+                o.tw2 = descs[c.second.call].tw_fwd3 + (c.second.tw - descs[c.second.call].tw_fwd);
                 kept[open].first += c.first;
                 open = SIZE_MAX;
             } else {
@@ -1614,7 +1649,11 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
                                                                : padded_words(g.N);
         const size_t sm = descs[it.second.call].fc_direct ? (size_t)std::min(g.rpp, g.n_out) * 4u : words * 4u;
         pl->smem_ntt = std::max(pl->smem_ntt, sm);
+        // 8192-point transforms and pairs of 4096-point ones can copy their
+        // twiddle tables into shared memory (two CTAs of kNttStageBytes fit an SM)
+        if (tu.tw_smem && it.second.src && (g.logN == 13 || it.second.src2)) pl->tw_stage = 1;
     }
+    if (pl->tw_stage) pl->smem_ntt = std::max(pl->smem_ntt, (size_t)kNttStageBytes);
     pl->n_ntt = (uint32_t)ntt.size();
     pl->n_fc = n_fc;
     auto upload = [&](ChanItem **dst, const std::vector<ChanItem> &v) -> cudaError_t {
@@ -1907,8 +1946,9 @@ he_status he_plan_check(he_plan_t plan) {
         if (st & kStatusBounds)
             return fail(HE_ERR_ARG, "a device-side bounds check failed: a work item addresses memory outside its "
                                     "call's buffers (status 0x%x)", st);
-        return fail(HE_ERR_TIMEOUT, "a bounded wait of a MAC kernel gave up (status 0x%x: bit 0 scalar, bit 1 tensor-core)",
-                    st);
+        return fail(HE_ERR_TIMEOUT,
+                    "a bounded wait gave up (status 0x%x: bit 0 scalar MAC, bit 1 tensor-core MAC, bit 3 input-NTT "
+                    "twiddle copy)", st);
     }
     return HE_OK;
 }
@@ -2091,8 +2131,8 @@ std::string plan_signature(const he_layer_call *calls, uint32_t ncalls) {
 }
 
 // mean run time (ms) of a plan built with tuning t; < 0 if it cannot be built or run
-float time_tuning(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning &t, uint32_t iters,
-                  cudaStream_t st) {
+float time_tuning_1(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning &t, uint32_t iters,
+                    cudaStream_t st) {
     he_plan_t pl = nullptr;
     if (he_plan_create_tuned(calls, ncalls, &t, &pl) != HE_OK) return -1.0f;
     cudaEvent_t a = nullptr, b = nullptr;
@@ -2120,14 +2160,107 @@ float time_tuning(const he_layer_call *calls, uint32_t ncalls, const he_plan_tun
     he_plan_destroy(pl);
     return ms;
 }
+
+// Milliseconds per plan run with `in_flight` runs in flight: that many plans
+// of the tuning, each captured in a CUDA graph on a stream of its own, run
+// k goes to plan k % in_flight; best of three batches of `iters` runs after
+// two warm-up runs of each.  Plan 0 works on the calls' buffers; the others
+// read the same inputs and write private outputs (allocated here).  -1 when
+// something fails.
+float time_tuning(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning &t, uint32_t iters,
+                  cudaStream_t st, uint32_t in_flight) {
+    if (in_flight <= 1) return time_tuning_1(calls, ncalls, t, iters, st);
+    std::vector<IoSeg> io_in, io_out;
+    size_t ws = 0;
+    if (plan_build(calls, ncalls, &t, nullptr, &ws, false, &io_in, &io_out) != HE_OK) return -1.0f;
+    size_t words = 0;
+    for (const IoSeg &sg : io_out) words += (sg.words + 63u) & ~(size_t)63u;  // 256-byte aligned pieces
+    const uint32_t k = in_flight;
+    std::vector<he_plan_t> pls(k, nullptr);
+    std::vector<uint32_t *> scratch(k, nullptr);
+    std::vector<cudaStream_t> ss(k, nullptr);
+    std::vector<cudaEvent_t> joins(k, nullptr);
+    std::vector<cudaGraphExec_t> ge(k, nullptr);
+    cudaEvent_t a = nullptr, b = nullptr;
+    float ms = -1.0f;
+    bool ok = cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess;
+    for (uint32_t j = 0; j < k && ok; ++j) {
+        ok = cudaStreamCreateWithFlags(&ss[j], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&joins[j], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) break;
+        if (j == 0) {
+            ok = he_plan_create_tuned(calls, ncalls, &t, &pls[0]) == HE_OK;
+        } else {
+            ok = cudaMalloc(&scratch[j], std::max<size_t>(words, 1) * sizeof(uint32_t)) == cudaSuccess;
+            std::vector<he_layer_call> cj(calls, calls + ncalls);
+            size_t off = 0, seg = 0;
+            for (uint32_t i = 0; i < ncalls && ok; ++i) {  // io_out's order: d_out, then d_rescaled
+                cj[i].d_out = scratch[j] + off;
+                off += (io_out[seg++].words + 63u) & ~(size_t)63u;
+                if (cj[i].d_rescaled) {
+                    cj[i].d_rescaled = scratch[j] + off;
+                    off += (io_out[seg++].words + 63u) & ~(size_t)63u;
+                }
+            }
+            ok = ok && he_plan_create_tuned(cj.data(), ncalls, &t, &pls[j]) == HE_OK;
+        }
+        // one run outside capture first (it also sets the kernels' attributes)
+        ok = ok && he_plan_run(pls[j], ss[j]) == HE_OK && cudaStreamSynchronize(ss[j]) == cudaSuccess;
+        cudaGraph_t g = nullptr;
+        ok = ok && cudaStreamBeginCapture(ss[j], cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const bool ran = he_plan_run(pls[j], ss[j]) == HE_OK;
+            ok = cudaStreamEndCapture(ss[j], &g) == cudaSuccess && ran;
+        }
+        ok = ok && cudaGraphInstantiate(&ge[j], g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+    }
+    auto window = [&](uint32_t n) -> bool {
+        if (cudaEventRecord(a, st) != cudaSuccess) return false;
+        for (uint32_t j = 0; j < k; ++j)
+            if (cudaStreamWaitEvent(ss[j], a, 0) != cudaSuccess) return false;
+        for (uint32_t r = 0; r < n; ++r)
+            if (cudaGraphLaunch(ge[r % k], ss[r % k]) != cudaSuccess) return false;
+        for (uint32_t j = 0; j < k; ++j)
+            if (cudaEventRecord(joins[j], ss[j]) != cudaSuccess || cudaStreamWaitEvent(st, joins[j], 0) != cudaSuccess)
+                return false;
+        return cudaEventRecord(b, st) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess;
+    };
+    ok = ok && window(2 * k);
+    for (int rep = 0; rep < 3 && ok; ++rep) {
+        const uint32_t n = std::max(iters, k);
+        float tm = 0.0f;
+        ok = window(n) && cudaEventElapsedTime(&tm, a, b) == cudaSuccess;
+        if (ok) ms = (ms < 0.0f || tm / n < ms) ? tm / n : ms;
+    }
+    for (uint32_t j = 0; j < k; ++j)
+        if (pls[j] && he_plan_check(pls[j]) != HE_OK) ok = false;
+    if (!ok) ms = -1.0f;
+    for (uint32_t j = 0; j < k; ++j) {
+        if (ge[j]) cudaGraphExecDestroy(ge[j]);
+        if (joins[j]) cudaEventDestroy(joins[j]);
+        if (ss[j]) cudaStreamDestroy(ss[j]);
+        he_plan_destroy(pls[j]);
+        cudaFree(scratch[j]);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    return ms;
+}
 }  // namespace
 
 he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t iters, void *stream,
                            he_plan_tuning *best, he_plan_t *out) {
+    return he_plan_autotune_inflight(calls, ncalls, iters, 1, stream, best, out);
+}
+
+he_status he_plan_autotune_inflight(const he_layer_call *calls, uint32_t ncalls, uint32_t iters, uint32_t in_flight,
+                                    void *stream, he_plan_tuning *best, he_plan_t *out) {
     if (!calls || !out || ncalls == 0) return fail(HE_ERR_ARG, "NULL argument or empty plan");
+    if (in_flight < 1 || in_flight > 8) return fail(HE_ERR_ARG, "in_flight must be 1 to 8");
     for (uint32_t i = 0; i < ncalls; ++i)
         if (!calls[i].filters) return fail(HE_ERR_ARG, "call %u: no filters", i);
-    const std::string key = plan_signature(calls, ncalls);
+    const std::string key = plan_signature(calls, ncalls) + "x" + std::to_string(in_flight);
     he_plan_tuning cur;
     he_plan_tuning_default(&cur);
     bool cached = false;
@@ -2144,7 +2277,7 @@ he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t
         DeviceGuard g(calls[0].filters->p->device);
         if (!g.ok) return fail(HE_ERR_CUDA, "cannot select the calls' device");
         // the default first: it must build and run, or there is nothing to tune
-        float best_ms = time_tuning(calls, ncalls, cur, iters, st);
+        float best_ms = time_tuning(calls, ncalls, cur, iters, st, in_flight);
         if (best_ms < 0.0f) return he_plan_create_tuned(calls, ncalls, &cur, out);  // reports the error
         // which knobs matter for these calls
         he_plan_t probe = nullptr;
@@ -2168,7 +2301,7 @@ he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t
                 if (v == keep) continue;
                 he_plan_tuning t = cur;
                 t.*knob = v;
-                const float ms = time_tuning(calls, ncalls, t, iters, st);
+                const float ms = time_tuning(calls, ncalls, t, iters, st, in_flight);
                 if (ms >= 0.0f && ms < best_ms) {
                     best_ms = ms;
                     cur = t;
@@ -2183,6 +2316,7 @@ he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t
             try_knob(&he_plan_tuning::mac_ctas_per_sm, {2u, 1u});
         }
         if (has_fused) try_knob(&he_plan_tuning::fused_max_nj, {16u, 8u, 4u, 2u});
+        if (info.ntt_items) try_knob(&he_plan_tuning::tw_smem, {0u, 1u});
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache.push_back({key, cur});
     }

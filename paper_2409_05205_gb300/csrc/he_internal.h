@@ -38,6 +38,8 @@ struct RingView {
     const uint2 *tw_fwd;      // [L][N]  (psi^brv(i), Shoup)
     const uint2 *tw_inv;      // [L][N]  (psi^-brv(i), Shoup)
     const uint32_t *psi_pow;  // [L][2N] psi^e
+    const uint2 *tw_fwd3;     // [L][N]  tw_fwd in the three-phase transform's read order (tw3_pos),
+                              //         N = 4096 .. 16384; nullptr otherwise
 };
 
 struct he_params_s {
@@ -48,6 +50,7 @@ struct he_params_s {
     uint2 *d_tw_fwd;
     uint2 *d_tw_inv;
     uint32_t *d_psi_pow;
+    uint2 *d_tw_fwd3;
     void *ws;
     size_t ws_bytes;
 };
@@ -57,6 +60,13 @@ enum { HE_KIND_CONV = 1, HE_KIND_FC = 2 };
 // words of shared memory for n values in the padded layout (one pad word
 // per 32, see pidx)
 __host__ __device__ __forceinline__ uint32_t padded_words(uint32_t n) { return n + (n >> 5) + 1; }
+// Shared memory of the input-NTT kernel when it stages twiddles: the data
+// area (one padded 8192-word polynomial or two padded 4096-word ones), at
+// kNttTwOff a copy of the item's forward table (8192 entries, or two tables
+// of 4096), then two mbarriers.
+constexpr uint32_t kNttTwOff = (2u * (4096u + 128u + 1u) * 4u + 15u) & ~15u;
+constexpr uint32_t kNttStageBytes = kNttTwOff + 8192u * 8u + 16u;
+static_assert(kNttTwOff >= (8192u + 256u + 1u) * 4u, "staged twiddles overlap the data area");
 
 // bytes of shared memory for the folded kernel's nj polynomials of M words
 __host__ __device__ __forceinline__ size_t fold_smem_bytes(uint32_t nj, uint32_t M) {
@@ -204,6 +214,7 @@ struct CallDesc {
     const uint32_t *x_coeff;  // coefficient-domain input (nullptr when the call's input is in NTT form);
                               // masked server calls: c0 in either domain (a_ntt); client calls: v (int32)
     const uint2 *tw_fwd;      // [L][N]
+    const uint2 *tw_fwd3;     // [L][N] three-phase read order (RingView::tw_fwd3)
     uint32_t *z;              // split form: folded channel sums [parts][L][ncols][co][M]
     const uint32_t *src_b;    // masked server calls: sh [B][G][N]; client calls: i + sh (int32 [B][G][N])
     uint32_t kind, nj, nb, cpt;
@@ -230,8 +241,10 @@ struct CallDesc {
     LimbK limb[HE_MAX_LIMBS];
 };
 // status bits of a plan run: 1, 2: a bounded wait of the split / tensor-core
-// MAC kernel gave up; 4: a device-side bounds check failed (checks mode)
+// MAC kernel gave up; 4: a device-side bounds check failed (checks mode);
+// 8: the input-NTT kernel's wait for its staged twiddles gave up
 constexpr uint32_t kStatusBounds = 4u;
+constexpr uint32_t kStatusTwWait = 8u;
 // does [p, p + n) lie within [lo, lo + words)?
 __host__ __device__ __forceinline__ bool in_range(const void *p, size_t n, const void *lo, size_t words) {
     const uintptr_t a = (uintptr_t)p, b = (uintptr_t)lo;
@@ -395,6 +408,7 @@ struct he_plan_s {
     uint32_t *d_status;                 // bit 0 / bit 1: a bounded wait in the MAC / tensor-core MAC kernel gave up
     uint32_t wait_polls;                // polls of the split MAC kernel's waits before it gives up (he_plan_set_wait_limit)
     uint32_t checks;                    // device-side bounds checks on (he_plan_set_checks)
+    uint32_t tw_stage;                  // k_plan_ntt stages twiddle tables in shared memory (tuning tw_smem)
     uint8_t *split;                     // host: per call, 1 if it takes the split form
     he_plan_tuning tuning;
     // grouped plan (tuning.groups > 1): no kernels of its own; sub-plan g

@@ -806,13 +806,57 @@ __global__ void __launch_bounds__(kThreads) k_fc(const ConvGeo a, const RingView
 // ---------------------------------------------------------------------------
 // plan kernels (one CTA per item; items are ordered longest first on the host)
 // ---------------------------------------------------------------------------
+// bounded mbarrier waits and bulk copies (the plan kernels below)
+constexpr uint32_t kSpinLimit = HE_WAIT_POLLS_DEFAULT;  // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+// One bulk copy global -> shared whose completion is counted on `bar`.
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Waits for phase `parity` of `bar`; gives up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kSpinLimit) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Forward stage on register bit B of 16 values: pairs (j, j + 2^B) with bit
-// B of j clear, pair j using twiddle t[j >> (B + 1)] (bf_fwd, as everywhere).
-template <int B>
+// B of j clear, pair j using twiddle t[D * (j >> (B + 1))] (bf_fwd, as
+// everywhere).  SM: t points into shared memory.
+template <int B, int D = 1, bool SM = false>
 __device__ __forceinline__ void reg_stage16(uint32_t (&v)[16], const uint2 *__restrict__ t, uint32_t q, uint32_t q2) {
 #pragma unroll
     for (int blk = 0; blk < (16 >> (B + 1)); ++blk) {
-        const uint2 w = __ldg(t + blk);
+        const uint2 w = SM ? t[D * blk] : __ldg(t + D * blk);
 #pragma unroll
         for (int u = 0; u < (1 << B); ++u) bf_fwd(v[blk * (2 << B) + u], v[blk * (2 << B) + u + (1 << B)], w, q, q2);
     }
@@ -841,10 +885,18 @@ __device__ __forceinline__ void reg_stage16(uint32_t (&v)[16], const uint2 *__re
 // transform; S = 2 + h for half h of a 16384-point transform after its first
 // stage (ntt_fwd_16384), whose stage-P twiddles are tw[2^(13-P) (2 + h) / 2 +
 // (i >> (P+1))] with i the index within the half.
-template <int LOGN, int BAR, bool FROM_SM = false>
+// `tw` is the table in the transform's own order (RingView::tw_fwd3): in
+// stages P = 2, 1, 0 lane l's twiddle j of its warp's segment sits at 32 j + l
+// of the segment, so each load of phase C reads 32 consecutive entries.
+// TWSM: phase C reads a copy of the whole table in shared memory (`twc`,
+// same offsets), which bulk copies counted on `bar` are filling; the threads
+// wait for it (at most `polls` polls, then bit kStatusTwWait of `status`)
+// after phase B.
+template <int LOGN, int BAR, bool FROM_SM = false, bool TWSM = false>
 __device__ __forceinline__ void ntt_fwd_3ph(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
                                             uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q, uint32_t t,
-                                            uint32_t S = 1) {
+                                            uint32_t S = 1, const uint2 *twc = nullptr, uint64_t *bar = nullptr,
+                                            uint32_t polls = 0, uint32_t *status = nullptr) {
     static_assert(LOGN == 12 || LOGN == 13, "three-phase transform: N = 4096 or 8192");
     constexpr uint32_t T = 1u << (LOGN - 4), C = 1u << (LOGN - 12);  // threads; phase-C twiddle scale
     const uint32_t q2 = 2u * q, w = t >> 5, l = t & 31u, CS = C * S;
@@ -880,8 +932,16 @@ __device__ __forceinline__ void ntt_fwd_3ph(const uint32_t *__restrict__ src, ui
     __syncwarp();
 #pragma unroll
     for (int m = 0; m < 16; ++m) v[m] = sm[pidx(b0 + 16u * l + m)];
+    const uint2 *tc = tw;
+    if constexpr (TWSM) {
+        if (!mbar_wait(bar, 0, polls)) {
+            atomicOr(status, kStatusTwWait);
+            mbar_wait(bar, 0);  // the copies land before the CTA's shared memory is released
+        }
+        tc = twc;
+    }
     {  // P = 4: element 16 l + m pairs with 16 (l ^ 1) + m
-        const uint2 w4 = __ldg(tw + 128 * CS + 16u * w + (l >> 1));
+        const uint2 w4 = TWSM ? tc[128 * CS + 16u * w + (l >> 1)] : __ldg(tw + 128 * CS + 16u * w + (l >> 1));
         const bool lower = (l & 1u) == 0u;
 #pragma unroll
         for (int m = 0; m < 16; ++m) {
@@ -893,10 +953,10 @@ __device__ __forceinline__ void ntt_fwd_3ph(const uint32_t *__restrict__ src, ui
             v[m] = lower ? U + Tw : U - Tw + q2;
         }
     }
-    reg_stage16<3>(v, tw + 256 * CS + 32u * w + l, q, q2);          // P = 3
-    reg_stage16<2>(v, tw + 512 * CS + 64u * w + 2u * l, q, q2);     // P = 2
-    reg_stage16<1>(v, tw + 1024 * CS + 128u * w + 4u * l, q, q2);   // P = 1
-    reg_stage16<0>(v, tw + 2048 * CS + 256u * w + 8u * l, q, q2);   // P = 0
+    reg_stage16<3, 1, TWSM>(v, tc + 256 * CS + 32u * w + l, q, q2);     // P = 3
+    reg_stage16<2, 32, TWSM>(v, tc + 512 * CS + 64u * w + l, q, q2);    // P = 2
+    reg_stage16<1, 32, TWSM>(v, tc + 1024 * CS + 128u * w + l, q, q2);  // P = 1
+    reg_stage16<0, 32, TWSM>(v, tc + 2048 * CS + 256u * w + l, q, q2);  // P = 0
     uint4 *d4 = reinterpret_cast<uint4 *>(dst + b0 + 16u * l);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -1057,13 +1117,14 @@ __device__ __forceinline__ void fc_direct_body(const CallDesc &cd, const LimbK &
 
 // The forward transform of one plan input polynomial: the three-phase
 // kernel above for N = 8192 with 512 threads, else the pass-by-pass one.
-__device__ __forceinline__ void plan_fwd_ntt(const uint32_t *src, uint32_t *dst, uint32_t logN, const uint2 *tw,
+__device__ __forceinline__ void plan_fwd_ntt(const uint32_t *src, uint32_t *dst, const CallDesc &cd, uint32_t l,
                                              const LimbK &K, uint4 *smem4) {
+    const uint32_t logN = cd.g.logN;
     if (logN == 13 && blockDim.x == 512) {
-        ntt_fwd_8192_warp(src, dst, reinterpret_cast<uint32_t *>(smem4), tw, K.q);
+        ntt_fwd_8192_warp(src, dst, reinterpret_cast<uint32_t *>(smem4), cd.tw_fwd3 + (size_t)l * 8192u, K.q);
         return;
     }
-    ntt_body(src, dst, logN, tw, K, false, smem4);
+    ntt_body(src, dst, logN, cd.tw_fwd + ((size_t)l << logN), K, false, smem4);
 }
 
 // 512 threads: a polynomial's transform is the CTA's work, and its passes
@@ -1091,9 +1152,23 @@ __device__ __forceinline__ bool ntt_item_in_bounds(const CallDesc *__restrict__ 
     return in_range(cd.g.x + (size_t)it.poly * N, N, cd.g.x, cd.x_words);
 }
 
+// One thread starts the copy of `entries` twiddles (a whole forward table,
+// 16-byte aligned, a multiple of 2048 entries) into shared memory, counted
+// on `bar`.
+__device__ __forceinline__ void stage_twiddles(uint2 *dst, const uint2 *src, uint32_t entries, uint64_t *bar) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect(bar, entries * 8u);
+    for (uint32_t c = 0; c < entries; c += 2048u) bulk_load(dst + c, src + c, 2048u * 8u, bar);
+}
+
+// tw_stage: the launch's shared memory holds kNttStageBytes, and the
+// 4096- and 8192-point transforms read their last stages' twiddles from a
+// copy there (he_plan_tuning::tw_smem); polls bounds the wait for it.
 __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__restrict__ calls,
                                                       const NttItem *__restrict__ items,
-                                                      uint32_t *__restrict__ status, uint32_t checks) {
+                                                      uint32_t *__restrict__ status, uint32_t checks,
+                                                      uint32_t tw_stage, uint32_t polls) {
     extern __shared__ uint4 smem4[];
     pdl_trigger();  // the MAC kernel may start streaming weights now
     const NttItem it = items[blockIdx.x];
@@ -1102,18 +1177,36 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
         return;
     }
     if (it.src) {  // an ordinary input transform
+        uint32_t *sm = reinterpret_cast<uint32_t *>(smem4);
+        uint2 *twc = reinterpret_cast<uint2 *>(reinterpret_cast<char *>(smem4) + kNttTwOff);
+        uint64_t *bar = reinterpret_cast<uint64_t *>(twc + 8192);
         if (it.logN == 13 && blockDim.x == 512) {
-            ntt_fwd_8192_warp(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.tw, it.q);
+            if (tw_stage) {
+                if (threadIdx.x == 0) stage_twiddles(twc, it.tw, 8192u, bar);
+                ntt_fwd_3ph<13, 0, false, true>(it.src, it.dst, sm, it.tw, it.q, threadIdx.x, 1u, twc, bar, polls,
+                                                status);
+            } else {
+                ntt_fwd_8192_warp(it.src, it.dst, sm, it.tw, it.q);
+            }
         } else if (it.logN == 14 && blockDim.x == 512) {
-            ntt_fwd_16384(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.tw, it.q);
+            ntt_fwd_16384(it.src, it.dst, sm, it.tw, it.q);
         } else if (it.logN == 12 && it.src2 && blockDim.x == 512) {
             // two 4096-point transforms, one per half of the CTA, each in its
             // own padded half of shared memory, synchronized by named barriers
-            uint32_t *sm = reinterpret_cast<uint32_t *>(smem4);
-            if (threadIdx.x < 256u)
-                ntt_fwd_3ph<12, 1>(it.src, it.dst, sm, it.tw, it.q, threadIdx.x);
-            else
-                ntt_fwd_3ph<12, 2>(it.src2, it.dst2, sm + padded_words(4096), it.tw2, it.q2, threadIdx.x - 256u);
+            const uint32_t h = threadIdx.x >> 8, t = threadIdx.x & 255u;
+            if (tw_stage) {
+                uint2 *twh = twc + 4096u * h;
+                if (t == 0) stage_twiddles(twh, h ? it.tw2 : it.tw, 4096u, bar + h);
+                if (h == 0)
+                    ntt_fwd_3ph<12, 1, false, true>(it.src, it.dst, sm, it.tw, it.q, t, 1u, twh, bar, polls, status);
+                else
+                    ntt_fwd_3ph<12, 2, false, true>(it.src2, it.dst2, sm + padded_words(4096), it.tw2, it.q2, t, 1u,
+                                                    twh, bar + 1, polls, status);
+            } else if (h == 0) {
+                ntt_fwd_3ph<12, 1>(it.src, it.dst, sm, it.tw, it.q, t);
+            } else {
+                ntt_fwd_3ph<12, 2>(it.src2, it.dst2, sm + padded_words(4096), it.tw2, it.q2, t);
+            }
         } else {
             ntt_fwd_c(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.logN, it.tw, it.q);
         }
@@ -1135,12 +1228,12 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
         const uint32_t G = cd.g.G >> 1, gz = (it.poly / L) % (2u * G), b = it.poly / (L * 2u * G);
         const size_t row = (size_t)b * G + (gz < G ? gz : gz - G);
         if (cd.msrc == 1u && gz >= G) {
-            plan_fwd_ntt(cd.src_b + row * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, smem4);
+            plan_fwd_ntt(cd.src_b + row * N, dst, cd, l, K, smem4);
         } else if (cd.msrc == 1u && cd.a_ntt) {
             const uint4 *s4 = reinterpret_cast<const uint4 *>(cd.x_coeff + (row * L + l) * N);
             for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) reinterpret_cast<uint4 *>(dst)[i] = __ldg(s4 + i);
         } else if (cd.msrc == 1u) {
-            plan_fwd_ntt(cd.x_coeff + (row * L + l) * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, smem4);
+            plan_fwd_ntt(cd.x_coeff + (row * L + l) * N, dst, cd, l, K, smem4);
         } else {
             const int32_t *src = reinterpret_cast<const int32_t *>(gz < G ? cd.x_coeff : cd.src_b) + row * N;
             uint32_t *a = reinterpret_cast<uint32_t *>(smem4);
@@ -1150,7 +1243,7 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
         }
         return;
     }
-    plan_fwd_ntt(cd.x_coeff + (size_t)it.poly * N, dst, cd.g.logN, cd.tw_fwd + (size_t)l * N, K, smem4);
+    plan_fwd_ntt(cd.x_coeff + (size_t)it.poly * N, dst, cd, l, K, smem4);
 }
 
 template <int NJ>
@@ -1182,47 +1275,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<NJ>::value) k_plan_chan(co
 // split form of the channel step (plans): a MAC kernel per slot tile, then a
 // finishing kernel per output polynomial
 // ---------------------------------------------------------------------------
-constexpr uint32_t kSpinLimit = HE_WAIT_POLLS_DEFAULT;  // bounded mbarrier waits
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-// One bulk copy global -> shared whose completion is counted on `bar`.
-// dst, src 16-byte aligned, bytes a multiple of 16.
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-
-// Waits for phase `parity` of `bar`; gives up after `limit` polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit = kSpinLimit) {
-    const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < limit; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 // Persistent MAC kernel of the split form (one ciphertext per call:
 // columns c0, c1).  Each CTA owns a list of work items (call, limb l, slot
@@ -2102,7 +2154,8 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     if (pl.n_ntt && (phase == -1 || phase == 0)) {
         e = set_smem(k_plan_ntt, pl.smem_ntt);
         if (e != cudaSuccess) return e;
-        k_plan_ntt<<<pl.n_ntt, kNttThreads, pl.smem_ntt, st>>>(pl.d_calls, pl.d_ntt, pl.d_status, pl.checks);
+        k_plan_ntt<<<pl.n_ntt, kNttThreads, pl.smem_ntt, st>>>(pl.d_calls, pl.d_ntt, pl.d_status, pl.checks,
+                                                               pl.tw_stage, pl.wait_polls);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

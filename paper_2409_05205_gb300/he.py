@@ -60,7 +60,8 @@ class he_op_counts(ctypes.Structure):
 
 class he_plan_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("split", "mac_item_kb", "mac_ctas_per_sm", "fused_max_nj",
-                                               "tc_min_batch", "fc_direct", "groups", "fin_parts")]
+                                               "tc_min_batch", "fc_direct", "groups", "fin_parts",
+                                               "tw_smem")]
 
 
 class he_plan_info(ctypes.Structure):
@@ -130,6 +131,8 @@ _SIGS = {
     "he_plan_set_checks": [_vp, _i32],
     "he_plan_autotune": [ctypes.POINTER(he_layer_call), _u32, _u32, _vp, ctypes.POINTER(he_plan_tuning),
                          ctypes.POINTER(_vp)],
+    "he_plan_autotune_inflight": [ctypes.POINTER(he_layer_call), _u32, _u32, _u32, _vp,
+                                  ctypes.POINTER(he_plan_tuning), ctypes.POINTER(_vp)],
     "he_plan_run": [_vp, _vp],
     "he_plan_run_host": [_vp, _vp, _vp, _vp],
     "he_plan_host_words": [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
@@ -452,7 +455,8 @@ def he_plan_tuning_default() -> dict:
 
 
 def he_plan_create_tuned(calls, tuning: dict) -> int:
-    t = he_plan_tuning(**tuning)
+    """tuning: knob -> value; knobs it leaves out keep their default."""
+    t = he_plan_tuning(**dict(he_plan_tuning_default(), **tuning))
     out = _vp()
     _check(lib().he_plan_create_tuned(_calls(calls), len(calls), ctypes.byref(t), ctypes.byref(out)))
     return out.value
@@ -483,6 +487,15 @@ def he_plan_autotune(calls, iters: int = 5, stream=None) -> tuple[int, dict]:
     out = _vp()
     _check(lib().he_plan_autotune(_calls(calls), len(calls), iters, _stream(stream), ctypes.byref(t),
                                   ctypes.byref(out)))
+    return out.value, _tuning_dict(t)
+
+
+def he_plan_autotune_inflight(calls, iters: int = 5, in_flight: int = 2, stream=None) -> tuple[int, dict]:
+    """(plan, chosen tuning) for `in_flight` runs in flight at once."""
+    t = he_plan_tuning()
+    out = _vp()
+    _check(lib().he_plan_autotune_inflight(_calls(calls), len(calls), iters, in_flight, _stream(stream),
+                                           ctypes.byref(t), ctypes.byref(out)))
     return out.value, _tuning_dict(t)
 
 

@@ -117,7 +117,10 @@ def test_plan_rescales_every_output(fin_parts):
                      (banks[0], cts2, H.HE_COEFF, outs[2], 2, None, None, rsc[2]),
                      (banks[2], fct, H.HE_COEFF, outs[3], 2, None, None, rsc[3]),
                      (banks[2], fcn, H.HE_NTT, outs[4], 2, None, None, rsc[4])]
-            plan = H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), fin_parts=fin_parts))
+            # the input transforms (4096-point pairs) read their twiddles from
+            # global memory with one part, from shared memory with two
+            plan = H.he_plan_create_tuned(calls, dict(H.he_plan_tuning_default(), fin_parts=fin_parts,
+                                                      tw_smem=fin_parts - 1))
             try:
                 info = H.he_plan_query(plan, len(calls))
                 # split Conv (scalar MAC), fused-form Conv, direct FC, FC on the transform path

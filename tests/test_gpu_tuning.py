@@ -46,15 +46,15 @@ def _check(H, calls, refs):
 # transforms; groups > 1 runs the calls in that many groups on the plan's own
 # streams
 TUNINGS = [dict(split=1, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=4, fc_direct=1, groups=1,
-                fin_parts=1),
+                fin_parts=1, tw_smem=1),
            dict(split=0, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=1, fc_direct=0, groups=2,
-                fin_parts=2),
+                fin_parts=2, tw_smem=0),
            dict(split=1, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=2, tc_min_batch=8, fc_direct=1, groups=3,
-                fin_parts=4),
+                fin_parts=4, tw_smem=1),
            dict(split=1, mac_item_kb=64, mac_ctas_per_sm=2, fused_max_nj=4, tc_min_batch=2, fc_direct=0, groups=2,
-                fin_parts=2),
+                fin_parts=2, tw_smem=0),
            dict(split=0, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=8, tc_min_batch=4, fc_direct=1, groups=3,
-                fin_parts=4)]
+                fin_parts=4, tw_smem=0)]
 
 
 def test_every_tuning_gives_the_oracle_words():
@@ -116,6 +116,44 @@ def test_autotune_picks_a_valid_tuning_and_caches_it():
             assert t2 == t
             assert all((U.from_dev(c[3]) == 0xFFFFFFFF).all() for c in calls)
             assert dt < 5.0
+        finally:
+            for f in banks:
+                H.he_filters_destroy(f)
+
+
+def test_autotune_in_flight_computes_the_calls_and_caches_per_regime():
+    """The in-flight autotuner times candidates as three plans in flight
+    (the first on the calls' buffers, the others on private outputs): the
+    calls' outputs hold the oracle's words afterwards, the returned plan
+    gives them again, and a second call with the same signature and regime
+    reuses the cached choice without running anything."""
+    H = U.he()
+    torch = U.torch_cuda()
+    with U.params(N, L) as p:
+        banks, calls, refs = _setup(H, p)
+        try:
+            s = torch.cuda.current_stream()
+            for c in calls:
+                c[3].fill_(-1)
+            plan, t = H.he_plan_autotune_inflight(calls, 3, 3, s)
+            try:
+                H.he_sync(s)
+                _check(H, calls, refs)
+                assert H.he_plan_query(plan)["tuning"] == t
+                for c in calls:
+                    c[3].fill_(-1)
+                H.he_plan_run(plan, s)
+                H.he_sync(s)
+                H.he_plan_check(plan)
+                _check(H, calls, refs)
+            finally:
+                H.he_plan_destroy(plan)
+            for c in calls:
+                c[3].fill_(-1)
+            plan2, t2 = H.he_plan_autotune_inflight(calls, 3, 3, s)
+            H.he_plan_destroy(plan2)
+            assert t2 == t
+            assert all((U.from_dev(c[3]) == 0xFFFFFFFF).all() for c in calls)
         finally:
             for f in banks:
                 H.he_filters_destroy(f)
