@@ -522,7 +522,12 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *                    its last stages read it there (99 KB of shared memory
  *                    per CTA instead of 34 KB); 0 (default): they read it
  *                    from global memory (L2), in an order that makes every
- *                    load coalesced. */
+ *                    load coalesced.
+ *   mac_pdl          1 (default): the MAC kernel (split form or tensor
+ *                    core) is launched as a programmatic dependent of the
+ *                    input-NTT kernel: its CTAs start streaming weights while
+ *                    the transforms run, then wait for them; 0: an ordinary
+ *                    launch, after the input-NTT kernel has finished. */
 typedef struct {
     uint32_t split;
     uint32_t mac_item_kb;
@@ -533,6 +538,7 @@ typedef struct {
     uint32_t groups;
     uint32_t fin_parts;
     uint32_t tw_smem;
+    uint32_t mac_pdl;
 } he_plan_tuning;
 
 /* The default tuning. */

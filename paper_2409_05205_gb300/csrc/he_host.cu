@@ -1047,6 +1047,7 @@ he_status he_plan_tuning_default(he_plan_tuning *t) {
     t->groups = 1;
     t->fin_parts = 1;
     t->tw_smem = 0;
+    t->mac_pdl = 1;
     return HE_OK;
 }
 
@@ -1065,6 +1066,7 @@ he_status check_tuning(const he_plan_tuning &t) {
     if (t.fin_parts != 1 && t.fin_parts != 2 && t.fin_parts != 4)
         return fail(HE_ERR_ARG, "tuning: fin_parts must be 1, 2 or 4");
     if (t.tw_smem > 1) return fail(HE_ERR_ARG, "tuning: tw_smem must be 0 or 1");
+    if (t.mac_pdl > 1) return fail(HE_ERR_ARG, "tuning: mac_pdl must be 0 or 1");
     return HE_OK;
 }
 }  // namespace
@@ -1654,6 +1656,7 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
         if (tu.tw_smem && it.second.src && (g.logN == 13 || it.second.src2)) pl->tw_stage = 1;
     }
     if (pl->tw_stage) pl->smem_ntt = std::max(pl->smem_ntt, (size_t)kNttStageBytes);
+    pl->mac_pdl = tu.mac_pdl;
     pl->n_ntt = (uint32_t)ntt.size();
     pl->n_fc = n_fc;
     auto upload = [&](ChanItem **dst, const std::vector<ChanItem> &v) -> cudaError_t {
@@ -2317,6 +2320,7 @@ he_status he_plan_autotune_inflight(const he_layer_call *calls, uint32_t ncalls,
         }
         if (has_fused) try_knob(&he_plan_tuning::fused_max_nj, {16u, 8u, 4u, 2u});
         if (info.ntt_items) try_knob(&he_plan_tuning::tw_smem, {0u, 1u});
+        if (info.mac_items || info.tc_items) try_knob(&he_plan_tuning::mac_pdl, {1u, 0u});
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache.push_back({key, cur});
     }

@@ -409,6 +409,7 @@ struct he_plan_s {
     uint32_t wait_polls;                // polls of the split MAC kernel's waits before it gives up (he_plan_set_wait_limit)
     uint32_t checks;                    // device-side bounds checks on (he_plan_set_checks)
     uint32_t tw_stage;                  // k_plan_ntt stages twiddle tables in shared memory (tuning tw_smem)
+    uint32_t mac_pdl;                   // MAC kernels launched as programmatic dependents (tuning mac_pdl)
     uint8_t *split;                     // host: per call, 1 if it takes the split form
     he_plan_tuning tuning;
     // grouped plan (tuning.groups > 1): no kernels of its own; sub-plan g

@@ -2124,7 +2124,7 @@ cudaError_t he_plan_prepare(const he_plan_s &pl) {
 // completes (programmatic dependent launch; the kernel calls pdl_wait()
 // before it reads what that kernel wrote).
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kern)(KArgs...), uint32_t grid, uint32_t block, size_t smem, cudaStream_t st,
+cudaError_t launch_pdl(bool pdl, void (*kern)(KArgs...), uint32_t grid, uint32_t block, size_t smem, cudaStream_t st,
                        Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -2135,7 +2135,7 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), uint32_t grid, uint32_t block, si
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
@@ -2161,13 +2161,14 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
     }
     if (phase == 0) return cudaSuccess;
     if (pl.n_mac && phase != 3) {
-        e = launch_pdl(k_plan_mac, pl.mac_ctas, kThreads + 32, pl.smem_mac, st, (const MacCopy *)pl.d_mac_copy,
+        e = launch_pdl(pl.mac_pdl != 0, k_plan_mac, pl.mac_ctas, kThreads + 32, pl.smem_mac, st,
+                       (const MacCopy *)pl.d_mac_copy,
                        (const MacDesc *)pl.d_mac_desc, (const uint32_t *)pl.d_mac_offs, pl.d_status, pl.mac_xw,
                        pl.mac_nst, pl.wait_polls, pl.checks);
         if (e != cudaSuccess) return e;
     }
     if (pl.n_tc && phase != 3) {
-        if ((e = he_launch_tc_mac(pl, st, true)) != cudaSuccess) return e;
+        if ((e = he_launch_tc_mac(pl, st, pl.mac_pdl != 0)) != cudaSuccess) return e;
     }
     if (phase == 2) return cudaSuccess;
     if (pl.n_fin) {
