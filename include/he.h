@@ -570,9 +570,11 @@ he_status he_plan_autotune(const he_layer_call *calls, uint32_t ncalls, uint32_t
  * a CUDA graph on its own stream, run k on plan k % in_flight (the
  * throughput of that regime, where kernels of different runs share the SMs;
  * it can pick another tuning than one run at a time does).  The first plan
- * works on the calls' buffers; the others read the same inputs and write
- * private output buffers, allocated and freed per candidate.  Cached per
- * signature and in_flight; in_flight = 1 is he_plan_autotune.  Blocking. */
+ * works on the calls' buffers; each other one on device copies of the
+ * calls' banks, inputs and outputs (allocated for the tuning and freed
+ * before it returns: in_flight - 1 times the calls' weight and I/O bytes),
+ * so that no run reads another's weights from L2.  Cached per signature and
+ * in_flight; in_flight = 1 is he_plan_autotune.  Blocking. */
 he_status he_plan_autotune_inflight(const he_layer_call *calls, uint32_t ncalls, uint32_t iters,
                                     uint32_t in_flight, void *stream, he_plan_tuning *best, he_plan_t *out);
 /* Runs every call of the plan.  Asynchronous on `stream`. */

@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <string>
@@ -2164,23 +2165,98 @@ float time_tuning_1(const he_layer_call *calls, uint32_t ncalls, const he_plan_t
     return ms;
 }
 
+// A device copy of a bank (weights, their scalar-layout or coefficient-domain
+// copy, bias), for timing runs that must not share weights through L2.
+he_status clone_filters(const he_filters_s *f, he_filters_t *out) {
+    he_filters_s *c = new (std::nothrow) he_filters_s(*f);
+    if (!c) return fail(HE_ERR_NOMEM, "out of host memory");
+    c->bank = c->bank_s = c->bias = nullptr;
+    const size_t nbias = f->bias ? (size_t)f->p->L * f->fl.n_out * sizeof(uint32_t) : 0;
+    cudaError_t e = cudaMalloc(&c->bank, f->bank_bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(c->bank, f->bank, f->bank_bytes, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && f->bank_s) e = cudaMalloc(&c->bank_s, f->bank_bytes);
+    if (e == cudaSuccess && f->bank_s) e = cudaMemcpy(c->bank_s, f->bank_s, f->bank_bytes, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess && nbias) e = cudaMalloc(&c->bias, nbias);
+    if (e == cudaSuccess && nbias) e = cudaMemcpy(c->bias, f->bias, nbias, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+        he_filters_destroy(c);
+        return cuda_fail(e, "copy of a bank for the in-flight autotuner");
+    }
+    *out = c;
+    return HE_OK;
+}
+
+// The calls over private device copies of every bank, input and output of
+// the originals (inputs copied, so every run computes on the same words):
+// one independent run for the in-flight autotuner's timing.
+struct Replica {
+    std::vector<he_layer_call> calls;
+    std::vector<he_filters_t> banks;
+    uint32_t *buf = nullptr;
+    Replica() = default;
+    Replica(const Replica &) = delete;
+    Replica &operator=(const Replica &) = delete;
+    ~Replica() {
+        for (he_filters_t f : banks) he_filters_destroy(f);
+        cudaFree(buf);
+    }
+};
+
+he_status make_replica(const he_layer_call *calls, uint32_t ncalls, Replica &r) {
+    he_plan_tuning t;
+    he_plan_tuning_default(&t);
+    std::vector<IoSeg> io_in, io_out;
+    size_t ws = 0;
+    he_status st = plan_build(calls, ncalls, &t, nullptr, &ws, false, &io_in, &io_out);
+    if (st != HE_OK) return st;
+    auto piece = [](size_t w) { return (w + 63u) & ~(size_t)63u; };  // 256-byte aligned pieces
+    size_t words = 0;
+    for (const IoSeg &sg : io_in) words += piece(sg.words);
+    for (const IoSeg &sg : io_out) words += piece(sg.words);
+    cudaError_t e = cudaMalloc(&r.buf, std::max<size_t>(words, 1) * sizeof(uint32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "buffers of the in-flight autotuner");
+    r.calls.assign(calls, calls + ncalls);
+    std::vector<std::pair<const he_filters_s *, he_filters_t>> cloned;
+    size_t off = 0, si = 0, so = 0;
+    auto take = [&](const IoSeg &sg, bool copy) -> uint32_t * {
+        uint32_t *d = r.buf + off;
+        off += piece(sg.words);
+        if (copy && e == cudaSuccess) e = cudaMemcpy(d, sg.dev, sg.words * sizeof(uint32_t), cudaMemcpyDeviceToDevice);
+        return d;
+    };
+    for (uint32_t i = 0; i < ncalls; ++i) {
+        he_layer_call &c = r.calls[i];
+        he_filters_t f = nullptr;
+        for (auto &kv : cloned)
+            if (kv.first == calls[i].filters) f = kv.second;
+        if (!f) {
+            if ((st = clone_filters(calls[i].filters, &f)) != HE_OK) return st;
+            r.banks.push_back(f);
+            cloned.push_back({calls[i].filters, f});
+        }
+        c.filters = f;
+        // the order of plan_build's segments: d_in, d_share, d_share_out; d_out, d_rescaled
+        c.d_in = take(io_in[si++], true);
+        if (calls[i].filters->masked) c.d_share = take(io_in[si++], true);
+        if (calls[i].filters->masked == 1u) c.d_share_out = take(io_in[si++], true);
+        c.d_out = take(io_out[so++], false);
+        if (c.d_rescaled) c.d_rescaled = take(io_out[so++], false);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "inputs of the in-flight autotuner");
+    return HE_OK;
+}
+
 // Milliseconds per plan run with `in_flight` runs in flight: that many plans
 // of the tuning, each captured in a CUDA graph on a stream of its own, run
 // k goes to plan k % in_flight; best of three batches of `iters` runs after
-// two warm-up runs of each.  Plan 0 works on the calls' buffers; the others
-// read the same inputs and write private outputs (allocated here).  -1 when
-// something fails.
+// two warm-up runs of each.  Plan 0 works on the calls' buffers, plan j >= 1
+// on reps[j - 1] (its own banks, inputs and outputs).  -1 when something
+// fails.
 float time_tuning(const he_layer_call *calls, uint32_t ncalls, const he_plan_tuning &t, uint32_t iters,
-                  cudaStream_t st, uint32_t in_flight) {
-    if (in_flight <= 1) return time_tuning_1(calls, ncalls, t, iters, st);
-    std::vector<IoSeg> io_in, io_out;
-    size_t ws = 0;
-    if (plan_build(calls, ncalls, &t, nullptr, &ws, false, &io_in, &io_out) != HE_OK) return -1.0f;
-    size_t words = 0;
-    for (const IoSeg &sg : io_out) words += (sg.words + 63u) & ~(size_t)63u;  // 256-byte aligned pieces
-    const uint32_t k = in_flight;
+                  cudaStream_t st, const std::vector<std::unique_ptr<Replica>> &reps) {
+    if (reps.empty()) return time_tuning_1(calls, ncalls, t, iters, st);
+    const uint32_t k = (uint32_t)reps.size() + 1u;
     std::vector<he_plan_t> pls(k, nullptr);
-    std::vector<uint32_t *> scratch(k, nullptr);
     std::vector<cudaStream_t> ss(k, nullptr);
     std::vector<cudaEvent_t> joins(k, nullptr);
     std::vector<cudaGraphExec_t> ge(k, nullptr);
@@ -2191,22 +2267,7 @@ float time_tuning(const he_layer_call *calls, uint32_t ncalls, const he_plan_tun
         ok = cudaStreamCreateWithFlags(&ss[j], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&joins[j], cudaEventDisableTiming) == cudaSuccess;
         if (!ok) break;
-        if (j == 0) {
-            ok = he_plan_create_tuned(calls, ncalls, &t, &pls[0]) == HE_OK;
-        } else {
-            ok = cudaMalloc(&scratch[j], std::max<size_t>(words, 1) * sizeof(uint32_t)) == cudaSuccess;
-            std::vector<he_layer_call> cj(calls, calls + ncalls);
-            size_t off = 0, seg = 0;
-            for (uint32_t i = 0; i < ncalls && ok; ++i) {  // io_out's order: d_out, then d_rescaled
-                cj[i].d_out = scratch[j] + off;
-                off += (io_out[seg++].words + 63u) & ~(size_t)63u;
-                if (cj[i].d_rescaled) {
-                    cj[i].d_rescaled = scratch[j] + off;
-                    off += (io_out[seg++].words + 63u) & ~(size_t)63u;
-                }
-            }
-            ok = ok && he_plan_create_tuned(cj.data(), ncalls, &t, &pls[j]) == HE_OK;
-        }
+        ok = he_plan_create_tuned(j ? reps[j - 1]->calls.data() : calls, ncalls, &t, &pls[j]) == HE_OK;
         // one run outside capture first (it also sets the kernels' attributes)
         ok = ok && he_plan_run(pls[j], ss[j]) == HE_OK && cudaStreamSynchronize(ss[j]) == cudaSuccess;
         cudaGraph_t g = nullptr;
@@ -2244,7 +2305,6 @@ float time_tuning(const he_layer_call *calls, uint32_t ncalls, const he_plan_tun
         if (joins[j]) cudaEventDestroy(joins[j]);
         if (ss[j]) cudaStreamDestroy(ss[j]);
         he_plan_destroy(pls[j]);
-        cudaFree(scratch[j]);
     }
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
@@ -2279,8 +2339,16 @@ he_status he_plan_autotune_inflight(const he_layer_call *calls, uint32_t ncalls,
         cudaStream_t st = (cudaStream_t)stream;
         DeviceGuard g(calls[0].filters->p->device);
         if (!g.ok) return fail(HE_ERR_CUDA, "cannot select the calls' device");
+        // in_flight - 1 independent copies of the calls (freed on return)
+        std::vector<std::unique_ptr<Replica>> reps;
+        for (uint32_t j = 1; j < in_flight; ++j) {
+            reps.emplace_back(new (std::nothrow) Replica());
+            if (!reps.back()) return fail(HE_ERR_NOMEM, "out of host memory");
+            const he_status rs = make_replica(calls, ncalls, *reps.back());
+            if (rs != HE_OK) return rs;
+        }
         // the default first: it must build and run, or there is nothing to tune
-        float best_ms = time_tuning(calls, ncalls, cur, iters, st, in_flight);
+        float best_ms = time_tuning(calls, ncalls, cur, iters, st, reps);
         if (best_ms < 0.0f) return he_plan_create_tuned(calls, ncalls, &cur, out);  // reports the error
         // which knobs matter for these calls
         he_plan_t probe = nullptr;
@@ -2304,7 +2372,7 @@ he_status he_plan_autotune_inflight(const he_layer_call *calls, uint32_t ncalls,
                 if (v == keep) continue;
                 he_plan_tuning t = cur;
                 t.*knob = v;
-                const float ms = time_tuning(calls, ncalls, t, iters, st, in_flight);
+                const float ms = time_tuning(calls, ncalls, t, iters, st, reps);
                 if (ms >= 0.0f && ms < best_ms) {
                     best_ms = ms;
                     cur = t;

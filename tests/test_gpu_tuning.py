@@ -123,7 +123,8 @@ def test_autotune_picks_a_valid_tuning_and_caches_it():
 
 def test_autotune_in_flight_computes_the_calls_and_caches_per_regime():
     """The in-flight autotuner times candidates as three plans in flight
-    (the first on the calls' buffers, the others on private outputs): the
+    (the first on the calls' buffers, the others on copies of the banks,
+    inputs and outputs): the
     calls' outputs hold the oracle's words afterwards, the returned plan
     gives them again, and a second call with the same signature and regime
     reuses the cached choice without running anything."""
