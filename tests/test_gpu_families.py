@@ -2,8 +2,8 @@
 the w3 variants at 48 / 96 / 192 channels, ResNet-style 1x1 layers with
 c_o < c_i and c_o > c_i, and their 3x3 layers at 14x14) at full size,
 N = 8192 and 3 limbs: a plan, single calls and the oracle give the same
-words (every word of one limb by the oracle's NTT tier, sampled words of
-every limb by its schoolbook dot products).  Every layer with an interleave
+words (every word of every limb by the oracle's NTT tier, and sampled words
+by its schoolbook dot products, an independent tier).  Every layer with an interleave
 s >= 4 takes the split form in the plan, its input groups taken in parts of
 8, 4, 2 or 1 (G = 12, 6, 3, 32 have 3, 3, 3, 4 parts)."""
 
@@ -51,10 +51,8 @@ def test_layer_family_full_size(ci, co, hw, f, pad, N, L):
                 H.he_plan_destroy(plan)
             got = U.from_dev(d_out).reshape(single.shape)
             np.testing.assert_array_equal(got, single, err_msg=f"fin_parts {fin_parts}")
-    l = (ci + co) % L
-    ref = O.conv_layer(np.ascontiguousarray(cts[:, :, :, l:l + 1]), F, [ps[l]], [psis[l]], lay, O.OUT_EXTRACTED,
-                       tier="ntt")
-    np.testing.assert_array_equal(got[:, :, :, l:l + 1], ref)
+    ref = O.conv_layer(cts, F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt")
+    np.testing.assert_array_equal(got, ref)
     rng = np.random.default_rng(co)
     picks = [(0, int(rng.integers(lay["H"])), int(rng.integers(2)), int(rng.integers(L)), int(rng.integers(N)))
              for _ in range(16)]
