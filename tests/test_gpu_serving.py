@@ -1,7 +1,7 @@
 """The request loop: inferences of two models on different rings arrive
 together, are batched per (model, layer) and run on several streams; each
 result is word for word the result of the same inference served alone, and
-the oracle's for sampled requests.  An HBM budget too small for more than a
+the oracle's (every request, every layer).  An HBM budget too small for more than a
 few batch buffers still serves everything, within the budget."""
 
 from __future__ import annotations
@@ -132,20 +132,23 @@ def test_served_in_a_mix_equals_served_alone_and_the_oracle(setup):
     for a, b in zip(got, ref):
         for x, y in zip(a, b):
             np.testing.assert_array_equal(x, y)
-    # two requests of each model against the oracle, every layer
+    # every request against the oracle, every layer (one batched oracle call
+    # per model and layer over that model's requests)
     for m in (0, 1):
         N, L, layers = MODELS[m]
         ps, psis = U.ring(N, L)
-        for k in [k for k, mm in enumerate(models) if mm == m][:2]:
-            for i, d in enumerate(layers):
-                x = mix[k][1][i].numpy().view(np.uint32).reshape(setup.geo[m][i][0])
-                if d["kind"] == "conv":
-                    lay, F = setup.layers[m][i]
-                    want = O.conv_layer(x[None], F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt")[0]
-                else:
-                    lay, W, Bv = setup.layers[m][i]
-                    want = O.fc_layer(x[None], W, Bv, ps, psis, U.T, lay, O.OUT_EXTRACTED, tier="ntt")[0]
-                np.testing.assert_array_equal(got[k][i].view(np.uint32).reshape(want.shape), want)
+        ks = [k for k, mm in enumerate(models) if mm == m]
+        for i, d in enumerate(layers):
+            x = np.stack([mix[k][1][i].numpy().view(np.uint32).reshape(setup.geo[m][i][0]) for k in ks])
+            if d["kind"] == "conv":
+                lay, F = setup.layers[m][i]
+                want = O.conv_layer(x, F, ps, psis, lay, O.OUT_EXTRACTED, tier="ntt")
+            else:
+                lay, W, Bv = setup.layers[m][i]
+                want = O.fc_layer(x, W, Bv, ps, psis, U.T, lay, O.OUT_EXTRACTED, tier="ntt")
+            for j, k in enumerate(ks):
+                np.testing.assert_array_equal(got[k][i].view(np.uint32).reshape(want[j].shape), want[j],
+                                              err_msg=f"request {k} (model {m}) layer {i}")
 
 
 # device memory the server's own bookkeeping may hold beyond its budget: the
