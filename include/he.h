@@ -527,7 +527,13 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *                    core) is launched as a programmatic dependent of the
  *                    input-NTT kernel: its CTAs start streaming weights while
  *                    the transforms run, then wait for them; 0: an ordinary
- *                    launch, after the input-NTT kernel has finished. */
+ *                    launch, after the input-NTT kernel has finished.
+ *   l2_hints         L2 eviction priorities of the input-NTT and split MAC
+ *                    kernels' accesses: 1 (default): the weights and the
+ *                    coefficient-domain inputs, read once per run, are
+ *                    evicted first, so that they do not push out the NTT
+ *                    images and folded sums the next kernel reads; 2: those
+ *                    are also kept (evicted last); 0: no hints. */
 typedef struct {
     uint32_t split;
     uint32_t mac_item_kb;
@@ -539,6 +545,7 @@ typedef struct {
     uint32_t fin_parts;
     uint32_t tw_smem;
     uint32_t mac_pdl;
+    uint32_t l2_hints;
 } he_plan_tuning;
 
 /* The default tuning. */

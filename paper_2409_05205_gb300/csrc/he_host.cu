@@ -1049,6 +1049,7 @@ he_status he_plan_tuning_default(he_plan_tuning *t) {
     t->fin_parts = 1;
     t->tw_smem = 0;
     t->mac_pdl = 1;
+    t->l2_hints = 1;
     return HE_OK;
 }
 
@@ -1068,6 +1069,7 @@ he_status check_tuning(const he_plan_tuning &t) {
         return fail(HE_ERR_ARG, "tuning: fin_parts must be 1, 2 or 4");
     if (t.tw_smem > 1) return fail(HE_ERR_ARG, "tuning: tw_smem must be 0 or 1");
     if (t.mac_pdl > 1) return fail(HE_ERR_ARG, "tuning: mac_pdl must be 0 or 1");
+    if (t.l2_hints > 2) return fail(HE_ERR_ARG, "tuning: l2_hints must be 0, 1 or 2");
     return HE_OK;
 }
 }  // namespace
@@ -1658,6 +1660,7 @@ he_status plan_build(const he_layer_call *calls, uint32_t ncalls, const he_plan_
     }
     if (pl->tw_stage) pl->smem_ntt = std::max(pl->smem_ntt, (size_t)kNttStageBytes);
     pl->mac_pdl = tu.mac_pdl;
+    pl->l2_hints = tu.l2_hints;
     pl->n_ntt = (uint32_t)ntt.size();
     pl->n_fc = n_fc;
     auto upload = [&](ChanItem **dst, const std::vector<ChanItem> &v) -> cudaError_t {
@@ -2389,6 +2392,7 @@ he_status he_plan_autotune_inflight(const he_layer_call *calls, uint32_t ncalls,
         if (has_fused) try_knob(&he_plan_tuning::fused_max_nj, {16u, 8u, 4u, 2u});
         if (info.ntt_items) try_knob(&he_plan_tuning::tw_smem, {0u, 1u});
         if (info.mac_items || info.tc_items) try_knob(&he_plan_tuning::mac_pdl, {1u, 0u});
+        if (info.mac_items) try_knob(&he_plan_tuning::l2_hints, {1u, 2u, 0u});
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache.push_back({key, cur});
     }

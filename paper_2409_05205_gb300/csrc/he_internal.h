@@ -410,6 +410,7 @@ struct he_plan_s {
     uint32_t checks;                    // device-side bounds checks on (he_plan_set_checks)
     uint32_t tw_stage;                  // k_plan_ntt stages twiddle tables in shared memory (tuning tw_smem)
     uint32_t mac_pdl;                   // MAC kernels launched as programmatic dependents (tuning mac_pdl)
+    uint32_t l2_hints;                  // L2 eviction priorities of the plan kernels (tuning l2_hints)
     uint8_t *split;                     // host: per call, 1 if it takes the split form
     he_plan_tuning tuning;
     // grouped plan (tuning.groups > 1): no kernels of its own; sub-plan g

@@ -849,6 +849,54 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// L2 eviction priorities for a plan's data (performance only): the weights
+// and inputs stream through L2 once per run and go first, so that what one
+// plan kernel writes for the next (the input transforms' NTT images, the
+// MAC's folded sums) stays for the next kernel to read from L2.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+// The policies of a plan run (he_plan_tuning::l2_hints): 0 none; 1 the
+// weights and the coefficient-domain inputs (read once per run) evicted
+// first; 2 also the NTT images and folded sums kept (evicted last) for the
+// kernel that reads them next.
+__device__ __forceinline__ uint64_t l2_once(uint32_t hints) { return hints ? l2_evict_first() : l2_evict_normal(); }
+__device__ __forceinline__ uint64_t l2_next(uint32_t hints) { return hints >= 2u ? l2_evict_last() : l2_evict_normal(); }
+__device__ __forceinline__ uint32_t ldg_l2(const uint32_t *p, uint64_t pol) {
+    uint32_t v;
+    asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+    return v;
+}
+// bulk_load with an L2 cache policy
+__device__ __forceinline__ void bulk_load_l2(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
+                                             uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ void st_l2(uint32_t *p, uint32_t v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(p), "r"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void st_l2(uint4 *p, uint4 v, uint64_t pol) {
+    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "r"(v.x), "r"(v.y),
+                 "r"(v.z), "r"(v.w), "l"(pol)
+                 : "memory");
+}
+
 // Forward stage on register bit B of 16 values: pairs (j, j + 2^B) with bit
 // B of j clear, pair j using twiddle t[D * (j >> (B + 1))] (bf_fwd, as
 // everywhere).  SM: t points into shared memory.
@@ -896,13 +944,19 @@ template <int LOGN, int BAR, bool FROM_SM = false, bool TWSM = false>
 __device__ __forceinline__ void ntt_fwd_3ph(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
                                             uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q, uint32_t t,
                                             uint32_t S = 1, const uint2 *twc = nullptr, uint64_t *bar = nullptr,
-                                            uint32_t polls = 0, uint32_t *status = nullptr) {
+                                            uint32_t polls = 0, uint32_t *status = nullptr, uint32_t hints = 0) {
     static_assert(LOGN == 12 || LOGN == 13, "three-phase transform: N = 4096 or 8192");
     constexpr uint32_t T = 1u << (LOGN - 4), C = 1u << (LOGN - 12);  // threads; phase-C twiddle scale
     const uint32_t q2 = 2u * q, w = t >> 5, l = t & 31u, CS = C * S;
     uint32_t v[16];
+    if constexpr (FROM_SM) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = FROM_SM ? sm[pidx(t + T * j)] : __ldg(src + t + T * j);
+        for (int j = 0; j < 16; ++j) v[j] = sm[pidx(t + T * j)];
+    } else {
+        const uint64_t once = l2_once(hints);  // the input is read once per run
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = ldg_l2(src + t + T * j, once);
+    }
     reg_stage16<3>(v, tw + 1 * S, q, q2);  // P = LOGN - 1
     reg_stage16<2>(v, tw + 2 * S, q, q2);
     reg_stage16<1>(v, tw + 4 * S, q, q2);
@@ -958,15 +1012,17 @@ __device__ __forceinline__ void ntt_fwd_3ph(const uint32_t *__restrict__ src, ui
     reg_stage16<1, 32, TWSM>(v, tc + 1024 * CS + 128u * w + l, q, q2);  // P = 1
     reg_stage16<0, 32, TWSM>(v, tc + 2048 * CS + 256u * w + l, q, q2);  // P = 0
     uint4 *d4 = reinterpret_cast<uint4 *>(dst + b0 + 16u * l);
+    const uint64_t keep = l2_next(hints);  // the MAC kernel reads the NTT image next
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        d4[k] = make_uint4(red_4q(v[4 * k], q2, q), red_4q(v[4 * k + 1], q2, q), red_4q(v[4 * k + 2], q2, q),
-                           red_4q(v[4 * k + 3], q2, q));
+        st_l2(d4 + k, make_uint4(red_4q(v[4 * k], q2, q), red_4q(v[4 * k + 1], q2, q), red_4q(v[4 * k + 2], q2, q),
+                                 red_4q(v[4 * k + 3], q2, q)), keep);
 }
 
 __device__ __forceinline__ void ntt_fwd_8192_warp(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
-                                                  uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q) {
-    ntt_fwd_3ph<13, 0>(src, dst, sm, tw, q, threadIdx.x);
+                                                  uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q,
+                                                  uint32_t hints = 0) {
+    ntt_fwd_3ph<13, 0>(src, dst, sm, tw, q, threadIdx.x, 1u, nullptr, nullptr, 0u, nullptr, hints);
 }
 
 // Forward negacyclic NTT of length 16384 by 512 threads: stage 13 (span
@@ -976,17 +1032,18 @@ __device__ __forceinline__ void ntt_fwd_8192_warp(const uint32_t *__restrict__ s
 // with its twiddle bases scaled by 2 + h (ntt_fwd_3ph).  `sm` holds
 // 2 padded_words(8192) words.
 __device__ __forceinline__ void ntt_fwd_16384(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
-                                           uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q) {
+                                           uint32_t *sm, const uint2 *__restrict__ tw, uint32_t q, uint32_t hints) {
     const uint32_t t = threadIdx.x, q2 = 2u * q;
     uint32_t *sm1 = sm + padded_words(8192);
     const uint2 w1 = __ldg(tw + 1);
+    const uint64_t once = l2_once(hints);
 #pragma unroll 1
     for (int r = 0; r < 4; ++r) {
         uint32_t a[4], b[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            a[u] = __ldg(src + t + 512u * (4 * r + u));
-            b[u] = __ldg(src + 8192u + t + 512u * (4 * r + u));
+            a[u] = ldg_l2(src + t + 512u * (4 * r + u), once);
+            b[u] = ldg_l2(src + 8192u + t + 512u * (4 * r + u), once);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -1000,7 +1057,8 @@ __device__ __forceinline__ void ntt_fwd_16384(const uint32_t *__restrict__ src, 
     // fit in the register budget)
 #pragma unroll 1
     for (uint32_t h = 0; h < 2; ++h)
-        ntt_fwd_3ph<13, 0, true>(nullptr, dst + 8192u * h, h ? sm1 : sm, tw, q, t, 2u + h);
+        ntt_fwd_3ph<13, 0, true>(nullptr, dst + 8192u * h, h ? sm1 : sm, tw, q, t, 2u + h, nullptr, nullptr, 0u,
+                                 nullptr, hints);
 }
 
 // ---------------------------------------------------------------------------
@@ -1118,10 +1176,10 @@ __device__ __forceinline__ void fc_direct_body(const CallDesc &cd, const LimbK &
 // The forward transform of one plan input polynomial: the three-phase
 // kernel above for N = 8192 with 512 threads, else the pass-by-pass one.
 __device__ __forceinline__ void plan_fwd_ntt(const uint32_t *src, uint32_t *dst, const CallDesc &cd, uint32_t l,
-                                             const LimbK &K, uint4 *smem4) {
+                                             const LimbK &K, uint4 *smem4, uint32_t hints) {
     const uint32_t logN = cd.g.logN;
     if (logN == 13 && blockDim.x == 512) {
-        ntt_fwd_8192_warp(src, dst, reinterpret_cast<uint32_t *>(smem4), cd.tw_fwd3 + (size_t)l * 8192u, K.q);
+        ntt_fwd_8192_warp(src, dst, reinterpret_cast<uint32_t *>(smem4), cd.tw_fwd3 + (size_t)l * 8192u, K.q, hints);
         return;
     }
     ntt_body(src, dst, logN, cd.tw_fwd + ((size_t)l << logN), K, false, smem4);
@@ -1168,7 +1226,7 @@ __device__ __forceinline__ void stage_twiddles(uint2 *dst, const uint2 *src, uin
 __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__restrict__ calls,
                                                       const NttItem *__restrict__ items,
                                                       uint32_t *__restrict__ status, uint32_t checks,
-                                                      uint32_t tw_stage, uint32_t polls) {
+                                                      uint32_t tw_stage, uint32_t polls, uint32_t hints) {
     extern __shared__ uint4 smem4[];
     pdl_trigger();  // the MAC kernel may start streaming weights now
     const NttItem it = items[blockIdx.x];
@@ -1184,12 +1242,12 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
             if (tw_stage) {
                 if (threadIdx.x == 0) stage_twiddles(twc, it.tw, 8192u, bar);
                 ntt_fwd_3ph<13, 0, false, true>(it.src, it.dst, sm, it.tw, it.q, threadIdx.x, 1u, twc, bar, polls,
-                                                status);
+                                                status, hints);
             } else {
-                ntt_fwd_8192_warp(it.src, it.dst, sm, it.tw, it.q);
+                ntt_fwd_8192_warp(it.src, it.dst, sm, it.tw, it.q, hints);
             }
         } else if (it.logN == 14 && blockDim.x == 512) {
-            ntt_fwd_16384(it.src, it.dst, sm, it.tw, it.q);
+            ntt_fwd_16384(it.src, it.dst, sm, it.tw, it.q, hints);
         } else if (it.logN == 12 && it.src2 && blockDim.x == 512) {
             // two 4096-point transforms, one per half of the CTA, each in its
             // own padded half of shared memory, synchronized by named barriers
@@ -1198,14 +1256,16 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
                 uint2 *twh = twc + 4096u * h;
                 if (t == 0) stage_twiddles(twh, h ? it.tw2 : it.tw, 4096u, bar + h);
                 if (h == 0)
-                    ntt_fwd_3ph<12, 1, false, true>(it.src, it.dst, sm, it.tw, it.q, t, 1u, twh, bar, polls, status);
+                    ntt_fwd_3ph<12, 1, false, true>(it.src, it.dst, sm, it.tw, it.q, t, 1u, twh, bar, polls, status,
+                                                    hints);
                 else
                     ntt_fwd_3ph<12, 2, false, true>(it.src2, it.dst2, sm + padded_words(4096), it.tw2, it.q2, t, 1u,
-                                                    twh, bar + 1, polls, status);
+                                                    twh, bar + 1, polls, status, hints);
             } else if (h == 0) {
-                ntt_fwd_3ph<12, 1>(it.src, it.dst, sm, it.tw, it.q, t);
+                ntt_fwd_3ph<12, 1>(it.src, it.dst, sm, it.tw, it.q, t, 1u, nullptr, nullptr, 0u, nullptr, hints);
             } else {
-                ntt_fwd_3ph<12, 2>(it.src2, it.dst2, sm + padded_words(4096), it.tw2, it.q2, t);
+                ntt_fwd_3ph<12, 2>(it.src2, it.dst2, sm + padded_words(4096), it.tw2, it.q2, t, 1u, nullptr, nullptr,
+                                   0u, nullptr, hints);
             }
         } else {
             ntt_fwd_c(it.src, it.dst, reinterpret_cast<uint32_t *>(smem4), it.logN, it.tw, it.q);
@@ -1228,12 +1288,12 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
         const uint32_t G = cd.g.G >> 1, gz = (it.poly / L) % (2u * G), b = it.poly / (L * 2u * G);
         const size_t row = (size_t)b * G + (gz < G ? gz : gz - G);
         if (cd.msrc == 1u && gz >= G) {
-            plan_fwd_ntt(cd.src_b + row * N, dst, cd, l, K, smem4);
+            plan_fwd_ntt(cd.src_b + row * N, dst, cd, l, K, smem4, hints);
         } else if (cd.msrc == 1u && cd.a_ntt) {
             const uint4 *s4 = reinterpret_cast<const uint4 *>(cd.x_coeff + (row * L + l) * N);
             for (uint32_t i = threadIdx.x; i < (N >> 2); i += blockDim.x) reinterpret_cast<uint4 *>(dst)[i] = __ldg(s4 + i);
         } else if (cd.msrc == 1u) {
-            plan_fwd_ntt(cd.x_coeff + (row * L + l) * N, dst, cd, l, K, smem4);
+            plan_fwd_ntt(cd.x_coeff + (row * L + l) * N, dst, cd, l, K, smem4, hints);
         } else {
             const int32_t *src = reinterpret_cast<const int32_t *>(gz < G ? cd.x_coeff : cd.src_b) + row * N;
             uint32_t *a = reinterpret_cast<uint32_t *>(smem4);
@@ -1243,7 +1303,7 @@ __global__ void __launch_bounds__(kNttThreads, 2) k_plan_ntt(const CallDesc *__r
         }
         return;
     }
-    plan_fwd_ntt(cd.x_coeff + (size_t)it.poly * N, dst, cd, l, K, smem4);
+    plan_fwd_ntt(cd.x_coeff + (size_t)it.poly * N, dst, cd, l, K, smem4, hints);
 }
 
 template <int NJ>
@@ -1303,7 +1363,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<NJ>::value) k_plan_chan(co
 template <int G, int CS>
 __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, uint64_t *xempty,
                                          const uint32_t *ring, uint64_t *full, uint64_t *empty, uint32_t &buf,
-                                         uint32_t &ph, uint32_t nstages, uint32_t spin) {
+                                         uint32_t &ph, uint32_t nstages, uint32_t spin, uint32_t hints) {
     constexpr uint32_t LT = split_tile_log(CS == 4 ? 2 : (CS == 2 ? 1 : 0));
     constexpr uint32_t ROWS = kMacStageWords >> LT;  // weight rows of TS words per stage
     constexpr uint32_t NCH = ROWS / G;               // channels per full stage
@@ -1326,6 +1386,7 @@ __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, ui
     K.r32s = d.r32s;
     K.ones = d.ones;
     uint32_t *zc = d.z + jj * d.colstride + ((4u * CS * c) >> d.logs);
+    const uint64_t keep = l2_next(hints);  // the finishing kernel reads the folded sums next
     const uint32_t M = d.M, nch = d.nch, nst = d.nst;
     const uint32_t lanes = max(1u, (1u << d.logs) / (4u * CS));  // threads whose sums make one block
     const bool lead = (lane & (lanes - 1u)) == 0 && jj < d.ncol;
@@ -1359,7 +1420,7 @@ __device__ __forceinline__ bool mac_item(const MacDesc &d, const uint32_t *X, ui
                     v += __shfl_xor_sync(0xffffffffu, v, o);
                     v = min(v, v - K.q);
                 }
-                if (lead) zc[(size_t)(n + ch) * M] = v;
+                if (lead) st_l2(zc + (size_t)(n + ch) * M, v, keep);
             }
         }
         __syncwarp();
@@ -1388,7 +1449,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
                                                               const MacDesc *__restrict__ descs,
                                                               const uint32_t *__restrict__ offs,
                                                               uint32_t *__restrict__ status, uint32_t xw,
-                                                              uint32_t nring, uint32_t spin, uint32_t checks) {
+                                                              uint32_t nring, uint32_t spin, uint32_t checks,
+                                                              uint32_t hints) {
     extern __shared__ uint4 smem4[];
     uint64_t *xfull = reinterpret_cast<uint64_t *>(smem4);  // [2]
     uint64_t *xempty = xfull + 2;                            // [2]
@@ -1435,13 +1497,15 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
         bool ok = true;
         uint32_t issued = 0, xiss = 0;
         MacCopy c = copies[ib];
+        const uint64_t stream_once = l2_once(hints);  // weights: read once per run
         // the weights do not depend on the input-NTT kernel: the first ring
         // stages go out before waiting for it
         uint32_t st0 = min(nring, (c.nwords + kMacStageWords - 1) / kMacStageWords);
         for (uint32_t st = 0; st < st0; ++st, ++issued) {
             const uint32_t w = min(kMacStageWords, c.nwords - st * kMacStageWords);
             mbar_expect(full + st, w * 4u);
-            bulk_load(ring + st * kMacStageWords, c.w + (size_t)st * kMacStageWords, w * 4u, full + st);
+            bulk_load_l2(ring + st * kMacStageWords, c.w + (size_t)st * kMacStageWords, w * 4u, full + st,
+                         stream_once);
         }
         pdl_wait();
         for (uint32_t k = ib; k < ie && k < ib + 2; ++k, ++xiss)
@@ -1462,7 +1526,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
                 }
                 const uint32_t w = min(kMacStageWords, c.nwords - st * kMacStageWords);
                 mbar_expect(full + b, w * 4u);
-                bulk_load(ring + b * kMacStageWords, c.w + (size_t)st * kMacStageWords, w * 4u, full + b);
+                bulk_load_l2(ring + b * kMacStageWords, c.w + (size_t)st * kMacStageWords, w * 4u, full + b,
+                             stream_once);
             }
             // inputs of item k + 2 once the compute warps hold item k's in registers
             if (ok && k + 2 < ie) {
@@ -1500,13 +1565,13 @@ __global__ void __launch_bounds__(kThreads + 32, 2) k_plan_mac(const MacCopy *__
         const MacDesc d = dslot[xb];
         const uint32_t *X = Xb + xb * xw;
         switch (d.cls) {
-            case 0: ok = mac_item<1, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
-            case 1: ok = mac_item<1, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
-            case 2: ok = mac_item<1, 4>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
-            case 3: ok = mac_item<2, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
-            case 4: ok = mac_item<2, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
-            case 5: ok = mac_item<4, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
-            default: ok = mac_item<8, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin); break;
+            case 0: ok = mac_item<1, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin, hints); break;
+            case 1: ok = mac_item<1, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin, hints); break;
+            case 2: ok = mac_item<1, 4>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin, hints); break;
+            case 3: ok = mac_item<2, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin, hints); break;
+            case 4: ok = mac_item<2, 2>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin, hints); break;
+            case 5: ok = mac_item<4, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin, hints); break;
+            default: ok = mac_item<8, 1>(d, X, xempty + xb, ring, full, empty, buf, ph, nring, spin, hints); break;
         }
     }
     if (!ok) atomicOr(status, 1u);
@@ -2155,7 +2220,7 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         e = set_smem(k_plan_ntt, pl.smem_ntt);
         if (e != cudaSuccess) return e;
         k_plan_ntt<<<pl.n_ntt, kNttThreads, pl.smem_ntt, st>>>(pl.d_calls, pl.d_ntt, pl.d_status, pl.checks,
-                                                               pl.tw_stage, pl.wait_polls);
+                                                               pl.tw_stage, pl.wait_polls, pl.l2_hints);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -2164,7 +2229,7 @@ cudaError_t he_launch_plan(const he_plan_s &pl, cudaStream_t st, int phase) {
         e = launch_pdl(pl.mac_pdl != 0, k_plan_mac, pl.mac_ctas, kThreads + 32, pl.smem_mac, st,
                        (const MacCopy *)pl.d_mac_copy,
                        (const MacDesc *)pl.d_mac_desc, (const uint32_t *)pl.d_mac_offs, pl.d_status, pl.mac_xw,
-                       pl.mac_nst, pl.wait_polls, pl.checks);
+                       pl.mac_nst, pl.wait_polls, pl.checks, pl.l2_hints);
         if (e != cudaSuccess) return e;
     }
     if (pl.n_tc && phase != 3) {

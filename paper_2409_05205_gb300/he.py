@@ -61,7 +61,7 @@ class he_op_counts(ctypes.Structure):
 class he_plan_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in ("split", "mac_item_kb", "mac_ctas_per_sm", "fused_max_nj",
                                                "tc_min_batch", "fc_direct", "groups", "fin_parts",
-                                               "tw_smem", "mac_pdl")]
+                                               "tw_smem", "mac_pdl", "l2_hints")]
 
 
 class he_plan_info(ctypes.Structure):

@@ -153,12 +153,12 @@ def test_shape_and_argument_errors(he):
 def test_plan_tuning_default_and_validation(he):
     t = he.he_plan_tuning_default()
     assert t == dict(split=1, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=2, fc_direct=1,
-                     groups=1, fin_parts=1, tw_smem=0, mac_pdl=1)
+                     groups=1, fin_parts=1, tw_smem=0, mac_pdl=1, l2_hints=1)
     # a bad knob is refused before any call is looked at or any device work
     for bad in (dict(t, split=2), dict(t, mac_item_kb=48), dict(t, mac_ctas_per_sm=3),
                 dict(t, fused_max_nj=3), dict(t, tc_min_batch=3), dict(t, fc_direct=3), dict(t, groups=0),
                 dict(t, groups=4), dict(t, fin_parts=3), dict(t, tw_smem=2),
-                dict(t, mac_pdl=2)):
+                dict(t, mac_pdl=2), dict(t, l2_hints=3)):
         with pytest.raises(he.HEError) as ei:
             he.he_plan_create_tuned([(0, 16, he.HE_COEFF, 4096, 1)], bad)
         assert ei.value.status == he.HE_ERR_ARG and "tuning" in str(ei.value)

@@ -46,15 +46,15 @@ def _check(H, calls, refs):
 # transforms; groups > 1 runs the calls in that many groups on the plan's own
 # streams
 TUNINGS = [dict(split=1, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=4, fc_direct=1, groups=1,
-                fin_parts=1, tw_smem=1, mac_pdl=0),
+                fin_parts=1, tw_smem=1, mac_pdl=0, l2_hints=0),
            dict(split=0, mac_item_kb=128, mac_ctas_per_sm=2, fused_max_nj=16, tc_min_batch=1, fc_direct=0, groups=2,
-                fin_parts=2, tw_smem=0, mac_pdl=1),
+                fin_parts=2, tw_smem=0, mac_pdl=1, l2_hints=1),
            dict(split=1, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=2, tc_min_batch=8, fc_direct=1, groups=3,
-                fin_parts=4, tw_smem=1, mac_pdl=0),
+                fin_parts=4, tw_smem=1, mac_pdl=0, l2_hints=2),
            dict(split=1, mac_item_kb=64, mac_ctas_per_sm=2, fused_max_nj=4, tc_min_batch=2, fc_direct=0, groups=2,
-                fin_parts=2, tw_smem=0, mac_pdl=0),
+                fin_parts=2, tw_smem=0, mac_pdl=0, l2_hints=0),
            dict(split=0, mac_item_kb=32, mac_ctas_per_sm=1, fused_max_nj=8, tc_min_batch=4, fc_direct=1, groups=3,
-                fin_parts=4, tw_smem=0, mac_pdl=1)]
+                fin_parts=4, tw_smem=0, mac_pdl=1, l2_hints=1)]
 
 
 def test_every_tuning_gives_the_oracle_words():
