@@ -366,9 +366,9 @@ class Arm:
 # DRAM bytes (read + write) of one k_plan_mac launch, from an ncu capture of
 # this workload (dram__bytes_read.sum + dram__bytes_write.sum); None where no
 # capture of the current kernel exists.
-TRAFFIC = {"plain20_c10": 141.75e6,          # ncu --set full of one launch (one CTA per SM, 128 KB items, the
-                                             # in-flight tuning): read 136.64 MB + write 5.11 MB (two CTAs per
-                                             # SM, 64 KB items: 141.84 MB)
+TRAFFIC = {"plain20_c10": 139.99e6,          # ncu --set full of one launch (one CTA per SM, 128 KB items, weights
+                                             # evicted first: the in-flight tuning): read 136.63 MB + write
+                                             # 3.36 MB
            "plain20_c10_masked": 269.68e6,   # read 264.23 MB + write 5.45 MB
            "f3_d20_w3": 1250.86e6}           # read 1168.25 MB + write 82.60 MB
 
