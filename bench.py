@@ -258,14 +258,19 @@ class Arm:
         for i in range(len(self.calls)):
             self._layer(r, i, stream, None if evs is None else evs[i])
 
+    def plan_calls(self, r):
+        """Replica r's layer calls, in plan form."""
+        H = self.H
+        return [(self.models[r].banks[i], self.x[r][i], H.HE_COEFF, self.y[r][i], c["B"])
+                for i, c in enumerate(self.calls)]
+
     def make_plans(self):
         """One plan per replica over all layer calls, and a CUDA graph of each."""
         torch, H = self.torch, self.H
         self.plans, self.graphs = [], []
         s = torch.cuda.Stream()
         for r in range(self.R):
-            calls = [(self.models[r].banks[i], self.x[r][i], H.HE_COEFF, self.y[r][i], c["B"])
-                     for i, c in enumerate(self.calls)]
+            calls = self.plan_calls(r)
             if NO_AUTOTUNE:
                 self.tuning = dict(H.he_plan_tuning_default(), **TUNING_OVERRIDE)
                 pl = H.he_plan_create_tuned(calls, self.tuning)
@@ -577,6 +582,7 @@ def run_ours(args, rank, world, device):
 
     # ---------------- e2e: pinned host buffers, H2D + plan + D2H every step
     e2e = run_e2e(arm, args)
+    one_run = None if NO_AUTOTUNE else one_run_tuning(torch, arm, K, W, k_phase, stream)
 
     ch_bytes, ntt_bytes, bfly = arm.algorithmic()
     ntt_bfly, fin_bfly = arm.butterflies(info["form"])
@@ -665,6 +671,8 @@ def run_ours(args, rank, world, device):
                            "replays on their own streams), one knob at a time; the same plans give the one-in-"
                            "flight and latency figures") if not NO_AUTOTUNE else "fixed (--no-autotune / --tuning)"},
         "e2e": e2e,
+        "one_run_tuning": (dict(one_run, mac_frac=mac_bytes / (one_run["mac_avg_launch_ms"] * 1e-3) / 1e9 / hbm)
+                           if one_run else None),
         "gpu_launches": info["kernels_per_run"] * K,
         "clocks": clk,
         "windows": {"layers_per_s": [arm.units * K / (w * 1e-3) for w in windows],
@@ -674,6 +682,64 @@ def run_ours(args, rank, world, device):
     }
     arm.free()
     return res
+
+
+def one_run_tuning(torch, arm, K, W, k_phase, stream):
+    """The same workload on plans autotuned for one run at a time
+    (he_plan_autotune), beside the headline's in-flight tuning: its rate with
+    one inference in flight, its per-inference latency, and its MAC kernel
+    alone (launched back to back over the replicas)."""
+    H = arm.H
+    s = torch.cuda.Stream()
+    plans, graphs, tuning = [], [], None
+    try:
+        for r in range(arm.R):
+            pl, tuning = H.he_plan_autotune(arm.plan_calls(r), 30, s)
+            plans.append(pl)
+        torch.cuda.synchronize()
+        for pl in plans:
+            with torch.cuda.stream(s):
+                H.he_plan_run(pl, s)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                H.he_plan_run(pl, s)
+            graphs.append(g)
+        torch.cuda.synchronize()
+        k1 = min(K, 5000)
+        replay_window(torch, graphs, W, [stream])
+        t0, t1 = replay_window(torch, graphs, k1, [stream])
+        torch.cuda.synchronize()
+        one_ms = t0.elapsed_time(t1)
+        k_lat = min(K, 2000)
+        ev = [_events(2) for _ in range(k_lat)]
+        with torch.cuda.stream(stream):
+            for k in range(k_lat):
+                ev[k][0].record(stream)
+                graphs[k % len(graphs)].replay()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        lat = [a.elapsed_time(b) for a, b in ev]
+        m0, m1 = _events(2)
+        with torch.cuda.stream(stream):
+            for k in range(W):
+                H.he_plan_run_phase(plans[k % len(plans)], H.HE_PHASE_MAC, stream)
+            m0.record(stream)
+            for k in range(k_phase):
+                H.he_plan_run_phase(plans[k % len(plans)], H.HE_PHASE_MAC, stream)
+            m1.record(stream)
+        torch.cuda.synchronize()
+        return {"tuning": tuning, "one_in_flight": arm.units * k1 / (one_ms * 1e-3), "unit": "layers/s",
+                "ms_per_step": one_ms / k1,
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "mac_avg_launch_ms": m0.elapsed_time(m1) / k_phase,
+                "how": "plans of the same calls autotuned by he_plan_autotune (one run at a time); "
+                       f"{k1} graph replays on one stream; the MAC kernel {k_phase} times back to back"}
+    finally:
+        del graphs
+        torch.cuda.synchronize()
+        for pl in plans:
+            H.he_plan_destroy(pl)
 
 
 def run_e2e(arm, args):
