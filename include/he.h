@@ -528,7 +528,7 @@ he_status he_plan_create(const he_layer_call *calls, uint32_t ncalls, he_plan_t 
  *                    input-NTT kernel: its CTAs start streaming weights while
  *                    the transforms run, then wait for them; 0: an ordinary
  *                    launch, after the input-NTT kernel has finished.
- *   l2_hints         L2 eviction priorities of the input-NTT and split MAC
+ *   l2_hints         L2 eviction priorities of the input-NTT and MAC
  *                    kernels' accesses: 1 (default): the weights and the
  *                    coefficient-domain inputs, read once per run, are
  *                    evicted first, so that they do not push out the NTT

@@ -2392,7 +2392,7 @@ he_status he_plan_autotune_inflight(const he_layer_call *calls, uint32_t ncalls,
         if (has_fused) try_knob(&he_plan_tuning::fused_max_nj, {16u, 8u, 4u, 2u});
         if (info.ntt_items) try_knob(&he_plan_tuning::tw_smem, {0u, 1u});
         if (info.mac_items || info.tc_items) try_knob(&he_plan_tuning::mac_pdl, {1u, 0u});
-        if (info.mac_items) try_knob(&he_plan_tuning::l2_hints, {1u, 2u, 0u});
+        if (info.mac_items || info.tc_items) try_knob(&he_plan_tuning::l2_hints, {1u, 2u, 0u});
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache.push_back({key, cur});
     }

@@ -117,11 +117,24 @@ __device__ __forceinline__ void bar_drain(uint64_t *b, uint32_t parity) {
 
 __device__ __forceinline__ void pdl_wait_tc() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *b) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     su32(dst)),
-                 "l"(src), "r"(bytes), "r"(su32(b))
-                 : "memory");
+// One bulk copy global -> shared counted on `b`, with an L2 cache policy
+// (createpolicy)
+__device__ __forceinline__ void bulk_g2s_l2(void *dst, const void *src, uint32_t bytes, uint64_t *b, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+            "r"(su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(b)), "l"(pol)
+        : "memory");
+}
+// The weights' L2 policy of a plan run (he_plan_tuning::l2_hints): evicted
+// first (read once per run), or normal.
+__device__ __forceinline__ uint64_t tc_weight_policy(uint32_t hints) {
+    uint64_t p;
+    if (hints)
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    else
+        asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 __device__ __forceinline__ void tensor5_g2s(void *dst, const void *tmap, uint32_t c0, uint32_t c1, uint64_t *b) {
     asm volatile(
@@ -219,7 +232,7 @@ __device__ __forceinline__ void limbs32(const uint32_t (&w)[32], uint32_t (&r)[3
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restrict__ calls,
                                                           const TcItem *__restrict__ items,
                                                           const uint32_t *__restrict__ offs,
-                                                          uint32_t *__restrict__ status) {
+                                                          uint32_t *__restrict__ status, uint32_t hints) {
     extern __shared__ __align__(1024) uint8_t smem[];
     TcBars &bars = *reinterpret_cast<TcBars *>(smem);
     uint8_t *wring = smem + kOffW;
@@ -272,6 +285,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
         if (lane == 0) {
             uint32_t ws = 0, xs = 0, pre = 0;
             bool ok = true;
+            const uint64_t wpol = tc_weight_policy(hints);
             {
                 const TcItem item = items[ib];
                 const TcCall &C = calls[item.call];
@@ -282,8 +296,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                     for (uint32_t off = 0; off < tile_words && pre < nst; off += kWStageBytes / 4u, ++pre) {
                         const uint32_t bytes = min(kWStageBytes, (tile_words - off) * 4u);
                         bar_expect(&bars.w_full[pre], bytes);
-                        bulk_g2s(wring + pre * kWStageBytes, src + (size_t)ch * tile_words + off, bytes,
-                                 &bars.w_full[pre]);
+                        bulk_g2s_l2(wring + pre * kWStageBytes, src + (size_t)ch * tile_words + off, bytes,
+                                    &bars.w_full[pre], wpol);
                     }
             }
             pdl_wait_tc();
@@ -319,7 +333,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_mac(const TcCall *__restri
                             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                             const uint32_t bytes = min(kWStageBytes, (tile_words - off) * 4u);
                             bar_expect(&bars.w_full[st], bytes);
-                            bulk_g2s(wring + st * kWStageBytes, src + off, bytes, &bars.w_full[st]);
+                            bulk_g2s_l2(wring + st * kWStageBytes, src + off, bytes, &bars.w_full[st], wpol);
                             ++ws;
                         }
                     }
@@ -652,7 +666,7 @@ cudaError_t he_launch_tc_mac(const he_plan_s &pl, cudaStream_t st, bool pdl) {
     cfg.attrs = at;
     cfg.numAttrs = pdl ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, k_tc_mac, (const TcCall *)pl.d_tc_calls, (const TcItem *)pl.d_tc_items,
-                              (const uint32_t *)pl.d_tc_offs, pl.d_status);
+                              (const uint32_t *)pl.d_tc_offs, pl.d_status, pl.l2_hints);
 }
 
 cudaError_t he_tc_prepare() {
