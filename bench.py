@@ -374,8 +374,8 @@ class Arm:
 TRAFFIC = {"plain20_c10": 139.99e6,          # ncu --set full of one launch (one CTA per SM, 128 KB items, weights
                                              # evicted first: the in-flight tuning): read 136.63 MB + write
                                              # 3.36 MB
-           "plain20_c10_masked": 269.68e6,   # read 264.23 MB + write 5.45 MB
-           "f3_d20_w3": 1250.86e6}           # read 1168.25 MB + write 82.60 MB
+           "plain20_c10_masked": 267.76e6,   # read 264.17 MB + write 3.59 MB (default tuning)
+           "f3_d20_w3": 1207.49e6}           # read 1165.21 MB + write 42.28 MB (default tuning)
 
 
 def _traffic(name):
